@@ -1,0 +1,636 @@
+/*
+ * dscreen_oracle.c -- plain, slow FP64 CPU oracle for dynamic screening
+ * (Bonnefoy, Emiya, Ralaivola, Gribonval, "Dynamic Screening: Accelerating
+ * First-Order Algorithms for the Lasso and Group-Lasso", arXiv 1412.4080).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is compiled and called by the test
+ * suite, by the smoke check and by the CPU-baseline leg of the benchmark.
+ * The product (the CUDA library and its Python binding) never links, loads
+ * or calls it, and it shares no code, header, table or helper with it.
+ *
+ * Everything is double precision, single threaded, written as plain loops
+ * so that each step can be checked against the paper by eye:
+ *
+ *   problem         eq. (1): min_x 1/2 ||D x - y||^2 + lambda * Omega(x)
+ *   Lasso           eq. (lasso), Omega = ||x||_1, prox = soft threshold (eq. softTh)
+ *   Group-Lasso     eq. (group-lasso), Omega = sum_g w_g ||x_g||_2,
+ *                   prox = group soft threshold (eq. gr_softTh)
+ *   lambda_*        Sec. 2.2.2 (Lasso: ||D^T y||_inf), eq. (gstar) (groups)
+ *   updates         Table 1 (ISTA and FISTA rows)
+ *   general loop    Algorithm 3 (screen after each update, cumulative set)
+ *   dual scaling    Lemma 8 (feasible scaled dual point closest to y/lambda)
+ *   tests           Lemma 2 (SAFE), Lemma 3 (DST3), Lemma 4 (dynamic Dome),
+ *                   Lemma 5 (GSAFE), Lemma 6 (DGST3), Lemma 7 (sphere test)
+ *   static variant  Algorithm 1 / Algorithm 4 (test once at theta = -y)
+ *
+ * Readings of the paper that this file takes (where the text is silent,
+ * garbled or specialised):
+ *  - theta follows Table 1's sign (theta = D u - y); the clip in Lemma 8
+ *    absorbs the sign.  ||theta|| = 0 gives mu = 0.
+ *  - the clip of mu uses the correlations of the atoms still active
+ *    (Algorithm 5 uses the z of the screened dictionary).
+ *  - lambda_* ties and d_*: lowest index attaining the maximum; sign +1
+ *    when the correlation is 0.
+ *  - atoms of any norm: the Lasso sphere tests are the sphere test of
+ *    Lemma 7 with singleton groups, (1 - |d_i^T c|) / ||d_i|| > r, which is
+ *    Lemmas 2/3 when ||d_i|| = 1.  DST3 projects y/lambda on the hyperplane
+ *    d_*^T theta = 1 (centre y/lambda - psi d_* / ||d_*||^2, offset
+ *    psi / ||d_*||, psi = lambda_* / lambda - 1), which is Lemma 3's centre
+ *    for a unit d_*.
+ *  - Lemma 4 (Dome): the printed inequality compares y^T d_i (the "x^T" and
+ *    the stray "l(" are typos), and its piecewise constants are those of the
+ *    static test (theta = y, ||y|| = 1).  The dynamic test used here is the
+ *    exact maximum of |d^T theta| over the dome {||theta - y/lambda|| <= R,
+ *    n^T theta <= 1/||d_*||} for the normalised atom d = d_i/||d_i|| and
+ *    normal n = d_* / ||d_*||; it reduces to the printed lemma when theta = y,
+ *    ||y|| = 1 and the atoms have unit norm.
+ *  - DGST3 radius: Lemma 6's sqrt(||y/lambda - mu theta||^2 -
+ *    ||y/lambda - c||^2), clamped at 0 (the appendix prints the operands
+ *    of the difference in the opposite order).
+ *  - Lemma 8 uses the group of the constraint (the subscript g(i) there is
+ *    a typo) and a closed feasible set.
+ *  - the duality gap pairs the primal point xbar_t of the iteration with
+ *    the dual point v_t = mu_t theta_t built in the same iteration; the
+ *    stopping rule is gap <= tol * 1/2 ||y||^2 (= tol * P(0)).
+ *  - step size: fixed L >= ||D||_2^2 (power iteration, then * (1 + 1e-6));
+ *    the paper's backtracking constants are not given.
+ *  - rounding at ties: every test screens only when its margin exceeds
+ *    OR_MARGIN = 1e-12 (the paper's strict inequalities, made robust to the
+ *    last-bit rounding of double precision).  Without it the atom d_*, which
+ *    lies exactly on its own half-space boundary (d_*^T theta <= 1), can be
+ *    screened by the Dome / DST3 tests through a rounding error.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_ISTA 0
+#define OR_FISTA 1
+
+#define OR_TEST_NONE 0
+#define OR_TEST_SAFE 1
+#define OR_TEST_DST3 2
+#define OR_TEST_DOME 3
+#define OR_TEST_GSAFE 4
+#define OR_TEST_DGST3 5
+
+/* history columns, one row per iteration */
+#define OR_H_ACTIVE 0 /* atoms still active after the screening of iteration t */
+#define OR_H_NNZ 1    /* ||xbar_t||_0 */
+#define OR_H_R 2      /* R_t = ||y/lambda - mu_t theta_t|| */
+#define OR_H_RADIUS 3 /* radius used by the test (R_t or the DST3/DGST3 radius) */
+#define OR_H_GAP 4    /* P(xbar_t) - Dual(mu_t theta_t) */
+#define OR_H_MU 5     /* mu_t */
+#define OR_NH 6
+
+#define OR_MARGIN 1e-12
+
+typedef struct {
+    int alg;            /* OR_ISTA / OR_FISTA */
+    int test;           /* OR_TEST_* */
+    int dynamic;        /* 1: test every iteration (Alg. 3); 0: once, at theta = -y (Alg. 1) */
+    int max_iter;       /* iteration cap */
+    double tol_gap_rel; /* stop when gap <= tol * 1/2 ||y||^2; 0 runs max_iter iterations */
+    double L;           /* step constant; <= 0: power iteration on D^T D, * (1 + 1e-6) */
+} or_options;
+
+typedef struct {
+    int iters;
+    int n_active;  /* atoms not screened at exit */
+    int nnz;
+    int status;    /* 0 converged (or max_iter with tol = 0), 1 max_iter reached, -1 bad input */
+    double gap;
+    double primal;
+    double dual;
+    double lambda_max;
+    double L;
+} or_result;
+
+/* ----------------------------------------------------------------- helpers */
+
+static double col_dot(const double* D, int64_t ld, int64_t i, const double* v, int64_t N)
+{
+    const double* d = D + i * ld;
+    double s = 0.0;
+    for (int64_t n = 0; n < N; n++) s += d[n] * v[n];
+    return s;
+}
+
+static double vec_dot(const double* a, const double* b, int64_t n)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* Group layout: goff == NULL means the Lasso, i.e. K singleton groups with weight 1. */
+static int64_t n_groups(const int64_t* goff, int64_t nG, int64_t K) { return goff ? nG : K; }
+static int64_t g_lo(const int64_t* goff, int64_t g) { return goff ? goff[g] : g; }
+static int64_t g_hi(const int64_t* goff, int64_t g) { return goff ? goff[g + 1] : g + 1; }
+static double g_w(const double* w, int64_t g) { return w ? w[g] : 1.0; }
+
+/* ------------------------------------------------------- lambda_* (Sec. 2.2) */
+
+/* b = D^T y; Lasso: lambda_* = ||D^T y||_inf (Sec. 2.2.2); groups: eq. (gstar),
+ * lambda_* = max_g ||D_g^T y|| / w_g.  *star = lowest index attaining it. */
+int or_lambda_max(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
+                  const int64_t* goff, const double* w, int64_t nG,
+                  double* lambda_max, int64_t* star, double* b)
+{
+    if (!D || !y || !b || N <= 0 || K <= 0 || ld < N) return -1;
+    if (!goff) w = NULL; /* the Lasso: singleton groups of weight 1 */
+    for (int64_t i = 0; i < K; i++) b[i] = col_dot(D, ld, i, y, N);
+    int64_t G = n_groups(goff, nG, K);
+    double best = -1.0;
+    int64_t arg = 0;
+    for (int64_t g = 0; g < G; g++) {
+        double s = 0.0;
+        for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) s += b[i] * b[i];
+        double v = sqrt(s) / g_w(w, g);
+        if (v > best) { best = v; arg = g; }
+    }
+    *lambda_max = best;
+    if (star) *star = arg;
+    return 0;
+}
+
+/* ---------------------------------------------- spectral norms (step size) */
+
+/* ||D||_2^2 by the power method on D^T D, from the all-ones start vector,
+ * until the relative change of the Rayleigh quotient is <= tol. */
+double or_spectral_norm_sq(const double* D, int64_t N, int64_t K, int64_t ld, double tol, int max_iter)
+{
+    double* v = (double*)malloc(sizeof(double) * K);
+    double* u = (double*)malloc(sizeof(double) * N);
+    for (int64_t i = 0; i < K; i++) v[i] = 1.0 / sqrt((double)K);
+    double rq = 0.0;
+    for (int it = 0; it < max_iter; it++) {
+        for (int64_t n = 0; n < N; n++) u[n] = 0.0;
+        for (int64_t i = 0; i < K; i++)
+            for (int64_t n = 0; n < N; n++) u[n] += D[i * ld + n] * v[i];
+        double rq_new = vec_dot(u, u, N); /* v^T D^T D v with ||v|| = 1 */
+        double nv = 0.0;
+        for (int64_t i = 0; i < K; i++) { v[i] = col_dot(D, ld, i, u, N); nv += v[i] * v[i]; }
+        nv = sqrt(nv);
+        if (nv == 0.0) { rq = 0.0; break; }
+        for (int64_t i = 0; i < K; i++) v[i] /= nv;
+        int done = it > 0 && fabs(rq_new - rq) <= tol * rq_new;
+        rq = rq_new;
+        if (done) break;
+    }
+    free(v);
+    free(u);
+    return rq;
+}
+
+/* Largest eigenvalue of the symmetric m x m matrix A (row-major, destroyed)
+ * by cyclic Jacobi rotations; returns max diagonal + Frobenius norm of the
+ * remaining off-diagonal part, an upper bound (Weyl) that is tight once
+ * the sweeps converge. */
+static double jacobi_max_eig(double* A, int m)
+{
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < m; p++)
+            for (int q = 0; q < m; q++)
+                if (p != q) off += A[p * m + q] * A[p * m + q];
+        if (off == 0.0) break;
+        for (int p = 0; p < m - 1; p++) {
+            for (int q = p + 1; q < m; q++) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                double app = A[p * m + p], aqq = A[q * m + q];
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < m; k++) { /* A <- A J (columns p, q) */
+                    double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = c * akp - s * akq;
+                    A[k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; k++) { /* A <- J^T A (rows p, q) */
+                    double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = c * apk - s * aqk;
+                    A[q * m + k] = s * apk + c * aqk;
+                }
+            }
+        }
+    }
+    double mx = A[0], off = 0.0;
+    for (int p = 0; p < m; p++) {
+        if (A[p * m + p] > mx) mx = A[p * m + p];
+        for (int q = 0; q < m; q++)
+            if (p != q) off += A[p * m + q] * A[p * m + q];
+    }
+    return mx + sqrt(off);
+}
+
+/* ||D_g||_2 (spectral norm of the columns c0..c1-1), used by Lemmas 5-7. */
+double or_group_spec_norm(const double* D, int64_t N, int64_t ld, int64_t c0, int64_t c1)
+{
+    int m = (int)(c1 - c0);
+    if (m <= 0) return 0.0;
+    double* A = (double*)malloc(sizeof(double) * m * m);
+    for (int p = 0; p < m; p++)
+        for (int q = 0; q < m; q++) A[p * m + q] = vec_dot(D + (c0 + p) * ld, D + (c0 + q) * ld, N);
+    double e = jacobi_max_eig(A, m);
+    free(A);
+    return sqrt(e > 0.0 ? e : 0.0);
+}
+
+/* --------------------------------------------------- Lemma 8: dual scaling */
+
+/* mu = [theta^T y / (lambda ||theta||^2)] projected on [-1/m, 1/m], where m is
+ * max_i |d_i^T theta| (Lasso) or max_g ||D_g^T theta|| / w_g (groups), i.e.
+ * 1/m = s_min of Lemma 8.  ||theta|| = 0 gives 0; m = 0 leaves it unclipped. */
+double or_dual_scaling(const double* theta, const double* y, int64_t N, double lambda, double m)
+{
+    double tt = vec_dot(theta, theta, N);
+    if (tt == 0.0) return 0.0;
+    double s = vec_dot(theta, y, N) / (lambda * tt);
+    if (m > 0.0) {
+        double lim = 1.0 / m;
+        if (s > lim) s = lim;
+        if (s < -lim) s = -lim;
+    }
+    return s;
+}
+
+/* --------------------------------------------------- Lemma 4: dynamic Dome */
+
+/* Maximum of d^T theta over the dome {||theta - c0|| <= R} cap {n^T theta <= off},
+ * for unit d and unit n with t = n^T d, dc0 = d^T c0 and psi = n^T c0 - off >= 0
+ * (the distance from c0 to the hyperplane, c0 lying outside).  If the unconstrained
+ * maximiser c0 + R d satisfies the half-space (t R <= -psi) the value is dc0 + R;
+ * otherwise the maximum is on the circle where the sphere meets the hyperplane:
+ * dc0 - psi t + sqrt(R^2 - psi^2) sqrt(1 - t^2). */
+double or_dome_max(double dc0, double t, double psi, double R)
+{
+    if (t * R <= -psi) return dc0 + R;
+    double rho2 = R * R - psi * psi;
+    double s2 = 1.0 - t * t;
+    return dc0 - psi * t + sqrt(rho2 > 0 ? rho2 : 0.0) * sqrt(s2 > 0 ? s2 : 0.0);
+}
+
+/* ------------------------------------------------------------------ solver */
+
+typedef struct {
+    /* per-problem data */
+    const double *D, *y;
+    int64_t N, K, ld, nG;
+    const int64_t* goff;
+    const double* w;
+    int lasso;
+    double lambda, lambda_star;
+    int64_t star;
+    int test;
+    /* per-test data (fixed for the whole solve: Sec. 2.2.4 "D^T c once for all") */
+    double* dtc;      /* Lasso: d_i^T c, K entries; groups: ||D_g^T c||, G entries */
+    double* nrm;      /* Lasso: ||d_i||; groups: ||D_g||_2 */
+    double delta;     /* ||y/lambda - c|| for DST3 / DGST3 (0 for SAFE / GSAFE) */
+    /* Dome data (Lasso only) */
+    double* b;        /* d_i^T y */
+    double* tdome;    /* (d_i / ||d_i||)^T (d_* / ||d_*||) */
+    double psi_dome;  /* (lambda_* / lambda - 1) / ||d_*|| */
+} or_ctx;
+
+/* Prepare the centre c of the chosen region and D^T c (Lemmas 2, 3, 5, 6). */
+static int prepare_test(or_ctx* c, const double* b)
+{
+    int64_t N = c->N, K = c->K, ld = c->ld;
+    int64_t G = n_groups(c->goff, c->nG, K);
+    double lam = c->lambda;
+    c->delta = 0.0;
+    if (c->test == OR_TEST_NONE) return 0;
+    if (c->test == OR_TEST_SAFE || c->test == OR_TEST_DST3 || c->test == OR_TEST_DOME) {
+        if (!c->lasso) return -1;
+    } else if (c->test != OR_TEST_GSAFE && c->test != OR_TEST_DGST3) {
+        return -1;
+    }
+    double* cvec = (double*)malloc(sizeof(double) * N);
+    for (int64_t n = 0; n < N; n++) cvec[n] = c->y[n] / lam; /* SAFE / GSAFE centre: y / lambda */
+    double psi = c->lambda_star / lam - 1.0;
+
+    if (c->test == OR_TEST_DST3 || c->test == OR_TEST_DOME) {
+        /* d_* = argmax over {+-d_i} of d^T y: sign(b_{i*}) d_{i*} (Lemma 3) */
+        int64_t is = c->star;
+        double sg = b[is] < 0 ? -1.0 : 1.0;
+        const double* ds = c->D + is * ld;
+        double ns2 = vec_dot(ds, ds, N);
+        /* projection of y/lambda on {d_*^T theta = 1}: d_*^T y / lambda - 1 = psi */
+        for (int64_t n = 0; n < N; n++) cvec[n] -= psi / ns2 * sg * ds[n];
+        c->delta = psi / sqrt(ns2);
+        if (c->test == OR_TEST_DOME) {
+            c->psi_dome = psi / sqrt(ns2);
+            for (int64_t i = 0; i < K; i++) {
+                double ni = sqrt(vec_dot(c->D + i * ld, c->D + i * ld, N));
+                c->tdome[i] = sg * vec_dot(c->D + i * ld, ds, N) / (ni * sqrt(ns2));
+            }
+        }
+    } else if (c->test == OR_TEST_DGST3) {
+        /* n = D_{g*} D_{g*}^T y / lambda_*  (Lemma 6) */
+        int64_t gs = c->star;
+        double* nv = (double*)calloc(N, sizeof(double));
+        for (int64_t i = g_lo(c->goff, gs); i < g_hi(c->goff, gs); i++)
+            for (int64_t n = 0; n < N; n++) nv[n] += c->D[i * ld + n] * b[i] / c->lambda_star;
+        double nn = vec_dot(nv, nv, N);
+        double wg = g_w(c->w, gs);
+        double coef = vec_dot(nv, c->y, N) / lam - wg * wg;
+        /* c = (I - n n^T/||n||^2) y/lambda + n w^2/||n||^2 = y/lambda - (n^T y/lambda - w^2) n/||n||^2 */
+        for (int64_t n = 0; n < N; n++) cvec[n] -= coef * nv[n] / nn;
+        c->delta = fabs(coef) / sqrt(nn);
+        free(nv);
+    }
+
+    if (c->lasso) {
+        for (int64_t i = 0; i < K; i++) {
+            c->dtc[i] = col_dot(c->D, ld, i, cvec, N);
+            c->nrm[i] = sqrt(vec_dot(c->D + i * ld, c->D + i * ld, N));
+        }
+    } else {
+        for (int64_t g = 0; g < G; g++) {
+            double s = 0.0;
+            for (int64_t i = g_lo(c->goff, g); i < g_hi(c->goff, g); i++) {
+                double v = col_dot(c->D, ld, i, cvec, N);
+                s += v * v;
+            }
+            c->dtc[g] = sqrt(s);
+            c->nrm[g] = or_group_spec_norm(c->D, N, ld, g_lo(c->goff, g), g_hi(c->goff, g));
+        }
+    }
+    free(cvec);
+    return 0;
+}
+
+/* Apply the test with dual point theta (whose correlations with the active
+ * atoms are z, m = max |z| or max ||z_g||/w_g over active groups).  Marks newly
+ * screened groups in scr_group[] with iteration number it.  Returns mu. */
+static double screen(or_ctx* c, const double* theta, double m, const char* active_g,
+                     int* scr_group, int it, double* R_out, double* rad_out)
+{
+    int64_t N = c->N, K = c->K;
+    int64_t G = n_groups(c->goff, c->nG, K);
+    double lam = c->lambda;
+    /* Lemma 8: mu, v = mu theta; radius R = ||y/lambda - v|| */
+    double mu = or_dual_scaling(theta, c->y, N, lam, m);
+    double R2 = 0.0;
+    for (int64_t n = 0; n < N; n++) {
+        double d = c->y[n] / lam - mu * theta[n];
+        R2 += d * d;
+    }
+    double R = sqrt(R2);
+    double rad = R;
+    if (c->test == OR_TEST_DST3 || c->test == OR_TEST_DGST3) {
+        double r2 = R2 - c->delta * c->delta; /* Lemma 3 / Lemma 6 radius */
+        rad = sqrt(r2 > 0 ? r2 : 0.0);
+    }
+    *R_out = R;
+    *rad_out = rad;
+    if (c->test == OR_TEST_NONE) return mu;
+    for (int64_t g = 0; g < G; g++) {
+        if (!active_g[g]) continue;
+        int kill = 0;
+        if (c->test == OR_TEST_DOME) {
+            /* Lemma 4 (dynamic form): max over the dome of |d_i^T theta| < 1 */
+            double ni = c->nrm[g];
+            double dc0 = c->b[g] / (lam * ni); /* (d_i/||d_i||)^T y / lambda */
+            double up = or_dome_max(dc0, c->tdome[g], c->psi_dome, R);
+            double lo = or_dome_max(-dc0, -c->tdome[g], c->psi_dome, R);
+            kill = 1.0 / ni - up > OR_MARGIN && 1.0 / ni - lo > OR_MARGIN;
+        } else if (c->lasso) {
+            /* Lemma 2 / Lemma 3: (1 - |d_i^T c|) / ||d_i|| > r */
+            kill = (1.0 - fabs(c->dtc[g])) / c->nrm[g] - rad > OR_MARGIN;
+        } else {
+            /* Lemma 5 / Lemma 6 via Lemma 7: (w_g - ||D_g^T c||) / ||D_g|| > r */
+            kill = (g_w(c->w, g) - c->dtc[g]) / c->nrm[g] - rad > OR_MARGIN;
+        }
+        if (kill) scr_group[g] = it;
+    }
+    return mu;
+}
+
+/* Proximal step of Table 1 on group g: x_g = prox_{t Omega}(v_g)
+ * (soft threshold eq. softTh, or group soft threshold eq. gr_softTh). */
+static void prox_group(const or_ctx* c, int64_t g, const double* v, double t, double* x)
+{
+    int64_t lo = g_lo(c->goff, g), hi = g_hi(c->goff, g);
+    if (c->lasso) {
+        double a = fabs(v[lo]) - t;
+        x[lo] = a > 0 ? (v[lo] > 0 ? a : -a) : 0.0;
+        return;
+    }
+    double s = 0.0;
+    for (int64_t i = lo; i < hi; i++) s += v[i] * v[i];
+    double nv = sqrt(s);
+    double f = nv > 0 ? (nv - t * g_w(c->w, g)) / nv : 0.0;
+    if (f < 0) f = 0.0;
+    for (int64_t i = lo; i < hi; i++) x[i] = f * v[i];
+}
+
+static double omega(const or_ctx* c, const double* x)
+{
+    int64_t G = n_groups(c->goff, c->nG, c->K);
+    double s = 0.0;
+    for (int64_t g = 0; g < G; g++) {
+        double q = 0.0;
+        for (int64_t i = g_lo(c->goff, g); i < g_hi(c->goff, g); i++) q += x[i] * x[i];
+        s += g_w(c->w, g) * sqrt(q);
+    }
+    return s;
+}
+
+/* Solve eq. (1) by Algorithm 3 with the ISTA or FISTA update of Table 1.
+ * x_out: K coefficients.  scr_iter (nullable): per atom, the iteration at which it
+ * was screened (0 = never, -1 = by the static test before the loop).
+ * hist (nullable): max_iter rows of OR_NH doubles. */
+int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y, double lambda,
+             const int64_t* goff, const double* w, int64_t nG,
+             const or_options* opt, const double* x0,
+             double* x_out, int* scr_iter, double* hist, or_result* res)
+{
+    if (!D || !y || !x_out || !opt || !res || N <= 0 || K <= 0 || ld < N || !(lambda > 0)) return -1;
+    if (!goff) w = NULL; /* the Lasso: singleton groups of weight 1 */
+    if (goff) {
+        if (nG <= 0 || goff[0] != 0 || goff[nG] != K) return -1;
+        for (int64_t g = 0; g < nG; g++)
+            if (goff[g + 1] <= goff[g] || (w && !(w[g] > 0))) return -1;
+    }
+    memset(res, 0, sizeof(*res));
+    or_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.D = D; c.y = y; c.N = N; c.K = K; c.ld = ld; c.goff = goff; c.w = w; c.nG = nG;
+    c.lasso = goff == NULL;
+    c.lambda = lambda;
+    c.test = opt->test;
+    int64_t G = n_groups(goff, nG, K);
+
+    double* b = (double*)malloc(sizeof(double) * K);
+    or_lambda_max(D, N, K, ld, y, goff, w, nG, &c.lambda_star, &c.star, b);
+    res->lambda_max = c.lambda_star;
+    double yy = vec_dot(y, y, N);
+
+    for (int64_t i = 0; i < K; i++) x_out[i] = 0.0;
+    if (scr_iter)
+        for (int64_t i = 0; i < K; i++) scr_iter[i] = 0;
+    /* lambda >= lambda_*: x = 0, theta = y/lambda is dual optimal (Sec. 2.2.2, eq. gstar) */
+    if (lambda >= c.lambda_star) {
+        res->primal = 0.5 * yy;
+        res->dual = 0.5 * yy;
+        res->gap = 0.0;
+        res->n_active = 0;
+        free(b);
+        return 0;
+    }
+
+    double L = opt->L;
+    if (!(L > 0)) L = or_spectral_norm_sq(D, N, K, ld, 1e-12, 100000) * (1.0 + 1e-6);
+    res->L = L;
+
+    c.dtc = (double*)malloc(sizeof(double) * (size_t)G);
+    c.nrm = (double*)malloc(sizeof(double) * (size_t)G);
+    c.b = b;
+    c.tdome = (double*)malloc(sizeof(double) * (size_t)K);
+    if (prepare_test(&c, b) != 0) {
+        free(b); free(c.dtc); free(c.nrm); free(c.tdome);
+        res->status = -1;
+        return -1;
+    }
+
+    double* x = (double*)calloc(K, sizeof(double));     /* xbar_{t-1} */
+    double* u = (double*)calloc(K, sizeof(double));     /* ubar_{t-1} */
+    double* xn = (double*)calloc(K, sizeof(double));    /* x_t */
+    double* v = (double*)calloc(K, sizeof(double));
+    double* z = (double*)calloc(K, sizeof(double));
+    double* theta = (double*)calloc(N, sizeof(double));
+    double* r = (double*)calloc(N, sizeof(double));
+    char* act = (char*)malloc((size_t)G);
+    int* scr = (int*)calloc((size_t)G, sizeof(int));
+    for (int64_t g = 0; g < G; g++) act[g] = 1;
+    if (x0)
+        for (int64_t i = 0; i < K; i++) { x[i] = x0[i]; u[i] = x0[i]; }
+
+    /* Algorithm 1 (static): one test at theta = D*0 - y = -y, before the loop */
+    if (!opt->dynamic && opt->test != OR_TEST_NONE) {
+        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];
+        double m = 0.0;
+        for (int64_t g = 0; g < G; g++) {
+            double q = 0.0;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) q += b[i] * b[i];
+            double val = sqrt(q) / g_w(w, g);
+            if (val > m) m = val;
+        }
+        double R, rad;
+        screen(&c, theta, m, act, scr, -1, &R, &rad);
+        for (int64_t g = 0; g < G; g++)
+            if (scr[g]) {
+                act[g] = 0;
+                for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) { x[i] = 0.0; u[i] = 0.0; }
+            }
+    }
+
+    double l = 1.0; /* FISTA l_0 */
+    int it;
+    double gap = INFINITY, primal = 0.0, dual = 0.0;
+    res->status = 1;
+    for (it = 1; it <= opt->max_iter; it++) {
+        /* Table 1: theta_t = D_{t-1} ubar_{t-1} - y */
+        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];
+        for (int64_t g = 0; g < G; g++) {
+            if (!act[g]) continue;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++)
+                if (u[i] != 0.0)
+                    for (int64_t n = 0; n < N; n++) theta[n] += D[i * ld + n] * u[i];
+        }
+        /* z_t = D_{t-1}^T theta_t and the proximal step x_t = prox(ubar - z/L) */
+        double m = 0.0;
+        for (int64_t g = 0; g < G; g++) {
+            if (!act[g]) continue;
+            double q = 0.0;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
+                z[i] = col_dot(D, ld, i, theta, N);
+                q += z[i] * z[i];
+                v[i] = u[i] - z[i] / L;
+            }
+            double val = sqrt(q) / g_w(w, g);
+            if (val > m) m = val;
+            prox_group(&c, g, v, lambda / L, xn);
+        }
+        /* FISTA: l_t and u_t = x_t + ((l_{t-1} - 1) / l_t)(x_t - xbar_{t-1}); ISTA: u_t = x_t */
+        double beta = 0.0;
+        if (opt->alg == OR_FISTA) {
+            double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));
+            beta = (l - 1.0) / ln;
+            l = ln;
+        }
+        for (int64_t g = 0; g < G; g++) {
+            if (!act[g]) continue;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
+                double xi = xn[i];
+                u[i] = xi + beta * (xi - x[i]);
+                x[i] = xi;
+            }
+        }
+        /* screening with theta_t (Algorithm 3 line "I_t <- {i : T_theta_t(i)} u I_{t-1}") */
+        double R, rad;
+        double mu;
+        if (opt->dynamic && opt->test != OR_TEST_NONE) {
+            mu = screen(&c, theta, m, act, scr, it, &R, &rad);
+        } else {
+            int save = c.test;
+            c.test = OR_TEST_NONE; /* R and mu only, for the gap */
+            mu = screen(&c, theta, m, act, scr, it, &R, &rad);
+            c.test = save;
+        }
+        /* xbar_t, ubar_t: restriction to the atoms still active */
+        for (int64_t g = 0; g < G; g++) {
+            if (act[g] && scr[g]) {
+                act[g] = 0;
+                for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) { x[i] = 0.0; u[i] = 0.0; }
+            }
+        }
+        /* duality gap P(xbar_t) - Dual(mu_t theta_t), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2 */
+        for (int64_t n = 0; n < N; n++) r[n] = -y[n];
+        for (int64_t i = 0; i < K; i++)
+            if (x[i] != 0.0)
+                for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * x[i];
+        primal = 0.5 * vec_dot(r, r, N) + lambda * omega(&c, x);
+        dual = 0.5 * yy - 0.5 * lambda * lambda * R * R;
+        gap = primal - dual;
+        int nact = 0, nnz = 0;
+        for (int64_t g = 0; g < G; g++)
+            if (act[g]) nact += (int)(g_hi(goff, g) - g_lo(goff, g));
+        for (int64_t i = 0; i < K; i++) nnz += x[i] != 0.0;
+        if (hist) {
+            double* h = hist + (size_t)(it - 1) * OR_NH;
+            h[OR_H_ACTIVE] = nact;
+            h[OR_H_NNZ] = nnz;
+            h[OR_H_R] = R;
+            h[OR_H_RADIUS] = rad;
+            h[OR_H_GAP] = gap;
+            h[OR_H_MU] = mu;
+        }
+        res->n_active = nact;
+        res->nnz = nnz;
+        if (opt->tol_gap_rel > 0 && gap <= opt->tol_gap_rel * 0.5 * yy) {
+            res->status = 0;
+            break;
+        }
+    }
+    if (it > opt->max_iter) {
+        it = opt->max_iter;
+        if (!(opt->tol_gap_rel > 0)) res->status = 0;
+    }
+    res->iters = it;
+    res->gap = gap;
+    res->primal = primal;
+    res->dual = dual;
+    for (int64_t i = 0; i < K; i++) x_out[i] = x[i];
+    if (scr_iter)
+        for (int64_t g = 0; g < G; g++)
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) scr_iter[i] = scr[g];
+
+    free(x); free(u); free(xn); free(v); free(z); free(theta); free(r); free(act); free(scr);
+    free(b); free(c.dtc); free(c.nrm); free(c.tdome);
+    return 0;
+}

@@ -1,0 +1,413 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a closed
+form, a brute-force enumeration, a printed formula of the paper, the KKT
+conditions, an independent library routine, or an invariance.  All run on
+the CPU (no GPU marker).
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+
+def _small_lasso(seed, N=30, K=80, k=4, sigma=0.01):
+    g = gen.rng(seed)
+    D = gen.gaussian_dict(N, K, g)
+    x0 = gen.sparse_x0(K, k, g)
+    y = gen.observe(D, x0, g, sigma=sigma)
+    return D, y
+
+
+# ---------------------------------------------------------------- lambda_*
+
+@pytest.mark.parametrize("groups", [False, True])
+def test_lambda_max_is_the_zero_threshold(groups):
+    """Sec. 2.2.2 / eq. (gstar): x = 0 iff lambda >= lambda_*."""
+    D, y = _small_lasso(1)
+    goff = gen.contiguous_groups(D.shape[1], 4) if groups else None
+    w = np.full(goff.size - 1, 2.0) if groups else None
+    lm, star, _ = oracle.lambda_max(D, y, goff, w)
+    test = "gsafe" if groups else "safe"
+    r = oracle.solve(D, y, lm * (1 + 1e-9), goff, w, test=test, tol=1e-12, max_iter=50)
+    assert r["iters"] == 0 and not r["x"].any() and r["gap"] == 0.0
+    lam = lm * (1 - 1e-3)
+    r = oracle.solve(D, y, lam, goff, w, test="none", tol=0, max_iter=5000)
+    nz = np.flatnonzero(r["x"])
+    if groups:
+        assert set(nz) <= set(range(goff[star], goff[star + 1])) and nz.size > 0
+    else:
+        # one active atom: x_* = sign(b_*) (lambda_* - lambda) / ||d_*||^2 (KKT with support {i_*})
+        b = D.T @ y
+        assert list(nz) == [star]
+        assert np.isclose(r["x"][star], np.sign(b[star]) * (lm - lam) / (D[:, star] @ D[:, star]), rtol=1e-8)
+
+
+# ----------------------------------------------------- closed forms (prox)
+
+def test_orthonormal_dictionary_soft_threshold():
+    """D^T D = I: the Lasso solution is soft(D^T y, lambda) (eq. softTh)."""
+    g = gen.rng(2)
+    D = gen.orthonormal_dict(64, g)
+    y = g.standard_normal(64)
+    b = D.T @ y
+    lam = 0.6 * np.abs(b).max()
+    want = np.sign(b) * np.maximum(np.abs(b) - lam, 0)
+    for alg in ("ista", "fista"):
+        for test in ("none", "safe", "dst3", "dome"):
+            r = oracle.solve(D, y, lam, alg=alg, test=test, tol=1e-15, max_iter=400, L=1.0)
+            np.testing.assert_allclose(r["x"], want, atol=1e-12)
+
+
+def test_orthonormal_dictionary_group_soft_threshold():
+    """D^T D = I: the Group-Lasso solution is the group soft threshold of D_g^T y
+    with threshold lambda w_g (eq. gr_softTh)."""
+    g = gen.rng(3)
+    D = gen.orthonormal_dict(60, g)
+    y = g.standard_normal(60)
+    goff = gen.contiguous_groups(60, 5)
+    w = np.sqrt(np.diff(goff).astype(float))
+    b = D.T @ y
+    lm = max(np.linalg.norm(b[goff[i]:goff[i + 1]]) / w[i] for i in range(goff.size - 1))
+    lam = 0.5 * lm
+    want = np.zeros(60)
+    for i in range(goff.size - 1):
+        bg = b[goff[i]:goff[i + 1]]
+        nb = np.linalg.norm(bg)
+        want[goff[i]:goff[i + 1]] = max(0.0, (nb - lam * w[i]) / nb) * bg
+    for test in ("none", "gsafe", "dgst3"):
+        r = oracle.solve(D, y, lam, goff, w, test=test, tol=1e-15, max_iter=400, L=1.0)
+        np.testing.assert_allclose(r["x"], want, atol=1e-12)
+
+
+# ------------------------------------------------- brute force (tiny Lasso)
+
+def _lasso_bruteforce(D, y, lam):
+    """Exact Lasso minimiser by enumerating supports and signs: on support S with
+    signs s, D_S^T D_S x_S = D_S^T y - lam s; accept when sign(x_S) = s and
+    |d_j^T (y - D_S x_S)| <= lam off the support (eq. primaldual)."""
+    N, K = D.shape
+    best = None
+    for size in range(0, min(N, K) + 1):
+        for S in itertools.combinations(range(K), size):
+            S = list(S)
+            for s in itertools.product((-1.0, 1.0), repeat=size):
+                s = np.array(s)
+                if size:
+                    A = D[:, S]
+                    xs = np.linalg.solve(A.T @ A, A.T @ y - lam * s)
+                    if np.any(np.sign(xs) != s):
+                        continue
+                    r = y - A @ xs
+                else:
+                    xs = np.zeros(0)
+                    r = y
+                c = D.T @ r
+                if np.all(np.abs(np.delete(c, S)) <= lam * (1 + 1e-12)):
+                    x = np.zeros(K)
+                    x[S] = xs
+                    return x
+        if best is not None:
+            break
+    raise AssertionError("no KKT point found")
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome"])
+@pytest.mark.parametrize("dynamic", [True, False])
+def test_bruteforce_and_safety_tiny(seed, test, dynamic):
+    """Definition 1 and Theorem 1: the screened solver returns the exact minimiser,
+    and no screened atom is nonzero in it."""
+    g = gen.rng(seed)
+    N, K = 6, 9
+    D = gen.gaussian_dict(N, K, g)
+    y = D @ gen.sparse_x0(K, 2, g) + 0.05 * g.standard_normal(N)
+    lm, _, _ = oracle.lambda_max(D, y)
+    for ratio in (0.3, 0.6, 0.9):
+        lam = ratio * lm
+        xbf = _lasso_bruteforce(D, y, lam)
+        for alg in ("ista", "fista"):
+            r = oracle.solve(D, y, lam, alg=alg, test=test, dynamic=dynamic, tol=0, max_iter=20000)
+            np.testing.assert_allclose(r["x"], xbf, atol=1e-8)
+            screened = r["scr_iter"] != 0
+            assert not np.any(xbf[screened] != 0), (test, ratio, alg)
+
+
+# ------------------------------------------------------------------- KKT
+
+def test_kkt_lasso_config1_shape():
+    """eq. (primaldual): |d_i^T (y - D x)| <= lambda, = lambda sign(x_i) on the support."""
+    D, y, _ = gen.config1(1001)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.5 * lm
+    r = oracle.solve(D, y, lam, alg="ista", test="dst3", tol=1e-13, max_iter=200000)
+    assert r["status"] == 0
+    c = D.T @ (y - D @ r["x"])
+    assert np.all(np.abs(c) <= lam * (1 + 1e-5))
+    S = r["x"] != 0
+    np.testing.assert_allclose(c[S], lam * np.sign(r["x"][S]), rtol=1e-5)
+
+
+def test_kkt_group_lasso():
+    """eq. (primaldualKKT_glasso): ||D_g^T r|| <= lambda w_g, with D_g^T r =
+    lambda w_g x_g/||x_g|| on active groups."""
+    D, y, _, goff, w = gen.config3(1003, N=60, K=200, gsize=5, n_active=3)
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.4 * lm
+    r = oracle.solve(D, y, lam, goff, w, test="dgst3", tol=1e-14, max_iter=100000)
+    res = y - D @ r["x"]
+    for i in range(goff.size - 1):
+        sl = slice(goff[i], goff[i + 1])
+        cg = D[:, sl].T @ res
+        xg = r["x"][sl]
+        assert np.linalg.norm(cg) <= lam * w[i] * (1 + 1e-5)
+        if np.any(xg != 0):
+            np.testing.assert_allclose(cg, lam * w[i] * xg / np.linalg.norm(xg), atol=1e-5 * lam * w[i])
+
+
+def test_matches_independent_coordinate_descent():
+    """An independent solver (scikit-learn coordinate descent) agrees on the minimiser."""
+    sk = pytest.importorskip("sklearn.linear_model")
+    D, y = _small_lasso(4, N=40, K=120, k=5)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.3 * lm
+    m = sk.Lasso(alpha=lam / D.shape[0], fit_intercept=False, tol=1e-14, max_iter=200000).fit(D, y)
+    r = oracle.solve(D, y, lam, test="dst3", tol=1e-15, max_iter=100000)
+    np.testing.assert_allclose(r["x"], m.coef_, atol=1e-7)
+
+
+# ------------------------------------------------------- gap / trajectories
+
+@pytest.mark.parametrize("test", ["none", "safe", "dst3", "dome"])
+def test_gap_nonnegative_and_sets_nested(test):
+    """A duality gap is >= 0 at every iteration; screened sets only grow (Alg. 3)."""
+    D, y = _small_lasso(5, N=50, K=300, k=5)
+    lm, _, _ = oracle.lambda_max(D, y)
+    r = oracle.solve(D, y, 0.5 * lm, test=test, tol=1e-12, max_iter=5000)
+    h = r["hist"]
+    assert np.all(h[:, 4] >= -1e-12 * 0.5 * (y @ y))
+    assert np.all(np.diff(h[:, 0]) <= 0)
+    assert r["status"] == 0 and r["gap"] <= 1e-12 * 0.5 * (y @ y)
+
+
+def test_scale_covariance():
+    """P(a lambda, D, a y) has solution a x(lambda, D, y)."""
+    D, y = _small_lasso(6)
+    lm, _, _ = oracle.lambda_max(D, y)
+    r1 = oracle.solve(D, y, 0.4 * lm, tol=1e-15, max_iter=50000)
+    r2 = oracle.solve(D, 3.0 * y, 1.2 * lm, tol=1e-15, max_iter=50000)
+    np.testing.assert_allclose(r2["x"], 3.0 * r1["x"], atol=1e-9)
+
+
+# ---------------------------------------------- static tests vs the paper
+
+def _unit_y_problem(seed, N=40, K=400, kind="gaussian"):
+    g = gen.rng(seed)
+    D = gen.pnoise_dict(N, K, g) if kind == "pnoise" else gen.gaussian_dict(N, K, g)
+    y = D @ gen.sparse_x0(K, 4, g) + 0.3 * g.standard_normal(N)
+    return D, y / np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("ratio", [0.5, 0.7, 0.9])
+def test_static_safe_is_algorithm4_formula(ratio):
+    """Algorithm 4 (||y|| = 1): screen i iff |d_i^T y| < lambda - 1 + lambda/lambda_*;
+    the dynamic test at the first ISTA iteration from 0 screens the same set."""
+    D, y = _unit_y_problem(7)
+    lm, _, b = oracle.lambda_max(D, y)
+    lam = ratio * lm
+    want = np.abs(b) < lam - 1 + lam / lm
+    rs = oracle.solve(D, y, lam, alg="ista", test="safe", dynamic=False, max_iter=1, tol=0)
+    rd = oracle.solve(D, y, lam, alg="ista", test="safe", dynamic=True, max_iter=1, tol=0)
+    np.testing.assert_array_equal(rs["scr_iter"] != 0, want)
+    np.testing.assert_array_equal(rd["scr_iter"] != 0, want)
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "pnoise"])
+@pytest.mark.parametrize("ratio", [0.6, 0.8, 0.95])
+def test_static_dome_is_printed_lemma(ratio, kind):
+    """Lemma 4 with theta = y, ||y|| = 1, unit atoms, in the printed form:
+    Q^l(t) < y^T d_i < Q^u(t), t = d_*^T d_i, with the printed constants."""
+    D, y = _unit_y_problem(8, kind=kind)
+    lm, star, b = oracle.lambda_max(D, y)
+    lam = ratio * lm
+    dstar = np.sign(b[star]) * D[:, star]
+    t = D.T @ dstar
+    r = np.sqrt((1 / lam - 1 / lm) ** 2 - (lm / lam - 1) ** 2)  # printed r_theta at theta = y
+    const = lam - 1 + lam / lm
+    Ql = np.where(t <= lm, (lm - lam) * t - lam + lam * r * np.sqrt(1 - t * t), -const)
+    Qu = np.where(t < -lm, const, (lm - lam) * t + lam - lam * r * np.sqrt(1 - t * t))
+    want = (Ql < b) & (b < Qu)
+    rs = oracle.solve(D, y, lam, alg="ista", test="dome", dynamic=False, max_iter=1, tol=0)
+    got = rs["scr_iter"] != 0
+    # an atom may sit on a boundary within rounding; there must be none in these draws
+    assert np.array_equal(got, want), np.flatnonzero(got != want)
+    if kind == "pnoise" or ratio > 0.9:
+        assert want.sum() > 0
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "pnoise"])
+@pytest.mark.parametrize("ratio", [0.6, 0.8, 0.95])
+def test_static_dst3_is_printed_lemma(ratio, kind):
+    """Lemma 3 with theta = y (the ST3 test): screen iff 1 - |d_i^T c| > r with
+    c = y/lambda - (lambda_*/lambda - 1) d_*, r = sqrt(||mu y - y/lambda||^2 - (lambda_*/lambda - 1)^2),
+    mu = 1/lambda_* for ||y|| = 1."""
+    D, y = _unit_y_problem(9, kind=kind)
+    lm, star, b = oracle.lambda_max(D, y)
+    lam = ratio * lm
+    dstar = np.sign(b[star]) * D[:, star]
+    c = y / lam - (lm / lam - 1) * dstar
+    r = np.sqrt(np.linalg.norm(y / lm - y / lam) ** 2 - (lm / lam - 1) ** 2)
+    want = 1 - np.abs(D.T @ c) > r
+    rs = oracle.solve(D, y, lam, alg="ista", test="dst3", dynamic=False, max_iter=1, tol=0)
+    np.testing.assert_array_equal(rs["scr_iter"] != 0, want)
+
+
+# ------------------------------------------- Lasso = singleton Group-Lasso
+
+@pytest.mark.parametrize("pair", [("safe", "gsafe"), ("dst3", "dgst3")])
+def test_lasso_tests_are_singleton_group_tests(pair):
+    """Appendix: Lemmas 2/3 are Lemmas 5/6 with groups of size one and w = 1."""
+    D, y = _small_lasso(10, N=40, K=200)
+    lm, _, _ = oracle.lambda_max(D, y)
+    goff = gen.contiguous_groups(200, 1)
+    w = np.ones(200)
+    a = oracle.solve(D, y, 0.5 * lm, test=pair[0], tol=1e-12, max_iter=3000)
+    b = oracle.solve(D, y, 0.5 * lm, goff, w, test=pair[1], tol=1e-12, max_iter=3000)
+    np.testing.assert_allclose(a["x"], b["x"], atol=1e-12)
+    np.testing.assert_array_equal(a["scr_iter"], b["scr_iter"])
+    assert a["iters"] == b["iters"]
+
+
+# -------------------------------------------------- regions contain theta~
+
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome"])
+def test_regions_contain_dual_optimum(test):
+    """Each iteration's sphere (or dome) contains theta~ = (y - D x~)/lambda."""
+    D, y = _small_lasso(14, N=40, K=300, k=4)
+    lm, star, b = oracle.lambda_max(D, y)
+    lam = 0.5 * lm
+    ref = oracle.solve(D, y, lam, test="none", tol=1e-15, max_iter=100000)
+    th = (y - D @ ref["x"]) / lam
+    r = oracle.solve(D, y, lam, test=test, tol=1e-10, max_iter=5000)
+    h = r["hist"]
+    dstar = np.sign(b[star]) * D[:, star]
+    if test == "safe":
+        dist = np.linalg.norm(th - y / lam)
+        assert np.all(dist <= h[:, 3] + 1e-9)
+    elif test == "dst3":
+        c = y / lam - (lm / lam - 1) * dstar / (dstar @ dstar)
+        assert np.all(np.linalg.norm(th - c) <= h[:, 3] + 1e-9)
+    else:
+        assert np.all(np.linalg.norm(th - y / lam) <= h[:, 2] + 1e-9)
+        assert dstar @ th <= 1 + 1e-9
+
+
+def test_group_regions_contain_dual_optimum():
+    D, y, _, goff, w = gen.config3(15, N=50, K=200, gsize=4, n_active=3)
+    lm, star, b = oracle.lambda_max(D, y, goff, w)
+    lam = 0.5 * lm
+    ref = oracle.solve(D, y, lam, goff, w, test="none", tol=1e-15, max_iter=100000)
+    th = (y - D @ ref["x"]) / lam
+    # every group constraint of Lemma 5's feasible set holds at theta~
+    for i in range(goff.size - 1):
+        assert np.linalg.norm(D[:, goff[i]:goff[i + 1]].T @ th) <= w[i] * (1 + 1e-8)
+    r = oracle.solve(D, y, lam, goff, w, test="gsafe", tol=1e-10, max_iter=5000)
+    assert np.all(np.linalg.norm(th - y / lam) <= r["hist"][:, 3] + 1e-9)
+    # DGST3 ball: bounding sphere of the half-space cap; containment of theta~
+    r = oracle.solve(D, y, lam, goff, w, test="dgst3", tol=1e-10, max_iter=5000)
+    Dg = D[:, goff[star]:goff[star + 1]]
+    n = Dg @ (Dg.T @ y) / lm
+    c = y / lam - (n @ y / lam - w[star] ** 2) * n / (n @ n)
+    assert np.all(np.linalg.norm(th - c) <= r["hist"][:, 3] + 1e-9)
+
+
+# ----------------------------------------------------- Lemma 8 and Lemma 4
+
+def test_dual_scaling_is_optimal_feasible_scaling():
+    """Lemma 8: mu minimises ||s theta - y/lambda|| over feasible s (|s| m <= 1);
+    checked against a fine 1-D scan."""
+    g = gen.rng(16)
+    for _ in range(20):
+        D = gen.gaussian_dict(20, 60, g)
+        y = g.standard_normal(20)
+        theta = g.standard_normal(20)
+        lam = g.uniform(0.1, 2.0)
+        m = np.abs(D.T @ theta).max()
+        mu = oracle.dual_scaling(theta, y, lam, m)
+        assert abs(mu) * m <= 1 + 1e-12
+        s = np.linspace(-1 / m, 1 / m, 200001)
+        f = np.linalg.norm(s[:, None] * theta[None, :] - y[None, :] / lam, axis=1)
+        assert np.linalg.norm(mu * theta - y / lam) <= f.min() + 1e-12
+
+
+def test_dome_max_matches_numeric_maximum():
+    """Lemma 4's region: the closed-form max of d^T theta over the dome agrees with
+    a brute-force maximisation over the plane spanned by n and d."""
+    g = gen.rng(17)
+    for _ in range(200):
+        t = g.uniform(-0.99, 0.99)
+        R = g.uniform(0.1, 2.0)
+        psi = g.uniform(0.0, R)
+        dc0 = g.uniform(-1, 1)
+        # coordinates: n = (1, 0), d = (t, sqrt(1 - t^2)); theta = c0 + (a, c); n^T c0 - off = psi
+        ang = np.linspace(0, 2 * np.pi, 4001)
+        rad = np.linspace(0, R, 801)
+        A = rad[:, None] * np.cos(ang)[None, :]
+        C = rad[:, None] * np.sin(ang)[None, :]
+        ok = A <= -psi
+        val = t * A + np.sqrt(1 - t * t) * C
+        num = dc0 + val[ok].max()
+        got = oracle.dome_max(dc0, t, psi, R)
+        assert got >= num - 1e-9
+        assert got <= num + 5e-3 * R
+
+
+# ---------------------------------------------------------- spectral norms
+
+def test_spectral_norms_match_library():
+    g = gen.rng(18)
+    D = gen.gaussian_dict(30, 90, g)
+    L = oracle.spectral_norm_sq(D, tol=1e-14)
+    assert np.isclose(L, np.linalg.norm(D, 2) ** 2, rtol=1e-9)
+    for c0, c1 in ((0, 1), (0, 5), (10, 30), (40, 73)):
+        s = oracle.group_spec_norm(D, c0, c1)
+        assert np.isclose(s, np.linalg.norm(D[:, c0:c1], 2), rtol=1e-12)
+
+
+@pytest.mark.parametrize("pair", [("safe", "gsafe"), ("dst3", "dgst3")])
+def test_singleton_groups_with_unequal_norms(pair):
+    """The singleton-group identity also holds for atoms of unequal norms (Lemma 7's
+    sphere test with ||D_g|| = ||d_i||, Lemma 6's n = sign(b_*) d_*)."""
+    D, y = _small_lasso(19, N=40, K=200)
+    D = D * gen.rng(20).uniform(0.5, 2.0, size=(1, 200))
+    lm, _, _ = oracle.lambda_max(D, y)
+    goff = gen.contiguous_groups(200, 1)
+    a = oracle.solve(D, y, 0.5 * lm, test=pair[0], tol=1e-12, max_iter=5000)
+    b = oracle.solve(D, y, 0.5 * lm, goff, np.ones(200), test=pair[1], tol=1e-12, max_iter=5000)
+    np.testing.assert_allclose(a["x"], b["x"], atol=1e-11)
+    np.testing.assert_array_equal(a["scr_iter"], b["scr_iter"])
+    assert (a["scr_iter"] != 0).sum() > 0
+
+
+def test_fista_rate_bound():
+    """FISTA (Table 1, l_0 = 1) satisfies Beck and Teboulle's bound
+    F(x_t) - F* <= 2 L ||x_0 - x*||^2 / (t + 1)^2 at every iteration, and its first
+    extrapolation is zero, so its first two iterates are ISTA's."""
+    D, y = _small_lasso(21, N=60, K=150, k=6)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.1 * lm
+    ref = oracle.solve(D, y, lam, test="none", tol=0, max_iter=60000)
+    Fs = 0.5 * np.sum((D @ ref["x"] - y) ** 2) + lam * np.abs(ref["x"]).sum()
+    L = oracle.spectral_norm_sq(D) * (1 + 1e-6)
+    r = oracle.solve(D, y, lam, alg="fista", test="none", tol=0, max_iter=400, L=L)
+    h = r["hist"]
+    yy = y @ y
+    F = h[:, 4] + 0.5 * yy - 0.5 * lam * lam * h[:, 2] ** 2  # primal = gap + dual
+    t = np.arange(1, F.size + 1)
+    assert np.all(F - Fs <= 2 * L * np.sum(ref["x"] ** 2) / (t + 1) ** 2 + 1e-12)
+    ri = oracle.solve(D, y, lam, alg="ista", test="none", tol=0, max_iter=3, L=L)
+    np.testing.assert_allclose(h[:2, 4], ri["hist"][:2, 4], rtol=1e-13)
+    assert abs(h[2, 4] - ri["hist"][2, 4]) > 1e-10 * yy
