@@ -1,0 +1,163 @@
+/*
+ * dscreen.h -- C ABI of a GB300 (sm_103a) solver for the Lasso and the
+ * Group-Lasso with dynamic screening (Bonnefoy, Emiya, Ralaivola, Gribonval,
+ * "Dynamic Screening: Accelerating First-Order Algorithms for the Lasso and
+ * Group-Lasso", arXiv 1412.4080).
+ *
+ * Problem (eq. 1):   x~ = argmin_x 1/2 ||D x - y||_2^2 + lambda * Omega(x)
+ *   Lasso (eq. lasso):              Omega(x) = ||x||_1
+ *   Group-Lasso (eq. group-lasso):  Omega(x) = sum_g w_g ||x_g||_2, G a partition
+ * D is N x K, y has N entries.  The solver runs ISTA or FISTA (Table 1) and,
+ * inside every iteration, a safe screening test (Lemmas 2-7, dual scaling by
+ * Lemma 8) that removes atoms from the working dictionary (Algorithm 3).
+ *
+ * Conventions shared by every call:
+ *  - Layout: D is column-major (atom i is the contiguous column D[:, i]),
+ *    with leading dimension ld >= N elements.  Vectors are contiguous.
+ *  - Element type: the dictionary's dtype (DS_FP32 -> float, DS_FP64 ->
+ *    double) is also the type of y, x0 and x_out.
+ *  - Pointers may be host or device memory; the library detects which with
+ *    cudaPointerGetAttributes and copies host data itself (pinned host
+ *    memory is fastest).  The caller owns every buffer it passes in and may
+ *    free it when the call returns (ds_dict_create copies D).
+ *  - Every call is ordered on the context's CUDA stream and returns when its
+ *    results are in the caller's buffers (synchronous), except where noted.
+ *  - Errors are returned as ds_status codes; nothing is thrown across the
+ *    ABI.  A failed call leaves its outputs unspecified.
+ *  - Not thread-safe per context: one call at a time on a given ds_ctx.
+ */
+#ifndef DSCREEN_H
+#define DSCREEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ds_ctx ds_ctx;
+typedef struct ds_dict ds_dict;
+
+typedef enum {
+    DS_OK = 0,
+    DS_ERR_INVALID = 1,       /* bad argument: null pointer, N/K <= 0, lambda <= 0, bad groups ... */
+    DS_ERR_OOM = 2,           /* device or pinned allocation failed */
+    DS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    DS_ERR_TIMEOUT = 4,       /* a bounded device-side wait (grid barrier) gave up */
+    DS_ERR_NOT_CONVERGED = 5, /* (ds_result.status only) max_iter reached above the gap tolerance */
+    DS_ERR_UNSUPPORTED = 6    /* valid request outside what this build handles (e.g. N too large) */
+} ds_status;
+
+typedef enum { DS_ISTA = 0, DS_FISTA = 1 } ds_alg; /* Table 1 rows */
+
+typedef enum {
+    DS_TEST_NONE = 0,
+    DS_SAFE = 1,  /* Lemma 2 (Lasso) */
+    DS_DST3 = 2,  /* Lemma 3 (Lasso) */
+    DS_DOME = 3,  /* Lemma 4 (Lasso), dynamic form of the dome maximum */
+    DS_GSAFE = 4, /* Lemma 5 (Group-Lasso; on a Lasso dictionary: singleton groups) */
+    DS_DGST3 = 5  /* Lemma 6 (Group-Lasso; on a Lasso dictionary: singleton groups) */
+} ds_test;
+
+typedef enum { DS_FP64 = 0, DS_FP32 = 1, DS_BF16 = 2, DS_FP8 = 3 } ds_prec;
+
+typedef struct {
+    int alg;            /* ds_alg */
+    int test;           /* ds_test */
+    int dynamic;        /* 1: test at every iteration (Algorithm 3); 0: once at theta = -y (Algorithm 1) */
+    int max_iter;       /* iteration cap (>= 1) */
+    double tol_gap_rel; /* stop when gap <= tol * 1/2 ||y||^2; 0 runs exactly max_iter iterations */
+    double L;           /* step constant; <= 0 uses the dictionary's ||D||_2^2 upper estimate */
+    int lambda_rel;     /* 1: lambda values are fractions of lambda_max (computed in the call) */
+} ds_options;
+
+typedef struct {
+    int iters;          /* iterations run */
+    int status;         /* DS_OK, DS_ERR_NOT_CONVERGED or DS_ERR_TIMEOUT */
+    int64_t n_active;   /* atoms not screened at exit */
+    int64_t nnz;        /* nonzeros of the returned x */
+    double gap;         /* P(x) - Dual(mu theta) at exit (absolute) */
+    double primal;      /* P(x) */
+    double dual;        /* Dual(mu theta) */
+    double lambda;      /* absolute lambda used */
+    double lambda_max;  /* lambda_* (Sec. 2.2.2 / eq. gstar) */
+    double ms;          /* device time of the solve kernel, milliseconds */
+} ds_result;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* ds_status_str(ds_status s);
+
+/* Fill *opt with defaults: FISTA, DST3, dynamic, max_iter 10000, tol 1e-6,
+ * L from the dictionary, absolute lambda.  DS_ERR_INVALID if opt is NULL. */
+ds_status ds_options_default(ds_options* opt);
+
+/* Create a context on CUDA device `device`, ordered on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The context owns the
+ * solver workspaces (grown on demand).  Errors: DS_ERR_INVALID (out == NULL or
+ * no such device), DS_ERR_CUDA. */
+ds_status ds_create(int device, void* cuda_stream, ds_ctx** out);
+
+/* Release a context and its workspaces (NULL is a no-op). */
+ds_status ds_destroy(ds_ctx* ctx);
+
+/* Register a dictionary D (N x K, column-major, leading dimension ld >= N,
+ * element type dtype = DS_FP32 or DS_FP64; host or device pointer).  The
+ * library copies D into a zero-padded device copy (16-byte aligned columns)
+ * and precomputes what does not depend on y or lambda (the Sec. 4.1 remark
+ * that the group norms ||D_g|| depend on the dictionary only):
+ *   - column norms ||d_i||;
+ *   - L = an upper estimate of ||D||_2^2 (Lanczos on D D^T with a residual bound);
+ *   - for Group-Lasso, ||D_g||_2 of every group (Gram matrix + Jacobi,
+ *     rounded up), used by Lemmas 5-7.
+ * Groups (eq. group-lasso): group_offsets (host, n_groups + 1 entries,
+ * 0 = off_0 < off_1 < ... < off_G = K) lists contiguous column ranges; weights
+ * (host, n_groups entries, > 0; NULL = sqrt(group size)).  group_offsets NULL
+ * = the Lasso.  Group sizes are limited to 32 columns (DS_ERR_UNSUPPORTED).
+ * work_prec must equal dtype in this build.  Errors: DS_ERR_INVALID,
+ * DS_ERR_UNSUPPORTED (N > the shared-memory limit, group > 32, work_prec),
+ * DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
+ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64_t ld, ds_prec dtype,
+                         const int64_t* group_offsets, const double* weights, int64_t n_groups,
+                         ds_prec work_prec, ds_dict** out);
+
+/* Release a dictionary (NULL is a no-op). */
+ds_status ds_dict_destroy(ds_dict* dict);
+
+/* Read back the dictionary's step constant L (>= ||D||_2^2 estimate). */
+ds_status ds_dict_lipschitz(const ds_dict* dict, double* L);
+
+/* lambda_* of y (Sec. 2.2.2: ||D^T y||_inf; eq. gstar: max_g ||D_g^T y|| / w_g)
+ * computed on the device with compensated FP32 (or FP64) dot products.
+ * y: N elements of the dictionary's type, host or device.  Errors:
+ * DS_ERR_INVALID, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
+ds_status ds_lambda_max(ds_ctx* ctx, const ds_dict* dict, const void* y, double* lambda_max);
+
+/* Solve eq. (1) for one y and one lambda > 0 with dynamic (or static)
+ * screening; one persistent cooperative kernel runs the whole solve.
+ * x0 (nullable, K elements): warm start.  x_out: K elements.  res (host):
+ * iterations, gap, status, ...  lambda >= lambda_max returns x = 0 with 0
+ * iterations.  The call returns DS_OK when the solve ran (res->status tells
+ * whether the gap tolerance was met).  Errors: DS_ERR_INVALID (null y/x_out/
+ * opt/res, lambda <= 0, max_iter < 1, test not valid for the dictionary),
+ * DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
+ds_status ds_solve(ds_ctx* ctx, const ds_dict* dict, const void* y, double lambda, const ds_options* opt,
+                   const void* x0, void* x_out, ds_result* res);
+
+/* Same as ds_solve for n_lambda values of lambda sharing one y (the precompute
+ * of D^T y, lambda_* and the test centres runs once).  lambdas: host array
+ * (absolute, or fractions of lambda_max when opt->lambda_rel).  X_out: K x
+ * n_lambda, column j = solution for lambdas[j].  res: n_lambda entries. */
+ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* dict, const void* y, int n_lambda, const double* lambdas,
+                        const ds_options* opt, const void* x0, void* X_out, ds_result* res);
+
+/* Record per-iteration history of the following solves into hist (device,
+ * max_rows x 6 doubles, row t-1 = iteration t: active atoms, nnz(x), R,
+ * test radius, gap, mu), or stop recording (hist NULL).  Only the first
+ * lambda of a path is recorded. */
+ds_status ds_set_history(ds_ctx* ctx, double* hist, int max_rows);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSCREEN_H */

@@ -1,0 +1,216 @@
+"""ctypes binding of libdscreen (include/dscreen.h), one Python function per C entry point.
+
+Argument marshalling only: every step of a solve runs in the CUDA library.
+Arrays may be CUDA ``torch.Tensor`` objects (device memory) or NumPy arrays
+(host memory); the library copies host data itself.  Dictionaries are
+column-major N x K (a torch tensor of shape (N, K) with stride (1, ld), or a
+Fortran-ordered NumPy array).  Non-OK statuses raise :class:`DscreenError`.
+There is no fallback: if the CUDA library cannot be built or loaded, importing
+a function raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dscreen.h")
+
+DS_OK, DS_ERR_INVALID, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_NOT_CONVERGED, DS_ERR_UNSUPPORTED = range(7)
+DS_ISTA, DS_FISTA = 0, 1
+DS_TEST_NONE, DS_SAFE, DS_DST3, DS_DOME, DS_GSAFE, DS_DGST3 = range(6)
+DS_FP64, DS_FP32, DS_BF16, DS_FP8 = range(4)
+TESTS = {"none": DS_TEST_NONE, "safe": DS_SAFE, "dst3": DS_DST3, "dome": DS_DOME, "gsafe": DS_GSAFE,
+         "dgst3": DS_DGST3}
+ALGS = {"ista": DS_ISTA, "fista": DS_FISTA}
+HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
+
+
+class ds_options(ctypes.Structure):
+    _fields_ = [("alg", ctypes.c_int), ("test", ctypes.c_int), ("dynamic", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
+                ("lambda_rel", ctypes.c_int)]
+
+
+class ds_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("n_active", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("gap", ctypes.c_double), ("primal", ctypes.c_double),
+                ("dual", ctypes.c_double), ("lambda_", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "status": self.status, "n_active": self.n_active, "nnz": self.nnz,
+                "gap": self.gap, "primal": self.primal, "dual": self.dual, "lambda": self.lambda_,
+                "lambda_max": self.lambda_max, "ms": self.ms}
+
+
+class DscreenError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {lib().ds_status_str(status).decode()} ({status})")
+
+
+def declared_functions():
+    """Names of the entry points declared in include/dscreen.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ds_[a-z_]+)\s*\(", txt)))
+
+
+def lib():
+    """Load (building first if needed) the CUDA library."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+            L.ds_status_str.restype = ctypes.c_char_p
+            L.ds_status_str.argtypes = [ctypes.c_int]
+            L.ds_options_default.argtypes = [ctypes.POINTER(ds_options)]
+            L.ds_create.argtypes = [ctypes.c_int, vp, ctypes.POINTER(vp)]
+            L.ds_destroy.argtypes = [vp]
+            L.ds_dict_create.argtypes = [vp, vp, i64, i64, i64, ctypes.c_int, vp, vp, i64, ctypes.c_int,
+                                         ctypes.POINTER(vp)]
+            L.ds_dict_destroy.argtypes = [vp]
+            L.ds_dict_lipschitz.argtypes = [vp, ctypes.POINTER(dp)]
+            L.ds_lambda_max.argtypes = [vp, vp, vp, ctypes.POINTER(dp)]
+            L.ds_solve.argtypes = [vp, vp, vp, dp, ctypes.POINTER(ds_options), vp, vp, ctypes.POINTER(ds_result)]
+            L.ds_solve_path.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ds_options), vp, vp,
+                                        ctypes.POINTER(ds_result)]
+            L.ds_set_history.argtypes = [vp, vp, ctypes.c_int]
+            for name in declared_functions():
+                if name != "ds_status_str":
+                    getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st, where):
+    if st != DS_OK:
+        raise DscreenError(st, where)
+
+
+# ----------------------------------------------------------------- marshalling
+
+def _ptr(a):
+    """(address, is_torch) of a torch tensor or NumPy array; None -> (None, False)."""
+    if a is None:
+        return None, False
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr(), True
+    return a.ctypes.data, False
+
+
+def _dtype_code(a):
+    name = str(a.dtype)
+    if name.endswith("float32"):
+        return DS_FP32
+    if name.endswith("float64"):
+        return DS_FP64
+    raise TypeError(f"dictionary dtype must be float32 or float64, got {a.dtype}")
+
+
+def _dict_layout(D):
+    N, K = D.shape
+    if hasattr(D, "stride"):
+        s0, s1 = D.stride()
+        if s0 != 1 and K > 1:
+            raise ValueError("torch dictionary must be column-major: stride (1, ld)")
+        return N, K, (s1 if K > 1 else N)
+    if not D.flags.f_contiguous:
+        raise ValueError("NumPy dictionary must be Fortran-ordered (column-major)")
+    return N, K, N
+
+
+# -------------------------------------------------------------------- entry points
+
+def ds_status_str(status: int) -> str:
+    return lib().ds_status_str(int(status)).decode()
+
+
+def ds_options_default(**kw) -> ds_options:
+    o = ds_options()
+    _check(lib().ds_options_default(ctypes.byref(o)), "ds_options_default")
+    for k, v in kw.items():
+        if k == "test" and isinstance(v, str):
+            v = TESTS[v]
+        if k == "alg" and isinstance(v, str):
+            v = ALGS[v]
+        setattr(o, k, v)
+    return o
+
+
+def ds_create(device: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = getattr(stream, "cuda_stream", stream)
+    _check(lib().ds_create(int(device), s, ctypes.byref(h)), "ds_create")
+    return h
+
+
+def ds_destroy(ctx):
+    _check(lib().ds_destroy(ctx), "ds_destroy")
+
+
+def ds_dict_create(ctx, D, group_offsets=None, weights=None, work_prec=None):
+    N, K, ld = _dict_layout(D)
+    dt = _dtype_code(D)
+    goff = None if group_offsets is None else np.ascontiguousarray(group_offsets, dtype=np.int64)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    h = ctypes.c_void_p()
+    p, _ = _ptr(D)
+    st = lib().ds_dict_create(ctx, p, N, K, ld, dt, None if goff is None else goff.ctypes.data,
+                              None if w is None else w.ctypes.data, 0 if goff is None else goff.size - 1,
+                              dt if work_prec is None else int(work_prec), ctypes.byref(h))
+    _check(st, "ds_dict_create")
+    return h
+
+
+def ds_dict_destroy(dct):
+    _check(lib().ds_dict_destroy(dct), "ds_dict_destroy")
+
+
+def ds_dict_lipschitz(dct) -> float:
+    L = ctypes.c_double()
+    _check(lib().ds_dict_lipschitz(dct, ctypes.byref(L)), "ds_dict_lipschitz")
+    return L.value
+
+
+def ds_lambda_max(ctx, dct, y) -> float:
+    v = ctypes.c_double()
+    _check(lib().ds_lambda_max(ctx, dct, _ptr(y)[0], ctypes.byref(v)), "ds_lambda_max")
+    return v.value
+
+
+def ds_solve(ctx, dct, y, lam, opt, x_out, x0=None):
+    r = ds_result()
+    st = lib().ds_solve(ctx, dct, _ptr(y)[0], float(lam), ctypes.byref(opt), _ptr(x0)[0], _ptr(x_out)[0],
+                        ctypes.byref(r))
+    _check(st, "ds_solve")
+    return r.as_dict()
+
+
+def ds_solve_path(ctx, dct, y, lambdas, opt, X_out, x0=None):
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    res = (ds_result * lam.size)()
+    st = lib().ds_solve_path(ctx, dct, _ptr(y)[0], int(lam.size), lam.ctypes.data, ctypes.byref(opt),
+                             _ptr(x0)[0], _ptr(X_out)[0], res)
+    _check(st, "ds_solve_path")
+    return [r.as_dict() for r in res]
+
+
+def ds_set_history(ctx, hist=None):
+    if hist is None:
+        _check(lib().ds_set_history(ctx, None, 0), "ds_set_history")
+    else:
+        _check(lib().ds_set_history(ctx, _ptr(hist)[0], int(hist.shape[0])), "ds_set_history")

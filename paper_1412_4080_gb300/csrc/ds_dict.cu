@@ -1,0 +1,438 @@
+// ds_dict.cu -- per-dictionary precompute (independent of y and lambda):
+//   - column norms ||d_i|| (compensated dot products);
+//   - per group: the Gram matrix D_g^T D_g and its largest eigenvalue by cyclic
+//     Jacobi, giving ||D_g||_2 rounded up (the group sphere test of Lemma 7 needs
+//     an upper bound), and ||D_g||_F / w_g for the rounding bound of the solver;
+//   - the step constant L >= ||D||_2^2 by Lanczos on D D^T (three-term
+//     recurrence, FP64 scalars), bounded above by the Ritz value plus its
+//     residual norm.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "ds_internal.h"
+
+namespace ds {
+
+constexpr int kDictThreads = 512;
+
+// ---------------------------------------------------------------- norms
+
+template <typename T>
+__global__ void colnorm_kernel(const T* __restrict__ D, int N, int K, int ld, double* __restrict__ out)
+{
+    using V = typename Vec4<T>::type;
+    constexpr int EV = 16 / sizeof(T);
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int ldv = ld / EV;
+    for (int i = gw; i < K; i += nwarps) {
+        const V* col = reinterpret_cast<const V*>(D + (size_t)i * ld);
+        typename Dot2<T>::type acc;
+        for (int v = lane; v < ldv; v += 32) {
+            V d = __ldg(col + v);
+            if constexpr (EV == 4) {
+                acc.add(d.x, d.x); acc.add(d.y, d.y); acc.add(d.z, d.z); acc.add(d.w, d.w);
+            } else {
+                acc.add(d.x, d.x); acc.add(d.y, d.y);
+            }
+        }
+        double s = warp_sum(acc.value());
+        if (lane == 0) out[i] = sqrt(s);
+    }
+}
+
+// One CTA per group: Gram matrix (compensated dots, one warp per entry pair),
+// then thread 0 runs cyclic Jacobi on it in FP64.  The largest eigenvalue is
+// bounded above by max diagonal + Frobenius norm of the off-diagonal rest
+// (Weyl), and rounded up by a relative 1e-12.
+template <typename T>
+__global__ void group_spec_kernel(const T* __restrict__ D, int N, int ld, const int* __restrict__ goff,
+                                  const double* __restrict__ w, double* __restrict__ spec, double* __restrict__ fw)
+{
+    __shared__ double A[32 * 32];
+    const int g = blockIdx.x;
+    const int c0 = goff[g], m = goff[g + 1] - c0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int npairs = m * (m + 1) / 2;
+    for (int pr = warp; pr < npairs; pr += nw) {
+        int p = 0, rem = pr;
+        while (rem >= m - p) { rem -= m - p; p++; }
+        const int q = p + rem;
+        const T* a = D + (size_t)(c0 + p) * ld;
+        const T* bcol = D + (size_t)(c0 + q) * ld;
+        typename Dot2<T>::type acc;
+        for (int r = lane; r < N; r += 32) acc.add(a[r], bcol[r]);
+        double s = warp_sum(acc.value());
+        if (lane == 0) { A[p * m + q] = s; A[q * m + p] = s; }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double tr = 0.0;
+    for (int p = 0; p < m; p++) tr += A[p * m + p];
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0, dg = 0.0;
+        for (int p = 0; p < m; p++)
+            for (int q = 0; q < m; q++) {
+                if (p != q) off += A[p * m + q] * A[p * m + q];
+                else dg += A[p * m + p] * A[p * m + p];
+            }
+        if (off <= 1e-30 * dg) break;
+        for (int p = 0; p < m - 1; p++)
+            for (int q = p + 1; q < m; q++) {
+                double apq = A[p * m + q];
+                if (apq == 0.0) continue;
+                double app = A[p * m + p], aqq = A[q * m + q];
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
+                for (int k = 0; k < m; k++) {
+                    double akp = A[k * m + p], akq = A[k * m + q];
+                    A[k * m + p] = c * akp - s * akq;
+                    A[k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; k++) {
+                    double apk = A[p * m + k], aqk = A[q * m + k];
+                    A[p * m + k] = c * apk - s * aqk;
+                    A[q * m + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    double mx = A[0], off = 0.0;
+    for (int p = 0; p < m; p++) {
+        mx = fmax(mx, A[p * m + p]);
+        for (int q = 0; q < m; q++)
+            if (p != q) off += A[p * m + q] * A[p * m + q];
+    }
+    double e = (mx + sqrt(off)) * (1.0 + 1e-12);
+    spec[g] = sqrt(fmax(e, 0.0)) * (1.0 + 1e-12);
+    fw[g] = sqrt(fmax(tr, 0.0)) * (1.0 + 1e-12) / w[g];
+}
+
+__global__ void max_kernel(const double* __restrict__ v, int n, double* out)
+{
+    __shared__ double s[32];
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, v[i]);
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) r = fmax(r, s[k]);
+        *out = r * (1.0 + 1e-12);
+    }
+}
+
+// ---------------------------------------------------------------- Lanczos
+
+template <typename T>
+struct LzP {
+    const T* D;
+    int N, K, ld;
+    int k0, k1;        // steps to run
+    double* q;         // N, current Lanczos vector q_k
+    double* qp;        // N, previous q_{k-1}
+    double* wv;        // N, work vector
+    T* p;              // K, D^T q
+    double* wpart;     // nseg x N partial products
+    double* part;      // G partials
+    double* alpha;     // steps
+    double* beta;      // steps
+    int nseg;
+    GridBarrier* bar;
+    int* err;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P)
+{
+    using V = typename Vec4<T>::type;
+    constexpr int EV = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* q_s = reinterpret_cast<T*>(smem_raw);
+    __shared__ double s_red[32];
+    __shared__ double s_sc[4];
+    __shared__ T s_acc[kDictThreads / 32][32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kDictThreads / 32;
+    const int b = blockIdx.x, G = gridDim.x;
+    unsigned int gen = 0;
+    const int N = P.N, K = P.K, ld = P.ld, ldv = ld / EV;
+    const int ntiles = (N + 31) / 32;
+    for (int k = P.k0; k < P.k1; k++) {
+        // p = D^T q_k
+        for (int r = tid; r < ldv * EV; r += kDictThreads) q_s[r] = r < N ? (T)__ldcg(P.q + r) : T(0);
+        __syncthreads();
+        const V* qv = reinterpret_cast<const V*>(q_s);
+        for (int i = b * nw + warp; i < K; i += G * nw) {
+            const V* col = reinterpret_cast<const V*>(P.D + (size_t)i * ld);
+            T s = T(0);
+            for (int v = lane; v < ldv; v += 32) {
+                V d = __ldg(col + v);
+                V qq = qv[v];
+                if constexpr (EV == 4) {
+                    s = fmaf(d.x, qq.x, s); s = fmaf(d.y, qq.y, s); s = fmaf(d.z, qq.z, s); s = fmaf(d.w, qq.w, s);
+                } else {
+                    s = fma(d.x, qq.x, s); s = fma(d.y, qq.y, s);
+                }
+            }
+            s = warp_sum(s);
+            if (lane == 0) P.p[i] = s;
+        }
+        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
+        // partial w = D p over (row tile, column segment)
+        for (int item = b; item < ntiles * P.nseg; item += G) {
+            const int tile = item % ntiles, seg = item / ntiles;
+            const int r = tile * 32 + lane;
+            const int cs = (int)((long long)seg * K / P.nseg), ce = (int)((long long)(seg + 1) * K / P.nseg);
+            T acc = T(0);
+            for (int i = cs + warp; i < ce; i += nw) {
+                T pi = __ldcg(P.p + i);
+                T d = r < N ? __ldg(P.D + (size_t)i * ld + r) : T(0);
+                acc = fma(pi, d, acc);
+            }
+            s_acc[warp][lane] = acc;
+            __syncthreads();
+            if (warp == 0 && r < N) {
+                double s = 0.0;
+                for (int k2 = 0; k2 < nw; k2++) s += (double)s_acc[k2][lane];
+                P.wpart[(size_t)seg * N + r] = s;
+            }
+            __syncthreads();
+        }
+        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
+        // w = sum of partials - beta_{k-1} q_{k-1};  alpha = q^T w
+        const double bprev = k > 0 ? P.beta[k - 1] : 0.0;
+        double pa = 0.0;
+        for (int r = b * kDictThreads + tid; r < N; r += G * kDictThreads) {
+            double s = 0.0;
+            for (int sg = 0; sg < P.nseg; sg++) s += __ldcg(P.wpart + (size_t)sg * N + r);
+            s -= bprev * __ldcg(P.qp + r);
+            P.wv[r] = s;
+            pa += s * __ldcg(P.q + r);
+        }
+        pa = warp_sum(pa);
+        if (lane == 0) s_red[warp] = pa;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k2 = 0; k2 < nw; k2++) t += s_red[k2];
+            P.part[b] = t;
+        }
+        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
+        if (warp == 0) {
+            double a = warp_sum_fixed(P.part, G, lane);
+            if (lane == 0) s_sc[0] = a;
+        }
+        __syncthreads();
+        const double alpha = s_sc[0];
+        double pb = 0.0;
+        for (int r = b * kDictThreads + tid; r < N; r += G * kDictThreads) {
+            double s = __ldcg(P.wv + r) - alpha * __ldcg(P.q + r);
+            P.wv[r] = s;
+            pb += s * s;
+        }
+        pb = warp_sum(pb);
+        __syncthreads();
+        if (lane == 0) s_red[warp] = pb;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int k2 = 0; k2 < nw; k2++) t += s_red[k2];
+            P.part[b] = t;
+        }
+        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
+        if (warp == 0) {
+            double bt = sqrt(warp_sum_fixed(P.part, G, lane));
+            if (lane == 0) s_sc[1] = bt;
+        }
+        __syncthreads();
+        const double beta = s_sc[1];
+        if (b == 0 && tid == 0) { P.alpha[k] = alpha; P.beta[k] = beta; }
+        for (int r = b * kDictThreads + tid; r < N; r += G * kDictThreads) {
+            double qk = __ldcg(P.q + r);
+            P.qp[r] = qk;
+            P.q[r] = beta > 0.0 ? __ldcg(P.wv + r) / beta : 0.0;
+        }
+        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
+        if (!(beta > 0.0)) return;  // invariant subspace: T_k is exact
+    }
+}
+
+// Largest eigenvalue of the symmetric tridiagonal (a[0..m), b[0..m-1)) by Sturm
+// bisection, and the last component of its unit eigenvector by inverse iteration.
+static void tridiag_top(const std::vector<double>& a, const std::vector<double>& bb, int m, double* theta,
+                        double* last)
+{
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < m; i++) {
+        double r = (i > 0 ? fabs(bb[i - 1]) : 0.0) + (i + 1 < m ? fabs(bb[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    auto count_below = [&](double x) {  // eigenvalues < x
+        int c = 0;
+        double d = 1.0;
+        for (int i = 0; i < m; i++) {
+            double off = i > 0 ? bb[i - 1] * bb[i - 1] : 0.0;
+            d = a[i] - x - (i > 0 ? off / d : 0.0);
+            if (d == 0.0) d = -1e-300;
+            if (d < 0) c++;
+        }
+        return c;
+    };
+    for (int it = 0; it < 200; it++) {
+        double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (count_below(mid) == m) hi = mid;
+        else lo = mid;
+    }
+    *theta = hi;
+    // inverse iteration with shift slightly above theta
+    double sh = hi + 1e-10 * std::max(1.0, fabs(hi));
+    std::vector<double> x(m, 1.0), cp(m), dp(m);
+    for (int it = 0; it < 4; it++) {
+        // solve (T - sh I) y = x (Thomas)
+        double den = a[0] - sh;
+        cp[0] = m > 1 ? bb[0] / den : 0.0;
+        dp[0] = x[0] / den;
+        for (int i = 1; i < m; i++) {
+            den = (a[i] - sh) - bb[i - 1] * cp[i - 1];
+            cp[i] = i + 1 < m ? bb[i] / den : 0.0;
+            dp[i] = (x[i] - bb[i - 1] * dp[i - 1]) / den;
+        }
+        x[m - 1] = dp[m - 1];
+        for (int i = m - 2; i >= 0; i--) x[i] = dp[i] - cp[i] * x[i + 1];
+        double nrm = 0.0;
+        for (int i = 0; i < m; i++) nrm += x[i] * x[i];
+        nrm = sqrt(nrm);
+        for (int i = 0; i < m; i++) x[i] /= nrm;
+    }
+    *last = x[m - 1];
+}
+
+template <typename T>
+static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
+{
+    const int N = (int)dict->N, K = (int)dict->K, ld = (int)dict->ld;
+    const int G = ctx->num_sms;
+    const int ntiles = (N + 31) / 32;
+    const int nseg = std::max(1, std::min(64, G / std::max(1, ntiles)));
+    const int maxsteps = std::min(N, 320);
+    // workspace
+    size_t bytes = 0;
+    auto sz = [&](size_t n) { bytes = align_up(bytes, 256) + n; };
+    sz(sizeof(GridBarrier)); sz(8 * N); sz(8 * N); sz(8 * N); sz(sizeof(T) * K); sz(8ull * nseg * N);
+    sz(8 * G); sz(8 * maxsteps); sz(8 * maxsteps); sz(sizeof(int));
+    ds_status st = ctx_reserve(ctx, bytes + 256);
+    if (st != DS_OK) return st;
+    char* base = reinterpret_cast<char*>(ctx->ws);
+    size_t off = 0;
+    auto take = [&](size_t n) { off = align_up(off, 256); void* p = base + off; off += n; return p; };
+    LzP<T> P;
+    P.D = reinterpret_cast<const T*>(dict->D);
+    P.N = N; P.K = K; P.ld = ld;
+    P.bar = (GridBarrier*)take(sizeof(GridBarrier));
+    P.q = (double*)take(8 * N);
+    P.qp = (double*)take(8 * N);
+    P.wv = (double*)take(8 * N);
+    P.p = (T*)take(sizeof(T) * K);
+    P.wpart = (double*)take(8ull * nseg * N);
+    P.part = (double*)take(8 * G);
+    P.alpha = (double*)take(8 * maxsteps);
+    P.beta = (double*)take(8 * maxsteps);
+    P.err = (int*)take(sizeof(int));
+    P.nseg = nseg;
+    cudaStream_t s = ctx->stream;
+    // deterministic pseudo-random unit start vector
+    std::vector<double> q0(N);
+    double nq = 0.0;
+    unsigned long long h = 0x9E3779B97F4A7C15ull;
+    for (int r = 0; r < N; r++) {
+        h ^= h >> 12; h ^= h << 25; h ^= h >> 27;
+        double v = (double)((h * 0x2545F4914F6CDD1Dull) >> 11) / 9007199254740992.0 - 0.5;
+        q0[r] = v;
+        nq += v * v;
+    }
+    for (int r = 0; r < N; r++) q0[r] /= sqrt(nq);
+    if (cudaMemcpyAsync(P.q, q0.data(), 8 * N, cudaMemcpyHostToDevice, s) != cudaSuccess) return DS_ERR_CUDA;
+    if (cudaMemsetAsync(P.qp, 0, 8 * N, s) != cudaSuccess) return DS_ERR_CUDA;
+    if (cudaMemsetAsync(P.err, 0, sizeof(int), s) != cudaSuccess) return DS_ERR_CUDA;
+    size_t smem = (size_t)ld * sizeof(T) + 16;
+    if (smem > ctx->smem_optin - 16 * 1024) return DS_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(lanczos_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    std::vector<double> a, bb;
+    int k = 0;
+    double theta = 0.0, res = 0.0;
+    while (k < maxsteps) {
+        int k1 = std::min(maxsteps, k == 0 ? 48 : k + 32);
+        P.k0 = k;
+        P.k1 = k1;
+        if (cudaMemsetAsync(P.bar, 0, sizeof(GridBarrier), s) != cudaSuccess) return DS_ERR_CUDA;
+        void* args[] = {(void*)&P};
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)lanczos_kernel<T>, dim3(G), dim3(kDictThreads), args,
+                                                    smem, s);
+        if (e != cudaSuccess) return DS_ERR_CUDA;
+        a.resize(k1);
+        bb.resize(k1);
+        int err = 0;
+        if (cudaMemcpyAsync(a.data(), P.alpha, 8 * k1, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DS_ERR_CUDA;
+        if (cudaMemcpyAsync(bb.data(), P.beta, 8 * k1, cudaMemcpyDeviceToHost, s) != cudaSuccess) return DS_ERR_CUDA;
+        if (cudaMemcpyAsync(&err, P.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return DS_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return DS_ERR_CUDA;
+        if (err) return DS_ERR_TIMEOUT;
+        // an exhausted Krylov space (beta == 0) ends the recurrence early
+        int m = k1;
+        for (int i = k; i < k1; i++)
+            if (!(bb[i] > 1e-300)) { m = i + 1; break; }
+        double last;
+        tridiag_top(a, bb, m, &theta, &last);
+        res = fabs(bb[m - 1] * last);
+        k = k1;
+        if (m < k1 || res <= 1e-9 * theta) break;
+    }
+    // FP32 products: add a relative margin for their rounding
+    const double margin = sizeof(T) == 4 ? 2e-5 : 1e-12;
+    dict->L = (theta + res) * (1.0 + margin);
+    return DS_OK;
+}
+
+template <typename T>
+static ds_status precompute_t(ds_ctx* ctx, ds_dict* dict, const double* w_host)
+{
+    cudaStream_t s = ctx->stream;
+    const int N = (int)dict->N, K = (int)dict->K, ld = (int)dict->ld;
+    colnorm_kernel<T><<<ctx->num_sms * 4, 256, 0, s>>>(reinterpret_cast<const T*>(dict->D), N, K, ld, dict->colnorm);
+    if (cudaGetLastError() != cudaSuccess) return DS_ERR_CUDA;
+    double* d_fmax = nullptr;
+    if (cudaMalloc(&d_fmax, sizeof(double)) != cudaSuccess) return DS_ERR_OOM;
+    if (dict->is_group) {
+        double* fw = nullptr;
+        if (cudaMalloc(&fw, sizeof(double) * dict->nG) != cudaSuccess) { cudaFree(d_fmax); return DS_ERR_OOM; }
+        group_spec_kernel<T><<<dict->nG, 256, 0, s>>>(reinterpret_cast<const T*>(dict->D), N, ld, dict->goff, dict->w,
+                                                      dict->spec, fw);
+        max_kernel<<<1, 1024, 0, s>>>(fw, dict->nG, d_fmax);
+        cudaStreamSynchronize(s);
+        cudaFree(fw);
+    } else {
+        max_kernel<<<1, 1024, 0, s>>>(dict->colnorm, K, d_fmax);
+    }
+    if (cudaGetLastError() != cudaSuccess) { cudaFree(d_fmax); return DS_ERR_CUDA; }
+    double fm = 0.0;
+    cudaMemcpyAsync(&fm, d_fmax, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) { cudaFree(d_fmax); return DS_ERR_CUDA; }
+    cudaFree(d_fmax);
+    dict->fmax = fm;
+    (void)w_host;
+    return lanczos_t<T>(ctx, dict);
+}
+
+ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host)
+{
+    if (dict->dtype == DS_FP32) return precompute_t<float>(ctx, dict, w_host);
+    return precompute_t<double>(ctx, dict, w_host);
+}
+
+}  // namespace ds

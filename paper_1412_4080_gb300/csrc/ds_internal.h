@@ -1,0 +1,90 @@
+// ds_internal.h -- structures shared by the translation units of libdscreen
+// (host side of the C ABI and the kernel launchers).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dscreen.h"
+#include "ds_common.cuh"
+
+struct ds_ctx {
+    int device;
+    cudaStream_t stream;
+    int num_sms;
+    size_t smem_optin;
+    // solve workspace (grown on demand, bump-allocated)
+    void* ws;
+    size_t ws_bytes;
+    // device-side result staging and pinned host copy
+    void* d_res;
+    void* h_res;
+    size_t res_cap;  // in results
+    // staging for host y / x0 / x_out
+    void* d_io;
+    size_t io_bytes;
+    double* hist;
+    int hist_rows;
+    cudaEvent_t ev0, ev1;
+};
+
+struct ds_dict {
+    ds_ctx* ctx;
+    int dtype;        // DS_FP32 or DS_FP64
+    int64_t N, K, ld; // ld: padded leading dimension of the owned copy (elements)
+    void* D;          // device copy, ld * K elements, zero rows N..ld-1
+    double* colnorm;  // device, K: ||d_i||
+    int is_group;
+    int nG;           // groups (Lasso: K)
+    int max_gsize;
+    int* goff;        // device, nG + 1 (Lasso: nullptr)
+    double* w;        // device, nG (Lasso: nullptr)
+    double* spec;     // device, nG: upper estimate of ||D_g||_2 (Lasso: nullptr)
+    double fmax;      // max_g ||D_g||_F / w_g (Lasso: max_i ||d_i||)
+    double L;         // upper estimate of ||D||_2^2
+};
+
+namespace ds {
+
+// Per-solve result written by the solve kernel (one per lambda).
+struct DevResult {
+    int iters;
+    int status;
+    long long n_active;
+    long long nnz;
+    double gap, primal, dual, lambda, lambda_max;
+};
+
+// Error codes raised inside kernels (DevResult.status).
+constexpr int kDevOk = 0;
+constexpr int kDevNotConverged = 5;
+constexpr int kDevTimeout = 4;
+
+// Host-side launchers (defined in ds_solve.cu / ds_dict.cu).
+ds_status launch_solve(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, const void* x0_dev, int n_lambda,
+                       const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,
+                       DevResult* res_host, float* ms);
+ds_status launch_lambda_max(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, double* lmax);
+ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host);
+
+// Workspace helpers (ds_api.cu).
+ds_status ctx_reserve(ds_ctx* ctx, size_t bytes);
+ds_status ctx_reserve_results(ds_ctx* ctx, size_t n);
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Simple bump allocator over a workspace block.
+struct Bump {
+    char* base;
+    size_t off;
+    template <typename U>
+    U* take(size_t n)
+    {
+        off = align_up(off, 256);
+        U* p = reinterpret_cast<U*>(base ? base + off : nullptr);
+        off += n * sizeof(U);
+        return p;
+    }
+};
+
+}  // namespace ds
