@@ -27,6 +27,11 @@ def ctx():
     ds.ds_destroy(c)
 
 
+def _f32(a):
+    """The FP32 problem the GPU solves, in FP64 for the oracle."""
+    return a.astype(np.float32).astype(np.float64)
+
+
 def _dev_dict(D, dtype):
     # column-major (N, K) device tensor: transpose of a contiguous (K, N)
     return torch.from_numpy(np.ascontiguousarray(D.T)).to("cuda", dtype).t()
@@ -70,6 +75,7 @@ CASES = [
 @pytest.mark.parametrize("test", ["none", "safe", "dst3", "dome"])
 def test_lasso_fp32_parity(ctx, N, K, ratio, test):
     D, y, _ = gen.lasso_problem(N, K, seed=N + K, p=0.02)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y)
     lam = ratio * lm
     L = oracle.spectral_norm_sq(D, tol=1e-10, max_iter=5000) * (1 + 1e-6)
@@ -92,6 +98,7 @@ def test_lasso_fp32_parity(ctx, N, K, ratio, test):
 def test_lasso_fp32_stops_on_gap(ctx, test, alg):
     N, K = 513, 2049
     D, y, _ = gen.lasso_problem(N, K, seed=7, p=0.01)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y)
     lam = 0.5 * lm
     dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
@@ -140,6 +147,7 @@ def test_config1_fp64_ista_dst3(ctx, dynamic):
 def test_group_lasso_fp32_parity(ctx, test, ratio):
     N, K = 600, 1800
     D, y, _, goff, w = gen.config3(31, N=N, K=K, gsize=10, n_active=6)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y, goff, w)
     lam = ratio * lm
     L = oracle.spectral_norm_sq(D, tol=1e-10, max_iter=5000) * (1 + 1e-6)
@@ -166,6 +174,7 @@ def test_group_lasso_ragged_groups(ctx):
     w = g.uniform(0.5, 2.0, size=len(sizes))
     x0 = gen.group_x0(goff, 4, g)
     y = gen.observe(D, x0, g)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y, goff, w)
     lam = 0.4 * lm
     L = oracle.spectral_norm_sq(D) * (1 + 1e-6)
@@ -180,13 +189,13 @@ def test_group_lasso_ragged_groups(ctx):
 
 def test_lambda_max_and_trivial_case(ctx):
     D, y, _ = gen.lasso_problem(333, 999, seed=5)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y)
     dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
     try:
         yt = torch.from_numpy(y).to("cuda", torch.float32)
         got = ds.ds_lambda_max(ctx, dct, yt)
-        # FP32 input rounding of y and D only
-        assert abs(got - lm) <= 1e-6 * lm
+        assert abs(got - lm) <= 1e-12 * lm
         x, r = _solve_gpu(ctx, dct, y, got * 1.0001, torch.float32, 999)
         assert r["iters"] == 0 and not x.any() and r["gap"] == 0.0
     finally:
@@ -197,6 +206,7 @@ def test_step_constant_upper_bound(ctx):
     for (N, K, seed) in ((100, 500, 1), (2000, 10000, 2), (257, 257, 3)):
         g = gen.rng(seed)
         D = gen.gaussian_dict(N, K, g)
+        D = _f32(D)
         dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
         L = ds.ds_dict_lipschitz(dct)
         ds.ds_dict_destroy(dct)
@@ -226,6 +236,7 @@ def test_path_and_host_buffers_match_device_single_solves(ctx):
 def test_warm_start_from_solution(ctx):
     N, K = 300, 1200
     D, y, _ = gen.lasso_problem(N, K, seed=13)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y)
     lam = 0.4 * lm
     ref = oracle.solve(D, y, lam, test="dst3", tol=1e-14, max_iter=100000)
@@ -243,12 +254,13 @@ def test_warm_start_from_solution(ctx):
 
 def test_history_nested_and_gap_nonnegative(ctx):
     D, y, _ = gen.lasso_problem(800, 4000, seed=17)
+    D, y = _f32(D), _f32(y)
     dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
     hist = torch.zeros((5000, 6), device="cuda", dtype=torch.float64)
     ds.ds_set_history(ctx, hist)
     try:
         lm, _, _ = oracle.lambda_max(D, y)
-        x, r = _solve_gpu(ctx, dct, y, 0.6 * lm, torch.float32, 4000, test="dome", tol_gap_rel=1e-6,
+        x, r = _solve_gpu(ctx, dct, y, 0.75 * lm, torch.float32, 4000, test="dome", tol_gap_rel=1e-6,
                           max_iter=5000)
     finally:
         ds.ds_set_history(ctx, None)
@@ -264,6 +276,7 @@ def test_config2_full_size(ctx, ratio):
     """2000 x 10000 FP32, FISTA + DST3, gap 1e-6 (the benchmark's problem):
     the GPU's answer checked by its FP64 duality gap and the KKT conditions."""
     D, y, _ = gen.config2(1002)
+    D, y = _f32(D), _f32(y)
     lm, _, _ = oracle.lambda_max(D, y)
     lam = ratio * lm
     dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
