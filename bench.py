@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the dynamic-screening Lasso solver on one GB300 (or N, one per rank).
+
+Workload (one "step"): the 2000 x 10000 FP32 Lasso problem of the paper's
+synthetic experiments -- Gaussian dictionary with unit-norm columns,
+Bernoulli(0.01)-Gaussian x0, y = D x0 + noise at exactly 20 dB (seed 1002) --
+solved by FISTA with dynamic SAFE, DST3 and Dome screening for
+lambda / lambda_max in {0.1, 0.3, 0.5, 0.7, 0.9}, each to duality gap
+1e-6 * 1/2 ||y||^2: 15 solves.  The step also registers the dictionary
+(column norms and the Lanczos step bound), so it measures the whole job from
+D and y resident in HBM to the 15 solutions.
+
+Metric: solves per second (whole job; N ranks each run the step on their own
+GPU, weak scaling, no collective on the data path).  The L2 (129 MB) is
+flushed by a 256 MB write before every timed step, since D (80 MB) fits in it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RATIOS = (0.1, 0.3, 0.5, 0.7, 0.9)
+TESTS = ("safe", "dst3", "dome")
+TOL = 1e-6
+METRIC = "Lasso solves/s to gap 1e-6 (batched+served vs plain); HBM GB/s; p50/p99 latency"
+WORKLOAD = ("Lasso FISTA + dynamic SAFE/DST3/Dome, FP32, D 2000x10000 Gaussian unit-norm columns, "
+            "x0 Bernoulli(0.01)-Gaussian, y = D x0 + noise at 20 dB (seed 1002), "
+            "lambda/lambda_max in {0.1,0.3,0.5,0.7,0.9}, gap 1e-6 * 1/2||y||^2; step = dictionary "
+            "precompute + 15 solves")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def problem():
+    import gen
+    D, y, _ = gen.config2(1002)
+    return D.astype(np.float32), y.astype(np.float32)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores (one core: it is single-threaded)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    D32, y32 = problem()
+    D = D32.astype(np.float64)
+    y = y32.astype(np.float64)
+    L = float(np.linalg.norm(D, 2) ** 2) * (1 + 1e-6)
+    oracle.build()
+
+    def step(k):
+        test = TESTS[k % len(TESTS)]
+        lm, _, _ = oracle.lambda_max(D, y)
+        n = 0
+        for r in RATIOS:
+            oracle.solve(D, y, r * lm, alg="fista", test=test, tol=TOL, max_iter=20000, L=L)
+            n += 1
+        return n
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    solves = 0
+    for k in range(args.steps):
+        solves += step(k)
+    dt = time.perf_counter() - t0
+    v = solves / dt
+    sample = ("oracle FISTA to gap 1e-6 on the same 2000x10000 problem, 5 lambda values per step with one "
+              "test per step (SAFE, DST3, Dome in turn); step constant from LAPACK, untimed")
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD},
+                      "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def cpu_baseline(D32, y32, budget_s=30.0):
+    """Oracle solves of a bounded sample of the workload (DST3, the 5 lambda values)."""
+    import oracle
+    D = D32.astype(np.float64)
+    y = y32.astype(np.float64)
+    L = float(np.linalg.norm(D, 2) ** 2) * (1 + 1e-6)
+    oracle.build()
+    lm, _, _ = oracle.lambda_max(D, y)
+    t0 = time.perf_counter()
+    n = 0
+    for r in (0.9, 0.7, 0.5, 0.3, 0.1):
+        oracle.solve(D, y, r * lm, alg="fista", test="dst3", tol=TOL, max_iter=20000, L=L)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} oracle FISTA+DST3 solves (lambda/lambda_max = 0.9, 0.7, 0.5, 0.3, 0.1 in turn) of the "
+                      f"same problem in {dt:.1f} s, single thread"}
+
+
+# ------------------------------------------------------------------------ our arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-large", action="store_true", help="skip the 8192x65536 HBM roofline run")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--profile-one", action="store_true",
+                    help="register the dictionary and run one 5-lambda DST3 path, then exit (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.profile_one:
+        profile_one()
+        return
+
+    import torch
+    import paper_1412_4080_gb300 as ds
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ds.lib()
+
+    D32, y32 = problem()
+    N, K = D32.shape
+    dev = torch.device("cuda", local)
+    Dt = torch.from_numpy(np.ascontiguousarray(D32.T)).to(dev).t()  # column-major (N, K)
+    yt = torch.from_numpy(y32).to(dev)
+    X = torch.empty((len(RATIOS), K), device=dev)
+    flush = torch.empty(64 * 1024 * 1024, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream(dev)
+    ctx = ds.ds_create(local, stream)
+    ratios = np.array(RATIOS)
+    opts = {t: ds.ds_options_default(test=t, alg="fista", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
+            for t in TESTS}
+
+    def step(y=yt, Xo=X, D=Dt):
+        dct = ds.ds_dict_create(ctx, D)
+        out = []
+        for t in TESTS:
+            out += ds.ds_solve_path(ctx, dct, y, ratios, opts[t], Xo)
+        ds.ds_dict_destroy(dct)
+        return out
+
+    for _ in range(args.warmup):
+        res = step()
+    bad = [r for r in res if r["status"] != 0]
+    if bad:
+        raise SystemExit(f"solves did not converge: {bad[:2]}")
+
+    launches0 = ds.ds_ctx_kernel_launches(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
+    kern_ms = 0.0
+    cols = 0
+    iters = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            res = step()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            total_ms += ev0.elapsed_time(ev1)
+            kern_ms += sum(r["ms"] for r in res)
+            cols += sum(r["cols_corr"] + r["cols_synth"] for r in res)
+            iters += [r["iters"] for r in res]
+    torch.cuda.synchronize()
+    launches = ds.ds_ctx_kernel_launches(ctx) - launches0
+    if dist:
+        dist.barrier()
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solves_per_step = len(TESTS) * len(RATIOS)
+    value = solves_per_step * args.steps * world / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the persistent solve kernel): algorithmic bytes =
+    # dictionary columns read (correlations + syntheses) x N x 4 bytes
+    peak, peak_kind = _peaks()
+    bytes_alg = cols * N * 4
+    achieved = bytes_alg / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_kind": peak_kind, "kernel": "solve_kernel<float>",
+            "note": "D (80 MB) is L2-resident across iterations inside a solve; see roofline_large for D > L2"}
+
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "solves_per_step": solves_per_step, "N": N, "K": K,
+                      "l2": "flushed before each timed step (256 MB write)", "parallelism": f"replicas{world}"},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+           "iters": {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},
+           "solve_kernel_ms_per_step": kern_ms / args.steps}
+
+    # ------------------------------------------------ e2e through the C ABI, host buffers
+    Dh = torch.from_numpy(np.asfortranarray(D32).T.copy()).pin_memory()  # (K, N) rows = atoms
+    Dh_np = Dh.numpy().T  # Fortran-ordered (N, K) view of pinned memory
+    yh = torch.from_numpy(y32.copy()).pin_memory().numpy()
+    Xh = torch.empty((len(RATIOS), K), dtype=torch.float32).pin_memory().numpy()
+    step(yh, Xh, Dh_np)
+    e2e_t = []
+    for _ in range(args.e2e_steps):
+        t0 = time.perf_counter()
+        step(yh, Xh, Dh_np)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t))
+    out["e2e"] = {"value": solves_per_step * world / e2e_s, "unit": "solves/s",
+                  "h2d_bytes_per_step": int(D32.nbytes + len(TESTS) * y32.nbytes),
+                  "d2h_bytes_per_step": int(len(TESTS) * Xh.nbytes)}
+
+    # ------------------------------------------------ HBM roofline with D larger than L2
+    if not args.no_large:
+        out["roofline_large"] = large_roofline(ds, ctx, dev, stream, peak, peak_kind)
+
+    ds.ds_destroy(ctx)
+    if rank == 0 and not args.no_cpu and world == 1:
+        out["cpu_baseline"] = cpu_baseline(D32, y32)
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def profile_one():
+    import torch
+    import paper_1412_4080_gb300 as ds
+    D32, y32 = problem()
+    Dt = torch.from_numpy(np.ascontiguousarray(D32.T)).cuda().t()
+    yt = torch.from_numpy(y32).cuda()
+    ctx = ds.ds_create(0, torch.cuda.current_stream())
+    dct = ds.ds_dict_create(ctx, Dt)
+    X = torch.empty((len(RATIOS), D32.shape[1]), device="cuda")
+    o = ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
+    res = ds.ds_solve_path(ctx, dct, yt, np.array(RATIOS), o, X)
+    ds.ds_dict_destroy(dct)
+    ds.ds_destroy(ctx)
+    print(json.dumps([{k: r[k] for k in ("iters", "ms", "n_active", "cols_corr", "cols_synth")} for r in res]))
+
+
+def large_roofline(ds, ctx, dev, stream, peak, peak_kind):
+    """One unscreened-regime solve (lambda = 0.5 lambda_max) on an 8192 x 65536 FP32
+    Gaussian unit-norm dictionary (2.1 GB > L2): algorithmic GB/s of the solve kernel."""
+    import torch
+    N, K = 8192, 65536
+    g = torch.Generator(device=dev).manual_seed(1102)
+    D = torch.randn((K, N), device=dev, generator=g)
+    D /= D.norm(dim=1, keepdim=True)
+    x0 = torch.zeros(K, device=dev)
+    m = torch.rand(K, device=dev, generator=g) < 0.01
+    x0[m] = torch.randn(int(m.sum()), device=dev, generator=g)
+    s = D.t() @ x0
+    e = torch.randn(N, device=dev, generator=g)
+    y = s + e * (s.norm() / e.norm()) * 0.1
+    Dt = D.t()  # column-major (N, K)
+    dct = ds.ds_dict_create(ctx, Dt)
+    x = torch.empty(K, device=dev)
+    o = ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
+    ds.ds_solve_path(ctx, dct, y, np.array([0.5]), o, x)  # warm
+    r = ds.ds_solve_path(ctx, dct, y, np.array([0.5]), o, x)[0]
+    ds.ds_dict_destroy(dct)
+    del D, Dt
+    torch.cuda.empty_cache()
+    gbs = (r["cols_corr"] + r["cols_synth"]) * N * 4 / (r["ms"] / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_kind": peak_kind, "traffic": None,
+            "workload": "8192x65536 FP32 Gaussian, FISTA+DST3, lambda = 0.5 lambda_max, gap 1e-6",
+            "iters": r["iters"], "kernel_ms": r["ms"]}
+
+
+if __name__ == "__main__":
+    main()

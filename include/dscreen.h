@@ -82,7 +82,9 @@ typedef struct {
     double dual;        /* Dual(mu theta) */
     double lambda;      /* absolute lambda used */
     double lambda_max;  /* lambda_* (Sec. 2.2.2 / eq. gstar) */
-    double ms;          /* device time of the solve kernel, milliseconds */
+    double ms;          /* device time of the solve kernel, milliseconds (path: shared equally) */
+    int64_t cols_corr;  /* dictionary columns read by correlations D_A^T theta (incl. D^T y, D^T n) */
+    int64_t cols_synth; /* dictionary columns read by the sparse syntheses D_A u, D_A x */
 } ds_result;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -150,6 +152,10 @@ ds_status ds_solve(ds_ctx* ctx, const ds_dict* dict, const void* y, double lambd
  * n_lambda, column j = solution for lambdas[j].  res: n_lambda entries. */
 ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* dict, const void* y, int n_lambda, const double* lambdas,
                         const ds_options* opt, const void* x0, void* X_out, ds_result* res);
+
+/* Number of CUDA kernels this context has launched so far (solves, lambda_max
+ * queries and dictionary precomputes).  Errors: DS_ERR_INVALID on NULL. */
+ds_status ds_ctx_kernel_launches(const ds_ctx* ctx, int64_t* n);
 
 /* Record per-iteration history of the following solves into hist (device,
  * max_rows x 6 doubles, row t-1 = iteration t: active atoms, nnz(x), R,

@@ -44,12 +44,13 @@ class ds_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("n_active", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("gap", ctypes.c_double), ("primal", ctypes.c_double),
                 ("dual", ctypes.c_double), ("lambda_", ctypes.c_double), ("lambda_max", ctypes.c_double),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("cols_corr", ctypes.c_int64), ("cols_synth", ctypes.c_int64)]
 
     def as_dict(self):
         return {"iters": self.iters, "status": self.status, "n_active": self.n_active, "nnz": self.nnz,
                 "gap": self.gap, "primal": self.primal, "dual": self.dual, "lambda": self.lambda_,
-                "lambda_max": self.lambda_max, "ms": self.ms}
+                "lambda_max": self.lambda_max, "ms": self.ms, "cols_corr": self.cols_corr,
+                "cols_synth": self.cols_synth}
 
 
 class DscreenError(RuntimeError):
@@ -87,6 +88,7 @@ def lib():
             L.ds_solve_path.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ds_options), vp, vp,
                                         ctypes.POINTER(ds_result)]
             L.ds_set_history.argtypes = [vp, vp, ctypes.c_int]
+            L.ds_ctx_kernel_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
             for name in declared_functions():
                 if name != "ds_status_str":
                     getattr(L, name).restype = ctypes.c_int
@@ -207,6 +209,12 @@ def ds_solve_path(ctx, dct, y, lambdas, opt, X_out, x0=None):
                              _ptr(x0)[0], _ptr(X_out)[0], res)
     _check(st, "ds_solve_path")
     return [r.as_dict() for r in res]
+
+
+def ds_ctx_kernel_launches(ctx) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ds_ctx_kernel_launches(ctx, ctypes.byref(n)), "ds_ctx_kernel_launches")
+    return n.value
 
 
 def ds_set_history(ctx, hist=None):

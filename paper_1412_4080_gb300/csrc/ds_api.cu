@@ -143,6 +143,13 @@ ds_status ds_destroy(ds_ctx* c)
     return DS_OK;
 }
 
+ds_status ds_ctx_kernel_launches(const ds_ctx* ctx, int64_t* n)
+{
+    if (!ctx || !n) return DS_ERR_INVALID;
+    *n = ctx->launches;
+    return DS_OK;
+}
+
 ds_status ds_set_history(ds_ctx* ctx, double* hist, int max_rows)
 {
     if (!ctx || (hist && max_rows < 1)) return DS_ERR_INVALID;
@@ -311,6 +318,8 @@ ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* d, const void* y, int n_lamb
         res[j].lambda = r[j].lambda;
         res[j].lambda_max = r[j].lambda_max;
         res[j].ms = ms / n_lambda;
+        res[j].cols_corr = r[j].cols_corr;
+        res[j].cols_synth = r[j].cols_synth;
     }
     return st;
 }

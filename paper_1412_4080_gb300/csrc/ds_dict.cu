@@ -372,6 +372,7 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
         P.k1 = k1;
         if (cudaMemsetAsync(P.bar, 0, sizeof(GridBarrier), s) != cudaSuccess) return DS_ERR_CUDA;
         void* args[] = {(void*)&P};
+        ctx->launches++;
         cudaError_t e = cudaLaunchCooperativeKernel((const void*)lanczos_kernel<T>, dim3(G), dim3(kDictThreads), args,
                                                     smem, s);
         if (e != cudaSuccess) return DS_ERR_CUDA;
@@ -404,6 +405,7 @@ static ds_status precompute_t(ds_ctx* ctx, ds_dict* dict, const double* w_host)
 {
     cudaStream_t s = ctx->stream;
     const int N = (int)dict->N, K = (int)dict->K, ld = (int)dict->ld;
+    ctx->launches += dict->is_group ? 3 : 2;  // norms, (group spectra), max
     colnorm_kernel<T><<<ctx->num_sms * 4, 256, 0, s>>>(reinterpret_cast<const T*>(dict->D), N, K, ld, dict->colnorm);
     if (cudaGetLastError() != cudaSuccess) return DS_ERR_CUDA;
     double* d_fmax = nullptr;

@@ -25,6 +25,7 @@ struct ds_ctx {
     size_t io_bytes;
     double* hist;
     int hist_rows;
+    long long launches;
     cudaEvent_t ev0, ev1;
 };
 
@@ -53,6 +54,7 @@ struct DevResult {
     long long n_active;
     long long nnz;
     double gap, primal, dual, lambda, lambda_max;
+    long long cols_corr, cols_synth;
 };
 
 // Error codes raised inside kernels (DevResult.status).

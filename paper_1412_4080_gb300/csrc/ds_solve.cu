@@ -550,6 +550,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         int t = 1;
         int iters = 0;
         long long nnz_last = 0;
+        // work counters (dictionary columns read), the precompute passes charged to the first lambda
+        long long cols_corr = j == 0 ? (long long)K * (need_n ? 2 : 1) : 0, cols_synth = 0;
         for (;; t++) {
             // ======================================== (A) scatter + synthesis
             {
@@ -602,6 +604,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     for (int k = 1; k <= G; k++) s_pref[k] += s_pref[k - 1];
                 __syncthreads();
                 const int E = s_pref[G];
+                cols_synth += E;
                 double pa_ = 0.0, pb_ = 0.0, pr_ = 0.0;
                 const int ntiles = (N + kRowTile - 1) / kRowTile;
                 for (int tile = b; tile < ntiles; tile += G) {
@@ -703,6 +706,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 alpha = s_sc[3];
                 beta = s_sc[4];
                 if (stop) break;
+                cols_corr += nA_a;
 
                 // stage theta_t
                 for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? __ldcg(W.theta + r) : T(0);
@@ -955,6 +959,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 R->dual = primal - gap;
                 R->lambda = lam;
                 R->lambda_max = lstar;
+                R->cols_corr = cols_corr;
+                R->cols_synth = cols_synth;
             }
         }
         ok = grid_sync(W.bar, G, gen);
@@ -1096,6 +1102,7 @@ static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, c
     if (occ < 1) return DS_ERR_UNSUPPORTED;
 
     void* args[] = {(void*)&P};
+    ctx->launches++;
     cudaEventRecord(ctx->ev0, s);
     cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel<T>, dim3(G), dim3(kThreads), args, smem, s);
     if (e != cudaSuccess) {
