@@ -321,7 +321,9 @@ def profile_one():
     res = ds.ds_solve_path(ctx, dct, yt, np.array(RATIOS), o, X)
     ds.ds_dict_destroy(dct)
     ds.ds_destroy(ctx)
-    print(json.dumps([{k: r[k] for k in ("iters", "ms", "n_active", "cols_corr", "cols_synth")} for r in res]))
+    yy = float(y32.astype(np.float64) @ y32.astype(np.float64))
+    print(json.dumps([{**{k: r[k] for k in ("iters", "status", "ms", "n_active", "nnz", "cols_corr", "cols_synth")},
+                       "gap_rel": r["gap"] / (0.5 * yy)} for r in res]))
 
 
 def large_roofline(ds, ctx, dev, stream, peak, peak_kind):

@@ -46,14 +46,16 @@ struct Ws {
     double* nvec;
     int* act[2];
     int* aoff[2];
-    T* xc[2];
-    T* uc[2];
-    T* xn;
-    T* un;
+    // iterates are kept in FP64 whatever the dictionary type: in FP32, u - z/L
+    // would quantise z to multiples of L ulp(x), a KKT floor near 1e-6 relative
+    double* xc[2];
+    double* uc[2];
+    double* xn;
+    double* un;
     int* keep;
     int* nz_col;
-    T* nz_u;
-    T* nz_x;
+    double* nz_u;
+    double* nz_x;
     int* s_alo;
     int* c_kg;
     int* c_ka;
@@ -122,6 +124,17 @@ __device__ __forceinline__ double dome_max(double dc0, double t, double psi, dou
     double s2 = fmax(1.0 - t * t, 0.0);
     return dc0 - psi * t + sqrt(rho2) * sqrt(s2);
 }
+
+// synthesis term d * c with an FP64 coefficient c: for FP32 dictionaries c is split
+// into hi + lo floats and d * hi is accumulated with error-free transformations
+__device__ __forceinline__ void syn_add(Dot2f& acc, float d, double c)
+{
+    const float hi = (float)c;
+    const float lo = (float)(c - (double)hi);
+    acc.add(d, hi);
+    acc.c = fmaf(d, lo, acc.c);
+}
+__device__ __forceinline__ void syn_add(Dot2d& acc, double d, double c) { acc.add(d, c); }
 
 __device__ __forceinline__ float4 v4zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ double2 v4zero(double2*) { return make_double2(0.0, 0.0); }
@@ -199,7 +212,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
     __shared__ double s_dred[32];
     __shared__ int s_ired[32];
     __shared__ int s_pref[1025];
-    __shared__ T s_red[2][kThreads / 32][kRowTile];
+    __shared__ double s_red[2][kThreads / 32][kRowTile];
     __shared__ double s_sc[16];
     __shared__ int s_si[8];
 
@@ -426,8 +439,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         const double delta = need_n && nn > 0.0 ? fabs(nty / lam - wstar2) / sqrt(nn) : 0.0;
         const double nstar = P.is_group ? 1.0 : P.colnorm[star];
         const double psi_dome = psi / nstar;
-        const T invL = T(1.0 / P.L);
-        const T thrL = T(lam / P.L);
+        const double invL = 1.0 / P.L;
+        const double thrL = lam / P.L;
         const bool ista = P.alg == 0;
         const bool dyn_test = P.dynamic && P.test != 0;
 
@@ -502,11 +515,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     kept = !kill;
                     W.keep[p] = kept;
                     for (int i = lo_a; i < hi_a; i++) {
-                        T xv = P.x0 ? P.x0[i] : T(0);
-                        if (!kept) xv = T(0);
+                        double xv = P.x0 ? (double)P.x0[i] : 0.0;
+                        if (!kept) xv = 0.0;
                         W.xn[i] = xv;
                         W.un[i] = xv;
-                        cnt += xv != T(0);
+                        cnt += xv != 0.0;
                     }
                     kg += kept;
                     ka += kept ? hi_a - lo_a : 0;
@@ -516,8 +529,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 if (valid && cnt) {
                     int e = a_lo + nz_base + pos;
                     for (int i = lo_a; i < hi_a; i++) {
-                        T xv = W.xn[i];
-                        if (xv != T(0)) {
+                        double xv = W.xn[i];
+                        if (xv != 0.0) {
                             W.nz_col[e] = i;
                             W.nz_u[e] = xv;
                             W.nz_x[e] = xv;
@@ -610,16 +623,18 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 for (int tile = b; tile < ntiles; tile += G) {
                     const int r = tile * kRowTile + lane;
                     const bool rv = r < N;
-                    T au = T(0), ax = T(0);
+                    // compensated accumulation: theta = D u - y is a small difference of two
+                    // large vectors, so the sum is carried to twice the working precision
+                    typename Dot2<T>::type au, ax;
                     for (int e0 = warp; e0 < E; e0 += nw * 4) {
                         int cols[4];
-                        T uv[4], xv[4];
+                        double uv[4], xv[4];
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
                             int e = e0 + q * nw;
                             cols[q] = -1;
-                            uv[q] = T(0);
-                            xv[q] = T(0);
+                            uv[q] = 0.0;
+                            xv[q] = 0.0;
                             if (e < E) {
                                 int lo = 0, hi = G;  // largest k with s_pref[k] <= e
                                 while (hi - lo > 1) {
@@ -638,23 +653,23 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         for (int q = 0; q < 4; q++) dv[q] = (cols[q] >= 0 && rv) ? __ldg(P.D + (size_t)cols[q] * ld + r) : T(0);
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
-                            au = fma(uv[q], dv[q], au);
-                            ax = fma(xv[q], dv[q], ax);
+                            syn_add(au, dv[q], uv[q]);
+                            syn_add(ax, dv[q], xv[q]);
                         }
                     }
-                    s_red[0][warp][lane] = au;
-                    s_red[1][warp][lane] = ax;
+                    s_red[0][warp][lane] = au.value();
+                    s_red[1][warp][lane] = ax.value();
                     __syncthreads();
                     if (warp == 0) {
-                        T wu = T(0), wx = T(0);
+                        double wu = 0.0, wx = 0.0;
                         for (int k = 0; k < nw; k++) { wu += s_red[0][k][lane]; wx += s_red[1][k][lane]; }
                         if (rv) {
-                            T yv = P.y[r];
-                            T th = wu - yv;
+                            const double yv = (double)P.y[r];
+                            const T th = (T)(wu - yv);
                             W.theta[r] = th;
-                            pa_ += (double)th * (double)yv;
+                            pa_ += (double)th * yv;
                             pb_ += (double)th * (double)th;
-                            double rx = (double)wx - (double)yv;
+                            const double rx = wx - yv;
                             pr_ += rx * rx;
                         }
                     }
@@ -779,7 +794,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         for (int c = 0; c < nchunk; c++) z += zpart[a * nchunk + c];
                         if (!P.is_group) {
                             const int ap = abase + a;
-                            T v = __ldcg(W.uc[cur] + ap) - z * invL;
+                            double v = __ldcg(W.uc[cur] + ap) - (double)z * invL;
                             W.xn[ap] = soft_thr(v, thrL);
                             mloc = fmax(mloc, (double)fabs(z));
                         } else {
@@ -795,17 +810,17 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                             double zq = 0.0, vq = 0.0;
                             for (int i = 0; i < sz; i++) {
                                 T z = zpart[(off - abase + i) * nchunk];
-                                T v = __ldcg(W.uc[cur] + off + i) - z * invL;
+                                double v = __ldcg(W.uc[cur] + off + i) - (double)z * invL;
                                 zq += (double)z * (double)z;
-                                vq += (double)v * (double)v;
+                                vq += v * v;
                             }
                             const double wg = P.w[g];
                             const double nv = sqrt(vq);
                             // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
-                            const T f = T(nv > 0.0 ? fmax(0.0, (nv - (double)thrL * wg) / nv) : 0.0);
+                            const double f = nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0;
                             for (int i = 0; i < sz; i++) {
                                 T z = zpart[(off - abase + i) * nchunk];
-                                T v = __ldcg(W.uc[cur] + off + i) - z * invL;
+                                double v = __ldcg(W.uc[cur] + off + i) - (double)z * invL;
                                 W.xn[off + i] = f * v;
                             }
                             mloc = fmax(mloc, sqrt(zq) / wg);
@@ -850,7 +865,6 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     bt = (lf - 1.0) / ln;
                     lf = ln;
                 }
-                const T btT = T(bt);
                 int p_lo, p_hi, a_lo;
                 cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 int nz_base = 0, kg = 0, ka = 0, nzx = 0;
@@ -882,13 +896,13 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         if (kept) {
                             double gq = 0.0;
                             for (int q = 0; q < sz; q++) {
-                                T xv = __ldcg(W.xn + lo_a + q);
-                                T xo = __ldcg(W.xc[cur] + lo_a + q);
-                                T uv = ista ? xv : xv + btT * (xv - xo);
+                                double xv = __ldcg(W.xn + lo_a + q);
+                                double xo = __ldcg(W.xc[cur] + lo_a + q);
+                                double uv = ista ? xv : xv + bt * (xv - xo);
                                 W.un[lo_a + q] = uv;
-                                cnt += (uv != T(0) || xv != T(0));
-                                nzx += xv != T(0);
-                                gq += (double)xv * (double)xv;
+                                cnt += (uv != 0.0 || xv != 0.0);
+                                nzx += xv != 0.0;
+                                gq += xv * xv;
                             }
                             l1 += (P.is_group ? P.w[gid] : 1.0) * sqrt(gq);
                             kg += 1;
@@ -900,9 +914,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     if (cnt) {
                         int e = a_lo + nz_base + pos;
                         for (int q = 0; q < sz; q++) {
-                            T xv = __ldcg(W.xn + lo_a + q);
-                            T uv = __ldcg(W.un + lo_a + q);
-                            if (uv != T(0) || xv != T(0)) {
+                            double xv = __ldcg(W.xn + lo_a + q);
+                            double uv = __ldcg(W.un + lo_a + q);
+                            if (uv != 0.0 || xv != 0.0) {
                                 const int col = P.is_group ? P.goff[gid] + q : gid;
                                 W.nz_col[e] = col;
                                 W.nz_u[e] = uv;
@@ -947,7 +961,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 int lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                 int c0 = P.is_group ? P.goff[gid] : gid;
                 int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
-                for (int q = 0; q < sz; q++) xout[c0 + q] = __ldcg(W.xc[cur] + lo_a + q);
+                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)__ldcg(W.xc[cur] + lo_a + q);
             }
             if (b == 0 && tid == 0) {
                 R->iters = iters;
@@ -1015,15 +1029,15 @@ static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, c
         for (int k = 0; k < 2; k++) {
             w.act[k] = bp.take<int>(nG);
             w.aoff[k] = bp.take<int>(nG + 1);
-            w.xc[k] = bp.take<T>(K);
-            w.uc[k] = bp.take<T>(K);
+            w.xc[k] = bp.take<double>(K);
+            w.uc[k] = bp.take<double>(K);
         }
-        w.xn = bp.take<T>(K);
-        w.un = bp.take<T>(K);
+        w.xn = bp.take<double>(K);
+        w.un = bp.take<double>(K);
         w.keep = bp.take<int>(nG);
         w.nz_col = bp.take<int>(K);
-        w.nz_u = bp.take<T>(K);
-        w.nz_x = bp.take<T>(K);
+        w.nz_u = bp.take<double>(K);
+        w.nz_x = bp.take<double>(K);
         w.s_alo = bp.take<int>(G);
         w.c_kg = bp.take<int>(G);
         w.c_ka = bp.take<int>(G);
