@@ -64,6 +64,33 @@ ds_status ctx_reserve(ds_ctx* ctx, size_t bytes)
     return DS_OK;
 }
 
+// The FISTA extrapolation coefficients depend on the iteration number only
+// (Table 1: l_0 = 1, l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient
+// (l_{t-1} - 1) / l_t); they are tabulated once per context in FP64 on the host.
+ds_status ctx_fista_table(ds_ctx* ctx, int n)
+{
+    const int cap = 1 << 20;
+    n = std::min(std::max(n, 1024), cap);
+    if (ctx->fista_n >= n) return DS_OK;
+    std::vector<double> tab(2 * (size_t)n);
+    double l = 1.0;
+    for (int t = 0; t < n; t++) {
+        const double ln = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * l * l));
+        tab[2 * t] = (l - 1.0) / ln;
+        tab[2 * t + 1] = ln;
+        l = ln;
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return DS_ERR_CUDA;
+    if (ctx->fista) cudaFree(ctx->fista);
+    ctx->fista = nullptr;
+    ctx->fista_n = 0;
+    if (cudaMalloc(&ctx->fista, sizeof(double) * tab.size()) != cudaSuccess) return DS_ERR_OOM;
+    if (cudaMemcpy(ctx->fista, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return DS_ERR_CUDA;
+    ctx->fista_n = n;
+    return DS_OK;
+}
+
 }  // namespace ds
 
 extern "C" {
@@ -137,6 +164,7 @@ ds_status ds_destroy(ds_ctx* c)
     if (c->ws) cudaFree(c->ws);
     if (c->d_io) cudaFree(c->d_io);
     if (c->h_res) cudaFreeHost(c->h_res);
+    if (c->fista) cudaFree(c->fista);
     cudaEventDestroy(c->ev0);
     cudaEventDestroy(c->ev1);
     delete c;

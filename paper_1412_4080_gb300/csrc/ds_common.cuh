@@ -12,14 +12,15 @@ constexpr int kWarp = 32;
 
 // ----------------------------------------------------------- grid barrier
 //
-// Sense-counting barrier for a cooperative grid (all CTAs co-resident).  The
-// last CTA to arrive resets the counter and bumps the generation; the others
-// spin on the generation with an iteration limit.  A wait that exceeds the
-// limit sets `err` and returns false; every CTA then leaves its loop, so a
-// lost CTA can never hang the GPU.
+// Barrier for a cooperative grid (all CTAs co-resident) on a monotonic
+// counter: the k-th barrier of a launch waits until the counter reaches
+// k * gridDim.x.  Arrival is one release-ordered atomic add; waiting is an
+// acquire-ordered poll with an iteration limit.  A wait that exceeds the limit
+// sets `err` and returns false; every CTA then leaves its loop, so a lost CTA
+// can never hang the GPU.  The counter is zeroed before each launch.
 struct GridBarrier {
     unsigned int count;
-    unsigned int gen;
+    unsigned int gen;  // unused by the counter barrier, kept for layout
     unsigned int err;
     unsigned int pad;
 };
@@ -40,35 +41,32 @@ __device__ __forceinline__ unsigned int ld_volatile_u32(const unsigned int* p)
     return v;
 }
 
+__device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned int v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" : : "l"(p), "r"(v) : "memory");
+}
+
 // Returns true when every CTA arrived; false when the barrier (now or earlier)
-// failed.  `gen` is the CTA's private copy of the generation counter.
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, unsigned int& gen)
+// failed.  `target` is the CTA's private running target (advanced by gridDim.x).
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, unsigned int& target)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned int g = gen;
+        target += nblocks;
         __threadfence();
-        unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (ld_acquire_u32(&bar->gen) == g) {
-                if (++spins > kSpinLimit || ld_volatile_u32(&bar->err)) {
-                    atomicExch(&bar->err, 1u);
-                    ok = 0;
-                    break;
-                }
-                if (spins > 64) __nanosleep(spins > 4096 ? 256 : 32);
+        red_release_add_u32(&bar->count, 1u);
+        unsigned long long spins = 0;
+        while (ld_acquire_u32(&bar->count) < target) {
+            if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_volatile_u32(&bar->err))) {
+                atomicExch(&bar->err, 1u);
+                ok = 0;
+                break;
             }
+            if (spins > 2048) __nanosleep(spins > 65536 ? 512 : 64);
         }
-        __threadfence();
         if (ld_volatile_u32(&bar->err)) ok = 0;
-        gen = g + 1;
         s_ok = ok;
     }
     __syncthreads();
@@ -97,6 +95,36 @@ struct Dot2f {
     }
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
+
+// Error-free accumulation of another (s, c) pair.
+__device__ __forceinline__ void dot2_merge(Dot2f& a, float s2, float c2)
+{
+    float t = a.s + s2;
+    float bb = t - a.s;
+    float e = (a.s - (t - bb)) + (s2 - bb);
+    a.s = t;
+    a.c += e + c2;
+}
+__device__ __forceinline__ Dot2f dot2_warp_reduce(Dot2f a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+        float c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+        dot2_merge(a, s2, c2);
+    }
+    return a;
+}
+__device__ __forceinline__ double dot2_warp_sum(Dot2f a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float s2 = __shfl_xor_sync(0xffffffffu, a.s, o);
+        float c2 = __shfl_xor_sync(0xffffffffu, a.c, o);
+        dot2_merge(a, s2, c2);
+    }
+    return a.value();
+}
 
 struct Dot2d {  // FP64 dictionaries: plain FP64 accumulation is already accurate enough
     double s;
@@ -189,6 +217,93 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* tmp, int* total)
     __syncthreads();
     *total = tot;
     return base + x - v;
+}
+
+// ------------------------------------------------------ float-float numbers
+//
+// An FF value is the unevaluated sum h + l of two floats with |l| <= ulp(h)/2
+// (about 48 significant bits).  The operations below are built from the
+// error-free transformations TwoSum (Knuth) and TwoProduct via FMA, in the
+// manner of Dekker's double-length arithmetic ("A floating-point technique
+// for extending the available precision", 1971).  They carry the solver's
+// iterates and reductions on the FP32 pipes: GB300 executes FP64 at a small
+// fraction of the FP32 rate, so per-atom and per-row FP64 arithmetic would
+// dominate an iteration.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return FF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b)  // requires |a| >= |b| or a == 0
+{
+    const float s = a + b;
+    return FF{s, b - (s - a)};
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b)
+{
+    FF s = ff_two_sum(a.h, b.h);
+    const FF t = ff_two_sum(a.l, b.l);
+    s.l += t.h;
+    s = ff_fast_two_sum(s.h, s.l);
+    s.l += t.l;
+    return ff_fast_two_sum(s.h, s.l);
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.h, -a.l}; }
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ FF ff_prod(float a, float b)
+{
+    const float p = a * b;
+    return FF{p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, FF b)
+{
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ double ff_to_double(FF a) { return (double)a.h + (double)a.l; }
+__host__ __device__ __forceinline__ FF ff_from_double(double d)
+{
+    const float h = (float)d;
+    return FF{h, (float)(d - (double)h)};
+}
+
+// ------------------------------------------- FP64 reciprocal and square root
+//
+// GB300 runs FP64 divide and square root as long instruction sequences on its
+// narrow FP64 pipe.  On the solver's serial path they are replaced by Newton's
+// iteration seeded with the correctly rounded FP32 result: for the reciprocal
+// r <- r + r (1 - a r), for the reciprocal square root r <- r + (r/2)(1 - a r^2).
+// Each step squares the relative error (quadratic convergence), so two steps
+// from a seed within 2^-23 reach the FP64 rounding level; the self-test entry
+// point compares them with CUDA's own division and square root.
+__device__ __forceinline__ double fast_rcp(double a)
+{
+    const float af = fabsf((float)a);
+    if (!(af > 1e-30f && af < 1e30f)) return 1.0 / a;  // outside the FP32 seed's range
+    double r = (double)__frcp_rn((float)a);
+    double e = fma(-a, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-a, r, 1.0);
+    return fma(r, e, r);
+}
+__device__ __forceinline__ double fast_sqrt(double a)  // a >= 0
+{
+    if (!(a > 0.0)) return 0.0;
+    if (!(a > 1e-30 && a < 1e30)) return sqrt(a);  // outside the FP32 seed's range
+    double r = (double)rsqrtf((float)a);
+    double e = fma(-a * r, r, 1.0);
+    r = fma(0.5 * r, e, r);
+    e = fma(-a * r, r, 1.0);
+    r = fma(0.5 * r, e, r);
+    return a * r;
 }
 
 // ------------------------------------------------------------ small helpers

@@ -26,6 +26,8 @@ struct ds_ctx {
     double* hist;
     int hist_rows;
     long long launches;
+    double* fista;  // device table of the FISTA sequence (coefficient, l_t), t = 1..fista_n
+    int fista_n;
     cudaEvent_t ev0, ev1;
 };
 
@@ -71,6 +73,7 @@ ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host);
 
 // Workspace helpers (ds_api.cu).
 ds_status ctx_reserve(ds_ctx* ctx, size_t bytes);
+ds_status ctx_fista_table(ds_ctx* ctx, int n);
 ds_status ctx_reserve_results(ds_ctx* ctx, size_t n);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }

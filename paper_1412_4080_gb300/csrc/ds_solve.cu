@@ -33,11 +33,19 @@
 namespace ds {
 
 constexpr int kThreads = 512;
+constexpr int kMaxG = 160;  // CTAs of the persistent grid (one per SM) handled by the fixed reductions
 constexpr int kU = 4;         // 16-byte vectors per lane per GEMV item
 constexpr int kRowTile = 32;  // rows per synthesis tile
 
+// Iterates (x, u) and per-CTA partial sums: float-float pairs for FP32
+// dictionaries, doubles for FP64 ones.
+template <typename T> struct IterT;
+template <> struct IterT<float> { using type = FF; };
+template <> struct IterT<double> { using type = double; };
+
 template <typename T>
 struct Ws {
+    using X = typename IterT<T>::type;
     GridBarrier* bar;
     T* theta;
     double* b;
@@ -46,26 +54,26 @@ struct Ws {
     double* nvec;
     int* act[2];
     int* aoff[2];
-    // iterates are kept in FP64 whatever the dictionary type: in FP32, u - z/L
-    // would quantise z to multiples of L ulp(x), a KKT floor near 1e-6 relative
-    double* xc[2];
-    double* uc[2];
-    double* xn;
-    double* un;
+    // iterates carry about twice the dictionary's precision: in plain FP32,
+    // u - z/L would quantise z to multiples of L ulp(x), a KKT floor near 1e-6
+    X* xc[2];
+    X* uc[2];
+    X* xn;
+    X* un;
     int* keep;
     int* nz_col;
-    double* nz_u;
-    double* nz_x;
+    X* nz_u;
+    X* nz_x;
     int* s_alo;
     int* c_kg;
     int* c_ka;
     int* c_nz;
     int* c_nnzx;
-    double* p_m;
-    double* p_l1;
-    double* p_a;
-    double* p_b;
-    double* p_r;
+    T* p_m;
+    X* p_l1;
+    X* p_a;
+    X* p_b;
+    X* p_r;
     double* p_v;
     int* p_i;
 };
@@ -93,6 +101,8 @@ struct SolveP {
     int hist_rows;
     Ws<T> ws;
     int RA, nchunk, npad;
+    const double* fista;  // FISTA table: (coefficient (l_{t-1} - 1) / l_t, l_t) for t = 1..fista_n
+    int fista_n;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -125,16 +135,148 @@ __device__ __forceinline__ double dome_max(double dc0, double t, double psi, dou
     return dc0 - psi * t + sqrt(rho2) * sqrt(s2);
 }
 
-// synthesis term d * c with an FP64 coefficient c: for FP32 dictionaries c is split
-// into hi + lo floats and d * hi is accumulated with error-free transformations
-__device__ __forceinline__ void syn_add(Dot2f& acc, float d, double c)
+template <typename T> __device__ __forceinline__ T round_up_to(double v);
+template <> __device__ __forceinline__ float round_up_to<float>(double v) { return __double2float_ru(v); }
+template <> __device__ __forceinline__ double round_up_to<double>(double v) { return v; }
+
+// ---- iterate arithmetic (float-float for FP32 dictionaries, FP64 otherwise)
+__device__ __forceinline__ FF ldcg_x(const FF* p)
 {
-    const float hi = (float)c;
-    const float lo = (float)(c - (double)hi);
-    acc.add(d, hi);
-    acc.c = fmaf(d, lo, acc.c);
+    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+    return FF{v.x, v.y};
+}
+__device__ __forceinline__ double ldcg_x(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ bool it_nz(FF a) { return a.h != 0.f; }
+__device__ __forceinline__ bool it_nz(double a) { return a != 0.0; }
+__device__ __forceinline__ FF it_zero(FF*) { return FF{0.f, 0.f}; }
+__device__ __forceinline__ double it_zero(double*) { return 0.0; }
+__device__ __forceinline__ FF it_from(float v, FF*) { return FF{v, 0.f}; }
+__device__ __forceinline__ double it_from(double v, double*) { return v; }
+__device__ __forceinline__ float it_round(FF a) { return a.h + a.l; }
+__device__ __forceinline__ double it_round(double a) { return a; }
+__device__ __forceinline__ double it_dbl(FF a) { return ff_to_double(a); }
+__device__ __forceinline__ double it_dbl(double a) { return a; }
+__device__ __forceinline__ FF it_cast(double a, FF*) { return ff_from_double(a); }
+__device__ __forceinline__ double it_cast(double a, double*) { return a; }
+// gradient step v = u - z * (1/L)
+__device__ __forceinline__ FF it_grad_step(FF u, float z, float invL) { return ff_sub(u, ff_prod(z, invL)); }
+__device__ __forceinline__ double it_grad_step(double u, double z, double invL) { return fma(-z, invL, u); }
+// soft threshold (eq. softTh): sign(v) max(|v| - thr, 0)
+__device__ __forceinline__ FF it_soft(FF v, FF thr)
+{
+    if (v.h > 0.f) {
+        const FF a = ff_sub(v, thr);
+        return a.h > 0.f ? a : FF{0.f, 0.f};
+    }
+    if (v.h < 0.f) {
+        const FF a = ff_add(v, thr);
+        return a.h < 0.f ? a : FF{0.f, 0.f};
+    }
+    return FF{0.f, 0.f};
+}
+__device__ __forceinline__ double it_soft(double v, double thr)
+{
+    const double a = fabs(v) - thr;
+    return a > 0.0 ? copysign(a, v) : 0.0;
+}
+// FISTA extrapolation u = x + bt (x - xo)
+__device__ __forceinline__ FF it_momentum(FF x, FF xo, FF bt) { return ff_add(x, ff_mul(ff_sub(x, xo), bt)); }
+__device__ __forceinline__ double it_momentum(double x, double xo, double bt) { return fma(bt, x - xo, x); }
+__device__ __forceinline__ FF it_scale(FF v, FF f) { return ff_mul(v, f); }
+__device__ __forceinline__ double it_scale(double v, double f) { return v * f; }
+// accumulators: |x| and x^2
+__device__ __forceinline__ void acc_abs(Dot2f& acc, FF x)
+{
+    const float sg = x.h < 0.f ? -1.f : 1.f;
+    dot2_merge(acc, sg * x.h, sg * x.l);
+}
+__device__ __forceinline__ void acc_abs(Dot2d& acc, double x) { acc.s += fabs(x); }
+__device__ __forceinline__ void acc_sq(Dot2f& acc, FF x)
+{
+    acc.add(x.h, x.h);
+    acc.c = fmaf(2.f * x.h, x.l, acc.c);
+}
+__device__ __forceinline__ void acc_sq(Dot2d& acc, double x) { acc.s = fma(x, x, acc.s); }
+__device__ __forceinline__ void acc_add_dbl(Dot2f& acc, double v)
+{
+    const FF f = ff_from_double(v);
+    dot2_merge(acc, f.h, f.l);
+}
+__device__ __forceinline__ void acc_add_dbl(Dot2d& acc, double v) { acc.s += v; }
+// synthesis term acc += d * c
+__device__ __forceinline__ void syn_add(Dot2f& acc, float d, FF c)
+{
+    acc.add(d, c.h);
+    acc.c = fmaf(d, c.l, acc.c);
 }
 __device__ __forceinline__ void syn_add(Dot2d& acc, double d, double c) { acc.add(d, c); }
+// per-CTA partials
+__device__ __forceinline__ void part_put(FF* p, const Dot2f& a) { *p = FF{a.s, a.c}; }
+__device__ __forceinline__ void part_put(double* p, const Dot2d& a) { *p = a.s; }
+__device__ __forceinline__ double part_sum_fixed(const FF* p, int n, int lane)
+{
+    Dot2f acc;
+    for (int i = lane; i < n; i += 32) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(p + i));
+        dot2_merge(acc, v.x, v.y);
+    }
+    return dot2_warp_sum(acc);
+}
+__device__ __forceinline__ double part_sum_fixed(const double* p, int n, int lane) { return warp_sum_fixed(p, n, lane); }
+template <int Q> __device__ __forceinline__ double part_sum_regs(const FF (&v)[Q])
+{
+    Dot2f acc;
+#pragma unroll
+    for (int q = 0; q < Q; q++) dot2_merge(acc, v[q].h, v[q].l);
+    return dot2_warp_sum(acc);
+}
+template <int Q> __device__ __forceinline__ double part_sum_regs(const double (&v)[Q])
+{
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) acc += v[q];
+    return warp_sum(acc);
+}
+__device__ __forceinline__ Dot2f acc_warp_reduce(Dot2f a) { return dot2_warp_reduce(a); }
+__device__ __forceinline__ Dot2d acc_warp_reduce(Dot2d a)
+{
+    a.s = warp_sum(a.s);
+    return a;
+}
+__device__ __forceinline__ void acc_merge_acc(Dot2f& a, const Dot2f& b) { dot2_merge(a, b.s, b.c); }
+__device__ __forceinline__ void acc_merge_acc(Dot2d& a, const Dot2d& b) { a.s += b.s; }
+// theta_r = w_u - y_r, computed from the compensated sum and rounded once
+__device__ __forceinline__ float theta_from(const Dot2f& wu, float y)
+{
+    const FF t = ff_two_sum(wu.s, -y);
+    return t.h + (t.l + wu.c);
+}
+__device__ __forceinline__ double theta_from(const Dot2d& wu, double y) { return wu.s - y; }
+// (w_x - y_r)^2 into an accumulator
+__device__ __forceinline__ void acc_resid_sq(Dot2f& acc, const Dot2f& wx, float y)
+{
+    FF t = ff_two_sum(wx.s, -y);
+    t = ff_fast_two_sum(t.h, t.l + wx.c);
+    acc_sq(acc, t);
+}
+__device__ __forceinline__ void acc_resid_sq(Dot2d& acc, const Dot2d& wx, double y)
+{
+    const double r = wx.s - y;
+    acc.s = fma(r, r, acc.s);
+}
+
+// float-float (or FP64) partial sums parked in one 8-byte shared slot
+__device__ __forceinline__ void acc_store(double* slot, const Dot2f& a)
+{
+    *reinterpret_cast<float2*>(slot) = make_float2(a.s, a.c);
+}
+__device__ __forceinline__ void acc_store(double* slot, const Dot2d& a) { *slot = a.s; }
+__device__ __forceinline__ void acc_merge(Dot2f& a, const double* slot)
+{
+    const float2 v = *reinterpret_cast<const float2*>(slot);
+    dot2_merge(a, v.x, v.y);
+}
+__device__ __forceinline__ void acc_merge(Dot2d& a, const double* slot) { a.s += *slot; }
 
 __device__ __forceinline__ float4 v4zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
 __device__ __forceinline__ double2 v4zero(double2*) { return make_double2(0.0, 0.0); }
@@ -202,6 +344,8 @@ template <typename T>
 __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
 {
     using V = typename Vec4<T>::type;
+    using X = typename IterT<T>::type;
+    using Acc = typename Dot2<T>::type;
     constexpr int EV = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* th_s = reinterpret_cast<T*>(smem_raw);
@@ -212,16 +356,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
     __shared__ double s_dred[32];
     __shared__ int s_ired[32];
     __shared__ int s_pref[1025];
+    __shared__ int s_alo_s[kThreads];
     __shared__ double s_red[2][kThreads / 32][kRowTile];
     __shared__ double s_sc[16];
-    __shared__ int s_si[8];
+    __shared__ int s_si[16];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kThreads / 32;
     const int b = blockIdx.x, G = gridDim.x;
     const Ws<T>& W = P.ws;
-    unsigned int gen = 0;
-    if (tid == 0) gen = ld_volatile_u32(&W.bar->gen);
-    // gen is only meaningful in thread 0, which is the only thread that reads it
+    unsigned int gen = 0;  // running barrier target, used by thread 0 only
 
     const int N = P.N, K = P.K, ld = P.ld, nG = P.nG;
     const int ldv = ld / EV;
@@ -258,9 +401,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         if (lane == 0) s_dred[warp] = yy;
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0;
-            for (int k = 0; k < nw; k++) s += s_dred[k];
-            W.p_a[b] = s;
+            Acc s;
+            for (int k = 0; k < nw; k++) acc_add_dbl(s, s_dred[k]);
+            part_put(W.p_a + b, s);
         }
     }
     ok = grid_sync(W.bar, G, gen);
@@ -320,7 +463,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 int oa = __shfl_xor_sync(0xffffffffu, ba, o);
                 if (ob > bb || (ob == bb && oa < ba)) { bb = ob; ba = oa; }
             }
-            double yy = warp_sum_fixed(W.p_a, G, lane);
+            double yy = part_sum_fixed(W.p_a, G, lane);
             if (lane == 0) { s_sc[0] = bb; s_si[0] = ba; s_sc[1] = yy; }
         }
         __syncthreads();
@@ -351,14 +494,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         if (lane == 0) s_dred[warp] = nq;
         __syncthreads();
         if (tid == 0) {
-            double s = 0.0;
-            for (int k = 0; k < nw; k++) s += s_dred[k];
-            W.p_r[b] = s;
+            Acc s;
+            for (int k = 0; k < nw; k++) acc_add_dbl(s, s_dred[k]);
+            part_put(W.p_r + b, s);
         }
         ok = grid_sync(W.bar, G, gen);
         if (!ok) return false;
         if (warp == 0) {
-            double s = warp_sum_fixed(W.p_r, G, lane);
+            double s = part_sum_fixed(W.p_r, G, lane);
             if (lane == 0) s_sc[2] = s;
         }
         // stage n in shared memory (hi/lo split for FP32 dictionaries)
@@ -439,8 +582,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         const double delta = need_n && nn > 0.0 ? fabs(nty / lam - wstar2) / sqrt(nn) : 0.0;
         const double nstar = P.is_group ? 1.0 : P.colnorm[star];
         const double psi_dome = psi / nstar;
-        const double invL = 1.0 / P.L;
+        const T invL = (T)(1.0 / P.L);
         const double thrL = lam / P.L;
+        const X thrX = it_cast(thrL, (X*)nullptr);
         const bool ista = P.alg == 0;
         const bool dyn_test = P.dynamic && P.test != 0;
 
@@ -515,11 +659,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     kept = !kill;
                     W.keep[p] = kept;
                     for (int i = lo_a; i < hi_a; i++) {
-                        double xv = P.x0 ? (double)P.x0[i] : 0.0;
-                        if (!kept) xv = 0.0;
+                        X xv = (P.x0 && kept) ? it_from(P.x0[i], (X*)nullptr) : it_zero((X*)nullptr);
                         W.xn[i] = xv;
                         W.un[i] = xv;
-                        cnt += xv != 0.0;
+                        cnt += it_nz(xv);
                     }
                     kg += kept;
                     ka += kept ? hi_a - lo_a : 0;
@@ -529,8 +672,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 if (valid && cnt) {
                     int e = a_lo + nz_base + pos;
                     for (int i = lo_a; i < hi_a; i++) {
-                        double xv = W.xn[i];
-                        if (xv != 0.0) {
+                        const X xv = W.xn[i];
+                        if (it_nz(xv)) {
                             W.nz_col[e] = i;
                             W.nz_u[e] = xv;
                             W.nz_x[e] = xv;
@@ -550,7 +693,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 W.c_ka[b] = tka;
                 W.c_nz[b] = nz_base;
                 W.c_nnzx[b] = nz_base;
-                W.p_l1[b] = 0.0;
+                Acc z0;
+                part_put(W.p_l1 + b, z0);
             }
             if (b == G - 1 && tid == 0 && P.is_group) W.aoff[cur][nG] = K;
         }
@@ -558,7 +702,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         if (!ok) return false;
 
         int nA_g = nG, nA_a = K;  // sizes of the list `cur` refers to
-        double alpha = 0.0, beta = 0.0, mu_nom = 0.0, R_nom = 0.0, rad = 0.0, lf = 1.0;
+        // scalar state, meaningful in thread 0 (the values every thread needs go through s_sc)
+        double alpha = 0.0, beta = 0.0, mu_nom = 0.0, R2n = 0.0, rad = 0.0, lf = 1.0;
+        double s_unc = 0.0, sqrt_beta = 0.0;
+        const double inv_lam = 1.0 / lam, yy_l2 = yy * inv_lam * inv_lam;
         double gap = INFINITY, primal = 0.0;
         int t = 1;
         int iters = 0;
@@ -571,54 +718,61 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 int p_lo, p_hi, a_lo;
                 cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 const int nxt = cur ^ 1;
+                // directory of the per-CTA nonzero lists (exclusive prefix of their lengths)
+                const int cnz = tid < G ? __ldcg(W.c_nz + tid) : 0;
+                if (tid < G) s_alo_s[tid] = __ldcg(W.s_alo + tid);
+                int totE;
+                const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
+                if (tid < G) s_pref[tid] = exE;
+                if (tid == 0) s_pref[G] = totE;
                 if (warp == 0) {
-                    long long g0 = 0, a0 = 0;
-                    for (int k = lane; k < b; k += 32) { g0 += __ldcg(W.c_kg + k); a0 += __ldcg(W.c_ka + k); }
+                    int gv[kMaxG / 32], av[kMaxG / 32];
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-                        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                    for (int q = 0; q < kMaxG / 32; q++) {
+                        const int k = lane + 32 * q;
+                        gv[q] = k < b ? __ldcg(W.c_kg + k) : 0;
+                        av[q] = k < b ? __ldcg(W.c_ka + k) : 0;
                     }
-                    if (lane == 0) { s_si[1] = (int)g0; s_si[2] = (int)a0; }
+                    int g0 = 0, a0 = 0;
+#pragma unroll
+                    for (int q = 0; q < kMaxG / 32; q++) { g0 += gv[q]; a0 += av[q]; }
+                    g0 = warp_sum(g0);
+                    a0 = warp_sum(a0);
+                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; }
                 }
                 __syncthreads();
+                // compaction (Algorithm 3: D_t = D_{t-1} Id, Xbar_t = Id X_t): kept groups move to
+                // their new positions; groups and atoms are counted in one packed scan
                 int gb = s_si[1], ab = s_si[2];
                 for (int base = p_lo; base < p_hi; base += kThreads) {
-                    int p = base + tid;
-                    bool valid = p < p_hi;
-                    int k = valid ? __ldcg(W.keep + p) : 0;
-                    int lo_a = 0, sz = 0;
+                    const int p = base + tid;
+                    const bool valid = p < p_hi;
+                    int k = 0, lo_a = 0, sz = 0;
                     if (valid) {
+                        k = __ldcg(W.keep + p);
                         lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                         sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
                     }
-                    int tg, ta;
-                    int pg = block_exclusive_scan(k, s_tmp, &tg);
-                    int pa = block_exclusive_scan(k ? sz : 0, s_tmp, &ta);
+                    int tot;
+                    const int pre = block_exclusive_scan(k ? ((1 << 16) | sz) : 0, s_tmp, &tot);
                     if (k) {
-                        int ng = gb + pg, na = ab + pa;
+                        const int ng = gb + (pre >> 16), na = ab + (pre & 0xffff);
                         W.act[nxt][ng] = __ldcg(W.act[cur] + p);
                         if (P.is_group) W.aoff[nxt][ng] = na;
                         for (int q = 0; q < sz; q++) {
-                            W.xc[nxt][na + q] = __ldcg(W.xn + lo_a + q);
-                            W.uc[nxt][na + q] = __ldcg(W.un + lo_a + q);
+                            W.xc[nxt][na + q] = ldcg_x(W.xn + lo_a + q);
+                            W.uc[nxt][na + q] = ldcg_x(W.un + lo_a + q);
                         }
                     }
-                    gb += tg;
-                    ab += ta;
+                    gb += tot >> 16;
+                    ab += tot & 0xffff;
                 }
                 if (b == G - 1 && tid == 0 && P.is_group) W.aoff[nxt][gb] = ab;
 
                 // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists
-                if (tid < G) s_pref[tid + 1] = __ldcg(W.c_nz + tid);
-                if (tid == 0) s_pref[0] = 0;
-                __syncthreads();
-                if (tid == 0)
-                    for (int k = 1; k <= G; k++) s_pref[k] += s_pref[k - 1];
-                __syncthreads();
                 const int E = s_pref[G];
                 cols_synth += E;
-                double pa_ = 0.0, pb_ = 0.0, pr_ = 0.0;
+                Acc pa_, pb_, pr_;
                 const int ntiles = (N + kRowTile - 1) / kRowTile;
                 for (int tile = b; tile < ntiles; tile += G) {
                     const int r = tile * kRowTile + lane;
@@ -628,24 +782,24 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     typename Dot2<T>::type au, ax;
                     for (int e0 = warp; e0 < E; e0 += nw * 4) {
                         int cols[4];
-                        double uv[4], xv[4];
+                        X uv[4], xv[4];
 #pragma unroll
                         for (int q = 0; q < 4; q++) {
-                            int e = e0 + q * nw;
+                            const int e = e0 + q * nw;
                             cols[q] = -1;
-                            uv[q] = 0.0;
-                            xv[q] = 0.0;
+                            uv[q] = it_zero((X*)nullptr);
+                            xv[q] = it_zero((X*)nullptr);
                             if (e < E) {
                                 int lo = 0, hi = G;  // largest k with s_pref[k] <= e
                                 while (hi - lo > 1) {
-                                    int mid = (lo + hi) >> 1;
+                                    const int mid = (lo + hi) >> 1;
                                     if (s_pref[mid] <= e) lo = mid;
                                     else hi = mid;
                                 }
-                                int idx = __ldcg(W.s_alo + lo) + (e - s_pref[lo]);
+                                const int idx = s_alo_s[lo] + (e - s_pref[lo]);
                                 cols[q] = __ldcg(W.nz_col + idx);
-                                uv[q] = __ldcg(W.nz_u + idx);
-                                xv[q] = __ldcg(W.nz_x + idx);
+                                uv[q] = ldcg_x(W.nz_u + idx);
+                                xv[q] = ldcg_x(W.nz_x + idx);
                             }
                         }
                         T dv[4];
@@ -657,29 +811,31 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                             syn_add(ax, dv[q], xv[q]);
                         }
                     }
-                    s_red[0][warp][lane] = au.value();
-                    s_red[1][warp][lane] = ax.value();
+                    acc_store(&s_red[0][warp][lane], au);
+                    acc_store(&s_red[1][warp][lane], ax);
                     __syncthreads();
                     if (warp == 0) {
-                        double wu = 0.0, wx = 0.0;
-                        for (int k = 0; k < nw; k++) { wu += s_red[0][k][lane]; wx += s_red[1][k][lane]; }
+                        typename Dot2<T>::type wu, wx;
+                        for (int k = 0; k < nw; k++) {
+                            acc_merge(wu, &s_red[0][k][lane]);
+                            acc_merge(wx, &s_red[1][k][lane]);
+                        }
                         if (rv) {
-                            const double yv = (double)P.y[r];
-                            const T th = (T)(wu - yv);
+                            const T yv = P.y[r];
+                            const T th = (T)theta_from(wu, yv);
                             W.theta[r] = th;
-                            pa_ += (double)th * yv;
-                            pb_ += (double)th * (double)th;
-                            const double rx = wx - yv;
-                            pr_ += rx * rx;
+                            pa_.add(th, yv);
+                            pb_.add(th, th);
+                            acc_resid_sq(pr_, wx, yv);
                         }
                     }
                     __syncthreads();
                 }
                 if (warp == 0) {
-                    pa_ = warp_sum(pa_);
-                    pb_ = warp_sum(pb_);
-                    pr_ = warp_sum(pr_);
-                    if (lane == 0) { W.p_a[b] = pa_; W.p_b[b] = pb_; W.p_r[b] = pr_; }
+                    pa_ = acc_warp_reduce(pa_);
+                    pb_ = acc_warp_reduce(pb_);
+                    pr_ = acc_warp_reduce(pr_);
+                    if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
                 }
                 cur = nxt;
             }
@@ -688,46 +844,82 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
 
             // ================================ (B) stop test, correlation + prox
             {
+                // warp 0 reduces the partials in a fixed order; lane 0 evaluates the gap of
+                // iteration t-1 and the stopping rule
                 if (warp == 0) {
-                    double a_ = warp_sum_fixed(W.p_a, G, lane);
-                    double b_ = warp_sum_fixed(W.p_b, G, lane);
-                    double r_ = warp_sum_fixed(W.p_r, G, lane);
-                    double l1 = warp_sum_fixed(W.p_l1, G, lane);
-                    long long ng = warp_sum_fixed(W.c_kg, G, lane);
-                    long long na = warp_sum_fixed(W.c_ka, G, lane);
-                    long long nx = warp_sum_fixed(W.c_nnzx, G, lane);
+                    // every load of the per-CTA partials is issued before any is combined
+                    X va[kMaxG / 32], vb[kMaxG / 32], vr[kMaxG / 32], vl[kMaxG / 32];
+                    int ig[kMaxG / 32], ia[kMaxG / 32], ix[kMaxG / 32];
+#pragma unroll
+                    for (int q = 0; q < kMaxG / 32; q++) {
+                        const int k = lane + 32 * q;
+                        const bool in = k < G;
+                        va[q] = in ? ldcg_x(W.p_a + k) : it_zero((X*)nullptr);
+                        vb[q] = in ? ldcg_x(W.p_b + k) : it_zero((X*)nullptr);
+                        vr[q] = in ? ldcg_x(W.p_r + k) : it_zero((X*)nullptr);
+                        vl[q] = in ? ldcg_x(W.p_l1 + k) : it_zero((X*)nullptr);
+                        ig[q] = in ? __ldcg(W.c_kg + k) : 0;
+                        ia[q] = in ? __ldcg(W.c_ka + k) : 0;
+                        ix[q] = in ? __ldcg(W.c_nnzx + k) : 0;
+                    }
+                    const double a_ = part_sum_regs<kMaxG / 32>(va);
+                    const double b_ = part_sum_regs<kMaxG / 32>(vb);
+                    const double r_ = part_sum_regs<kMaxG / 32>(vr);
+                    const double l1 = part_sum_regs<kMaxG / 32>(vl);
+                    int ng = 0, na = 0, nx = 0;
+#pragma unroll
+                    for (int q = 0; q < kMaxG / 32; q++) { ng += ig[q]; na += ia[q]; nx += ix[q]; }
+                    ng = warp_sum(ng);
+                    na = warp_sum(na);
+                    nx = warp_sum(nx);
                     if (lane == 0) {
-                        s_sc[3] = a_; s_sc[4] = b_; s_sc[5] = r_; s_sc[6] = l1;
-                        s_si[3] = (int)ng; s_si[4] = (int)na; s_si[5] = (int)nx;
+                        int stop = 0;
+                        if (t > 1) {
+                            // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
+                            primal = 0.5 * r_ + lam * l1;
+                            gap = primal - 0.5 * yy + 0.5 * lam * lam * R2n;
+                            iters = t - 1;
+                            if (record && b == 0 && t - 1 <= P.hist_rows) {
+                                double* h = P.hist + (size_t)(t - 2) * 6;
+                                h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
+                            }
+                            stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                        }
+                        alpha = a_;
+                        beta = b_;
+                        // the parts of Lemma 8 that do not need max |z|, off the critical path of (C)
+                        s_unc = beta > 0.0 ? alpha * inv_lam * fast_rcp(beta) : 0.0;
+                        // an upper bound of ||theta|| is all the rounding bound of (C) needs
+                        sqrt_beta = (double)sqrtf((float)beta) * (1.0 + 1e-6);
+                        double bt = 0.0;
+                        if (!ista) {
+                            // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
+                            // read from the table (the sequence depends on t only)
+                            if (t <= P.fista_n) {
+                                bt = P.fista[2 * (t - 1)];
+                                lf = P.fista[2 * (t - 1) + 1];
+                            } else {
+                                const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
+                                bt = (lf - 1.0) / ln;
+                                lf = ln;
+                            }
+                        }
+                        s_sc[10] = bt;
+                        s_si[3] = (int)ng; s_si[4] = (int)na; s_si[5] = (int)nx; s_si[6] = stop;
                     }
                 }
                 __syncthreads();
-                const double rho = s_sc[5], l1 = s_sc[6];
                 nA_g = s_si[3];
                 nA_a = s_si[4];
                 nnz_last = s_si[5];
-                bool stop = false;
-                if (t > 1) {
-                    // gap of iteration t-1: P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                    primal = 0.5 * rho + lam * l1;
-                    gap = primal - 0.5 * yy + 0.5 * lam * lam * R_nom * R_nom;
-                    iters = t - 1;
-                    if (record && b == 0 && tid == 0 && t - 1 <= P.hist_rows) {
-                        double* h = P.hist + (size_t)(t - 2) * 6;
-                        h[0] = (double)nA_a; h[1] = (double)nnz_last; h[2] = R_nom; h[3] = rad; h[4] = gap; h[5] = mu_nom;
-                    }
-                    stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
-                }
-                alpha = s_sc[3];
-                beta = s_sc[4];
-                if (stop) break;
+                if (s_si[6]) break;
                 cols_corr += nA_a;
 
                 // stage theta_t
                 for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? __ldcg(W.theta + r) : T(0);
                 int p_lo, p_hi, a_lo;
                 cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                double mloc = 0.0;
+                T mloc = T(0);
                 const V* thv = reinterpret_cast<const V*>(th_s);
                 int p = p_lo;
                 while (p < p_hi) {
@@ -737,21 +929,28 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         p_end = min(p_hi, p + P.RA);
                         natoms = p_end - p;
                     } else {
-                        while (p_end < p_hi) {
-                            int g = __ldcg(W.act[cur] + p_end);
-                            int sz = P.goff[g + 1] - P.goff[g];
-                            if (natoms + sz > P.RA) break;
-                            natoms += sz;
-                            p_end++;
+                        if (tid == 0) {
+                            while (p_end < p_hi) {
+                                const int g = __ldcg(W.act[cur] + p_end);
+                                const int sz = P.goff[g + 1] - P.goff[g];
+                                if (natoms + sz > P.RA) break;
+                                natoms += sz;
+                                p_end++;
+                            }
+                            s_si[7] = p_end;
+                            s_si[8] = natoms;
                         }
+                        __syncthreads();
+                        p_end = s_si[7];
+                        natoms = s_si[8];
                     }
                     const int abase = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                     if (!P.is_group) {
                         for (int a = tid; a < natoms; a += kThreads) cols_s[a] = __ldcg(W.act[cur] + p + a);
                     } else {
                         for (int q = p + tid; q < p_end; q += kThreads) {
-                            int g = __ldcg(W.act[cur] + q);
-                            int off = __ldcg(W.aoff[cur] + q) - abase;
+                            const int g = __ldcg(W.act[cur] + q);
+                            const int off = __ldcg(W.aoff[cur] + q) - abase;
                             for (int i = P.goff[g]; i < P.goff[g + 1]; i++) cols_s[off + i - P.goff[g]] = i;
                         }
                     }
@@ -794,9 +993,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         for (int c = 0; c < nchunk; c++) z += zpart[a * nchunk + c];
                         if (!P.is_group) {
                             const int ap = abase + a;
-                            double v = __ldcg(W.uc[cur] + ap) - (double)z * invL;
-                            W.xn[ap] = soft_thr(v, thrL);
-                            mloc = fmax(mloc, (double)fabs(z));
+                            W.xn[ap] = it_soft(it_grad_step(ldcg_x(W.uc[cur] + ap), z, invL), thrX);
+                            mloc = fmax(mloc, fabs(z));
                         } else {
                             zpart[a * nchunk] = z;
                         }
@@ -804,37 +1002,38 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     if (P.is_group) {
                         __syncthreads();
                         for (int q = p + tid; q < p_end; q += kThreads) {
-                            int g = __ldcg(W.act[cur] + q);
-                            int off = __ldcg(W.aoff[cur] + q);
-                            int sz = P.goff[g + 1] - P.goff[g];
-                            double zq = 0.0, vq = 0.0;
+                            const int g = __ldcg(W.act[cur] + q);
+                            const int off = __ldcg(W.aoff[cur] + q);
+                            const int sz = P.goff[g + 1] - P.goff[g];
+                            Acc zq, vq;
                             for (int i = 0; i < sz; i++) {
-                                T z = zpart[(off - abase + i) * nchunk];
-                                double v = __ldcg(W.uc[cur] + off + i) - (double)z * invL;
-                                zq += (double)z * (double)z;
-                                vq += v * v;
+                                const T z = zpart[(off - abase + i) * nchunk];
+                                const X v = it_grad_step(ldcg_x(W.uc[cur] + off + i), z, invL);
+                                zq.add(z, z);
+                                acc_sq(vq, v);
                             }
                             const double wg = P.w[g];
-                            const double nv = sqrt(vq);
+                            const double nv = sqrt(vq.value());
                             // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
-                            const double f = nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0;
+                            const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0, (X*)nullptr);
                             for (int i = 0; i < sz; i++) {
-                                T z = zpart[(off - abase + i) * nchunk];
-                                double v = __ldcg(W.uc[cur] + off + i) - (double)z * invL;
-                                W.xn[off + i] = f * v;
+                                const T z = zpart[(off - abase + i) * nchunk];
+                                W.xn[off + i] = it_scale(it_grad_step(ldcg_x(W.uc[cur] + off + i), z, invL), f);
                             }
-                            mloc = fmax(mloc, sqrt(zq) / wg);
+                            // rounded up so that the FP32 max stays an upper bound of the FP64 value
+                            mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
                         }
                     }
                     __syncthreads();
                     p = p_end;
                 }
-                mloc = warp_max(mloc);
-                if (lane == 0) s_dred[warp] = mloc;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+                if (lane == 0) s_dred[warp] = (double)mloc;
                 __syncthreads();
                 if (tid == 0) {
-                    double m = 0.0;
-                    for (int k = 0; k < nw; k++) m = fmax(m, s_dred[k]);
+                    T m = T(0);
+                    for (int k = 0; k < nw; k++) m = fmax(m, (T)s_dred[k]);
                     W.p_m[b] = m;
                 }
             }
@@ -844,35 +1043,43 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
             // ===================================== (C) screening + momentum
             {
                 if (warp == 0) {
-                    double m = warp_max_fixed(W.p_m, G, lane);
-                    if (lane == 0) s_sc[7] = m;
+                    T mv[kMaxG / 32];
+#pragma unroll
+                    for (int j = 0; j < kMaxG / 32; j++) mv[j] = lane + 32 * j < G ? __ldcg(W.p_m + lane + 32 * j) : T(0);
+                    T mf = T(0);
+#pragma unroll
+                    for (int j = 0; j < kMaxG / 32; j++) mf = fmax(mf, mv[j]);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+                    const double m_nom = (double)mf;
+                    if (lane == 0) {
+                        // Lemma 8 with the nominal max |z| (for the gap) and with a rigorous upper
+                        // bound on it given the FP rounding of z (for the screening radius)
+                        const double m_up = m_nom + P.gamma * sqrt_beta * P.fmax;
+                        mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
+                        const double mu_s = (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) ? copysign(fast_rcp(m_up), s_unc) : s_unc;
+                        // R^2 = ||y/lambda - mu theta||^2
+                        R2n = fmax(fma(mu_nom, fma(mu_nom, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
+                        const double R2s = fmax(fma(mu_s, fma(mu_s, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
+                        // radii rounded up a little: a larger radius only screens less
+                        const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
+                        rad = (P.test == 2 || P.test == 5) ? fast_sqrt(fmax(R2s - delta * delta, 0.0)) * (1.0 + 1e-13) : Rs;
+                        s_sc[8] = rad;
+                        s_sc[9] = Rs;
+                    }
                 }
                 __syncthreads();
-                const double m_nom = s_sc[7];
-                // rigorous upper bound on max |d_i^T theta| given the FP rounding of z
-                const double m_up = m_nom + P.gamma * sqrt(beta) * P.fmax;
-                mu_nom = dual_scale(alpha, beta, lam, m_nom);
-                const double mu_s = dual_scale(alpha, beta, lam, m_up);
-                const double R2n = fmax(yy / (lam * lam) - 2.0 * mu_nom * alpha / lam + mu_nom * mu_nom * beta, 0.0);
-                const double R2s = fmax(yy / (lam * lam) - 2.0 * mu_s * alpha / lam + mu_s * mu_s * beta, 0.0);
-                R_nom = sqrt(R2n);
-                const double Rs = sqrt(R2s);
-                rad = (P.test == 2 || P.test == 5) ? sqrt(fmax(R2s - delta * delta, 0.0)) : Rs;
-                // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t
-                double bt = 0.0;
-                if (!ista) {
-                    double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
-                    bt = (lf - 1.0) / ln;
-                    lf = ln;
-                }
+                const double radB = s_sc[8], RsB = s_sc[9];
+                const X btX = it_cast(s_sc[10], (X*)nullptr);
                 int p_lo, p_hi, a_lo;
                 cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 int nz_base = 0, kg = 0, ka = 0, nzx = 0;
-                double l1 = 0.0;
+                Acc l1;
                 for (int base = p_lo; base < p_hi; base += kThreads) {
-                    int p = base + tid;
-                    bool valid = p < p_hi;
-                    int kept = 0, cnt = 0, lo_a = 0, sz = 0, gid = 0;
+                    const int p = base + tid;
+                    const bool valid = p < p_hi;
+                    int cnt = 0, lo_a = 0, sz = 0, gid = 0;
+                    X x1 = it_zero((X*)nullptr), u1 = it_zero((X*)nullptr);  // Lasso: the atom's values
                     if (valid) {
                         gid = __ldcg(W.act[cur] + p);
                         lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
@@ -881,44 +1088,50 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         if (dyn_test) {
                             if (P.test == 3) {
                                 // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
-                                double ni = P.colnorm[gid];
-                                double dc0 = __ldcg(W.b + gid) / (lam * ni);
-                                double tt = __ldcg(W.tv + gid) / (ni * nstar);
-                                double up = dome_max(dc0, tt, psi_dome, Rs);
-                                double dn = dome_max(-dc0, -tt, psi_dome, Rs);
+                                const double ni = P.colnorm[gid];
+                                const double dc0 = __ldcg(W.b + gid) / (lam * ni);
+                                const double tt = __ldcg(W.tv + gid) / (ni * nstar);
+                                const double up = dome_max(dc0, tt, psi_dome, RsB);
+                                const double dn = dome_max(-dc0, -tt, psi_dome, RsB);
                                 kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
                             } else {
-                                kill = __ldcg(W.thr + gid) - rad > P.eps_test;
+                                kill = __ldcg(W.thr + gid) - radB > P.eps_test;
                             }
                         }
-                        kept = !kill;
-                        W.keep[p] = kept;
-                        if (kept) {
-                            double gq = 0.0;
+                        W.keep[p] = !kill;
+                        if (!kill) {
+                            Acc gq;
                             for (int q = 0; q < sz; q++) {
-                                double xv = __ldcg(W.xn + lo_a + q);
-                                double xo = __ldcg(W.xc[cur] + lo_a + q);
-                                double uv = ista ? xv : xv + bt * (xv - xo);
+                                const X xv = ldcg_x(W.xn + lo_a + q);
+                                const X xo = ldcg_x(W.xc[cur] + lo_a + q);
+                                const X uv = ista ? xv : it_momentum(xv, xo, btX);
                                 W.un[lo_a + q] = uv;
-                                cnt += (uv != 0.0 || xv != 0.0);
-                                nzx += xv != 0.0;
-                                gq += xv * xv;
+                                x1 = xv;
+                                u1 = uv;
+                                cnt += (it_nz(uv) || it_nz(xv));
+                                nzx += it_nz(xv);
+                                if (P.is_group) acc_sq(gq, xv);
+                                else acc_abs(l1, xv);
                             }
-                            l1 += (P.is_group ? P.w[gid] : 1.0) * sqrt(gq);
+                            if (P.is_group) acc_add_dbl(l1, P.w[gid] * sqrt(gq.value()));
                             kg += 1;
                             ka += sz;
                         }
                     }
                     int tot;
-                    int pos = block_exclusive_scan(cnt, s_tmp, &tot);
-                    if (cnt) {
+                    const int pos = block_exclusive_scan(cnt, s_tmp, &tot);
+                    if (cnt && !P.is_group) {
+                        const int e = a_lo + nz_base + pos;
+                        W.nz_col[e] = gid;
+                        W.nz_u[e] = u1;
+                        W.nz_x[e] = x1;
+                    } else if (cnt) {
                         int e = a_lo + nz_base + pos;
                         for (int q = 0; q < sz; q++) {
-                            double xv = __ldcg(W.xn + lo_a + q);
-                            double uv = __ldcg(W.un + lo_a + q);
-                            if (uv != 0.0 || xv != 0.0) {
-                                const int col = P.is_group ? P.goff[gid] + q : gid;
-                                W.nz_col[e] = col;
+                            const X xv = ldcg_x(W.xn + lo_a + q);
+                            const X uv = ldcg_x(W.un + lo_a + q);
+                            if (it_nz(uv) || it_nz(xv)) {
+                                W.nz_col[e] = P.is_group ? P.goff[gid] + q : gid;
                                 W.nz_u[e] = uv;
                                 W.nz_x[e] = xv;
                                 e++;
@@ -927,17 +1140,21 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     }
                     nz_base += tot;
                 }
-                int tkg, tka, tnx;
-                block_exclusive_scan(kg, s_tmp, &tkg);
-                block_exclusive_scan(ka, s_tmp, &tka);
-                block_exclusive_scan(nzx, s_tmp, &tnx);
-                l1 = warp_sum(l1);
-                if (lane == 0) s_dred[warp] = l1;
+                // per-CTA totals: one warp-level reduction and a single block barrier
+                const int rkg = warp_sum(kg), rka = warp_sum(ka), rnx = warp_sum(nzx);
+                const Acc rl1 = acc_warp_reduce(l1);
+                if (lane == 0) { s_ired[warp] = rkg; s_tmp[warp] = rka; s_pref[warp] = rnx; acc_store(&s_red[0][warp][0], rl1); }
                 __syncthreads();
                 if (tid == 0) {
-                    double s = 0.0;
-                    for (int k = 0; k < nw; k++) s += s_dred[k];
-                    W.p_l1[b] = s;
+                    int tkg = 0, tka = 0, tnx = 0;
+                    Acc tl1;
+                    for (int k = 0; k < nw; k++) {
+                        tkg += s_ired[k];
+                        tka += s_tmp[k];
+                        tnx += s_pref[k];
+                        acc_merge(tl1, &s_red[0][k][0]);
+                    }
+                    part_put(W.p_l1 + b, tl1);
                     W.s_alo[b] = a_lo;
                     W.c_kg[b] = tkg;
                     W.c_ka[b] = tka;
@@ -961,7 +1178,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                 int lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                 int c0 = P.is_group ? P.goff[gid] : gid;
                 int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
-                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)__ldcg(W.xc[cur] + lo_a + q);
+                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(W.xc[cur] + lo_a + q));
             }
             if (b == 0 && tid == 0) {
                 R->iters = iters;
@@ -1004,8 +1221,7 @@ static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, c
     const int chunk = 32 * EV * kU;
     const int nchunk = (N + chunk - 1) / chunk;
     const int npad = nchunk * chunk;
-    const int G = ctx->num_sms;
-    if (G > kThreads) return DS_ERR_UNSUPPORTED;  // per-CTA prefix arrays are filled one per thread
+    const int G = std::min(ctx->num_sms, kMaxG);  // one CTA per SM, within the fixed-size reductions
 
     // shared memory: theta + zpart + cols, and room for n (hi/lo) in the precompute
     size_t fixed = npad * sizeof(T);
@@ -1029,25 +1245,25 @@ static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, c
         for (int k = 0; k < 2; k++) {
             w.act[k] = bp.take<int>(nG);
             w.aoff[k] = bp.take<int>(nG + 1);
-            w.xc[k] = bp.take<double>(K);
-            w.uc[k] = bp.take<double>(K);
+            w.xc[k] = bp.take<typename IterT<T>::type>(K);
+            w.uc[k] = bp.take<typename IterT<T>::type>(K);
         }
-        w.xn = bp.take<double>(K);
-        w.un = bp.take<double>(K);
+        w.xn = bp.take<typename IterT<T>::type>(K);
+        w.un = bp.take<typename IterT<T>::type>(K);
         w.keep = bp.take<int>(nG);
         w.nz_col = bp.take<int>(K);
-        w.nz_u = bp.take<double>(K);
-        w.nz_x = bp.take<double>(K);
+        w.nz_u = bp.take<typename IterT<T>::type>(K);
+        w.nz_x = bp.take<typename IterT<T>::type>(K);
         w.s_alo = bp.take<int>(G);
         w.c_kg = bp.take<int>(G);
         w.c_ka = bp.take<int>(G);
         w.c_nz = bp.take<int>(G);
         w.c_nnzx = bp.take<int>(G);
-        w.p_m = bp.take<double>(G);
-        w.p_l1 = bp.take<double>(G);
-        w.p_a = bp.take<double>(G);
-        w.p_b = bp.take<double>(G);
-        w.p_r = bp.take<double>(G);
+        w.p_m = bp.take<T>(G);
+        w.p_l1 = bp.take<typename IterT<T>::type>(G);
+        w.p_a = bp.take<typename IterT<T>::type>(G);
+        w.p_b = bp.take<typename IterT<T>::type>(G);
+        w.p_r = bp.take<typename IterT<T>::type>(G);
         w.p_v = bp.take<double>(G);
         w.p_i = bp.take<int>(G);
         *lam_dev = bp.take<double>(std::max(n_lambda, 1));
@@ -1062,7 +1278,14 @@ static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, c
     bp = Bump{reinterpret_cast<char*>(ctx->ws), 0};
     layout(w, &lam_dev, &res_dev);
 
+    if (opt && opt->alg == DS_FISTA) {
+        ds_status fs = ctx_fista_table(ctx, opt->max_iter);
+        if (fs != DS_OK) return fs;
+    }
+
     SolveP<T> P;
+    P.fista = ctx->fista;
+    P.fista_n = ctx->fista_n;
     P.D = reinterpret_cast<const T*>(dict->D);
     P.N = N; P.K = K; P.ld = (int)dict->ld; P.nG = nG; P.is_group = dict->is_group;
     P.goff = dict->goff; P.w = dict->w; P.spec = dict->spec; P.colnorm = dict->colnorm;
