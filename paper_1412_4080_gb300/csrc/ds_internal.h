@@ -64,6 +64,39 @@ constexpr int kDevOk = 0;
 constexpr int kDevNotConverged = 5;
 constexpr int kDevTimeout = 4;
 
+// Dictionary as the solve kernel sees it.
+struct DictDesc {
+    const void* D;
+    int dtype;
+    int N, K, ld, nG, is_group, max_gsize;
+    const int* goff;
+    const double* w;
+    const double* spec;
+    const double* colnorm;  // may be null when norms_in_kernel
+    double fmax, L;
+    bool norms_in_kernel;   // Lasso only: the kernel computes ||d_i|| and their max itself
+};
+
+// Where and how a solve runs: a context (workspace reserved on demand, timing
+// events, FISTA table) or, with ctx == nullptr, a caller-provided workspace.
+struct SolveEnv {
+    cudaStream_t stream;
+    int num_sms;
+    size_t smem_optin;
+    void* ws;
+    size_t ws_bytes;
+    ds_ctx* ctx;
+    const double* fista;
+    int fista_n;
+    double* hist;
+    int hist_rows;
+};
+
+size_t solve_ws_bytes(const DictDesc& dd, int num_sms, size_t smem_optin, int n_lambda);
+ds_status launch_solve_env(const SolveEnv& env, const DictDesc& dd, const void* y_dev, const void* x0_dev, int n_lambda,
+                           const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,
+                           DevResult* res_host, float* ms);
+
 // Host-side launchers (defined in ds_solve.cu / ds_dict.cu).
 ds_status launch_solve(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, const void* x0_dev, int n_lambda,
                        const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,

@@ -76,6 +76,7 @@ struct Ws {
     X* p_r;
     double* p_v;
     int* p_i;
+    double* p_cn;
 };
 
 template <typename T>
@@ -101,6 +102,7 @@ struct SolveP {
     int hist_rows;
     Ws<T> ws;
     int RA, nchunk, npad;
+    double* colnorm_w;    // non-null: the kernel computes ||d_i|| here (and fmax) in its first pass
     const double* fista;  // FISTA table: (coefficient (l_{t-1} - 1) / l_t, l_t) for t = 1..fista_n
     int fista_n;
 };
@@ -377,20 +379,40 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
     __syncthreads();
     {
         const V* yv = reinterpret_cast<const V*>(th_s);
+        const bool norms = P.colnorm_w != nullptr;
+        double cmax = 0.0;
         for (int i = gwarp; i < K; i += total_warps) {
             const V* col = reinterpret_cast<const V*>(P.D + (size_t)i * ld);
-            typename Dot2<T>::type acc;
+            typename Dot2<T>::type acc, nrm;
             for (int v = lane; v < ldv; v += 32) {
                 V d = __ldg(col + v);
                 V q = yv[v];
                 if constexpr (EV == 4) {
                     acc.add(d.x, q.x); acc.add(d.y, q.y); acc.add(d.z, q.z); acc.add(d.w, q.w);
+                    if (norms) { nrm.add(d.x, d.x); nrm.add(d.y, d.y); nrm.add(d.z, d.z); nrm.add(d.w, d.w); }
                 } else {
                     acc.add(d.x, q.x); acc.add(d.y, q.y);
+                    if (norms) { nrm.add(d.x, d.x); nrm.add(d.y, d.y); }
                 }
             }
             double s = warp_sum(acc.value());
             if (lane == 0) W.b[i] = s;
+            if (norms) {
+                const double c = sqrt(warp_sum(nrm.value()));
+                if (lane == 0) P.colnorm_w[i] = c;
+                cmax = fmax(cmax, c);
+            }
+        }
+        if (norms) {
+            cmax = warp_max(cmax);
+            if (lane == 0) s_dred[warp] = cmax;
+            __syncthreads();
+            if (tid == 0) {
+                double m = 0.0;
+                for (int k = 0; k < nw; k++) m = fmax(m, s_dred[k]);
+                W.p_cn[b] = m;
+            }
+            __syncthreads();
         }
         double yy = 0.0;
         for (int r = b * kThreads + tid; r < N; r += G * kThreads) {
@@ -408,6 +430,17 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
     }
     ok = grid_sync(W.bar, G, gen);
     if (!ok) return false;
+    // column norms computed above: their maximum bounds the GEMV rounding (Lasso)
+    const double* colnorm = P.colnorm_w ? P.colnorm_w : P.colnorm;
+    double fmax_d = P.fmax;
+    if (P.colnorm_w) {
+        if (warp == 0) {
+            const double m = warp_max_fixed(W.p_cn, G, lane);
+            if (lane == 0) s_sc[11] = m * (1.0 + 1e-12);
+        }
+        __syncthreads();
+        fmax_d = s_sc[11];
+    }
 
     // --------------------------------- P0b: lambda_* (Sec. 2.2.2 / eq. gstar)
     {
@@ -580,7 +613,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
         // DST3 / DGST3 centre c = y/lam - coef n, offset delta = ||y/lam - c|| (Lemmas 3, 6)
         const double coef = need_n && nn > 0.0 ? (nty / lam - wstar2) / nn : 0.0;
         const double delta = need_n && nn > 0.0 ? fabs(nty / lam - wstar2) / sqrt(nn) : 0.0;
-        const double nstar = P.is_group ? 1.0 : P.colnorm[star];
+        const double nstar = P.is_group ? 1.0 : colnorm[star];
         const double psi_dome = psi / nstar;
         const T invL = (T)(1.0 / P.L);
         const double thrL = lam / P.L;
@@ -639,14 +672,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                             q += dtc * dtc;
                         }
                         double wg = P.is_group ? P.w[p] : 1.0;
-                        double sg = P.is_group ? P.spec[p] : P.colnorm[p];
+                        double sg = P.is_group ? P.spec[p] : colnorm[p];
                         th = (wg - sqrt(q)) / sg;
                         W.thr[p] = th;
                     }
                     bool kill = false;
                     if (stat) {
                         if (P.test == 3) {
-                            double ni = P.colnorm[p];
+                            double ni = colnorm[p];
                             double dc0 = __ldcg(W.b + p) / (lam * ni);
                             double tt = __ldcg(W.tv + p) / (ni * nstar);
                             double up = dome_max(dc0, tt, psi_dome, rad0);
@@ -1055,7 +1088,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                     if (lane == 0) {
                         // Lemma 8 with the nominal max |z| (for the gap) and with a rigorous upper
                         // bound on it given the FP rounding of z (for the screening radius)
-                        const double m_up = m_nom + P.gamma * sqrt_beta * P.fmax;
+                        const double m_up = m_nom + P.gamma * sqrt_beta * fmax_d;
                         mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
                         const double mu_s = (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) ? copysign(fast_rcp(m_up), s_unc) : s_unc;
                         // R^2 = ||y/lambda - mu theta||^2
@@ -1088,7 +1121,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P)
                         if (dyn_test) {
                             if (P.test == 3) {
                                 // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
-                                const double ni = P.colnorm[gid];
+                                const double ni = colnorm[gid];
                                 const double dc0 = __ldcg(W.b + gid) / (lam * ni);
                                 const double tt = __ldcg(W.tv + gid) / (ni * nstar);
                                 const double up = dome_max(dc0, tt, psi_dome, RsB);
@@ -1211,90 +1244,134 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(const SolveP<T> P)
 
 // ------------------------------------------------------------ host launcher
 
+namespace {
+
+struct Geometry {
+    int nchunk, npad, RA, G;
+    size_t smem;
+};
+
 template <typename T>
-static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, const void* x0_dev, int n_lambda,
-                          const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,
-                          DevResult* res_host, float* ms)
+ds_status geometry(const DictDesc& dd, int num_sms, size_t smem_optin, Geometry* g)
 {
     constexpr int EV = 16 / sizeof(T);
-    const int N = (int)dict->N, K = (int)dict->K, nG = dict->nG;
     const int chunk = 32 * EV * kU;
-    const int nchunk = (N + chunk - 1) / chunk;
-    const int npad = nchunk * chunk;
-    const int G = std::min(ctx->num_sms, kMaxG);  // one CTA per SM, within the fixed-size reductions
-
+    g->nchunk = (dd.N + chunk - 1) / chunk;
+    g->npad = g->nchunk * chunk;
+    g->G = std::min(num_sms, kMaxG);  // one CTA per SM, within the fixed-size reductions
     // shared memory: theta + zpart + cols, and room for n (hi/lo) in the precompute
-    size_t fixed = npad * sizeof(T);
-    size_t budget = ctx->smem_optin > 48 * 1024 ? ctx->smem_optin - 40 * 1024 : 48 * 1024;
-    if (fixed + 64 * (nchunk * sizeof(T) + 4) > budget) return DS_ERR_UNSUPPORTED;
-    int RA = (int)std::min<size_t>(512, (budget - fixed) / (nchunk * sizeof(T) + 4));
-    if (dict->is_group && RA < dict->max_gsize) return DS_ERR_UNSUPPORTED;
-    size_t smem = fixed + (size_t)RA * (nchunk * sizeof(T) + 4);
-    smem = std::max(smem, (size_t)npad * 8);
-    if (smem > budget) return DS_ERR_UNSUPPORTED;
+    const size_t fixed = g->npad * sizeof(T);
+    const size_t budget = smem_optin > 48 * 1024 ? smem_optin - 40 * 1024 : 48 * 1024;
+    if (fixed + 64 * (g->nchunk * sizeof(T) + 4) > budget) return DS_ERR_UNSUPPORTED;
+    g->RA = (int)std::min<size_t>(512, (budget - fixed) / (g->nchunk * sizeof(T) + 4));
+    if (dd.is_group && g->RA < dd.max_gsize) return DS_ERR_UNSUPPORTED;
+    g->smem = std::max(fixed + (size_t)g->RA * (g->nchunk * sizeof(T) + 4), (size_t)g->npad * 8);
+    if (g->smem > budget) return DS_ERR_UNSUPPORTED;
+    return DS_OK;
+}
 
-    // workspace
-    Bump bp{nullptr, 0};
-    auto layout = [&](Ws<T>& w, double** lam_dev, DevResult** res_dev) {
-        w.bar = bp.take<GridBarrier>(1);
-        w.theta = bp.take<T>(npad);
-        w.b = bp.take<double>(K);
-        w.tv = bp.take<double>(K);
-        w.thr = bp.take<double>(nG);
-        w.nvec = bp.take<double>(N);
-        for (int k = 0; k < 2; k++) {
-            w.act[k] = bp.take<int>(nG);
-            w.aoff[k] = bp.take<int>(nG + 1);
-            w.xc[k] = bp.take<typename IterT<T>::type>(K);
-            w.uc[k] = bp.take<typename IterT<T>::type>(K);
-        }
-        w.xn = bp.take<typename IterT<T>::type>(K);
-        w.un = bp.take<typename IterT<T>::type>(K);
-        w.keep = bp.take<int>(nG);
-        w.nz_col = bp.take<int>(K);
-        w.nz_u = bp.take<typename IterT<T>::type>(K);
-        w.nz_x = bp.take<typename IterT<T>::type>(K);
-        w.s_alo = bp.take<int>(G);
-        w.c_kg = bp.take<int>(G);
-        w.c_ka = bp.take<int>(G);
-        w.c_nz = bp.take<int>(G);
-        w.c_nnzx = bp.take<int>(G);
-        w.p_m = bp.take<T>(G);
-        w.p_l1 = bp.take<typename IterT<T>::type>(G);
-        w.p_a = bp.take<typename IterT<T>::type>(G);
-        w.p_b = bp.take<typename IterT<T>::type>(G);
-        w.p_r = bp.take<typename IterT<T>::type>(G);
-        w.p_v = bp.take<double>(G);
-        w.p_i = bp.take<int>(G);
-        *lam_dev = bp.take<double>(std::max(n_lambda, 1));
-        *res_dev = bp.take<DevResult>(std::max(n_lambda, 1));
-    };
+// Carves the solve workspace out of `base` (nullptr: only measures it).
+template <typename T>
+size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_lambda, Ws<T>* w, double** lam_dev,
+              DevResult** res_dev, double** colnorm_w)
+{
+    using X = typename IterT<T>::type;
+    const int N = dd.N, K = dd.K, nG = dd.nG, G = g.G;
+    Bump bp{base, 0};
+    w->bar = bp.take<GridBarrier>(1);
+    w->theta = bp.take<T>(g.npad);
+    w->b = bp.take<double>(K);
+    w->tv = bp.take<double>(K);
+    w->thr = bp.take<double>(nG);
+    w->nvec = bp.take<double>(N);
+    for (int k = 0; k < 2; k++) {
+        w->act[k] = bp.take<int>(nG);
+        w->aoff[k] = bp.take<int>(nG + 1);
+        w->xc[k] = bp.take<X>(K);
+        w->uc[k] = bp.take<X>(K);
+    }
+    w->xn = bp.take<X>(K);
+    w->un = bp.take<X>(K);
+    w->keep = bp.take<int>(nG);
+    w->nz_col = bp.take<int>(K);
+    w->nz_u = bp.take<X>(K);
+    w->nz_x = bp.take<X>(K);
+    w->s_alo = bp.take<int>(G);
+    w->c_kg = bp.take<int>(G);
+    w->c_ka = bp.take<int>(G);
+    w->c_nz = bp.take<int>(G);
+    w->c_nnzx = bp.take<int>(G);
+    w->p_m = bp.take<T>(G);
+    w->p_l1 = bp.take<X>(G);
+    w->p_a = bp.take<X>(G);
+    w->p_b = bp.take<X>(G);
+    w->p_r = bp.take<X>(G);
+    w->p_v = bp.take<double>(G);
+    w->p_i = bp.take<int>(G);
+    w->p_cn = bp.take<double>(G);
+    *lam_dev = bp.take<double>(std::max(n_lambda, 1));
+    *res_dev = bp.take<DevResult>(std::max(n_lambda, 1));
+    *colnorm_w = dd.norms_in_kernel ? bp.take<double>(K) : nullptr;
+    return bp.off + 256;
+}
+
+}  // namespace
+
+template <typename T>
+size_t solve_ws_bytes_t(const DictDesc& dd, int num_sms, size_t smem_optin, int n_lambda)
+{
+    Geometry g;
+    if (geometry<T>(dd, num_sms, smem_optin, &g) != DS_OK) return 0;
+    Ws<T> w;
+    double* l;
+    DevResult* r;
+    double* c;
+    return layout<T>(nullptr, dd, g, n_lambda, &w, &l, &r, &c);
+}
+
+size_t solve_ws_bytes(const DictDesc& dd, int num_sms, size_t smem_optin, int n_lambda)
+{
+    return dd.dtype == DS_FP32 ? solve_ws_bytes_t<float>(dd, num_sms, smem_optin, n_lambda)
+                               : solve_ws_bytes_t<double>(dd, num_sms, smem_optin, n_lambda);
+}
+
+template <typename T>
+static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const void* y_dev, const void* x0_dev,
+                              int n_lambda, const double* lambdas_host, const ds_options* opt, void* xout_dev,
+                              int64_t ldx, DevResult* res_host, float* ms)
+{
+    constexpr int EV = 16 / sizeof(T);
+    Geometry g;
+    ds_status st = geometry<T>(dd, env.num_sms, env.smem_optin, &g);
+    if (st != DS_OK) return st;
     Ws<T> w;
     double* lam_dev;
     DevResult* res_dev;
-    layout(w, &lam_dev, &res_dev);
-    ds_status st = ctx_reserve(ctx, bp.off + 256);
-    if (st != DS_OK) return st;
-    bp = Bump{reinterpret_cast<char*>(ctx->ws), 0};
-    layout(w, &lam_dev, &res_dev);
-
-    if (opt && opt->alg == DS_FISTA) {
-        ds_status fs = ctx_fista_table(ctx, opt->max_iter);
-        if (fs != DS_OK) return fs;
+    double* colnorm_w;
+    const size_t need = layout<T>(nullptr, dd, g, n_lambda, &w, &lam_dev, &res_dev, &colnorm_w);
+    char* base = reinterpret_cast<char*>(env.ws);
+    if (env.ctx) {
+        st = ctx_reserve(env.ctx, need);
+        if (st != DS_OK) return st;
+        base = reinterpret_cast<char*>(env.ctx->ws);
+    } else if (!base || env.ws_bytes < need) {
+        return DS_ERR_UNSUPPORTED;
     }
+    layout<T>(base, dd, g, n_lambda, &w, &lam_dev, &res_dev, &colnorm_w);
 
     SolveP<T> P;
-    P.fista = ctx->fista;
-    P.fista_n = ctx->fista_n;
-    P.D = reinterpret_cast<const T*>(dict->D);
-    P.N = N; P.K = K; P.ld = (int)dict->ld; P.nG = nG; P.is_group = dict->is_group;
-    P.goff = dict->goff; P.w = dict->w; P.spec = dict->spec; P.colnorm = dict->colnorm;
-    P.fmax = dict->fmax;
+    P.fista = env.fista;
+    P.fista_n = env.fista_n;
+    P.D = reinterpret_cast<const T*>(dd.D);
+    P.N = dd.N; P.K = dd.K; P.ld = dd.ld; P.nG = dd.nG; P.is_group = dd.is_group;
+    P.goff = dd.goff; P.w = dd.w; P.spec = dd.spec; P.colnorm = dd.colnorm;
+    P.fmax = dd.fmax;
+    P.colnorm_w = colnorm_w;
     {
         // worst-case rounding of the FP GEMV: each product goes through at most
         // kU*EV FMAs in a lane, 5 shuffle additions and nchunk chunk additions
         const double u = sizeof(T) == 4 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
-        const double k = kU * EV + 5 + nchunk;
+        const double k = kU * EV + 5 + g.nchunk;
         P.gamma = 1.01 * k * u / (1.0 - k * u);
     }
     P.eps_test = sizeof(T) == 4 ? 1e-9 : 1e-11;
@@ -1308,62 +1385,114 @@ static ds_status launch_t(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, c
     P.dynamic = opt ? opt->dynamic : 1;
     P.max_iter = opt ? opt->max_iter : 1;
     P.tol = opt ? opt->tol_gap_rel : 0.0;
-    P.L = (opt && opt->L > 0) ? opt->L : dict->L;
+    P.L = (opt && opt->L > 0) ? opt->L : dd.L;
     P.x_out = reinterpret_cast<T*>(xout_dev);
     P.ldx = ldx;
     P.res = res_dev;
-    P.hist = ctx->hist;
-    P.hist_rows = ctx->hist_rows;
+    P.hist = env.hist;
+    P.hist_rows = env.hist_rows;
     P.ws = w;
-    P.RA = RA;
-    P.nchunk = nchunk;
-    P.npad = npad;
+    P.RA = g.RA;
+    P.nchunk = g.nchunk;
+    P.npad = g.npad;
 
-    cudaStream_t s = ctx->stream;
+    cudaStream_t s = env.stream;
     if (n_lambda > 0 &&
         cudaMemcpyAsync(lam_dev, lambdas_host, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DS_ERR_CUDA;
     if (cudaMemsetAsync(w.bar, 0, sizeof(GridBarrier), s) != cudaSuccess) return DS_ERR_CUDA;
     if (cudaMemsetAsync(res_dev, 0, sizeof(DevResult) * std::max(n_lambda, 1), s) != cudaSuccess) return DS_ERR_CUDA;
 
-    static bool attr_set = false;
-    if (!attr_set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return DS_ERR_CUDA;
+    static bool attr_set[64] = {};
+    if (dev < 64 && !attr_set[dev]) {
         if (cudaFuncSetAttribute(solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(ctx->smem_optin - 40 * 1024)) != cudaSuccess)
+                                 (int)(env.smem_optin - 40 * 1024)) != cudaSuccess)
             return DS_ERR_CUDA;
-        attr_set = true;
+        attr_set[dev] = true;
     }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel<T>, kThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel<T>, kThreads, g.smem) != cudaSuccess)
         return DS_ERR_CUDA;
     if (occ < 1) return DS_ERR_UNSUPPORTED;
 
     void* args[] = {(void*)&P};
-    ctx->launches++;
-    cudaEventRecord(ctx->ev0, s);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel<T>, dim3(G), dim3(kThreads), args, smem, s);
+    if (env.ctx) {
+        env.ctx->launches++;
+        cudaEventRecord(env.ctx->ev0, s);
+    }
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel<T>, dim3(g.G), dim3(kThreads), args, g.smem, s);
     if (e != cudaSuccess) {
         fprintf(stderr, "dscreen: solve launch failed: %s\n", cudaGetErrorString(e));
         return DS_ERR_CUDA;
     }
-    cudaEventRecord(ctx->ev1, s);
+    if (env.ctx) cudaEventRecord(env.ctx->ev1, s);
     if (cudaMemcpyAsync(res_host, res_dev, sizeof(DevResult) * std::max(n_lambda, 1), cudaMemcpyDeviceToHost, s) !=
         cudaSuccess)
         return DS_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DS_ERR_CUDA;
-    if (ms) cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1);
+    if (ms) {
+        *ms = 0.f;
+        if (env.ctx) cudaEventElapsedTime(ms, env.ctx->ev0, env.ctx->ev1);
+    }
     for (int j = 0; j < std::max(n_lambda, 1); j++)
         if (res_host[j].status == kDevTimeout) return DS_ERR_TIMEOUT;
+    (void)EV;
     return DS_OK;
+}
+
+ds_status launch_solve_env(const SolveEnv& env, const DictDesc& dd, const void* y_dev, const void* x0_dev, int n_lambda,
+                           const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,
+                           DevResult* res_host, float* ms)
+{
+    if (dd.dtype == DS_FP32)
+        return launch_env_t<float>(env, dd, y_dev, x0_dev, n_lambda, lambdas_host, opt, xout_dev, ldx, res_host, ms);
+    return launch_env_t<double>(env, dd, y_dev, x0_dev, n_lambda, lambdas_host, opt, xout_dev, ldx, res_host, ms);
+}
+
+DictDesc dict_desc(const ds_dict* d)
+{
+    DictDesc dd;
+    dd.D = d->D;
+    dd.dtype = d->dtype;
+    dd.N = (int)d->N;
+    dd.K = (int)d->K;
+    dd.ld = (int)d->ld;
+    dd.nG = d->nG;
+    dd.is_group = d->is_group;
+    dd.max_gsize = d->max_gsize;
+    dd.goff = d->goff;
+    dd.w = d->w;
+    dd.spec = d->spec;
+    dd.colnorm = d->colnorm;
+    dd.fmax = d->fmax;
+    dd.L = d->L;
+    dd.norms_in_kernel = false;
+    return dd;
 }
 
 ds_status launch_solve(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, const void* x0_dev, int n_lambda,
                        const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,
                        DevResult* res_host, float* ms)
 {
-    if (dict->dtype == DS_FP32)
-        return launch_t<float>(ctx, dict, y_dev, x0_dev, n_lambda, lambdas_host, opt, xout_dev, ldx, res_host, ms);
-    return launch_t<double>(ctx, dict, y_dev, x0_dev, n_lambda, lambdas_host, opt, xout_dev, ldx, res_host, ms);
+    if (opt && opt->alg == DS_FISTA) {
+        ds_status fs = ctx_fista_table(ctx, opt->max_iter);
+        if (fs != DS_OK) return fs;
+    }
+    SolveEnv env;
+    env.stream = ctx->stream;
+    env.num_sms = ctx->num_sms;
+    env.smem_optin = ctx->smem_optin;
+    env.ws = nullptr;
+    env.ws_bytes = 0;
+    env.ctx = ctx;
+    env.fista = ctx->fista;
+    env.fista_n = ctx->fista_n;
+    env.hist = ctx->hist;
+    env.hist_rows = ctx->hist_rows;
+    return launch_solve_env(env, dict_desc(dict), y_dev, x0_dev, n_lambda, lambdas_host, opt, xout_dev, ldx, res_host,
+                            ms);
 }
 
 ds_status launch_lambda_max(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, double* lmax)
