@@ -153,6 +153,38 @@ ds_status ds_solve(ds_ctx* ctx, const ds_dict* dict, const void* y, double lambd
 ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* dict, const void* y, int n_lambda, const double* lambdas,
                         const ds_options* opt, const void* x0, void* X_out, ds_result* res);
 
+/* Allocation-free Lasso solve.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- a framework whose
+ * caching allocator owns all device memory, a service with a fixed memory
+ * budget committed up front, or a latency-critical loop that must not pay for
+ * cudaMalloc/cudaFree (cudaFree can synchronize the whole device).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: the solver's scratch is
+ * one fixed 3 MiB array in device memory that every GPU loading this library
+ * holds until the process exits.
+ *
+ * Same computation as ds_solve with a Lasso dictionary (FISTA/ISTA, any test;
+ * DS_GSAFE / DS_DGST3 act as singleton groups), run on `device` and ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ *   D      device, FP32, column-major N x K, leading dimension ld >= N with
+ *          ld % 4 == 0 and D 16-byte aligned; rows N..ld-1, if any, must hold
+ *          finite values (they are multiplied by zero).
+ *   y      device, FP32, N entries.      x_out  device, FP32, K entries.
+ *   opt    host; opt->L > 0 is required (e.g. ds_dict_lipschitz of a
+ *          registered copy of D, or any upper bound of ||D||_2^2).
+ *   res    host.
+ * Limits: N <= 4096 and K <= 16384, else DS_ERR_UNSUPPORTED (the fixed
+ * scratch would be too small; a message names the limits).
+ * The first call on a device resolves the scratch array's device address
+ * (set-up, once per device); make that first call before any stream capture.
+ * Every call shares the one scratch array per device and it keeps the last
+ * call's contents; the call clears what must start at zero.  Calls whose GPU
+ * work overlaps (concurrent streams, several host threads) race on the array:
+ * serialise them.  Synchronous like ds_solve.  Errors: DS_ERR_INVALID (null or
+ * host pointers, bad sizes or alignment, lambda <= 0, opt->L <= 0),
+ * DS_ERR_UNSUPPORTED, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
+ds_status ds_solve_lasso_noalloc(int device, void* cuda_stream, const float* D, int64_t N, int64_t K, int64_t ld,
+                                 const float* y, double lambda, const ds_options* opt, float* x_out, ds_result* res);
+
 /* Number of CUDA kernels this context has launched so far (solves, lambda_max
  * queries and dictionary precomputes).  Errors: DS_ERR_INVALID on NULL. */
 ds_status ds_ctx_kernel_launches(const ds_ctx* ctx, int64_t* n);

@@ -89,6 +89,8 @@ def lib():
                                         ctypes.POINTER(ds_result)]
             L.ds_set_history.argtypes = [vp, vp, ctypes.c_int]
             L.ds_ctx_kernel_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+            L.ds_solve_lasso_noalloc.argtypes = [ctypes.c_int, vp, vp, i64, i64, i64, vp, dp,
+                                                 ctypes.POINTER(ds_options), vp, ctypes.POINTER(ds_result)]
             for name in declared_functions():
                 if name != "ds_status_str":
                     getattr(L, name).restype = ctypes.c_int
@@ -215,6 +217,17 @@ def ds_ctx_kernel_launches(ctx) -> int:
     n = ctypes.c_int64()
     _check(lib().ds_ctx_kernel_launches(ctx, ctypes.byref(n)), "ds_ctx_kernel_launches")
     return n.value
+
+
+def ds_solve_lasso_noalloc(device, stream, D, y, lam, opt, x_out):
+    """Allocation-free Lasso solve on caller-owned device buffers (opt.L > 0 required)."""
+    N, K, ld = _dict_layout(D)
+    r = ds_result()
+    s = None if stream is None else getattr(stream, "cuda_stream", stream)
+    st = lib().ds_solve_lasso_noalloc(int(device), s, _ptr(D)[0], N, K, ld, _ptr(y)[0], float(lam),
+                                      ctypes.byref(opt), _ptr(x_out)[0], ctypes.byref(r))
+    _check(st, "ds_solve_lasso_noalloc")
+    return r.as_dict()
 
 
 def ds_set_history(ctx, hist=None):
