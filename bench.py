@@ -39,6 +39,25 @@ WORKLOAD = ("Lasso FISTA + dynamic SAFE/DST3/Dome, FP32, D 2000x10000 Gaussian u
             "precompute + 15 solves")
 
 
+def _kernel_traffic():
+    """DRAM bytes per solve-kernel launch from the committed ncu summary, if the
+    kernel sources still hash to the value recorded there (else None)."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "solve_kernel_config2.md")
+    if not os.path.exists(prof):
+        return None
+    src = b"".join(open(os.path.join(ROOT, "paper_1412_4080_gb300", "csrc", f), "rb").read()
+                   for f in ("ds_solve.cu", "ds_common.cuh"))
+    h = hashlib.sha256(src).hexdigest()[:16]
+    rec, val = None, None
+    for line in open(prof):
+        if line.startswith("source-sha256:"):
+            rec = line.split()[1]
+        if line.startswith("dram_bytes_per_launch:"):
+            val = float(line.split()[1])
+    return val if rec == h else None
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -267,7 +286,8 @@ def main():
     bytes_alg = cols * N * 4
     achieved = bytes_alg / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_kind": peak_kind, "kernel": "solve_kernel<float>",
+            "traffic": _kernel_traffic(), "peak_kind": peak_kind, "kernel": "solve_kernel<float>",
+            "bytes_per_launch": bytes_alg / (args.steps * len(TESTS)),
             "note": "D (80 MB) is L2-resident across iterations inside a solve; see roofline_large for D > L2"}
 
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
