@@ -153,6 +153,34 @@ ds_status ds_solve(ds_ctx* ctx, const ds_dict* dict, const void* y, double lambd
 ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* dict, const void* y, int n_lambda, const double* lambdas,
                         const ds_options* opt, const void* x0, void* X_out, ds_result* res);
 
+/* ----------------------------------------------------------------- batches
+ * Many solves in one persistent launch.  n instances; instance i has a
+ * registered dictionary dicts[i] (all of one dtype, on this context),
+ * n_rhs[i] right-hand sides Y[i] (device, N_i x n_rhs[i], column r contiguous)
+ * and one lambda per right-hand side lambdas[i][r] (host; absolute, or
+ * fractions of each y's lambda_max when opt->lambda_rel).  Solutions go to
+ * X_out[i] (device, K_i x n_rhs[i]).  Every (instance, rhs) pair is one problem
+ * of Algorithm 3; a persistent kernel splits the GPU into teams of CTAs that
+ * take problems from a queue, largest instances first, so uneven problems run
+ * side by side; problems of one instance run next to each other and share its
+ * dictionary through the L2.  The device work of a run (descriptor upload,
+ * counters, the launch, result download) is captured once into a CUDA graph by
+ * ds_batch_create and replayed by every ds_batch_run; buffers are read at run
+ * time, so new y values (same addresses) and new lambdas (same host arrays)
+ * are picked up.  res: host, sum(n_rhs) entries, instance-major.
+ * Errors: DS_ERR_INVALID, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_UNSUPPORTED,
+ * DS_ERR_TIMEOUT. */
+typedef struct ds_batch ds_batch;
+ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
+                          const double* const* lambdas, const ds_options* opt, void* const* X_out, ds_batch** out);
+ds_status ds_batch_run(ds_batch* batch, ds_result* res);
+/* Whether the run replays a CUDA graph, and the team layout chosen. */
+ds_status ds_batch_info(const ds_batch* batch, int* uses_graph, int* teams, int* team_size);
+ds_status ds_batch_destroy(ds_batch* batch);
+/* One-shot form: create, run once, destroy. */
+ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
+                         const double* const* lambdas, const ds_options* opt, void* const* X_out, ds_result* res);
+
 /* Allocation-free Lasso solve.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- a framework whose
  * caching allocator owns all device memory, a service with a fixed memory

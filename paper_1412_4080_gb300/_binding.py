@@ -89,6 +89,13 @@ def lib():
                                         ctypes.POINTER(ds_result)]
             L.ds_set_history.argtypes = [vp, vp, ctypes.c_int]
             L.ds_ctx_kernel_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+            L.ds_batch_create.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp,
+                                          ctypes.POINTER(vp)]
+            L.ds_batch_run.argtypes = [vp, vp]
+            L.ds_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]
+            L.ds_batch_destroy.argtypes = [vp]
+            L.ds_solve_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp, vp]
             L.ds_solve_lasso_noalloc.argtypes = [ctypes.c_int, vp, vp, i64, i64, i64, vp, dp,
                                                  ctypes.POINTER(ds_options), vp, ctypes.POINTER(ds_result)]
             for name in declared_functions():
@@ -217,6 +224,59 @@ def ds_ctx_kernel_launches(ctx) -> int:
     n = ctypes.c_int64()
     _check(lib().ds_ctx_kernel_launches(ctx, ctypes.byref(n)), "ds_ctx_kernel_launches")
     return n.value
+
+
+class _BatchArgs:
+    """ctypes arrays describing a batch (kept alive as long as the plan)."""
+
+    def __init__(self, dicts, Ys, lambdas, Xs):
+        n = len(dicts)
+        self.n = n
+        self.dicts = (ctypes.c_void_p * n)(*[d.value for d in dicts])
+        self.Y = (ctypes.c_void_p * n)(*[_ptr(y)[0] for y in Ys])
+        self.nrhs = (ctypes.c_int * n)(*[int(y.shape[0]) if len(y.shape) == 2 else 1 for y in Ys])
+        self.lam_arrays = [np.ascontiguousarray(l, dtype=np.float64) for l in lambdas]
+        self.lam = (ctypes.c_void_p * n)(*[a.ctypes.data for a in self.lam_arrays])
+        self.X = (ctypes.c_void_p * n)(*[_ptr(x)[0] for x in Xs])
+        self.total = sum(self.nrhs)
+
+
+class ds_batch_handle:
+    def __init__(self, h, args, opt):
+        self.h, self.args, self.opt = h, args, opt
+
+
+def ds_batch_create(ctx, dicts, Ys, lambdas, opt, Xs):
+    """Ys[i]: device (n_rhs_i, N_i) tensor (row r = right-hand side r); Xs[i]: (n_rhs_i, K_i)."""
+    a = _BatchArgs(dicts, Ys, lambdas, Xs)
+    h = ctypes.c_void_p()
+    _check(lib().ds_batch_create(ctx, a.n, a.dicts, a.Y, a.nrhs, a.lam, ctypes.byref(opt), a.X, ctypes.byref(h)),
+           "ds_batch_create")
+    return ds_batch_handle(h, a, opt)
+
+
+def ds_batch_run(batch):
+    res = (ds_result * batch.args.total)()
+    _check(lib().ds_batch_run(batch.h, res), "ds_batch_run")
+    return [r.as_dict() for r in res]
+
+
+def ds_batch_info(batch):
+    g, t, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().ds_batch_info(batch.h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(s)), "ds_batch_info")
+    return {"uses_graph": bool(g.value), "teams": t.value, "team_size": s.value}
+
+
+def ds_batch_destroy(batch):
+    _check(lib().ds_batch_destroy(batch.h), "ds_batch_destroy")
+
+
+def ds_solve_batch(ctx, dicts, Ys, lambdas, opt, Xs):
+    a = _BatchArgs(dicts, Ys, lambdas, Xs)
+    res = (ds_result * a.total)()
+    _check(lib().ds_solve_batch(ctx, a.n, a.dicts, a.Y, a.nrhs, a.lam, ctypes.byref(opt), a.X, res),
+           "ds_solve_batch")
+    return [r.as_dict() for r in res]
 
 
 def ds_solve_lasso_noalloc(device, stream, D, y, lam, opt, x_out):

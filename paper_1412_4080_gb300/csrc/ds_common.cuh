@@ -51,6 +51,10 @@ __device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned in
 __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, unsigned int& target)
 {
     __shared__ int s_ok;
+    if (nblocks == 1) {  // a team of one CTA: the block barrier is enough
+        __syncthreads();
+        return true;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;

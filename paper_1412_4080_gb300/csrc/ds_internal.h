@@ -93,6 +93,7 @@ struct SolveEnv {
 };
 
 size_t solve_ws_bytes(const DictDesc& dd, int num_sms, size_t smem_optin, int n_lambda);
+DictDesc dict_desc(const ds_dict* d);
 ds_status launch_solve_env(const SolveEnv& env, const DictDesc& dd, const void* y_dev, const void* x0_dev, int n_lambda,
                            const double* lambdas_host, const ds_options* opt, void* xout_dev, int64_t ldx,
                            DevResult* res_host, float* ms);

@@ -24,1219 +24,15 @@
 //
 // Reductions are per-CTA partials summed in a fixed order by every CTA, so all
 // CTAs take identical decisions and the results do not depend on timing.
-#include <algorithm>
-#include <cmath>
-#include <cstdio>
-
-#include "ds_internal.h"
+#include "ds_solve_body.cuh"
 
 namespace ds {
-
-constexpr int kThreads = 512;
-constexpr int kMaxG = 160;  // CTAs of the persistent grid (one per SM) handled by the fixed reductions
-constexpr int kU = 4;         // 16-byte vectors per lane per GEMV item
-constexpr int kRowTile = 32;  // rows per synthesis tile
-
-// Iterates (x, u) and per-CTA partial sums: float-float pairs for FP32
-// dictionaries, doubles for FP64 ones.
-template <typename T> struct IterT;
-template <> struct IterT<float> { using type = FF; };
-template <> struct IterT<double> { using type = double; };
-
-template <typename T>
-struct Ws {
-    using X = typename IterT<T>::type;
-    GridBarrier* bar;
-    T* theta;
-    double* b;
-    double* tv;
-    double* thr;
-    double* nvec;
-    int* act[2];
-    int* aoff[2];
-    // iterates carry about twice the dictionary's precision: in plain FP32,
-    // u - z/L would quantise z to multiples of L ulp(x), a KKT floor near 1e-6
-    X* xc[2];
-    X* uc[2];
-    X* xn;
-    X* un;
-    int* keep;
-    int* nz_col;
-    X* nz_u;
-    X* nz_x;
-    int* s_alo;
-    int* c_kg;
-    int* c_ka;
-    int* c_nz;
-    int* c_nnzx;
-    T* p_m;
-    X* p_l1;
-    X* p_a;
-    X* p_b;
-    X* p_r;
-    double* p_v;
-    int* p_i;
-    double* p_cn;
-};
-
-template <typename T>
-struct SolveP {
-    const T* D;
-    int N, K, ld, nG, is_group;
-    const int* goff;
-    const double* w;
-    const double* spec;
-    const double* colnorm;
-    double fmax, gamma, eps_test;
-    const T* y;
-    const T* x0;
-    int n_lambda;
-    const double* lambdas;  // device copy
-    int lambda_rel;
-    int alg, test, dynamic, max_iter;
-    double tol, L;
-    T* x_out;
-    long long ldx;
-    DevResult* res;
-    double* hist;
-    int hist_rows;
-    Ws<T> ws;
-    int RA, nchunk, npad;
-    double* colnorm_w;    // non-null: the kernel computes ||d_i|| here (and fmax) in its first pass
-    const double* fista;  // FISTA table: (coefficient (l_{t-1} - 1) / l_t, l_t) for t = 1..fista_n
-    int fista_n;
-};
-
-// ------------------------------------------------------------------ helpers
-
-template <typename T> __device__ __forceinline__ T soft_thr(T v, T t)
-{
-    T a = fabs(v) - t;
-    return a > T(0) ? (v > T(0) ? a : -a) : T(0);
-}
-
-__device__ __forceinline__ double dual_scale(double alpha, double beta, double lam, double m)
-{
-    // Lemma 8: [theta^T y / (lambda ||theta||^2)] projected on [-1/m, 1/m]
-    if (!(beta > 0.0)) return 0.0;
-    double s = alpha / (lam * beta);
-    if (m > 0.0) {
-        double lim = 1.0 / m;
-        s = fmin(fmax(s, -lim), lim);
-    }
-    return s;
-}
-
-// Maximum of d^T theta over {||theta - c0|| <= R} cap {n^T theta <= off} for unit d,
-// unit n, t = n^T d, dc0 = d^T c0 and psi = n^T c0 - off >= 0 (dynamic form of Lemma 4).
-__device__ __forceinline__ double dome_max(double dc0, double t, double psi, double R)
-{
-    if (t * R <= -psi) return dc0 + R;
-    double rho2 = fmax(R * R - psi * psi, 0.0);
-    double s2 = fmax(1.0 - t * t, 0.0);
-    return dc0 - psi * t + sqrt(rho2) * sqrt(s2);
-}
-
-template <typename T> __device__ __forceinline__ T round_up_to(double v);
-template <> __device__ __forceinline__ float round_up_to<float>(double v) { return __double2float_ru(v); }
-template <> __device__ __forceinline__ double round_up_to<double>(double v) { return v; }
-
-// ---- iterate arithmetic (float-float for FP32 dictionaries, FP64 otherwise)
-__device__ __forceinline__ FF ldcg_x(const FF* p)
-{
-    const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
-    return FF{v.x, v.y};
-}
-__device__ __forceinline__ double ldcg_x(const double* p) { return __ldcg(p); }
-__device__ __forceinline__ bool it_nz(FF a) { return a.h != 0.f; }
-__device__ __forceinline__ bool it_nz(double a) { return a != 0.0; }
-__device__ __forceinline__ FF it_zero(FF*) { return FF{0.f, 0.f}; }
-__device__ __forceinline__ double it_zero(double*) { return 0.0; }
-__device__ __forceinline__ FF it_from(float v, FF*) { return FF{v, 0.f}; }
-__device__ __forceinline__ double it_from(double v, double*) { return v; }
-__device__ __forceinline__ float it_round(FF a) { return a.h + a.l; }
-__device__ __forceinline__ double it_round(double a) { return a; }
-__device__ __forceinline__ double it_dbl(FF a) { return ff_to_double(a); }
-__device__ __forceinline__ double it_dbl(double a) { return a; }
-__device__ __forceinline__ FF it_cast(double a, FF*) { return ff_from_double(a); }
-__device__ __forceinline__ double it_cast(double a, double*) { return a; }
-// gradient step v = u - z * (1/L)
-__device__ __forceinline__ FF it_grad_step(FF u, float z, float invL) { return ff_sub(u, ff_prod(z, invL)); }
-__device__ __forceinline__ double it_grad_step(double u, double z, double invL) { return fma(-z, invL, u); }
-// soft threshold (eq. softTh): sign(v) max(|v| - thr, 0)
-__device__ __forceinline__ FF it_soft(FF v, FF thr)
-{
-    if (v.h > 0.f) {
-        const FF a = ff_sub(v, thr);
-        return a.h > 0.f ? a : FF{0.f, 0.f};
-    }
-    if (v.h < 0.f) {
-        const FF a = ff_add(v, thr);
-        return a.h < 0.f ? a : FF{0.f, 0.f};
-    }
-    return FF{0.f, 0.f};
-}
-__device__ __forceinline__ double it_soft(double v, double thr)
-{
-    const double a = fabs(v) - thr;
-    return a > 0.0 ? copysign(a, v) : 0.0;
-}
-// FISTA extrapolation u = x + bt (x - xo)
-__device__ __forceinline__ FF it_momentum(FF x, FF xo, FF bt) { return ff_add(x, ff_mul(ff_sub(x, xo), bt)); }
-__device__ __forceinline__ double it_momentum(double x, double xo, double bt) { return fma(bt, x - xo, x); }
-__device__ __forceinline__ FF it_scale(FF v, FF f) { return ff_mul(v, f); }
-__device__ __forceinline__ double it_scale(double v, double f) { return v * f; }
-// accumulators: |x| and x^2
-__device__ __forceinline__ void acc_abs(Dot2f& acc, FF x)
-{
-    const float sg = x.h < 0.f ? -1.f : 1.f;
-    dot2_merge(acc, sg * x.h, sg * x.l);
-}
-__device__ __forceinline__ void acc_abs(Dot2d& acc, double x) { acc.s += fabs(x); }
-__device__ __forceinline__ void acc_sq(Dot2f& acc, FF x)
-{
-    acc.add(x.h, x.h);
-    acc.c = fmaf(2.f * x.h, x.l, acc.c);
-}
-__device__ __forceinline__ void acc_sq(Dot2d& acc, double x) { acc.s = fma(x, x, acc.s); }
-__device__ __forceinline__ void acc_add_dbl(Dot2f& acc, double v)
-{
-    const FF f = ff_from_double(v);
-    dot2_merge(acc, f.h, f.l);
-}
-__device__ __forceinline__ void acc_add_dbl(Dot2d& acc, double v) { acc.s += v; }
-// synthesis term acc += d * c
-__device__ __forceinline__ void syn_add(Dot2f& acc, float d, FF c)
-{
-    acc.add(d, c.h);
-    acc.c = fmaf(d, c.l, acc.c);
-}
-__device__ __forceinline__ void syn_add(Dot2d& acc, double d, double c) { acc.add(d, c); }
-// per-CTA partials
-__device__ __forceinline__ void part_put(FF* p, const Dot2f& a) { *p = FF{a.s, a.c}; }
-__device__ __forceinline__ void part_put(double* p, const Dot2d& a) { *p = a.s; }
-__device__ __forceinline__ double part_sum_fixed(const FF* p, int n, int lane)
-{
-    Dot2f acc;
-    for (int i = lane; i < n; i += 32) {
-        const float2 v = __ldcg(reinterpret_cast<const float2*>(p + i));
-        dot2_merge(acc, v.x, v.y);
-    }
-    return dot2_warp_sum(acc);
-}
-__device__ __forceinline__ double part_sum_fixed(const double* p, int n, int lane) { return warp_sum_fixed(p, n, lane); }
-template <int Q> __device__ __forceinline__ double part_sum_regs(const FF (&v)[Q])
-{
-    Dot2f acc;
-#pragma unroll
-    for (int q = 0; q < Q; q++) dot2_merge(acc, v[q].h, v[q].l);
-    return dot2_warp_sum(acc);
-}
-template <int Q> __device__ __forceinline__ double part_sum_regs(const double (&v)[Q])
-{
-    double acc = 0.0;
-#pragma unroll
-    for (int q = 0; q < Q; q++) acc += v[q];
-    return warp_sum(acc);
-}
-__device__ __forceinline__ Dot2f acc_warp_reduce(Dot2f a) { return dot2_warp_reduce(a); }
-__device__ __forceinline__ Dot2d acc_warp_reduce(Dot2d a)
-{
-    a.s = warp_sum(a.s);
-    return a;
-}
-__device__ __forceinline__ void acc_merge_acc(Dot2f& a, const Dot2f& b) { dot2_merge(a, b.s, b.c); }
-__device__ __forceinline__ void acc_merge_acc(Dot2d& a, const Dot2d& b) { a.s += b.s; }
-// theta_r = w_u - y_r, computed from the compensated sum and rounded once
-__device__ __forceinline__ float theta_from(const Dot2f& wu, float y)
-{
-    const FF t = ff_two_sum(wu.s, -y);
-    return t.h + (t.l + wu.c);
-}
-__device__ __forceinline__ double theta_from(const Dot2d& wu, double y) { return wu.s - y; }
-// (w_x - y_r)^2 into an accumulator
-__device__ __forceinline__ void acc_resid_sq(Dot2f& acc, const Dot2f& wx, float y)
-{
-    FF t = ff_two_sum(wx.s, -y);
-    t = ff_fast_two_sum(t.h, t.l + wx.c);
-    acc_sq(acc, t);
-}
-__device__ __forceinline__ void acc_resid_sq(Dot2d& acc, const Dot2d& wx, double y)
-{
-    const double r = wx.s - y;
-    acc.s = fma(r, r, acc.s);
-}
-
-// float-float (or FP64) partial sums parked in one 8-byte shared slot
-__device__ __forceinline__ void acc_store(double* slot, const Dot2f& a)
-{
-    *reinterpret_cast<float2*>(slot) = make_float2(a.s, a.c);
-}
-__device__ __forceinline__ void acc_store(double* slot, const Dot2d& a) { *slot = a.s; }
-__device__ __forceinline__ void acc_merge(Dot2f& a, const double* slot)
-{
-    const float2 v = *reinterpret_cast<const float2*>(slot);
-    dot2_merge(a, v.x, v.y);
-}
-__device__ __forceinline__ void acc_merge(Dot2d& a, const double* slot) { a.s += *slot; }
-
-__device__ __forceinline__ float4 v4zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
-__device__ __forceinline__ double2 v4zero(double2*) { return make_double2(0.0, 0.0); }
-__device__ __forceinline__ float vdot(float4 a, float4 b, float s)
-{
-    s = fmaf(a.x, b.x, s);
-    s = fmaf(a.y, b.y, s);
-    s = fmaf(a.z, b.z, s);
-    s = fmaf(a.w, b.w, s);
-    return s;
-}
-__device__ __forceinline__ double vdot(double2 a, double2 b, double s)
-{
-    s = fma(a.x, b.x, s);
-    s = fma(a.y, b.y, s);
-    return s;
-}
-__device__ __forceinline__ void vdot2(float4 a, float hi0, float hi1, float hi2, float hi3, Dot2f& acc)
-{
-    acc.add(a.x, hi0);
-    acc.add(a.y, hi1);
-    acc.add(a.z, hi2);
-    acc.add(a.w, hi3);
-}
-
-// Column slice [p_lo, p_hi) of the active list owned by CTA b, balanced in atoms
-// and cut at group boundaries.  Returns the atom offset of p_lo.
-template <typename T>
-__device__ __forceinline__ void cta_slice(const SolveP<T>& P, const int* aoff, int nA_g, int nA_a, int b, int G,
-                                          int* p_lo, int* p_hi, int* a_lo)
-{
-    __shared__ int s_slice[3];
-    if (threadIdx.x == 0) {
-        if (!P.is_group) {
-            s_slice[0] = (int)((long long)b * nA_g / G);
-            s_slice[1] = (int)((long long)(b + 1) * nA_g / G);
-            s_slice[2] = s_slice[0];
-        } else {
-            int bounds[2];
-            for (int k = 0; k < 2; k++) {
-                long long target = (long long)(b + k) * nA_a / G;
-                int lo = 0, hi = nA_g;  // first p with aoff[p] >= target
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (__ldcg(aoff + mid) < target) lo = mid + 1;
-                    else hi = mid;
-                }
-                bounds[k] = lo;
-            }
-            s_slice[0] = bounds[0];
-            s_slice[1] = bounds[1];
-            s_slice[2] = bounds[0] < nA_g ? __ldcg(aoff + bounds[0]) : nA_a;
-        }
-    }
-    __syncthreads();
-    *p_lo = s_slice[0];
-    *p_hi = s_slice[1];
-    *a_lo = s_slice[2];
-    __syncthreads();
-}
-
-// --------------------------------------------------------------- the kernel
-
-template <typename T>
-__device__ __forceinline__ bool solve_body(const SolveP<T>& P)
-{
-    using V = typename Vec4<T>::type;
-    using X = typename IterT<T>::type;
-    using Acc = typename Dot2<T>::type;
-    constexpr int EV = 16 / sizeof(T);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* th_s = reinterpret_cast<T*>(smem_raw);
-    T* zpart = th_s + P.npad;
-    int* cols_s = reinterpret_cast<int*>(zpart + (size_t)P.RA * P.nchunk);
-
-    __shared__ int s_tmp[32];
-    __shared__ double s_dred[32];
-    __shared__ int s_ired[32];
-    __shared__ int s_pref[1025];
-    __shared__ int s_alo_s[kThreads];
-    __shared__ double s_red[2][kThreads / 32][kRowTile];
-    __shared__ double s_sc[16];
-    __shared__ int s_si[16];
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kThreads / 32;
-    const int b = blockIdx.x, G = gridDim.x;
-    const Ws<T>& W = P.ws;
-    unsigned int gen = 0;  // running barrier target, used by thread 0 only
-
-    const int N = P.N, K = P.K, ld = P.ld, nG = P.nG;
-    const int ldv = ld / EV;
-    const int total_warps = G * nw;
-    const int gwarp = b * nw + warp;
-    bool ok = true;
-
-    // ---------------------------------------------------- P0a: b = D^T y, ||y||^2
-    for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? P.y[r] : T(0);
-    __syncthreads();
-    {
-        const V* yv = reinterpret_cast<const V*>(th_s);
-        const bool norms = P.colnorm_w != nullptr;
-        double cmax = 0.0;
-        for (int i = gwarp; i < K; i += total_warps) {
-            const V* col = reinterpret_cast<const V*>(P.D + (size_t)i * ld);
-            typename Dot2<T>::type acc, nrm;
-            for (int v = lane; v < ldv; v += 32) {
-                V d = __ldg(col + v);
-                V q = yv[v];
-                if constexpr (EV == 4) {
-                    acc.add(d.x, q.x); acc.add(d.y, q.y); acc.add(d.z, q.z); acc.add(d.w, q.w);
-                    if (norms) { nrm.add(d.x, d.x); nrm.add(d.y, d.y); nrm.add(d.z, d.z); nrm.add(d.w, d.w); }
-                } else {
-                    acc.add(d.x, q.x); acc.add(d.y, q.y);
-                    if (norms) { nrm.add(d.x, d.x); nrm.add(d.y, d.y); }
-                }
-            }
-            double s = warp_sum(acc.value());
-            if (lane == 0) W.b[i] = s;
-            if (norms) {
-                const double c = sqrt(warp_sum(nrm.value()));
-                if (lane == 0) P.colnorm_w[i] = c;
-                cmax = fmax(cmax, c);
-            }
-        }
-        if (norms) {
-            cmax = warp_max(cmax);
-            if (lane == 0) s_dred[warp] = cmax;
-            __syncthreads();
-            if (tid == 0) {
-                double m = 0.0;
-                for (int k = 0; k < nw; k++) m = fmax(m, s_dred[k]);
-                W.p_cn[b] = m;
-            }
-            __syncthreads();
-        }
-        double yy = 0.0;
-        for (int r = b * kThreads + tid; r < N; r += G * kThreads) {
-            double v = (double)P.y[r];
-            yy += v * v;
-        }
-        yy = warp_sum(yy);
-        if (lane == 0) s_dred[warp] = yy;
-        __syncthreads();
-        if (tid == 0) {
-            Acc s;
-            for (int k = 0; k < nw; k++) acc_add_dbl(s, s_dred[k]);
-            part_put(W.p_a + b, s);
-        }
-    }
-    ok = grid_sync(W.bar, G, gen);
-    if (!ok) return false;
-    // column norms computed above: their maximum bounds the GEMV rounding (Lasso)
-    const double* colnorm = P.colnorm_w ? P.colnorm_w : P.colnorm;
-    double fmax_d = P.fmax;
-    if (P.colnorm_w) {
-        if (warp == 0) {
-            const double m = warp_max_fixed(W.p_cn, G, lane);
-            if (lane == 0) s_sc[11] = m * (1.0 + 1e-12);
-        }
-        __syncthreads();
-        fmax_d = s_sc[11];
-    }
-
-    // --------------------------------- P0b: lambda_* (Sec. 2.2.2 / eq. gstar)
-    {
-        double best = -1.0;
-        int arg = 0x7fffffff;
-        for (int g = b * kThreads + tid; g < nG; g += G * kThreads) {
-            double s;
-            if (!P.is_group) {
-                s = fabs(__ldcg(W.b + g));
-            } else {
-                double q = 0.0;
-                for (int i = P.goff[g]; i < P.goff[g + 1]; i++) {
-                    double v = __ldcg(W.b + i);
-                    q += v * v;
-                }
-                s = sqrt(q) / P.w[g];
-            }
-            if (s > best || (s == best && g < arg)) { best = s; arg = g; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oa = __shfl_xor_sync(0xffffffffu, arg, o);
-            if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
-        }
-        if (lane == 0) { s_dred[warp] = best; s_ired[warp] = arg; }
-        __syncthreads();
-        if (tid == 0) {
-            double bb = -1.0;
-            int ba = 0x7fffffff;
-            for (int k = 0; k < nw; k++)
-                if (s_dred[k] > bb || (s_dred[k] == bb && s_ired[k] < ba)) { bb = s_dred[k]; ba = s_ired[k]; }
-            W.p_v[b] = bb;
-            W.p_i[b] = ba;
-        }
-    }
-    ok = grid_sync(W.bar, G, gen);
-    if (!ok) return false;
-
-    {
-        // every CTA reduces the same partials in the same order
-        if (warp == 0) {
-            double bb = -1.0;
-            int ba = 0x7fffffff;
-            for (int k = lane; k < G; k += 32) {
-                double v = __ldcg(W.p_v + k);
-                int a = __ldcg(W.p_i + k);
-                if (v > bb || (v == bb && a < ba)) { bb = v; ba = a; }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                double ob = __shfl_xor_sync(0xffffffffu, bb, o);
-                int oa = __shfl_xor_sync(0xffffffffu, ba, o);
-                if (ob > bb || (ob == bb && oa < ba)) { bb = ob; ba = oa; }
-            }
-            double yy = part_sum_fixed(W.p_a, G, lane);
-            if (lane == 0) { s_sc[0] = bb; s_si[0] = ba; s_sc[1] = yy; }
-        }
-        __syncthreads();
-    }
-    const double lstar = s_sc[0];
-    const int star = s_si[0];
-    const double yy = s_sc[1];
-    if (P.n_lambda == 0) {  // lambda_max query only
-        if (b == 0 && tid == 0) { P.res[0].lambda_max = lstar; P.res[0].status = kDevOk; }
-        return true;
-    }
-
-    const bool need_n = P.test == 2 || P.test == 3 || P.test == 5;  // DST3, DOME, DGST3
-    double nn = 0.0, nty = 0.0, wstar2 = 1.0;
-    if (need_n && lstar > 0.0) {
-        // ---------------- n = D_{g*} D_{g*}^T y / lambda_*  (Lemma 6; Lasso: n = d_*)
-        const int c0 = P.is_group ? P.goff[star] : star;
-        const int c1 = P.is_group ? P.goff[star + 1] : star + 1;
-        double nq = 0.0;
-        for (int r = b * kThreads + tid; r < N; r += G * kThreads) {
-            double s = 0.0;
-            for (int i = c0; i < c1; i++) s += (double)P.D[(size_t)i * ld + r] * (__ldcg(W.b + i) / lstar);
-            W.nvec[r] = s;
-            nq += s * s;
-        }
-        nq = warp_sum(nq);
-        __syncthreads();
-        if (lane == 0) s_dred[warp] = nq;
-        __syncthreads();
-        if (tid == 0) {
-            Acc s;
-            for (int k = 0; k < nw; k++) acc_add_dbl(s, s_dred[k]);
-            part_put(W.p_r + b, s);
-        }
-        ok = grid_sync(W.bar, G, gen);
-        if (!ok) return false;
-        if (warp == 0) {
-            double s = part_sum_fixed(W.p_r, G, lane);
-            if (lane == 0) s_sc[2] = s;
-        }
-        // stage n in shared memory (hi/lo split for FP32 dictionaries)
-        if constexpr (EV == 4) {
-            float* nh = reinterpret_cast<float*>(smem_raw);
-            float* nl = nh + P.npad;
-            for (int r = tid; r < P.npad; r += kThreads) {
-                double v = r < N ? __ldcg(W.nvec + r) : 0.0;
-                float h = (float)v;
-                nh[r] = h;
-                nl[r] = (float)(v - (double)h);
-            }
-        } else {
-            for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? (T)__ldcg(W.nvec + r) : T(0);
-        }
-        __syncthreads();
-        nn = s_sc[2];
-        {
-            double q = 0.0;
-            for (int i = c0; i < c1; i++) {
-                double v = __ldcg(W.b + i);
-                q += v * v;
-            }
-            nty = q / lstar;  // n^T y = ||D_{g*}^T y||^2 / lambda_*
-        }
-        if (P.is_group) wstar2 = P.w[star] * P.w[star];
-        // ---------------- tv = D^T n (compensated)
-        for (int i = gwarp; i < K; i += total_warps) {
-            const V* col = reinterpret_cast<const V*>(P.D + (size_t)i * ld);
-            double s;
-            if constexpr (EV == 4) {
-                const float4* nh4 = reinterpret_cast<const float4*>(smem_raw);
-                const float4* nl4 = nh4 + P.npad / 4;
-                Dot2f acc;
-                float lo = 0.f;
-                for (int v = lane; v < ldv; v += 32) {
-                    float4 d = __ldg(reinterpret_cast<const float4*>(col) + v);
-                    float4 h = nh4[v], l = nl4[v];
-                    vdot2(d, h.x, h.y, h.z, h.w, acc);
-                    lo = fmaf(d.x, l.x, lo); lo = fmaf(d.y, l.y, lo); lo = fmaf(d.z, l.z, lo); lo = fmaf(d.w, l.w, lo);
-                }
-                s = warp_sum(acc.value() + (double)lo);
-            } else {
-                const V* nv = reinterpret_cast<const V*>(th_s);
-                Dot2d acc;
-                for (int v = lane; v < ldv; v += 32) {
-                    V d = __ldg(col + v);
-                    V q = nv[v];
-                    acc.add(d.x, q.x);
-                    acc.add(d.y, q.y);
-                }
-                s = warp_sum(acc.value());
-            }
-            if (lane == 0) W.tv[i] = s;
-        }
-        ok = grid_sync(W.bar, G, gen);
-        if (!ok) return false;
-    }
-
-    // ================================================================ lambdas
-    for (int j = 0; j < P.n_lambda; j++) {
-        const double lam = P.lambda_rel ? P.lambdas[j] * lstar : P.lambdas[j];
-        T* xout = P.x_out + (size_t)j * P.ldx;
-        DevResult* R = P.res + j;
-        if (!(lam < lstar)) {
-            // x = 0 and theta = y / lambda is dual optimal (Sec. 2.2.2)
-            for (int i = b * kThreads + tid; i < K; i += G * kThreads) xout[i] = T(0);
-            if (b == 0 && tid == 0) {
-                R->iters = 0; R->status = kDevOk; R->n_active = 0; R->nnz = 0;
-                R->gap = 0.0; R->primal = 0.5 * yy; R->dual = 0.5 * yy; R->lambda = lam; R->lambda_max = lstar;
-            }
-            continue;
-        }
-        const bool record = (j == 0) && P.hist != nullptr;
-        const double psi = lstar / lam - 1.0;
-        // DST3 / DGST3 centre c = y/lam - coef n, offset delta = ||y/lam - c|| (Lemmas 3, 6)
-        const double coef = need_n && nn > 0.0 ? (nty / lam - wstar2) / nn : 0.0;
-        const double delta = need_n && nn > 0.0 ? fabs(nty / lam - wstar2) / sqrt(nn) : 0.0;
-        const double nstar = P.is_group ? 1.0 : colnorm[star];
-        const double psi_dome = psi / nstar;
-        const T invL = (T)(1.0 / P.L);
-        const double thrL = lam / P.L;
-        const X thrX = it_cast(thrL, (X*)nullptr);
-        const bool ista = P.alg == 0;
-        const bool dyn_test = P.dynamic && P.test != 0;
-
-        // ------------------------------------------------ (C0) initial state
-        int cur = 0;
-        {
-            int p_lo = (int)((long long)b * nG / G), p_hi = (int)((long long)(b + 1) * nG / G);
-            if (P.is_group) {
-                // cut at group boundaries, balanced in atoms
-                int bounds[2];
-                for (int k = 0; k < 2; k++) {
-                    long long target = (long long)(b + k) * K / G;
-                    int lo = 0, hi = nG;
-                    while (lo < hi) {
-                        int mid = (lo + hi) >> 1;
-                        if (P.goff[mid] < target) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    bounds[k] = lo;
-                }
-                p_lo = bounds[0];
-                p_hi = bounds[1];
-            }
-            const int a_lo = P.is_group ? (p_lo < nG ? P.goff[p_lo] : K) : p_lo;
-            // static screening (Algorithm 1): the test at theta = -y, m = lambda_*
-            double rad0 = 0.0;
-            const bool stat = !P.dynamic && P.test != 0;
-            if (stat) {
-                double mup = lstar * (1.0 + 1e-12);
-                double mu = dual_scale(-yy, yy, lam, mup);
-                double R2 = yy / (lam * lam) + 2.0 * mu * yy / lam + mu * mu * yy;
-                R2 = fmax(R2, 0.0);
-                rad0 = (P.test == 2 || P.test == 5) ? sqrt(fmax(R2 - delta * delta, 0.0)) : sqrt(R2);
-            }
-            int nz_base = 0, kg = 0, ka = 0;
-            for (int base = p_lo; base < p_hi; base += kThreads) {
-                int p = base + tid;
-                bool valid = p < p_hi;
-                int kept = 0, cnt = 0;
-                int lo_a = 0, hi_a = 0;
-                if (valid) {
-                    lo_a = P.is_group ? P.goff[p] : p;
-                    hi_a = P.is_group ? P.goff[p + 1] : p + 1;
-                    W.act[cur][p] = p;
-                    if (P.is_group) W.aoff[cur][p] = lo_a;
-                    // threshold of the sphere tests: (w_g - ||(D^T c)_g||) / ||D_g||  (Lemma 7)
-                    double th = 0.0;
-                    if (P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5) {
-                        double q = 0.0;
-                        for (int i = lo_a; i < hi_a; i++) {
-                            double dtc = __ldcg(W.b + i) / lam - ((P.test == 2 || P.test == 5) ? coef * __ldcg(W.tv + i) : 0.0);
-                            q += dtc * dtc;
-                        }
-                        double wg = P.is_group ? P.w[p] : 1.0;
-                        double sg = P.is_group ? P.spec[p] : colnorm[p];
-                        th = (wg - sqrt(q)) / sg;
-                        W.thr[p] = th;
-                    }
-                    bool kill = false;
-                    if (stat) {
-                        if (P.test == 3) {
-                            double ni = colnorm[p];
-                            double dc0 = __ldcg(W.b + p) / (lam * ni);
-                            double tt = __ldcg(W.tv + p) / (ni * nstar);
-                            double up = dome_max(dc0, tt, psi_dome, rad0);
-                            double dn = dome_max(-dc0, -tt, psi_dome, rad0);
-                            kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
-                        } else {
-                            kill = th - rad0 > P.eps_test;
-                        }
-                    }
-                    kept = !kill;
-                    W.keep[p] = kept;
-                    for (int i = lo_a; i < hi_a; i++) {
-                        X xv = (P.x0 && kept) ? it_from(P.x0[i], (X*)nullptr) : it_zero((X*)nullptr);
-                        W.xn[i] = xv;
-                        W.un[i] = xv;
-                        cnt += it_nz(xv);
-                    }
-                    kg += kept;
-                    ka += kept ? hi_a - lo_a : 0;
-                }
-                int tot;
-                int pos = block_exclusive_scan(cnt, s_tmp, &tot);
-                if (valid && cnt) {
-                    int e = a_lo + nz_base + pos;
-                    for (int i = lo_a; i < hi_a; i++) {
-                        const X xv = W.xn[i];
-                        if (it_nz(xv)) {
-                            W.nz_col[e] = i;
-                            W.nz_u[e] = xv;
-                            W.nz_x[e] = xv;
-                            e++;
-                        }
-                    }
-                }
-                nz_base += tot;
-            }
-            int tkg, tka, dummy;
-            block_exclusive_scan(kg, s_tmp, &tkg);
-            block_exclusive_scan(ka, s_tmp, &tka);
-            (void)dummy;
-            if (tid == 0) {
-                W.s_alo[b] = a_lo;
-                W.c_kg[b] = tkg;
-                W.c_ka[b] = tka;
-                W.c_nz[b] = nz_base;
-                W.c_nnzx[b] = nz_base;
-                Acc z0;
-                part_put(W.p_l1 + b, z0);
-            }
-            if (b == G - 1 && tid == 0 && P.is_group) W.aoff[cur][nG] = K;
-        }
-        ok = grid_sync(W.bar, G, gen);
-        if (!ok) return false;
-
-        int nA_g = nG, nA_a = K;  // sizes of the list `cur` refers to
-        // scalar state, meaningful in thread 0 (the values every thread needs go through s_sc)
-        double alpha = 0.0, beta = 0.0, mu_nom = 0.0, R2n = 0.0, rad = 0.0, lf = 1.0;
-        double s_unc = 0.0, sqrt_beta = 0.0;
-        const double inv_lam = 1.0 / lam, yy_l2 = yy * inv_lam * inv_lam;
-        double gap = INFINITY, primal = 0.0;
-        int t = 1;
-        int iters = 0;
-        long long nnz_last = 0;
-        // work counters (dictionary columns read), the precompute passes charged to the first lambda
-        long long cols_corr = j == 0 ? (long long)K * (need_n ? 2 : 1) : 0, cols_synth = 0;
-        for (;; t++) {
-            // ======================================== (A) scatter + synthesis
-            {
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                const int nxt = cur ^ 1;
-                // directory of the per-CTA nonzero lists (exclusive prefix of their lengths)
-                const int cnz = tid < G ? __ldcg(W.c_nz + tid) : 0;
-                if (tid < G) s_alo_s[tid] = __ldcg(W.s_alo + tid);
-                int totE;
-                const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
-                if (tid < G) s_pref[tid] = exE;
-                if (tid == 0) s_pref[G] = totE;
-                if (warp == 0) {
-                    int gv[kMaxG / 32], av[kMaxG / 32];
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) {
-                        const int k = lane + 32 * q;
-                        gv[q] = k < b ? __ldcg(W.c_kg + k) : 0;
-                        av[q] = k < b ? __ldcg(W.c_ka + k) : 0;
-                    }
-                    int g0 = 0, a0 = 0;
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) { g0 += gv[q]; a0 += av[q]; }
-                    g0 = warp_sum(g0);
-                    a0 = warp_sum(a0);
-                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; }
-                }
-                __syncthreads();
-                // compaction (Algorithm 3: D_t = D_{t-1} Id, Xbar_t = Id X_t): kept groups move to
-                // their new positions; groups and atoms are counted in one packed scan
-                int gb = s_si[1], ab = s_si[2];
-                for (int base = p_lo; base < p_hi; base += kThreads) {
-                    const int p = base + tid;
-                    const bool valid = p < p_hi;
-                    int k = 0, lo_a = 0, sz = 0;
-                    if (valid) {
-                        k = __ldcg(W.keep + p);
-                        lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                        sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
-                    }
-                    int tot;
-                    const int pre = block_exclusive_scan(k ? ((1 << 16) | sz) : 0, s_tmp, &tot);
-                    if (k) {
-                        const int ng = gb + (pre >> 16), na = ab + (pre & 0xffff);
-                        W.act[nxt][ng] = __ldcg(W.act[cur] + p);
-                        if (P.is_group) W.aoff[nxt][ng] = na;
-                        for (int q = 0; q < sz; q++) {
-                            W.xc[nxt][na + q] = ldcg_x(W.xn + lo_a + q);
-                            W.uc[nxt][na + q] = ldcg_x(W.un + lo_a + q);
-                        }
-                    }
-                    gb += tot >> 16;
-                    ab += tot & 0xffff;
-                }
-                if (b == G - 1 && tid == 0 && P.is_group) W.aoff[nxt][gb] = ab;
-
-                // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists
-                const int E = s_pref[G];
-                cols_synth += E;
-                Acc pa_, pb_, pr_;
-                const int ntiles = (N + kRowTile - 1) / kRowTile;
-                for (int tile = b; tile < ntiles; tile += G) {
-                    const int r = tile * kRowTile + lane;
-                    const bool rv = r < N;
-                    // compensated accumulation: theta = D u - y is a small difference of two
-                    // large vectors, so the sum is carried to twice the working precision
-                    typename Dot2<T>::type au, ax;
-                    for (int e0 = warp; e0 < E; e0 += nw * 4) {
-                        int cols[4];
-                        X uv[4], xv[4];
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const int e = e0 + q * nw;
-                            cols[q] = -1;
-                            uv[q] = it_zero((X*)nullptr);
-                            xv[q] = it_zero((X*)nullptr);
-                            if (e < E) {
-                                int lo = 0, hi = G;  // largest k with s_pref[k] <= e
-                                while (hi - lo > 1) {
-                                    const int mid = (lo + hi) >> 1;
-                                    if (s_pref[mid] <= e) lo = mid;
-                                    else hi = mid;
-                                }
-                                const int idx = s_alo_s[lo] + (e - s_pref[lo]);
-                                cols[q] = __ldcg(W.nz_col + idx);
-                                uv[q] = ldcg_x(W.nz_u + idx);
-                                xv[q] = ldcg_x(W.nz_x + idx);
-                            }
-                        }
-                        T dv[4];
-#pragma unroll
-                        for (int q = 0; q < 4; q++) dv[q] = (cols[q] >= 0 && rv) ? __ldg(P.D + (size_t)cols[q] * ld + r) : T(0);
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            syn_add(au, dv[q], uv[q]);
-                            syn_add(ax, dv[q], xv[q]);
-                        }
-                    }
-                    acc_store(&s_red[0][warp][lane], au);
-                    acc_store(&s_red[1][warp][lane], ax);
-                    __syncthreads();
-                    if (warp == 0) {
-                        typename Dot2<T>::type wu, wx;
-                        for (int k = 0; k < nw; k++) {
-                            acc_merge(wu, &s_red[0][k][lane]);
-                            acc_merge(wx, &s_red[1][k][lane]);
-                        }
-                        if (rv) {
-                            const T yv = P.y[r];
-                            const T th = (T)theta_from(wu, yv);
-                            W.theta[r] = th;
-                            pa_.add(th, yv);
-                            pb_.add(th, th);
-                            acc_resid_sq(pr_, wx, yv);
-                        }
-                    }
-                    __syncthreads();
-                }
-                if (warp == 0) {
-                    pa_ = acc_warp_reduce(pa_);
-                    pb_ = acc_warp_reduce(pb_);
-                    pr_ = acc_warp_reduce(pr_);
-                    if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
-                }
-                cur = nxt;
-            }
-            ok = grid_sync(W.bar, G, gen);
-            if (!ok) return false;
-
-            // ================================ (B) stop test, correlation + prox
-            {
-                // warp 0 reduces the partials in a fixed order; lane 0 evaluates the gap of
-                // iteration t-1 and the stopping rule
-                if (warp == 0) {
-                    // every load of the per-CTA partials is issued before any is combined
-                    X va[kMaxG / 32], vb[kMaxG / 32], vr[kMaxG / 32], vl[kMaxG / 32];
-                    int ig[kMaxG / 32], ia[kMaxG / 32], ix[kMaxG / 32];
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) {
-                        const int k = lane + 32 * q;
-                        const bool in = k < G;
-                        va[q] = in ? ldcg_x(W.p_a + k) : it_zero((X*)nullptr);
-                        vb[q] = in ? ldcg_x(W.p_b + k) : it_zero((X*)nullptr);
-                        vr[q] = in ? ldcg_x(W.p_r + k) : it_zero((X*)nullptr);
-                        vl[q] = in ? ldcg_x(W.p_l1 + k) : it_zero((X*)nullptr);
-                        ig[q] = in ? __ldcg(W.c_kg + k) : 0;
-                        ia[q] = in ? __ldcg(W.c_ka + k) : 0;
-                        ix[q] = in ? __ldcg(W.c_nnzx + k) : 0;
-                    }
-                    const double a_ = part_sum_regs<kMaxG / 32>(va);
-                    const double b_ = part_sum_regs<kMaxG / 32>(vb);
-                    const double r_ = part_sum_regs<kMaxG / 32>(vr);
-                    const double l1 = part_sum_regs<kMaxG / 32>(vl);
-                    int ng = 0, na = 0, nx = 0;
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) { ng += ig[q]; na += ia[q]; nx += ix[q]; }
-                    ng = warp_sum(ng);
-                    na = warp_sum(na);
-                    nx = warp_sum(nx);
-                    if (lane == 0) {
-                        int stop = 0;
-                        if (t > 1) {
-                            // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                            primal = 0.5 * r_ + lam * l1;
-                            gap = primal - 0.5 * yy + 0.5 * lam * lam * R2n;
-                            iters = t - 1;
-                            if (record && b == 0 && t - 1 <= P.hist_rows) {
-                                double* h = P.hist + (size_t)(t - 2) * 6;
-                                h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
-                            }
-                            stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
-                        }
-                        alpha = a_;
-                        beta = b_;
-                        // the parts of Lemma 8 that do not need max |z|, off the critical path of (C)
-                        s_unc = beta > 0.0 ? alpha * inv_lam * fast_rcp(beta) : 0.0;
-                        // an upper bound of ||theta|| is all the rounding bound of (C) needs
-                        sqrt_beta = (double)sqrtf((float)beta) * (1.0 + 1e-6);
-                        double bt = 0.0;
-                        if (!ista) {
-                            // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
-                            // read from the table (the sequence depends on t only)
-                            if (t <= P.fista_n) {
-                                bt = P.fista[2 * (t - 1)];
-                                lf = P.fista[2 * (t - 1) + 1];
-                            } else {
-                                const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
-                                bt = (lf - 1.0) / ln;
-                                lf = ln;
-                            }
-                        }
-                        s_sc[10] = bt;
-                        s_si[3] = (int)ng; s_si[4] = (int)na; s_si[5] = (int)nx; s_si[6] = stop;
-                    }
-                }
-                __syncthreads();
-                nA_g = s_si[3];
-                nA_a = s_si[4];
-                nnz_last = s_si[5];
-                if (s_si[6]) break;
-                cols_corr += nA_a;
-
-                // stage theta_t
-                for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? __ldcg(W.theta + r) : T(0);
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                T mloc = T(0);
-                const V* thv = reinterpret_cast<const V*>(th_s);
-                int p = p_lo;
-                while (p < p_hi) {
-                    // gather a round of whole groups, at most RA atoms
-                    int p_end = p, natoms = 0;
-                    if (!P.is_group) {
-                        p_end = min(p_hi, p + P.RA);
-                        natoms = p_end - p;
-                    } else {
-                        if (tid == 0) {
-                            while (p_end < p_hi) {
-                                const int g = __ldcg(W.act[cur] + p_end);
-                                const int sz = P.goff[g + 1] - P.goff[g];
-                                if (natoms + sz > P.RA) break;
-                                natoms += sz;
-                                p_end++;
-                            }
-                            s_si[7] = p_end;
-                            s_si[8] = natoms;
-                        }
-                        __syncthreads();
-                        p_end = s_si[7];
-                        natoms = s_si[8];
-                    }
-                    const int abase = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                    if (!P.is_group) {
-                        for (int a = tid; a < natoms; a += kThreads) cols_s[a] = __ldcg(W.act[cur] + p + a);
-                    } else {
-                        for (int q = p + tid; q < p_end; q += kThreads) {
-                            const int g = __ldcg(W.act[cur] + q);
-                            const int off = __ldcg(W.aoff[cur] + q) - abase;
-                            for (int i = P.goff[g]; i < P.goff[g + 1]; i++) cols_s[off + i - P.goff[g]] = i;
-                        }
-                    }
-                    __syncthreads();
-                    // z = D_A^T theta: items (atom, row chunk), two per warp in flight
-                    const int nchunk = P.nchunk;
-                    const int nitems = natoms * nchunk;
-                    for (int j0 = warp * 2; j0 < nitems; j0 += nw * 2) {
-                        const int j1 = j0 + 1;
-                        const bool h1 = j1 < nitems;
-                        const int a0 = j0 / nchunk, c0 = j0 - a0 * nchunk;
-                        const int a1 = h1 ? j1 / nchunk : a0, c1 = h1 ? j1 - a1 * nchunk : c0;
-                        const V* col0 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a0] * ld);
-                        const V* col1 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a1] * ld);
-                        V d0[kU], d1[kU];
-#pragma unroll
-                        for (int k = 0; k < kU; k++) {
-                            const int v0 = c0 * (32 * kU) + k * 32 + lane;
-                            const int v1 = c1 * (32 * kU) + k * 32 + lane;
-                            d0[k] = v0 < ldv ? __ldg(col0 + v0) : v4zero((V*)nullptr);
-                            d1[k] = (h1 && v1 < ldv) ? __ldg(col1 + v1) : v4zero((V*)nullptr);
-                        }
-                        T s0 = T(0), s1 = T(0);
-#pragma unroll
-                        for (int k = 0; k < kU; k++) {
-                            s0 = vdot(d0[k], thv[c0 * (32 * kU) + k * 32 + lane], s0);
-                            s1 = vdot(d1[k], thv[c1 * (32 * kU) + k * 32 + lane], s1);
-                        }
-                        s0 = warp_sum(s0);
-                        s1 = warp_sum(s1);
-                        if (lane == 0) {
-                            zpart[a0 * nchunk + c0] = s0;
-                            if (h1) zpart[a1 * nchunk + c1] = s1;
-                        }
-                    }
-                    __syncthreads();
-                    // proximal step (Table 1): x = prox_{lambda/L Omega}(u - z / L)
-                    for (int a = tid; a < natoms; a += kThreads) {
-                        T z = T(0);
-                        for (int c = 0; c < nchunk; c++) z += zpart[a * nchunk + c];
-                        if (!P.is_group) {
-                            const int ap = abase + a;
-                            W.xn[ap] = it_soft(it_grad_step(ldcg_x(W.uc[cur] + ap), z, invL), thrX);
-                            mloc = fmax(mloc, fabs(z));
-                        } else {
-                            zpart[a * nchunk] = z;
-                        }
-                    }
-                    if (P.is_group) {
-                        __syncthreads();
-                        for (int q = p + tid; q < p_end; q += kThreads) {
-                            const int g = __ldcg(W.act[cur] + q);
-                            const int off = __ldcg(W.aoff[cur] + q);
-                            const int sz = P.goff[g + 1] - P.goff[g];
-                            Acc zq, vq;
-                            for (int i = 0; i < sz; i++) {
-                                const T z = zpart[(off - abase + i) * nchunk];
-                                const X v = it_grad_step(ldcg_x(W.uc[cur] + off + i), z, invL);
-                                zq.add(z, z);
-                                acc_sq(vq, v);
-                            }
-                            const double wg = P.w[g];
-                            const double nv = sqrt(vq.value());
-                            // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
-                            const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0, (X*)nullptr);
-                            for (int i = 0; i < sz; i++) {
-                                const T z = zpart[(off - abase + i) * nchunk];
-                                W.xn[off + i] = it_scale(it_grad_step(ldcg_x(W.uc[cur] + off + i), z, invL), f);
-                            }
-                            // rounded up so that the FP32 max stays an upper bound of the FP64 value
-                            mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
-                        }
-                    }
-                    __syncthreads();
-                    p = p_end;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-                if (lane == 0) s_dred[warp] = (double)mloc;
-                __syncthreads();
-                if (tid == 0) {
-                    T m = T(0);
-                    for (int k = 0; k < nw; k++) m = fmax(m, (T)s_dred[k]);
-                    W.p_m[b] = m;
-                }
-            }
-            ok = grid_sync(W.bar, G, gen);
-            if (!ok) return false;
-
-            // ===================================== (C) screening + momentum
-            {
-                if (warp == 0) {
-                    T mv[kMaxG / 32];
-#pragma unroll
-                    for (int j = 0; j < kMaxG / 32; j++) mv[j] = lane + 32 * j < G ? __ldcg(W.p_m + lane + 32 * j) : T(0);
-                    T mf = T(0);
-#pragma unroll
-                    for (int j = 0; j < kMaxG / 32; j++) mf = fmax(mf, mv[j]);
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-                    const double m_nom = (double)mf;
-                    if (lane == 0) {
-                        // Lemma 8 with the nominal max |z| (for the gap) and with a rigorous upper
-                        // bound on it given the FP rounding of z (for the screening radius)
-                        const double m_up = m_nom + P.gamma * sqrt_beta * fmax_d;
-                        mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
-                        const double mu_s = (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) ? copysign(fast_rcp(m_up), s_unc) : s_unc;
-                        // R^2 = ||y/lambda - mu theta||^2
-                        R2n = fmax(fma(mu_nom, fma(mu_nom, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
-                        const double R2s = fmax(fma(mu_s, fma(mu_s, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
-                        // radii rounded up a little: a larger radius only screens less
-                        const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
-                        rad = (P.test == 2 || P.test == 5) ? fast_sqrt(fmax(R2s - delta * delta, 0.0)) * (1.0 + 1e-13) : Rs;
-                        s_sc[8] = rad;
-                        s_sc[9] = Rs;
-                    }
-                }
-                __syncthreads();
-                const double radB = s_sc[8], RsB = s_sc[9];
-                const X btX = it_cast(s_sc[10], (X*)nullptr);
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                int nz_base = 0, kg = 0, ka = 0, nzx = 0;
-                Acc l1;
-                for (int base = p_lo; base < p_hi; base += kThreads) {
-                    const int p = base + tid;
-                    const bool valid = p < p_hi;
-                    int cnt = 0, lo_a = 0, sz = 0, gid = 0;
-                    X x1 = it_zero((X*)nullptr), u1 = it_zero((X*)nullptr);  // Lasso: the atom's values
-                    if (valid) {
-                        gid = __ldcg(W.act[cur] + p);
-                        lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                        sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
-                        bool kill = false;
-                        if (dyn_test) {
-                            if (P.test == 3) {
-                                // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
-                                const double ni = colnorm[gid];
-                                const double dc0 = __ldcg(W.b + gid) / (lam * ni);
-                                const double tt = __ldcg(W.tv + gid) / (ni * nstar);
-                                const double up = dome_max(dc0, tt, psi_dome, RsB);
-                                const double dn = dome_max(-dc0, -tt, psi_dome, RsB);
-                                kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
-                            } else {
-                                kill = __ldcg(W.thr + gid) - radB > P.eps_test;
-                            }
-                        }
-                        W.keep[p] = !kill;
-                        if (!kill) {
-                            Acc gq;
-                            for (int q = 0; q < sz; q++) {
-                                const X xv = ldcg_x(W.xn + lo_a + q);
-                                const X xo = ldcg_x(W.xc[cur] + lo_a + q);
-                                const X uv = ista ? xv : it_momentum(xv, xo, btX);
-                                W.un[lo_a + q] = uv;
-                                x1 = xv;
-                                u1 = uv;
-                                cnt += (it_nz(uv) || it_nz(xv));
-                                nzx += it_nz(xv);
-                                if (P.is_group) acc_sq(gq, xv);
-                                else acc_abs(l1, xv);
-                            }
-                            if (P.is_group) acc_add_dbl(l1, P.w[gid] * sqrt(gq.value()));
-                            kg += 1;
-                            ka += sz;
-                        }
-                    }
-                    int tot;
-                    const int pos = block_exclusive_scan(cnt, s_tmp, &tot);
-                    if (cnt && !P.is_group) {
-                        const int e = a_lo + nz_base + pos;
-                        W.nz_col[e] = gid;
-                        W.nz_u[e] = u1;
-                        W.nz_x[e] = x1;
-                    } else if (cnt) {
-                        int e = a_lo + nz_base + pos;
-                        for (int q = 0; q < sz; q++) {
-                            const X xv = ldcg_x(W.xn + lo_a + q);
-                            const X uv = ldcg_x(W.un + lo_a + q);
-                            if (it_nz(uv) || it_nz(xv)) {
-                                W.nz_col[e] = P.is_group ? P.goff[gid] + q : gid;
-                                W.nz_u[e] = uv;
-                                W.nz_x[e] = xv;
-                                e++;
-                            }
-                        }
-                    }
-                    nz_base += tot;
-                }
-                // per-CTA totals: one warp-level reduction and a single block barrier
-                const int rkg = warp_sum(kg), rka = warp_sum(ka), rnx = warp_sum(nzx);
-                const Acc rl1 = acc_warp_reduce(l1);
-                if (lane == 0) { s_ired[warp] = rkg; s_tmp[warp] = rka; s_pref[warp] = rnx; acc_store(&s_red[0][warp][0], rl1); }
-                __syncthreads();
-                if (tid == 0) {
-                    int tkg = 0, tka = 0, tnx = 0;
-                    Acc tl1;
-                    for (int k = 0; k < nw; k++) {
-                        tkg += s_ired[k];
-                        tka += s_tmp[k];
-                        tnx += s_pref[k];
-                        acc_merge(tl1, &s_red[0][k][0]);
-                    }
-                    part_put(W.p_l1 + b, tl1);
-                    W.s_alo[b] = a_lo;
-                    W.c_kg[b] = tkg;
-                    W.c_ka[b] = tka;
-                    W.c_nz[b] = nz_base;
-                    W.c_nnzx[b] = tnx;
-                }
-            }
-            ok = grid_sync(W.bar, G, gen);
-            if (!ok) return false;
-        }
-
-        // ------------------------------------------------------------ output
-        for (int i = b * kThreads + tid; i < K; i += G * kThreads) xout[i] = T(0);
-        ok = grid_sync(W.bar, G, gen);
-        if (!ok) return false;
-        {
-            int p_lo, p_hi, a_lo;
-            cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-            for (int p = p_lo + tid; p < p_hi; p += kThreads) {
-                int gid = __ldcg(W.act[cur] + p);
-                int lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                int c0 = P.is_group ? P.goff[gid] : gid;
-                int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
-                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(W.xc[cur] + lo_a + q));
-            }
-            if (b == 0 && tid == 0) {
-                R->iters = iters;
-                R->status = (P.tol > 0.0 && !(gap <= P.tol * 0.5 * yy)) ? kDevNotConverged : kDevOk;
-                R->n_active = nA_a;
-                R->nnz = nnz_last;
-                R->gap = gap;
-                R->primal = primal;
-                R->dual = primal - gap;
-                R->lambda = lam;
-                R->lambda_max = lstar;
-                R->cols_corr = cols_corr;
-                R->cols_synth = cols_synth;
-            }
-        }
-        ok = grid_sync(W.bar, G, gen);
-        if (!ok) return false;
-    }
-    return true;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(const SolveP<T> P)
 {
-    if (!solve_body<T>(P) && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned int gen = 0;  // running barrier target, used by thread 0 only
+    if (!solve_body<T>(P, blockIdx.x, gridDim.x, P.ws.bar, gen) && blockIdx.x == 0 && threadIdx.x == 0) {
         const int n = P.n_lambda > 0 ? P.n_lambda : 1;
         for (int j = 0; j < n; j++) P.res[j].status = kDevTimeout;
     }
@@ -1244,78 +40,6 @@ __global__ void __launch_bounds__(kThreads, 1) solve_kernel(const SolveP<T> P)
 
 // ------------------------------------------------------------ host launcher
 
-namespace {
-
-struct Geometry {
-    int nchunk, npad, RA, G;
-    size_t smem;
-};
-
-template <typename T>
-ds_status geometry(const DictDesc& dd, int num_sms, size_t smem_optin, Geometry* g)
-{
-    constexpr int EV = 16 / sizeof(T);
-    const int chunk = 32 * EV * kU;
-    g->nchunk = (dd.N + chunk - 1) / chunk;
-    g->npad = g->nchunk * chunk;
-    g->G = std::min(num_sms, kMaxG);  // one CTA per SM, within the fixed-size reductions
-    // shared memory: theta + zpart + cols, and room for n (hi/lo) in the precompute
-    const size_t fixed = g->npad * sizeof(T);
-    const size_t budget = smem_optin > 48 * 1024 ? smem_optin - 40 * 1024 : 48 * 1024;
-    if (fixed + 64 * (g->nchunk * sizeof(T) + 4) > budget) return DS_ERR_UNSUPPORTED;
-    g->RA = (int)std::min<size_t>(512, (budget - fixed) / (g->nchunk * sizeof(T) + 4));
-    if (dd.is_group && g->RA < dd.max_gsize) return DS_ERR_UNSUPPORTED;
-    g->smem = std::max(fixed + (size_t)g->RA * (g->nchunk * sizeof(T) + 4), (size_t)g->npad * 8);
-    if (g->smem > budget) return DS_ERR_UNSUPPORTED;
-    return DS_OK;
-}
-
-// Carves the solve workspace out of `base` (nullptr: only measures it).
-template <typename T>
-size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_lambda, Ws<T>* w, double** lam_dev,
-              DevResult** res_dev, double** colnorm_w)
-{
-    using X = typename IterT<T>::type;
-    const int N = dd.N, K = dd.K, nG = dd.nG, G = g.G;
-    Bump bp{base, 0};
-    w->bar = bp.take<GridBarrier>(1);
-    w->theta = bp.take<T>(g.npad);
-    w->b = bp.take<double>(K);
-    w->tv = bp.take<double>(K);
-    w->thr = bp.take<double>(nG);
-    w->nvec = bp.take<double>(N);
-    for (int k = 0; k < 2; k++) {
-        w->act[k] = bp.take<int>(nG);
-        w->aoff[k] = bp.take<int>(nG + 1);
-        w->xc[k] = bp.take<X>(K);
-        w->uc[k] = bp.take<X>(K);
-    }
-    w->xn = bp.take<X>(K);
-    w->un = bp.take<X>(K);
-    w->keep = bp.take<int>(nG);
-    w->nz_col = bp.take<int>(K);
-    w->nz_u = bp.take<X>(K);
-    w->nz_x = bp.take<X>(K);
-    w->s_alo = bp.take<int>(G);
-    w->c_kg = bp.take<int>(G);
-    w->c_ka = bp.take<int>(G);
-    w->c_nz = bp.take<int>(G);
-    w->c_nnzx = bp.take<int>(G);
-    w->p_m = bp.take<T>(G);
-    w->p_l1 = bp.take<X>(G);
-    w->p_a = bp.take<X>(G);
-    w->p_b = bp.take<X>(G);
-    w->p_r = bp.take<X>(G);
-    w->p_v = bp.take<double>(G);
-    w->p_i = bp.take<int>(G);
-    w->p_cn = bp.take<double>(G);
-    *lam_dev = bp.take<double>(std::max(n_lambda, 1));
-    *res_dev = bp.take<DevResult>(std::max(n_lambda, 1));
-    *colnorm_w = dd.norms_in_kernel ? bp.take<double>(K) : nullptr;
-    return bp.off + 256;
-}
-
-}  // namespace
 
 template <typename T>
 size_t solve_ws_bytes_t(const DictDesc& dd, int num_sms, size_t smem_optin, int n_lambda)
@@ -1360,41 +84,20 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
     layout<T>(base, dd, g, n_lambda, &w, &lam_dev, &res_dev, &colnorm_w);
 
     SolveP<T> P;
+    fill_params<T>(P, dd, g, opt);
     P.fista = env.fista;
     P.fista_n = env.fista_n;
-    P.D = reinterpret_cast<const T*>(dd.D);
-    P.N = dd.N; P.K = dd.K; P.ld = dd.ld; P.nG = dd.nG; P.is_group = dd.is_group;
-    P.goff = dd.goff; P.w = dd.w; P.spec = dd.spec; P.colnorm = dd.colnorm;
-    P.fmax = dd.fmax;
     P.colnorm_w = colnorm_w;
-    {
-        // worst-case rounding of the FP GEMV: each product goes through at most
-        // kU*EV FMAs in a lane, 5 shuffle additions and nchunk chunk additions
-        const double u = sizeof(T) == 4 ? std::ldexp(1.0, -24) : std::ldexp(1.0, -53);
-        const double k = kU * EV + 5 + g.nchunk;
-        P.gamma = 1.01 * k * u / (1.0 - k * u);
-    }
-    P.eps_test = sizeof(T) == 4 ? 1e-9 : 1e-11;
     P.y = reinterpret_cast<const T*>(y_dev);
     P.x0 = reinterpret_cast<const T*>(x0_dev);
     P.n_lambda = n_lambda;
     P.lambdas = lam_dev;
-    P.lambda_rel = opt ? opt->lambda_rel : 0;
-    P.alg = opt ? opt->alg : 1;
-    P.test = opt ? opt->test : 0;
-    P.dynamic = opt ? opt->dynamic : 1;
-    P.max_iter = opt ? opt->max_iter : 1;
-    P.tol = opt ? opt->tol_gap_rel : 0.0;
-    P.L = (opt && opt->L > 0) ? opt->L : dd.L;
     P.x_out = reinterpret_cast<T*>(xout_dev);
     P.ldx = ldx;
     P.res = res_dev;
     P.hist = env.hist;
     P.hist_rows = env.hist_rows;
     P.ws = w;
-    P.RA = g.RA;
-    P.nchunk = g.nchunk;
-    P.npad = g.npad;
 
     cudaStream_t s = env.stream;
     if (n_lambda > 0 &&
