@@ -46,7 +46,8 @@ typedef enum {
     DS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
     DS_ERR_TIMEOUT = 4,       /* a bounded device-side wait (grid barrier) gave up */
     DS_ERR_NOT_CONVERGED = 5, /* (ds_result.status only) max_iter reached above the gap tolerance */
-    DS_ERR_UNSUPPORTED = 6    /* valid request outside what this build handles (e.g. N too large) */
+    DS_ERR_UNSUPPORTED = 6,   /* valid request outside what this build handles (e.g. N too large) */
+    DS_PENDING = 7            /* (ds_server_poll only) the request has not completed yet */
 } ds_status;
 
 typedef enum { DS_ISTA = 0, DS_FISTA = 1 } ds_alg; /* Table 1 rows */
@@ -180,6 +181,35 @@ ds_status ds_batch_destroy(ds_batch* batch);
 /* One-shot form: create, run once, destroy. */
 ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
                          const double* const* lambdas, const ds_options* opt, void* const* X_out, ds_result* res);
+
+/* ----------------------------------------------------------------- serving
+ * A continuous-batching server: requests (one y and one lambda on a registered
+ * FP32 dictionary, Lasso or Group-Lasso) are admitted while others run.  A
+ * persistent kernel splits the GPU into teams of team_size CTAs (0 = 4); each
+ * team takes the next admitted request, keeps its iterate, residual and
+ * shrinking active set on the device, and retires it when the duality gap is
+ * met, then takes another.  A request is admitted when a ring slot is free and
+ * its workspace (sized for its N and K) fits in the hbm_budget_bytes pool
+ * (admission by HBM footprint); otherwise it waits in a host queue.  When no
+ * work arrives for a while the kernel exits and the next submission relaunches
+ * it.  Requests of any N <= max_N, K <= max_K mix freely.
+ *   ds_server_submit: y (host, N floats) is copied during the call; x_out (host,
+ *     K floats) must stay valid until ds_server_poll returns DS_OK for the
+ *     ticket.  Returns a ticket.  DS_ERR_UNSUPPORTED beyond max_N / max_K or
+ *     for an FP64 dictionary.
+ *   ds_server_poll: DS_PENDING while the request runs; DS_OK fills res
+ *     (res->ms = latency from submission to completion) and forgets the ticket.
+ *   ds_server_stats: completed, in flight, waiting, kernel launches, pool bytes.
+ * A server drives its own CUDA stream; calls are serialised internally. */
+typedef struct ds_server ds_server;
+ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, int64_t max_K, int team_size,
+                           ds_server** out);
+ds_status ds_server_submit(ds_server* server, const ds_dict* dict, const void* y, double lambda, const ds_options* opt,
+                           void* x_out, uint64_t* ticket);
+ds_status ds_server_poll(ds_server* server, uint64_t ticket, ds_result* res);
+ds_status ds_server_stats(ds_server* server, int64_t* completed, int64_t* in_flight, int64_t* pending,
+                          int64_t* launches, size_t* pool_in_use);
+ds_status ds_server_destroy(ds_server* server);
 
 /* Allocation-free Lasso solve.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- a framework whose

@@ -24,7 +24,8 @@ _lib = None
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "dscreen.h")
 
-DS_OK, DS_ERR_INVALID, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_NOT_CONVERGED, DS_ERR_UNSUPPORTED = range(7)
+(DS_OK, DS_ERR_INVALID, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_NOT_CONVERGED, DS_ERR_UNSUPPORTED,
+ DS_PENDING) = range(8)
 DS_ISTA, DS_FISTA = 0, 1
 DS_TEST_NONE, DS_SAFE, DS_DST3, DS_DOME, DS_GSAFE, DS_DGST3 = range(6)
 DS_FP64, DS_FP32, DS_BF16, DS_FP8 = range(4)
@@ -96,6 +97,12 @@ def lib():
                                         ctypes.POINTER(ctypes.c_int)]
             L.ds_batch_destroy.argtypes = [vp]
             L.ds_solve_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp, vp]
+            L.ds_server_create.argtypes = [vp, ctypes.c_size_t, i64, i64, ctypes.c_int, ctypes.POINTER(vp)]
+            L.ds_server_submit.argtypes = [vp, vp, vp, dp, ctypes.POINTER(ds_options), vp,
+                                           ctypes.POINTER(ctypes.c_uint64)]
+            L.ds_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(ds_result)]
+            L.ds_server_stats.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int64)] * 4 + [ctypes.POINTER(ctypes.c_size_t)]
+            L.ds_server_destroy.argtypes = [vp]
             L.ds_solve_lasso_noalloc.argtypes = [ctypes.c_int, vp, vp, i64, i64, i64, vp, dp,
                                                  ctypes.POINTER(ds_options), vp, ctypes.POINTER(ds_result)]
             for name in declared_functions():
@@ -277,6 +284,43 @@ def ds_solve_batch(ctx, dicts, Ys, lambdas, opt, Xs):
     _check(lib().ds_solve_batch(ctx, a.n, a.dicts, a.Y, a.nrhs, a.lam, ctypes.byref(opt), a.X, res),
            "ds_solve_batch")
     return [r.as_dict() for r in res]
+
+
+def ds_server_create(ctx, hbm_budget_bytes, max_N, max_K, team_size=0):
+    h = ctypes.c_void_p()
+    _check(lib().ds_server_create(ctx, int(hbm_budget_bytes), int(max_N), int(max_K), int(team_size),
+                                  ctypes.byref(h)), "ds_server_create")
+    return h
+
+
+def ds_server_submit(server, dct, y, lam, opt, x_out):
+    """y, x_out: host float32 NumPy arrays; keep x_out alive until ds_server_poll returns a result."""
+    t = ctypes.c_uint64()
+    _check(lib().ds_server_submit(server, dct, _ptr(y)[0], float(lam), ctypes.byref(opt), _ptr(x_out)[0],
+                                  ctypes.byref(t)), "ds_server_submit")
+    return t.value
+
+
+def ds_server_poll(server, ticket):
+    """The result dict when the request has completed, None while it is pending."""
+    r = ds_result()
+    st = lib().ds_server_poll(server, ctypes.c_uint64(ticket), ctypes.byref(r))
+    if st == DS_PENDING:
+        return None
+    _check(st, "ds_server_poll")
+    return r.as_dict()
+
+
+def ds_server_stats(server):
+    v = [ctypes.c_int64() for _ in range(4)]
+    m = ctypes.c_size_t()
+    _check(lib().ds_server_stats(server, *[ctypes.byref(x) for x in v], ctypes.byref(m)), "ds_server_stats")
+    return {"completed": v[0].value, "in_flight": v[1].value, "pending": v[2].value, "launches": v[3].value,
+            "pool_in_use": m.value}
+
+
+def ds_server_destroy(server):
+    _check(lib().ds_server_destroy(server), "ds_server_destroy")
 
 
 def ds_solve_lasso_noalloc(device, stream, D, y, lam, opt, x_out):

@@ -105,6 +105,7 @@ const char* ds_status_str(ds_status s)
     case DS_ERR_TIMEOUT: return "DS_ERR_TIMEOUT";
     case DS_ERR_NOT_CONVERGED: return "DS_ERR_NOT_CONVERGED";
     case DS_ERR_UNSUPPORTED: return "DS_ERR_UNSUPPORTED";
+    case DS_PENDING: return "DS_PENDING";
     }
     return "DS_ERR_UNKNOWN";
 }

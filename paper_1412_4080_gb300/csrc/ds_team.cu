@@ -11,7 +11,9 @@
 //   - server: a ring of problem descriptors in mapped host memory that the host
 //     fills while the kernel runs (continuous batching, ds_server_*).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <map>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -23,6 +25,16 @@
 #include "ds_solve_body.cuh"
 
 namespace ds {
+
+// A served request: solve parameters (with the request's own workspace, carved
+// from the server's memory pool) and device staging for y, x and the result.
+template <typename T>
+struct ServerJob {
+    SolveP<T> P;  // P.y, P.x_out, P.res point to mapped host memory; P.ws to the request's pool block
+    T* y_dev;
+    T* x_dev;
+    DevResult* res_dev;
+};
 
 template <typename T>
 struct TeamArgs {
@@ -39,10 +51,7 @@ struct TeamArgs {
     const volatile int* published;  // mapped host: number of problems published
     const volatile int* stop;       // mapped host: shutdown request
     volatile int* done;             // mapped host: per slot, sequence number + 1 when finished
-    T* stage_y;                     // per team, max_N
-    T* stage_x;                     // per team, max_K
-    DevResult* stage_res;           // per team
-    int max_N, max_K;
+    ServerJob<T>* ring;             // mapped host: request descriptors, one per slot
     long long idle_polls;           // server: give up waiting for work after this many polls
 };
 
@@ -57,6 +66,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
 {
     __shared__ SolveP<T> sP;
+    __shared__ T* s_stage[2];
+    __shared__ DevResult* s_res_dev;
     __shared__ int s_job;
     const int team = blockIdx.x / A.team_size, rank = blockIdx.x % A.team_size;
     GridBarrier* bar = A.bars + team;
@@ -99,18 +110,23 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
         if (threadIdx.x == 0) {
             if (A.server) {
                 // the descriptor lives in host memory: copy it word by word with volatile loads
-                const volatile unsigned int* src = reinterpret_cast<const volatile unsigned int*>(A.jobs + slot);
-                unsigned int* dst = reinterpret_cast<unsigned int*>(&sP);
-                for (int k = 0; k < (int)(sizeof(SolveP<T>) / 4); k++) dst[k] = src[k];
+                const volatile unsigned int* src = reinterpret_cast<const volatile unsigned int*>(A.ring + slot);
+                ServerJob<T> job;
+                unsigned int* dst = reinterpret_cast<unsigned int*>(&job);
+                for (int k = 0; k < (int)(sizeof(ServerJob<T>) / 4); k++) dst[k] = src[k];
+                sP = job.P;
+                s_stage[0] = job.y_dev;
+                s_stage[1] = job.x_dev;
+                s_res_dev = job.res_dev;
             } else {
                 sP = A.jobs[slot];
+                sP.ws = A.team_ws[team];
             }
-            sP.ws = A.team_ws[team];
         }
         __syncthreads();
         if (A.server) {
-            // stage y in device memory; outputs go to team staging, copied out at the end
-            T* ys = A.stage_y + (size_t)team * A.max_N;
+            // stage y in device memory; x and the result go to device staging, copied out at the end
+            T* ys = s_stage[0];
             const volatile T* yh = sP.y;
             for (int r = rank * kThreads + threadIdx.x; r < sP.N; r += A.team_size * kThreads) ys[r] = yh[r];
             host_x = sP.x_out;
@@ -118,9 +134,9 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
             __syncthreads();
             if (threadIdx.x == 0) {
                 sP.y = ys;
-                sP.x_out = A.stage_x + (size_t)team * A.max_K;
-                sP.ldx = A.max_K;
-                sP.res = A.stage_res + team;
+                sP.x_out = s_stage[1];
+                sP.ldx = sP.K;
+                sP.res = s_res_dev;
             }
             if (!grid_sync(bar, A.team_size, gen)) {
                 if (threadIdx.x == 0) atomicExch(A.error, 1);
@@ -491,6 +507,440 @@ ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const 
     st = ds_batch_run(B, res);
     ds_batch_destroy(B);
     return st;
+}
+
+}  // extern "C"
+
+// =================================================================== server
+
+namespace ds {
+
+// First-fit allocator of 256-byte aligned blocks in the server's device pool.
+class PoolAlloc {
+  public:
+    void init(size_t size)
+    {
+        free_.clear();
+        free_[0] = size;
+    }
+    bool alloc(size_t n, size_t* off)
+    {
+        n = align_up(n, 256);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, o2 = it->first + n;
+            free_.erase(it);
+            if (rest) free_[o2] = rest;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n)
+    {
+        n = align_up(n, 256);
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+
+  private:
+    std::map<size_t, size_t> free_;
+};
+
+static double now_ms()
+{
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace ds
+
+struct ds_server {
+    struct Ticket {
+        int64_t seq = -1;   // publication order (-1: pending)
+        int slot = -1;
+        size_t off = 0, bytes = 0;
+        void* x_out = nullptr;
+        std::vector<float> y;  // copy of y while pending
+        const ds_dict* dict = nullptr;
+        double lambda = 0.0;
+        ds_options opt;
+        double t_submit = 0.0;
+        int state = 0;  // 0 pending, 1 published, 2 done
+        ds_result res;
+    };
+    ds_ctx* ctx = nullptr;
+    cudaStream_t stream = nullptr;
+    int team_size = 0, n_teams = 0, ring = 0;
+    int64_t max_N = 0, max_K = 0;
+    size_t budget = 0, in_use = 0;
+    void* pool = nullptr;
+    ds::PoolAlloc alloc;
+    ds::ServerJob<float>* ring_h = nullptr;
+    ds::ServerJob<float>* ring_d = nullptr;
+    double* lam_h = nullptr;
+    double* lam_d = nullptr;
+    float* y_h = nullptr;
+    float* y_d = nullptr;
+    float* x_h = nullptr;
+    float* x_d = nullptr;
+    ds::DevResult* res_h = nullptr;
+    ds::DevResult* res_d = nullptr;
+    int* done_h = nullptr;
+    int* done_d = nullptr;
+    int* ctl_h = nullptr;  // [0] published, [1] stop
+    int* ctl_d = nullptr;
+    void* dctl = nullptr;  // bars, team_job, next_job, error
+    size_t dctl_bytes = 0, bars_bytes = 0;
+    int* derr = nullptr;
+    double* fista = nullptr;
+    int fista_n = 0;
+    ds::TeamArgs<float> args;
+    int smem = 0;
+    std::unordered_map<uint64_t, Ticket> tickets;
+    std::deque<uint64_t> pending;
+    std::vector<int64_t> slot_seq;
+    std::vector<uint64_t> slot_ticket;
+    uint64_t next_ticket = 1;
+    int64_t published = 0;
+    int64_t completed = 0;
+    long long launches = 0;
+    std::mutex mu;
+};
+
+namespace ds {
+
+static size_t request_bytes(ds_server* S, const ds_dict* d, const ds_options* opt, Geometry* g_out, DictDesc* dd_out)
+{
+    DictDesc dd = dict_desc(d);
+    Geometry g;
+    if (geometry<float>(dd, S->team_size, S->ctx->smem_optin, &g) != DS_OK) return 0;
+    Ws<float> w;
+    double* l;
+    DevResult* r;
+    double* c;
+    size_t b = align_up(layout<float>(nullptr, dd, g, 1, &w, &l, &r, &c), 256);
+    b += align_up(sizeof(float) * d->N, 256) + align_up(sizeof(float) * d->K, 256) + align_up(sizeof(DevResult), 256);
+    (void)opt;
+    *g_out = g;
+    *dd_out = dd;
+    return b;
+}
+
+// Publish a pending request if its ring slot is free and the pool has room.
+static bool server_publish(ds_server* S, uint64_t tid, ds_server::Ticket& t, const float* y_src)
+{
+    const int64_t seq = S->published;
+    const int slot = (int)(seq % S->ring);
+    if (S->slot_seq[slot] >= 0) return false;  // previous occupant not harvested yet
+    Geometry g;
+    DictDesc dd;
+    const size_t bytes = request_bytes(S, t.dict, &t.opt, &g, &dd);
+    size_t off = 0;
+    if (!bytes || !S->alloc.alloc(bytes, &off)) return false;  // admission by HBM footprint
+    char* blk = reinterpret_cast<char*>(S->pool) + off;
+    Ws<float> w;
+    double* l;
+    DevResult* r;
+    double* c;
+    const size_t wsb = align_up(layout<float>(blk, dd, g, 1, &w, &l, &r, &c), 256);
+    ServerJob<float> job;
+    std::memset(&job, 0, sizeof(job));
+    fill_params<float>(job.P, dd, g, &t.opt);
+    job.P.fista = S->fista;
+    job.P.fista_n = S->fista_n;
+    job.P.n_lambda = 1;
+    job.P.lambdas = S->lam_d + slot;
+    job.P.y = S->y_d + (size_t)slot * S->max_N;
+    job.P.x_out = S->x_d + (size_t)slot * S->max_K;
+    job.P.ldx = t.dict->K;
+    job.P.res = S->res_d + slot;
+    job.P.ws = w;
+    job.y_dev = reinterpret_cast<float*>(blk + wsb);
+    job.x_dev = reinterpret_cast<float*>(blk + wsb + align_up(sizeof(float) * t.dict->N, 256));
+    job.res_dev = reinterpret_cast<DevResult*>(blk + wsb + align_up(sizeof(float) * t.dict->N, 256) +
+                                               align_up(sizeof(float) * t.dict->K, 256));
+    S->lam_h[slot] = t.lambda;
+    std::memcpy(S->y_h + (size_t)slot * S->max_N, y_src, sizeof(float) * t.dict->N);
+    S->ring_h[slot] = job;
+    reinterpret_cast<volatile int*>(S->done_h)[slot] = 0;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    reinterpret_cast<volatile int*>(S->ctl_h)[0] = (int)(seq + 1);
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    S->published = seq + 1;
+    S->slot_seq[slot] = seq;
+    S->slot_ticket[slot] = tid;
+    S->in_use += bytes;
+    t.seq = seq;
+    t.slot = slot;
+    t.off = off;
+    t.bytes = bytes;
+    t.state = 1;
+    t.y.clear();
+    t.y.shrink_to_fit();
+    return true;
+}
+
+static void server_harvest(ds_server* S)
+{
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    for (int slot = 0; slot < S->ring; slot++) {
+        const int64_t seq = S->slot_seq[slot];
+        if (seq < 0) continue;
+        if (reinterpret_cast<volatile int*>(S->done_h)[slot] != (int)(seq + 1)) continue;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        auto it = S->tickets.find(S->slot_ticket[slot]);
+        if (it != S->tickets.end()) {
+            ds_server::Ticket& t = it->second;
+            std::memcpy(t.x_out, S->x_h + (size_t)slot * S->max_K, sizeof(float) * t.dict->K);
+            const DevResult& r = S->res_h[slot];
+            t.res.iters = r.iters;
+            t.res.status = r.status;
+            t.res.n_active = r.n_active;
+            t.res.nnz = r.nnz;
+            t.res.gap = r.gap;
+            t.res.primal = r.primal;
+            t.res.dual = r.dual;
+            t.res.lambda = r.lambda;
+            t.res.lambda_max = r.lambda_max;
+            t.res.cols_corr = r.cols_corr;
+            t.res.cols_synth = r.cols_synth;
+            t.res.ms = now_ms() - t.t_submit;  // latency: submission to completion observed by the host
+            t.state = 2;
+            S->alloc.release(t.off, t.bytes);
+            S->in_use -= t.bytes;
+        }
+        S->slot_seq[slot] = -1;
+        S->completed++;
+    }
+}
+
+static ds_status server_launch(ds_server* S)
+{
+    // counters of the previous launch: barriers restart, the queue head persists
+    if (cudaMemsetAsync(S->dctl, 0, S->bars_bytes, S->stream) != cudaSuccess) return DS_ERR_CUDA;
+    void* a[] = {(void*)&S->args};
+    const int grid = S->n_teams * S->team_size;
+    if (cudaLaunchCooperativeKernel((const void*)team_kernel<float>, dim3(grid), dim3(kThreads), a, S->smem,
+                                    S->stream) != cudaSuccess)
+        return DS_ERR_CUDA;
+    S->launches++;
+    S->ctx->launches++;
+    return DS_OK;
+}
+
+static ds_status server_pump(ds_server* S)
+{
+    server_harvest(S);
+    while (!S->pending.empty()) {
+        auto it = S->tickets.find(S->pending.front());
+        if (it == S->tickets.end()) {
+            S->pending.pop_front();
+            continue;
+        }
+        if (!server_publish(S, it->first, it->second, it->second.y.data())) break;
+        S->pending.pop_front();
+    }
+    // a kernel that went idle exits; relaunch it while published work is outstanding
+    if (S->published > S->completed) {
+        const cudaError_t q = cudaStreamQuery(S->stream);
+        if (q == cudaSuccess) return server_launch(S);
+        if (q != cudaErrorNotReady) return DS_ERR_CUDA;
+    }
+    int err = 0;
+    cudaMemcpy(&err, S->derr, sizeof(int), cudaMemcpyDeviceToHost);
+    return err ? DS_ERR_TIMEOUT : DS_OK;
+}
+
+}  // namespace ds
+
+extern "C" {
+
+ds_status ds_server_destroy(ds_server* S)
+{
+    if (!S) return DS_OK;
+    if (S->ctx) cudaSetDevice(S->ctx->device);
+    if (S->ctl_h) {
+        reinterpret_cast<volatile int*>(S->ctl_h)[1] = 1;  // stop
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+    }
+    if (S->stream) {
+        cudaStreamSynchronize(S->stream);
+        cudaStreamDestroy(S->stream);
+    }
+    if (S->pool) cudaFree(S->pool);
+    if (S->dctl) cudaFree(S->dctl);
+    if (S->ring_h) cudaFreeHost(S->ring_h);
+    if (S->lam_h) cudaFreeHost(S->lam_h);
+    if (S->y_h) cudaFreeHost(S->y_h);
+    if (S->x_h) cudaFreeHost(S->x_h);
+    if (S->res_h) cudaFreeHost(S->res_h);
+    if (S->done_h) cudaFreeHost(S->done_h);
+    if (S->ctl_h) cudaFreeHost(S->ctl_h);
+    delete S;
+    return DS_OK;
+}
+
+ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, int64_t max_K, int team_size,
+                           ds_server** out)
+{
+    if (!ctx || !out || max_N < 1 || max_K < 1 || hbm_budget_bytes < (1u << 20) || team_size < 0 || team_size > 16)
+        return DS_ERR_INVALID;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return DS_ERR_CUDA;
+    ds_server* S = new (std::nothrow) ds_server();
+    if (!S) return DS_ERR_OOM;
+    S->ctx = ctx;
+    S->team_size = team_size ? team_size : 4;
+    S->n_teams = std::max(1, ctx->num_sms / S->team_size);
+    S->ring = std::max(16, 4 * S->n_teams);
+    S->max_N = max_N;
+    S->max_K = max_K;
+    S->budget = hbm_budget_bytes;
+    auto fail = [&](ds_status st) {
+        ds_server_destroy(S);
+        return st;
+    };
+    // the largest request must fit the pool at least once
+    ds::DictDesc dmax;
+    std::memset(&dmax, 0, sizeof(dmax));
+    dmax.dtype = DS_FP32;
+    dmax.N = (int)max_N;
+    dmax.K = (int)max_K;
+    dmax.ld = (int)max_N;
+    dmax.nG = (int)max_K;
+    dmax.max_gsize = 32;
+    dmax.is_group = 1;
+    ds::Geometry gmax;
+    if (ds::geometry<float>(dmax, S->team_size, ctx->smem_optin, &gmax) != DS_OK) return fail(DS_ERR_UNSUPPORTED);
+    S->smem = (int)gmax.smem;
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(DS_ERR_CUDA);
+    if (cudaMalloc(&S->pool, hbm_budget_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        S->pool = nullptr;
+        return fail(DS_ERR_OOM);
+    }
+    S->alloc.init(hbm_budget_bytes);
+    const unsigned fl = cudaHostAllocMapped;
+    if (cudaHostAlloc((void**)&S->ring_h, sizeof(ds::ServerJob<float>) * S->ring, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->lam_h, sizeof(double) * S->ring, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->y_h, sizeof(float) * max_N * S->ring, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->x_h, sizeof(float) * max_K * S->ring, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->res_h, sizeof(ds::DevResult) * S->ring, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->done_h, sizeof(int) * S->ring, fl) != cudaSuccess ||
+        cudaHostAlloc((void**)&S->ctl_h, sizeof(int) * 2, fl) != cudaSuccess)
+        return fail(DS_ERR_OOM);
+    std::memset(S->done_h, 0, sizeof(int) * S->ring);
+    std::memset(S->ctl_h, 0, sizeof(int) * 2);
+    if (cudaHostGetDevicePointer((void**)&S->ring_d, S->ring_h, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&S->lam_d, S->lam_h, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&S->y_d, S->y_h, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&S->x_d, S->x_h, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&S->res_d, S->res_h, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&S->done_d, S->done_h, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&S->ctl_d, S->ctl_h, 0) != cudaSuccess)
+        return fail(DS_ERR_CUDA);
+    // device control: barriers + team_job (reset per launch), queue head + error (persistent), FISTA table
+    S->bars_bytes = ds::align_up(sizeof(ds::GridBarrier) * S->n_teams + sizeof(int) * S->n_teams, 256);
+    ds_status st = ds::ctx_fista_table(ctx, 1 << 16);
+    if (st != DS_OK) return fail(st);
+    S->fista_n = ctx->fista_n;
+    S->dctl_bytes = S->bars_bytes + 256 + ds::align_up(sizeof(double) * 2 * S->fista_n, 256);
+    if (cudaMalloc(&S->dctl, S->dctl_bytes) != cudaSuccess) return fail(DS_ERR_OOM);
+    if (cudaMemset(S->dctl, 0, S->dctl_bytes) != cudaSuccess) return fail(DS_ERR_CUDA);
+    char* c = reinterpret_cast<char*>(S->dctl);
+    int* next_job = reinterpret_cast<int*>(c + S->bars_bytes);
+    S->derr = next_job + 1;
+    S->fista = reinterpret_cast<double*>(c + S->bars_bytes + 256);
+    if (cudaMemcpy(S->fista, ctx->fista, sizeof(double) * 2 * S->fista_n, cudaMemcpyDeviceToDevice) != cudaSuccess)
+        return fail(DS_ERR_CUDA);
+    ds::TeamArgs<float>& A = S->args;
+    std::memset(&A, 0, sizeof(A));
+    A.n_jobs = S->ring;
+    A.bars = reinterpret_cast<ds::GridBarrier*>(c);
+    A.team_job = reinterpret_cast<int*>(c + sizeof(ds::GridBarrier) * S->n_teams);
+    A.next_job = next_job;
+    A.error = S->derr;
+    A.team_size = S->team_size;
+    A.server = 1;
+    A.published = S->ctl_d;
+    A.stop = S->ctl_d + 1;
+    A.done = S->done_d;
+    A.ring = S->ring_d;
+    A.idle_polls = 20000;
+    if (cudaFuncSetAttribute(ds::team_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(ctx->smem_optin - 40 * 1024)) != cudaSuccess)
+        return fail(DS_ERR_CUDA);
+    S->slot_seq.assign(S->ring, -1);
+    S->slot_ticket.assign(S->ring, 0);
+    *out = S;
+    return DS_OK;
+}
+
+ds_status ds_server_submit(ds_server* S, const ds_dict* dict, const void* y, double lambda, const ds_options* opt,
+                           void* x_out, uint64_t* ticket)
+{
+    if (!S || !dict || !y || !opt || !x_out || !ticket || dict->ctx != S->ctx) return DS_ERR_INVALID;
+    if (dict->dtype != DS_FP32) return DS_ERR_UNSUPPORTED;
+    if (dict->N > S->max_N || dict->K > S->max_K) return DS_ERR_UNSUPPORTED;
+    if (!(lambda > 0.0) || opt->max_iter < 1 || !(opt->tol_gap_rel >= 0.0) || opt->test < DS_TEST_NONE ||
+        opt->test > DS_DGST3 || (opt->alg != DS_ISTA && opt->alg != DS_FISTA) || opt->L < 0.0)
+        return DS_ERR_INVALID;
+    if (dict->is_group && (opt->test == DS_SAFE || opt->test == DS_DST3 || opt->test == DS_DOME)) return DS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (cudaSetDevice(S->ctx->device) != cudaSuccess) return DS_ERR_CUDA;
+    const uint64_t tid = S->next_ticket++;
+    ds_server::Ticket& t = S->tickets[tid];
+    t.dict = dict;
+    t.lambda = lambda;
+    t.opt = *opt;
+    t.x_out = x_out;
+    t.t_submit = ds::now_ms();
+    bool done = false;
+    if (S->pending.empty()) done = ds::server_publish(S, tid, t, reinterpret_cast<const float*>(y));
+    if (!done) {
+        t.y.assign(reinterpret_cast<const float*>(y), reinterpret_cast<const float*>(y) + dict->N);
+        S->pending.push_back(tid);
+    }
+    *ticket = tid;
+    return ds::server_pump(S);
+}
+
+ds_status ds_server_poll(ds_server* S, uint64_t ticket, ds_result* res)
+{
+    if (!S || !res) return DS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (cudaSetDevice(S->ctx->device) != cudaSuccess) return DS_ERR_CUDA;
+    ds_status st = ds::server_pump(S);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return DS_ERR_INVALID;
+    if (it->second.state != 2) return st == DS_OK ? DS_PENDING : st;
+    *res = it->second.res;
+    S->tickets.erase(it);
+    return DS_OK;
+}
+
+ds_status ds_server_stats(ds_server* S, int64_t* completed, int64_t* in_flight, int64_t* pending, int64_t* launches,
+                          size_t* pool_in_use)
+{
+    if (!S) return DS_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (completed) *completed = S->completed;
+    if (in_flight) *in_flight = S->published - S->completed;
+    if (pending) *pending = (int64_t)S->pending.size();
+    if (launches) *launches = S->launches;
+    if (pool_in_use) *pool_in_use = S->in_use;
+    return DS_OK;
 }
 
 }  // extern "C"

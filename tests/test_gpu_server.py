@@ -1,0 +1,107 @@
+"""Continuous-batching server: every request gives the same result alone and in
+a mix of concurrent requests (Lasso and Group-Lasso, different sizes and
+lambdas), and matches the single-solve entry point within the parity
+tolerance."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import gen
+import paper_1412_4080_gb300 as ds
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev_dict(D):
+    return torch.from_numpy(np.ascontiguousarray(D.T)).to("cuda", torch.float32).t()
+
+
+def _wait(server, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t not in out:
+                r = ds.ds_server_poll(server, t)
+                if r is not None:
+                    out[t] = r
+        assert time.time() - t0 < timeout, "server requests did not complete"
+        time.sleep(0.0005)
+    return [out[t] for t in tickets]
+
+
+def test_server_alone_equals_mix_and_single_solves():
+    g = gen.rng(303)
+    ctx = ds.ds_create(0, None)
+    specs = [(600, 2400, None), (512, 2048, 8), (257, 1024, None)]
+    dicts, mats = [], []
+    for (N, K, gs) in specs:
+        D = gen.gaussian_dict(N, K, g)
+        goff = gen.contiguous_groups(K, gs) if gs else None
+        dicts.append(ds.ds_dict_create(ctx, _dev_dict(D), goff))
+        mats.append((D, goff))
+    reqs = []
+    for k in range(12):
+        di = k % len(specs)
+        D, goff = mats[di]
+        y = gen.observe(D, gen.bernoulli_gaussian_x0(D.shape[1], 0.02, g), g).astype(np.float32)
+        ratio = float(g.uniform(0.3, 0.9))
+        test = "dgst3" if goff is not None else ("dst3", "dome", "safe")[k % 3]
+        reqs.append((di, y, ratio, test))
+    server = ds.ds_server_create(ctx, 256 << 20, 1024, 4096, 4)
+    try:
+        def opt(test):
+            return ds.ds_options_default(test=test, tol_gap_rel=0.0, max_iter=700, lambda_rel=1)
+        # alone: one request in flight at a time
+        alone = []
+        for (di, y, ratio, test) in reqs:
+            x = np.zeros(mats[di][0].shape[1], dtype=np.float32)
+            t = ds.ds_server_submit(server, dicts[di], y, ratio, opt(test), x)
+            r = _wait(server, [t])[0]
+            alone.append((x, r))
+        # mix: all requests in flight together
+        xs, ts = [], []
+        for (di, y, ratio, test) in reqs:
+            x = np.zeros(mats[di][0].shape[1], dtype=np.float32)
+            xs.append(x)
+            ts.append(ds.ds_server_submit(server, dicts[di], y, ratio, opt(test), x))
+        mix = _wait(server, ts)
+        st = ds.ds_server_stats(server)
+        print("server stats:", st)
+        for k, (di, y, ratio, test) in enumerate(reqs):
+            xa, ra = alone[k]
+            assert ra["status"] == 0 and mix[k]["status"] == 0
+            # same team size, fixed-order reductions: bitwise the same alone and in the mix
+            np.testing.assert_array_equal(xa, xs[k])
+            assert ra["iters"] == mix[k]["iters"] == 700
+            # and the single-solve entry point agrees within the parity tolerance
+            x1 = torch.zeros(mats[di][0].shape[1], device="cuda")
+            ds.ds_solve(ctx, dicts[di], torch.from_numpy(y).cuda(), ratio, opt(test), x1)
+            a = x1.double().cpu().numpy()
+            assert np.abs(a - xa.astype(np.float64)).max() <= 1e-5 * max(np.abs(a).max(), 1e-30)
+    finally:
+        ds.ds_server_destroy(server)
+        for d in dicts:
+            ds.ds_dict_destroy(d)
+        ds.ds_destroy(ctx)
+
+
+def test_server_rejects_oversized_and_admits_by_pool():
+    g = gen.rng(304)
+    ctx = ds.ds_create(0, None)
+    D = gen.gaussian_dict(700, 3000, g)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D))
+    server = ds.ds_server_create(ctx, 8 << 20, 512, 4096, 2)  # N above 512 is refused; a small pool
+    try:
+        y = gen.observe(D, gen.bernoulli_gaussian_x0(3000, 0.02, g), g).astype(np.float32)
+        x = np.zeros(3000, dtype=np.float32)
+        with pytest.raises(ds.DscreenError) as e:
+            ds.ds_server_submit(server, dct, y, 0.5, ds.ds_options_default(lambda_rel=1), x)
+        assert e.value.status == ds.DS_ERR_UNSUPPORTED
+    finally:
+        ds.ds_server_destroy(server)
+        ds.ds_dict_destroy(dct)
+        ds.ds_destroy(ctx)
