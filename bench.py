@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-large", action="store_true", help="skip the 8192x65536 HBM roofline run")
+    ap.add_argument("--no-modes", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--profile-one", action="store_true",
                     help="register the dictionary and run one 5-lambda DST3 path, then exit (profiling)")
@@ -319,6 +320,9 @@ def main():
     if not args.no_large:
         out["roofline_large"] = large_roofline(ds, ctx, dev, stream, peak, peak_kind)
 
+    if world == 1 and not args.no_modes:
+        out["batched"] = batched_measure(ds, ctx, D32, dev, flush)
+        out["served"] = served_measure(ds, ctx, dev)
     ds.ds_destroy(ctx)
     if rank == 0 and not args.no_cpu and world == 1:
         out["cpu_baseline"] = cpu_baseline(D32, y32)
@@ -344,6 +348,140 @@ def profile_one():
     yy = float(y32.astype(np.float64) @ y32.astype(np.float64))
     print(json.dumps([{**{k: r[k] for k in ("iters", "status", "ms", "n_active", "nnz", "cols_corr", "cols_synth")},
                        "gap_rel": r["gap"] / (0.5 * yy)} for r in res]))
+
+
+def batched_measure(ds, ctx, D32, dev, flush):
+    """64 right-hand sides on the 2000 x 10000 dictionary (Bernoulli(0.01)-Gaussian x0,
+    20 dB, lambda/lambda_max ~ U[0.1, 0.9]), FISTA + DST3 to gap 1e-6: one batch
+    (persistent multi-team launch replayed from its CUDA graph) against the plain
+    form (the same 64 problems solved one at a time)."""
+    import torch
+    R = 64
+    g = np.random.default_rng(2002)
+    N, K = D32.shape
+    X0 = np.zeros((K, R))
+    mask = g.uniform(size=(K, R)) < 0.01
+    X0[mask] = g.standard_normal(int(mask.sum()))
+    S = D32.astype(np.float64) @ X0
+    E = g.standard_normal((N, R))
+    Y = (S + E * (np.linalg.norm(S, axis=0) / np.linalg.norm(E, axis=0)) * 0.1).T.astype(np.float32)  # (R, N)
+    ratios = g.uniform(0.1, 0.9, size=R)
+    Dt = torch.from_numpy(np.ascontiguousarray(D32.T)).to(dev).t()
+    dct = ds.ds_dict_create(ctx, Dt)
+    Yt = torch.from_numpy(Y).to(dev)
+    Xb = torch.zeros((R, K), device=dev)
+    opt = ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
+    plan = ds.ds_batch_create(ctx, [dct], [Yt], [ratios], opt, [Xb])
+    info = ds.ds_batch_info(plan)
+    ds.ds_batch_run(plan)  # warm
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    ev0.record()
+    res = ds.ds_batch_run(plan)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_batch = ev0.elapsed_time(ev1) / 1e3
+    ok_b = all(r["status"] == 0 for r in res)
+    # plain form: one solve at a time
+    x1 = torch.zeros(K, device=dev)
+    flush.fill_(2.0)
+    torch.cuda.synchronize()
+    ev0.record()
+    for r in range(R):
+        ds.ds_solve(ctx, dct, Yt[r], float(ratios[r]), opt, x1)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_plain = ev0.elapsed_time(ev1) / 1e3
+    ds.ds_batch_destroy(plan)
+    ds.ds_dict_destroy(dct)
+    return {"value": R / t_batch, "unit": "solves/s", "plain_value": R / t_plain, "vs_plain": t_plain / t_batch,
+            "converged": ok_b, "plan": info,
+            "iters_median": float(np.median([r["iters"] for r in res])),
+            "workload": "64 rhs x 2000x10000 FP32 Gaussian dictionary, lambda/lambda_max ~ U[0.1,0.9], "
+                        "FISTA+DST3, gap 1e-6; one graph-replayed persistent launch vs 64 sequential ds_solve"}
+
+
+def served_measure(ds, ctx, dev, seconds=3.0, rate=100.0, drain_s=20.0):
+    """Open-loop Poisson stream of mixed requests (80% Lasso / 20% Group-Lasso with
+    groups of 8) on AR(1) dictionaries (rho = 0.9, unit-norm columns) of N in
+    {512..2048} and K in {4096..16384}, lambda/lambda_max ~ U[0.1, 0.9], gap 1e-6:
+    p50/p99 latency from submission to completion and completed solves/s."""
+    import time
+    import torch
+    g = np.random.default_rng(2005)
+    tg = torch.Generator(device=dev).manual_seed(2005)
+    pool = []
+    for (N, K) in ((512, 4096), (1024, 8192), (1536, 12288), (2048, 16384)):
+        E = torch.randn((N, K), device=dev, generator=tg)
+        D = torch.empty_like(E)
+        D[0] = E[0]
+        s = (1 - 0.9 ** 2) ** 0.5
+        for n in range(1, N):
+            D[n] = 0.9 * D[n - 1] + s * E[n]
+        D /= D.norm(dim=0, keepdim=True)
+        Dc = D.t().contiguous().t()  # column-major
+        lasso = ds.ds_dict_create(ctx, Dc)
+        goff = np.arange(0, K + 1, 8, dtype=np.int64)
+        group = ds.ds_dict_create(ctx, Dc, goff)
+        # a bank of observations per dictionary: 1% active atoms (groups), 20 dB
+        B = 16
+        X0 = torch.zeros((K, B), device=dev)
+        m = torch.rand((K, B), device=dev, generator=tg) < 0.01
+        X0[m] = torch.randn(int(m.sum()), device=dev, generator=tg)
+        S = D @ X0
+        Nz = torch.randn(S.shape, device=dev, generator=tg)
+        Y = (S + Nz * (S.norm(dim=0) / Nz.norm(dim=0)) * 0.1).t().contiguous().cpu().numpy()
+        pool.append((N, K, lasso, group, Y))
+        del E, D
+    server = ds.ds_server_create(ctx, 4 << 30, 2048, 16384, 4)
+    opts = {"lasso": ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1),
+            "group": ds.ds_options_default(test="dgst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)}
+    # warm the server (kernel load, first launch)
+    N, K, lasso, group, Y = pool[0]
+    xw = np.zeros(K, dtype=np.float32)
+    tw = ds.ds_server_submit(server, lasso, Y[0], 0.5, opts["lasso"], xw)
+    while ds.ds_server_poll(server, tw) is None:
+        time.sleep(0.001)
+    arrivals = np.cumsum(g.exponential(1.0 / rate, size=int(rate * seconds * 1.5)))
+    arrivals = arrivals[arrivals < seconds]
+    outstanding, lat, keep = {}, [], []
+    t0 = time.perf_counter()
+    i = 0
+    while i < len(arrivals) or outstanding:
+        now = time.perf_counter() - t0
+        if now > seconds + drain_s:
+            break  # saturated: what is still outstanding is reported, not hidden
+        while i < len(arrivals) and arrivals[i] <= now:
+            N, K, lasso, group, Y = pool[g.integers(len(pool))]
+            kind = "group" if g.uniform() < 0.2 else "lasso"
+            x = np.zeros(K, dtype=np.float32)
+            t = ds.ds_server_submit(server, group if kind == "group" else lasso, Y[g.integers(Y.shape[0])],
+                                    float(g.uniform(0.1, 0.9)), opts[kind], x)
+            outstanding[t] = x
+            i += 1
+        for t in list(outstanding):
+            r = ds.ds_server_poll(server, t)
+            if r is not None:
+                lat.append(r["ms"])
+                keep.append(r["status"])
+                del outstanding[t]
+        time.sleep(0.0002)
+    wall = time.perf_counter() - t0
+    unfinished = len(outstanding)
+    st = ds.ds_server_stats(server)
+    ds.ds_server_destroy(server)
+    for (_, _, lasso, group, _) in pool:
+        ds.ds_dict_destroy(lasso)
+        ds.ds_dict_destroy(group)
+    lat = np.array(lat)
+    return {"value": len(lat) / wall, "unit": "solves/s", "offered_rate": rate, "requests": int(len(lat)),
+            "unfinished_at_deadline": unfinished, "window_s": seconds, "wall_s": wall,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "converged": int(sum(1 for s_ in keep if s_ == 0)), "kernel_launches": st["launches"],
+            "workload": "Poisson arrivals, 80% Lasso / 20% Group-Lasso (groups of 8), AR(1) rho=0.9 dictionaries "
+                        "N in {512,1024,1536,2048}, K in {4096,8192,12288,16384}, lambda/lambda_max ~ U[0.1,0.9], "
+                        "gap 1e-6, FISTA + DST3/DGST3, teams of 4 CTAs, 4 GiB pool"}
 
 
 def large_roofline(ds, ctx, dev, stream, peak, peak_kind):

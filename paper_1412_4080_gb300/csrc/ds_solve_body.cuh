@@ -86,6 +86,7 @@ struct SolveP {
     double* colnorm_w;    // non-null: the kernel computes ||d_i|| here (and fmax) in its first pass
     const double* fista;  // FISTA table: (coefficient (l_{t-1} - 1) / l_t, l_t) for t = 1..fista_n
     int fista_n;
+    const volatile int* abort_flag;  // non-null: a nonzero value ends the solve at the next check
 };
 
 // ------------------------------------------------------------------ helpers
@@ -899,6 +900,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
                             }
                             stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                            // an owner shutting down (the server) may end the solve early, every 16 iterations
+                            if (P.abort_flag && (t & 15) == 0 && *P.abort_flag) stop = 1;
                         }
                         alpha = a_;
                         beta = b_;
@@ -1322,6 +1325,7 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.colnorm_w = nullptr;
     P.fista = nullptr;
     P.fista_n = 0;
+    P.abort_flag = nullptr;
 }
 
 }  // namespace ds

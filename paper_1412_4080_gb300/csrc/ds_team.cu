@@ -666,6 +666,7 @@ static bool server_publish(ds_server* S, uint64_t tid, ds_server::Ticket& t, con
     job.P.ldx = t.dict->K;
     job.P.res = S->res_d + slot;
     job.P.ws = w;
+    job.P.abort_flag = S->ctl_d + 1;  // the stop flag: destroy ends in-flight solves
     job.y_dev = reinterpret_cast<float*>(blk + wsb);
     job.x_dev = reinterpret_cast<float*>(blk + wsb + align_up(sizeof(float) * t.dict->N, 256));
     job.res_dev = reinterpret_cast<DevResult*>(blk + wsb + align_up(sizeof(float) * t.dict->N, 256) +
