@@ -71,6 +71,9 @@ typedef struct {
     double tol_gap_rel; /* stop when gap <= tol * 1/2 ||y||^2; 0 runs exactly max_iter iterations */
     double L;           /* step constant; <= 0 uses the dictionary's ||D||_2^2 upper estimate */
     int lambda_rel;     /* 1: lambda values are fractions of lambda_max (computed in the call) */
+    double lowp_switch; /* dictionaries with a BF16/FP8 copy: relative gap at which the solve leaves the
+                           copy for the FP32 master (also left after 25 iterations without 1% progress);
+                           <= 0: the gap tolerance (1e-6 when it is 0) */
 } ds_options;
 
 typedef struct {
@@ -86,6 +89,7 @@ typedef struct {
     double ms;          /* device time of the solve kernel, milliseconds (path: shared equally) */
     int64_t cols_corr;  /* dictionary columns read by correlations D_A^T theta (incl. D^T y, D^T n) */
     int64_t cols_synth; /* dictionary columns read by the sparse syntheses D_A u, D_A x */
+    int64_t cols_lowp;  /* of cols_corr, the columns read from the BF16/FP8 working copy */
 } ds_result;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -117,7 +121,13 @@ ds_status ds_destroy(ds_ctx* ctx);
  * 0 = off_0 < off_1 < ... < off_G = K) lists contiguous column ranges; weights
  * (host, n_groups entries, > 0; NULL = sqrt(group size)).  group_offsets NULL
  * = the Lasso.  Group sizes are limited to 32 columns (DS_ERR_UNSUPPORTED).
- * work_prec must equal dtype in this build.  Errors: DS_ERR_INVALID,
+ * work_prec: dtype, or (FP32 dictionaries) DS_BF16 / DS_FP8 for the precision
+ * variant: the library also keeps a BF16 copy or an FP8 e4m3 copy with one
+ * scale per column (max|d_i| / 448) and the exact error norms ||d_i - copy_i||;
+ * solves then run their bulk iterations on the copy (2 or 1 bytes per entry),
+ * with every screening radius inflated by the copy's error bound so the tests
+ * stay safe, and finish with FP32 iterations on the surviving atoms.
+ * Errors: DS_ERR_INVALID,
  * DS_ERR_UNSUPPORTED (N > the shared-memory limit, group > 32, work_prec),
  * DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
 ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64_t ld, ds_prec dtype,

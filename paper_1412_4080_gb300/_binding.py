@@ -38,20 +38,21 @@ HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
 class ds_options(ctypes.Structure):
     _fields_ = [("alg", ctypes.c_int), ("test", ctypes.c_int), ("dynamic", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
-                ("lambda_rel", ctypes.c_int)]
+                ("lambda_rel", ctypes.c_int), ("lowp_switch", ctypes.c_double)]
 
 
 class ds_result(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("n_active", ctypes.c_int64),
                 ("nnz", ctypes.c_int64), ("gap", ctypes.c_double), ("primal", ctypes.c_double),
                 ("dual", ctypes.c_double), ("lambda_", ctypes.c_double), ("lambda_max", ctypes.c_double),
-                ("ms", ctypes.c_double), ("cols_corr", ctypes.c_int64), ("cols_synth", ctypes.c_int64)]
+                ("ms", ctypes.c_double), ("cols_corr", ctypes.c_int64), ("cols_synth", ctypes.c_int64),
+                ("cols_lowp", ctypes.c_int64)]
 
     def as_dict(self):
         return {"iters": self.iters, "status": self.status, "n_active": self.n_active, "nnz": self.nnz,
                 "gap": self.gap, "primal": self.primal, "dual": self.dual, "lambda": self.lambda_,
                 "lambda_max": self.lambda_max, "ms": self.ms, "cols_corr": self.cols_corr,
-                "cols_synth": self.cols_synth}
+                "cols_synth": self.cols_synth, "cols_lowp": self.cols_lowp}
 
 
 class DscreenError(RuntimeError):

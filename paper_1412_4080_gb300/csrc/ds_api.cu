@@ -120,6 +120,7 @@ ds_status ds_options_default(ds_options* opt)
     opt->tol_gap_rel = 1e-6;
     opt->L = 0.0;
     opt->lambda_rel = 0;
+    opt->lowp_switch = 0.0;
     return DS_OK;
 }
 
@@ -194,7 +195,8 @@ ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64
     if (!ctx || !D || !out || N <= 0 || K <= 0 || ld < N) return DS_ERR_INVALID;
     *out = nullptr;
     if (dtype != DS_FP32 && dtype != DS_FP64) return DS_ERR_INVALID;
-    if (work_prec != dtype) return DS_ERR_UNSUPPORTED;
+    if (work_prec != dtype && !(dtype == DS_FP32 && (work_prec == DS_BF16 || work_prec == DS_FP8)))
+        return DS_ERR_UNSUPPORTED;
     if (K >= (1ll << 31) || N >= (1ll << 30)) return DS_ERR_UNSUPPORTED;
     int max_gsize = 1;
     if (group_offsets) {
@@ -248,6 +250,10 @@ ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64
     }
     ds_status st = dict_precompute(ctx, d, wh.empty() ? nullptr : wh.data());
     if (st != DS_OK) return fail(st);
+    if (work_prec == DS_BF16 || work_prec == DS_FP8) {
+        st = dict_lowp(ctx, d, work_prec == DS_BF16 ? 1 : 2);
+        if (st != DS_OK) return fail(st);
+    }
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(DS_ERR_CUDA);
     *out = d;
     return DS_OK;
@@ -265,6 +271,8 @@ ds_status ds_dict_destroy(ds_dict* d)
     if (d->goff) cudaFree(d->goff);
     if (d->w) cudaFree(d->w);
     if (d->spec) cudaFree(d->spec);
+    if (d->Dlo) cudaFree(d->Dlo);
+    if (d->lo_scale) cudaFree(d->lo_scale);
     delete d;
     return DS_OK;
 }
@@ -349,6 +357,7 @@ ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* d, const void* y, int n_lamb
         res[j].ms = ms / n_lambda;
         res[j].cols_corr = r[j].cols_corr;
         res[j].cols_synth = r[j].cols_synth;
+        res[j].cols_lowp = r[j].cols_lowp;
     }
     return st;
 }

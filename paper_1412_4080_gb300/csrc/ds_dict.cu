@@ -11,6 +11,9 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "ds_internal.h"
 
 namespace ds {
@@ -399,6 +402,96 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
     // FP32 products: add a relative margin for their rounding
     const double margin = sizeof(T) == 4 ? 2e-5 : 1e-12;
     dict->L = (theta + res) * (1.0 + margin);
+    return DS_OK;
+}
+
+// Low-precision working copy of an FP32 dictionary: BF16 (round to nearest)
+// or FP8 e4m3 with a per-column scale max|d_i| / 448.  err[i] receives the exact
+// ||d_i - dlo_i||_2 (compensated), which bounds the correlation error of the
+// copy by ||d_i - dlo_i|| ||theta|| (Cauchy-Schwarz).
+__global__ void quantize_kernel(const float* __restrict__ D, int N, int K, int ld, int kind, void* __restrict__ out,
+                                int ld_lo, float* __restrict__ scale, double* __restrict__ err)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = gw; i < K; i += nwarps) {
+        const float* d = D + (size_t)i * ld;
+        float s = 1.f;
+        if (kind == 2) {
+            float mx = 0.f;
+            for (int r = lane; r < N; r += 32) mx = fmaxf(mx, fabsf(d[r]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            s = mx > 0.f ? mx / 448.f : 1.f;
+            if (lane == 0) scale[i] = s;
+        }
+        Dot2f e2;
+        for (int r = lane; r < ld_lo; r += 32) {
+            const float v = r < N ? d[r] : 0.f;
+            float back;
+            if (kind == 1) {
+                const __nv_bfloat16 q = __float2bfloat16_rn(v);
+                reinterpret_cast<__nv_bfloat16*>(out)[(size_t)i * ld_lo + r] = q;
+                back = __bfloat162float(q);
+            } else {
+                const __nv_fp8_e4m3 q(v / s);
+                reinterpret_cast<__nv_fp8_e4m3*>(out)[(size_t)i * ld_lo + r] = q;
+                back = float(q) * s;
+            }
+            const float df = v - back;
+            e2.add(df, df);
+        }
+        const double e = sqrt(warp_sum(e2.value()));
+        if (lane == 0) err[i] = e * (1.0 + 1e-12);
+    }
+}
+
+// per group: ||E_g||_F / w_g  (Lasso: err_i itself)
+__global__ void group_err_kernel(const double* __restrict__ err, const int* __restrict__ goff,
+                                 const double* __restrict__ w, int nG, double* __restrict__ out)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nG) return;
+    double s = 0.0;
+    for (int i = goff[g]; i < goff[g + 1]; i++) s += err[i] * err[i];
+    out[g] = sqrt(s) * (1.0 + 1e-12) / w[g];
+}
+
+ds_status dict_lowp(ds_ctx* ctx, ds_dict* dict, int kind)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t N = dict->N, K = dict->K;
+    const int64_t align = kind == 1 ? 8 : 16;  // 16-byte vectors of the copy
+    dict->ld_lo = (N + align - 1) / align * align;
+    const size_t es = kind == 1 ? 2 : 1;
+    if (cudaMalloc(&dict->Dlo, (size_t)dict->ld_lo * K * es) != cudaSuccess) return DS_ERR_OOM;
+    if (kind == 2 && cudaMalloc(&dict->lo_scale, sizeof(float) * K) != cudaSuccess) return DS_ERR_OOM;
+    double *err = nullptr, *gerr = nullptr, *dmax = nullptr;
+    if (cudaMalloc(&err, sizeof(double) * K) != cudaSuccess) return DS_ERR_OOM;
+    if (cudaMalloc(&dmax, sizeof(double)) != cudaSuccess) { cudaFree(err); return DS_ERR_OOM; }
+    ctx->launches += dict->is_group ? 3 : 2;
+    quantize_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(reinterpret_cast<const float*>(dict->D), (int)N, (int)K,
+                                                     (int)dict->ld, kind, dict->Dlo, (int)dict->ld_lo, dict->lo_scale,
+                                                     err);
+    const double* src = err;
+    int n = (int)K;
+    if (dict->is_group) {
+        if (cudaMalloc(&gerr, sizeof(double) * dict->nG) != cudaSuccess) { cudaFree(err); cudaFree(dmax); return DS_ERR_OOM; }
+        group_err_kernel<<<(dict->nG + 255) / 256, 256, 0, s>>>(err, dict->goff, dict->w, dict->nG, gerr);
+        src = gerr;
+        n = dict->nG;
+    }
+    max_kernel<<<1, 1024, 0, s>>>(src, n, dmax);
+    double e = 0.0;
+    cudaMemcpyAsync(&e, dmax, sizeof(double), cudaMemcpyDeviceToHost, s);
+    const cudaError_t st = cudaStreamSynchronize(s);
+    cudaFree(err);
+    if (gerr) cudaFree(gerr);
+    cudaFree(dmax);
+    if (st != cudaSuccess) return DS_ERR_CUDA;
+    dict->emax = e;
+    dict->lo_kind = kind;
     return DS_OK;
 }
 

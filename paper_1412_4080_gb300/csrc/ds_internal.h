@@ -45,6 +45,12 @@ struct ds_dict {
     double* spec;     // device, nG: upper estimate of ||D_g||_2 (Lasso: nullptr)
     double fmax;      // max_g ||D_g||_F / w_g (Lasso: max_i ||d_i||)
     double L;         // upper estimate of ||D||_2^2
+    // low-precision working copy (work_prec BF16 or FP8), next to the FP32 master
+    int lo_kind;      // 0 none, 1 BF16, 2 FP8 e4m3 with a per-column scale
+    void* Dlo;        // ld_lo * K elements, zero rows N..ld_lo-1
+    int64_t ld_lo;
+    float* lo_scale;  // FP8: per-column scale (d_i ~ scale_i * q_i)
+    double emax;      // max_g ||D_g - Dlo_g||_F / w_g: rounding of the copy, for the radius bound
 };
 
 namespace ds {
@@ -56,7 +62,7 @@ struct DevResult {
     long long n_active;
     long long nnz;
     double gap, primal, dual, lambda, lambda_max;
-    long long cols_corr, cols_synth;
+    long long cols_corr, cols_synth, cols_lowp;
 };
 
 // Error codes raised inside kernels (DevResult.status).
@@ -75,6 +81,11 @@ struct DictDesc {
     const double* colnorm;  // may be null when norms_in_kernel
     double fmax, L;
     bool norms_in_kernel;   // Lasso only: the kernel computes ||d_i|| and their max itself
+    int lo_kind;            // low-precision copy: 0 none, 1 BF16, 2 FP8
+    const void* Dlo;
+    int ld_lo;
+    const float* lo_scale;
+    double emax;
 };
 
 // Where and how a solve runs: a context (workspace reserved on demand, timing
@@ -104,6 +115,7 @@ ds_status launch_solve(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, cons
                        DevResult* res_host, float* ms);
 ds_status launch_lambda_max(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, double* lmax);
 ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host);
+ds_status dict_lowp(ds_ctx* ctx, ds_dict* dict, int kind);
 
 // Workspace helpers (ds_api.cu).
 ds_status ctx_reserve(ds_ctx* ctx, size_t bytes);

@@ -136,5 +136,6 @@ extern "C" ds_status ds_solve_lasso_noalloc(int device, void* cuda_stream, const
     res->ms = 0.0;
     res->cols_corr = r.cols_corr;
     res->cols_synth = r.cols_synth;
+    res->cols_lowp = r.cols_lowp;
     return st;
 }

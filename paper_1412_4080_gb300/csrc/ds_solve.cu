@@ -172,6 +172,11 @@ DictDesc dict_desc(const ds_dict* d)
     dd.fmax = d->fmax;
     dd.L = d->L;
     dd.norms_in_kernel = false;
+    dd.lo_kind = d->lo_kind;
+    dd.Dlo = d->Dlo;
+    dd.ld_lo = (int)d->ld_lo;
+    dd.lo_scale = d->lo_scale;
+    dd.emax = d->emax;
     return dd;
 }
 

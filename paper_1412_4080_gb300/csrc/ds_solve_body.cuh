@@ -9,6 +9,9 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include "ds_internal.h"
 
 namespace ds {
@@ -87,6 +90,11 @@ struct SolveP {
     const double* fista;  // FISTA table: (coefficient (l_{t-1} - 1) / l_t, l_t) for t = 1..fista_n
     int fista_n;
     const volatile int* abort_flag;  // non-null: a nonzero value ends the solve at the next check
+    // low-precision working copy (precision variant): bulk iterations read it, FP32 polish follows
+    const void* Dlo;
+    int lo_kind, ld_lo;
+    const float* lo_scale;
+    double emax, gamma_lo, lo_switch;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -286,6 +294,87 @@ __device__ __forceinline__ void vdot2(float4 a, float hi0, float hi1, float hi2,
     acc.add(a.w, hi3);
 }
 
+// ---- correlation from the low-precision copy: one 512-row chunk per item, like
+// the FP32 path (BF16: two 16-byte vectors of 8 values per lane; FP8: one of 16),
+// accumulated in FP32 against theta in shared memory.
+__device__ __forceinline__ float bf16_lo(unsigned int w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned int w) { return __uint_as_float(w & 0xffff0000u); }
+__device__ __forceinline__ float dot_lo_bf16(uint4 d, float4 t0, float4 t1, float s)
+{
+    s = fmaf(bf16_lo(d.x), t0.x, s);
+    s = fmaf(bf16_hi(d.x), t0.y, s);
+    s = fmaf(bf16_lo(d.y), t0.z, s);
+    s = fmaf(bf16_hi(d.y), t0.w, s);
+    s = fmaf(bf16_lo(d.z), t1.x, s);
+    s = fmaf(bf16_hi(d.z), t1.y, s);
+    s = fmaf(bf16_lo(d.w), t1.z, s);
+    s = fmaf(bf16_hi(d.w), t1.w, s);
+    return s;
+}
+__device__ __forceinline__ float2 fp8x2_to_float2(unsigned int w16)
+{
+    const __half2_raw h = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w16 & 0xffffu), __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2*>(&h));
+}
+__device__ __forceinline__ float dot_lo_fp8_word(unsigned int w, float4 t, float s)
+{
+    const float2 a = fp8x2_to_float2(w), b = fp8x2_to_float2(w >> 16);
+    s = fmaf(a.x, t.x, s);
+    s = fmaf(a.y, t.y, s);
+    s = fmaf(b.x, t.z, s);
+    s = fmaf(b.y, t.w, s);
+    return s;
+}
+
+template <int KIND, int IPW>
+__device__ __noinline__ void gemv_lowp(const void* Dlo, int ld_lo, const float* lo_scale, const float* th_s,
+                                          float* zpart, const int* cols_s, int natoms, int nchunk, int lane, int warp,
+                                          int nw)
+{
+    constexpr int VPI = KIND == 1 ? 2 : 1;   // 16-byte vectors per item per lane
+    constexpr int EPV = KIND == 1 ? 8 : 16;  // elements per vector
+    constexpr int ES = KIND == 1 ? 2 : 1;    // bytes per element
+    const int ldv = ld_lo / EPV;
+    const float4* thv = reinterpret_cast<const float4*>(th_s);
+    const int nitems = natoms * nchunk;
+    for (int j0 = warp * IPW; j0 < nitems; j0 += nw * IPW) {
+        uint4 dv[IPW][VPI];
+        int aa[IPW], cc[IPW];
+#pragma unroll
+        for (int q = 0; q < IPW; q++) {
+            const int j = j0 + q < nitems ? j0 + q : j0;
+            aa[q] = j / nchunk;
+            cc[q] = j - aa[q] * nchunk;
+            const uint4* col =
+                reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(Dlo) + (size_t)cols_s[aa[q]] * ld_lo * ES);
+#pragma unroll
+            for (int k = 0; k < VPI; k++) {
+                const int v = cc[q] * (32 * VPI) + k * 32 + lane;
+                dv[q][k] = (j0 + q < nitems && v < ldv) ? __ldg(col + v) : make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPW; q++) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < VPI; k++) {
+                const int v = cc[q] * (32 * VPI) + k * 32 + lane;
+                if (KIND == 1) {
+                    s = dot_lo_bf16(dv[q][k], thv[2 * v], thv[2 * v + 1], s);
+                } else {
+                    s = dot_lo_fp8_word(dv[q][k].x, thv[4 * v], s);
+                    s = dot_lo_fp8_word(dv[q][k].y, thv[4 * v + 1], s);
+                    s = dot_lo_fp8_word(dv[q][k].z, thv[4 * v + 2], s);
+                    s = dot_lo_fp8_word(dv[q][k].w, thv[4 * v + 3], s);
+                }
+            }
+            s = warp_sum(s);
+            if (KIND == 2) s *= __ldg(lo_scale + cols_s[aa[q]]);
+            if (lane == 0 && j0 + q < nitems) zpart[aa[q] * nchunk + cc[q]] = s;
+        }
+    }
+}
+
 // Column slice [p_lo, p_hi) of the active list owned by CTA b, balanced in atoms
 // and cut at group boundaries.  Returns the atom offset of p_lo.
 template <typename T>
@@ -324,6 +413,14 @@ __device__ __forceinline__ void cta_slice(const SolveP<T>& P, const int* aoff, i
 
 // --------------------------------------------------------------- the kernel
 
+// Per-solve scalar state that only thread 0 of each CTA updates, kept in shared
+// memory so that it occupies no registers in the other threads.
+struct ScalarState {
+    double alpha, beta, mu_nom, R2n, R2s_last, rad, lf, s_unc, sqrt_beta, gap, primal, best_gap;
+    long long cols_corr, cols_synth, cols_lowp;
+    int iters, since_best, low, t0;  // t0: iteration at which the current FISTA sequence started
+};
+
 // One solve (or lambda path) by a team of G CTAs (rank b) that synchronise on
 // `bar`; `gen` is the calling thread's running barrier target.
 template <typename T>
@@ -347,6 +444,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     __shared__ double s_red[2][kThreads / 32][kRowTile];
     __shared__ double s_sc[16];
     __shared__ int s_si[16];
+    __shared__ ScalarState S_;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kThreads / 32;
     const Ws<T>& W = P.ws;
@@ -719,15 +817,27 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 
         int nA_g = nG, nA_a = K;  // sizes of the list `cur` refers to
         // scalar state, meaningful in thread 0 (the values every thread needs go through s_sc)
-        double alpha = 0.0, beta = 0.0, mu_nom = 0.0, R2n = 0.0, rad = 0.0, lf = 1.0;
-        double s_unc = 0.0, sqrt_beta = 0.0;
-        const double inv_lam = 1.0 / lam, yy_l2 = yy * inv_lam * inv_lam;
-        double gap = INFINITY, primal = 0.0;
-        int t = 1;
-        int iters = 0;
-        long long nnz_last = 0;
+        double &alpha = S_.alpha, &beta = S_.beta, &mu_nom = S_.mu_nom, &R2n = S_.R2n, &R2s_last = S_.R2s_last;
+        double &rad = S_.rad, &lf = S_.lf, &s_unc = S_.s_unc, &sqrt_beta = S_.sqrt_beta;
+        double &gap = S_.gap, &primal = S_.primal, &best_gap = S_.best_gap;
+        int &iters = S_.iters, &since_best = S_.since_best, &low = S_.low, &t0 = S_.t0;
         // work counters (dictionary columns read), the precompute passes charged to the first lambda
-        long long cols_corr = j == 0 ? (long long)K * (need_n ? 2 : 1) : 0, cols_synth = 0;
+        long long &cols_corr = S_.cols_corr, &cols_synth = S_.cols_synth, &cols_lowp = S_.cols_lowp;
+        if (tid == 0) {
+            alpha = beta = mu_nom = R2n = R2s_last = rad = s_unc = sqrt_beta = primal = 0.0;
+            lf = 1.0;
+            gap = best_gap = INFINITY;
+            iters = since_best = t0 = 0;
+            // precision variant: bulk phase on the low-precision copy, then FP32 polish
+            low = (P.lo_kind != 0 && sizeof(T) == 4) ? 1 : 0;
+            cols_corr = j == 0 ? (long long)K * (need_n ? 2 : 1) : 0;
+            cols_synth = cols_lowp = 0;
+        }
+        __syncthreads();
+        bool lowB = false;  // this iteration's correlation reads the low-precision copy
+        const double inv_lam = 1.0 / lam, yy_l2 = yy * inv_lam * inv_lam;
+        int t = 1;
+        long long nnz_last = 0;
         for (;; t++) {
             // ======================================== (A) scatter + synthesis
             {
@@ -787,7 +897,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 
                 // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists
                 const int E = s_pref[G];
-                cols_synth += E;
+                if (tid == 0) cols_synth += E;
                 Acc pa_, pb_, pr_;
                 const int ntiles = (N + kRowTile - 1) / kRowTile;
                 for (int tile = b; tile < ntiles; tile += G) {
@@ -895,6 +1005,26 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             primal = 0.5 * r_ + lam * l1;
                             gap = primal - 0.5 * yy + 0.5 * lam * lam * R2n;
                             iters = t - 1;
+                            if (low) {
+                                // the nominal gap rests on the copy's correlations: stop only on the
+                                // rigorous one (dual point scaled with the bounded max), and switch to the
+                                // FP32 master once the bulk phase reaches its tolerance or stalls
+                                const double gap_safe = primal - 0.5 * yy + 0.5 * lam * lam * R2s_last;
+                                if (gap < 0.99 * best_gap) {
+                                    best_gap = gap;
+                                    since_best = 0;
+                                } else {
+                                    since_best++;
+                                }
+                                if (!(P.tol > 0.0 && gap_safe <= P.tol * 0.5 * yy) &&
+                                    (gap <= P.lo_switch * 0.5 * yy || since_best >= 25)) {
+                                    // FP32 polish: a fresh FISTA sequence warm-started at the bulk iterate
+                                    low = 0;
+                                    t0 = t - 1;
+                                    lf = 1.0;
+                                }
+                                gap = gap_safe;
+                            }
                             if (record && b == 0 && t - 1 <= P.hist_rows) {
                                 double* h = P.hist + (size_t)(t - 2) * 6;
                                 h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
@@ -913,9 +1043,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         if (!ista) {
                             // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
                             // read from the table (the sequence depends on t only)
-                            if (t <= P.fista_n) {
-                                bt = P.fista[2 * (t - 1)];
-                                lf = P.fista[2 * (t - 1) + 1];
+                            const int tf = t - t0;  // index in the current FISTA sequence
+                            if (tf <= P.fista_n) {
+                                bt = P.fista[2 * (tf - 1)];
+                                lf = P.fista[2 * (tf - 1) + 1];
                             } else {
                                 const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
                                 bt = (lf - 1.0) / ln;
@@ -924,14 +1055,19 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                         s_sc[10] = bt;
                         s_si[3] = (int)ng; s_si[4] = (int)na; s_si[5] = (int)nx; s_si[6] = stop;
+                        s_si[9] = low;
                     }
                 }
                 __syncthreads();
                 nA_g = s_si[3];
                 nA_a = s_si[4];
                 nnz_last = s_si[5];
+                lowB = s_si[9] != 0;
                 if (s_si[6]) break;
-                cols_corr += nA_a;
+                if (tid == 0) {
+                    cols_corr += nA_a;
+                    if (lowB) cols_lowp += nA_a;
+                }
 
                 // stage theta_t
                 for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? __ldcg(W.theta + r) : T(0);
@@ -975,7 +1111,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     __syncthreads();
                     // z = D_A^T theta: items (atom, row chunk), two per warp in flight
                     const int nchunk = P.nchunk;
-                    const int nitems = natoms * nchunk;
+                    const int nitems = lowB ? 0 : natoms * nchunk;
+                    if constexpr (sizeof(T) == 4) {
+                        if (lowB && P.lo_kind == 1)
+                            gemv_lowp<1, 4>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
+                                            reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
+                        else if (lowB)
+                            gemv_lowp<2, 8>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
+                                            reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
+                    }
                     for (int j0 = warp * 2; j0 < nitems; j0 += nw * 2) {
                         const int j1 = j0 + 1;
                         const bool h1 = j1 < nitems;
@@ -1073,12 +1217,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     if (lane == 0) {
                         // Lemma 8 with the nominal max |z| (for the gap) and with a rigorous upper
                         // bound on it given the FP rounding of z (for the screening radius)
-                        const double m_up = m_nom + P.gamma * sqrt_beta * fmax_d;
+                        // (copy: |z_i - zlo_i| <= ||d_i - dlo_i|| ||theta|| + the FP32 rounding of dlo_i^T theta)
+                        const double m_up = m_nom + (lowB ? P.emax + P.gamma_lo * (fmax_d + P.emax) : P.gamma * fmax_d) *
+                                                        sqrt_beta;
                         mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
                         const double mu_s = (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) ? copysign(fast_rcp(m_up), s_unc) : s_unc;
                         // R^2 = ||y/lambda - mu theta||^2
                         R2n = fmax(fma(mu_nom, fma(mu_nom, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
                         const double R2s = fmax(fma(mu_s, fma(mu_s, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
+                        R2s_last = R2s;
                         // radii rounded up a little: a larger radius only screens less
                         const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
                         rad = (P.test == 2 || P.test == 5) ? fast_sqrt(fmax(R2s - delta * delta, 0.0)) * (1.0 + 1e-13) : Rs;
@@ -1210,6 +1357,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 R->lambda_max = lstar;
                 R->cols_corr = cols_corr;
                 R->cols_synth = cols_synth;
+                R->cols_lowp = cols_lowp;
             }
         }
         ok = grid_sync(bar, G, gen);
@@ -1326,6 +1474,20 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.fista = nullptr;
     P.fista_n = 0;
     P.abort_flag = nullptr;
+    P.Dlo = dd.Dlo;
+    P.lo_kind = sizeof(T) == 4 ? dd.lo_kind : 0;
+    P.ld_lo = dd.ld_lo;
+    P.lo_scale = dd.lo_scale;
+    P.emax = dd.emax;
+    {
+        // rounding of the copy's FP32 accumulation: 16 FMAs a lane, 5 shuffles, the chunks, the FP8 scale
+        const double u = std::ldexp(1.0, -24);
+        const double k = 16 + 5 + g.nchunk + 1;
+        P.gamma_lo = 1.01 * k * u / (1.0 - k * u);
+    }
+    // default: the bulk phase runs until its nominal gap reaches the target (or stalls);
+    // the FP32 iterations then only have to certify it
+    P.lo_switch = (opt && opt->lowp_switch > 0.0) ? opt->lowp_switch : ((opt && opt->tol_gap_rel > 0.0) ? opt->tol_gap_rel : 1e-6);
 }
 
 }  // namespace ds

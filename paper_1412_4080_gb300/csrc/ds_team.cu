@@ -716,6 +716,7 @@ static void server_harvest(ds_server* S)
             t.res.lambda_max = r.lambda_max;
             t.res.cols_corr = r.cols_corr;
             t.res.cols_synth = r.cols_synth;
+            t.res.cols_lowp = r.cols_lowp;
             t.res.ms = now_ms() - t.t_submit;  // latency: submission to completion observed by the host
             t.state = 2;
             S->alloc.release(t.off, t.bytes);
