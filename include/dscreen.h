@@ -74,6 +74,9 @@ typedef struct {
     double lowp_switch; /* dictionaries with a BF16/FP8 copy: relative gap at which the solve leaves the
                            copy for the FP32 master (also left after 25 iterations without 1% progress);
                            <= 0: the gap tolerance (1e-6 when it is 0) */
+    int batch_multi_rhs; /* batches: 1 (default) solves the right-hand sides of an FP32 Lasso instance
+                            together, up to 64 per block, so each dictionary column read serves them all;
+                            0 runs every (instance, rhs) problem on its own */
 } ds_options;
 
 typedef struct {
@@ -187,6 +190,20 @@ ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const
 ds_status ds_batch_run(ds_batch* batch, ds_result* res);
 /* Whether the run replays a CUDA graph, and the team layout chosen. */
 ds_status ds_batch_info(const ds_batch* batch, int* uses_graph, int* teams, int* team_size);
+/* How the batch's problems run (any output pointer may be NULL):
+ *   multi_rhs_blocks: blocks of up to 64 right-hand sides of one FP32 Lasso
+ *     instance solved together (opt->batch_multi_rhs, tests NONE/SAFE/DST3/DOME,
+ *     instances with >= 2 right-hand sides).  A block runs Algorithm 3 for all
+ *     its problems in lockstep: the correlation of every iteration is one
+ *     contraction D_A^T [theta_1 ... theta_R] over the union A of their active
+ *     sets, so each dictionary column read serves all of them; screening,
+ *     iterates, gaps and stopping stay per problem, and a problem leaves the
+ *     block when its gap is met.  multi_rhs_teams / multi_rhs_team_size: the
+ *     persistent launch that runs the blocks;
+ *   single_problems: (instance, rhs) problems run one per team as above.
+ * Errors: DS_ERR_INVALID on NULL batch. */
+ds_status ds_batch_layout(const ds_batch* batch, int* multi_rhs_blocks, int* multi_rhs_teams, int* multi_rhs_team_size,
+                          int* single_problems);
 ds_status ds_batch_destroy(ds_batch* batch);
 /* One-shot form: create, run once, destroy. */
 ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,

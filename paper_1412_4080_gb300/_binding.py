@@ -38,7 +38,8 @@ HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
 class ds_options(ctypes.Structure):
     _fields_ = [("alg", ctypes.c_int), ("test", ctypes.c_int), ("dynamic", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
-                ("lambda_rel", ctypes.c_int), ("lowp_switch", ctypes.c_double)]
+                ("lambda_rel", ctypes.c_int), ("lowp_switch", ctypes.c_double),
+                ("batch_multi_rhs", ctypes.c_int)]
 
 
 class ds_result(ctypes.Structure):
@@ -96,6 +97,7 @@ def lib():
             L.ds_batch_run.argtypes = [vp, vp]
             L.ds_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]
+            L.ds_batch_layout.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
             L.ds_batch_destroy.argtypes = [vp]
             L.ds_solve_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp, vp]
             L.ds_server_create.argtypes = [vp, ctypes.c_size_t, i64, i64, ctypes.c_int, ctypes.POINTER(vp)]
@@ -273,6 +275,13 @@ def ds_batch_info(batch):
     g, t, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().ds_batch_info(batch.h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(s)), "ds_batch_info")
     return {"uses_graph": bool(g.value), "teams": t.value, "team_size": s.value}
+
+
+def ds_batch_layout(batch):
+    v = [ctypes.c_int() for _ in range(4)]
+    _check(lib().ds_batch_layout(batch.h, *[ctypes.byref(x) for x in v]), "ds_batch_layout")
+    return {"multi_rhs_blocks": v[0].value, "multi_rhs_teams": v[1].value, "multi_rhs_team_size": v[2].value,
+            "single_problems": v[3].value}
 
 
 def ds_batch_destroy(batch):

@@ -121,6 +121,7 @@ ds_status ds_options_default(ds_options* opt)
     opt->L = 0.0;
     opt->lambda_rel = 0;
     opt->lowp_switch = 0.0;
+    opt->batch_multi_rhs = 1;
     return DS_OK;
 }
 

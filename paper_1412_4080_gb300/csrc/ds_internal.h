@@ -117,6 +117,28 @@ ds_status launch_lambda_max(ds_ctx* ctx, const ds_dict* dict, const void* y_dev,
 ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host);
 ds_status dict_lowp(ds_ctx* ctx, ds_dict* dict, int kind);
 
+// Right-hand sides sharing a dictionary, solved together (ds_mrhs.cu): a block
+// is up to 64 problems of one FP32 Lasso dictionary, y_r at Y + r * N and x_r at
+// X + r * K; inst / r0 locate the block in the caller's batch.
+struct MrhsBlock {
+    const ds_dict* dict;
+    const void* Y;
+    int R;
+    void* X;
+    int inst, r0;
+};
+struct MrhsPlan;
+constexpr int kMrhsMaxR = 64;
+ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, const ds_options* opt,
+                           const double* fista_dev, int fista_n, MrhsPlan** out);
+const MrhsBlock* mrhs_plan_blocks(const MrhsPlan* M, int* n);  // in job order
+double* mrhs_plan_lambdas(MrhsPlan* M);                        // pinned, [job][kMrhsMaxR]
+const DevResult* mrhs_plan_results(const MrhsPlan* M);         // pinned, [job][kMrhsMaxR]
+ds_status mrhs_plan_enqueue(MrhsPlan* M, cudaStream_t s);
+int* mrhs_plan_error_flag(MrhsPlan* M);                        // device int
+void mrhs_plan_info(const MrhsPlan* M, int* teams, int* team_size);
+void mrhs_plan_destroy(MrhsPlan* M);
+
 // Workspace helpers (ds_api.cu).
 ds_status ctx_reserve(ds_ctx* ctx, size_t bytes);
 ds_status ctx_fista_table(ds_ctx* ctx, int n);

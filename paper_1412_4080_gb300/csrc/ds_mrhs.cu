@@ -1,0 +1,1341 @@
+// ds_mrhs.cu -- right-hand sides that share a dictionary, solved together.
+//
+// A block of up to 64 Lasso problems on one FP32 dictionary (each with its own
+// y and lambda) runs Algorithm 3 in lockstep on a team of CTAs.  What the
+// problems share is the dominant cost: every iteration correlates the union of
+// their active sets with all their dual points at once,
+//
+//     Z = D_A^T [theta_1 ... theta_R]       (A = union of the active sets),
+//
+// a dense contraction in which each dictionary entry loaded from HBM (or L2)
+// is used R times from shared memory, instead of once per problem.  Everything
+// that differs between the problems stays per problem: y, lambda, lambda_*,
+// d_*, the screening radius (Lemmas 2-4, 8), the screened set (a 64-bit mask
+// per atom), the iterates, the nonzero lists of the syntheses and the stopping
+// rule.  A problem that meets its gap tolerance is written out and leaves the
+// block; the contraction then runs over the remaining ones only.
+//
+// Per iteration, three team phases separated by the bounded barrier:
+//   (A) compaction of the union list; syntheses theta_r = D u_r - y_r and
+//       D x_r over each problem's nonzeros (compensated, row tiles of 64);
+//   (B) gaps and stopping per problem; Z over tiles of 128 atoms x 64 problems
+//       (register-tiled FP32 FMA on operands staged by cp.async, split over
+//       rows when the list is short, the last CTA of a tile summing the row
+//       splits in a fixed order), fused with the proximal step;
+//   (C) per problem: dual scaling, radius, test; FISTA extrapolation; the next
+//       nonzero lists (lanes run over problems, so per-problem arrays are
+//       contiguous).
+// Reductions run in a fixed order, so results do not depend on timing.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ds_solve_body.cuh"
+
+namespace ds {
+
+constexpr int kMR = kMrhsMaxR;     // problems per block
+constexpr int kMTA = 128;          // atoms per correlation tile
+constexpr int kMKC = 32;           // rows per staged chunk
+constexpr int kMST = kMKC + 4;     // shared row stride (floats): conflict-free 16-byte reads
+constexpr int kMSynRows = 64;      // rows per synthesis item (two per lane)
+constexpr int kMW = kThreads / 32; // warps per CTA
+constexpr int kMMaxSplit = 8;      // row splits of a correlation tile
+
+struct MrhsWs {
+    float* Yt;   // [kMR][npad] y, zero padded
+    float* Th;   // [kMR][npad] theta
+    float* Dst;  // [kMR][npad] d_* of each problem (precompute)
+    double* Q0;  // [K][kMR] D^T y; then SAFE/DST3 thresholds, or (Dome) d_i^T y / ||d_i||
+    double* Q1;  // [K][kMR] D^T d_*; then (Dome) t_i = d_i^T d_* / (||d_i|| ||d_*||)
+    double* Q2;  // [K][kMR] (Dome) sqrt(1 - t_i^2)
+    double* invn;  // [K] 1 / ||d_i||
+    FF* xb[2];   // [K][kMR] iterates x (two generations)
+    FF* u;       // [K][kMR] extrapolated points
+    unsigned long long* amask;   // [K] problems for which atom i is still active
+    unsigned long long* nzmask;  // [K] problems for which (u_i, x_i) != 0
+    int* act[2];  // union active list (two generations)
+    int* keep;    // [K] per list position: atom stays
+    int* nz_col;  // [kMR][K] nonzero lists, per CTA segment
+    FF* nz_u;
+    FF* nz_x;
+    float* part;  // row-split partial tiles
+    int* tilecnt; // per tile: row splits finished
+    float* p_m;   // [kMR][G] max |z| per CTA
+    FF* p_l1;     // [kMR][G]
+    int* c_na;    // [kMR][G]
+    int* c_nnzx;  // [kMR][G]
+    int* c_nz;    // [kMR][G] nonzero-list lengths
+    int* c_keep;  // [G]
+    int* s_alo;   // [G] start of each CTA's list segment
+    double* p_v;  // [kMR][G] max |d_i^T y| per CTA
+    int* p_i;     // [kMR][G] its lowest index
+    FF* p_a;      // [kMR][ntile] theta^T y per row tile
+    FF* p_b;      // [kMR][ntile] ||theta||^2
+    FF* p_r;      // [kMR][ntile] ||D x - y||^2
+};
+
+struct MrhsP {
+    const float* D;
+    int N, K, ld, npad, ntile;
+    const double* colnorm;
+    double fmax, L, gamma, eps_test, tol;
+    int alg, test, dynamic, max_iter, lambda_rel;
+    const float* Y;          // problem r: y at Y + r * N
+    int R;                   // problems in the block (<= kMR)
+    const double* lambdas;   // R entries (device)
+    float* X;                // problem r: x at X + r * K
+    DevResult* res;          // R entries
+    const double* fista;
+    int fista_n;
+    MrhsWs ws;
+};
+
+struct MrhsShared {
+    float Ds[2][kMTA][kMST];
+    float Ts[2][kMR][kMST];
+    int cols[kMTA];
+    int slot_r[kMR];       // live slot -> problem (-1 past the live ones)
+    int dir[kMW][kMaxG + 1];
+    int alo[kMaxG];
+    int cnt[kMW][kMR];
+    float red_s[kMW][kMR], red_c[kMW][kMR];
+    int red_na[kMW][kMR], red_nx[kMW][kMR];
+    double bv[kMW][kMR];
+    int bi[kMW][kMR];
+    unsigned int zmax[kMR];
+    double lam[kMR], yy[kMR], lstar[kMR], psi_d[kMR], coef[kMR], delta[kMR], nstar[kMR];
+    double alpha[kMR], beta[kMR], s_unc[kMR], sqrt_beta[kMR], R2n[kMR], rad[kMR], Rs[kMR], rho[kMR];
+    double gap[kMR], primal[kMR];
+    FF thrX[kMR];
+    int istar[kMR], iters[kMR], na[kMR], nnzx[kMR], stopnow[kMR];
+    long long csyn[kMR];
+    unsigned long long live;
+    int n_slots, nA, last;
+    long long ccorr;
+    double bt, lf;
+    int ired[kMW];
+    int scan_tmp[32];
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One compensated product-accumulation (TwoProduct by FMA, Knuth's TwoSum);
+// the explicitly rounded operations keep the compiler from contracting them.
+__device__ __forceinline__ void d2_add(float& s, float& c, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float bb = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ void d2_merge(float& s, float& c, float s2, float c2)
+{
+    const float t = __fadd_rn(s, s2);
+    const float bb = __fsub_rn(t, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bb)), __fsub_rn(s2, bb));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(e, c2));
+}
+
+// Z tile = D[:, cols]^T Theta[:, slots] over row chunks [c_lo, c_hi) of 32 rows.
+// Thread (ta, tr) owns atoms ta + 32j (j < 4) and slots tr + 16q (q < JJ).
+// COMP: compensated sums (s in acc, error in cmp); otherwise cmp holds the
+// chunk's partial sum, added to acc once per chunk (two-level summation keeps
+// the rounding bound at 32 + chunks terms).
+template <int JJ, bool COMP>
+__device__ __forceinline__ void mr_gemm(MrhsShared& S, const float* __restrict__ D, int ld,
+                                        const float* __restrict__ Th, int ldt, int c_lo, int c_hi, float (&acc)[4][4],
+                                        float (&cmp)[4][4])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            acc[j][q] = 0.f;
+            cmp[j][q] = 0.f;
+        }
+    if (c_lo >= c_hi) return;
+    auto issue = [&](int c, int buf) {
+        const int n0 = c * kMKC;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int qd = tid + h * kThreads;
+            const int a = qd >> 3, v = qd & 7;
+            const int col = S.cols[a];
+            const int n = n0 + 4 * v;
+            const bool ok = col >= 0 && n < ld;  // rows N..ld-1 of the owned copy are zero
+            const float* src = ok ? D + (size_t)col * ld + n : D;
+            cp_async16(&S.Ds[buf][a][4 * v], src, ok ? 16 : 0);
+        }
+        if (tid < JJ * 16 * 8) {
+            const int s = tid >> 3, v = tid & 7;
+            const int r = S.slot_r[s];
+            const bool ok = r >= 0;
+            const float* src = ok ? Th + (size_t)r * ldt + n0 + 4 * v : Th;
+            cp_async16(&S.Ts[buf][s][4 * v], src, ok ? 16 : 0);
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    issue(c_lo, 0);
+    for (int c = c_lo; c < c_hi; c++) {
+        if (c + 1 < c_hi) {
+            issue(c + 1, buf ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k4 = 0; k4 < kMKC / 4; k4++) {
+            float4 a4[4], t4[JJ];
+#pragma unroll
+            for (int j = 0; j < 4; j++) a4[j] = *reinterpret_cast<const float4*>(&S.Ds[buf][ta + 32 * j][4 * k4]);
+#pragma unroll
+            for (int q = 0; q < JJ; q++) t4[q] = *reinterpret_cast<const float4*>(&S.Ts[buf][tr + 16 * q][4 * k4]);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int q = 0; q < JJ; q++) {
+                    if (COMP) {
+                        d2_add(acc[j][q], cmp[j][q], a4[j].x, t4[q].x);
+                        d2_add(acc[j][q], cmp[j][q], a4[j].y, t4[q].y);
+                        d2_add(acc[j][q], cmp[j][q], a4[j].z, t4[q].z);
+                        d2_add(acc[j][q], cmp[j][q], a4[j].w, t4[q].w);
+                    } else {
+                        cmp[j][q] = fmaf(a4[j].x, t4[q].x, cmp[j][q]);
+                        cmp[j][q] = fmaf(a4[j].y, t4[q].y, cmp[j][q]);
+                        cmp[j][q] = fmaf(a4[j].z, t4[q].z, cmp[j][q]);
+                        cmp[j][q] = fmaf(a4[j].w, t4[q].w, cmp[j][q]);
+                    }
+                }
+        }
+        if (!COMP) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int q = 0; q < JJ; q++) {
+                    acc[j][q] += cmp[j][q];
+                    cmp[j][q] = 0.f;
+                }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+}
+
+template <bool COMP>
+__device__ __forceinline__ void mr_gemm_any(int JJ, MrhsShared& S, const float* D, int ld, const float* Th, int ldt,
+                                            int c_lo, int c_hi, float (&acc)[4][4], float (&cmp)[4][4])
+{
+    switch (JJ) {
+        case 1: mr_gemm<1, COMP>(S, D, ld, Th, ldt, c_lo, c_hi, acc, cmp); break;
+        case 2: mr_gemm<2, COMP>(S, D, ld, Th, ldt, c_lo, c_hi, acc, cmp); break;
+        case 3: mr_gemm<3, COMP>(S, D, ld, Th, ldt, c_lo, c_hi, acc, cmp); break;
+        default: mr_gemm<4, COMP>(S, D, ld, Th, ldt, c_lo, c_hi, acc, cmp); break;
+    }
+}
+
+// Row splits of the tiles: fill the team's CTAs in whole waves where possible.
+__device__ __forceinline__ int mr_splits(int TA, int G, int nc)
+{
+    if (TA >= G) return 1;
+    int best = 1;
+    double best_eff = 0.0;
+    const int smax = min(kMMaxSplit, max(1, nc / 2));
+    for (int s = 1; s <= smax; s++) {
+        const double w = (double)TA * s / G;
+        const double eff = w / ceil(w);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = s;
+        }
+    }
+    return best;
+}
+
+// The tiles of `nA` list atoms (ids from `list`, or the identity when null),
+// split over rows; calls epi(acc, cmp) in the CTA that finishes a tile, with
+// S.cols holding the tile's atoms.  Returns false on a failed wait.
+template <bool COMP, typename Epi>
+__device__ __forceinline__ void mr_tiles(MrhsShared& S, const MrhsP& P, const int* list, int nA, const float* Th,
+                                         int JJ, int b, int G, Epi epi)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
+    const MrhsWs& W = P.ws;
+    const int TA = (nA + kMTA - 1) / kMTA;
+    const int nc = P.npad / kMKC;
+    const int Sk = mr_splits(TA, G, nc);
+    const int items = TA * Sk;
+    constexpr int TS = kMTA * kMR * (COMP ? 2 : 1);
+    for (int it = b; it < items; it += G) {
+        const int ti = it / Sk, sk = it - ti * Sk;
+        const int c_lo = sk * nc / Sk, c_hi = (sk + 1) * nc / Sk;
+        if (tid < kMTA) {
+            const int p = ti * kMTA + tid;
+            S.cols[tid] = p < nA ? (list ? __ldcg(list + p) : p) : -1;
+        }
+        __syncthreads();
+        float acc[4][4], cmp[4][4];
+        mr_gemm_any<COMP>(JJ, S, P.D, P.ld, Th, P.npad, c_lo, c_hi, acc, cmp);
+        bool fin = true;
+        if (Sk > 1) {
+            float* pt = W.part + (size_t)it * TS;
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (q < JJ) {
+                        const int o = (ta + 32 * j) * kMR + tr + 16 * q;
+                        pt[o] = acc[j][q];
+                        if (COMP) pt[kMTA * kMR + o] = cmp[j][q];
+                    }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) S.last = (atomicAdd(W.tilecnt + ti, 1) == Sk - 1);
+            __syncthreads();
+            fin = S.last != 0;
+            if (fin) {
+                __threadfence();
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (q < JJ) {
+                            const int o = (ta + 32 * j) * kMR + tr + 16 * q;
+                            float s = 0.f, c = 0.f;
+                            for (int s2 = 0; s2 < Sk; s2++) {
+                                const float* ps = W.part + (size_t)(ti * Sk + s2) * TS;
+                                if (COMP) d2_merge(s, c, __ldcg(ps + o), __ldcg(ps + kMTA * kMR + o));
+                                else s += __ldcg(ps + o);
+                            }
+                            acc[j][q] = s;
+                            cmp[j][q] = c;
+                        }
+                if (tid == 0) W.tilecnt[ti] = 0;
+            }
+        }
+        if (fin) epi(acc, cmp);
+        __syncthreads();
+    }
+}
+
+// Sum of n float-float partials in a fixed order (one warp).
+__device__ __forceinline__ double mr_ff_sum(const FF* p, int n, int lane) { return part_sum_fixed(p, n, lane); }
+__device__ __forceinline__ int mr_int_sum(const int* p, int n, int lane) { return (int)warp_sum_fixed(p, n, lane); }
+
+// --------------------------------------------------------------- the body
+
+// One block of problems by a team of G CTAs (rank b) on barrier `bar`.
+__device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G, GridBarrier* bar, unsigned int& gen)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MrhsShared& S = *reinterpret_cast<MrhsShared*>(smem_raw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
+    const MrhsWs& W = P.ws;
+    const int N = P.N, K = P.K, ld = P.ld, npad = P.npad, ntile = P.ntile, R = P.R;
+    const int gwarp = b * kMW + warp, twarps = G * kMW;
+    const bool dome = P.test == 3;
+    const bool need_n = P.test == 2 || P.test == 3;
+    const bool ista = P.alg == 0;
+    const float invL = (float)(1.0 / P.L);
+
+    // -------------------------------------------- (C0a) staging, ||y_r||^2
+    if (tid < kMR) S.slot_r[tid] = tid < R ? tid : -1;
+    if (tid == 0) S.n_slots = R;
+    for (size_t k = (size_t)b * kThreads + tid; k < (size_t)kMR * npad; k += (size_t)G * kThreads) {
+        const int r = (int)(k / npad), n = (int)(k - (size_t)r * npad);
+        W.Yt[k] = (r < R && n < N) ? P.Y[(size_t)r * N + n] : 0.f;
+        W.Th[k] = 0.f;
+        W.Dst[k] = 0.f;
+    }
+    for (size_t k = (size_t)b * kThreads + tid; k < (size_t)R * K; k += (size_t)G * kThreads) {
+        const int r = (int)(k / K);
+        P.X[(size_t)r * K + (k - (size_t)r * K)] = 0.f;
+    }
+    for (int k = b * kThreads + tid; k < (K + kMTA - 1) / kMTA; k += G * kThreads) W.tilecnt[k] = 0;
+    for (int it = gwarp; it < ntile * R; it += twarps) {
+        const int r = it / ntile, rt = it - r * ntile;
+        Dot2f acc;
+        for (int k = 0; k < kMSynRows / 32; k++) {
+            const int n = rt * kMSynRows + 32 * k + lane;
+            if (n < N) {
+                const float v = P.Y[(size_t)r * N + n];
+                acc.add(v, v);
+            }
+        }
+        acc = dot2_warp_reduce(acc);
+        if (lane == 0) W.p_a[r * ntile + rt] = FF{acc.s, acc.c};
+    }
+    if (!grid_sync(bar, G, gen)) return false;
+
+    // -------------------------------------------- (C0b) B = D^T Y (compensated), lambda_*
+    for (int r = warp; r < R; r += kMW) {
+        const double s = mr_ff_sum(W.p_a + r * ntile, ntile, lane);
+        if (lane == 0) S.yy[r] = s;
+    }
+    {
+        const int JJ = (R + 15) / 16;
+        double best[4];
+        int arg[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) { best[q] = -1.0; arg[q] = 0x7fffffff; }
+        mr_tiles<true>(S, P, nullptr, K, W.Yt, JJ, b, G, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int i = S.cols[ta + 32 * j];
+                if (i < 0) continue;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (q >= JJ) continue;
+                    const int r = S.slot_r[tr + 16 * q];
+                    if (r < 0) continue;
+                    const double v = (double)acc[j][q] + (double)cmp[j][q];
+                    W.Q0[(size_t)i * kMR + r] = v;
+                    const double a = fabs(v);
+                    if (a > best[q] || (a == best[q] && i < arg[q])) { best[q] = a; arg[q] = i; }
+                }
+            }
+        });
+        // per-CTA argmax: the two halves of each warp, then the warps in order
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best[q], 16);
+            const int oa = __shfl_xor_sync(0xffffffffu, arg[q], 16);
+            if (ob > best[q] || (ob == best[q] && oa < arg[q])) { best[q] = ob; arg[q] = oa; }
+            if (lane < 16 && q < JJ) { S.bv[warp][tr + 16 * q] = best[q]; S.bi[warp][tr + 16 * q] = arg[q]; }
+        }
+        __syncthreads();
+        if (tid < R) {
+            double bb = -1.0;
+            int ba = 0x7fffffff;
+            for (int w = 0; w < kMW; w++)
+                if (S.bv[w][tid] > bb || (S.bv[w][tid] == bb && S.bi[w][tid] < ba)) { bb = S.bv[w][tid]; ba = S.bi[w][tid]; }
+            W.p_v[tid * G + b] = bb;
+            W.p_i[tid * G + b] = ba;
+        }
+    }
+    if (!grid_sync(bar, G, gen)) return false;
+
+    // -------------------------------------------- (C0c) per problem: lambda, the test centres
+    for (int r = warp; r < R; r += kMW) {
+        double bb = -1.0;
+        int ba = 0x7fffffff;
+        for (int k = lane; k < G; k += 32) {
+            const double v = __ldcg(W.p_v + r * G + k);
+            const int a = __ldcg(W.p_i + r * G + k);
+            if (v > bb || (v == bb && a < ba)) { bb = v; ba = a; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, bb, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, ba, o);
+            if (ob > bb || (ob == bb && oa < ba)) { bb = ob; ba = oa; }
+        }
+        if (lane == 0) {
+            const double lstar = bb;
+            const double lam = P.lambda_rel ? P.lambdas[r] * lstar : P.lambdas[r];
+            S.lstar[r] = lstar;
+            S.istar[r] = ba;
+            S.lam[r] = lam;
+            S.thrX[r] = ff_from_double(lam / P.L);
+            const double nstar = P.colnorm[ba];
+            const double psi = lstar / lam - 1.0;
+            // Lasso: n = d_* (Lemma 3), n^T y = lambda_*, ||n|| = ||d_*||
+            const double nn = nstar * nstar;
+            S.nstar[r] = nstar;
+            S.psi_d[r] = psi / nstar;
+            S.coef[r] = need_n ? psi / nn : 0.0;
+            S.delta[r] = need_n ? fabs(psi) / nstar : 0.0;
+            S.csyn[r] = 0;
+            S.R2n[r] = 0.0;
+            S.gap[r] = INFINITY;
+            S.primal[r] = 0.0;
+            S.iters[r] = 0;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long live = 0;
+        for (int r = 0; r < R; r++)
+            if (S.lam[r] < S.lstar[r]) live |= 1ull << r;
+        S.live = live;
+        S.ccorr = (long long)K * (need_n ? 2 : 1);
+        S.lf = 1.0;
+        int k = 0;
+        for (int r = 0; r < kMR; r++)
+            if ((live >> r) & 1) S.slot_r[k++] = r;
+        S.n_slots = k;
+        for (int q = k; q < kMR; q++) S.slot_r[q] = -1;
+    }
+    __syncthreads();
+    // problems with lambda >= lambda_*: x = 0, y / lambda is dual optimal (Sec. 2.2.2)
+    if (b == 0 && tid < R && !((S.live >> tid) & 1)) {
+        DevResult& o = P.res[tid];
+        o.iters = 0; o.status = kDevOk; o.n_active = 0; o.nnz = 0; o.gap = 0.0;
+        o.primal = 0.5 * S.yy[tid]; o.dual = 0.5 * S.yy[tid]; o.lambda = S.lam[tid]; o.lambda_max = S.lstar[tid];
+        o.cols_corr = S.ccorr; o.cols_synth = 0; o.cols_lowp = 0;
+    }
+    if (need_n && S.live) {
+        // d_* = sign(b_{i*}) d_{i*} of every problem (Lemma 3)
+        for (size_t k = (size_t)b * kThreads + tid; k < (size_t)R * npad; k += (size_t)G * kThreads) {
+            const int r = (int)(k / npad), n = (int)(k - (size_t)r * npad);
+            float v = 0.f;
+            if (((S.live >> r) & 1) && n < N) {
+                const int is = S.istar[r];
+                const float d = P.D[(size_t)is * ld + n];
+                v = __ldcg(W.Q0 + (size_t)is * kMR + r) < 0.0 ? -d : d;
+            }
+            W.Dst[k] = v;
+        }
+        if (!grid_sync(bar, G, gen)) return false;
+        const int JJ = (S.n_slots + 15) / 16;
+        mr_tiles<true>(S, P, nullptr, K, W.Dst, JJ, b, G, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int i = S.cols[ta + 32 * j];
+                if (i < 0) continue;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if (q >= JJ) continue;
+                    const int r = S.slot_r[tr + 16 * q];
+                    if (r < 0) continue;
+                    W.Q1[(size_t)i * kMR + r] = (double)acc[j][q] + (double)cmp[j][q];
+                }
+            }
+        });
+        if (!grid_sync(bar, G, gen)) return false;
+    }
+
+    // -------------------------------------------- (C0d) thresholds, static test, initial state
+    {
+        const int p_lo = (int)((long long)b * K / G), p_hi = (int)((long long)(b + 1) * K / G);
+        const int w_lo = p_lo + (int)((long long)warp * (p_hi - p_lo) / kMW);
+        const int w_hi = p_lo + (int)((long long)(warp + 1) * (p_hi - p_lo) / kMW);
+        const bool stat = !P.dynamic && P.test != 0;
+        const unsigned long long live = S.live;
+        double rad0[2] = {0.0, 0.0}, R0[2] = {0.0, 0.0};
+        for (int h = 0; h < 2; h++) {
+            const int r = lane + 32 * h;
+            if (stat && ((live >> r) & 1)) {
+                // Algorithm 1: the test at theta = -y, with m = lambda_*
+                const double lam = S.lam[r], yy = S.yy[r];
+                const double mu = dual_scale(-yy, yy, lam, S.lstar[r] * (1.0 + 1e-12));
+                const double R2 = fmax(yy / (lam * lam) + 2.0 * mu * yy / lam + mu * mu * yy, 0.0);
+                R0[h] = sqrt(R2);
+                rad0[h] = P.test == 2 ? sqrt(fmax(R2 - S.delta[r] * S.delta[r], 0.0)) : R0[h];
+            }
+        }
+        int kept = 0;
+        for (int i = w_lo; i < w_hi; i++) {
+            const double inv = 1.0 / P.colnorm[i];
+            if (lane == 0) W.invn[i] = inv;
+            bool on[2];
+            for (int h = 0; h < 2; h++) {
+                const int r = lane + 32 * h;
+                const size_t idx = (size_t)i * kMR + r;
+                on[h] = (live >> r) & 1;
+                if (on[h] && P.test != 0) {
+                    const double bi = __ldcg(W.Q0 + idx), lam = S.lam[r];
+                    bool kill = false;
+                    if (!dome) {
+                        // sphere tests (Lemmas 2, 3): (1 - |d_i^T c|) / ||d_i||
+                        const double dtc = bi / lam - (P.test == 2 ? S.coef[r] * __ldcg(W.Q1 + idx) : 0.0);
+                        const double th = (1.0 - fabs(dtc)) * inv;
+                        W.Q0[idx] = th;
+                        kill = stat && th - rad0[h] > P.eps_test;
+                    } else {
+                        const double dc = bi * inv;
+                        const double tt = __ldcg(W.Q1 + idx) * inv / S.nstar[r];
+                        const double sq = sqrt(fmax(1.0 - tt * tt, 0.0));
+                        W.Q0[idx] = dc;
+                        W.Q1[idx] = tt;
+                        W.Q2[idx] = sq;
+                        if (stat) {
+                            const double dc0 = dc / lam, psi = S.psi_d[r], Rr = R0[h];
+                            const double rho = sqrt(fmax(Rr * Rr - psi * psi, 0.0));
+                            const double up = (tt * Rr <= -psi) ? dc0 + Rr : dc0 - psi * tt + rho * sq;
+                            const double dn = (-tt * Rr <= -psi) ? -dc0 + Rr : -dc0 + psi * tt + rho * sq;
+                            kill = (inv - up > P.eps_test) && (inv - dn > P.eps_test);
+                        }
+                    }
+                    if (kill) on[h] = false;
+                }
+                W.xb[0][idx] = FF{0.f, 0.f};
+                W.xb[1][idx] = FF{0.f, 0.f};
+                W.u[idx] = FF{0.f, 0.f};
+            }
+            const unsigned lo = __ballot_sync(0xffffffffu, on[0]), hi = __ballot_sync(0xffffffffu, on[1]);
+            const unsigned long long m = ((unsigned long long)hi << 32) | lo;
+            if (lane == 0) {
+                W.amask[i] = m;
+                W.nzmask[i] = 0ull;
+                W.act[0][i] = i;
+                W.keep[i] = m != 0ull;
+            }
+            kept += m != 0ull;
+        }
+        if (lane == 0) S.ired[warp] = kept;
+        if (tid < kMR) {
+            W.c_nz[tid * G + b] = 0;
+            W.p_l1[tid * G + b] = FF{0.f, 0.f};
+            W.c_na[tid * G + b] = 0;
+            W.c_nnzx[tid * G + b] = 0;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int k = 0;
+            for (int w = 0; w < kMW; w++) k += S.ired[w];
+            W.c_keep[b] = k;
+            W.s_alo[b] = p_lo;
+            S.nA = K;
+        }
+    }
+    if (!grid_sync(bar, G, gen)) return false;
+
+    // ================================================================ iterations
+    int cur = 0;  // list generation
+    int xi = 0;   // xb[xi] holds the current x
+    for (int t = 1;; t++) {
+        // ======================================== (A) compaction + syntheses
+        {
+            const int nA = S.nA;
+            const int nxt = cur ^ 1;
+            const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
+            if (warp == 0) {
+                int base = 0, tot = 0;
+                for (int k = lane; k < G; k += 32) {
+                    const int c = __ldcg(W.c_keep + k);
+                    if (k < b) base += c;
+                    tot += c;
+                }
+                base = warp_sum(base);
+                tot = warp_sum(tot);
+                if (lane == 0) { S.ired[0] = base; S.ired[1] = tot; }
+            }
+            for (int k = tid; k < G; k += kThreads) S.alo[k] = __ldcg(W.s_alo + k);
+            __syncthreads();
+            int gb = S.ired[0];
+            const int nA_new = S.ired[1];
+            for (int base = p_lo; base < p_hi; base += kThreads) {
+                const int p = base + tid;
+                const int k = p < p_hi ? __ldcg(W.keep + p) : 0;
+                int tot;
+                const int pre = block_exclusive_scan(k, S.scan_tmp, &tot);
+                if (k) W.act[nxt][gb + pre] = __ldcg(W.act[cur] + p);
+                gb += tot;
+            }
+            // syntheses: items (row tile, live problem)
+            const int ns = S.n_slots;
+            for (int it = gwarp; it < ntile * ns; it += twarps) {
+                const int s = it / ntile, rt = it - s * ntile;
+                const int r = S.slot_r[s];
+                int run = 0;
+                for (int b0 = 0; b0 < G; b0 += 32) {
+                    const int bb = b0 + lane;
+                    const int c = bb < G ? __ldcg(W.c_nz + r * G + bb) : 0;
+                    int x = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (lane >= o) x += y;
+                    }
+                    if (bb < G) S.dir[warp][bb] = run + x - c;
+                    run += __shfl_sync(0xffffffffu, x, 31);
+                }
+                if (lane == 0) S.dir[warp][G] = run;
+                __syncwarp();
+                const int E = run;
+                const int n0 = rt * kMSynRows + lane, n1 = n0 + 32;
+                Dot2f au0, au1, ax0, ax1;
+                const size_t rb = (size_t)r * K;
+                for (int e0 = 0; e0 < E; e0 += 32) {
+                    const int e = e0 + lane;
+                    int col = 0;
+                    FF uu{0.f, 0.f}, xx{0.f, 0.f};
+                    if (e < E) {
+                        int lo = 0, hi = G;  // largest segment start <= e
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (S.dir[warp][mid] <= e) lo = mid;
+                            else hi = mid;
+                        }
+                        const size_t idx = rb + S.alo[lo] + (e - S.dir[warp][lo]);
+                        col = __ldcg(W.nz_col + idx);
+                        uu = ldcg_x(W.nz_u + idx);
+                        xx = ldcg_x(W.nz_x + idx);
+                    }
+                    const int ne = min(32, E - e0);
+                    for (int k0 = 0; k0 < ne; k0 += 4) {
+                        float d0[4], d1[4];
+                        FF uk[4], xk[4];
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const int k = min(k0 + q, 31);
+                            const bool in = k0 + q < ne;
+                            const int c = __shfl_sync(0xffffffffu, col, k);
+                            uk[q].h = __shfl_sync(0xffffffffu, uu.h, k);
+                            uk[q].l = __shfl_sync(0xffffffffu, uu.l, k);
+                            xk[q].h = __shfl_sync(0xffffffffu, xx.h, k);
+                            xk[q].l = __shfl_sync(0xffffffffu, xx.l, k);
+                            const float* dc = P.D + (size_t)c * ld;
+                            d0[q] = (in && n0 < N) ? __ldg(dc + n0) : 0.f;
+                            d1[q] = (in && n1 < N) ? __ldg(dc + n1) : 0.f;
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            syn_add(au0, d0[q], uk[q]);
+                            syn_add(ax0, d0[q], xk[q]);
+                            syn_add(au1, d1[q], uk[q]);
+                            syn_add(ax1, d1[q], xk[q]);
+                        }
+                    }
+                }
+                Dot2f pa, pb, pr;
+                {
+                    if (n0 < N) {
+                        const float yv = __ldcg(W.Yt + (size_t)r * npad + n0);
+                        const float th = theta_from(au0, yv);
+                        W.Th[(size_t)r * npad + n0] = th;
+                        pa.add(th, yv);
+                        pb.add(th, th);
+                        acc_resid_sq(pr, ax0, yv);
+                    }
+                    if (n1 < N) {
+                        const float yv = __ldcg(W.Yt + (size_t)r * npad + n1);
+                        const float th = theta_from(au1, yv);
+                        W.Th[(size_t)r * npad + n1] = th;
+                        pa.add(th, yv);
+                        pb.add(th, th);
+                        acc_resid_sq(pr, ax1, yv);
+                    }
+                }
+                pa = dot2_warp_reduce(pa);
+                pb = dot2_warp_reduce(pb);
+                pr = dot2_warp_reduce(pr);
+                if (lane == 0) {
+                    W.p_a[r * ntile + rt] = FF{pa.s, pa.c};
+                    W.p_b[r * ntile + rt] = FF{pb.s, pb.c};
+                    W.p_r[r * ntile + rt] = FF{pr.s, pr.c};
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+            if (tid == 0) S.nA = nA_new;
+            cur = nxt;
+        }
+        if (!grid_sync(bar, G, gen)) return false;
+
+        // ======================================== (B) gaps, stop, correlation + prox
+        {
+            const int nA = S.nA;
+            const int ns = S.n_slots;
+            for (int s = warp; s < ns; s += kMW) {
+                const int r = S.slot_r[s];
+                const double a_ = mr_ff_sum(W.p_a + r * ntile, ntile, lane);
+                const double b_ = mr_ff_sum(W.p_b + r * ntile, ntile, lane);
+                const double r_ = mr_ff_sum(W.p_r + r * ntile, ntile, lane);
+                const double l1 = mr_ff_sum(W.p_l1 + r * G, G, lane);
+                const int na = mr_int_sum(W.c_na + r * G, G, lane);
+                const int nx = mr_int_sum(W.c_nnzx + r * G, G, lane);
+                const int ne = mr_int_sum(W.c_nz + r * G, G, lane);
+                if (lane == 0) {
+                    const double lam = S.lam[r], yy = S.yy[r];
+                    int stop = 0;
+                    if (t > 1) {
+                        // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
+                        const double primal = 0.5 * r_ + lam * l1;
+                        const double gap = primal - 0.5 * yy + 0.5 * lam * lam * S.R2n[r];
+                        S.primal[r] = primal;
+                        S.gap[r] = gap;
+                        S.iters[r] = t - 1;
+                        S.na[r] = na;
+                        S.nnzx[r] = nx;
+                        stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                    }
+                    S.csyn[r] += ne;
+                    S.alpha[r] = a_;
+                    S.beta[r] = b_;
+                    S.s_unc[r] = b_ > 0.0 ? a_ / lam * fast_rcp(b_) : 0.0;
+                    S.sqrt_beta[r] = (double)sqrtf((float)b_) * (1.0 + 1e-6);
+                    S.stopnow[r] = stop;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double bt = 0.0;
+                if (!ista) {
+                    // FISTA (Table 1): l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t
+                    if (t <= P.fista_n) {
+                        bt = P.fista[2 * (t - 1)];
+                        S.lf = P.fista[2 * (t - 1) + 1];
+                    } else {
+                        const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * S.lf * S.lf));
+                        bt = (S.lf - 1.0) / ln;
+                        S.lf = ln;
+                    }
+                }
+                S.bt = bt;
+                unsigned long long dm = 0;
+                for (int s = 0; s < ns; s++)
+                    if (S.stopnow[S.slot_r[s]]) dm |= 1ull << S.slot_r[s];
+                S.ired[2] = (int)(dm & 0xffffffffu);
+                S.ired[3] = (int)(dm >> 32);
+            }
+            __syncthreads();
+            const unsigned long long dm =
+                ((unsigned long long)(unsigned)S.ired[3] << 32) | (unsigned long long)(unsigned)S.ired[2];
+            if (dm) {
+                // problems that met their tolerance leave the block: x of iteration t-1 out
+                const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
+                for (int p = p_lo + warp; p < p_hi; p += kMW) {
+                    const int i = __ldcg(W.act[cur] + p);
+                    for (int h = 0; h < 2; h++) {
+                        const int r = lane + 32 * h;
+                        if ((dm >> r) & 1) {
+                            const FF x = ldcg_x(W.xb[xi] + (size_t)i * kMR + r);
+                            P.X[(size_t)r * K + i] = it_round(x);
+                        }
+                    }
+                }
+                if (b == 0 && tid < kMR && ((dm >> tid) & 1)) {
+                    const int r = tid;
+                    DevResult& o = P.res[r];
+                    o.iters = S.iters[r];
+                    o.status = (P.tol > 0.0 && !(S.gap[r] <= P.tol * 0.5 * S.yy[r])) ? kDevNotConverged : kDevOk;
+                    o.n_active = S.na[r];
+                    o.nnz = S.nnzx[r];
+                    o.gap = S.gap[r];
+                    o.primal = S.primal[r];
+                    o.dual = S.primal[r] - S.gap[r];
+                    o.lambda = S.lam[r];
+                    o.lambda_max = S.lstar[r];
+                    o.cols_corr = S.ccorr;
+                    o.cols_synth = S.csyn[r];
+                    o.cols_lowp = 0;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    S.live &= ~dm;
+                    int k = 0;
+                    for (int r = 0; r < kMR; r++)
+                        if ((S.live >> r) & 1) S.slot_r[k++] = r;
+                    S.n_slots = k;
+                    for (int s = k; s < kMR; s++) S.slot_r[s] = -1;
+                }
+                __syncthreads();
+            }
+            if (S.live == 0ull) break;
+            if (tid == 0) S.ccorr += nA;
+            if (tid < kMR) S.zmax[tid] = 0u;
+            __syncthreads();
+            const int ns2 = S.n_slots;
+            const int JJ = (ns2 + 15) / 16;
+            float zm[4] = {0.f, 0.f, 0.f, 0.f};
+            FF* xo = W.xb[xi ^ 1];
+            mr_tiles<false>(S, P, W.act[cur], nA, W.Th, JJ, b, G, [&](float (&acc)[4][4], float (&)[4][4]) {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int i = S.cols[ta + 32 * j];
+                    if (i < 0) continue;
+                    const unsigned long long m = __ldcg(W.amask + i);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if (q >= JJ) continue;
+                        const int r = S.slot_r[tr + 16 * q];
+                        if (r < 0) continue;
+                        const size_t idx = (size_t)i * kMR + r;
+                        FF xn{0.f, 0.f};
+                        if ((m >> r) & 1) {
+                            // proximal step (Table 1): x = soft(u - z / L, lambda / L)
+                            const float z = acc[j][q];
+                            xn = it_soft(it_grad_step(ldcg_x(W.u + idx), z, invL), S.thrX[r]);
+                            zm[q] = fmaxf(zm[q], fabsf(z));
+                        }
+                        xo[idx] = xn;
+                    }
+                }
+            });
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (q < JJ) atomicMax(&S.zmax[tr + 16 * q], __float_as_uint(zm[q]));
+            __syncthreads();
+            if (tid < ns2) W.p_m[S.slot_r[tid] * G + b] = __uint_as_float(S.zmax[tid]);
+        }
+        if (!grid_sync(bar, G, gen)) return false;
+
+        // ======================================== (C) screening + momentum
+        {
+            const int nA = S.nA;
+            const int ns = S.n_slots;
+            for (int s = warp; s < ns; s += kMW) {
+                const int r = S.slot_r[s];
+                float mf = 0.f;
+                for (int k = lane; k < G; k += 32) mf = fmaxf(mf, __ldcg(W.p_m + r * G + k));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+                if (lane == 0) {
+                    // Lemma 8 with the nominal max |z| (gap) and a rigorous upper bound of it (radius)
+                    const double m_nom = (double)mf;
+                    const double m_up = m_nom + P.gamma * P.fmax * S.sqrt_beta[r];
+                    const double su = S.s_unc[r];
+                    const double mu_nom = (m_nom > 0.0 && fabs(su) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), su) : su;
+                    const double mu_s = (m_up > 0.0 && fabs(su) * m_up > 1.0) ? copysign(fast_rcp(m_up), su) : su;
+                    const double il = 1.0 / S.lam[r];
+                    const double yyl2 = S.yy[r] * il * il;
+                    S.R2n[r] = fmax(fma(mu_nom, fma(mu_nom, S.beta[r], -2.0 * S.alpha[r] * il), yyl2), 0.0);
+                    const double R2s = fmax(fma(mu_s, fma(mu_s, S.beta[r], -2.0 * S.alpha[r] * il), yyl2), 0.0);
+                    const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
+                    S.Rs[r] = Rs;
+                    S.rad[r] = P.test == 2 ? fast_sqrt(fmax(R2s - S.delta[r] * S.delta[r], 0.0)) * (1.0 + 1e-13) : Rs;
+                    const double psi = S.psi_d[r];
+                    S.rho[r] = fast_sqrt(fmax(Rs * Rs - psi * psi, 0.0)) * (1.0 + 1e-13);
+                }
+            }
+            __syncthreads();
+            const unsigned long long live = S.live;
+            const FF btX = ff_from_double(S.bt);
+            const bool dyn = P.dynamic && P.test != 0;
+            const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
+            const int w_lo = p_lo + (int)((long long)warp * (p_hi - p_lo) / kMW);
+            const int w_hi = p_lo + (int)((long long)(warp + 1) * (p_hi - p_lo) / kMW);
+            FF* xnew = W.xb[xi ^ 1];
+            const FF* xold = W.xb[xi];
+            int cnt[2] = {0, 0}, na[2] = {0, 0}, nx[2] = {0, 0}, kept = 0;
+            Dot2f l1[2];
+            double radh[2], Rsh[2], rhoh[2], psih[2], ilh[2];
+            bool lv[2];
+            for (int h = 0; h < 2; h++) {
+                const int r = lane + 32 * h;
+                lv[h] = (live >> r) & 1;
+                radh[h] = lv[h] ? S.rad[r] : 0.0;
+                Rsh[h] = lv[h] ? S.Rs[r] : 0.0;
+                rhoh[h] = lv[h] ? S.rho[r] : 0.0;
+                psih[h] = lv[h] ? S.psi_d[r] : 0.0;
+                ilh[h] = lv[h] ? 1.0 / S.lam[r] : 0.0;
+            }
+            for (int p = w_lo; p < w_hi; p++) {
+                const int i = __ldcg(W.act[cur] + p);
+                const unsigned long long m = __ldcg(W.amask + i);
+                bool on[2], nz[2];
+                for (int h = 0; h < 2; h++) {
+                    const int r = lane + 32 * h;
+                    const size_t idx = (size_t)i * kMR + r;
+                    on[h] = lv[h] && ((m >> r) & 1);
+                    nz[h] = false;
+                    if (!on[h]) continue;
+                    bool kill = false;
+                    if (dyn) {
+                        if (!dome) {
+                            kill = __ldcg(W.Q0 + idx) - radh[h] > P.eps_test;
+                        } else {
+                            // Lemma 4 in its dynamic form: max over the dome of |d_i^T theta| < 1
+                            const double dc0 = __ldcg(W.Q0 + idx) * ilh[h];
+                            const double tt = __ldcg(W.Q1 + idx), sq = __ldcg(W.Q2 + idx);
+                            const double inv = __ldcg(W.invn + i);
+                            const double Rr = Rsh[h], psi = psih[h], rho = rhoh[h];
+                            const double up = (tt * Rr <= -psi) ? dc0 + Rr : dc0 - psi * tt + rho * sq;
+                            const double dn = (-tt * Rr <= -psi) ? -dc0 + Rr : -dc0 + psi * tt + rho * sq;
+                            kill = (inv - up > P.eps_test) && (inv - dn > P.eps_test);
+                        }
+                    }
+                    if (kill) {
+                        on[h] = false;
+                        xnew[idx] = FF{0.f, 0.f};
+                        W.u[idx] = FF{0.f, 0.f};
+                        continue;
+                    }
+                    const FF x = ldcg_x(xnew + idx);
+                    const FF uu = ista ? x : it_momentum(x, ldcg_x(xold + idx), btX);
+                    W.u[idx] = uu;
+                    nz[h] = it_nz(x) || it_nz(uu);
+                    nx[h] += it_nz(x);
+                    acc_abs(l1[h], x);
+                    na[h] += 1;
+                    cnt[h] += nz[h];
+                }
+                const unsigned lo = __ballot_sync(0xffffffffu, on[0]), hi = __ballot_sync(0xffffffffu, on[1]);
+                const unsigned zlo = __ballot_sync(0xffffffffu, nz[0]), zhi = __ballot_sync(0xffffffffu, nz[1]);
+                const unsigned long long onm = ((unsigned long long)hi << 32) | lo;
+                if (lane == 0) {
+                    W.amask[i] = (m & ~live) | onm;
+                    W.nzmask[i] = ((unsigned long long)zhi << 32) | zlo;
+                    W.keep[p] = onm != 0ull;
+                }
+                kept += onm != 0ull;
+            }
+            for (int h = 0; h < 2; h++) {
+                const int r = lane + 32 * h;
+                S.cnt[warp][r] = cnt[h];
+                S.red_s[warp][r] = l1[h].s;
+                S.red_c[warp][r] = l1[h].c;
+                S.red_na[warp][r] = na[h];
+                S.red_nx[warp][r] = nx[h];
+            }
+            if (lane == 0) S.ired[warp] = kept;
+            __syncthreads();
+            if (tid < kMR) {
+                const int r = tid;
+                int run = 0, a = 0, x = 0;
+                Dot2f l;
+                for (int w = 0; w < kMW; w++) {
+                    const int c = S.cnt[w][r];
+                    S.cnt[w][r] = run;
+                    run += c;
+                    dot2_merge(l, S.red_s[w][r], S.red_c[w][r]);
+                    a += S.red_na[w][r];
+                    x += S.red_nx[w][r];
+                }
+                W.c_nz[r * G + b] = run;
+                W.p_l1[r * G + b] = FF{l.s, l.c};
+                W.c_na[r * G + b] = a;
+                W.c_nnzx[r * G + b] = x;
+            }
+            if (tid == 0) {
+                int k = 0;
+                for (int w = 0; w < kMW; w++) k += S.ired[w];
+                W.c_keep[b] = k;
+                W.s_alo[b] = p_lo;
+            }
+            __syncthreads();
+            // the nonzero lists of the next syntheses, per problem, in list order
+            int e[2] = {S.cnt[warp][lane], S.cnt[warp][lane + 32]};
+            for (int p = w_lo; p < w_hi; p++) {
+                const int i = __ldcg(W.act[cur] + p);
+                const unsigned long long z = __ldcg(W.nzmask + i);
+                for (int h = 0; h < 2; h++) {
+                    const int r = lane + 32 * h;
+                    if ((z >> r) & 1) {
+                        const size_t idx = (size_t)i * kMR + r;
+                        const size_t o = (size_t)r * K + p_lo + e[h]++;
+                        W.nz_col[o] = i;
+                        W.nz_u[o] = ldcg_x(W.u + idx);
+                        W.nz_x[o] = ldcg_x(xnew + idx);
+                    }
+                }
+            }
+            xi ^= 1;
+        }
+        if (!grid_sync(bar, G, gen)) return false;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------ team kernel
+
+struct MrhsTeamArgs {
+    const MrhsP* jobs;
+    int n_jobs;
+    const MrhsWs* team_ws;
+    GridBarrier* bars;
+    int* team_job;
+    int* next_job;
+    int* error;
+    int team_size;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) mrhs_team_kernel(const MrhsTeamArgs A)
+{
+    __shared__ MrhsP sP;
+    __shared__ int s_job;
+    const int team = blockIdx.x / A.team_size, rank = blockIdx.x % A.team_size;
+    GridBarrier* bar = A.bars + team;
+    unsigned int gen = 0;
+    for (;;) {
+        if (threadIdx.x == 0 && rank == 0) {
+            int j = atomicAdd(A.next_job, 1);
+            A.team_job[team] = j < A.n_jobs ? j : -1;
+        }
+        if (!grid_sync(bar, A.team_size, gen)) {
+            if (threadIdx.x == 0) atomicExch(A.error, 1);
+            return;
+        }
+        if (threadIdx.x == 0) s_job = __ldcg(A.team_job + team);
+        __syncthreads();
+        const int j = s_job;
+        if (j < 0) return;
+        if (threadIdx.x == 0) {
+            sP = A.jobs[j];
+            sP.ws = A.team_ws[team];
+        }
+        __syncthreads();
+        if (!mrhs_body(sP, rank, A.team_size, bar, gen)) {
+            if (threadIdx.x == 0) atomicExch(A.error, 1);
+            if (threadIdx.x == 0 && rank == 0)
+                for (int r = 0; r < sP.R; r++) sP.res[r].status = kDevTimeout;
+            return;
+        }
+        // the next job reuses the team's workspace: every CTA leaves this one first
+        if (!grid_sync(bar, A.team_size, gen)) {
+            if (threadIdx.x == 0) atomicExch(A.error, 1);
+            return;
+        }
+    }
+}
+
+// ------------------------------------------------------------ host side
+
+namespace {
+
+struct MrhsGeom {
+    int npad, ntile;
+    size_t ws_bytes;
+};
+
+size_t mrhs_layout(char* base, int N, int K, int G, bool dome, MrhsWs* w)
+{
+    const int npad = (N + kMSynRows - 1) / kMSynRows * kMSynRows;
+    const int ntile = npad / kMSynRows;
+    Bump bp{base, 0};
+    w->Yt = bp.take<float>((size_t)kMR * npad);
+    w->Th = bp.take<float>((size_t)kMR * npad);
+    w->Dst = bp.take<float>((size_t)kMR * npad);
+    w->Q0 = bp.take<double>((size_t)K * kMR);
+    w->Q1 = bp.take<double>((size_t)K * kMR);
+    w->Q2 = dome ? bp.take<double>((size_t)K * kMR) : nullptr;
+    w->invn = bp.take<double>(K);
+    w->xb[0] = bp.take<FF>((size_t)K * kMR);
+    w->xb[1] = bp.take<FF>((size_t)K * kMR);
+    w->u = bp.take<FF>((size_t)K * kMR);
+    w->amask = bp.take<unsigned long long>(K);
+    w->nzmask = bp.take<unsigned long long>(K);
+    w->act[0] = bp.take<int>(K);
+    w->act[1] = bp.take<int>(K);
+    w->keep = bp.take<int>(K);
+    w->nz_col = bp.take<int>((size_t)kMR * K);
+    w->nz_u = bp.take<FF>((size_t)kMR * K);
+    w->nz_x = bp.take<FF>((size_t)kMR * K);
+    w->part = bp.take<float>((size_t)kMMaxSplit * G * kMTA * kMR * 2);
+    w->tilecnt = bp.take<int>((K + kMTA - 1) / kMTA);
+    w->p_m = bp.take<float>((size_t)kMR * G);
+    w->p_l1 = bp.take<FF>((size_t)kMR * G);
+    w->c_na = bp.take<int>((size_t)kMR * G);
+    w->c_nnzx = bp.take<int>((size_t)kMR * G);
+    w->c_nz = bp.take<int>((size_t)kMR * G);
+    w->c_keep = bp.take<int>(G);
+    w->s_alo = bp.take<int>(G);
+    w->p_v = bp.take<double>((size_t)kMR * G);
+    w->p_i = bp.take<int>((size_t)kMR * G);
+    w->p_a = bp.take<FF>((size_t)kMR * ntile);
+    w->p_b = bp.take<FF>((size_t)kMR * ntile);
+    w->p_r = bp.take<FF>((size_t)kMR * ntile);
+    return bp.off + 256;
+}
+
+}  // namespace
+
+struct MrhsPlan {
+    ds_ctx* ctx;
+    int n_jobs;
+    std::vector<MrhsBlock> blocks;
+    void* dmem;
+    MrhsP* hjobs;       // pinned
+    double* hlam;       // pinned, [n_jobs][kMR]
+    DevResult* hres;    // pinned, [n_jobs][kMR]
+    MrhsP* djobs;
+    double* dlam;
+    DevResult* dres;
+    void* dctl;
+    size_t ctl_bytes;
+    int* derr;
+    MrhsTeamArgs args;
+    int grid;
+    size_t smem;
+};
+
+ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, const ds_options* opt,
+                           const double* fista_dev, int fista_n, MrhsPlan** out)
+{
+    *out = nullptr;
+    if (n_blocks < 1) return DS_ERR_INVALID;
+    MrhsPlan* M = new (std::nothrow) MrhsPlan();
+    if (!M) return DS_ERR_OOM;
+    M->ctx = ctx;
+    M->n_jobs = n_blocks;
+    M->blocks.assign(blocks, blocks + n_blocks);
+    // largest blocks first
+    std::vector<int> ord(n_blocks);
+    for (int i = 0; i < n_blocks; i++) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
+        return (double)blocks[a].dict->N * blocks[a].dict->K * blocks[a].R >
+               (double)blocks[c].dict->N * blocks[c].dict->K * blocks[c].R;
+    });
+    int maxN = 1, maxK = 1;
+    for (int i = 0; i < n_blocks; i++) {
+        maxN = std::max(maxN, (int)blocks[i].dict->N);
+        maxK = std::max(maxK, (int)blocks[i].dict->K);
+    }
+    const int team = std::max(1, std::min(ctx->num_sms, kMaxG) / n_blocks);
+    const int n_teams = std::max(1, std::min(std::min(ctx->num_sms, kMaxG) / team, n_blocks));
+    const bool dome = opt->test == DS_DOME;
+    MrhsWs wtmp;
+    const size_t ws_team = align_up(mrhs_layout(nullptr, maxN, maxK, team, dome, &wtmp), 256);
+    const size_t jobs_bytes = align_up(sizeof(MrhsP) * n_blocks, 256);
+    const size_t lam_bytes = align_up(sizeof(double) * kMR * n_blocks, 256);
+    const size_t res_bytes = align_up(sizeof(DevResult) * kMR * n_blocks, 256);
+    const size_t tws_bytes = align_up(sizeof(MrhsWs) * n_teams, 256);
+    M->ctl_bytes = align_up(sizeof(GridBarrier) * n_teams + sizeof(int) * (n_teams + 2), 256);
+    const size_t total = ws_team * n_teams + jobs_bytes + lam_bytes + res_bytes + tws_bytes + M->ctl_bytes;
+    auto fail = [&](ds_status s) {
+        mrhs_plan_destroy(M);
+        return s;
+    };
+    if (cudaMalloc(&M->dmem, total) != cudaSuccess) {
+        cudaGetLastError();
+        M->dmem = nullptr;
+        return fail(DS_ERR_OOM);
+    }
+    if (cudaMallocHost((void**)&M->hjobs, jobs_bytes) != cudaSuccess ||
+        cudaMallocHost((void**)&M->hlam, lam_bytes) != cudaSuccess ||
+        cudaMallocHost((void**)&M->hres, res_bytes) != cudaSuccess)
+        return fail(DS_ERR_OOM);
+    char* d = reinterpret_cast<char*>(M->dmem);
+    char* wsbase = d;
+    d += ws_team * n_teams;
+    M->djobs = reinterpret_cast<MrhsP*>(d);
+    d += jobs_bytes;
+    M->dlam = reinterpret_cast<double*>(d);
+    d += lam_bytes;
+    M->dres = reinterpret_cast<DevResult*>(d);
+    d += res_bytes;
+    MrhsWs* dtws = reinterpret_cast<MrhsWs*>(d);
+    d += tws_bytes;
+    M->dctl = d;
+    GridBarrier* bars = reinterpret_cast<GridBarrier*>(M->dctl);
+    int* team_job = reinterpret_cast<int*>(bars + n_teams);
+    int* next_job = team_job + n_teams;
+    M->derr = next_job + 1;
+    std::vector<MrhsWs> tws(n_teams);
+    for (int t = 0; t < n_teams; t++) mrhs_layout(wsbase + ws_team * t, maxN, maxK, team, dome, &tws[t]);
+    if (cudaMemcpy(dtws, tws.data(), sizeof(MrhsWs) * n_teams, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(DS_ERR_CUDA);
+    for (int jj = 0; jj < n_blocks; jj++) {
+        const int j = ord[jj];
+        const MrhsBlock& B = blocks[j];
+        const ds_dict* dc = B.dict;
+        MrhsP P;
+        std::memset(&P, 0, sizeof(P));
+        P.D = reinterpret_cast<const float*>(dc->D);
+        P.N = (int)dc->N;
+        P.K = (int)dc->K;
+        P.ld = (int)dc->ld;
+        P.npad = (P.N + kMSynRows - 1) / kMSynRows * kMSynRows;
+        P.ntile = P.npad / kMSynRows;
+        P.colnorm = dc->colnorm;
+        P.fmax = dc->fmax;
+        P.L = opt->L > 0.0 ? opt->L : dc->L;
+        {
+            // rounding of the FP32 contraction: 32 FMAs a chunk, the chunk sums, the row splits
+            const double u = std::ldexp(1.0, -24);
+            const double k = 32.0 + 2.0 * (P.npad / kMKC) + 2.0;
+            P.gamma = 1.01 * k * u / (1.0 - k * u);
+        }
+        P.eps_test = 1e-9;
+        P.tol = opt->tol_gap_rel;
+        P.alg = opt->alg;
+        P.test = opt->test;
+        P.dynamic = opt->dynamic;
+        P.max_iter = opt->max_iter;
+        P.lambda_rel = opt->lambda_rel;
+        P.Y = reinterpret_cast<const float*>(B.Y);
+        P.R = B.R;
+        P.lambdas = M->dlam + (size_t)jj * kMR;
+        P.X = reinterpret_cast<float*>(B.X);
+        P.res = M->dres + (size_t)jj * kMR;
+        P.fista = fista_dev;
+        P.fista_n = fista_n;
+        M->hjobs[jj] = P;
+    }
+    // keep the job order for lambdas/results
+    std::vector<MrhsBlock> sorted(n_blocks);
+    for (int jj = 0; jj < n_blocks; jj++) sorted[jj] = blocks[ord[jj]];
+    M->blocks = sorted;
+    std::memset(&M->args, 0, sizeof(M->args));
+    M->args.jobs = M->djobs;
+    M->args.n_jobs = n_blocks;
+    M->args.team_ws = dtws;
+    M->args.bars = bars;
+    M->args.team_job = team_job;
+    M->args.next_job = next_job;
+    M->args.error = M->derr;
+    M->args.team_size = team;
+    M->grid = n_teams * team;
+    M->smem = sizeof(MrhsShared);
+    if (cudaFuncSetAttribute(mrhs_team_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M->smem) !=
+        cudaSuccess)
+        return fail(DS_ERR_CUDA);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mrhs_team_kernel, kThreads, M->smem) != cudaSuccess ||
+        occ < 1)
+        return fail(DS_ERR_UNSUPPORTED);
+    *out = M;
+    return DS_OK;
+}
+
+const MrhsBlock* mrhs_plan_blocks(const MrhsPlan* M, int* n)
+{
+    *n = M->n_jobs;
+    return M->blocks.data();
+}
+
+double* mrhs_plan_lambdas(MrhsPlan* M) { return M->hlam; }
+const DevResult* mrhs_plan_results(const MrhsPlan* M) { return M->hres; }
+
+ds_status mrhs_plan_enqueue(MrhsPlan* M, cudaStream_t s)
+{
+    if (cudaMemcpyAsync(M->djobs, M->hjobs, sizeof(MrhsP) * M->n_jobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return DS_ERR_CUDA;
+    if (cudaMemcpyAsync(M->dlam, M->hlam, sizeof(double) * kMR * M->n_jobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return DS_ERR_CUDA;
+    if (cudaMemsetAsync(M->dctl, 0, M->ctl_bytes, s) != cudaSuccess) return DS_ERR_CUDA;
+    if (cudaMemsetAsync(M->dres, 0, sizeof(DevResult) * kMR * M->n_jobs, s) != cudaSuccess) return DS_ERR_CUDA;
+    void* args[] = {(void*)&M->args};
+    if (cudaLaunchCooperativeKernel((const void*)mrhs_team_kernel, dim3(M->grid), dim3(kThreads), args, M->smem, s) !=
+        cudaSuccess)
+        return DS_ERR_CUDA;
+    if (cudaMemcpyAsync(M->hres, M->dres, sizeof(DevResult) * kMR * M->n_jobs, cudaMemcpyDeviceToHost, s) !=
+        cudaSuccess)
+        return DS_ERR_CUDA;
+    return DS_OK;
+}
+
+int* mrhs_plan_error_flag(MrhsPlan* M) { return M->derr; }
+
+void mrhs_plan_info(const MrhsPlan* M, int* teams, int* team_size)
+{
+    if (team_size) *team_size = M->args.team_size;
+    if (teams) *teams = M->grid / M->args.team_size;
+}
+
+void mrhs_plan_destroy(MrhsPlan* M)
+{
+    if (!M) return;
+    if (M->dmem) cudaFree(M->dmem);
+    if (M->hjobs) cudaFreeHost(M->hjobs);
+    if (M->hlam) cudaFreeHost(M->hlam);
+    if (M->hres) cudaFreeHost(M->hres);
+    delete M;
+}
+
+}  // namespace ds

@@ -207,6 +207,8 @@ struct ds_batch {
     cudaGraphExec_t exec;
     bool use_graph;
     float ms_last;
+    ds::MrhsPlan* mplan;  // right-hand sides solved together (FP32 Lasso instances)
+    double* mfista;       // the multi-rhs plan's copy of the FISTA table
 };
 
 namespace ds {
@@ -216,16 +218,60 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
                                 const int* n_rhs, const double* const* lambdas, const ds_options* opt,
                                 void* const* X_out, ds_batch* B)
 {
-    // problems (instance, rhs), instances ordered largest first
-    std::vector<int> inst(n);
-    std::iota(inst.begin(), inst.end(), 0);
+    if (opt->alg == DS_FISTA) {
+        ds_status fs = ctx_fista_table(ctx, opt->max_iter);
+        if (fs != DS_OK) return fs;
+    }
+    // instances whose right-hand sides are solved together (FP32 Lasso, tests of Lemmas 2-4)
+    std::vector<char> multi(n, 0);
+    std::vector<MrhsBlock> blocks;
+    for (int i = 0; i < n; i++) {
+        multi[i] = sizeof(T) == 4 && opt->batch_multi_rhs && !dicts[i]->is_group && opt->test <= DS_DOME &&
+                   n_rhs[i] >= 2;
+        if (!multi[i]) continue;
+        for (int r0 = 0; r0 < n_rhs[i]; r0 += kMrhsMaxR) {
+            MrhsBlock blk;
+            blk.dict = dicts[i];
+            blk.R = std::min(kMrhsMaxR, n_rhs[i] - r0);
+            blk.Y = reinterpret_cast<const char*>(Y[i]) + sizeof(T) * dicts[i]->N * r0;
+            blk.X = reinterpret_cast<char*>(X_out[i]) + sizeof(T) * dicts[i]->K * r0;
+            blk.inst = i;
+            blk.r0 = r0;
+            blocks.push_back(blk);
+        }
+    }
+    // problems (instance, rhs) of the other instances, instances ordered largest first
+    std::vector<int> inst;
+    for (int i = 0; i < n; i++)
+        if (!multi[i]) inst.push_back(i);
     std::stable_sort(inst.begin(), inst.end(), [&](int a, int b) {
         return (double)dicts[a]->N * dicts[a]->K > (double)dicts[b]->N * dicts[b]->K;
     });
     std::vector<int> res_base(n, 0);
     for (int i = 1; i < n; i++) res_base[i] = res_base[i - 1] + n_rhs[i - 1];
+    B->lam_src.assign(lambdas, lambdas + n);
+    B->n_inst = n;
+    B->n_rhs.assign(n_rhs, n_rhs + n);
+    if (!blocks.empty()) {
+        // the plan copies the FISTA table pointer: the context's table stays valid while the plan
+        // lives (it only grows on later calls), so take a private copy below as for the teams
+        ds_status ms = DS_OK;
+        double* mf = nullptr;
+        if (ctx->fista_n > 0) {
+            if (cudaMalloc(&mf, sizeof(double) * 2 * (size_t)ctx->fista_n) != cudaSuccess) {
+                cudaGetLastError();
+                return DS_ERR_OOM;
+            }
+            B->mfista = mf;
+            if (cudaMemcpy(mf, ctx->fista, sizeof(double) * 2 * (size_t)ctx->fista_n, cudaMemcpyDeviceToDevice) !=
+                cudaSuccess)
+                return DS_ERR_CUDA;
+        }
+        ms = mrhs_plan_create(ctx, (int)blocks.size(), blocks.data(), opt, mf, ctx->fista_n, &B->mplan);
+        if (ms != DS_OK) return ms;
+    }
     int n_jobs = 0, maxN = 1, maxK = 1, maxG = 1, maxgs = 1;
-    for (int i = 0; i < n; i++) {
+    for (int i : inst) {
         n_jobs += n_rhs[i];
         maxN = std::max(maxN, (int)dicts[i]->N);
         maxK = std::max(maxK, (int)dicts[i]->K);
@@ -233,6 +279,7 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
         maxgs = std::max(maxgs, dicts[i]->max_gsize);
     }
     B->n_jobs = n_jobs;
+    if (n_jobs == 0) return DS_OK;
     const int team = pick_team_size(n_jobs, ctx->num_sms);
     const int n_teams = std::max(1, std::min(ctx->num_sms / team, n_jobs));
     // workspace of one team, sized for the largest problem
@@ -251,10 +298,6 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
     const size_t lam_bytes = align_up(sizeof(double) * n_jobs, 256);
     const size_t res_bytes = align_up(sizeof(DevResult) * n_jobs, 256);
     const size_t tws_bytes = align_up(sizeof(Ws<T>) * n_teams, 256);
-    if (opt->alg == DS_FISTA) {
-        st = ctx_fista_table(ctx, opt->max_iter);
-        if (st != DS_OK) return st;
-    }
     // the plan keeps its own copy of the FISTA table (the context's may be regrown)
     const size_t fista_bytes = align_up(sizeof(double) * 2 * (size_t)ctx->fista_n, 256);
     B->ctl_bytes = align_up(sizeof(GridBarrier) * n_teams + sizeof(int) * (n_teams + 2), 256);
@@ -293,7 +336,7 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
     B->job_inst.resize(n_jobs);
     B->job_rhs.resize(n_jobs);
     int j = 0;
-    for (int ii = 0; ii < n; ii++) {
+    for (int ii = 0; ii < (int)inst.size(); ii++) {
         const int i = inst[ii];
         const ds_dict* dc = dicts[i];
         DictDesc dd = dict_desc(dc);
@@ -319,9 +362,6 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
             B->job_rhs[j] = r;
         }
     }
-    B->lam_src.assign(lambdas, lambdas + n);
-    B->n_inst = n;
-    B->n_rhs.assign(n_rhs, n_rhs + n);
     // the persistent launch
     TeamArgs<T>* A = new TeamArgs<T>();
     std::memset(A, 0, sizeof(*A));
@@ -350,6 +390,11 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
 template <typename T>
 static ds_status batch_enqueue_t(ds_batch* B, cudaStream_t s)
 {
+    if (B->mplan) {
+        ds_status ms = mrhs_plan_enqueue(B->mplan, s);
+        if (ms != DS_OK) return ms;
+    }
+    if (B->n_jobs == 0) return DS_OK;
     TeamArgs<T>* A = reinterpret_cast<TeamArgs<T>*>(B->args);
     if (cudaMemcpyAsync(B->djobs, B->hjobs, sizeof(SolveP<T>) * B->n_jobs, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DS_ERR_CUDA;
@@ -384,6 +429,8 @@ ds_status ds_batch_destroy(ds_batch* B)
     }
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->mplan) ds::mrhs_plan_destroy(B->mplan);
+    if (B->mfista) cudaFree(B->mfista);
     if (B->dmem) cudaFree(B->dmem);
     if (B->hjobs) cudaFreeHost(B->hjobs);
     if (B->hlam) cudaFreeHost(B->hlam);
@@ -453,6 +500,13 @@ ds_status ds_batch_run(ds_batch* B, ds_result* res)
     if (!B || !res) return DS_ERR_INVALID;
     if (cudaSetDevice(B->ctx->device) != cudaSuccess) return DS_ERR_CUDA;
     for (int j = 0; j < B->n_jobs; j++) B->hlam[j] = B->lam_src[B->job_inst[j]][B->job_rhs[j]];
+    int nb = 0;
+    const ds::MrhsBlock* blks = B->mplan ? ds::mrhs_plan_blocks(B->mplan, &nb) : nullptr;
+    if (B->mplan) {
+        double* ml = ds::mrhs_plan_lambdas(B->mplan);
+        for (int j = 0; j < nb; j++)
+            for (int r = 0; r < blks[j].R; r++) ml[(size_t)j * ds::kMrhsMaxR + r] = B->lam_src[blks[j].inst][blks[j].r0 + r];
+    }
     cudaStream_t s = B->ctx->stream;
     cudaEventRecord(B->ctx->ev0, s);
     if (B->use_graph) {
@@ -466,7 +520,35 @@ ds_status ds_batch_run(ds_batch* B, ds_result* res)
     if (cudaStreamSynchronize(s) != cudaSuccess) return DS_ERR_CUDA;
     cudaEventElapsedTime(&B->ms_last, B->ctx->ev0, B->ctx->ev1);
     int err = 0;
-    if (cudaMemcpy(&err, B->derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DS_ERR_CUDA;
+    if (B->n_jobs > 0 && cudaMemcpy(&err, B->derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return DS_ERR_CUDA;
+    if (B->mplan) {
+        int merr = 0;
+        if (cudaMemcpy(&merr, ds::mrhs_plan_error_flag(B->mplan), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return DS_ERR_CUDA;
+        err |= merr;
+        const ds::DevResult* mr = ds::mrhs_plan_results(B->mplan);
+        std::vector<int> base(B->n_inst, 0);
+        for (int i = 1; i < B->n_inst; i++) base[i] = base[i - 1] + B->n_rhs[i - 1];
+        for (int j = 0; j < nb; j++)
+            for (int r = 0; r < blks[j].R; r++) {
+                const ds::DevResult& q = mr[(size_t)j * ds::kMrhsMaxR + r];
+                ds_result& o = res[base[blks[j].inst] + blks[j].r0 + r];
+                o.iters = q.iters;
+                o.status = q.status;
+                o.n_active = q.n_active;
+                o.nnz = q.nnz;
+                o.gap = q.gap;
+                o.primal = q.primal;
+                o.dual = q.dual;
+                o.lambda = q.lambda;
+                o.lambda_max = q.lambda_max;
+                o.ms = B->ms_last;
+                o.cols_corr = q.cols_corr;
+                o.cols_synth = q.cols_synth;
+                o.cols_lowp = 0;
+            }
+    }
     for (int j = 0; j < B->n_jobs; j++) {
         const ds::DevResult& r = B->hres[j];
         ds_result& o = res[B->order[j]];
@@ -489,11 +571,31 @@ ds_status ds_batch_run(ds_batch* B, ds_result* res)
 ds_status ds_batch_info(const ds_batch* B, int* uses_graph, int* teams, int* team_size)
 {
     if (!B) return DS_ERR_INVALID;
+    if (uses_graph) *uses_graph = B->use_graph ? 1 : 0;
+    if (B->n_jobs == 0) {  // every instance runs in the multi-rhs kernel
+        ds::mrhs_plan_info(B->mplan, teams, team_size);
+        return DS_OK;
+    }
     const int ts = B->dtype == DS_FP32 ? reinterpret_cast<ds::TeamArgs<float>*>(B->args)->team_size
                                        : reinterpret_cast<ds::TeamArgs<double>*>(B->args)->team_size;
-    if (uses_graph) *uses_graph = B->use_graph ? 1 : 0;
     if (team_size) *team_size = ts;
     if (teams) *teams = B->grid / ts;
+    return DS_OK;
+}
+
+ds_status ds_batch_layout(const ds_batch* B, int* multi_rhs_blocks, int* multi_rhs_teams, int* multi_rhs_team_size,
+                          int* single_problems)
+{
+    if (!B) return DS_ERR_INVALID;
+    int nb = 0, t = 0, ts = 0;
+    if (B->mplan) {
+        ds::mrhs_plan_blocks(B->mplan, &nb);
+        ds::mrhs_plan_info(B->mplan, &t, &ts);
+    }
+    if (multi_rhs_blocks) *multi_rhs_blocks = nb;
+    if (multi_rhs_teams) *multi_rhs_teams = t;
+    if (multi_rhs_team_size) *multi_rhs_team_size = ts;
+    if (single_problems) *single_problems = B->n_jobs;
     return DS_OK;
 }
 
