@@ -32,6 +32,9 @@
 #include <vector>
 
 #include "ds_solve_body.cuh"
+#include "ds_tc.cuh"
+
+#include <cuda_bf16.h>
 
 namespace ds {
 
@@ -42,11 +45,27 @@ constexpr int kMST = kMKC + 4;     // shared row stride (floats): conflict-free 
 constexpr int kMSynRows = 64;      // rows per synthesis item (two per lane)
 constexpr int kMW = kThreads / 32; // warps per CTA
 constexpr int kMMaxSplit = 8;      // row splits of a correlation tile
+constexpr int kMStages = 3;        // cp.async pipeline depth of the FP32 contraction
+constexpr int kCB = 4;             // atoms per step of the screening pass (loads in flight)
+// tensor-core contraction on the BF16 copy: stages of a 128 x 64 A tile (16 KB)
+// and a B tile of up to 128 rows (theta hi | lo, 16 KB), 128-byte swizzled
+constexpr int kTcRows = 64;        // rows (K) per stage
+constexpr int kTcStages = 5;       // ring depth
+constexpr int kTcAhead = 3;        // stages in flight ahead of the MMA
+constexpr int kTcStageBytes = 32768;
+constexpr int kTcCols = 128;       // tensor-memory columns (FP32 accumulators)
+constexpr int kZst = kMR + 1;      // row stride of the transposed accumulator tile
+// staging of the contractions, also the scratch of the block reductions
+constexpr int kStage32Bytes = kMStages * (kMTA + kMR) * kMST * 4;
+constexpr int kStageBytes = kTcStages * kTcStageBytes > kStage32Bytes ? kTcStages * kTcStageBytes : kStage32Bytes;
+static_assert(kMTA * kZst * 4 <= kStageBytes, "accumulator tile exceeds the staging area");
 
 struct MrhsWs {
     float* Yt;   // [kMR][npad] y, zero padded
     float* Th;   // [kMR][npad] theta
     float* Dst;  // [kMR][npad] d_* of each problem (precompute)
+    uint16_t* Thi;  // [kMR][npad] BF16 theta, rounded to nearest
+    uint16_t* Tlo;  // [kMR][npad] BF16 of theta - Thi
     double* Q0;  // [K][kMR] D^T y; then SAFE/DST3 thresholds, or (Dome) d_i^T y / ||d_i||
     double* Q1;  // [K][kMR] D^T d_*; then (Dome) t_i = d_i^T d_* / (||d_i|| ||d_*||)
     double* Q2;  // [K][kMR] (Dome) sqrt(1 - t_i^2)
@@ -62,18 +81,20 @@ struct MrhsWs {
     FF* nz_x;
     float* part;  // row-split partial tiles
     int* tilecnt; // per tile: row splits finished
-    float* p_m;   // [kMR][G] max |z| per CTA
-    FF* p_l1;     // [kMR][G]
-    int* c_na;    // [kMR][G]
-    int* c_nnzx;  // [kMR][G]
-    int* c_nz;    // [kMR][G] nonzero-list lengths
-    int* c_keep;  // [G]
-    int* s_alo;   // [G] start of each CTA's list segment
-    double* p_v;  // [kMR][G] max |d_i^T y| per CTA
-    int* p_i;     // [kMR][G] its lowest index
-    FF* p_a;      // [kMR][ntile] theta^T y per row tile
-    FF* p_b;      // [kMR][ntile] ||theta||^2
-    FF* p_r;      // [kMR][ntile] ||D x - y||^2
+    int* ctr;     // 3 work counters (dynamic claiming), used in turn
+    // per-unit partials, [unit][kMR] (problem index contiguous)
+    float* p_m;   // [G] max |z| per CTA
+    FF* p_l1;     // [G]
+    int* c_na;    // [G]
+    int* c_nnzx;  // [G]
+    int* c_nz;    // [G] nonzero-list lengths
+    int* c_keep;  // [G] (no problem index)
+    int* s_alo;   // [G] start of each CTA's list segment (no problem index)
+    double* p_v;  // [G] max |d_i^T y| per CTA
+    int* p_i;     // [G] its lowest index
+    FF* p_a;      // [ntile] theta^T y per row tile
+    FF* p_b;      // [ntile] ||theta||^2
+    FF* p_r;      // [ntile] ||D x - y||^2
 };
 
 struct MrhsP {
@@ -89,21 +110,37 @@ struct MrhsP {
     DevResult* res;          // R entries
     const double* fista;
     int fista_n;
+    // bulk phase on the tensor cores (dictionaries with a BF16 copy), then FP32
+    const uint16_t* Dlo;   // BF16 copy, column i at Dlo + i * ld_lo, zero rows N..ld_lo-1
+    int ld_lo;
+    int use_tc;
+    double emax;           // max_i ||d_i - copy_i||
+    double gamma_tc;       // accumulation bound of the tensor-core sums
+    double lo_switch;      // relative nominal gap at which the block leaves the copy
     MrhsWs ws;
 };
 
+// Tensor-core state of a CTA (kernel lifetime): accumulator columns, the
+// mbarriers of the ring, and the running stage counter.
+struct TcState {
+    uint32_t tmem;
+    uint64_t* mbar;  // kTcStages
+    unsigned q;      // stages consumed so far (selects slot and phase)
+    unsigned issued; // stages whose MMAs were committed
+};
+
+struct MrhsStage32 {
+    float Ds[kMStages][kMTA][kMST];
+    float Ts[kMStages][kMR][kMST];
+};
+
 struct MrhsShared {
-    float Ds[2][kMTA][kMST];
-    float Ts[2][kMR][kMST];
+    alignas(1024) unsigned char stage[kStageBytes];  // MrhsStage32, or reduction scratch
     int cols[kMTA];
     int slot_r[kMR];       // live slot -> problem (-1 past the live ones)
     int dir[kMW][kMaxG + 1];
     int alo[kMaxG];
     int cnt[kMW][kMR];
-    float red_s[kMW][kMR], red_c[kMW][kMR];
-    int red_na[kMW][kMR], red_nx[kMW][kMR];
-    double bv[kMW][kMR];
-    int bi[kMW][kMR];
     unsigned int zmax[kMR];
     double lam[kMR], yy[kMR], lstar[kMR], psi_d[kMR], coef[kMR], delta[kMR], nstar[kMR];
     double alpha[kMR], beta[kMR], s_unc[kMR], sqrt_beta[kMR], R2n[kMR], rad[kMR], Rs[kMR], rho[kMR];
@@ -112,7 +149,12 @@ struct MrhsShared {
     int istar[kMR], iters[kMR], na[kMR], nnzx[kMR], stopnow[kMR];
     long long csyn[kMR];
     unsigned long long live;
-    int n_slots, nA, last;
+    int n_slots, nA, last, claim, keep_base, keep_tot;
+    unsigned long long dm;
+    // precision phase of the block (bulk on the BF16 copy, then FP32)
+    int low, lowB, t0, swok[kMR], since[kMR];
+    double best_gap[kMR], R2s[kMR];
+    long long clowp;
     long long ccorr;
     double bt, lf;
     int ired[kMW];
@@ -131,6 +173,15 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait()
 {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// 16-byte shared-memory load by shared address (the contraction runs out of
+// line, where a generic pointer would not be known to point to shared memory).
+__device__ __forceinline__ float4 lds128(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
 }
 
 // One compensated product-accumulation (TwoProduct by FMA, Knuth's TwoSum);
@@ -154,16 +205,20 @@ __device__ __forceinline__ void d2_merge(float& s, float& c, float s2, float c2)
     c = __fadd_rn(c, __fadd_rn(e, c2));
 }
 
-// Z tile = D[:, cols]^T Theta[:, slots] over row chunks [c_lo, c_hi) of 32 rows.
-// Thread (ta, tr) owns atoms ta + 32j (j < 4) and slots tr + 16q (q < JJ).
-// COMP: compensated sums (s in acc, error in cmp); otherwise cmp holds the
-// chunk's partial sum, added to acc once per chunk (two-level summation keeps
-// the rounding bound at 32 + chunks terms).
+// Z tile = D[:, cols]^T Theta[:, slots] over row chunks [c_lo, c_hi) of 32 rows,
+// staged through a kMStages-deep cp.async ring.  Thread (ta, tr) owns atoms
+// ta + 32j (j < 4) and slots tr + 16q (q < JJ).  COMP: compensated sums (s in
+// acc, error in cmp); otherwise cmp holds the chunk's partial sum, added to acc
+// once per chunk (two-level summation keeps the rounding bound at 32 + chunks
+// terms).
 template <int JJ, bool COMP>
-__device__ __forceinline__ void mr_gemm(MrhsShared& S, const float* __restrict__ D, int ld,
-                                        const float* __restrict__ Th, int ldt, int c_lo, int c_hi, float (&acc)[4][4],
-                                        float (&cmp)[4][4])
+__device__ __noinline__ void mr_gemm(MrhsShared& S, const float* __restrict__ D, int ld,
+                                        const float* __restrict__ Th, int ldt, int c_lo, int c_hi, float (&acc_out)[4][4],
+                                        float (&cmp_out)[4][4])
 {
+    // accumulators in registers of this function; the caller's arrays are written once at the end
+    float acc[4][4], cmp[4][4];
+    MrhsStage32& St = *reinterpret_cast<MrhsStage32*>(S.stage);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
 #pragma unroll
@@ -173,7 +228,19 @@ __device__ __forceinline__ void mr_gemm(MrhsShared& S, const float* __restrict__
             acc[j][q] = 0.f;
             cmp[j][q] = 0.f;
         }
-    if (c_lo >= c_hi) return;
+    auto store = [&]() {
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                acc_out[j][q] = acc[j][q];
+                cmp_out[j][q] = cmp[j][q];
+            }
+    };
+    if (c_lo >= c_hi) {
+        store();
+        return;
+    }
     auto issue = [&](int c, int buf) {
         const int n0 = c * kMKC;
 #pragma unroll
@@ -184,34 +251,39 @@ __device__ __forceinline__ void mr_gemm(MrhsShared& S, const float* __restrict__
             const int n = n0 + 4 * v;
             const bool ok = col >= 0 && n < ld;  // rows N..ld-1 of the owned copy are zero
             const float* src = ok ? D + (size_t)col * ld + n : D;
-            cp_async16(&S.Ds[buf][a][4 * v], src, ok ? 16 : 0);
+            cp_async16(&St.Ds[buf][a][4 * v], src, ok ? 16 : 0);
         }
         if (tid < JJ * 16 * 8) {
-            const int s = tid >> 3, v = tid & 7;
-            const int r = S.slot_r[s];
+            const int sl = tid >> 3, v = tid & 7;
+            const int r = S.slot_r[sl];
             const bool ok = r >= 0;
             const float* src = ok ? Th + (size_t)r * ldt + n0 + 4 * v : Th;
-            cp_async16(&S.Ts[buf][s][4 * v], src, ok ? 16 : 0);
+            cp_async16(&St.Ts[buf][sl][4 * v], src, ok ? 16 : 0);
         }
-        cp_async_commit();
     };
+    // prologue: kMStages - 1 chunks in flight (empty groups keep the counting uniform)
+#pragma unroll
+    for (int k = 0; k < kMStages - 1; k++) {
+        if (c_lo + k < c_hi) issue(c_lo + k, k);
+        cp_async_commit();
+    }
     int buf = 0;
-    issue(c_lo, 0);
     for (int c = c_lo; c < c_hi; c++) {
-        if (c + 1 < c_hi) {
-            issue(c + 1, buf ^ 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
+        cp_async_wait<kMStages - 2>();
+        __syncthreads();  // chunk c landed for every thread; chunk c-1's buffer is free
+        {
+            const int cn = c + kMStages - 1;
+            if (cn < c_hi) issue(cn, (buf + kMStages - 1) % kMStages);
+            cp_async_commit();
         }
-        __syncthreads();
+        const uint32_t dsb = smem_u32(&St.Ds[buf][ta][0]), tsb = smem_u32(&St.Ts[buf][tr][0]);
 #pragma unroll
         for (int k4 = 0; k4 < kMKC / 4; k4++) {
             float4 a4[4], t4[JJ];
 #pragma unroll
-            for (int j = 0; j < 4; j++) a4[j] = *reinterpret_cast<const float4*>(&S.Ds[buf][ta + 32 * j][4 * k4]);
+            for (int j = 0; j < 4; j++) a4[j] = lds128(dsb + (32 * j * kMST + 4 * k4) * 4);
 #pragma unroll
-            for (int q = 0; q < JJ; q++) t4[q] = *reinterpret_cast<const float4*>(&S.Ts[buf][tr + 16 * q][4 * k4]);
+            for (int q = 0; q < JJ; q++) t4[q] = lds128(tsb + (16 * q * kMST + 4 * k4) * 4);
 #pragma unroll
             for (int j = 0; j < 4; j++)
 #pragma unroll
@@ -238,9 +310,127 @@ __device__ __forceinline__ void mr_gemm(MrhsShared& S, const float* __restrict__
                     cmp[j][q] = 0.f;
                 }
         }
-        __syncthreads();
-        buf ^= 1;
+        buf = (buf + 1) % kMStages;
     }
+    cp_async_wait<0>();
+    __syncthreads();  // the staging is free for the caller
+    store();
+}
+
+// Z tile on the tensor cores: the BF16 copy of the tile's atoms times theta
+// split in BF16 (hi | lo), over row chunks [c_lo, c_hi) of 64 rows, through a
+// kTcStages-deep ring of 128-byte-swizzled stages (cp.async into the swizzled
+// positions, then one thread issues 4 MMAs of K = 16 per stage and commits them
+// to the stage's mbarrier, which frees the stage for reuse).  The FP32
+// accumulators (hi columns, then lo columns) go through a transposed shared
+// tile so that acc[j][q] has the thread mapping of the FP32 path.
+__device__ __noinline__ bool mr_gemm_tc(MrhsShared& S, const MrhsP& P, int c_lo, int c_hi, int JJ, TcState& tc,
+                                           float (&acc)[4][4])
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
+    const MrhsWs& W = P.ws;
+    const int nb = 16 * JJ;  // B rows per half
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[j][q] = 0.f;
+    if (c_lo >= c_hi) return true;
+    const int n = c_hi - c_lo;
+    const unsigned q0 = tc.q;
+    const uint32_t st0 = smem_u32(S.stage);
+    auto issue = [&](int i) {
+        const unsigned g = q0 + i;
+        unsigned char* A = S.stage + (g % kTcStages) * kTcStageBytes;
+        unsigned char* B = A + 16384;
+        const int n0 = (c_lo + i) * kTcRows;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int qd = tid + h * kThreads;
+            const int a = qd >> 3, cc = qd & 7;
+            const int col = S.cols[a];
+            const int nn = n0 + cc * 8;
+            const bool ok = col >= 0 && nn < P.ld_lo;  // rows N..ld_lo-1 of the copy are zero
+            const uint16_t* src = ok ? P.Dlo + (size_t)col * P.ld_lo + nn : P.Dlo;
+            cp_async16(A + sw128_offset(a, cc), src, ok ? 16 : 0);
+        }
+        for (int qd = tid; qd < 2 * nb * 8; qd += kThreads) {
+            const int row = qd >> 3, cc = qd & 7;
+            const int r = S.slot_r[row < nb ? row : row - nb];
+            const uint16_t* base = row < nb ? W.Thi : W.Tlo;
+            const bool ok = r >= 0;
+            const uint16_t* src = ok ? base + (size_t)r * P.npad + n0 + cc * 8 : base;
+            cp_async16(B + sw128_offset(row, cc), src, ok ? 16 : 0);
+        }
+    };
+    // a slot is rewritten only after the MMAs that read its previous stage completed
+    auto slot_free = [&](int i) -> bool {
+        const unsigned g = q0 + i;
+        if (g < (unsigned)kTcStages) return true;
+        const unsigned prev = g - kTcStages;
+        return mbar_wait(tc.mbar + (prev % kTcStages), (prev / kTcStages) & 1u);
+    };
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < kTcAhead; i++) {
+        if (i < n && ok) {
+            if (slot_free(i)) issue(i);
+            else ok = false;
+        }
+        cp_async_commit();
+    }
+    const uint32_t idesc = idesc_bf16_f32(128, 2 * nb);
+    for (int i = 0; i < n; i++) {
+        const int ia = i + kTcAhead;
+        if (ia < n && ok) {
+            if (slot_free(ia)) issue(ia);
+            else ok = false;
+        }
+        cp_async_commit();
+        cp_async_wait<kTcAhead>();  // this thread's copies of stage i landed
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0 && ok) {
+            tc_fence_after();
+            const unsigned g = q0 + i;
+            const uint32_t A = st0 + (g % kTcStages) * kTcStageBytes, B = A + 16384;
+#pragma unroll
+            for (int k = 0; k < kTcRows / 16; k++)
+                mma_bf16(tc.tmem, sw128_desc(A + 32 * k), sw128_desc(B + 32 * k), idesc, (i > 0 || k > 0) ? 1u : 0u);
+            mma_commit(tc.mbar + (g % kTcStages));
+        }
+    }
+    cp_async_wait<0>();
+    if (!__syncthreads_and(ok)) return false;
+    tc.q = q0 + n;
+    tc.issued = tc.q;
+    {
+        const unsigned g = q0 + n - 1;
+        if (!__syncthreads_and(mbar_wait(tc.mbar + (g % kTcStages), (g / kTcStages) & 1u))) return false;
+    }
+    tc_fence_after();
+    float* Zs = reinterpret_cast<float*>(S.stage);  // [kMTA][kZst]; every stage has been consumed
+    {
+        const int qw = warp & 3, pw = warp >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * qw) << 16;
+        for (int cc = 0; cc < JJ; cc++) {
+            const int c0 = pw * 4 * JJ + 4 * cc;
+            float hi[4], lo[4];
+            tmem_ld4(tc.tmem + lane_base + c0, hi);
+            tmem_ld4(tc.tmem + lane_base + nb + c0, lo);
+#pragma unroll
+            for (int k = 0; k < 4; k++) Zs[(32 * qw + lane) * kZst + c0 + k] = hi[k] + lo[k];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (q < JJ) acc[j][q] = Zs[(ta + 32 * j) * kZst + tr + 16 * q];
+    __syncthreads();  // the staging is free again
+    return true;
 }
 
 template <bool COMP>
@@ -273,22 +463,38 @@ __device__ __forceinline__ int mr_splits(int TA, int G, int nc)
     return best;
 }
 
-// The tiles of `nA` list atoms (ids from `list`, or the identity when null),
-// split over rows; calls epi(acc, cmp) in the CTA that finishes a tile, with
-// S.cols holding the tile's atoms.  Returns false on a failed wait.
-template <bool COMP, typename Epi>
-__device__ __forceinline__ void mr_tiles(MrhsShared& S, const MrhsP& P, const int* list, int nA, const float* Th,
-                                         int JJ, int b, int G, Epi epi)
+// Work counter of the team's next claim loop: the loops take the three
+// counters in turn, and each resets the one the next loop will use (its last
+// use was two grid phases earlier).
+__device__ __forceinline__ int* mr_counter(const MrhsWs& W, int& cu, int b)
 {
+    int* c = W.ctr + (cu % 3);
+    if (b == 0 && threadIdx.x == 0) W.ctr[(cu + 1) % 3] = 0;
+    cu++;
+    return c;
+}
+
+// The tiles of `nA` list atoms (ids from `list`, or the identity when null),
+// split over rows and claimed by the team's CTAs from `ctr`; calls epi(acc, cmp)
+// in the CTA that finishes a tile, with S.cols holding the tile's atoms.
+template <int KIND, typename Epi>
+__device__ __forceinline__ bool mr_tiles(MrhsShared& S, const MrhsP& P, const int* list, int nA, const float* Th,
+                                         int JJ, int G, int* ctr, TcState& tc, Epi epi)
+{
+    constexpr bool COMP = KIND == 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
     const MrhsWs& W = P.ws;
     const int TA = (nA + kMTA - 1) / kMTA;
-    const int nc = P.npad / kMKC;
+    const int nc = P.npad / (KIND == 2 ? kTcRows : kMKC);
     const int Sk = mr_splits(TA, G, nc);
     const int items = TA * Sk;
     constexpr int TS = kMTA * kMR * (COMP ? 2 : 1);
-    for (int it = b; it < items; it += G) {
+    for (;;) {
+        if (tid == 0) S.claim = atomicAdd(ctr, 1);
+        __syncthreads();
+        const int it = S.claim;
+        if (it >= items) return true;
         const int ti = it / Sk, sk = it - ti * Sk;
         const int c_lo = sk * nc / Sk, c_hi = (sk + 1) * nc / Sk;
         if (tid < kMTA) {
@@ -297,7 +503,11 @@ __device__ __forceinline__ void mr_tiles(MrhsShared& S, const MrhsP& P, const in
         }
         __syncthreads();
         float acc[4][4], cmp[4][4];
-        mr_gemm_any<COMP>(JJ, S, P.D, P.ld, Th, P.npad, c_lo, c_hi, acc, cmp);
+        if (KIND == 2) {
+            if (!mr_gemm_tc(S, P, c_lo, c_hi, JJ, tc, acc)) return false;
+        } else {
+            mr_gemm_any<COMP>(JJ, S, P.D, P.ld, Th, P.npad, c_lo, c_hi, acc, cmp);
+        }
         bool fin = true;
         if (Sk > 1) {
             float* pt = W.part + (size_t)it * TS;
@@ -340,17 +550,30 @@ __device__ __forceinline__ void mr_tiles(MrhsShared& S, const MrhsP& P, const in
     }
 }
 
-// Sum of n float-float partials in a fixed order (one warp).
-__device__ __forceinline__ double mr_ff_sum(const FF* p, int n, int lane) { return part_sum_fixed(p, n, lane); }
-__device__ __forceinline__ int mr_int_sum(const int* p, int n, int lane) { return (int)warp_sum_fixed(p, n, lane); }
+// ----------------------------------------------------- block-wide reductions
+//
+// Per-problem partials are laid out [unit][kMR].  Warp w adds units w, w+16,
+// ... for problems lane and lane + 32 (fixed order); thread r < kMR then adds
+// the 16 warp results in warp order.  Every CTA that reduces the same
+// partials gets the same bits.
+
+struct RedScratch {
+    float s[8][kMW][kMR];  // up to four float-float sums
+    int n[3][kMW][kMR];    // up to three integer sums
+};
+static_assert(sizeof(RedScratch) <= kStageBytes, "reduction scratch exceeds the staging area");
 
 // --------------------------------------------------------------- the body
 
 // One block of problems by a team of G CTAs (rank b) on barrier `bar`.
-__device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G, GridBarrier* bar, unsigned int& gen)
+__device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G, GridBarrier* bar, unsigned int& gen,
+                                       TcState& tc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    MrhsShared& S = *reinterpret_cast<MrhsShared*>(smem_raw);
+    // the staging area starts on a 1024-byte boundary (swizzled tensor-core tiles)
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_raw);
+    MrhsShared& S = *reinterpret_cast<MrhsShared*>(smem_raw + ((1024u - (sa & 1023u)) & 1023u));
+    RedScratch& RS = *reinterpret_cast<RedScratch*>(S.stage);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ta = warp * 2 + (lane >> 4), tr = lane & 15;
     const MrhsWs& W = P.ws;
@@ -360,6 +583,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
     const bool need_n = P.test == 2 || P.test == 3;
     const bool ista = P.alg == 0;
     const float invL = (float)(1.0 / P.L);
+    int cu = 0;  // claim loops so far (same in every CTA)
 
     // -------------------------------------------- (C0a) staging, ||y_r||^2
     if (tid < kMR) S.slot_r[tid] = tid < R ? tid : -1;
@@ -369,39 +593,60 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         W.Yt[k] = (r < R && n < N) ? P.Y[(size_t)r * N + n] : 0.f;
         W.Th[k] = 0.f;
         W.Dst[k] = 0.f;
+        if (P.use_tc) {
+            W.Thi[k] = 0;
+            W.Tlo[k] = 0;
+        }
     }
     for (size_t k = (size_t)b * kThreads + tid; k < (size_t)R * K; k += (size_t)G * kThreads) {
         const int r = (int)(k / K);
         P.X[(size_t)r * K + (k - (size_t)r * K)] = 0.f;
     }
     for (int k = b * kThreads + tid; k < (K + kMTA - 1) / kMTA; k += G * kThreads) W.tilecnt[k] = 0;
-    for (int it = gwarp; it < ntile * R; it += twarps) {
-        const int r = it / ntile, rt = it - r * ntile;
+    if (b == 0 && tid < 3) W.ctr[tid] = 0;
+    for (int it = gwarp; it < ntile * kMR; it += twarps) {
+        const int rt = it / kMR, r = it - rt * kMR;
         Dot2f acc;
-        for (int k = 0; k < kMSynRows / 32; k++) {
-            const int n = rt * kMSynRows + 32 * k + lane;
-            if (n < N) {
-                const float v = P.Y[(size_t)r * N + n];
-                acc.add(v, v);
+        if (r < R) {
+            for (int k = 0; k < kMSynRows / 32; k++) {
+                const int n = rt * kMSynRows + 32 * k + lane;
+                if (n < N) {
+                    const float v = P.Y[(size_t)r * N + n];
+                    acc.add(v, v);
+                }
             }
         }
         acc = dot2_warp_reduce(acc);
-        if (lane == 0) W.p_a[r * ntile + rt] = FF{acc.s, acc.c};
+        if (lane == 0) W.p_a[rt * kMR + r] = FF{acc.s, acc.c};
     }
     if (!grid_sync(bar, G, gen)) return false;
 
     // -------------------------------------------- (C0b) B = D^T Y (compensated), lambda_*
-    for (int r = warp; r < R; r += kMW) {
-        const double s = mr_ff_sum(W.p_a + r * ntile, ntile, lane);
-        if (lane == 0) S.yy[r] = s;
-    }
     {
+        // ||y_r||^2
+        for (int h = 0; h < 2; h++) {
+            const int r = lane + 32 * h;
+            Dot2f a;
+            for (int u = warp; u < ntile; u += kMW) {
+                const FF v = ldcg_x(W.p_a + u * kMR + r);
+                dot2_merge(a, v.h, v.l);
+            }
+            RS.s[0][warp][r] = a.s;
+            RS.s[1][warp][r] = a.c;
+        }
+        __syncthreads();
+        if (tid < kMR) {
+            Dot2f a;
+            for (int w = 0; w < kMW; w++) dot2_merge(a, RS.s[0][w][tid], RS.s[1][w][tid]);
+            S.yy[tid] = a.value();
+        }
+        __syncthreads();
         const int JJ = (R + 15) / 16;
         double best[4];
         int arg[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) { best[q] = -1.0; arg[q] = 0x7fffffff; }
-        mr_tiles<true>(S, P, nullptr, K, W.Yt, JJ, b, G, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
+        if (!mr_tiles<1>(S, P, nullptr, K, W.Yt, JJ, G, mr_counter(W, cu, b), tc, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int i = S.cols[ta + 32 * j];
@@ -417,43 +662,60 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     if (a > best[q] || (a == best[q] && i < arg[q])) { best[q] = a; arg[q] = i; }
                 }
             }
-        });
+        })) return false;
         // per-CTA argmax: the two halves of each warp, then the warps in order
+        double* bv = reinterpret_cast<double*>(S.stage);        // [kMW][kMR]
+        int* bi = reinterpret_cast<int*>(bv + kMW * kMR);        // [kMW][kMR]
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const double ob = __shfl_xor_sync(0xffffffffu, best[q], 16);
             const int oa = __shfl_xor_sync(0xffffffffu, arg[q], 16);
             if (ob > best[q] || (ob == best[q] && oa < arg[q])) { best[q] = ob; arg[q] = oa; }
-            if (lane < 16 && q < JJ) { S.bv[warp][tr + 16 * q] = best[q]; S.bi[warp][tr + 16 * q] = arg[q]; }
+            if (lane < 16 && q < JJ) { bv[warp * kMR + tr + 16 * q] = best[q]; bi[warp * kMR + tr + 16 * q] = arg[q]; }
         }
         __syncthreads();
         if (tid < R) {
             double bb = -1.0;
             int ba = 0x7fffffff;
-            for (int w = 0; w < kMW; w++)
-                if (S.bv[w][tid] > bb || (S.bv[w][tid] == bb && S.bi[w][tid] < ba)) { bb = S.bv[w][tid]; ba = S.bi[w][tid]; }
-            W.p_v[tid * G + b] = bb;
-            W.p_i[tid * G + b] = ba;
+            for (int w = 0; w < kMW; w++) {
+                const double v = bv[w * kMR + tid];
+                const int a = bi[w * kMR + tid];
+                if (v > bb || (v == bb && a < ba)) { bb = v; ba = a; }
+            }
+            W.p_v[b * kMR + tid] = bb;
+            W.p_i[b * kMR + tid] = ba;
         }
+        __syncthreads();
     }
     if (!grid_sync(bar, G, gen)) return false;
 
     // -------------------------------------------- (C0c) per problem: lambda, the test centres
-    for (int r = warp; r < R; r += kMW) {
-        double bb = -1.0;
-        int ba = 0x7fffffff;
-        for (int k = lane; k < G; k += 32) {
-            const double v = __ldcg(W.p_v + r * G + k);
-            const int a = __ldcg(W.p_i + r * G + k);
-            if (v > bb || (v == bb && a < ba)) { bb = v; ba = a; }
+    {
+        double* bv = reinterpret_cast<double*>(S.stage);
+        int* bi = reinterpret_cast<int*>(bv + kMW * kMR);
+        for (int h = 0; h < 2; h++) {
+            const int r = lane + 32 * h;
+            double bb = -1.0;
+            int ba = 0x7fffffff;
+            if (r < R)
+                for (int u = warp; u < G; u += kMW) {
+                    const double v = __ldcg(W.p_v + u * kMR + r);
+                    const int a = __ldcg(W.p_i + u * kMR + r);
+                    if (v > bb || (v == bb && a < ba)) { bb = v; ba = a; }
+                }
+            bv[warp * kMR + r] = bb;
+            bi[warp * kMR + r] = ba;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, bb, o);
-            const int oa = __shfl_xor_sync(0xffffffffu, ba, o);
-            if (ob > bb || (ob == bb && oa < ba)) { bb = ob; ba = oa; }
-        }
-        if (lane == 0) {
+        __syncthreads();
+        if (tid < R) {
+            const int r = tid;
+            double bb = -1.0;
+            int ba = 0x7fffffff;
+            for (int w = 0; w < kMW; w++) {
+                const double v = bv[w * kMR + r];
+                const int a = bi[w * kMR + r];
+                if (v > bb || (v == bb && a < ba)) { bb = v; ba = a; }
+            }
             const double lstar = bb;
             const double lam = P.lambda_rel ? P.lambdas[r] * lstar : P.lambdas[r];
             S.lstar[r] = lstar;
@@ -474,8 +736,8 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
             S.primal[r] = 0.0;
             S.iters[r] = 0;
         }
+        __syncthreads();
     }
-    __syncthreads();
     if (tid == 0) {
         unsigned long long live = 0;
         for (int r = 0; r < R; r++)
@@ -483,6 +745,16 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         S.live = live;
         S.ccorr = (long long)K * (need_n ? 2 : 1);
         S.lf = 1.0;
+        S.low = P.use_tc ? 1 : 0;
+        S.lowB = 0;
+        S.t0 = 0;
+        S.clowp = 0;
+        for (int r = 0; r < kMR; r++) {
+            S.best_gap[r] = INFINITY;
+            S.since[r] = 0;
+            S.swok[r] = 1;
+            S.R2s[r] = 0.0;
+        }
         int k = 0;
         for (int r = 0; r < kMR; r++)
             if ((live >> r) & 1) S.slot_r[k++] = r;
@@ -511,7 +783,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         }
         if (!grid_sync(bar, G, gen)) return false;
         const int JJ = (S.n_slots + 15) / 16;
-        mr_tiles<true>(S, P, nullptr, K, W.Dst, JJ, b, G, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
+        if (!mr_tiles<1>(S, P, nullptr, K, W.Dst, JJ, G, mr_counter(W, cu, b), tc, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int i = S.cols[ta + 32 * j];
@@ -524,7 +796,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     W.Q1[(size_t)i * kMR + r] = (double)acc[j][q] + (double)cmp[j][q];
                 }
             }
-        });
+        })) return false;
         if (!grid_sync(bar, G, gen)) return false;
     }
 
@@ -598,10 +870,10 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         }
         if (lane == 0) S.ired[warp] = kept;
         if (tid < kMR) {
-            W.c_nz[tid * G + b] = 0;
-            W.p_l1[tid * G + b] = FF{0.f, 0.f};
-            W.c_na[tid * G + b] = 0;
-            W.c_nnzx[tid * G + b] = 0;
+            W.c_nz[b * kMR + tid] = 0;
+            W.p_l1[b * kMR + tid] = FF{0.f, 0.f};
+            W.c_na[b * kMR + tid] = 0;
+            W.c_nnzx[b * kMR + tid] = 0;
         }
         __syncthreads();
         if (tid == 0) {
@@ -632,12 +904,12 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 }
                 base = warp_sum(base);
                 tot = warp_sum(tot);
-                if (lane == 0) { S.ired[0] = base; S.ired[1] = tot; }
+                if (lane == 0) { S.keep_base = base; S.keep_tot = tot; }
             }
             for (int k = tid; k < G; k += kThreads) S.alo[k] = __ldcg(W.s_alo + k);
             __syncthreads();
-            int gb = S.ired[0];
-            const int nA_new = S.ired[1];
+            int gb = S.keep_base;
+            const int nA_new = S.keep_tot;
             for (int base = p_lo; base < p_hi; base += kThreads) {
                 const int p = base + tid;
                 const int k = p < p_hi ? __ldcg(W.keep + p) : 0;
@@ -646,15 +918,20 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 if (k) W.act[nxt][gb + pre] = __ldcg(W.act[cur] + p);
                 gb += tot;
             }
-            // syntheses: items (row tile, live problem)
+            // syntheses: items (live problem, row tile), claimed by warps
             const int ns = S.n_slots;
-            for (int it = gwarp; it < ntile * ns; it += twarps) {
+            int* ctr = mr_counter(W, cu, b);
+            for (;;) {
+                int it = 0;
+                if (lane == 0) it = atomicAdd(ctr, 1);
+                it = __shfl_sync(0xffffffffu, it, 0);
+                if (it >= ntile * ns) break;
                 const int s = it / ntile, rt = it - s * ntile;
                 const int r = S.slot_r[s];
                 int run = 0;
                 for (int b0 = 0; b0 < G; b0 += 32) {
                     const int bb = b0 + lane;
-                    const int c = bb < G ? __ldcg(W.c_nz + r * G + bb) : 0;
+                    const int c = bb < G ? __ldcg(W.c_nz + bb * kMR + r) : 0;
                     int x = c;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
@@ -713,31 +990,43 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     }
                 }
                 Dot2f pa, pb, pr;
-                {
-                    if (n0 < N) {
-                        const float yv = __ldcg(W.Yt + (size_t)r * npad + n0);
-                        const float th = theta_from(au0, yv);
-                        W.Th[(size_t)r * npad + n0] = th;
-                        pa.add(th, yv);
-                        pb.add(th, th);
-                        acc_resid_sq(pr, ax0, yv);
+                if (n0 < N) {
+                    const float yv = __ldcg(W.Yt + (size_t)r * npad + n0);
+                    const float th = theta_from(au0, yv);
+                    W.Th[(size_t)r * npad + n0] = th;
+                    if (P.use_tc) {
+                        // theta = hi + lo + O(2^-18 |theta|) in BF16, for the tensor cores
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(th);
+                        const __nv_bfloat16 lb = __float2bfloat16_rn(th - __bfloat162float(hb));
+                        W.Thi[(size_t)r * npad + n0] = __bfloat16_as_ushort(hb);
+                        W.Tlo[(size_t)r * npad + n0] = __bfloat16_as_ushort(lb);
                     }
-                    if (n1 < N) {
-                        const float yv = __ldcg(W.Yt + (size_t)r * npad + n1);
-                        const float th = theta_from(au1, yv);
-                        W.Th[(size_t)r * npad + n1] = th;
-                        pa.add(th, yv);
-                        pb.add(th, th);
-                        acc_resid_sq(pr, ax1, yv);
+                    pa.add(th, yv);
+                    pb.add(th, th);
+                    acc_resid_sq(pr, ax0, yv);
+                }
+                if (n1 < N) {
+                    const float yv = __ldcg(W.Yt + (size_t)r * npad + n1);
+                    const float th = theta_from(au1, yv);
+                    W.Th[(size_t)r * npad + n1] = th;
+                    if (P.use_tc) {
+                        // theta = hi + lo + O(2^-18 |theta|) in BF16, for the tensor cores
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(th);
+                        const __nv_bfloat16 lb = __float2bfloat16_rn(th - __bfloat162float(hb));
+                        W.Thi[(size_t)r * npad + n1] = __bfloat16_as_ushort(hb);
+                        W.Tlo[(size_t)r * npad + n1] = __bfloat16_as_ushort(lb);
                     }
+                    pa.add(th, yv);
+                    pb.add(th, th);
+                    acc_resid_sq(pr, ax1, yv);
                 }
                 pa = dot2_warp_reduce(pa);
                 pb = dot2_warp_reduce(pb);
                 pr = dot2_warp_reduce(pr);
                 if (lane == 0) {
-                    W.p_a[r * ntile + rt] = FF{pa.s, pa.c};
-                    W.p_b[r * ntile + rt] = FF{pb.s, pb.c};
-                    W.p_r[r * ntile + rt] = FF{pr.s, pr.c};
+                    W.p_a[rt * kMR + r] = FF{pa.s, pa.c};
+                    W.p_b[rt * kMR + r] = FF{pb.s, pb.c};
+                    W.p_r[rt * kMR + r] = FF{pr.s, pr.c};
                 }
                 __syncwarp();
             }
@@ -751,45 +1040,110 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         {
             const int nA = S.nA;
             const int ns = S.n_slots;
-            for (int s = warp; s < ns; s += kMW) {
-                const int r = S.slot_r[s];
-                const double a_ = mr_ff_sum(W.p_a + r * ntile, ntile, lane);
-                const double b_ = mr_ff_sum(W.p_b + r * ntile, ntile, lane);
-                const double r_ = mr_ff_sum(W.p_r + r * ntile, ntile, lane);
-                const double l1 = mr_ff_sum(W.p_l1 + r * G, G, lane);
-                const int na = mr_int_sum(W.c_na + r * G, G, lane);
-                const int nx = mr_int_sum(W.c_nnzx + r * G, G, lane);
-                const int ne = mr_int_sum(W.c_nz + r * G, G, lane);
-                if (lane == 0) {
-                    const double lam = S.lam[r], yy = S.yy[r];
-                    int stop = 0;
-                    if (t > 1) {
-                        // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                        const double primal = 0.5 * r_ + lam * l1;
-                        const double gap = primal - 0.5 * yy + 0.5 * lam * lam * S.R2n[r];
-                        S.primal[r] = primal;
-                        S.gap[r] = gap;
-                        S.iters[r] = t - 1;
-                        S.na[r] = na;
-                        S.nnzx[r] = nx;
-                        stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+            const unsigned long long live = S.live;
+            // per-problem sums of the row-tile partials and of the CTA partials of (C)
+            for (int h = 0; h < 2; h++) {
+                const int r = lane + 32 * h;
+                Dot2f a, bq, rq, l1;
+                int na = 0, nx = 0, ne = 0;
+                if ((live >> r) & 1) {
+#pragma unroll 2
+                    for (int u = warp; u < ntile; u += kMW) {
+                        const FF va = ldcg_x(W.p_a + u * kMR + r), vb = ldcg_x(W.p_b + u * kMR + r);
+                        const FF vr = ldcg_x(W.p_r + u * kMR + r);
+                        dot2_merge(a, va.h, va.l);
+                        dot2_merge(bq, vb.h, vb.l);
+                        dot2_merge(rq, vr.h, vr.l);
                     }
-                    S.csyn[r] += ne;
-                    S.alpha[r] = a_;
-                    S.beta[r] = b_;
-                    S.s_unc[r] = b_ > 0.0 ? a_ / lam * fast_rcp(b_) : 0.0;
-                    S.sqrt_beta[r] = (double)sqrtf((float)b_) * (1.0 + 1e-6);
-                    S.stopnow[r] = stop;
+#pragma unroll 4
+                    for (int u = warp; u < G; u += kMW) {
+                        const FF vl = ldcg_x(W.p_l1 + u * kMR + r);
+                        const int c0 = __ldcg(W.c_na + u * kMR + r), c1 = __ldcg(W.c_nnzx + u * kMR + r);
+                        const int c2 = __ldcg(W.c_nz + u * kMR + r);
+                        dot2_merge(l1, vl.h, vl.l);
+                        na += c0;
+                        nx += c1;
+                        ne += c2;
+                    }
                 }
+                RS.s[0][warp][r] = a.s;  RS.s[1][warp][r] = a.c;
+                RS.s[2][warp][r] = bq.s; RS.s[3][warp][r] = bq.c;
+                RS.s[4][warp][r] = rq.s; RS.s[5][warp][r] = rq.c;
+                RS.s[6][warp][r] = l1.s; RS.s[7][warp][r] = l1.c;
+                RS.n[0][warp][r] = na;   RS.n[1][warp][r] = nx;   RS.n[2][warp][r] = ne;
+            }
+            __syncthreads();
+            if (tid < kMR && ((live >> tid) & 1)) {
+                const int r = tid;
+                Dot2f a, bq, rq, l1;
+                int na = 0, nx = 0, ne = 0;
+                for (int w = 0; w < kMW; w++) {
+                    dot2_merge(a, RS.s[0][w][r], RS.s[1][w][r]);
+                    dot2_merge(bq, RS.s[2][w][r], RS.s[3][w][r]);
+                    dot2_merge(rq, RS.s[4][w][r], RS.s[5][w][r]);
+                    dot2_merge(l1, RS.s[6][w][r], RS.s[7][w][r]);
+                    na += RS.n[0][w][r];
+                    nx += RS.n[1][w][r];
+                    ne += RS.n[2][w][r];
+                }
+                const double a_ = a.value(), b_ = bq.value(), r_ = rq.value(), l1_ = l1.value();
+                const double lam = S.lam[r], yy = S.yy[r];
+                int stop = 0;
+                S.swok[r] = 1;
+                if (t > 1) {
+                    // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
+                    const double primal = 0.5 * r_ + lam * l1_;
+                    double gap = primal - 0.5 * yy + 0.5 * lam * lam * S.R2n[r];
+                    if (S.lowB) {
+                        // the nominal gap rests on the copy's correlations: stop only on the rigorous
+                        // one (dual point scaled with the bounded max), and let the block leave the copy
+                        // once every problem's nominal gap reached the switch level or stalled
+                        if (gap < 0.99 * S.best_gap[r]) {
+                            S.best_gap[r] = gap;
+                            S.since[r] = 0;
+                        } else {
+                            S.since[r]++;
+                        }
+                        S.swok[r] = (gap <= P.lo_switch * 0.5 * yy) || S.since[r] >= 25;
+                        gap = primal - 0.5 * yy + 0.5 * lam * lam * S.R2s[r];
+                    }
+                    S.primal[r] = primal;
+                    S.gap[r] = gap;
+                    S.iters[r] = t - 1;
+                    S.na[r] = na;
+                    S.nnzx[r] = nx;
+                    stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                }
+                S.csyn[r] += ne;
+                S.alpha[r] = a_;
+                S.beta[r] = b_;
+                S.s_unc[r] = b_ > 0.0 ? a_ / lam * fast_rcp(b_) : 0.0;
+                S.sqrt_beta[r] = (double)sqrtf((float)b_) * (1.0 + 1e-6);
+                S.stopnow[r] = stop;
             }
             __syncthreads();
             if (tid == 0) {
+                if (S.low && t > 1) {
+                    // FP32 polish: a fresh FISTA sequence from the bulk iterate, for the whole block
+                    bool all = true;
+                    for (int q = 0; q < ns; q++) {
+                        const int r = S.slot_r[q];
+                        if (!S.stopnow[r] && !S.swok[r]) all = false;
+                    }
+                    if (all) {
+                        S.low = 0;
+                        S.t0 = t - 1;
+                        S.lf = 1.0;
+                    }
+                }
+                S.lowB = S.low;
                 double bt = 0.0;
+                const int tf = t - S.t0;  // index in the current FISTA sequence
                 if (!ista) {
                     // FISTA (Table 1): l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t
-                    if (t <= P.fista_n) {
-                        bt = P.fista[2 * (t - 1)];
-                        S.lf = P.fista[2 * (t - 1) + 1];
+                    if (tf <= P.fista_n) {
+                        bt = P.fista[2 * (tf - 1)];
+                        S.lf = P.fista[2 * (tf - 1) + 1];
                     } else {
                         const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * S.lf * S.lf));
                         bt = (S.lf - 1.0) / ln;
@@ -800,12 +1154,10 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 unsigned long long dm = 0;
                 for (int s = 0; s < ns; s++)
                     if (S.stopnow[S.slot_r[s]]) dm |= 1ull << S.slot_r[s];
-                S.ired[2] = (int)(dm & 0xffffffffu);
-                S.ired[3] = (int)(dm >> 32);
+                S.dm = dm;
             }
             __syncthreads();
-            const unsigned long long dm =
-                ((unsigned long long)(unsigned)S.ired[3] << 32) | (unsigned long long)(unsigned)S.ired[2];
+            const unsigned long long dm = S.dm;
             if (dm) {
                 // problems that met their tolerance leave the block: x of iteration t-1 out
                 const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
@@ -833,7 +1185,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     o.lambda_max = S.lstar[r];
                     o.cols_corr = S.ccorr;
                     o.cols_synth = S.csyn[r];
-                    o.cols_lowp = 0;
+                    o.cols_lowp = S.clowp;
                 }
                 __syncthreads();
                 if (tid == 0) {
@@ -847,14 +1199,17 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 __syncthreads();
             }
             if (S.live == 0ull) break;
-            if (tid == 0) S.ccorr += nA;
+            if (tid == 0) {
+                S.ccorr += nA;
+                if (S.lowB) S.clowp += nA;
+            }
             if (tid < kMR) S.zmax[tid] = 0u;
             __syncthreads();
             const int ns2 = S.n_slots;
             const int JJ = (ns2 + 15) / 16;
             float zm[4] = {0.f, 0.f, 0.f, 0.f};
             FF* xo = W.xb[xi ^ 1];
-            mr_tiles<false>(S, P, W.act[cur], nA, W.Th, JJ, b, G, [&](float (&acc)[4][4], float (&)[4][4]) {
+            auto prox = [&](float (&acc)[4][4], float (&)[4][4]) {
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int i = S.cols[ta + 32 * j];
@@ -876,29 +1231,55 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                         xo[idx] = xn;
                     }
                 }
-            });
+            };
+            // bulk phase: the BF16 copy on the tensor cores; then the FP32 master
+            int* ctr = mr_counter(W, cu, b);
+            const bool okt = S.lowB ? mr_tiles<2>(S, P, W.act[cur], nA, W.Th, JJ, G, ctr, tc, prox)
+                                    : mr_tiles<0>(S, P, W.act[cur], nA, W.Th, JJ, G, ctr, tc, prox);
+            if (!okt) return false;
 #pragma unroll
             for (int q = 0; q < 4; q++)
                 if (q < JJ) atomicMax(&S.zmax[tr + 16 * q], __float_as_uint(zm[q]));
             __syncthreads();
-            if (tid < ns2) W.p_m[S.slot_r[tid] * G + b] = __uint_as_float(S.zmax[tid]);
+            if (tid < kMR) {
+                const int r = tid;
+                // this CTA's max |z| of every live problem (0 when it finished no tile)
+                float v = 0.f;
+                for (int s = 0; s < ns2; s++)
+                    if (S.slot_r[s] == r) v = __uint_as_float(S.zmax[s]);
+                if ((S.live >> r) & 1) W.p_m[b * kMR + r] = v;
+            }
         }
         if (!grid_sync(bar, G, gen)) return false;
 
         // ======================================== (C) screening + momentum
         {
             const int nA = S.nA;
-            const int ns = S.n_slots;
-            for (int s = warp; s < ns; s += kMW) {
-                const int r = S.slot_r[s];
-                float mf = 0.f;
-                for (int k = lane; k < G; k += 32) mf = fmaxf(mf, __ldcg(W.p_m + r * G + k));
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-                if (lane == 0) {
+            const unsigned long long live = S.live;
+            {
+                // m_r = max_i |z_i| over the CTA partials, then Lemma 8 and the radius per problem
+                float* mx = reinterpret_cast<float*>(S.stage);  // [kMW][kMR]
+                for (int h = 0; h < 2; h++) {
+                    const int r = lane + 32 * h;
+                    float m = 0.f;
+                    if ((live >> r) & 1) {
+#pragma unroll 4
+                        for (int u = warp; u < G; u += kMW) m = fmaxf(m, __ldcg(W.p_m + u * kMR + r));
+                    }
+                    mx[warp * kMR + r] = m;
+                }
+                __syncthreads();
+                if (tid < kMR && ((live >> tid) & 1)) {
+                    const int r = tid;
+                    float mf = 0.f;
+                    for (int w = 0; w < kMW; w++) mf = fmaxf(mf, mx[w * kMR + r]);
                     // Lemma 8 with the nominal max |z| (gap) and a rigorous upper bound of it (radius)
                     const double m_nom = (double)mf;
-                    const double m_up = m_nom + P.gamma * P.fmax * S.sqrt_beta[r];
+                    // copy: |z_i - zc_i| <= ||d_i - copy_i|| ||theta|| + ||copy_i|| (||theta - hi - lo|| +
+                    // the accumulation bound of the tensor-core sums)
+                    const double m_up =
+                        m_nom + (S.lowB ? P.emax + (P.fmax + P.emax) * (0x1p-17 + P.gamma_tc) : P.gamma * P.fmax) *
+                                    S.sqrt_beta[r];
                     const double su = S.s_unc[r];
                     const double mu_nom = (m_nom > 0.0 && fabs(su) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), su) : su;
                     const double mu_s = (m_up > 0.0 && fabs(su) * m_up > 1.0) ? copysign(fast_rcp(m_up), su) : su;
@@ -906,15 +1287,15 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     const double yyl2 = S.yy[r] * il * il;
                     S.R2n[r] = fmax(fma(mu_nom, fma(mu_nom, S.beta[r], -2.0 * S.alpha[r] * il), yyl2), 0.0);
                     const double R2s = fmax(fma(mu_s, fma(mu_s, S.beta[r], -2.0 * S.alpha[r] * il), yyl2), 0.0);
+                    S.R2s[r] = R2s;
                     const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
                     S.Rs[r] = Rs;
                     S.rad[r] = P.test == 2 ? fast_sqrt(fmax(R2s - S.delta[r] * S.delta[r], 0.0)) * (1.0 + 1e-13) : Rs;
                     const double psi = S.psi_d[r];
                     S.rho[r] = fast_sqrt(fmax(Rs * Rs - psi * psi, 0.0)) * (1.0 + 1e-13);
                 }
+                __syncthreads();
             }
-            __syncthreads();
-            const unsigned long long live = S.live;
             const FF btX = ff_from_double(S.bt);
             const bool dyn = P.dynamic && P.test != 0;
             const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
@@ -935,63 +1316,90 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 psih[h] = lv[h] ? S.psi_d[r] : 0.0;
                 ilh[h] = lv[h] ? 1.0 / S.lam[r] : 0.0;
             }
-            for (int p = w_lo; p < w_hi; p++) {
-                const int i = __ldcg(W.act[cur] + p);
-                const unsigned long long m = __ldcg(W.amask + i);
-                bool on[2], nz[2];
-                for (int h = 0; h < 2; h++) {
-                    const int r = lane + 32 * h;
-                    const size_t idx = (size_t)i * kMR + r;
-                    on[h] = lv[h] && ((m >> r) & 1);
-                    nz[h] = false;
-                    if (!on[h]) continue;
-                    bool kill = false;
-                    if (dyn) {
-                        if (!dome) {
-                            kill = __ldcg(W.Q0 + idx) - radh[h] > P.eps_test;
-                        } else {
-                            // Lemma 4 in its dynamic form: max over the dome of |d_i^T theta| < 1
-                            const double dc0 = __ldcg(W.Q0 + idx) * ilh[h];
-                            const double tt = __ldcg(W.Q1 + idx), sq = __ldcg(W.Q2 + idx);
-                            const double inv = __ldcg(W.invn + i);
-                            const double Rr = Rsh[h], psi = psih[h], rho = rhoh[h];
-                            const double up = (tt * Rr <= -psi) ? dc0 + Rr : dc0 - psi * tt + rho * sq;
-                            const double dn = (-tt * Rr <= -psi) ? -dc0 + Rr : -dc0 + psi * tt + rho * sq;
-                            kill = (inv - up > P.eps_test) && (inv - dn > P.eps_test);
+            for (int p0 = w_lo; p0 < w_hi; p0 += kCB) {
+                // kCB atoms per step, every load of the step issued before it is used
+                int iv[kCB];
+                unsigned long long mv[kCB];
+#pragma unroll
+                for (int q = 0; q < kCB; q++) iv[q] = p0 + q < w_hi ? __ldcg(W.act[cur] + p0 + q) : -1;
+#pragma unroll
+                for (int q = 0; q < kCB; q++) mv[q] = iv[q] >= 0 ? __ldcg(W.amask + iv[q]) : 0ull;
+                bool on[kCB][2];
+                double tq[kCB][2];
+                FF xv[kCB][2], xw[kCB][2];
+#pragma unroll
+                for (int q = 0; q < kCB; q++)
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int r = lane + 32 * h;
+                        on[q][h] = iv[q] >= 0 && lv[h] && ((mv[q] >> r) & 1);
+                        tq[q][h] = 0.0;
+                        xv[q][h] = FF{0.f, 0.f};
+                        xw[q][h] = FF{0.f, 0.f};
+                        if (on[q][h]) {
+                            const size_t idx = (size_t)iv[q] * kMR + r;
+                            if (dyn) tq[q][h] = __ldcg(W.Q0 + idx);
+                            xv[q][h] = ldcg_x(xnew + idx);
+                            if (!ista) xw[q][h] = ldcg_x(xold + idx);
                         }
                     }
-                    if (kill) {
-                        on[h] = false;
-                        xnew[idx] = FF{0.f, 0.f};
-                        W.u[idx] = FF{0.f, 0.f};
-                        continue;
+#pragma unroll
+                for (int q = 0; q < kCB; q++) {
+                    bool nz[2];
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        nz[h] = false;
+                        if (!on[q][h]) continue;
+                        const int r = lane + 32 * h;
+                        const size_t idx = (size_t)iv[q] * kMR + r;
+                        bool kill = false;
+                        if (dyn) {
+                            if (!dome) {
+                                kill = tq[q][h] - radh[h] > P.eps_test;
+                            } else {
+                                // Lemma 4 in its dynamic form: max over the dome of |d_i^T theta| < 1
+                                const double dc0 = tq[q][h] * ilh[h];
+                                const double tt = __ldcg(W.Q1 + idx), sq = __ldcg(W.Q2 + idx);
+                                const double inv = __ldcg(W.invn + iv[q]);
+                                const double Rr = Rsh[h], psi = psih[h], rho = rhoh[h];
+                                const double up = (tt * Rr <= -psi) ? dc0 + Rr : dc0 - psi * tt + rho * sq;
+                                const double dn = (-tt * Rr <= -psi) ? -dc0 + Rr : -dc0 + psi * tt + rho * sq;
+                                kill = (inv - up > P.eps_test) && (inv - dn > P.eps_test);
+                            }
+                        }
+                        if (kill) {
+                            on[q][h] = false;
+                            xnew[idx] = FF{0.f, 0.f};
+                            W.u[idx] = FF{0.f, 0.f};
+                            continue;
+                        }
+                        const FF x = xv[q][h];
+                        const FF uu = ista ? x : it_momentum(x, xw[q][h], btX);
+                        W.u[idx] = uu;
+                        nz[h] = it_nz(x) || it_nz(uu);
+                        nx[h] += it_nz(x);
+                        acc_abs(l1[h], x);
+                        na[h] += 1;
+                        cnt[h] += nz[h];
                     }
-                    const FF x = ldcg_x(xnew + idx);
-                    const FF uu = ista ? x : it_momentum(x, ldcg_x(xold + idx), btX);
-                    W.u[idx] = uu;
-                    nz[h] = it_nz(x) || it_nz(uu);
-                    nx[h] += it_nz(x);
-                    acc_abs(l1[h], x);
-                    na[h] += 1;
-                    cnt[h] += nz[h];
+                    const unsigned lo = __ballot_sync(0xffffffffu, on[q][0]), hi = __ballot_sync(0xffffffffu, on[q][1]);
+                    const unsigned zlo = __ballot_sync(0xffffffffu, nz[0]), zhi = __ballot_sync(0xffffffffu, nz[1]);
+                    const unsigned long long onm = ((unsigned long long)hi << 32) | lo;
+                    if (lane == 0 && iv[q] >= 0) {
+                        W.amask[iv[q]] = (mv[q] & ~live) | onm;
+                        W.nzmask[iv[q]] = ((unsigned long long)zhi << 32) | zlo;
+                        W.keep[p0 + q] = onm != 0ull;
+                    }
+                    kept += (iv[q] >= 0 && onm != 0ull);
                 }
-                const unsigned lo = __ballot_sync(0xffffffffu, on[0]), hi = __ballot_sync(0xffffffffu, on[1]);
-                const unsigned zlo = __ballot_sync(0xffffffffu, nz[0]), zhi = __ballot_sync(0xffffffffu, nz[1]);
-                const unsigned long long onm = ((unsigned long long)hi << 32) | lo;
-                if (lane == 0) {
-                    W.amask[i] = (m & ~live) | onm;
-                    W.nzmask[i] = ((unsigned long long)zhi << 32) | zlo;
-                    W.keep[p] = onm != 0ull;
-                }
-                kept += onm != 0ull;
             }
             for (int h = 0; h < 2; h++) {
                 const int r = lane + 32 * h;
                 S.cnt[warp][r] = cnt[h];
-                S.red_s[warp][r] = l1[h].s;
-                S.red_c[warp][r] = l1[h].c;
-                S.red_na[warp][r] = na[h];
-                S.red_nx[warp][r] = nx[h];
+                RS.s[0][warp][r] = l1[h].s;
+                RS.s[1][warp][r] = l1[h].c;
+                RS.n[0][warp][r] = na[h];
+                RS.n[1][warp][r] = nx[h];
             }
             if (lane == 0) S.ired[warp] = kept;
             __syncthreads();
@@ -1003,14 +1411,14 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     const int c = S.cnt[w][r];
                     S.cnt[w][r] = run;
                     run += c;
-                    dot2_merge(l, S.red_s[w][r], S.red_c[w][r]);
-                    a += S.red_na[w][r];
-                    x += S.red_nx[w][r];
+                    dot2_merge(l, RS.s[0][w][r], RS.s[1][w][r]);
+                    a += RS.n[0][w][r];
+                    x += RS.n[1][w][r];
                 }
-                W.c_nz[r * G + b] = run;
-                W.p_l1[r * G + b] = FF{l.s, l.c};
-                W.c_na[r * G + b] = a;
-                W.c_nnzx[r * G + b] = x;
+                W.c_nz[b * kMR + r] = run;
+                W.p_l1[b * kMR + r] = FF{l.s, l.c};
+                W.c_na[b * kMR + r] = a;
+                W.c_nnzx[b * kMR + r] = x;
             }
             if (tid == 0) {
                 int k = 0;
@@ -1021,19 +1429,26 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
             __syncthreads();
             // the nonzero lists of the next syntheses, per problem, in list order
             int e[2] = {S.cnt[warp][lane], S.cnt[warp][lane + 32]};
-            for (int p = w_lo; p < w_hi; p++) {
-                const int i = __ldcg(W.act[cur] + p);
-                const unsigned long long z = __ldcg(W.nzmask + i);
-                for (int h = 0; h < 2; h++) {
-                    const int r = lane + 32 * h;
-                    if ((z >> r) & 1) {
-                        const size_t idx = (size_t)i * kMR + r;
-                        const size_t o = (size_t)r * K + p_lo + e[h]++;
-                        W.nz_col[o] = i;
-                        W.nz_u[o] = ldcg_x(W.u + idx);
-                        W.nz_x[o] = ldcg_x(xnew + idx);
+            for (int p0 = w_lo; p0 < w_hi; p0 += kCB) {
+                int iv[kCB];
+                unsigned long long zv[kCB];
+#pragma unroll
+                for (int q = 0; q < kCB; q++) iv[q] = p0 + q < w_hi ? __ldcg(W.act[cur] + p0 + q) : -1;
+#pragma unroll
+                for (int q = 0; q < kCB; q++) zv[q] = iv[q] >= 0 ? __ldcg(W.nzmask + iv[q]) : 0ull;
+#pragma unroll
+                for (int q = 0; q < kCB; q++)
+#pragma unroll
+                    for (int h = 0; h < 2; h++) {
+                        const int r = lane + 32 * h;
+                        if ((zv[q] >> r) & 1) {
+                            const size_t idx = (size_t)iv[q] * kMR + r;
+                            const size_t o = (size_t)r * K + p_lo + e[h]++;
+                            W.nz_col[o] = iv[q];
+                            W.nz_u[o] = ldcg_x(W.u + idx);
+                            W.nz_x[o] = ldcg_x(xnew + idx);
+                        }
                     }
-                }
             }
             xi ^= 1;
         }
@@ -1053,15 +1468,49 @@ struct MrhsTeamArgs {
     int* next_job;
     int* error;
     int team_size;
+    int use_tc;  // some block runs its bulk phase on the tensor cores
 };
+
+// Leaves the kernel with nothing of the CTA's in flight: outstanding copies
+// waited for, the last committed MMAs waited for (bounded), tensor memory freed.
+__device__ __forceinline__ void mrhs_exit(TcState& tc, bool tc_on)
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (tc_on) {
+        if (tc.issued > 0) {
+            const unsigned g = tc.issued - 1;
+            mbar_wait(tc.mbar + (g % kTcStages), (g / kTcStages) & 1u);
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tmem_dealloc(tc.tmem, kTcCols);
+    }
+}
 
 __global__ void __launch_bounds__(kThreads, 1) mrhs_team_kernel(const MrhsTeamArgs A)
 {
     __shared__ MrhsP sP;
     __shared__ int s_job;
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[kTcStages];
     const int team = blockIdx.x / A.team_size, rank = blockIdx.x % A.team_size;
     GridBarrier* bar = A.bars + team;
     unsigned int gen = 0;
+    // tensor-core state for the whole launch (one CTA per SM: the allocation cannot wait)
+    TcState tc;
+    tc.q = 0;
+    tc.issued = 0;
+    tc.mbar = s_mbar;
+    tc.tmem = 0;
+    if (A.use_tc) {
+        if (threadIdx.x < kTcStages) mbar_init(&s_mbar[threadIdx.x], 1);
+        if (threadIdx.x < 32) tmem_alloc(&s_tmem, kTcCols);
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        tc.tmem = s_tmem;
+    }
     for (;;) {
         if (threadIdx.x == 0 && rank == 0) {
             int j = atomicAdd(A.next_job, 1);
@@ -1069,26 +1518,32 @@ __global__ void __launch_bounds__(kThreads, 1) mrhs_team_kernel(const MrhsTeamAr
         }
         if (!grid_sync(bar, A.team_size, gen)) {
             if (threadIdx.x == 0) atomicExch(A.error, 1);
+            mrhs_exit(tc, A.use_tc);
             return;
         }
         if (threadIdx.x == 0) s_job = __ldcg(A.team_job + team);
         __syncthreads();
         const int j = s_job;
-        if (j < 0) return;
+        if (j < 0) {
+            mrhs_exit(tc, A.use_tc);
+            return;
+        }
         if (threadIdx.x == 0) {
             sP = A.jobs[j];
             sP.ws = A.team_ws[team];
         }
         __syncthreads();
-        if (!mrhs_body(sP, rank, A.team_size, bar, gen)) {
+        if (!mrhs_body(sP, rank, A.team_size, bar, gen, tc)) {
             if (threadIdx.x == 0) atomicExch(A.error, 1);
             if (threadIdx.x == 0 && rank == 0)
                 for (int r = 0; r < sP.R; r++) sP.res[r].status = kDevTimeout;
+            mrhs_exit(tc, A.use_tc);
             return;
         }
         // the next job reuses the team's workspace: every CTA leaves this one first
         if (!grid_sync(bar, A.team_size, gen)) {
             if (threadIdx.x == 0) atomicExch(A.error, 1);
+            mrhs_exit(tc, A.use_tc);
             return;
         }
     }
@@ -1111,6 +1566,8 @@ size_t mrhs_layout(char* base, int N, int K, int G, bool dome, MrhsWs* w)
     w->Yt = bp.take<float>((size_t)kMR * npad);
     w->Th = bp.take<float>((size_t)kMR * npad);
     w->Dst = bp.take<float>((size_t)kMR * npad);
+    w->Thi = bp.take<uint16_t>((size_t)kMR * npad);
+    w->Tlo = bp.take<uint16_t>((size_t)kMR * npad);
     w->Q0 = bp.take<double>((size_t)K * kMR);
     w->Q1 = bp.take<double>((size_t)K * kMR);
     w->Q2 = dome ? bp.take<double>((size_t)K * kMR) : nullptr;
@@ -1128,6 +1585,7 @@ size_t mrhs_layout(char* base, int N, int K, int G, bool dome, MrhsWs* w)
     w->nz_x = bp.take<FF>((size_t)kMR * K);
     w->part = bp.take<float>((size_t)kMMaxSplit * G * kMTA * kMR * 2);
     w->tilecnt = bp.take<int>((K + kMTA - 1) / kMTA);
+    w->ctr = bp.take<int>(3);
     w->p_m = bp.take<float>((size_t)kMR * G);
     w->p_l1 = bp.take<FF>((size_t)kMR * G);
     w->c_na = bp.take<int>((size_t)kMR * G);
@@ -1230,6 +1688,7 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
     for (int t = 0; t < n_teams; t++) mrhs_layout(wsbase + ws_team * t, maxN, maxK, team, dome, &tws[t]);
     if (cudaMemcpy(dtws, tws.data(), sizeof(MrhsWs) * n_teams, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(DS_ERR_CUDA);
+    int use_tc = 0;
     for (int jj = 0; jj < n_blocks; jj++) {
         const int j = ord[jj];
         const MrhsBlock& B = blocks[j];
@@ -1265,6 +1724,22 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
         P.res = M->dres + (size_t)jj * kMR;
         P.fista = fista_dev;
         P.fista_n = fista_n;
+        if (dc->lo_kind == 1) {
+            // precision variant with a BF16 copy: bulk iterations on the tensor cores
+            P.Dlo = reinterpret_cast<const uint16_t*>(dc->Dlo);
+            P.ld_lo = (int)dc->ld_lo;
+            P.use_tc = 1;
+            P.emax = dc->emax;
+            {
+                // tensor-core sums, bounded as if every addition of a K = 16 step (16 products and
+                // the accumulator) truncated to FP32 (unit 2^-23), plus the row-split sums
+                const double u = std::ldexp(1.0, -23);
+                const double k = 17.0 * (P.npad / 16) + 16.0;
+                P.gamma_tc = 1.01 * k * u / (1.0 - k * u);
+            }
+            P.lo_switch = opt->lowp_switch > 0.0 ? opt->lowp_switch : (opt->tol_gap_rel > 0.0 ? opt->tol_gap_rel : 1e-6);
+            use_tc = 1;
+        }
         M->hjobs[jj] = P;
     }
     // keep the job order for lambdas/results
@@ -1280,8 +1755,9 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
     M->args.next_job = next_job;
     M->args.error = M->derr;
     M->args.team_size = team;
+    M->args.use_tc = use_tc;
     M->grid = n_teams * team;
-    M->smem = sizeof(MrhsShared);
+    M->smem = sizeof(MrhsShared) + 1024;  // + alignment of the staging area
     if (cudaFuncSetAttribute(mrhs_team_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)M->smem) !=
         cudaSuccess)
         return fail(DS_ERR_CUDA);

@@ -546,7 +546,7 @@ ds_status ds_batch_run(ds_batch* B, ds_result* res)
                 o.ms = B->ms_last;
                 o.cols_corr = q.cols_corr;
                 o.cols_synth = q.cols_synth;
-                o.cols_lowp = 0;
+                o.cols_lowp = q.cols_lowp;
             }
     }
     for (int j = 0; j < B->n_jobs; j++) {

@@ -180,3 +180,53 @@ def test_multi_rhs_can_be_turned_off(ctx):
     finally:
         for d in dicts:
             ds.ds_dict_destroy(d)
+
+
+def _run_batch_dicts(ctx, dicts, insts, opt):
+    Ys = [torch.from_numpy(Y).to("cuda", torch.float32) for (D, Y, lam) in insts]
+    Xs = [torch.full((Y.shape[0], D.shape[1]), float("nan"), device="cuda") for (D, Y, lam) in insts]
+    plan = ds.ds_batch_create(ctx, dicts, Ys, [lam.copy() for (_, _, lam) in insts], opt, Xs)
+    res = ds.ds_batch_run(plan)
+    torch.cuda.synchronize()
+    ds.ds_batch_destroy(plan)
+    return Xs, res
+
+
+@pytest.mark.parametrize("test", ["dst3", "dome"])
+def test_multi_rhs_tensor_core_bulk_matches_fp32(ctx, test):
+    # BF16 copy: the bulk iterations contract on the tensor cores (theta split in BF16 hi + lo),
+    # then the block finishes on the FP32 master; at a fixed iteration count the solutions
+    # equal the FP32 block's within the parity tolerance
+    insts = [_instance(306, 300, 1500, 70)]
+    D = insts[0][0]
+    Dt = _dev_dict(D)
+    d32 = ds.ds_dict_create(ctx, Dt)
+    dbf = ds.ds_dict_create(ctx, Dt, work_prec=ds.DS_BF16)
+    try:
+        opt = ds.ds_options_default(test=test, tol_gap_rel=0.0, max_iter=3000, lambda_rel=1)
+        xa, ra = _run_batch_dicts(ctx, [d32], insts, opt)
+        xb, rb = _run_batch_dicts(ctx, [dbf], insts, opt)
+        a = xa[0].double().cpu().numpy()
+        b = xb[0].double().cpu().numpy()
+        assert np.isfinite(b).all()
+        for r in range(a.shape[0]):
+            assert rb[r]["iters"] == ra[r]["iters"] == 3000
+            assert 0 < rb[r]["cols_lowp"] < rb[r]["cols_corr"], rb[r]
+            assert np.abs(a[r] - b[r]).max() <= 1e-5 * max(np.abs(a[r]).max(), 1e-30), (r, np.abs(a[r] - b[r]).max())
+        # with the gap rule the tensor-core block certifies the tolerance, at the oracle's optimum
+        tol = 1e-6
+        opt = ds.ds_options_default(test=test, tol_gap_rel=tol, max_iter=50000, lambda_rel=1)
+        xc, rc = _run_batch_dicts(ctx, [dbf], insts, opt)
+        D32 = D.astype(np.float32).astype(np.float64)
+        Y = insts[0][1]
+        for r in range(0, Y.shape[0], 7):
+            y = Y[r].astype(np.float32).astype(np.float64)
+            yy = float(y @ y)
+            assert rc[r]["status"] == 0 and rc[r]["gap"] <= tol * 0.5 * yy, rc[r]
+            o = oracle.solve(D32, y, rc[r]["lambda"], test="none", tol=1e-13, max_iter=200000)
+            x = xc[0][r].double().cpu().numpy()
+            p = _primal(D32, y, x, rc[r]["lambda"])
+            assert p - o["primal"] <= 1.05 * tol * 0.5 * yy + 1e-9 * yy, (r, p - o["primal"])
+    finally:
+        ds.ds_dict_destroy(d32)
+        ds.ds_dict_destroy(dbf)
