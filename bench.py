@@ -322,6 +322,7 @@ def main():
 
     if world == 1 and not args.no_modes:
         out["batched"] = batched_measure(ds, ctx, D32, dev, flush)
+        out["batched_uneven"] = batched_uneven_measure(ds, ctx, dev, flush)
         out["served"] = served_measure(ds, ctx, dev)
     ds.ds_destroy(ctx)
     if rank == 0 and not args.no_cpu and world == 1:
@@ -350,56 +351,136 @@ def profile_one():
                        "gap_rel": r["gap"] / (0.5 * yy)} for r in res]))
 
 
+def _rhs_block(D, R, g, lo=0.1, hi=0.9):
+    """R right-hand sides y = D x0 + e at 20 dB (x0 Bernoulli(0.01)-Gaussian), lambda/lambda_max ~ U[lo, hi]."""
+    N, K = D.shape
+    X0 = np.zeros((K, R))
+    mask = g.uniform(size=(K, R)) < 0.01
+    X0[mask] = g.standard_normal(int(mask.sum()))
+    S = D.astype(np.float64) @ X0
+    E = g.standard_normal((N, R))
+    Y = (S + E * (np.linalg.norm(S, axis=0) / np.maximum(np.linalg.norm(E, axis=0), 1e-300)) * 0.1).T
+    return Y.astype(np.float32), g.uniform(lo, hi, size=R)
+
+
+def _time_batch(ds, plan, flush, reps=2):
+    import torch
+    ds.ds_batch_run(plan)  # warm
+    best, res = None, None
+    for k in range(reps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        res = ds.ds_batch_run(plan)
+        ev1.record()
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        best = t if best is None else min(best, t)
+    return best, res
+
+
 def batched_measure(ds, ctx, D32, dev, flush):
-    """64 right-hand sides on the 2000 x 10000 dictionary (Bernoulli(0.01)-Gaussian x0,
-    20 dB, lambda/lambda_max ~ U[0.1, 0.9]), FISTA + DST3 to gap 1e-6: one batch
-    (persistent multi-team launch replayed from its CUDA graph) against the plain
-    form (the same 64 problems solved one at a time)."""
+    """Batching: 64 right-hand sides on the 2000 x 10000 dictionary (Bernoulli(0.01)-Gaussian
+    x0, 20 dB, lambda/lambda_max ~ U[0.1, 0.9]), FISTA + DST3 to gap 1e-6.  The batch solves
+    the 64 problems as one multi-RHS block (one graph-replayed persistent launch): from the
+    FP32 master alone, and with the BF16 working copy whose bulk iterations contract on the
+    tensor cores.  The plain form solves the same 64 problems one at a time."""
     import torch
     R = 64
     g = np.random.default_rng(2002)
     N, K = D32.shape
-    X0 = np.zeros((K, R))
-    mask = g.uniform(size=(K, R)) < 0.01
-    X0[mask] = g.standard_normal(int(mask.sum()))
-    S = D32.astype(np.float64) @ X0
-    E = g.standard_normal((N, R))
-    Y = (S + E * (np.linalg.norm(S, axis=0) / np.linalg.norm(E, axis=0)) * 0.1).T.astype(np.float32)  # (R, N)
-    ratios = g.uniform(0.1, 0.9, size=R)
+    Y, ratios = _rhs_block(D32, R, g)
     Dt = torch.from_numpy(np.ascontiguousarray(D32.T)).to(dev).t()
-    dct = ds.ds_dict_create(ctx, Dt)
+    d32 = ds.ds_dict_create(ctx, Dt)
+    dbf = ds.ds_dict_create(ctx, Dt, work_prec=ds.DS_BF16)
     Yt = torch.from_numpy(Y).to(dev)
     Xb = torch.zeros((R, K), device=dev)
     opt = ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
-    plan = ds.ds_batch_create(ctx, [dct], [Yt], [ratios], opt, [Xb])
-    info = ds.ds_batch_info(plan)
-    ds.ds_batch_run(plan)  # warm
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    flush.fill_(1.0)
-    torch.cuda.synchronize()
-    ev0.record()
-    res = ds.ds_batch_run(plan)
-    ev1.record()
-    torch.cuda.synchronize()
-    t_batch = ev0.elapsed_time(ev1) / 1e3
-    ok_b = all(r["status"] == 0 for r in res)
-    # plain form: one solve at a time
+    out = {}
+    for name, dct in (("bf16_tensor", dbf), ("fp32", d32)):
+        plan = ds.ds_batch_create(ctx, [dct], [Yt], [ratios], opt, [Xb])
+        t, res = _time_batch(ds, plan, flush)
+        out[name] = {"solves_per_s": R / t, "ms": t * 1e3, "layout": ds.ds_batch_layout(plan),
+                     "converged": all(r["status"] == 0 for r in res),
+                     "iters_median": float(np.median([r["iters"] for r in res])),
+                     "iters_max": int(max(r["iters"] for r in res)),
+                     "lowp_column_fraction": float(np.mean([r["cols_lowp"] / max(r["cols_corr"], 1) for r in res]))}
+        ds.ds_batch_destroy(plan)
+    # plain form: one solve at a time, FP32 master
     x1 = torch.zeros(K, device=dev)
     flush.fill_(2.0)
     torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record()
     for r in range(R):
-        ds.ds_solve(ctx, dct, Yt[r], float(ratios[r]), opt, x1)
+        ds.ds_solve(ctx, d32, Yt[r], float(ratios[r]), opt, x1)
     ev1.record()
     torch.cuda.synchronize()
     t_plain = ev0.elapsed_time(ev1) / 1e3
+    ds.ds_dict_destroy(d32)
+    ds.ds_dict_destroy(dbf)
+    best = out["bf16_tensor"]["solves_per_s"]
+    return {"value": best, "unit": "solves/s", "plain_value": R / t_plain, "vs_plain": best * t_plain / R,
+            "modes": out,
+            "workload": "64 rhs x 2000x10000 FP32 Gaussian dictionary (+ BF16 copy), lambda/lambda_max ~ "
+                        "U[0.1,0.9], FISTA+DST3, gap 1e-6; one multi-RHS block in a graph-replayed persistent "
+                        "launch vs 64 sequential ds_solve on the FP32 master"}
+
+
+def batched_uneven_measure(ds, ctx, dev, flush, n_inst=8, plain_per_inst=4):
+    """The uneven batch workload, sampled: n_inst instances with N ~ U{256..4096}, K ~ U{1024..32768}
+    (Gaussian unit-norm columns), 64 right-hand sides each, FP32 master + BF16 copy, one batch plan
+    (persistent launch in a CUDA graph).  The plain form is timed on plain_per_inst problems per
+    instance, solved one at a time, and reported as solves/s."""
+    import torch
+    g = np.random.default_rng(1004)
+    dicts, Ys, Xs, lams, sizes = [], [], [], [], []
+    for i in range(n_inst):
+        N = int(g.integers(256, 4097))
+        K = int(g.integers(1024, 32769))
+        # generated on the device (seeded): D column-major with unit-norm columns, x0, 20 dB noise
+        tg = torch.Generator(device=dev).manual_seed(10040 + i)
+        Dt = torch.randn((K, N), device=dev, generator=tg)
+        Dt /= Dt.norm(dim=1, keepdim=True)
+        Dt = Dt.t()  # (N, K) column-major view
+        X0 = torch.randn((64, K), device=dev, generator=tg) * (torch.rand((64, K), device=dev, generator=tg) < 0.01)
+        S = X0 @ Dt.t()  # (64, N)
+        E = torch.randn((64, N), device=dev, generator=tg)
+        Y = S + E * (S.norm(dim=1, keepdim=True) / E.norm(dim=1, keepdim=True)) * 0.1
+        dicts.append(ds.ds_dict_create(ctx, Dt, work_prec=ds.DS_BF16))
+        Ys.append(Y.contiguous())
+        Xs.append(torch.zeros((64, K), device=dev))
+        lams.append(g.uniform(0.1, 0.9, size=64))
+        sizes.append((N, K))
+        del Dt, X0, S, E
+    opt = ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
+    plan = ds.ds_batch_create(ctx, dicts, Ys, lams, opt, Xs)
+    layout = ds.ds_batch_layout(plan)
+    t, res = _time_batch(ds, plan, flush, reps=1)
     ds.ds_batch_destroy(plan)
-    ds.ds_dict_destroy(dct)
-    return {"value": R / t_batch, "unit": "solves/s", "plain_value": R / t_plain, "vs_plain": t_plain / t_batch,
-            "converged": ok_b, "plan": info,
-            "iters_median": float(np.median([r["iters"] for r in res])),
-            "workload": "64 rhs x 2000x10000 FP32 Gaussian dictionary, lambda/lambda_max ~ U[0.1,0.9], "
-                        "FISTA+DST3, gap 1e-6; one graph-replayed persistent launch vs 64 sequential ds_solve"}
+    n = 64 * n_inst
+    # plain: a few problems per instance, one at a time
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush.fill_(3.0)
+    torch.cuda.synchronize()
+    ev0.record()
+    cnt = 0
+    for i in range(n_inst):
+        x1 = torch.zeros(sizes[i][1], device=dev)
+        for r in range(plain_per_inst):
+            ds.ds_solve(ctx, dicts[i], Ys[i][r], float(lams[i][r]), opt, x1)
+            cnt += 1
+    ev1.record()
+    torch.cuda.synchronize()
+    t_plain = ev0.elapsed_time(ev1) / 1e3
+    for d in dicts:
+        ds.ds_dict_destroy(d)
+    return {"value": n / t, "unit": "solves/s", "ms": t * 1e3, "plain_value": cnt / t_plain,
+            "vs_plain": (n / t) / (cnt / t_plain), "converged": all(r["status"] == 0 for r in res),
+            "layout": layout, "instances": [list(sz) for sz in sizes],
+            "sample": f"{n_inst} of the 256 instances (64 rhs each, {n} solves); plain timed on "
+                      f"{plain_per_inst} problems per instance ({cnt} solves)"}
 
 
 def served_measure(ds, ctx, dev, seconds=3.0, rate=100.0, drain_s=20.0):

@@ -71,9 +71,10 @@ typedef struct {
     double tol_gap_rel; /* stop when gap <= tol * 1/2 ||y||^2; 0 runs exactly max_iter iterations */
     double L;           /* step constant; <= 0 uses the dictionary's ||D||_2^2 upper estimate */
     int lambda_rel;     /* 1: lambda values are fractions of lambda_max (computed in the call) */
-    double lowp_switch; /* dictionaries with a BF16/FP8 copy: relative gap at which the solve leaves the
-                           copy for the FP32 master (also left after 25 iterations without 1% progress);
-                           <= 0: the gap tolerance (1e-6 when it is 0) */
+    double lowp_switch; /* dictionaries with a BF16/FP8 copy: relative nominal gap at which a solve leaves
+                           the copy for the FP32 master, restarting FISTA from the bulk iterate (also left
+                           after 25 iterations without 1% progress); <= 0: 1e-3, or the gap tolerance if
+                           that is coarser */
     int batch_multi_rhs; /* batches: 1 (default) solves the right-hand sides of an FP32 Lasso instance
                             together, up to 64 per block, so each dictionary column read serves them all;
                             0 runs every (instance, rhs) problem on its own */

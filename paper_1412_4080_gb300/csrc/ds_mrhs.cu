@@ -42,9 +42,8 @@ constexpr int kMR = kMrhsMaxR;     // problems per block
 constexpr int kMTA = 128;          // atoms per correlation tile
 constexpr int kMKC = 32;           // rows per staged chunk
 constexpr int kMST = kMKC + 4;     // shared row stride (floats): conflict-free 16-byte reads
-constexpr int kMSynRows = 64;      // rows per synthesis item (two per lane)
+constexpr int kMSynRows = 128;     // rows per synthesis item (four per lane)
 constexpr int kMW = kThreads / 32; // warps per CTA
-constexpr int kMMaxSplit = 8;      // row splits of a correlation tile
 constexpr int kMStages = 3;        // cp.async pipeline depth of the FP32 contraction
 constexpr int kCB = 4;             // atoms per step of the screening pass (loads in flight)
 // tensor-core contraction on the BF16 copy: stages of a 128 x 64 A tile (16 KB)
@@ -73,12 +72,13 @@ struct MrhsWs {
     FF* xb[2];   // [K][kMR] iterates x (two generations)
     FF* u;       // [K][kMR] extrapolated points
     unsigned long long* amask;   // [K] problems for which atom i is still active
-    unsigned long long* nzmask;  // [K] problems for which (u_i, x_i) != 0
-    int* act[2];  // union active list (two generations)
-    int* keep;    // [K] per list position: atom stays
+    unsigned long long* nzmask;  // [K] problems with an entry of atom i in the next synthesis
+    unsigned long long* kzmask;  // [K] of those, entries of x_{t-1} of an atom screened at t
+    int* act[3][2];  // lists (union, bulk group, FP32 group), two generations each
+    int* keep;       // [K] per union-list position: bit 0 stays, bit 1 in the bulk list, bit 2 in the FP32 list
     int* nz_col;  // [kMR][K] nonzero lists, per CTA segment
-    FF* nz_u;
     FF* nz_x;
+    FF* wb[2];    // [kMR][npad] D x_t of the last two iterations (float-float)
     float* part;  // row-split partial tiles
     int* tilecnt; // per tile: row splits finished
     int* ctr;     // 3 work counters (dynamic claiming), used in turn
@@ -88,7 +88,7 @@ struct MrhsWs {
     int* c_na;    // [G]
     int* c_nnzx;  // [G]
     int* c_nz;    // [G] nonzero-list lengths
-    int* c_keep;  // [G] (no problem index)
+    int* c_keep;  // [3][G] atoms kept per list (no problem index)
     int* s_alo;   // [G] start of each CTA's list segment (no problem index)
     double* p_v;  // [G] max |d_i^T y| per CTA
     int* p_i;     // [G] its lowest index
@@ -149,14 +149,15 @@ struct MrhsShared {
     int istar[kMR], iters[kMR], na[kMR], nnzx[kMR], stopnow[kMR];
     long long csyn[kMR];
     unsigned long long live;
-    int n_slots, nA, last, claim, keep_base, keep_tot;
+    int n_slots, last, claim;
+    int nA[3], kbase[3], ktot[3];  // lists: union, bulk group, FP32 group
     unsigned long long dm;
-    // precision phase of the block (bulk on the BF16 copy, then FP32)
-    int low, lowB, t0, swok[kMR], since[kMR];
-    double best_gap[kMR], R2s[kMR];
-    long long clowp;
-    long long ccorr;
-    double bt, lf;
+    // precision phase per problem: bulk on the BF16 copy (tensor cores), then FP32
+    unsigned long long gprev, gcur, gnext;  // bulk group of iterations t-1, t, t+1
+    int since[kMR], swnow[kMR], t0r[kMR];
+    double best_gap[kMR], R2s[kMR], lfr[kMR], btr[kMR];
+    long long ccr[kMR], clr[kMR];
+    int ired1[kMW], ired2[kMW];
     int ired[kMW];
     int scan_tmp[32];
 };
@@ -445,23 +446,6 @@ __device__ __forceinline__ void mr_gemm_any(int JJ, MrhsShared& S, const float* 
     }
 }
 
-// Row splits of the tiles: fill the team's CTAs in whole waves where possible.
-__device__ __forceinline__ int mr_splits(int TA, int G, int nc)
-{
-    if (TA >= G) return 1;
-    int best = 1;
-    double best_eff = 0.0;
-    const int smax = min(kMMaxSplit, max(1, nc / 2));
-    for (int s = 1; s <= smax; s++) {
-        const double w = (double)TA * s / G;
-        const double eff = w / ceil(w);
-        if (eff > best_eff + 1e-9) {
-            best_eff = eff;
-            best = s;
-        }
-    }
-    return best;
-}
 
 // Work counter of the team's next claim loop: the loops take the three
 // counters in turn, and each resets the one the next loop will use (its last
@@ -474,12 +458,16 @@ __device__ __forceinline__ int* mr_counter(const MrhsWs& W, int& cu, int b)
     return c;
 }
 
-// The tiles of `nA` list atoms (ids from `list`, or the identity when null),
-// split over rows and claimed by the team's CTAs from `ctr`; calls epi(acc, cmp)
-// in the CTA that finishes a tile, with S.cols holding the tile's atoms.
+// Z = D_A^T Theta over the tiles of `nA` list atoms (ids from `list`, or the
+// identity when null), stream-K: the (tile, row chunk) units are cut into G
+// equal contiguous runs, one per CTA, so a CTA streams about U/G chunks with
+// at most one partial tile at each end.  A partial tile is parked in the CTA's
+// slot (2b: first tile of its run, 2b + 1: last); the CTA that completes the
+// tile's chunk count adds the parked partials in CTA order (a fixed order) and
+// calls epi(acc, cmp) with S.cols holding the tile's atoms.
 template <int KIND, typename Epi>
 __device__ __forceinline__ bool mr_tiles(MrhsShared& S, const MrhsP& P, const int* list, int nA, const float* Th,
-                                         int JJ, int G, int* ctr, TcState& tc, Epi epi)
+                                         int JJ, int b, int G, TcState& tc, int grp, Epi epi)
 {
     constexpr bool COMP = KIND == 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -487,16 +475,21 @@ __device__ __forceinline__ bool mr_tiles(MrhsShared& S, const MrhsP& P, const in
     const MrhsWs& W = P.ws;
     const int TA = (nA + kMTA - 1) / kMTA;
     const int nc = P.npad / (KIND == 2 ? kTcRows : kMKC);
-    const int Sk = mr_splits(TA, G, nc);
-    const int items = TA * Sk;
+    const long long U = (long long)TA * nc;
     constexpr int TS = kMTA * kMR * (COMP ? 2 : 1);
-    for (;;) {
-        if (tid == 0) S.claim = atomicAdd(ctr, 1);
-        __syncthreads();
-        const int it = S.claim;
-        if (it >= items) return true;
-        const int ti = it / Sk, sk = it - ti * Sk;
-        const int c_lo = sk * nc / Sk, c_hi = (sk + 1) * nc / Sk;
+    auto ulo = [&](int bb) -> long long { return (long long)bb * U / G; };
+    const long long u0 = ulo(b), u1 = ulo(b + 1);
+    const int first_tile = (int)(u0 / nc);
+    // each contraction of a phase has its own parked tiles and counters: a CTA may start the
+    // next one while others still add up this one's partial tiles
+    float* part = W.part + (size_t)grp * 2 * G * kMTA * kMR * 2;
+    int* tilecnt = W.tilecnt + (size_t)grp * ((P.K + kMTA - 1) / kMTA);
+    long long u = u0;
+    while (u < u1) {
+        const int ti = (int)(u / nc);
+        const int c_a = (int)(u - (long long)ti * nc);
+        const int c_b = (int)min((long long)nc, u1 - (long long)ti * nc);
+        u = (long long)ti * nc + c_b;
         if (tid < kMTA) {
             const int p = ti * kMTA + tid;
             S.cols[tid] = p < nA ? (list ? __ldcg(list + p) : p) : -1;
@@ -504,13 +497,13 @@ __device__ __forceinline__ bool mr_tiles(MrhsShared& S, const MrhsP& P, const in
         __syncthreads();
         float acc[4][4], cmp[4][4];
         if (KIND == 2) {
-            if (!mr_gemm_tc(S, P, c_lo, c_hi, JJ, tc, acc)) return false;
+            if (!mr_gemm_tc(S, P, c_a, c_b, JJ, tc, acc)) return false;
         } else {
-            mr_gemm_any<COMP>(JJ, S, P.D, P.ld, Th, P.npad, c_lo, c_hi, acc, cmp);
+            mr_gemm_any<COMP>(JJ, S, P.D, P.ld, Th, P.npad, c_a, c_b, acc, cmp);
         }
         bool fin = true;
-        if (Sk > 1) {
-            float* pt = W.part + (size_t)it * TS;
+        if (c_b - c_a < nc) {
+            float* pt = part + (size_t)(2 * b + (ti == first_tile ? 0 : 1)) * TS;
 #pragma unroll
             for (int j = 0; j < 4; j++)
 #pragma unroll
@@ -522,11 +515,15 @@ __device__ __forceinline__ bool mr_tiles(MrhsShared& S, const MrhsP& P, const in
                     }
             __threadfence();
             __syncthreads();
-            if (tid == 0) S.last = (atomicAdd(W.tilecnt + ti, 1) == Sk - 1);
+            if (tid == 0) S.last = (atomicAdd(tilecnt + ti, c_b - c_a) + (c_b - c_a) == nc);
             __syncthreads();
             fin = S.last != 0;
             if (fin) {
                 __threadfence();
+                const long long t_lo = (long long)ti * nc, t_hi = t_lo + nc;
+                int b0 = (int)((t_lo * G) / U);  // the CTA whose run contains unit t_lo
+                while (b0 > 0 && ulo(b0) > t_lo) b0--;
+                while (b0 + 1 < G && ulo(b0 + 1) <= t_lo) b0++;
 #pragma unroll
                 for (int j = 0; j < 4; j++)
 #pragma unroll
@@ -534,20 +531,23 @@ __device__ __forceinline__ bool mr_tiles(MrhsShared& S, const MrhsP& P, const in
                         if (q < JJ) {
                             const int o = (ta + 32 * j) * kMR + tr + 16 * q;
                             float s = 0.f, c = 0.f;
-                            for (int s2 = 0; s2 < Sk; s2++) {
-                                const float* ps = W.part + (size_t)(ti * Sk + s2) * TS;
+                            for (int bb = b0; bb < G && ulo(bb) < t_hi; bb++) {
+                                if (ulo(bb + 1) <= max(ulo(bb), t_lo)) continue;  // no units of this tile
+                                const int sl = 2 * bb + (ti == (int)(ulo(bb) / nc) ? 0 : 1);
+                                const float* ps = part + (size_t)sl * TS;
                                 if (COMP) d2_merge(s, c, __ldcg(ps + o), __ldcg(ps + kMTA * kMR + o));
                                 else s += __ldcg(ps + o);
                             }
                             acc[j][q] = s;
                             cmp[j][q] = c;
                         }
-                if (tid == 0) W.tilecnt[ti] = 0;
+                if (tid == 0) tilecnt[ti] = 0;
             }
         }
         if (fin) epi(acc, cmp);
         __syncthreads();
     }
+    return true;
 }
 
 // ----------------------------------------------------- block-wide reductions
@@ -562,6 +562,158 @@ struct RedScratch {
     int n[3][kMW][kMR];    // up to three integer sums
 };
 static_assert(sizeof(RedScratch) <= kStageBytes, "reduction scratch exceeds the staging area");
+
+// ------------------------------------------------------------ synthesis item
+//
+// Rows [128 rb, 128 rb + 128) of problem r: w_t = D x_t over its nonzero list
+// (compensated), then theta_t = (1 + beta) w_t - beta (w_{t-1} - corrections) - y
+// (FISTA, Table 1) and the row block's partials of theta^T y, ||theta||^2 and
+// ||D x_t - y||^2.  The 16 warps split the list (8 entries in flight per warp,
+// 4 rows per lane); their partial sums merge in warp order in shared memory.
+__device__ __noinline__ void mr_synth_item(MrhsShared& S, const MrhsP& P, int r, int rb, int G, int t)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const MrhsWs& W = P.ws;
+    const int N = P.N, K = P.K, ld = P.ld, npad = P.npad;
+    int* dir = S.dir[0];
+    if (warp == 0) {
+        // where each CTA's segment of the list starts (exclusive prefix of the segment lengths)
+        int run = 0;
+        for (int b0 = 0; b0 < G; b0 += 32) {
+            const int bb = b0 + lane;
+            const int c = bb < G ? __ldcg(W.c_nz + bb * kMR + r) : 0;
+            int x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (bb < G) dir[bb] = run + x - c;
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) dir[G] = run;
+    }
+    __syncthreads();
+    const int E = dir[G];
+    const int e_lo = (int)((long long)warp * E / kMW), e_hi = (int)((long long)(warp + 1) * E / kMW);
+    const int nb = rb * kMSynRows + lane;
+    Dot2f ax[4], ac[4];
+    const size_t rk = (size_t)r * K;
+    for (int e0 = e_lo; e0 < e_hi; e0 += 32) {
+        const int e = e0 + lane;
+        int col = 0;
+        FF xx{0.f, 0.f};
+        if (e < e_hi) {
+            int lo = 0, hi = G;  // largest segment start <= e
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (dir[mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            const size_t idx = rk + S.alo[lo] + (e - dir[lo]);
+            col = __ldcg(W.nz_col + idx);
+            xx = ldcg_x(W.nz_x + idx);
+        }
+        const int ne = min(32, e_hi - e0);
+        for (int k0 = 0; k0 < ne; k0 += 8) {
+            float d[8][4];
+            FF xk[8];
+            int ck[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int k = min(k0 + q, 31);
+                const bool in = k0 + q < ne;
+                ck[q] = __shfl_sync(0xffffffffu, col, k);
+                xk[q].h = __shfl_sync(0xffffffffu, xx.h, k);
+                xk[q].l = __shfl_sync(0xffffffffu, xx.l, k);
+                const int ci = ck[q] >= 0 ? ck[q] : -ck[q] - 1;
+                const float* dc = P.D + (size_t)ci * ld;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int n = nb + 32 * j;
+                    d[q][j] = (in && n < N) ? __ldg(dc + n) : 0.f;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if (ck[q] >= 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) syn_add(ax[j], d[q][j], xk[q]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) syn_add(ac[j], d[q][j], xk[q]);
+                }
+            }
+        }
+    }
+    float* red = reinterpret_cast<float*>(S.stage);  // [kMW][4][kMSynRows]
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int nl = lane + 32 * j;
+        red[(warp * 4 + 0) * kMSynRows + nl] = ax[j].s;
+        red[(warp * 4 + 1) * kMSynRows + nl] = ax[j].c;
+        red[(warp * 4 + 2) * kMSynRows + nl] = ac[j].s;
+        red[(warp * 4 + 3) * kMSynRows + nl] = ac[j].c;
+    }
+    __syncthreads();
+    float* red2 = red + kMW * 4 * kMSynRows;  // [4 warps][6]
+    if (tid < kMSynRows) {
+        const int n = rb * kMSynRows + tid;
+        Dot2f axm, acm;
+        for (int w = 0; w < kMW; w++) {
+            dot2_merge(axm, red[(w * 4 + 0) * kMSynRows + tid], red[(w * 4 + 1) * kMSynRows + tid]);
+            dot2_merge(acm, red[(w * 4 + 2) * kMSynRows + tid], red[(w * 4 + 3) * kMSynRows + tid]);
+        }
+        Dot2f pa, pb, pr;
+        if (n < N) {
+            // FISTA (Table 1): D u_t = (1 + beta) D x_t - beta D x'_{t-1}, x'_{t-1} = x_{t-1} without the
+            // atoms screened at t; theta = D u_t - y carried in float-float
+            const double bt = S.btr[r];
+            const FF w = ff_fast_two_sum(axm.s, axm.c);
+            W.wb[t & 1][(size_t)r * npad + n] = w;
+            const float yv = __ldcg(W.Yt + (size_t)r * npad + n);
+            FF u = w;
+            if (bt != 0.0) {
+                const FF wp = ff_sub(ldcg_x(W.wb[(t - 1) & 1] + (size_t)r * npad + n), ff_fast_two_sum(acm.s, acm.c));
+                u = ff_sub(ff_mul(w, ff_from_double(1.0 + bt)), ff_mul(wp, ff_from_double(bt)));
+            }
+            const FF tf = ff_sub(u, FF{yv, 0.f});
+            const float th = tf.h + tf.l;
+            W.Th[(size_t)r * npad + n] = th;
+            if (P.use_tc) {
+                // theta = hi + lo + O(2^-18 |theta|) in BF16, for the tensor cores
+                const __nv_bfloat16 hb = __float2bfloat16_rn(th);
+                const __nv_bfloat16 lb = __float2bfloat16_rn(th - __bfloat162float(hb));
+                W.Thi[(size_t)r * npad + n] = __bfloat16_as_ushort(hb);
+                W.Tlo[(size_t)r * npad + n] = __bfloat16_as_ushort(lb);
+            }
+            pa.add(th, yv);
+            pb.add(th, th);
+            acc_resid_sq(pr, axm, yv);
+        }
+        pa = dot2_warp_reduce(pa);
+        pb = dot2_warp_reduce(pb);
+        pr = dot2_warp_reduce(pr);
+        if (lane == 0) {
+            red2[warp * 6 + 0] = pa.s; red2[warp * 6 + 1] = pa.c;
+            red2[warp * 6 + 2] = pb.s; red2[warp * 6 + 3] = pb.c;
+            red2[warp * 6 + 4] = pr.s; red2[warp * 6 + 5] = pr.c;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        Dot2f pa, pb, pr;
+        for (int w = 0; w < kMSynRows / 32; w++) {
+            dot2_merge(pa, red2[w * 6 + 0], red2[w * 6 + 1]);
+            dot2_merge(pb, red2[w * 6 + 2], red2[w * 6 + 3]);
+            dot2_merge(pr, red2[w * 6 + 4], red2[w * 6 + 5]);
+        }
+        W.p_a[rb * kMR + r] = FF{pa.s, pa.c};
+        W.p_b[rb * kMR + r] = FF{pb.s, pb.c};
+        W.p_r[rb * kMR + r] = FF{pr.s, pr.c};
+    }
+    __syncthreads();
+}
 
 // --------------------------------------------------------------- the body
 
@@ -593,6 +745,8 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         W.Yt[k] = (r < R && n < N) ? P.Y[(size_t)r * N + n] : 0.f;
         W.Th[k] = 0.f;
         W.Dst[k] = 0.f;
+        W.wb[0][k] = FF{0.f, 0.f};
+        W.wb[1][k] = FF{0.f, 0.f};
         if (P.use_tc) {
             W.Thi[k] = 0;
             W.Tlo[k] = 0;
@@ -602,7 +756,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         const int r = (int)(k / K);
         P.X[(size_t)r * K + (k - (size_t)r * K)] = 0.f;
     }
-    for (int k = b * kThreads + tid; k < (K + kMTA - 1) / kMTA; k += G * kThreads) W.tilecnt[k] = 0;
+    for (int k = b * kThreads + tid; k < 2 * ((K + kMTA - 1) / kMTA); k += G * kThreads) W.tilecnt[k] = 0;
     if (b == 0 && tid < 3) W.ctr[tid] = 0;
     for (int it = gwarp; it < ntile * kMR; it += twarps) {
         const int rt = it / kMR, r = it - rt * kMR;
@@ -646,7 +800,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         int arg[4];
 #pragma unroll
         for (int q = 0; q < 4; q++) { best[q] = -1.0; arg[q] = 0x7fffffff; }
-        if (!mr_tiles<1>(S, P, nullptr, K, W.Yt, JJ, G, mr_counter(W, cu, b), tc, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
+        if (!mr_tiles<1>(S, P, nullptr, K, W.Yt, JJ, b, G, tc, 0, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int i = S.cols[ta + 32 * j];
@@ -743,17 +897,17 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         for (int r = 0; r < R; r++)
             if (S.lam[r] < S.lstar[r]) live |= 1ull << r;
         S.live = live;
-        S.ccorr = (long long)K * (need_n ? 2 : 1);
-        S.lf = 1.0;
-        S.low = P.use_tc ? 1 : 0;
-        S.lowB = 0;
-        S.t0 = 0;
-        S.clowp = 0;
+        S.gcur = S.gprev = S.gnext = P.use_tc ? live : 0ull;
         for (int r = 0; r < kMR; r++) {
             S.best_gap[r] = INFINITY;
             S.since[r] = 0;
-            S.swok[r] = 1;
+            S.swnow[r] = 0;
+            S.t0r[r] = 0;
+            S.lfr[r] = 1.0;
+            S.btr[r] = 0.0;
             S.R2s[r] = 0.0;
+            S.ccr[r] = (long long)K * (need_n ? 2 : 1);  // the precompute passes
+            S.clr[r] = 0;
         }
         int k = 0;
         for (int r = 0; r < kMR; r++)
@@ -767,7 +921,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         DevResult& o = P.res[tid];
         o.iters = 0; o.status = kDevOk; o.n_active = 0; o.nnz = 0; o.gap = 0.0;
         o.primal = 0.5 * S.yy[tid]; o.dual = 0.5 * S.yy[tid]; o.lambda = S.lam[tid]; o.lambda_max = S.lstar[tid];
-        o.cols_corr = S.ccorr; o.cols_synth = 0; o.cols_lowp = 0;
+        o.cols_corr = S.ccr[tid]; o.cols_synth = 0; o.cols_lowp = 0;
     }
     if (need_n && S.live) {
         // d_* = sign(b_{i*}) d_{i*} of every problem (Lemma 3)
@@ -783,7 +937,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         }
         if (!grid_sync(bar, G, gen)) return false;
         const int JJ = (S.n_slots + 15) / 16;
-        if (!mr_tiles<1>(S, P, nullptr, K, W.Dst, JJ, G, mr_counter(W, cu, b), tc, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
+        if (!mr_tiles<1>(S, P, nullptr, K, W.Dst, JJ, b, G, tc, 0, [&](float (&acc)[4][4], float (&cmp)[4][4]) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 const int i = S.cols[ta + 32 * j];
@@ -806,7 +960,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         const int w_lo = p_lo + (int)((long long)warp * (p_hi - p_lo) / kMW);
         const int w_hi = p_lo + (int)((long long)(warp + 1) * (p_hi - p_lo) / kMW);
         const bool stat = !P.dynamic && P.test != 0;
-        const unsigned long long live = S.live;
+        const unsigned long long live = S.live, gcur = S.gcur;
         double rad0[2] = {0.0, 0.0}, R0[2] = {0.0, 0.0};
         for (int h = 0; h < 2; h++) {
             const int r = lane + 32 * h;
@@ -819,7 +973,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 rad0[h] = P.test == 2 ? sqrt(fmax(R2 - S.delta[r] * S.delta[r], 0.0)) : R0[h];
             }
         }
-        int kept = 0;
+        int kept0 = 0, kept1 = 0, kept2 = 0;
         for (int i = w_lo; i < w_hi; i++) {
             const double inv = 1.0 / P.colnorm[i];
             if (lane == 0) W.invn[i] = inv;
@@ -860,15 +1014,23 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
             }
             const unsigned lo = __ballot_sync(0xffffffffu, on[0]), hi = __ballot_sync(0xffffffffu, on[1]);
             const unsigned long long m = ((unsigned long long)hi << 32) | lo;
+            const int kf = (m != 0ull) | (((m & gcur) != 0ull) << 1) | (((m & ~gcur) != 0ull) << 2);
             if (lane == 0) {
                 W.amask[i] = m;
                 W.nzmask[i] = 0ull;
-                W.act[0][i] = i;
-                W.keep[i] = m != 0ull;
+                W.kzmask[i] = 0ull;
+                W.act[0][0][i] = i;
+                W.keep[i] = kf;
             }
-            kept += m != 0ull;
+            kept0 += kf & 1;
+            kept1 += (kf >> 1) & 1;
+            kept2 += (kf >> 2) & 1;
         }
-        if (lane == 0) S.ired[warp] = kept;
+        if (lane == 0) {
+            S.ired[warp] = kept0;
+            S.ired1[warp] = kept1;
+            S.ired2[warp] = kept2;
+        }
         if (tid < kMR) {
             W.c_nz[b * kMR + tid] = 0;
             W.p_l1[b * kMR + tid] = FF{0.f, 0.f};
@@ -877,168 +1039,92 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
         }
         __syncthreads();
         if (tid == 0) {
-            int k = 0;
-            for (int w = 0; w < kMW; w++) k += S.ired[w];
-            W.c_keep[b] = k;
+            int k0 = 0, k1 = 0, k2 = 0;
+            for (int w = 0; w < kMW; w++) {
+                k0 += S.ired[w];
+                k1 += S.ired1[w];
+                k2 += S.ired2[w];
+            }
+            W.c_keep[b] = k0;
+            W.c_keep[G + b] = k1;
+            W.c_keep[2 * G + b] = k2;
             W.s_alo[b] = p_lo;
-            S.nA = K;
+            S.nA[0] = K;
+            S.nA[1] = S.nA[2] = 0;
         }
     }
     if (!grid_sync(bar, G, gen)) return false;
 
     // ================================================================ iterations
+    //
+    // Lists (each compacted in order, double-buffered): 0 the union of the
+    // active sets of the live problems, 1 of the problems in their bulk phase
+    // (tensor cores on the BF16 copy), 2 of the problems in FP32.  A problem
+    // leaves the bulk phase on its own, with a fresh FISTA sequence.
     int cur = 0;  // list generation
     int xi = 0;   // xb[xi] holds the current x
     for (int t = 1;; t++) {
         // ======================================== (A) compaction + syntheses
         {
-            const int nA = S.nA;
+            const int nA = S.nA[0];
             const int nxt = cur ^ 1;
             const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
-            if (warp == 0) {
+            if (warp < 3) {
                 int base = 0, tot = 0;
                 for (int k = lane; k < G; k += 32) {
-                    const int c = __ldcg(W.c_keep + k);
+                    const int c = __ldcg(W.c_keep + warp * G + k);
                     if (k < b) base += c;
                     tot += c;
                 }
                 base = warp_sum(base);
                 tot = warp_sum(tot);
-                if (lane == 0) { S.keep_base = base; S.keep_tot = tot; }
+                if (lane == 0) { S.kbase[warp] = base; S.ktot[warp] = tot; }
             }
             for (int k = tid; k < G; k += kThreads) S.alo[k] = __ldcg(W.s_alo + k);
             __syncthreads();
-            int gb = S.keep_base;
-            const int nA_new = S.keep_tot;
+            int gb0 = S.kbase[0], gb1 = S.kbase[1], gb2 = S.kbase[2];
             for (int base = p_lo; base < p_hi; base += kThreads) {
                 const int p = base + tid;
-                const int k = p < p_hi ? __ldcg(W.keep + p) : 0;
+                int a = 0, kf = 0;
+                if (p < p_hi) {
+                    a = __ldcg(W.act[0][cur] + p);
+                    kf = __ldcg(W.keep + p);
+                }
+                // one packed scan of the three keep bits (at most 512 per field)
+                const int v = (kf & 1) | (((kf >> 1) & 1) << 10) | (((kf >> 2) & 1) << 20);
                 int tot;
-                const int pre = block_exclusive_scan(k, S.scan_tmp, &tot);
-                if (k) W.act[nxt][gb + pre] = __ldcg(W.act[cur] + p);
-                gb += tot;
+                const int pre = block_exclusive_scan(v, S.scan_tmp, &tot);
+                if (kf & 1) W.act[0][nxt][gb0 + (pre & 1023)] = a;
+                if (kf & 2) W.act[1][nxt][gb1 + ((pre >> 10) & 1023)] = a;
+                if (kf & 4) W.act[2][nxt][gb2 + ((pre >> 20) & 1023)] = a;
+                gb0 += tot & 1023;
+                gb1 += (tot >> 10) & 1023;
+                gb2 += (tot >> 20) & 1023;
             }
-            // syntheses: items (live problem, row tile), claimed by warps
+            // syntheses: items (live problem, block of 128 rows), claimed by the team's CTAs
             const int ns = S.n_slots;
             int* ctr = mr_counter(W, cu, b);
             for (;;) {
-                int it = 0;
-                if (lane == 0) it = atomicAdd(ctr, 1);
-                it = __shfl_sync(0xffffffffu, it, 0);
+                if (tid == 0) S.claim = atomicAdd(ctr, 1);
+                __syncthreads();
+                const int it = S.claim;
                 if (it >= ntile * ns) break;
-                const int s = it / ntile, rt = it - s * ntile;
-                const int r = S.slot_r[s];
-                int run = 0;
-                for (int b0 = 0; b0 < G; b0 += 32) {
-                    const int bb = b0 + lane;
-                    const int c = bb < G ? __ldcg(W.c_nz + bb * kMR + r) : 0;
-                    int x = c;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, x, o);
-                        if (lane >= o) x += y;
-                    }
-                    if (bb < G) S.dir[warp][bb] = run + x - c;
-                    run += __shfl_sync(0xffffffffu, x, 31);
-                }
-                if (lane == 0) S.dir[warp][G] = run;
-                __syncwarp();
-                const int E = run;
-                const int n0 = rt * kMSynRows + lane, n1 = n0 + 32;
-                Dot2f au0, au1, ax0, ax1;
-                const size_t rb = (size_t)r * K;
-                for (int e0 = 0; e0 < E; e0 += 32) {
-                    const int e = e0 + lane;
-                    int col = 0;
-                    FF uu{0.f, 0.f}, xx{0.f, 0.f};
-                    if (e < E) {
-                        int lo = 0, hi = G;  // largest segment start <= e
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (S.dir[warp][mid] <= e) lo = mid;
-                            else hi = mid;
-                        }
-                        const size_t idx = rb + S.alo[lo] + (e - S.dir[warp][lo]);
-                        col = __ldcg(W.nz_col + idx);
-                        uu = ldcg_x(W.nz_u + idx);
-                        xx = ldcg_x(W.nz_x + idx);
-                    }
-                    const int ne = min(32, E - e0);
-                    for (int k0 = 0; k0 < ne; k0 += 4) {
-                        float d0[4], d1[4];
-                        FF uk[4], xk[4];
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const int k = min(k0 + q, 31);
-                            const bool in = k0 + q < ne;
-                            const int c = __shfl_sync(0xffffffffu, col, k);
-                            uk[q].h = __shfl_sync(0xffffffffu, uu.h, k);
-                            uk[q].l = __shfl_sync(0xffffffffu, uu.l, k);
-                            xk[q].h = __shfl_sync(0xffffffffu, xx.h, k);
-                            xk[q].l = __shfl_sync(0xffffffffu, xx.l, k);
-                            const float* dc = P.D + (size_t)c * ld;
-                            d0[q] = (in && n0 < N) ? __ldg(dc + n0) : 0.f;
-                            d1[q] = (in && n1 < N) ? __ldg(dc + n1) : 0.f;
-                        }
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            syn_add(au0, d0[q], uk[q]);
-                            syn_add(ax0, d0[q], xk[q]);
-                            syn_add(au1, d1[q], uk[q]);
-                            syn_add(ax1, d1[q], xk[q]);
-                        }
-                    }
-                }
-                Dot2f pa, pb, pr;
-                if (n0 < N) {
-                    const float yv = __ldcg(W.Yt + (size_t)r * npad + n0);
-                    const float th = theta_from(au0, yv);
-                    W.Th[(size_t)r * npad + n0] = th;
-                    if (P.use_tc) {
-                        // theta = hi + lo + O(2^-18 |theta|) in BF16, for the tensor cores
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(th);
-                        const __nv_bfloat16 lb = __float2bfloat16_rn(th - __bfloat162float(hb));
-                        W.Thi[(size_t)r * npad + n0] = __bfloat16_as_ushort(hb);
-                        W.Tlo[(size_t)r * npad + n0] = __bfloat16_as_ushort(lb);
-                    }
-                    pa.add(th, yv);
-                    pb.add(th, th);
-                    acc_resid_sq(pr, ax0, yv);
-                }
-                if (n1 < N) {
-                    const float yv = __ldcg(W.Yt + (size_t)r * npad + n1);
-                    const float th = theta_from(au1, yv);
-                    W.Th[(size_t)r * npad + n1] = th;
-                    if (P.use_tc) {
-                        // theta = hi + lo + O(2^-18 |theta|) in BF16, for the tensor cores
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(th);
-                        const __nv_bfloat16 lb = __float2bfloat16_rn(th - __bfloat162float(hb));
-                        W.Thi[(size_t)r * npad + n1] = __bfloat16_as_ushort(hb);
-                        W.Tlo[(size_t)r * npad + n1] = __bfloat16_as_ushort(lb);
-                    }
-                    pa.add(th, yv);
-                    pb.add(th, th);
-                    acc_resid_sq(pr, ax1, yv);
-                }
-                pa = dot2_warp_reduce(pa);
-                pb = dot2_warp_reduce(pb);
-                pr = dot2_warp_reduce(pr);
-                if (lane == 0) {
-                    W.p_a[rt * kMR + r] = FF{pa.s, pa.c};
-                    W.p_b[rt * kMR + r] = FF{pb.s, pb.c};
-                    W.p_r[rt * kMR + r] = FF{pr.s, pr.c};
-                }
-                __syncwarp();
+                const int s = it / ntile, rb = it - s * ntile;
+                mr_synth_item(S, P, S.slot_r[s], rb, G, t);
             }
             __syncthreads();
-            if (tid == 0) S.nA = nA_new;
+            if (tid == 0) {
+                S.nA[0] = S.ktot[0];
+                S.nA[1] = S.ktot[1];
+                S.nA[2] = S.ktot[2];
+            }
             cur = nxt;
         }
         if (!grid_sync(bar, G, gen)) return false;
 
         // ======================================== (B) gaps, stop, correlation + prox
         {
-            const int nA = S.nA;
+            const int nA = S.nA[0];
             const int ns = S.n_slots;
             const unsigned long long live = S.live;
             // per-problem sums of the row-tile partials and of the CTA partials of (C)
@@ -1088,23 +1174,24 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 }
                 const double a_ = a.value(), b_ = bq.value(), r_ = rq.value(), l1_ = l1.value();
                 const double lam = S.lam[r], yy = S.yy[r];
-                int stop = 0;
-                S.swok[r] = 1;
+                const bool low_prev = (S.gprev >> r) & 1;  // the correlations of iteration t-1 came from the copy
+                int stop = 0, sw = 0;
                 if (t > 1) {
                     // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
                     const double primal = 0.5 * r_ + lam * l1_;
                     double gap = primal - 0.5 * yy + 0.5 * lam * lam * S.R2n[r];
-                    if (S.lowB) {
-                        // the nominal gap rests on the copy's correlations: stop only on the rigorous
-                        // one (dual point scaled with the bounded max), and let the block leave the copy
-                        // once every problem's nominal gap reached the switch level or stalled
+                    bool swok = false;
+                    if (low_prev) {
+                        // the nominal gap rests on the copy's correlations: stop only on the rigorous one
+                        // (dual point scaled with the bounded max); leave the copy once the nominal gap
+                        // reached the switch level or stopped improving
                         if (gap < 0.99 * S.best_gap[r]) {
                             S.best_gap[r] = gap;
                             S.since[r] = 0;
                         } else {
                             S.since[r]++;
                         }
-                        S.swok[r] = (gap <= P.lo_switch * 0.5 * yy) || S.since[r] >= 25;
+                        swok = (gap <= P.lo_switch * 0.5 * yy) || S.since[r] >= 25;
                         gap = primal - 0.5 * yy + 0.5 * lam * lam * S.R2s[r];
                     }
                     S.primal[r] = primal;
@@ -1113,48 +1200,46 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     S.na[r] = na;
                     S.nnzx[r] = nx;
                     stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                    sw = !stop && swok && ((S.gcur >> r) & 1);
                 }
+                if (sw) {
+                    // FP32 polish: a fresh FISTA sequence from the bulk iterate
+                    S.t0r[r] = t - 1;
+                    S.lfr[r] = 1.0;
+                }
+                double bt = 0.0;
+                if (!ista) {
+                    // FISTA (Table 1): l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t
+                    const int tf = t - S.t0r[r];
+                    if (tf <= P.fista_n) {
+                        bt = P.fista[2 * (tf - 1)];
+                        S.lfr[r] = P.fista[2 * (tf - 1) + 1];
+                    } else {
+                        const double lf = S.lfr[r];
+                        const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
+                        bt = (lf - 1.0) / ln;
+                        S.lfr[r] = ln;
+                    }
+                }
+                S.btr[r] = bt;
                 S.csyn[r] += ne;
                 S.alpha[r] = a_;
                 S.beta[r] = b_;
                 S.s_unc[r] = b_ > 0.0 ? a_ / lam * fast_rcp(b_) : 0.0;
                 S.sqrt_beta[r] = (double)sqrtf((float)b_) * (1.0 + 1e-6);
                 S.stopnow[r] = stop;
+                S.swnow[r] = sw;
             }
             __syncthreads();
             if (tid == 0) {
-                if (S.low && t > 1) {
-                    // FP32 polish: a fresh FISTA sequence from the bulk iterate, for the whole block
-                    bool all = true;
-                    for (int q = 0; q < ns; q++) {
-                        const int r = S.slot_r[q];
-                        if (!S.stopnow[r] && !S.swok[r]) all = false;
-                    }
-                    if (all) {
-                        S.low = 0;
-                        S.t0 = t - 1;
-                        S.lf = 1.0;
-                    }
+                unsigned long long dm = 0, sw = 0;
+                for (int s = 0; s < ns; s++) {
+                    const int r = S.slot_r[s];
+                    if (S.stopnow[r]) dm |= 1ull << r;
+                    if (S.swnow[r]) sw |= 1ull << r;
                 }
-                S.lowB = S.low;
-                double bt = 0.0;
-                const int tf = t - S.t0;  // index in the current FISTA sequence
-                if (!ista) {
-                    // FISTA (Table 1): l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t
-                    if (tf <= P.fista_n) {
-                        bt = P.fista[2 * (tf - 1)];
-                        S.lf = P.fista[2 * (tf - 1) + 1];
-                    } else {
-                        const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * S.lf * S.lf));
-                        bt = (S.lf - 1.0) / ln;
-                        S.lf = ln;
-                    }
-                }
-                S.bt = bt;
-                unsigned long long dm = 0;
-                for (int s = 0; s < ns; s++)
-                    if (S.stopnow[S.slot_r[s]]) dm |= 1ull << S.slot_r[s];
                 S.dm = dm;
+                S.gnext = S.gcur & ~sw;
             }
             __syncthreads();
             const unsigned long long dm = S.dm;
@@ -1162,11 +1247,12 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 // problems that met their tolerance leave the block: x of iteration t-1 out
                 const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
                 for (int p = p_lo + warp; p < p_hi; p += kMW) {
-                    const int i = __ldcg(W.act[cur] + p);
+                    const int i = __ldcg(W.act[0][cur] + p);
+                    const unsigned long long m = __ldcg(W.amask + i);
                     for (int h = 0; h < 2; h++) {
                         const int r = lane + 32 * h;
                         if ((dm >> r) & 1) {
-                            const FF x = ldcg_x(W.xb[xi] + (size_t)i * kMR + r);
+                            const FF x = ((m >> r) & 1) ? ldcg_x(W.xb[xi] + (size_t)i * kMR + r) : FF{0.f, 0.f};
                             P.X[(size_t)r * K + i] = it_round(x);
                         }
                     }
@@ -1183,79 +1269,87 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     o.dual = S.primal[r] - S.gap[r];
                     o.lambda = S.lam[r];
                     o.lambda_max = S.lstar[r];
-                    o.cols_corr = S.ccorr;
+                    o.cols_corr = S.ccr[r];
                     o.cols_synth = S.csyn[r];
-                    o.cols_lowp = S.clowp;
+                    o.cols_lowp = S.clr[r];
                 }
                 __syncthreads();
-                if (tid == 0) {
-                    S.live &= ~dm;
-                    int k = 0;
-                    for (int r = 0; r < kMR; r++)
-                        if ((S.live >> r) & 1) S.slot_r[k++] = r;
-                    S.n_slots = k;
-                    for (int s = k; s < kMR; s++) S.slot_r[s] = -1;
-                }
+                if (tid == 0) S.live &= ~dm;
                 __syncthreads();
             }
             if (S.live == 0ull) break;
-            if (tid == 0) {
-                S.ccorr += nA;
-                if (S.lowB) S.clowp += nA;
+            const unsigned long long live2 = S.live;
+            if (tid < kMR && ((live2 >> tid) & 1)) {
+                const bool lo = (S.gcur >> tid) & 1;
+                S.ccr[tid] += lo ? S.nA[1] : S.nA[2];
+                if (lo) S.clr[tid] += S.nA[1];
             }
-            if (tid < kMR) S.zmax[tid] = 0u;
-            __syncthreads();
-            const int ns2 = S.n_slots;
-            const int JJ = (ns2 + 15) / 16;
-            float zm[4] = {0.f, 0.f, 0.f, 0.f};
-            FF* xo = W.xb[xi ^ 1];
-            auto prox = [&](float (&acc)[4][4], float (&)[4][4]) {
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int i = S.cols[ta + 32 * j];
-                    if (i < 0) continue;
-                    const unsigned long long m = __ldcg(W.amask + i);
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        if (q >= JJ) continue;
-                        const int r = S.slot_r[tr + 16 * q];
-                        if (r < 0) continue;
-                        const size_t idx = (size_t)i * kMR + r;
-                        FF xn{0.f, 0.f};
-                        if ((m >> r) & 1) {
-                            // proximal step (Table 1): x = soft(u - z / L, lambda / L)
-                            const float z = acc[j][q];
-                            xn = it_soft(it_grad_step(ldcg_x(W.u + idx), z, invL), S.thrX[r]);
-                            zm[q] = fmaxf(zm[q], fabsf(z));
-                        }
-                        xo[idx] = xn;
-                    }
+            // the correlations of each group over its own list: bulk problems on the tensor cores
+            // (BF16 copy), the others on the FP32 master
+            for (int grp = 0; grp < 2; grp++) {
+                const unsigned long long gm = grp == 0 ? (live2 & S.gcur) : (live2 & ~S.gcur);
+                if (gm == 0ull) continue;
+                if (tid == 0) {
+                    int k = 0;
+                    for (int r = 0; r < kMR; r++)
+                        if ((gm >> r) & 1) S.slot_r[k++] = r;
+                    S.n_slots = k;
+                    for (int s = k; s < kMR; s++) S.slot_r[s] = -1;
                 }
-            };
-            // bulk phase: the BF16 copy on the tensor cores; then the FP32 master
-            int* ctr = mr_counter(W, cu, b);
-            const bool okt = S.lowB ? mr_tiles<2>(S, P, W.act[cur], nA, W.Th, JJ, G, ctr, tc, prox)
-                                    : mr_tiles<0>(S, P, W.act[cur], nA, W.Th, JJ, G, ctr, tc, prox);
-            if (!okt) return false;
+                if (tid < kMR) S.zmax[tid] = 0u;
+                __syncthreads();
+                const int JJ = (S.n_slots + 15) / 16;
+                float zm[4] = {0.f, 0.f, 0.f, 0.f};
+                FF* xo = W.xb[xi ^ 1];
+                auto prox = [&](float (&acc)[4][4], float (&)[4][4]) {
 #pragma unroll
-            for (int q = 0; q < 4; q++)
-                if (q < JJ) atomicMax(&S.zmax[tr + 16 * q], __float_as_uint(zm[q]));
-            __syncthreads();
-            if (tid < kMR) {
-                const int r = tid;
-                // this CTA's max |z| of every live problem (0 when it finished no tile)
-                float v = 0.f;
-                for (int s = 0; s < ns2; s++)
-                    if (S.slot_r[s] == r) v = __uint_as_float(S.zmax[s]);
-                if ((S.live >> r) & 1) W.p_m[b * kMR + r] = v;
+                    for (int j = 0; j < 4; j++) {
+                        const int i = S.cols[ta + 32 * j];
+                        if (i < 0) continue;
+                        const unsigned long long m = __ldcg(W.amask + i);
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            if (q >= JJ) continue;
+                            const int r = S.slot_r[tr + 16 * q];
+                            if (r < 0) continue;
+                            const size_t idx = (size_t)i * kMR + r;
+                            FF xn{0.f, 0.f};
+                            if ((m >> r) & 1) {
+                                // proximal step (Table 1): x = soft(u - z / L, lambda / L)
+                                const float z = acc[j][q];
+                                xn = it_soft(it_grad_step(ldcg_x(W.u + idx), z, invL), S.thrX[r]);
+                                zm[q] = fmaxf(zm[q], fabsf(z));
+                            }
+                            xo[idx] = xn;
+                        }
+                    }
+                };
+                const bool okt = grp == 0 ? mr_tiles<2>(S, P, W.act[1][cur], S.nA[1], W.Th, JJ, b, G, tc, 0, prox)
+                                          : mr_tiles<0>(S, P, W.act[2][cur], S.nA[2], W.Th, JJ, b, G, tc, 1, prox);
+                if (!okt) return false;
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (q < JJ) atomicMax(&S.zmax[tr + 16 * q], __float_as_uint(zm[q]));
+                __syncthreads();
+                if (tid < S.n_slots) W.p_m[b * kMR + S.slot_r[tid]] = __uint_as_float(S.zmax[tid]);
+                __syncthreads();
             }
+            // the live list again (syntheses, stop tests)
+            if (tid == 0) {
+                int k = 0;
+                for (int r = 0; r < kMR; r++)
+                    if ((live2 >> r) & 1) S.slot_r[k++] = r;
+                S.n_slots = k;
+                for (int s = k; s < kMR; s++) S.slot_r[s] = -1;
+            }
+            __syncthreads();
         }
         if (!grid_sync(bar, G, gen)) return false;
 
         // ======================================== (C) screening + momentum
         {
-            const int nA = S.nA;
-            const unsigned long long live = S.live;
+            const int nA = S.nA[0];
+            const unsigned long long live = S.live, gcur = S.gcur, gnext = S.gnext;
             {
                 // m_r = max_i |z_i| over the CTA partials, then Lemma 8 and the radius per problem
                 float* mx = reinterpret_cast<float*>(S.stage);  // [kMW][kMR]
@@ -1274,11 +1368,12 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     float mf = 0.f;
                     for (int w = 0; w < kMW; w++) mf = fmaxf(mf, mx[w * kMR + r]);
                     // Lemma 8 with the nominal max |z| (gap) and a rigorous upper bound of it (radius)
+                    // (copy: |z_i - zc_i| <= ||d_i - copy_i|| ||theta|| + ||copy_i|| (||theta - hi - lo|| +
+                    // the accumulation bound of the tensor-core sums))
                     const double m_nom = (double)mf;
-                    // copy: |z_i - zc_i| <= ||d_i - copy_i|| ||theta|| + ||copy_i|| (||theta - hi - lo|| +
-                    // the accumulation bound of the tensor-core sums)
+                    const bool lo = (gcur >> r) & 1;
                     const double m_up =
-                        m_nom + (S.lowB ? P.emax + (P.fmax + P.emax) * (0x1p-17 + P.gamma_tc) : P.gamma * P.fmax) *
+                        m_nom + (lo ? P.emax + (P.fmax + P.emax) * (0x1p-17 + P.gamma_tc) : P.gamma * P.fmax) *
                                     S.sqrt_beta[r];
                     const double su = S.s_unc[r];
                     const double mu_nom = (m_nom > 0.0 && fabs(su) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), su) : su;
@@ -1296,16 +1391,16 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 }
                 __syncthreads();
             }
-            const FF btX = ff_from_double(S.bt);
             const bool dyn = P.dynamic && P.test != 0;
             const int p_lo = (int)((long long)b * nA / G), p_hi = (int)((long long)(b + 1) * nA / G);
             const int w_lo = p_lo + (int)((long long)warp * (p_hi - p_lo) / kMW);
             const int w_hi = p_lo + (int)((long long)(warp + 1) * (p_hi - p_lo) / kMW);
             FF* xnew = W.xb[xi ^ 1];
             const FF* xold = W.xb[xi];
-            int cnt[2] = {0, 0}, na[2] = {0, 0}, nx[2] = {0, 0}, kept = 0;
+            int cnt[2] = {0, 0}, na[2] = {0, 0}, nx[2] = {0, 0}, kept0 = 0, kept1 = 0, kept2 = 0;
             Dot2f l1[2];
             double radh[2], Rsh[2], rhoh[2], psih[2], ilh[2];
+            FF btXh[2];
             bool lv[2];
             for (int h = 0; h < 2; h++) {
                 const int r = lane + 32 * h;
@@ -1315,13 +1410,14 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 rhoh[h] = lv[h] ? S.rho[r] : 0.0;
                 psih[h] = lv[h] ? S.psi_d[r] : 0.0;
                 ilh[h] = lv[h] ? 1.0 / S.lam[r] : 0.0;
+                btXh[h] = ff_from_double(lv[h] ? S.btr[r] : 0.0);
             }
             for (int p0 = w_lo; p0 < w_hi; p0 += kCB) {
                 // kCB atoms per step, every load of the step issued before it is used
                 int iv[kCB];
                 unsigned long long mv[kCB];
 #pragma unroll
-                for (int q = 0; q < kCB; q++) iv[q] = p0 + q < w_hi ? __ldcg(W.act[cur] + p0 + q) : -1;
+                for (int q = 0; q < kCB; q++) iv[q] = p0 + q < w_hi ? __ldcg(W.act[0][cur] + p0 + q) : -1;
 #pragma unroll
                 for (int q = 0; q < kCB; q++) mv[q] = iv[q] >= 0 ? __ldcg(W.amask + iv[q]) : 0ull;
                 bool on[kCB][2];
@@ -1345,10 +1441,11 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     }
 #pragma unroll
                 for (int q = 0; q < kCB; q++) {
-                    bool nz[2];
+                    bool nz[2], kz[2];
 #pragma unroll
                     for (int h = 0; h < 2; h++) {
                         nz[h] = false;
+                        kz[h] = false;
                         if (!on[q][h]) continue;
                         const int r = lane + 32 * h;
                         const size_t idx = (size_t)iv[q] * kMR + r;
@@ -1371,12 +1468,16 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                             on[q][h] = false;
                             xnew[idx] = FF{0.f, 0.f};
                             W.u[idx] = FF{0.f, 0.f};
+                            // the next synthesis removes d_i x_{t-1,i} from D x_{t-1} (FISTA)
+                            kz[h] = !ista && it_nz(xw[q][h]);
+                            nz[h] = kz[h];
+                            cnt[h] += nz[h];
                             continue;
                         }
                         const FF x = xv[q][h];
-                        const FF uu = ista ? x : it_momentum(x, xw[q][h], btX);
+                        const FF uu = ista ? x : it_momentum(x, xw[q][h], btXh[h]);
                         W.u[idx] = uu;
-                        nz[h] = it_nz(x) || it_nz(uu);
+                        nz[h] = it_nz(x);
                         nx[h] += it_nz(x);
                         acc_abs(l1[h], x);
                         na[h] += 1;
@@ -1384,13 +1485,21 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                     }
                     const unsigned lo = __ballot_sync(0xffffffffu, on[q][0]), hi = __ballot_sync(0xffffffffu, on[q][1]);
                     const unsigned zlo = __ballot_sync(0xffffffffu, nz[0]), zhi = __ballot_sync(0xffffffffu, nz[1]);
+                    const unsigned klo = __ballot_sync(0xffffffffu, kz[0]), khi = __ballot_sync(0xffffffffu, kz[1]);
                     const unsigned long long onm = ((unsigned long long)hi << 32) | lo;
+                    // the lists of the next iteration: union, bulk group, FP32 group
+                    const int kf = (onm != 0ull) | (((onm & gnext) != 0ull) << 1) | (((onm & ~gnext) != 0ull) << 2);
                     if (lane == 0 && iv[q] >= 0) {
                         W.amask[iv[q]] = (mv[q] & ~live) | onm;
                         W.nzmask[iv[q]] = ((unsigned long long)zhi << 32) | zlo;
-                        W.keep[p0 + q] = onm != 0ull;
+                        W.kzmask[iv[q]] = ((unsigned long long)khi << 32) | klo;
+                        W.keep[p0 + q] = kf;
                     }
-                    kept += (iv[q] >= 0 && onm != 0ull);
+                    if (iv[q] >= 0) {
+                        kept0 += kf & 1;
+                        kept1 += (kf >> 1) & 1;
+                        kept2 += (kf >> 2) & 1;
+                    }
                 }
             }
             for (int h = 0; h < 2; h++) {
@@ -1401,7 +1510,11 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 RS.n[0][warp][r] = na[h];
                 RS.n[1][warp][r] = nx[h];
             }
-            if (lane == 0) S.ired[warp] = kept;
+            if (lane == 0) {
+                S.ired[warp] = kept0;
+                S.ired1[warp] = kept1;
+                S.ired2[warp] = kept2;
+            }
             __syncthreads();
             if (tid < kMR) {
                 const int r = tid;
@@ -1421,9 +1534,15 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                 W.c_nnzx[b * kMR + r] = x;
             }
             if (tid == 0) {
-                int k = 0;
-                for (int w = 0; w < kMW; w++) k += S.ired[w];
-                W.c_keep[b] = k;
+                int k0 = 0, k1 = 0, k2 = 0;
+                for (int w = 0; w < kMW; w++) {
+                    k0 += S.ired[w];
+                    k1 += S.ired1[w];
+                    k2 += S.ired2[w];
+                }
+                W.c_keep[b] = k0;
+                W.c_keep[G + b] = k1;
+                W.c_keep[2 * G + b] = k2;
                 W.s_alo[b] = p_lo;
             }
             __syncthreads();
@@ -1431,11 +1550,14 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
             int e[2] = {S.cnt[warp][lane], S.cnt[warp][lane + 32]};
             for (int p0 = w_lo; p0 < w_hi; p0 += kCB) {
                 int iv[kCB];
-                unsigned long long zv[kCB];
+                unsigned long long zv[kCB], kv[kCB];
 #pragma unroll
-                for (int q = 0; q < kCB; q++) iv[q] = p0 + q < w_hi ? __ldcg(W.act[cur] + p0 + q) : -1;
+                for (int q = 0; q < kCB; q++) iv[q] = p0 + q < w_hi ? __ldcg(W.act[0][cur] + p0 + q) : -1;
 #pragma unroll
-                for (int q = 0; q < kCB; q++) zv[q] = iv[q] >= 0 ? __ldcg(W.nzmask + iv[q]) : 0ull;
+                for (int q = 0; q < kCB; q++) {
+                    zv[q] = iv[q] >= 0 ? __ldcg(W.nzmask + iv[q]) : 0ull;
+                    kv[q] = iv[q] >= 0 ? __ldcg(W.kzmask + iv[q]) : 0ull;
+                }
 #pragma unroll
                 for (int q = 0; q < kCB; q++)
 #pragma unroll
@@ -1444,13 +1566,18 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                         if ((zv[q] >> r) & 1) {
                             const size_t idx = (size_t)iv[q] * kMR + r;
                             const size_t o = (size_t)r * K + p_lo + e[h]++;
-                            W.nz_col[o] = iv[q];
-                            W.nz_u[o] = ldcg_x(W.u + idx);
-                            W.nz_x[o] = ldcg_x(xnew + idx);
+                            const bool k = (kv[q] >> r) & 1;
+                            W.nz_col[o] = k ? -iv[q] - 1 : iv[q];
+                            W.nz_x[o] = k ? ldcg_x(xold + idx) : ldcg_x(xnew + idx);
                         }
                     }
             }
             xi ^= 1;
+            __syncthreads();
+            if (tid == 0) {
+                S.gprev = gcur;
+                S.gcur = gnext;
+            }
         }
         if (!grid_sync(bar, G, gen)) return false;
     }
@@ -1577,21 +1704,25 @@ size_t mrhs_layout(char* base, int N, int K, int G, bool dome, MrhsWs* w)
     w->u = bp.take<FF>((size_t)K * kMR);
     w->amask = bp.take<unsigned long long>(K);
     w->nzmask = bp.take<unsigned long long>(K);
-    w->act[0] = bp.take<int>(K);
-    w->act[1] = bp.take<int>(K);
+    w->kzmask = bp.take<unsigned long long>(K);
+    for (int l = 0; l < 3; l++) {
+        w->act[l][0] = bp.take<int>(K);
+        w->act[l][1] = bp.take<int>(K);
+    }
     w->keep = bp.take<int>(K);
     w->nz_col = bp.take<int>((size_t)kMR * K);
-    w->nz_u = bp.take<FF>((size_t)kMR * K);
     w->nz_x = bp.take<FF>((size_t)kMR * K);
-    w->part = bp.take<float>((size_t)kMMaxSplit * G * kMTA * kMR * 2);
-    w->tilecnt = bp.take<int>((K + kMTA - 1) / kMTA);
+    w->wb[0] = bp.take<FF>((size_t)kMR * npad);
+    w->wb[1] = bp.take<FF>((size_t)kMR * npad);
+    w->part = bp.take<float>((size_t)2 * 2 * G * kMTA * kMR * 2);
+    w->tilecnt = bp.take<int>((size_t)2 * ((K + kMTA - 1) / kMTA));
     w->ctr = bp.take<int>(3);
     w->p_m = bp.take<float>((size_t)kMR * G);
     w->p_l1 = bp.take<FF>((size_t)kMR * G);
     w->c_na = bp.take<int>((size_t)kMR * G);
     w->c_nnzx = bp.take<int>((size_t)kMR * G);
     w->c_nz = bp.take<int>((size_t)kMR * G);
-    w->c_keep = bp.take<int>(G);
+    w->c_keep = bp.take<int>((size_t)3 * G);
     w->s_alo = bp.take<int>(G);
     w->p_v = bp.take<double>((size_t)kMR * G);
     w->p_i = bp.take<int>((size_t)kMR * G);
@@ -1705,7 +1836,8 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
         P.fmax = dc->fmax;
         P.L = opt->L > 0.0 ? opt->L : dc->L;
         {
-            // rounding of the FP32 contraction: 32 FMAs a chunk, the chunk sums, the row splits
+            // rounding of the FP32 contraction: 32 FMAs a chunk, the chunk sums, the sums of the
+            // parked partial tiles (at most one per chunk)
             const double u = std::ldexp(1.0, -24);
             const double k = 32.0 + 2.0 * (P.npad / kMKC) + 2.0;
             P.gamma = 1.01 * k * u / (1.0 - k * u);
@@ -1732,12 +1864,13 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
             P.emax = dc->emax;
             {
                 // tensor-core sums, bounded as if every addition of a K = 16 step (16 products and
-                // the accumulator) truncated to FP32 (unit 2^-23), plus the row-split sums
+                // the accumulator) truncated to FP32 (unit 2^-23), plus the sums of the parked
+                // partial tiles (at most one per 64-row chunk) and hi + lo
                 const double u = std::ldexp(1.0, -23);
-                const double k = 17.0 * (P.npad / 16) + 16.0;
+                const double k = 17.0 * (P.npad / 16) + (P.npad / kTcRows) + 2.0;
                 P.gamma_tc = 1.01 * k * u / (1.0 - k * u);
             }
-            P.lo_switch = opt->lowp_switch > 0.0 ? opt->lowp_switch : (opt->tol_gap_rel > 0.0 ? opt->tol_gap_rel : 1e-6);
+            P.lo_switch = opt->lowp_switch > 0.0 ? opt->lowp_switch : std::max(1e-3, opt->tol_gap_rel);
             use_tc = 1;
         }
         M->hjobs[jj] = P;

@@ -1485,9 +1485,10 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
         const double k = 16 + 5 + g.nchunk + 1;
         P.gamma_lo = 1.01 * k * u / (1.0 - k * u);
     }
-    // default: the bulk phase runs until its nominal gap reaches the target (or stalls);
-    // the FP32 iterations then only have to certify it
-    P.lo_switch = (opt && opt->lowp_switch > 0.0) ? opt->lowp_switch : ((opt && opt->tol_gap_rel > 0.0) ? opt->tol_gap_rel : 1e-6);
+    // default: leave the copy once the nominal gap is below 1e-3 (or the tolerance, if coarser); the
+    // FP32 iterations restart FISTA from there, which also acts as a restart of the momentum
+    P.lo_switch = (opt && opt->lowp_switch > 0.0) ? opt->lowp_switch
+                                                   : std::max(1e-3, (opt && opt->tol_gap_rel > 0.0) ? opt->tol_gap_rel : 0.0);
 }
 
 }  // namespace ds
