@@ -52,7 +52,10 @@ struct TeamArgs {
     const volatile int* stop;       // mapped host: shutdown request
     volatile int* done;             // mapped host: per slot, sequence number + 1 when finished
     ServerJob<T>* ring;             // mapped host: request descriptors, one per slot
-    long long idle_polls;           // server: give up waiting for work after this many polls
+    long long idle_polls;           // server: a team counts itself idle after this many empty polls
+    int n_teams;                    // server: teams of the launch
+    int* idle_teams;                // server: teams counted idle (zeroed per launch)
+    int* exiting;                   // server: set when every team was idle (zeroed per launch)
 };
 
 __device__ __forceinline__ int ld_acquire_sys(const volatile int* p)
@@ -80,17 +83,35 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
                 j = atomicAdd(A.next_job, 1);
                 if (j >= A.n_jobs) j = -1;
             } else {
+                // the launch ends only when every team is idle: a team that has waited long enough
+                // counts itself idle (and uncounts itself if work arrives); the team that sees all
+                // teams idle raises `exiting`, which takes every team out, and the host relaunches on
+                // the next request.  (A team leaving on its own would leave the rest of the launch
+                // to its remaining teams, which would then serve every later request.)
                 long long polls = 0;
+                bool counted = false;
                 while (!*A.stop) {
+                    if (atomicAdd(A.exiting, 0)) break;
                     const int head = atomicAdd(A.next_job, 0);
                     if (head < ld_acquire_sys(A.published)) {
+                        if (counted) {
+                            atomicSub(A.idle_teams, 1);
+                            counted = false;
+                        }
                         if (atomicCAS(A.next_job, head, head + 1) == head) {
                             j = head;
                             break;
                         }
                         continue;
                     }
-                    if (++polls > A.idle_polls) break;  // idle: the host relaunches on the next request
+                    if (++polls > A.idle_polls && !counted) {
+                        atomicAdd(A.idle_teams, 1);
+                        counted = true;
+                    }
+                    if (counted && atomicAdd(A.idle_teams, 0) >= A.n_teams) {
+                        atomicExch(A.exiting, 1);
+                        break;
+                    }
                     __nanosleep(polls < 64 ? 200 : 2000);
                 }
             }
@@ -955,7 +976,7 @@ ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, 
         cudaHostGetDevicePointer((void**)&S->ctl_d, S->ctl_h, 0) != cudaSuccess)
         return fail(DS_ERR_CUDA);
     // device control: barriers + team_job (reset per launch), queue head + error (persistent), FISTA table
-    S->bars_bytes = ds::align_up(sizeof(ds::GridBarrier) * S->n_teams + sizeof(int) * S->n_teams, 256);
+    S->bars_bytes = ds::align_up(sizeof(ds::GridBarrier) * S->n_teams + sizeof(int) * (S->n_teams + 2), 256);
     ds_status st = ds::ctx_fista_table(ctx, 1 << 16);
     if (st != DS_OK) return fail(st);
     S->fista_n = ctx->fista_n;
@@ -973,6 +994,9 @@ ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, 
     A.n_jobs = S->ring;
     A.bars = reinterpret_cast<ds::GridBarrier*>(c);
     A.team_job = reinterpret_cast<int*>(c + sizeof(ds::GridBarrier) * S->n_teams);
+    A.idle_teams = A.team_job + S->n_teams;
+    A.exiting = A.idle_teams + 1;
+    A.n_teams = S->n_teams;
     A.next_job = next_job;
     A.error = S->derr;
     A.team_size = S->team_size;

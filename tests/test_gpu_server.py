@@ -105,3 +105,38 @@ def test_server_rejects_oversized_and_admits_by_pool():
         ds.ds_server_destroy(server)
         ds.ds_dict_destroy(dct)
         ds.ds_destroy(ctx)
+
+
+def test_server_requests_after_a_lull_run_side_by_side():
+    # A long request keeps one team busy while the others wait long enough to count themselves
+    # idle; requests submitted then must still be spread over all teams (the launch ends only when
+    # every team is idle), not queued behind the busy team.
+    g = gen.rng(304)
+    ctx = ds.ds_create(0, None)
+    N, K = 700, 4000
+    D = gen.gaussian_dict(N, K, g)
+    d = ds.ds_dict_create(ctx, _dev_dict(D))
+    ys = [gen.observe(D, gen.bernoulli_gaussian_x0(K, 0.02, g), g).astype(np.float32) for _ in range(9)]
+    o = ds.ds_options_default(test="dst3", tol_gap_rel=0.0, max_iter=4000, lambda_rel=1)
+    srv = ds.ds_server_create(ctx, 1 << 30, N, K, 4)
+    try:
+        x = np.zeros(K, dtype=np.float32)
+        t0 = time.time()
+        (r0,) = _wait(srv, [ds.ds_server_submit(srv, d, ys[0], 0.5, o, x)])
+        t_one = time.time() - t0
+        long_x = np.zeros(K, dtype=np.float32)
+        o_long = ds.ds_options_default(test="dst3", tol_gap_rel=0.0, max_iter=40000, lambda_rel=1)
+        t_long = ds.ds_server_submit(srv, d, ys[0], 0.5, o_long, long_x)
+        time.sleep(0.2)  # the idle teams pass their idle limit meanwhile
+        xs = [np.zeros(K, dtype=np.float32) for _ in range(8)]
+        t1 = time.time()
+        res = _wait(srv, [ds.ds_server_submit(srv, d, ys[k + 1], 0.5, o, xs[k]) for k in range(8)])
+        t_eight = time.time() - t1
+        _wait(srv, [t_long])
+        assert all(r["iters"] == 4000 for r in res)
+        # side by side: eight requests take about as long as one (queued they would take eight times as long)
+        assert t_eight < 4.0 * t_one, (t_eight, t_one)
+    finally:
+        ds.ds_server_destroy(srv)
+        ds.ds_dict_destroy(d)
+        ds.ds_destroy(ctx)
