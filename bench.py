@@ -483,11 +483,13 @@ def batched_uneven_measure(ds, ctx, dev, flush, n_inst=8, plain_per_inst=4):
                       f"{plain_per_inst} problems per instance ({cnt} solves)"}
 
 
-def served_measure(ds, ctx, dev, seconds=3.0, rate=100.0, drain_s=20.0):
+def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=24):
     """Open-loop Poisson stream of mixed requests (80% Lasso / 20% Group-Lasso with
     groups of 8) on AR(1) dictionaries (rho = 0.9, unit-norm columns) of N in
-    {512..2048} and K in {4096..16384}, lambda/lambda_max ~ U[0.1, 0.9], gap 1e-6:
-    p50/p99 latency from submission to completion and completed solves/s."""
+    {512..2048} and K in {4096..16384}, FP32 master + FP8 e4m3 working copy with a
+    scale per column, lambda/lambda_max ~ U[0.1, 0.9], gap 1e-6: p50/p99 latency from
+    submission to completion and completed solves/s, against the plain form (a sample
+    of plain_n requests of the same mix solved one at a time)."""
     import time
     import torch
     g = np.random.default_rng(2005)
@@ -502,9 +504,9 @@ def served_measure(ds, ctx, dev, seconds=3.0, rate=100.0, drain_s=20.0):
             D[n] = 0.9 * D[n - 1] + s * E[n]
         D /= D.norm(dim=0, keepdim=True)
         Dc = D.t().contiguous().t()  # column-major
-        lasso = ds.ds_dict_create(ctx, Dc)
+        lasso = ds.ds_dict_create(ctx, Dc, work_prec=ds.DS_FP8)
         goff = np.arange(0, K + 1, 8, dtype=np.int64)
-        group = ds.ds_dict_create(ctx, Dc, goff)
+        group = ds.ds_dict_create(ctx, Dc, goff, work_prec=ds.DS_FP8)
         # a bank of observations per dictionary: 1% active atoms (groups), 20 dB
         B = 16
         X0 = torch.zeros((K, B), device=dev)
@@ -552,17 +554,31 @@ def served_measure(ds, ctx, dev, seconds=3.0, rate=100.0, drain_s=20.0):
     unfinished = len(outstanding)
     st = ds.ds_server_stats(server)
     ds.ds_server_destroy(server)
+    # plain form: requests of the same mix, one at a time (the whole GPU per solve)
+    gp = np.random.default_rng(2006)
+    torch.cuda.synchronize()
+    tp0 = time.perf_counter()
+    for _ in range(plain_n):
+        N, K, lasso, group, Y = pool[gp.integers(len(pool))]
+        kind = "group" if gp.uniform() < 0.2 else "lasso"
+        yd = torch.from_numpy(Y[gp.integers(Y.shape[0])].copy()).to(dev)
+        xd = torch.zeros(K, device=dev)
+        ds.ds_solve(ctx, group if kind == "group" else lasso, yd, float(gp.uniform(0.1, 0.9)), opts[kind], xd)
+    torch.cuda.synchronize()
+    plain = plain_n / (time.perf_counter() - tp0)
     for (_, _, lasso, group, _) in pool:
         ds.ds_dict_destroy(lasso)
         ds.ds_dict_destroy(group)
     lat = np.array(lat)
-    return {"value": len(lat) / wall, "unit": "solves/s", "offered_rate": rate, "requests": int(len(lat)),
+    return {"value": len(lat) / wall, "unit": "solves/s", "plain_value": plain, "vs_plain": len(lat) / wall / plain,
+            "offered_rate": rate, "requests": int(len(lat)),
             "unfinished_at_deadline": unfinished, "window_s": seconds, "wall_s": wall,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "converged": int(sum(1 for s_ in keep if s_ == 0)), "kernel_launches": st["launches"],
             "workload": "Poisson arrivals, 80% Lasso / 20% Group-Lasso (groups of 8), AR(1) rho=0.9 dictionaries "
                         "N in {512,1024,1536,2048}, K in {4096,8192,12288,16384}, lambda/lambda_max ~ U[0.1,0.9], "
-                        "gap 1e-6, FISTA + DST3/DGST3, teams of 4 CTAs, 4 GiB pool"}
+                        "FP8 e4m3 copy with per-column scale + FP32 master, gap 1e-6, FISTA + DST3/DGST3, teams of 4 "
+                        "CTAs, 4 GiB pool; plain: a sample of the same mix solved one at a time"}
 
 
 def large_roofline(ds, ctx, dev, stream, peak, peak_kind):
