@@ -201,12 +201,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--profile-one", action="store_true",
                     help="register the dictionary and run one 5-lambda DST3 path, then exit (profiling)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run one 64-rhs multi-RHS batch on the BF16 copy of the dictionary, then exit (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.profile_one:
         profile_one()
+        return
+    if args.profile_batch:
+        profile_batch()
         return
 
     import torch
@@ -331,6 +336,30 @@ def main():
         print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
+
+
+def profile_batch():
+    """One launch of the multi-RHS kernel: 64 right-hand sides on the 2000 x 10000 dictionary
+    with its BF16 copy (tensor-core bulk phase, FP32 polish), FISTA + DST3 to gap 1e-6."""
+    import torch
+    import paper_1412_4080_gb300 as ds
+    D32, _ = problem()
+    g = np.random.default_rng(2002)
+    Y, ratios = _rhs_block(D32, 64, g)
+    Dt = torch.from_numpy(np.ascontiguousarray(D32.T)).cuda().t()
+    ctx = ds.ds_create(0, torch.cuda.current_stream())
+    dct = ds.ds_dict_create(ctx, Dt, work_prec=ds.DS_BF16)
+    Yt = torch.from_numpy(Y).cuda()
+    X = torch.zeros((64, D32.shape[1]), device="cuda")
+    opt = ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)
+    plan = ds.ds_batch_create(ctx, [dct], [Yt], [ratios], opt, [X])
+    res = ds.ds_batch_run(plan)
+    ds.ds_batch_destroy(plan)
+    ds.ds_dict_destroy(dct)
+    ds.ds_destroy(ctx)
+    print(json.dumps({"solves": len(res), "converged": sum(r["status"] == 0 for r in res),
+                      "iters_max": max(r["iters"] for r in res), "ms": res[0]["ms"],
+                      "cols_corr": sum(r["cols_corr"] for r in res), "cols_lowp": sum(r["cols_lowp"] for r in res)}))
 
 
 def profile_one():
