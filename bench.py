@@ -316,8 +316,8 @@ def main():
         t0 = time.perf_counter()
         step(yh, Xh, Dh_np)
         e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
-    out["e2e"] = {"value": solves_per_step * world / e2e_s, "unit": "solves/s",
+    e2e_s = float(np.mean(e2e_t)) if e2e_t else float("nan")
+    out["e2e"] = {"value": solves_per_step * world / e2e_s if e2e_t else None, "unit": "solves/s",
                   "h2d_bytes_per_step": int(D32.nbytes + len(TESTS) * y32.nbytes),
                   "d2h_bytes_per_step": int(len(TESTS) * Xh.nbytes)}
 
