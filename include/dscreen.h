@@ -205,6 +205,20 @@ ds_status ds_batch_info(const ds_batch* batch, int* uses_graph, int* teams, int*
  * Errors: DS_ERR_INVALID on NULL batch. */
 ds_status ds_batch_layout(const ds_batch* batch, int* multi_rhs_blocks, int* multi_rhs_teams, int* multi_rhs_team_size,
                           int* single_problems);
+/* Autotuner of the multi-RHS schedule.  Runs the batch once under each of up to
+ * max_candidates schedules -- the plan's own first, then: blocks of 32 right-hand sides
+ * grouped by lambda (similar iteration counts and screened sets per block), and, when a
+ * dictionary has a BF16 copy, the tensor-core bulk phase turned off / on and a coarser
+ * switch level (1e-2) -- timing each run on the device, and keeps the fastest for the
+ * following ds_batch_run calls (the batch's handle stays valid).  Every tuning run
+ * solves the batch, so X_out holds a valid solution afterwards.  ms_tried (nullable,
+ * max_candidates entries) receives each run's device time in ms (-1 when a candidate
+ * could not be built); *chosen the index of the kept schedule (0: unchanged).
+ * Errors: DS_ERR_INVALID, and the errors of ds_batch_run for the plan's own run. */
+ds_status ds_batch_autotune(ds_batch* batch, int max_candidates, int* chosen, int* n_tried, float* ms_tried);
+/* The batch's current multi-RHS schedule (any output pointer may be NULL). */
+ds_status ds_batch_schedule(const ds_batch* batch, int* tensor_bulk, int* block_rhs, int* sort_lambda,
+                            double* lowp_switch);
 ds_status ds_batch_destroy(ds_batch* batch);
 /* One-shot form: create, run once, destroy. */
 ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,

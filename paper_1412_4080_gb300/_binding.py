@@ -98,6 +98,9 @@ def lib():
             L.ds_batch_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]
             L.ds_batch_layout.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 4
+            L.ds_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)]
+            L.ds_batch_schedule.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 3 + [ctypes.POINTER(ctypes.c_double)]
             L.ds_batch_destroy.argtypes = [vp]
             L.ds_solve_batch.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp, vp]
             L.ds_server_create.argtypes = [vp, ctypes.c_size_t, i64, i64, ctypes.c_int, ctypes.POINTER(vp)]
@@ -282,6 +285,20 @@ def ds_batch_layout(batch):
     _check(lib().ds_batch_layout(batch.h, *[ctypes.byref(x) for x in v]), "ds_batch_layout")
     return {"multi_rhs_blocks": v[0].value, "multi_rhs_teams": v[1].value, "multi_rhs_team_size": v[2].value,
             "single_problems": v[3].value}
+
+
+def ds_batch_autotune(batch, max_candidates=8):
+    ms = (ctypes.c_float * max_candidates)()
+    c, n = ctypes.c_int(), ctypes.c_int()
+    _check(lib().ds_batch_autotune(batch.h, max_candidates, ctypes.byref(c), ctypes.byref(n), ms), "ds_batch_autotune")
+    return {"chosen": c.value, "ms": [ms[k] for k in range(n.value)], "schedule": ds_batch_schedule(batch)}
+
+
+def ds_batch_schedule(batch):
+    v = [ctypes.c_int() for _ in range(3)]
+    sw = ctypes.c_double()
+    _check(lib().ds_batch_schedule(batch.h, *[ctypes.byref(x) for x in v], ctypes.byref(sw)), "ds_batch_schedule")
+    return {"tensor_bulk": v[0].value, "block_rhs": v[1].value, "sort_lambda": v[2].value, "lowp_switch": sw.value}
 
 
 def ds_batch_destroy(batch):

@@ -118,19 +118,25 @@ ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host);
 ds_status dict_lowp(ds_ctx* ctx, ds_dict* dict, int kind);
 
 // Right-hand sides sharing a dictionary, solved together (ds_mrhs.cu): a block
-// is up to 64 problems of one FP32 Lasso dictionary, y_r at Y + r * N and x_r at
-// X + r * K; inst / r0 locate the block in the caller's batch.
+// is up to 64 problems of one FP32 Lasso instance; problem r of the block is the
+// instance's right-hand side ridx[r] (y at Y + ridx[r] * N, x at X + ridx[r] * K).
+constexpr int kMrhsMaxR = 64;
 struct MrhsBlock {
     const ds_dict* dict;
-    const void* Y;
+    const void* Y;  // the instance's right-hand sides (column 0)
     int R;
-    void* X;
-    int inst, r0;
+    void* X;        // the instance's solutions (column 0)
+    int inst;
+    int ridx[kMrhsMaxR];
+};
+// Schedule choices of a plan (the batch autotuner varies them).
+struct MrhsCfg {
+    int allow_tc;      // bulk phase on the tensor cores when the dictionary has a BF16 copy
+    double lo_switch;  // > 0: overrides the bulk-to-FP32 switch level
 };
 struct MrhsPlan;
-constexpr int kMrhsMaxR = 64;
 ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, const ds_options* opt,
-                           const double* fista_dev, int fista_n, MrhsPlan** out);
+                           const double* fista_dev, int fista_n, const MrhsCfg& cfg, MrhsPlan** out);
 const MrhsBlock* mrhs_plan_blocks(const MrhsPlan* M, int* n);  // in job order
 double* mrhs_plan_lambdas(MrhsPlan* M);                        // pinned, [job][kMrhsMaxR]
 const DevResult* mrhs_plan_results(const MrhsPlan* M);         // pinned, [job][kMrhsMaxR]

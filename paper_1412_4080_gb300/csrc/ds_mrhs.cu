@@ -103,10 +103,11 @@ struct MrhsP {
     const double* colnorm;
     double fmax, L, gamma, eps_test, tol;
     int alg, test, dynamic, max_iter, lambda_rel;
-    const float* Y;          // problem r: y at Y + r * N
+    const float* Y;          // problem r: y at Y + ridx[r] * N
     int R;                   // problems in the block (<= kMR)
+    int ridx[kMR];           // the instance's right-hand side of each problem
     const double* lambdas;   // R entries (device)
-    float* X;                // problem r: x at X + r * K
+    float* X;                // problem r: x at X + ridx[r] * K
     DevResult* res;          // R entries
     const double* fista;
     int fista_n;
@@ -742,7 +743,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
     if (tid == 0) S.n_slots = R;
     for (size_t k = (size_t)b * kThreads + tid; k < (size_t)kMR * npad; k += (size_t)G * kThreads) {
         const int r = (int)(k / npad), n = (int)(k - (size_t)r * npad);
-        W.Yt[k] = (r < R && n < N) ? P.Y[(size_t)r * N + n] : 0.f;
+        W.Yt[k] = (r < R && n < N) ? P.Y[(size_t)P.ridx[r] * N + n] : 0.f;
         W.Th[k] = 0.f;
         W.Dst[k] = 0.f;
         W.wb[0][k] = FF{0.f, 0.f};
@@ -754,7 +755,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
     }
     for (size_t k = (size_t)b * kThreads + tid; k < (size_t)R * K; k += (size_t)G * kThreads) {
         const int r = (int)(k / K);
-        P.X[(size_t)r * K + (k - (size_t)r * K)] = 0.f;
+        P.X[(size_t)P.ridx[r] * K + (k - (size_t)r * K)] = 0.f;
     }
     for (int k = b * kThreads + tid; k < 2 * ((K + kMTA - 1) / kMTA); k += G * kThreads) W.tilecnt[k] = 0;
     if (b == 0 && tid < 3) W.ctr[tid] = 0;
@@ -765,7 +766,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
             for (int k = 0; k < kMSynRows / 32; k++) {
                 const int n = rt * kMSynRows + 32 * k + lane;
                 if (n < N) {
-                    const float v = P.Y[(size_t)r * N + n];
+                    const float v = P.Y[(size_t)P.ridx[r] * N + n];
                     acc.add(v, v);
                 }
             }
@@ -1253,7 +1254,7 @@ __device__ __noinline__ bool mrhs_body(const MrhsP& P, const int b, const int G,
                         const int r = lane + 32 * h;
                         if ((dm >> r) & 1) {
                             const FF x = ((m >> r) & 1) ? ldcg_x(W.xb[xi] + (size_t)i * kMR + r) : FF{0.f, 0.f};
-                            P.X[(size_t)r * K + i] = it_round(x);
+                            P.X[(size_t)P.ridx[r] * K + i] = it_round(x);
                         }
                     }
                 }
@@ -1754,7 +1755,7 @@ struct MrhsPlan {
 };
 
 ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, const ds_options* opt,
-                           const double* fista_dev, int fista_n, MrhsPlan** out)
+                           const double* fista_dev, int fista_n, const MrhsCfg& cfg, MrhsPlan** out)
 {
     *out = nullptr;
     if (n_blocks < 1) return DS_ERR_INVALID;
@@ -1851,12 +1852,13 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
         P.lambda_rel = opt->lambda_rel;
         P.Y = reinterpret_cast<const float*>(B.Y);
         P.R = B.R;
+        for (int r = 0; r < kMR; r++) P.ridx[r] = r < B.R ? B.ridx[r] : 0;
         P.lambdas = M->dlam + (size_t)jj * kMR;
         P.X = reinterpret_cast<float*>(B.X);
         P.res = M->dres + (size_t)jj * kMR;
         P.fista = fista_dev;
         P.fista_n = fista_n;
-        if (dc->lo_kind == 1) {
+        if (dc->lo_kind == 1 && cfg.allow_tc) {
             // precision variant with a BF16 copy: bulk iterations on the tensor cores
             P.Dlo = reinterpret_cast<const uint16_t*>(dc->Dlo);
             P.ld_lo = (int)dc->ld_lo;
@@ -1870,7 +1872,8 @@ ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, c
                 const double k = 17.0 * (P.npad / 16) + (P.npad / kTcRows) + 2.0;
                 P.gamma_tc = 1.01 * k * u / (1.0 - k * u);
             }
-            P.lo_switch = opt->lowp_switch > 0.0 ? opt->lowp_switch : std::max(1e-3, opt->tol_gap_rel);
+            P.lo_switch = cfg.lo_switch > 0.0 ? cfg.lo_switch
+                                              : (opt->lowp_switch > 0.0 ? opt->lowp_switch : std::max(1e-3, opt->tol_gap_rel));
             use_tc = 1;
         }
         M->hjobs[jj] = P;

@@ -230,6 +230,18 @@ struct ds_batch {
     float ms_last;
     ds::MrhsPlan* mplan;  // right-hand sides solved together (FP32 Lasso instances)
     double* mfista;       // the multi-rhs plan's copy of the FISTA table
+    // schedule of the multi-rhs blocks (chosen by ds_batch_autotune) and the creation
+    // arguments, kept so that the autotuner can build the other candidates
+    struct Cfg {
+        int allow_tc = 1;       // tensor-core bulk phase on BF16 copies
+        int block_r = 64;       // right-hand sides per block
+        int sort_lambda = 0;    // group right-hand sides of similar lambda into a block
+        double lo_switch = 0;   // > 0: bulk-to-FP32 switch level
+    } cfg;
+    std::vector<const ds_dict*> c_dicts;
+    std::vector<const void*> c_Y;
+    std::vector<void*> c_X;
+    ds_options c_opt;
 };
 
 namespace ds {
@@ -239,6 +251,7 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
                                 const int* n_rhs, const double* const* lambdas, const ds_options* opt,
                                 void* const* X_out, ds_batch* B)
 {
+    const ds_batch::Cfg& cfg = B->cfg;
     if (opt->alg == DS_FISTA) {
         ds_status fs = ctx_fista_table(ctx, opt->max_iter);
         if (fs != DS_OK) return fs;
@@ -250,14 +263,22 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
         multi[i] = sizeof(T) == 4 && opt->batch_multi_rhs && !dicts[i]->is_group && opt->test <= DS_DOME &&
                    n_rhs[i] >= 2;
         if (!multi[i]) continue;
-        for (int r0 = 0; r0 < n_rhs[i]; r0 += kMrhsMaxR) {
+        // right-hand sides in order, or sorted by lambda (similar iteration counts and
+        // screened sets in a block: a tighter union list and fewer idle slots)
+        std::vector<int> ord(n_rhs[i]);
+        std::iota(ord.begin(), ord.end(), 0);
+        if (cfg.sort_lambda)
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return lambdas[i][a] < lambdas[i][b]; });
+        const int br = std::max(2, std::min(kMrhsMaxR, cfg.block_r));
+        for (int r0 = 0; r0 < n_rhs[i]; r0 += br) {
             MrhsBlock blk;
+            std::memset(&blk, 0, sizeof(blk));
             blk.dict = dicts[i];
-            blk.R = std::min(kMrhsMaxR, n_rhs[i] - r0);
-            blk.Y = reinterpret_cast<const char*>(Y[i]) + sizeof(T) * dicts[i]->N * r0;
-            blk.X = reinterpret_cast<char*>(X_out[i]) + sizeof(T) * dicts[i]->K * r0;
+            blk.R = std::min(br, n_rhs[i] - r0);
+            blk.Y = Y[i];
+            blk.X = X_out[i];
             blk.inst = i;
-            blk.r0 = r0;
+            for (int r = 0; r < blk.R; r++) blk.ridx[r] = ord[r0 + r];
             blocks.push_back(blk);
         }
     }
@@ -288,7 +309,10 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
                 cudaSuccess)
                 return DS_ERR_CUDA;
         }
-        ms = mrhs_plan_create(ctx, (int)blocks.size(), blocks.data(), opt, mf, ctx->fista_n, &B->mplan);
+        MrhsCfg mc;
+        mc.allow_tc = cfg.allow_tc;
+        mc.lo_switch = cfg.lo_switch;
+        ms = mrhs_plan_create(ctx, (int)blocks.size(), blocks.data(), opt, mf, ctx->fista_n, mc, &B->mplan);
         if (ms != DS_OK) return ms;
     }
     int n_jobs = 0, maxN = 1, maxK = 1, maxG = 1, maxgs = 1;
@@ -464,8 +488,9 @@ ds_status ds_batch_destroy(ds_batch* B)
     return DS_OK;
 }
 
-ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
-                          const double* const* lambdas, const ds_options* opt, void* const* X_out, ds_batch** out)
+static ds_status batch_create_cfg(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y,
+                                  const int* n_rhs, const double* const* lambdas, const ds_options* opt,
+                                  void* const* X_out, const ds_batch::Cfg& cfg, ds_batch** out)
 {
     if (!ctx || n < 1 || !dicts || !Y || !n_rhs || !lambdas || !opt || !X_out || !out) return DS_ERR_INVALID;
     *out = nullptr;
@@ -487,6 +512,11 @@ ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const
     if (!B) return DS_ERR_OOM;
     B->ctx = ctx;
     B->dtype = dtype;
+    B->cfg = cfg;
+    B->c_dicts.assign(dicts, dicts + n);
+    B->c_Y.assign(Y, Y + n);
+    B->c_X.assign(X_out, X_out + n);
+    B->c_opt = *opt;
     ds_status st = dtype == DS_FP32 ? ds::batch_create_t<float>(ctx, n, dicts, Y, n_rhs, lambdas, opt, X_out, B)
                                     : ds::batch_create_t<double>(ctx, n, dicts, Y, n_rhs, lambdas, opt, X_out, B);
     if (st != DS_OK) {
@@ -516,6 +546,12 @@ ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const
     return DS_OK;
 }
 
+ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
+                          const double* const* lambdas, const ds_options* opt, void* const* X_out, ds_batch** out)
+{
+    return batch_create_cfg(ctx, n, dicts, Y, n_rhs, lambdas, opt, X_out, ds_batch::Cfg(), out);
+}
+
 ds_status ds_batch_run(ds_batch* B, ds_result* res)
 {
     if (!B || !res) return DS_ERR_INVALID;
@@ -526,7 +562,7 @@ ds_status ds_batch_run(ds_batch* B, ds_result* res)
     if (B->mplan) {
         double* ml = ds::mrhs_plan_lambdas(B->mplan);
         for (int j = 0; j < nb; j++)
-            for (int r = 0; r < blks[j].R; r++) ml[(size_t)j * ds::kMrhsMaxR + r] = B->lam_src[blks[j].inst][blks[j].r0 + r];
+            for (int r = 0; r < blks[j].R; r++) ml[(size_t)j * ds::kMrhsMaxR + r] = B->lam_src[blks[j].inst][blks[j].ridx[r]];
     }
     cudaStream_t s = B->ctx->stream;
     cudaEventRecord(B->ctx->ev0, s);
@@ -554,7 +590,7 @@ ds_status ds_batch_run(ds_batch* B, ds_result* res)
         for (int j = 0; j < nb; j++)
             for (int r = 0; r < blks[j].R; r++) {
                 const ds::DevResult& q = mr[(size_t)j * ds::kMrhsMaxR + r];
-                ds_result& o = res[base[blks[j].inst] + blks[j].r0 + r];
+                ds_result& o = res[base[blks[j].inst] + blks[j].ridx[r]];
                 o.iters = q.iters;
                 o.status = q.status;
                 o.n_active = q.n_active;
@@ -601,6 +637,91 @@ ds_status ds_batch_info(const ds_batch* B, int* uses_graph, int* teams, int* tea
                                        : reinterpret_cast<ds::TeamArgs<double>*>(B->args)->team_size;
     if (team_size) *team_size = ts;
     if (teams) *teams = B->grid / ts;
+    return DS_OK;
+}
+
+ds_status ds_batch_schedule(const ds_batch* B, int* tensor_bulk, int* block_rhs, int* sort_lambda, double* lowp_switch)
+{
+    if (!B) return DS_ERR_INVALID;
+    if (tensor_bulk) *tensor_bulk = B->cfg.allow_tc;
+    if (block_rhs) *block_rhs = B->cfg.block_r;
+    if (sort_lambda) *sort_lambda = B->cfg.sort_lambda;
+    if (lowp_switch) *lowp_switch = B->cfg.lo_switch;
+    return DS_OK;
+}
+
+ds_status ds_batch_autotune(ds_batch* B, int max_candidates, int* chosen, int* n_tried, float* ms_tried)
+{
+    if (!B || max_candidates < 1) return DS_ERR_INVALID;
+    const int n = (int)B->c_dicts.size();
+    bool bf16 = false, multi = false;
+    int total = 0;
+    for (int i = 0; i < n; i++) {
+        total += B->n_rhs[i];
+        bf16 |= B->c_dicts[i]->lo_kind == 1;
+        multi |= B->n_rhs[i] >= 2;
+    }
+    // candidate schedules of the multi-rhs blocks; the plan's own schedule first
+    std::vector<ds_batch::Cfg> cands;
+    auto add = [&](int tc, int br, int sorted, double sw) {
+        ds_batch::Cfg c;
+        c.allow_tc = tc;
+        c.block_r = br;
+        c.sort_lambda = sorted;
+        c.lo_switch = sw;
+        for (const auto& d : cands)
+            if (d.allow_tc == c.allow_tc && d.block_r == c.block_r && d.sort_lambda == c.sort_lambda &&
+                d.lo_switch == c.lo_switch)
+                return;
+        cands.push_back(c);
+    };
+    cands.push_back(B->cfg);
+    if (multi) {
+        add(B->cfg.allow_tc, 32, 1, B->cfg.lo_switch);
+        if (bf16) {
+            add(1 - B->cfg.allow_tc, B->cfg.block_r, B->cfg.sort_lambda, B->cfg.lo_switch);
+            add(1 - B->cfg.allow_tc, 32, 1, B->cfg.lo_switch);
+            add(1, 64, 0, 1e-2);
+        }
+    }
+    if ((int)cands.size() > max_candidates) cands.resize(max_candidates);
+    std::vector<ds_result> res(total);
+    int best = 0;
+    float best_ms = 0.f;
+    ds_batch* best_plan = nullptr;  // a candidate that beats the plan's own schedule
+    for (int k = 0; k < (int)cands.size(); k++) {
+        ds_batch* P = B;
+        if (k > 0) {
+            ds_status st = batch_create_cfg(B->ctx, n, B->c_dicts.data(), B->c_Y.data(), B->n_rhs.data(),
+                                            B->lam_src.data(), &B->c_opt, B->c_X.data(), cands[k], &P);
+            if (st != DS_OK) {
+                if (ms_tried) ms_tried[k] = -1.f;
+                continue;
+            }
+        }
+        ds_status st = ds_batch_run(P, res.data());
+        const float ms = st == DS_OK ? P->ms_last : -1.f;
+        if (ms_tried) ms_tried[k] = ms;
+        const bool better = st == DS_OK && (k == 0 || (ms > 0.f && ms < best_ms));
+        if (better) {
+            best = k;
+            best_ms = ms;
+            if (k > 0) {
+                if (best_plan) ds_batch_destroy(best_plan);
+                best_plan = P;
+                P = nullptr;
+            }
+        }
+        if (k > 0 && P) ds_batch_destroy(P);
+        if (k == 0 && st != DS_OK) return st;
+    }
+    if (best_plan) {
+        // the batch takes over the faster plan; its old internals go with the candidate
+        std::swap(*B, *best_plan);
+        ds_batch_destroy(best_plan);
+    }
+    if (chosen) *chosen = best;
+    if (n_tried) *n_tried = (int)cands.size();
     return DS_OK;
 }
 

@@ -230,3 +230,34 @@ def test_multi_rhs_tensor_core_bulk_matches_fp32(ctx, test):
     finally:
         ds.ds_dict_destroy(d32)
         ds.ds_dict_destroy(dbf)
+
+
+def test_autotuner_keeps_a_valid_schedule_and_lambda_sorted_blocks_map_back(ctx):
+    # two candidates: the default schedule, then blocks of 32 grouped by lambda; the last tuning
+    # run (the lambda-sorted one) leaves its solutions in X, which must map back to the caller's
+    # right-hand sides; the kept schedule must then solve the batch again
+    insts = [_instance(307, 300, 1500, 70)]
+    D, Y, lam = insts[0]
+    d = ds.ds_dict_create(ctx, _dev_dict(D))
+    try:
+        Yt = torch.from_numpy(Y).to("cuda", torch.float32)
+        X = torch.full((70, 1500), float("nan"), device="cuda")
+        opt = ds.ds_options_default(test="dst3", tol_gap_rel=0.0, max_iter=200, lambda_rel=1)
+        plan = ds.ds_batch_create(ctx, [d], [Yt], [lam.copy()], opt, [X])
+        tune = ds.ds_batch_autotune(plan, max_candidates=2)
+        assert len(tune["ms"]) == 2 and all(m > 0 for m in tune["ms"]), tune
+        assert tune["chosen"] in (0, 1)
+        for r in range(0, 70, 5):
+            x1 = torch.zeros(1500, device="cuda")
+            one = ds.ds_solve(ctx, d, Yt[r].contiguous(), float(lam[r]), opt, x1)
+            a = x1.double().cpu().numpy()
+            b = X[r].double().cpu().numpy()
+            assert one["iters"] == 200
+            assert np.abs(a - b).max() <= 1e-5 * max(np.abs(a).max(), 1e-30), r
+        X.fill_(float("nan"))
+        res = ds.ds_batch_run(plan)
+        assert all(rr["iters"] == 200 for rr in res)
+        assert torch.isfinite(X).all()
+        ds.ds_batch_destroy(plan)
+    finally:
+        ds.ds_dict_destroy(d)
