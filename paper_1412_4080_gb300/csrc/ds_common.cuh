@@ -59,7 +59,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks
     if (threadIdx.x == 0) {
         int ok = 1;
         target += nblocks;
-        __threadfence();
+        // the release add orders every write of the CTA (made before the block
+        // barrier above) before the arrival; no separate fence is needed
         red_release_add_u32(&bar->count, 1u);
         unsigned long long spins = 0;
         while (ld_acquire_u32(&bar->count) < target) {

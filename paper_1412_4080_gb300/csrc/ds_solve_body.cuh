@@ -20,6 +20,7 @@ constexpr int kThreads = 512;
 constexpr int kMaxG = 160;  // CTAs of the persistent grid (one per SM) handled by the fixed reductions
 constexpr int kU = 4;         // 16-byte vectors per lane per GEMV item
 constexpr int kRowTile = 32;  // rows per synthesis tile
+constexpr int kSyn = 8;       // dictionary loads in flight per lane in the synthesis
 
 // Iterates (x, u) and per-CTA partial sums: float-float pairs for FP32
 // dictionaries, doubles for FP64 ones.
@@ -86,6 +87,7 @@ struct SolveP {
     int hist_rows;
     Ws<T> ws;
     int RA, nchunk, npad;
+    int syn_cap;          // nonzero-list entries the dynamic shared buffer holds (multiple of 16)
     double* colnorm_w;    // non-null: the kernel computes ||d_i|| here (and fmax) in its first pass
     const double* fista;  // FISTA table: (coefficient (l_{t-1} - 1) / l_t, l_t) for t = 1..fista_n
     int fista_n;
@@ -375,6 +377,43 @@ __device__ __noinline__ void gemv_lowp(const void* Dlo, int ld_lo, const float* 
     }
 }
 
+// ---- correlation from the FP32 dictionary: item (atom, 512-row chunk), IPW items
+// of kU 16-byte vectors per lane in flight per warp (the loads of a round are all
+// issued before the first product), theta read from shared memory; each item's
+// dot product is summed in the same order whatever IPW is.
+template <int IPW>
+__device__ __noinline__ void gemv_f32(const float* D, int ld, const float* th_s, float* zpart, const int* cols_s,
+                                      int natoms, int nchunk, int lane, int warp, int nw)
+{
+    const int ldv = ld / 4;
+    const float4* thv = reinterpret_cast<const float4*>(th_s);
+    const int nitems = natoms * nchunk;
+    for (int j0 = warp * IPW; j0 < nitems; j0 += nw * IPW) {
+        float4 dv[IPW][kU];
+        int aa[IPW], cc[IPW];
+#pragma unroll
+        for (int q = 0; q < IPW; q++) {
+            const int j = j0 + q < nitems ? j0 + q : j0;
+            aa[q] = j / nchunk;
+            cc[q] = j - aa[q] * nchunk;
+            const float4* col = reinterpret_cast<const float4*>(D + (size_t)cols_s[aa[q]] * ld);
+#pragma unroll
+            for (int k = 0; k < kU; k++) {
+                const int v = cc[q] * (32 * kU) + k * 32 + lane;
+                dv[q][k] = (j0 + q < nitems && v < ldv) ? __ldg(col + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < IPW; q++) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < kU; k++) s = vdot(dv[q][k], thv[cc[q] * (32 * kU) + k * 32 + lane], s);
+            s = warp_sum(s);
+            if (lane == 0 && j0 + q < nitems) zpart[aa[q] * nchunk + cc[q]] = s;
+        }
+    }
+}
+
 // Column slice [p_lo, p_hi) of the active list owned by CTA b, balanced in atoms
 // and cut at group boundaries.  Returns the atom offset of p_lo.
 template <typename T>
@@ -441,6 +480,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     __shared__ int s_ired[32];
     __shared__ int s_pref[1025];
     __shared__ int s_alo_s[kThreads];
+    __shared__ int s_kg[kMaxG], s_ka[kMaxG];
     __shared__ double s_red[2][kThreads / 32][kRowTile];
     __shared__ double s_sc[16];
     __shared__ int s_si[16];
@@ -448,6 +488,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kThreads / 32;
     const Ws<T>& W = P.ws;
+    auto xbuf = [&](int i) -> X* { return i == 0 ? W.xc[0] : (i == 1 ? W.xc[1] : W.xn); };
+    auto ubuf = [&](int i) -> X* { return i == 0 ? W.uc[0] : (i == 1 ? W.uc[1] : W.un); };
 
     const int N = P.N, K = P.K, ld = P.ld, nG = P.nG;
     const int ldv = ld / EV;
@@ -816,6 +858,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         if (!ok) return false;
 
         int nA_g = nG, nA_a = K;  // sizes of the list `cur` refers to
+        // roles of the three iterate buffers: iC the compacted current iterate (list `cur`), iN the
+        // new values at the same positions (prox output, next momentum point), iS a spare
+        int iC = 0, iN = 2, iS = 1;
         // scalar state, meaningful in thread 0 (the values every thread needs go through s_sc)
         double &alpha = S_.alpha, &beta = S_.beta, &mu_nom = S_.mu_nom, &R2n = S_.R2n, &R2s_last = S_.R2s_last;
         double &rad = S_.rad, &lf = S_.lf, &s_unc = S_.s_unc, &sqrt_beta = S_.sqrt_beta;
@@ -841,100 +886,147 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         for (;; t++) {
             // ======================================== (A) scatter + synthesis
             {
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                const int nxt = cur ^ 1;
+                // the previous test's per-CTA counts: kept groups and atoms, nonzero-list lengths
+                int cnz = 0;
+                if (tid < G) {
+                    cnz = __ldcg(W.c_nz + tid);
+                    s_alo_s[tid] = __ldcg(W.s_alo + tid);
+                    s_kg[tid] = __ldcg(W.c_kg + tid);
+                    s_ka[tid] = __ldcg(W.c_ka + tid);
+                }
                 // directory of the per-CTA nonzero lists (exclusive prefix of their lengths)
-                const int cnz = tid < G ? __ldcg(W.c_nz + tid) : 0;
-                if (tid < G) s_alo_s[tid] = __ldcg(W.s_alo + tid);
                 int totE;
                 const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
                 if (tid < G) s_pref[tid] = exE;
                 if (tid == 0) s_pref[G] = totE;
                 if (warp == 0) {
-                    int gv[kMaxG / 32], av[kMaxG / 32];
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) {
-                        const int k = lane + 32 * q;
-                        gv[q] = k < b ? __ldcg(W.c_kg + k) : 0;
-                        av[q] = k < b ? __ldcg(W.c_ka + k) : 0;
+                    int g0 = 0, a0 = 0, gt = 0;
+                    for (int k = lane; k < G; k += 32) {
+                        const int g = s_kg[k];
+                        gt += g;
+                        if (k < b) { g0 += g; a0 += s_ka[k]; }
                     }
-                    int g0 = 0, a0 = 0;
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) { g0 += gv[q]; a0 += av[q]; }
                     g0 = warp_sum(g0);
                     a0 = warp_sum(a0);
-                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; }
+                    gt = warp_sum(gt);
+                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; s_si[10] = gt; }
                 }
                 __syncthreads();
-                // compaction (Algorithm 3: D_t = D_{t-1} Id, Xbar_t = Id X_t): kept groups move to
-                // their new positions; groups and atoms are counted in one packed scan
-                int gb = s_si[1], ab = s_si[2];
-                for (int base = p_lo; base < p_hi; base += kThreads) {
-                    const int p = base + tid;
-                    const bool valid = p < p_hi;
-                    int k = 0, lo_a = 0, sz = 0;
-                    if (valid) {
-                        k = __ldcg(W.keep + p);
-                        lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                        sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
-                    }
-                    int tot;
-                    const int pre = block_exclusive_scan(k ? ((1 << 16) | sz) : 0, s_tmp, &tot);
-                    if (k) {
-                        const int ng = gb + (pre >> 16), na = ab + (pre & 0xffff);
-                        W.act[nxt][ng] = __ldcg(W.act[cur] + p);
-                        if (P.is_group) W.aoff[nxt][ng] = na;
-                        for (int q = 0; q < sz; q++) {
-                            W.xc[nxt][na + q] = ldcg_x(W.xn + lo_a + q);
-                            W.uc[nxt][na + q] = ldcg_x(W.un + lo_a + q);
+                if (s_si[10] != nA_g) {
+                    // compaction (Algorithm 3: D_t = D_{t-1} Id, Xbar_t = Id X_t): kept groups move to
+                    // their new positions; groups and atoms are counted in one packed scan
+                    int p_lo, p_hi, a_lo;
+                    cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
+                    const int nxt = cur ^ 1;
+                    X* const xS = xbuf(iS);
+                    X* const uS = ubuf(iS);
+                    const X* const xN = xbuf(iN);
+                    const X* const uN = ubuf(iN);
+                    int gb = s_si[1], ab = s_si[2];
+                    for (int base = p_lo; base < p_hi; base += kThreads) {
+                        const int p = base + tid;
+                        const bool valid = p < p_hi;
+                        int k = 0, lo_a = 0, sz = 0;
+                        if (valid) {
+                            k = __ldcg(W.keep + p);
+                            lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
+                            sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
                         }
+                        int tot;
+                        const int pre = block_exclusive_scan(k ? ((1 << 16) | sz) : 0, s_tmp, &tot);
+                        if (k) {
+                            const int ng = gb + (pre >> 16), na = ab + (pre & 0xffff);
+                            W.act[nxt][ng] = __ldcg(W.act[cur] + p);
+                            if (P.is_group) W.aoff[nxt][ng] = na;
+                            for (int q = 0; q < sz; q++) {
+                                xS[na + q] = ldcg_x(xN + lo_a + q);
+                                uS[na + q] = ldcg_x(uN + lo_a + q);
+                            }
+                        }
+                        gb += tot >> 16;
+                        ab += tot & 0xffff;
                     }
-                    gb += tot >> 16;
-                    ab += tot & 0xffff;
+                    if (b == G - 1 && tid == 0 && P.is_group) W.aoff[nxt][gb] = ab;
+                    cur = nxt;
+                    const int tmp = iC;
+                    iC = iS;
+                    iS = tmp;
+                } else {
+                    // nothing screened: the new iterates already sit at their positions, so the
+                    // buffers swap roles instead of being copied
+                    const int tmp = iC;
+                    iC = iN;
+                    iN = tmp;
                 }
-                if (b == G - 1 && tid == 0 && P.is_group) W.aoff[nxt][gb] = ab;
 
-                // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists
+                // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists of
+                // all CTAs, staged in shared memory (the correlation's buffer is free here)
                 const int E = s_pref[G];
                 if (tid == 0) cols_synth += E;
                 Acc pa_, pb_, pr_;
                 const int ntiles = (N + kRowTile - 1) / kRowTile;
+                const int cap = P.syn_cap;
+                int* const sl_col = reinterpret_cast<int*>(smem_raw);
+                X* const sl_u = reinterpret_cast<X*>(smem_raw + (size_t)cap * sizeof(int));
+                X* const sl_x = sl_u + cap;
+                const bool one = E <= cap;
+                if (one && b < ntiles) {
+                    for (int e = tid; e < E; e += kThreads) {
+                        int lo = 0, hi = G;  // largest k with s_pref[k] <= e
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (s_pref[mid] <= e) lo = mid;
+                            else hi = mid;
+                        }
+                        const int idx = s_alo_s[lo] + (e - s_pref[lo]);
+                        sl_col[e] = __ldcg(W.nz_col + idx);
+                        sl_u[e] = ldcg_x(W.nz_u + idx);
+                        sl_x[e] = ldcg_x(W.nz_x + idx);
+                    }
+                    __syncthreads();
+                }
                 for (int tile = b; tile < ntiles; tile += G) {
                     const int r = tile * kRowTile + lane;
                     const bool rv = r < N;
+                    const T yv = (warp == 0 && rv) ? P.y[r] : T(0);
                     // compensated accumulation: theta = D u - y is a small difference of two
                     // large vectors, so the sum is carried to twice the working precision
                     typename Dot2<T>::type au, ax;
-                    for (int e0 = warp; e0 < E; e0 += nw * 4) {
-                        int cols[4];
-                        X uv[4], xv[4];
-#pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            const int e = e0 + q * nw;
-                            cols[q] = -1;
-                            uv[q] = it_zero((X*)nullptr);
-                            xv[q] = it_zero((X*)nullptr);
-                            if (e < E) {
-                                int lo = 0, hi = G;  // largest k with s_pref[k] <= e
+                    for (int c0 = 0; c0 < E; c0 += cap) {
+                        const int ce = min(cap, E - c0);
+                        if (!one) {
+                            __syncthreads();
+                            for (int e = tid; e < ce; e += kThreads) {
+                                const int ee = c0 + e;
+                                int lo = 0, hi = G;
                                 while (hi - lo > 1) {
                                     const int mid = (lo + hi) >> 1;
-                                    if (s_pref[mid] <= e) lo = mid;
+                                    if (s_pref[mid] <= ee) lo = mid;
                                     else hi = mid;
                                 }
-                                const int idx = s_alo_s[lo] + (e - s_pref[lo]);
-                                cols[q] = __ldcg(W.nz_col + idx);
-                                uv[q] = ldcg_x(W.nz_u + idx);
-                                xv[q] = ldcg_x(W.nz_x + idx);
+                                const int idx = s_alo_s[lo] + (ee - s_pref[lo]);
+                                sl_col[e] = __ldcg(W.nz_col + idx);
+                                sl_u[e] = ldcg_x(W.nz_u + idx);
+                                sl_x[e] = ldcg_x(W.nz_x + idx);
                             }
+                            __syncthreads();
                         }
-                        T dv[4];
+                        // warp w sums entries w, w + nw, w + 2 nw, ... (kSyn loads in flight a lane)
+                        for (int e0 = warp; e0 < ce; e0 += nw * kSyn) {
+                            T dv[kSyn];
 #pragma unroll
-                        for (int q = 0; q < 4; q++) dv[q] = (cols[q] >= 0 && rv) ? __ldg(P.D + (size_t)cols[q] * ld + r) : T(0);
+                            for (int q = 0; q < kSyn; q++) {
+                                const int e = e0 + q * nw;
+                                dv[q] = (e < ce && rv) ? __ldg(P.D + (size_t)sl_col[e] * ld + r) : T(0);
+                            }
 #pragma unroll
-                        for (int q = 0; q < 4; q++) {
-                            syn_add(au, dv[q], uv[q]);
-                            syn_add(ax, dv[q], xv[q]);
+                            for (int q = 0; q < kSyn; q++) {
+                                const int e = e0 + q * nw;
+                                if (e < ce) {
+                                    syn_add(au, dv[q], sl_u[e]);
+                                    syn_add(ax, dv[q], sl_x[e]);
+                                }
+                            }
                         }
                     }
                     acc_store(&s_red[0][warp][lane], au);
@@ -947,7 +1039,6 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             acc_merge(wx, &s_red[1][k][lane]);
                         }
                         if (rv) {
-                            const T yv = P.y[r];
                             const T th = (T)theta_from(wu, yv);
                             W.theta[r] = th;
                             pa_.add(th, yv);
@@ -963,16 +1054,36 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     pr_ = acc_warp_reduce(pr_);
                     if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
                 }
-                cur = nxt;
             }
             ok = grid_sync(bar, G, gen);
             if (!ok) return false;
 
             // ================================ (B) stop test, correlation + prox
             {
-                // warp 0 reduces the partials in a fixed order; lane 0 evaluates the gap of
-                // iteration t-1 and the stopping rule
+                // warps 1.. stage theta_t in shared memory while warp 0 reduces the partials in
+                // a fixed order and lane 0 evaluates the gap of iteration t-1 and the stopping rule
+                if (warp > 0) {
+                    constexpr int kST = kThreads - 32, kSU = 8;
+                    for (int r0 = tid - 32; r0 < P.npad; r0 += kSU * kST) {
+                        T v[kSU];
+#pragma unroll
+                        for (int q = 0; q < kSU; q++) {
+                            const int r = r0 + q * kST;
+                            v[q] = r < N ? __ldcg(W.theta + r) : T(0);
+                        }
+#pragma unroll
+                        for (int q = 0; q < kSU; q++) {
+                            const int r = r0 + q * kST;
+                            if (r < P.npad) th_s[r] = v[q];
+                        }
+                    }
+                }
                 if (warp == 0) {
+                    // FISTA coefficient of this iteration, fetched ahead of the reductions
+                    const int tf_pre = t - t0;
+                    const bool tab_pre = !ista && tf_pre >= 1 && tf_pre <= P.fista_n;
+                    const double bt_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1)) : 0.0;
+                    const double lf_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1) + 1) : 0.0;
                     // every load of the per-CTA partials is issued before any is combined
                     X va[kMaxG / 32], vb[kMaxG / 32], vr[kMaxG / 32], vl[kMaxG / 32];
                     int ig[kMaxG / 32], ia[kMaxG / 32], ix[kMaxG / 32];
@@ -1044,7 +1155,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
                             // read from the table (the sequence depends on t only)
                             const int tf = t - t0;  // index in the current FISTA sequence
-                            if (tf <= P.fista_n) {
+                            if (tf == tf_pre && tab_pre) {
+                                bt = bt_pre;
+                                lf = lf_pre;
+                            } else if (tf <= P.fista_n) {
                                 bt = P.fista[2 * (tf - 1)];
                                 lf = P.fista[2 * (tf - 1) + 1];
                             } else {
@@ -1069,8 +1183,6 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     if (lowB) cols_lowp += nA_a;
                 }
 
-                // stage theta_t
-                for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? __ldcg(W.theta + r) : T(0);
                 int p_lo, p_hi, a_lo;
                 cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 T mloc = T(0);
@@ -1120,32 +1232,36 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             gemv_lowp<2, 8>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
                                             reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
                     }
-                    for (int j0 = warp * 2; j0 < nitems; j0 += nw * 2) {
-                        const int j1 = j0 + 1;
-                        const bool h1 = j1 < nitems;
-                        const int a0 = j0 / nchunk, c0 = j0 - a0 * nchunk;
-                        const int a1 = h1 ? j1 / nchunk : a0, c1 = h1 ? j1 - a1 * nchunk : c0;
-                        const V* col0 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a0] * ld);
-                        const V* col1 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a1] * ld);
-                        V d0[kU], d1[kU];
+                    if constexpr (sizeof(T) == 4) {
+                        if (!lowB) gemv_f32<4>(P.D, ld, th_s, zpart, cols_s, natoms, nchunk, lane, warp, nw);
+                    } else {
+                        for (int j0 = warp * 2; j0 < nitems; j0 += nw * 2) {
+                            const int j1 = j0 + 1;
+                            const bool h1 = j1 < nitems;
+                            const int a0 = j0 / nchunk, c0 = j0 - a0 * nchunk;
+                            const int a1 = h1 ? j1 / nchunk : a0, c1 = h1 ? j1 - a1 * nchunk : c0;
+                            const V* col0 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a0] * ld);
+                            const V* col1 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a1] * ld);
+                            V d0[kU], d1[kU];
 #pragma unroll
-                        for (int k = 0; k < kU; k++) {
-                            const int v0 = c0 * (32 * kU) + k * 32 + lane;
-                            const int v1 = c1 * (32 * kU) + k * 32 + lane;
-                            d0[k] = v0 < ldv ? __ldg(col0 + v0) : v4zero((V*)nullptr);
-                            d1[k] = (h1 && v1 < ldv) ? __ldg(col1 + v1) : v4zero((V*)nullptr);
-                        }
-                        T s0 = T(0), s1 = T(0);
+                            for (int k = 0; k < kU; k++) {
+                                const int v0 = c0 * (32 * kU) + k * 32 + lane;
+                                const int v1 = c1 * (32 * kU) + k * 32 + lane;
+                                d0[k] = v0 < ldv ? __ldg(col0 + v0) : v4zero((V*)nullptr);
+                                d1[k] = (h1 && v1 < ldv) ? __ldg(col1 + v1) : v4zero((V*)nullptr);
+                            }
+                            T s0 = T(0), s1 = T(0);
 #pragma unroll
-                        for (int k = 0; k < kU; k++) {
-                            s0 = vdot(d0[k], thv[c0 * (32 * kU) + k * 32 + lane], s0);
-                            s1 = vdot(d1[k], thv[c1 * (32 * kU) + k * 32 + lane], s1);
-                        }
-                        s0 = warp_sum(s0);
-                        s1 = warp_sum(s1);
-                        if (lane == 0) {
-                            zpart[a0 * nchunk + c0] = s0;
-                            if (h1) zpart[a1 * nchunk + c1] = s1;
+                            for (int k = 0; k < kU; k++) {
+                                s0 = vdot(d0[k], thv[c0 * (32 * kU) + k * 32 + lane], s0);
+                                s1 = vdot(d1[k], thv[c1 * (32 * kU) + k * 32 + lane], s1);
+                            }
+                            s0 = warp_sum(s0);
+                            s1 = warp_sum(s1);
+                            if (lane == 0) {
+                                zpart[a0 * nchunk + c0] = s0;
+                                if (h1) zpart[a1 * nchunk + c1] = s1;
+                            }
                         }
                     }
                     __syncthreads();
@@ -1155,7 +1271,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         for (int c = 0; c < nchunk; c++) z += zpart[a * nchunk + c];
                         if (!P.is_group) {
                             const int ap = abase + a;
-                            W.xn[ap] = it_soft(it_grad_step(ldcg_x(W.uc[cur] + ap), z, invL), thrX);
+                            xbuf(iN)[ap] = it_soft(it_grad_step(ldcg_x(ubuf(iC) + ap), z, invL), thrX);
                             mloc = fmax(mloc, fabs(z));
                         } else {
                             zpart[a * nchunk] = z;
@@ -1170,7 +1286,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             Acc zq, vq;
                             for (int i = 0; i < sz; i++) {
                                 const T z = zpart[(off - abase + i) * nchunk];
-                                const X v = it_grad_step(ldcg_x(W.uc[cur] + off + i), z, invL);
+                                const X v = it_grad_step(ldcg_x(ubuf(iC) + off + i), z, invL);
                                 zq.add(z, z);
                                 acc_sq(vq, v);
                             }
@@ -1180,7 +1296,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0, (X*)nullptr);
                             for (int i = 0; i < sz; i++) {
                                 const T z = zpart[(off - abase + i) * nchunk];
-                                W.xn[off + i] = it_scale(it_grad_step(ldcg_x(W.uc[cur] + off + i), z, invL), f);
+                                xbuf(iN)[off + i] = it_scale(it_grad_step(ldcg_x(ubuf(iC) + off + i), z, invL), f);
                             }
                             // rounded up so that the FP32 max stays an upper bound of the FP64 value
                             mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
@@ -1204,6 +1320,28 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 
             // ===================================== (C) screening + momentum
             {
+                // atoms are handled by warps 1.. (kCT per round); warp 0 evaluates Lemma 8
+                // while they fetch the first round's inputs (Lasso)
+                constexpr int kCT = kThreads - 32;
+                int p_lo, p_hi, a_lo;
+                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
+                int pf_gid = 0;
+                double pf_t0 = 0.0, pf_t1 = 0.0, pf_t2 = 0.0;
+                X pf_x = it_zero((X*)nullptr), pf_xo = it_zero((X*)nullptr);
+                const bool pf = !P.is_group && warp > 0 && p_lo + tid - 32 < p_hi;
+                if (pf) {
+                    const int p = p_lo + tid - 32;
+                    pf_gid = __ldcg(W.act[cur] + p);
+                    pf_x = ldcg_x(xbuf(iN) + p);
+                    pf_xo = ldcg_x(xbuf(iC) + p);
+                    if (dyn_test && P.test == 3) {
+                        pf_t0 = colnorm[pf_gid];
+                        pf_t1 = __ldcg(W.b + pf_gid);
+                        pf_t2 = __ldcg(W.tv + pf_gid);
+                    } else if (dyn_test) {
+                        pf_t0 = __ldcg(W.thr + pf_gid);
+                    }
+                }
                 if (warp == 0) {
                     T mv[kMaxG / 32];
 #pragma unroll
@@ -1236,41 +1374,40 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 __syncthreads();
                 const double radB = s_sc[8], RsB = s_sc[9];
                 const X btX = it_cast(s_sc[10], (X*)nullptr);
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 int nz_base = 0, kg = 0, ka = 0, nzx = 0;
                 Acc l1;
-                for (int base = p_lo; base < p_hi; base += kThreads) {
-                    const int p = base + tid;
-                    const bool valid = p < p_hi;
+                for (int base = p_lo; base < p_hi; base += kCT) {
+                    const int p = base + tid - 32;
+                    const bool valid = warp > 0 && p < p_hi;
+                    const bool use_pf = pf && base == p_lo;  // inputs fetched above
                     int cnt = 0, lo_a = 0, sz = 0, gid = 0;
                     X x1 = it_zero((X*)nullptr), u1 = it_zero((X*)nullptr);  // Lasso: the atom's values
                     if (valid) {
-                        gid = __ldcg(W.act[cur] + p);
+                        gid = use_pf ? pf_gid : __ldcg(W.act[cur] + p);
                         lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                         sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
                         bool kill = false;
                         if (dyn_test) {
                             if (P.test == 3) {
                                 // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
-                                const double ni = colnorm[gid];
-                                const double dc0 = __ldcg(W.b + gid) / (lam * ni);
-                                const double tt = __ldcg(W.tv + gid) / (ni * nstar);
+                                const double ni = use_pf ? pf_t0 : colnorm[gid];
+                                const double dc0 = (use_pf ? pf_t1 : __ldcg(W.b + gid)) / (lam * ni);
+                                const double tt = (use_pf ? pf_t2 : __ldcg(W.tv + gid)) / (ni * nstar);
                                 const double up = dome_max(dc0, tt, psi_dome, RsB);
                                 const double dn = dome_max(-dc0, -tt, psi_dome, RsB);
                                 kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
                             } else {
-                                kill = __ldcg(W.thr + gid) - radB > P.eps_test;
+                                kill = (use_pf ? pf_t0 : __ldcg(W.thr + gid)) - radB > P.eps_test;
                             }
                         }
                         W.keep[p] = !kill;
                         if (!kill) {
                             Acc gq;
                             for (int q = 0; q < sz; q++) {
-                                const X xv = ldcg_x(W.xn + lo_a + q);
-                                const X xo = ldcg_x(W.xc[cur] + lo_a + q);
+                                const X xv = use_pf ? pf_x : ldcg_x(xbuf(iN) + lo_a + q);
+                                const X xo = use_pf ? pf_xo : ldcg_x(xbuf(iC) + lo_a + q);
                                 const X uv = ista ? xv : it_momentum(xv, xo, btX);
-                                W.un[lo_a + q] = uv;
+                                ubuf(iN)[lo_a + q] = uv;
                                 x1 = xv;
                                 u1 = uv;
                                 cnt += (it_nz(uv) || it_nz(xv));
@@ -1293,8 +1430,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     } else if (cnt) {
                         int e = a_lo + nz_base + pos;
                         for (int q = 0; q < sz; q++) {
-                            const X xv = ldcg_x(W.xn + lo_a + q);
-                            const X uv = ldcg_x(W.un + lo_a + q);
+                            const X xv = ldcg_x(xbuf(iN) + lo_a + q);
+                            const X uv = ldcg_x(ubuf(iN) + lo_a + q);
                             if (it_nz(uv) || it_nz(xv)) {
                                 W.nz_col[e] = P.is_group ? P.goff[gid] + q : gid;
                                 W.nz_u[e] = uv;
@@ -1343,7 +1480,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 int lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                 int c0 = P.is_group ? P.goff[gid] : gid;
                 int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
-                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(W.xc[cur] + lo_a + q));
+                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(xbuf(iC) + lo_a + q));
             }
             if (b == 0 && tid == 0) {
                 R->iters = iters;
@@ -1467,6 +1604,7 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.RA = g.RA;
     P.nchunk = g.nchunk;
     P.npad = g.npad;
+    P.syn_cap = (int)(g.smem / (sizeof(int) + 2 * sizeof(typename IterT<T>::type))) & ~15;
     P.hist = nullptr;
     P.hist_rows = 0;
     P.x0 = nullptr;
