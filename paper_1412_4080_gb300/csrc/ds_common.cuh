@@ -71,7 +71,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks
             }
             if (spins > 2048) __nanosleep(spins > 65536 ? 512 : 64);
         }
-        if (ld_volatile_u32(&bar->err)) ok = 0;
+        // a CTA that gave up raised `err` and left; the others notice it while they poll at
+        // their next barrier, so a completed wait needs no further load here
         s_ok = ok;
     }
     __syncthreads();

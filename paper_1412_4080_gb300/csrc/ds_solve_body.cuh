@@ -39,6 +39,8 @@ struct Ws {
     double* nvec;
     int* act[2];
     int* aoff[2];
+    // FP32 dictionaries, sphere tests: (threshold - eps) rounded down to FP32, in list order
+    float* thrc[2];
     // iterates carry about twice the dictionary's precision: in plain FP32,
     // u - z/L would quantise z to multiples of L ulp(x), a KKT floor near 1e-6
     X* xc[2];
@@ -481,6 +483,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     __shared__ int s_pref[1025];
     __shared__ int s_alo_s[kThreads];
     __shared__ int s_kg[kMaxG], s_ka[kMaxG];
+    __shared__ float s_radf;
     __shared__ double s_red[2][kThreads / 32][kRowTile];
     __shared__ double s_sc[16];
     __shared__ int s_si[16];
@@ -743,6 +746,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         const X thrX = it_cast(thrL, (X*)nullptr);
         const bool ista = P.alg == 0;
         const bool dyn_test = P.dynamic && P.test != 0;
+        const bool sphere = P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5;
+        // FP32 dictionaries run the sphere tests in FP32: thresholds rounded down, radius rounded up
+        const bool f32_sphere = sizeof(T) == 4 && sphere;
+        // absolute slack on the radius^2 for the FP64 rounding of its terms (all of size <= ||y||^2/lambda^2)
+        const double rad2_slack = 1e-14 * yy / (lam * lam);
 
         // ------------------------------------------------ (C0) initial state
         int cur = 0;
@@ -798,6 +806,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         double sg = P.is_group ? P.spec[p] : colnorm[p];
                         th = (wg - sqrt(q)) / sg;
                         W.thr[p] = th;
+                        if (sizeof(T) == 4) W.thrc[cur][p] = __double2float_rd(th - P.eps_test);
                     }
                     bool kill = false;
                     if (stat) {
@@ -900,19 +909,22 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 if (tid < G) s_pref[tid] = exE;
                 if (tid == 0) s_pref[G] = totE;
                 if (warp == 0) {
-                    int g0 = 0, a0 = 0, gt = 0;
+                    int g0 = 0, a0 = 0, gt = 0, at = 0;
                     for (int k = lane; k < G; k += 32) {
-                        const int g = s_kg[k];
+                        const int g = s_kg[k], a = s_ka[k];
                         gt += g;
-                        if (k < b) { g0 += g; a0 += s_ka[k]; }
+                        at += a;
+                        if (k < b) { g0 += g; a0 += a; }
                     }
                     g0 = warp_sum(g0);
                     a0 = warp_sum(a0);
                     gt = warp_sum(gt);
-                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; s_si[10] = gt; }
+                    at = warp_sum(at);
+                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; s_si[10] = gt; s_si[11] = at; }
                 }
                 __syncthreads();
-                if (s_si[10] != nA_g) {
+                const int newA_g = s_si[10], newA_a = s_si[11];
+                if (newA_g != nA_g) {
                     // compaction (Algorithm 3: D_t = D_{t-1} Id, Xbar_t = Id X_t): kept groups move to
                     // their new positions; groups and atoms are counted in one packed scan
                     int p_lo, p_hi, a_lo;
@@ -938,6 +950,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const int ng = gb + (pre >> 16), na = ab + (pre & 0xffff);
                             W.act[nxt][ng] = __ldcg(W.act[cur] + p);
                             if (P.is_group) W.aoff[nxt][ng] = na;
+                            if (f32_sphere) W.thrc[nxt][ng] = __ldcg(W.thrc[cur] + p);
                             for (int q = 0; q < sz; q++) {
                                 xS[na + q] = ldcg_x(xN + lo_a + q);
                                 uS[na + q] = ldcg_x(uN + lo_a + q);
@@ -958,6 +971,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     iC = iN;
                     iN = tmp;
                 }
+                nA_g = newA_g;
+                nA_a = newA_a;
 
                 // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists of
                 // all CTAs, staged in shared memory (the correlation's buffer is free here)
@@ -1060,9 +1075,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 
             // ================================ (B) stop test, correlation + prox
             {
-                // warps 1.. stage theta_t in shared memory while warp 0 reduces the partials in
-                // a fixed order and lane 0 evaluates the gap of iteration t-1 and the stopping rule
+                // warps 1.. stage theta_t in shared memory (and, Lasso, the first round's columns)
+                // while warp 0 reduces the partials in a fixed order and lane 0 evaluates the gap
+                // of iteration t-1 and the stopping rule
+                int p_lo, p_hi, a_lo;
+                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
+                const int n0 = P.is_group ? 0 : min(p_hi - p_lo, P.RA);
+                const X u_pf = tid < n0 ? ldcg_x(ubuf(iC) + p_lo + tid) : it_zero((X*)nullptr);
                 if (warp > 0) {
+                    for (int a = tid - 32; a < n0; a += kThreads - 32) cols_s[a] = __ldcg(W.act[cur] + p_lo + a);
                     constexpr int kST = kThreads - 32, kSU = 8;
                     for (int r0 = tid - 32; r0 < P.npad; r0 += kSU * kST) {
                         T v[kSU];
@@ -1086,7 +1107,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     const double lf_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1) + 1) : 0.0;
                     // every load of the per-CTA partials is issued before any is combined
                     X va[kMaxG / 32], vb[kMaxG / 32], vr[kMaxG / 32], vl[kMaxG / 32];
-                    int ig[kMaxG / 32], ia[kMaxG / 32], ix[kMaxG / 32];
+                    int ix[kMaxG / 32];
 #pragma unroll
                     for (int q = 0; q < kMaxG / 32; q++) {
                         const int k = lane + 32 * q;
@@ -1095,19 +1116,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         vb[q] = in ? ldcg_x(W.p_b + k) : it_zero((X*)nullptr);
                         vr[q] = in ? ldcg_x(W.p_r + k) : it_zero((X*)nullptr);
                         vl[q] = in ? ldcg_x(W.p_l1 + k) : it_zero((X*)nullptr);
-                        ig[q] = in ? __ldcg(W.c_kg + k) : 0;
-                        ia[q] = in ? __ldcg(W.c_ka + k) : 0;
                         ix[q] = in ? __ldcg(W.c_nnzx + k) : 0;
                     }
                     const double a_ = part_sum_regs<kMaxG / 32>(va);
                     const double b_ = part_sum_regs<kMaxG / 32>(vb);
                     const double r_ = part_sum_regs<kMaxG / 32>(vr);
                     const double l1 = part_sum_regs<kMaxG / 32>(vl);
-                    int ng = 0, na = 0, nx = 0;
+                    int nx = 0;
 #pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) { ng += ig[q]; na += ia[q]; nx += ix[q]; }
-                    ng = warp_sum(ng);
-                    na = warp_sum(na);
+                    for (int q = 0; q < kMaxG / 32; q++) nx += ix[q];
                     nx = warp_sum(nx);
                     if (lane == 0) {
                         int stop = 0;
@@ -1138,7 +1155,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                             if (record && b == 0 && t - 1 <= P.hist_rows) {
                                 double* h = P.hist + (size_t)(t - 2) * 6;
-                                h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
+                                h[0] = (double)nA_a; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
                             }
                             stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
                             // an owner shutting down (the server) may end the solve early, every 16 iterations
@@ -1168,13 +1185,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                         }
                         s_sc[10] = bt;
-                        s_si[3] = (int)ng; s_si[4] = (int)na; s_si[5] = (int)nx; s_si[6] = stop;
+                        s_si[5] = (int)nx; s_si[6] = stop;
                         s_si[9] = low;
                     }
                 }
                 __syncthreads();
-                nA_g = s_si[3];
-                nA_a = s_si[4];
                 nnz_last = s_si[5];
                 lowB = s_si[9] != 0;
                 if (s_si[6]) break;
@@ -1183,8 +1198,6 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     if (lowB) cols_lowp += nA_a;
                 }
 
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 T mloc = T(0);
                 const V* thv = reinterpret_cast<const V*>(th_s);
                 int p = p_lo;
@@ -1212,7 +1225,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     }
                     const int abase = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
                     if (!P.is_group) {
-                        for (int a = tid; a < natoms; a += kThreads) cols_s[a] = __ldcg(W.act[cur] + p + a);
+                        if (p != p_lo)  // the first round's columns were staged above
+                            for (int a = tid; a < natoms; a += kThreads) cols_s[a] = __ldcg(W.act[cur] + p + a);
                     } else {
                         for (int q = p + tid; q < p_end; q += kThreads) {
                             const int g = __ldcg(W.act[cur] + q);
@@ -1271,7 +1285,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         for (int c = 0; c < nchunk; c++) z += zpart[a * nchunk + c];
                         if (!P.is_group) {
                             const int ap = abase + a;
-                            xbuf(iN)[ap] = it_soft(it_grad_step(ldcg_x(ubuf(iC) + ap), z, invL), thrX);
+                            const X uv = (p == p_lo && a == tid) ? u_pf : ldcg_x(ubuf(iC) + ap);
+                            xbuf(iN)[ap] = it_soft(it_grad_step(uv, z, invL), thrX);
                             mloc = fmax(mloc, fabs(z));
                         } else {
                             zpart[a * nchunk] = z;
@@ -1327,6 +1342,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
                 int pf_gid = 0;
                 double pf_t0 = 0.0, pf_t1 = 0.0, pf_t2 = 0.0;
+                float pf_thf = 0.f;
                 X pf_x = it_zero((X*)nullptr), pf_xo = it_zero((X*)nullptr);
                 const bool pf = !P.is_group && warp > 0 && p_lo + tid - 32 < p_hi;
                 if (pf) {
@@ -1334,7 +1350,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     pf_gid = __ldcg(W.act[cur] + p);
                     pf_x = ldcg_x(xbuf(iN) + p);
                     pf_xo = ldcg_x(xbuf(iC) + p);
-                    if (dyn_test && P.test == 3) {
+                    if (dyn_test && f32_sphere) {
+                        pf_thf = __ldcg(W.thrc[cur] + p);
+                    } else if (dyn_test && P.test == 3) {
                         pf_t0 = colnorm[pf_gid];
                         pf_t1 = __ldcg(W.b + pf_gid);
                         pf_t2 = __ldcg(W.tv + pf_gid);
@@ -1342,7 +1360,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         pf_t0 = __ldcg(W.thr + pf_gid);
                     }
                 }
-                if (warp == 0) {
+                if (warp <= 1) {
+                    // warps 0 and 1 reduce the same per-CTA maxima in the same order
                     T mv[kMaxG / 32];
 #pragma unroll
                     for (int j = 0; j < kMaxG / 32; j++) mv[j] = lane + 32 * j < G ? __ldcg(W.p_m + lane + 32 * j) : T(0);
@@ -1352,27 +1371,46 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, o));
                     const double m_nom = (double)mf;
-                    if (lane == 0) {
-                        // Lemma 8 with the nominal max |z| (for the gap) and with a rigorous upper
-                        // bound on it given the FP rounding of z (for the screening radius)
-                        // (copy: |z_i - zlo_i| <= ||d_i - dlo_i|| ||theta|| + the FP32 rounding of dlo_i^T theta)
+                    if (warp == 1 && lane == 0) {
+                        // Lemma 8 with the nominal max |z|: the dual point of the gap (a stopping rule)
+                        mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
+                        R2n = fmax(fma(mu_nom, fma(mu_nom, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
+                    }
+                    if (warp == 0 && lane == 0) {
+                        // Lemma 8 with a rigorous upper bound on max |z| given the FP rounding of z, for
+                        // the screening radius (copy: |z_i - zlo_i| <= ||d_i - dlo_i|| ||theta|| + the FP32
+                        // rounding of dlo_i^T theta).  Any |mu| <= 1 / max|z| gives a feasible dual point, so
+                        // the clip uses 1 / m_up rounded down.
                         const double m_up = m_nom + (lowB ? P.emax + P.gamma_lo * (fmax_d + P.emax) : P.gamma * fmax_d) *
                                                         sqrt_beta;
-                        mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
-                        const double mu_s = (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) ? copysign(fast_rcp(m_up), s_unc) : s_unc;
+                        double mu_s = s_unc;
+                        if (sizeof(T) == 8) {
+                            if (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) mu_s = copysign(fast_rcp(m_up), s_unc);
+                        } else if (m_up > 0.0) {
+                            const float mf_up = __double2float_ru(m_up);
+                            const double r_dn = mf_up < 3.0e38f ? (double)__frcp_rd(mf_up) : 0.0;
+                            if (fabs(s_unc) > r_dn) mu_s = copysign(r_dn, s_unc);
+                        }
                         // R^2 = ||y/lambda - mu theta||^2
-                        R2n = fmax(fma(mu_nom, fma(mu_nom, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
                         const double R2s = fmax(fma(mu_s, fma(mu_s, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
                         R2s_last = R2s;
-                        // radii rounded up a little: a larger radius only screens less
-                        const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
-                        rad = (P.test == 2 || P.test == 5) ? fast_sqrt(fmax(R2s - delta * delta, 0.0)) * (1.0 + 1e-13) : Rs;
-                        s_sc[8] = rad;
-                        s_sc[9] = Rs;
+                        if (f32_sphere) {
+                            // radius of the sphere test (DST3/DGST3: sqrt(R^2 - delta^2)), rounded up to FP32
+                            const double r2 = ((P.test == 2 || P.test == 5) ? R2s - delta * delta : R2s) + rad2_slack;
+                            s_radf = __fsqrt_ru(__double2float_ru(fmax(r2, 0.0)));
+                        }
+                        if (!f32_sphere || record) {
+                            // radii rounded up a little: a larger radius only screens less
+                            const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
+                            rad = (P.test == 2 || P.test == 5) ? fast_sqrt(fmax(R2s - delta * delta, 0.0)) * (1.0 + 1e-13) : Rs;
+                            s_sc[8] = rad;
+                            s_sc[9] = Rs;
+                        }
                     }
                 }
                 __syncthreads();
                 const double radB = s_sc[8], RsB = s_sc[9];
+                const float radF = s_radf;
                 const X btX = it_cast(s_sc[10], (X*)nullptr);
                 int nz_base = 0, kg = 0, ka = 0, nzx = 0;
                 Acc l1;
@@ -1396,6 +1434,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 const double up = dome_max(dc0, tt, psi_dome, RsB);
                                 const double dn = dome_max(-dc0, -tt, psi_dome, RsB);
                                 kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
+                            } else if (f32_sphere) {
+                                kill = (use_pf ? pf_thf : __ldcg(W.thrc[cur] + p)) > radF;
                             } else {
                                 kill = (use_pf ? pf_t0 : __ldcg(W.thr + gid)) - radB > P.eps_test;
                             }
@@ -1547,6 +1587,7 @@ inline size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_la
     for (int k = 0; k < 2; k++) {
         w->act[k] = bp.take<int>(nG);
         w->aoff[k] = bp.take<int>(nG + 1);
+        w->thrc[k] = bp.take<float>(nG);
         w->xc[k] = bp.take<X>(K);
         w->uc[k] = bp.take<X>(K);
     }
