@@ -21,6 +21,7 @@ constexpr int kMaxG = 160;  // CTAs of the persistent grid (one per SM) handled 
 constexpr int kU = 4;         // 16-byte vectors per lane per GEMV item
 constexpr int kRowTile = 32;  // rows per synthesis tile
 constexpr int kSyn = 8;       // dictionary loads in flight per lane in the synthesis
+constexpr int kSpec = 2;      // entries of every nonzero list fetched with its length
 
 // Iterates (x, u) and per-CTA partial sums: float-float pairs for FP32
 // dictionaries, doubles for FP64 ones.
@@ -45,13 +46,11 @@ struct Ws {
     // u - z/L would quantise z to multiples of L ulp(x), a KKT floor near 1e-6
     X* xc[2];
     X* uc[2];
-    X* xn;
-    X* un;
     int* keep;
     int* nz_col;
     X* nz_u;
     X* nz_x;
-    int* s_alo;
+    int* nz_t;  // test data of the entry's group: FP32 threshold bits (FP32 sphere tests) or group id
     int* c_kg;
     int* c_ka;
     int* c_nz;
@@ -416,42 +415,6 @@ __device__ __noinline__ void gemv_f32(const float* D, int ld, const float* th_s,
     }
 }
 
-// Column slice [p_lo, p_hi) of the active list owned by CTA b, balanced in atoms
-// and cut at group boundaries.  Returns the atom offset of p_lo.
-template <typename T>
-__device__ __forceinline__ void cta_slice(const SolveP<T>& P, const int* aoff, int nA_g, int nA_a, int b, int G,
-                                          int* p_lo, int* p_hi, int* a_lo)
-{
-    __shared__ int s_slice[3];
-    if (threadIdx.x == 0) {
-        if (!P.is_group) {
-            s_slice[0] = (int)((long long)b * nA_g / G);
-            s_slice[1] = (int)((long long)(b + 1) * nA_g / G);
-            s_slice[2] = s_slice[0];
-        } else {
-            int bounds[2];
-            for (int k = 0; k < 2; k++) {
-                long long target = (long long)(b + k) * nA_a / G;
-                int lo = 0, hi = nA_g;  // first p with aoff[p] >= target
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (__ldcg(aoff + mid) < target) lo = mid + 1;
-                    else hi = mid;
-                }
-                bounds[k] = lo;
-            }
-            s_slice[0] = bounds[0];
-            s_slice[1] = bounds[1];
-            s_slice[2] = bounds[0] < nA_g ? __ldcg(aoff + bounds[0]) : nA_a;
-        }
-    }
-    __syncthreads();
-    *p_lo = s_slice[0];
-    *p_hi = s_slice[1];
-    *a_lo = s_slice[2];
-    __syncthreads();
-}
-
 // --------------------------------------------------------------- the kernel
 
 // Per-solve scalar state that only thread 0 of each CTA updates, kept in shared
@@ -460,6 +423,35 @@ struct ScalarState {
     double alpha, beta, mu_nom, R2n, R2s_last, rad, lf, s_unc, sqrt_beta, gap, primal, best_gap;
     long long cols_corr, cols_synth, cols_lowp;
     int iters, since_best, low, t0;  // t0: iteration at which the current FISTA sequence started
+};
+
+// Asynchronous copies global -> shared (cp.async): prefetched values wait in shared memory, not
+// in registers, until the thread that issued them reads them after pf_wait().
+__device__ __forceinline__ void pf4(void* s, const void* g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void pf8(void* s, const void* g)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void pf_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// The first kSpec entries of one CTA's nonzero list, fetched with its length.
+template <typename X>
+struct __align__(8) SpecSlot {
+    X u[kSpec], x[kSpec];
+    int col[kSpec], t[kSpec];
+};
+
+// CTA-uniform constants of a launch and of its current lambda, kept in shared memory:
+// the persistent kernel needs its registers for the loads it keeps in flight.
+template <typename T>
+struct SolveK {
+    double fmax_d, nn, nty, wstar2;
+    double lam, inv_lam, yy_l2, psi, coef, delta, nstar, psi_dome, thrL, rad2_slack;
+    T invL;
+    typename IterT<T>::type thrX;
 };
 
 // One solve (or lambda path) by a team of G CTAs (rank b) that synchronise on
@@ -482,17 +474,26 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     __shared__ int s_ired[32];
     __shared__ int s_pref[1025];
     __shared__ int s_alo_s[kThreads];
-    __shared__ int s_kg[kMaxG], s_ka[kMaxG];
+    __shared__ int s_kg[kMaxG];
     __shared__ float s_radf;
     __shared__ double s_red[2][kThreads / 32][kRowTile];
     __shared__ double s_sc[16];
     __shared__ int s_si[16];
     __shared__ ScalarState S_;
+    __shared__ SolveK<T> C_;
+    // per-thread prefetch slots (cp.async): two ints, a float and two iterate values
+    __shared__ int s_pf_i0[kThreads], s_pf_i1[kThreads];
+    __shared__ float s_pf_f0[kThreads];
+    __shared__ __align__(8) X s_pf_u[kThreads];
+    __shared__ __align__(8) X s_pf_x[kThreads];
+    // the nonzero-list heads of every CTA, in the synthesis merge buffer (free when they are read)
+    static_assert(sizeof(SpecSlot<X>) * kMaxG <= sizeof(double) * 2 * (kThreads / 32) * kRowTile, "spec slots");
+    SpecSlot<X>* const s_spec = reinterpret_cast<SpecSlot<X>*>(&s_red[0][0][0]);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kThreads / 32;
     const Ws<T>& W = P.ws;
-    auto xbuf = [&](int i) -> X* { return i == 0 ? W.xc[0] : (i == 1 ? W.xc[1] : W.xn); };
-    auto ubuf = [&](int i) -> X* { return i == 0 ? W.uc[0] : (i == 1 ? W.uc[1] : W.un); };
+    auto xbuf = [&](int i) -> X* { return i == 0 ? W.xc[0] : W.xc[1]; };
+    auto ubuf = [&](int i) -> X* { return i == 0 ? W.uc[0] : W.uc[1]; };
 
     const int N = P.N, K = P.K, ld = P.ld, nG = P.nG;
     const int ldv = ld / EV;
@@ -558,14 +559,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     if (!ok) return false;
     // column norms computed above: their maximum bounds the GEMV rounding (Lasso)
     const double* colnorm = P.colnorm_w ? P.colnorm_w : P.colnorm;
-    double fmax_d = P.fmax;
+    if (tid == 0) C_.fmax_d = P.fmax;
+    const double& fmax_d = C_.fmax_d;
     if (P.colnorm_w) {
         if (warp == 0) {
             const double m = warp_max_fixed(W.p_cn, G, lane);
             if (lane == 0) s_sc[11] = m * (1.0 + 1e-12);
         }
         __syncthreads();
-        fmax_d = s_sc[11];
+        if (tid == 0) C_.fmax_d = s_sc[11];
     }
 
     // --------------------------------- P0b: lambda_* (Sec. 2.2.2 / eq. gstar)
@@ -627,16 +629,16 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         }
         __syncthreads();
     }
-    const double lstar = s_sc[0];
-    const int star = s_si[0];
-    const double yy = s_sc[1];
+    const double& lstar = s_sc[0];
+    const int& star = s_si[0];
+    const double& yy = s_sc[1];
     if (P.n_lambda == 0) {  // lambda_max query only
         if (b == 0 && tid == 0) { P.res[0].lambda_max = lstar; P.res[0].status = kDevOk; }
         return true;
     }
 
     const bool need_n = P.test == 2 || P.test == 3 || P.test == 5;  // DST3, DOME, DGST3
-    double nn = 0.0, nty = 0.0, wstar2 = 1.0;
+    if (tid == 0) { C_.nn = 0.0; C_.nty = 0.0; C_.wstar2 = 1.0; }
     if (need_n && lstar > 0.0) {
         // ---------------- n = D_{g*} D_{g*}^T y / lambda_*  (Lemma 6; Lasso: n = d_*)
         const int c0 = P.is_group ? P.goff[star] : star;
@@ -677,16 +679,16 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             for (int r = tid; r < P.npad; r += kThreads) th_s[r] = r < N ? (T)__ldcg(W.nvec + r) : T(0);
         }
         __syncthreads();
-        nn = s_sc[2];
-        {
+        if (tid == 0) {
+            C_.nn = s_sc[2];
             double q = 0.0;
             for (int i = c0; i < c1; i++) {
                 double v = __ldcg(W.b + i);
                 q += v * v;
             }
-            nty = q / lstar;  // n^T y = ||D_{g*}^T y||^2 / lambda_*
+            C_.nty = q / lstar;  // n^T y = ||D_{g*}^T y||^2 / lambda_*
+            if (P.is_group) C_.wstar2 = P.w[star] * P.w[star];
         }
-        if (P.is_group) wstar2 = P.w[star] * P.w[star];
         // ---------------- tv = D^T n (compensated)
         for (int i = gwarp; i < K; i += total_warps) {
             const V* col = reinterpret_cast<const V*>(P.D + (size_t)i * ld);
@@ -720,9 +722,56 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         if (!ok) return false;
     }
 
+    // fixed slice of every CTA for the whole launch: groups [slice(k), slice(k+1)), cut at group
+    // boundaries and balanced in atoms; s_alo_s[k] = its first atom (start of its nonzero list)
+    auto slice_start = [&](int k) -> int {
+        if (k >= G) return nG;
+        if (!P.is_group) return (int)((long long)k * nG / G);
+        const long long target = (long long)k * K / G;
+        int lo = 0, hi = nG;  // first g with goff[g] >= target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (P.goff[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+    const int g_lo = slice_start(b), g_hi = slice_start(b + 1);
+    const int a_lo0 = P.is_group ? (g_lo < nG ? P.goff[g_lo] : K) : g_lo;
+    const int a_hi0 = P.is_group ? (g_hi < nG ? P.goff[g_hi] : K) : g_hi;
+    for (int k = tid; k < G; k += kThreads) {
+        const int gk = slice_start(k);
+        s_alo_s[k] = P.is_group ? (gk < nG ? P.goff[gk] : K) : gk;
+    }
+    __syncthreads();
+
     // ================================================================ lambdas
+    const double &nn = C_.nn, &nty = C_.nty, &wstar2 = C_.wstar2;
     for (int j = 0; j < P.n_lambda; j++) {
-        const double lam = P.lambda_rel ? P.lambdas[j] * lstar : P.lambdas[j];
+        __syncthreads();  // every thread is done with the previous lambda's constants
+        if (tid == 0) {
+            const double lm = P.lambda_rel ? P.lambdas[j] * lstar : P.lambdas[j];
+            C_.lam = lm;
+            C_.inv_lam = 1.0 / lm;
+            C_.yy_l2 = yy / (lm * lm);
+            C_.psi = lstar / lm - 1.0;
+            // DST3 / DGST3 centre c = y/lam - coef n, offset delta = ||y/lam - c|| (Lemmas 3, 6)
+            C_.coef = need_n && nn > 0.0 ? (nty / lm - wstar2) / nn : 0.0;
+            C_.delta = need_n && nn > 0.0 ? fabs(nty / lm - wstar2) / sqrt(nn) : 0.0;
+            C_.nstar = P.is_group ? 1.0 : colnorm[star];
+            C_.psi_dome = C_.psi / C_.nstar;
+            C_.invL = (T)(1.0 / P.L);
+            C_.thrL = lm / P.L;
+            C_.thrX = it_cast(C_.thrL, (X*)nullptr);
+            // absolute slack on the radius^2 for the FP64 rounding of its terms (all <= ||y||^2/lambda^2)
+            C_.rad2_slack = 1e-14 * yy / (lm * lm);
+        }
+        __syncthreads();
+        const double &lam = C_.lam, &psi = C_.psi, &coef = C_.coef, &delta = C_.delta, &nstar = C_.nstar;
+        const double &psi_dome = C_.psi_dome, &thrL = C_.thrL, &rad2_slack = C_.rad2_slack;
+        const double &inv_lam = C_.inv_lam, &yy_l2 = C_.yy_l2;
+        const T& invL = C_.invL;
+        const X& thrX = C_.thrX;
         T* xout = P.x_out + (size_t)j * P.ldx;
         DevResult* R = P.res + j;
         if (!(lam < lstar)) {
@@ -735,44 +784,19 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             continue;
         }
         const bool record = (j == 0) && P.hist != nullptr;
-        const double psi = lstar / lam - 1.0;
-        // DST3 / DGST3 centre c = y/lam - coef n, offset delta = ||y/lam - c|| (Lemmas 3, 6)
-        const double coef = need_n && nn > 0.0 ? (nty / lam - wstar2) / nn : 0.0;
-        const double delta = need_n && nn > 0.0 ? fabs(nty / lam - wstar2) / sqrt(nn) : 0.0;
-        const double nstar = P.is_group ? 1.0 : colnorm[star];
-        const double psi_dome = psi / nstar;
-        const T invL = (T)(1.0 / P.L);
-        const double thrL = lam / P.L;
-        const X thrX = it_cast(thrL, (X*)nullptr);
         const bool ista = P.alg == 0;
         const bool dyn_test = P.dynamic && P.test != 0;
         const bool sphere = P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5;
         // FP32 dictionaries run the sphere tests in FP32: thresholds rounded down, radius rounded up
         const bool f32_sphere = sizeof(T) == 4 && sphere;
-        // absolute slack on the radius^2 for the FP64 rounding of its terms (all of size <= ||y||^2/lambda^2)
-        const double rad2_slack = 1e-14 * yy / (lam * lam);
 
         // ------------------------------------------------ (C0) initial state
-        int cur = 0;
+        // Every CTA owns the fixed slice [g_lo, g_hi) of the groups for the whole solve and keeps the
+        // survivors of each test compacted inside it: act / aoff / thrc[cur] at g_lo + k (k < n_own) list
+        // the live groups, the iterates of their atoms sit at a_lo0 + (0 .. na_own) of the buffers iO.
+        int cur = 0, iO = 0;
+        int n_own = 0, na_own = 0;
         {
-            int p_lo = (int)((long long)b * nG / G), p_hi = (int)((long long)(b + 1) * nG / G);
-            if (P.is_group) {
-                // cut at group boundaries, balanced in atoms
-                int bounds[2];
-                for (int k = 0; k < 2; k++) {
-                    long long target = (long long)(b + k) * K / G;
-                    int lo = 0, hi = nG;
-                    while (lo < hi) {
-                        int mid = (lo + hi) >> 1;
-                        if (P.goff[mid] < target) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    bounds[k] = lo;
-                }
-                p_lo = bounds[0];
-                p_hi = bounds[1];
-            }
-            const int a_lo = P.is_group ? (p_lo < nG ? P.goff[p_lo] : K) : p_lo;
             // static screening (Algorithm 1): the test at theta = -y, m = lambda_*
             double rad0 = 0.0;
             const bool stat = !P.dynamic && P.test != 0;
@@ -783,37 +807,35 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 R2 = fmax(R2, 0.0);
                 rad0 = (P.test == 2 || P.test == 5) ? sqrt(fmax(R2 - delta * delta, 0.0)) : sqrt(R2);
             }
-            int nz_base = 0, kg = 0, ka = 0;
-            for (int base = p_lo; base < p_hi; base += kThreads) {
-                int p = base + tid;
-                bool valid = p < p_hi;
-                int kept = 0, cnt = 0;
-                int lo_a = 0, hi_a = 0;
+            int nzc = 0;
+            for (int base = g_lo; base < g_hi; base += kThreads) {
+                const int g = base + tid;
+                const bool valid = g < g_hi;
+                int kept = 0, lo_a = 0, hi_a = 0, cnt = 0;
+                float thf = 0.f;
                 if (valid) {
-                    lo_a = P.is_group ? P.goff[p] : p;
-                    hi_a = P.is_group ? P.goff[p + 1] : p + 1;
-                    W.act[cur][p] = p;
-                    if (P.is_group) W.aoff[cur][p] = lo_a;
+                    lo_a = P.is_group ? P.goff[g] : g;
+                    hi_a = P.is_group ? P.goff[g + 1] : g + 1;
                     // threshold of the sphere tests: (w_g - ||(D^T c)_g||) / ||D_g||  (Lemma 7)
                     double th = 0.0;
-                    if (P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5) {
+                    if (sphere) {
                         double q = 0.0;
                         for (int i = lo_a; i < hi_a; i++) {
                             double dtc = __ldcg(W.b + i) / lam - ((P.test == 2 || P.test == 5) ? coef * __ldcg(W.tv + i) : 0.0);
                             q += dtc * dtc;
                         }
-                        double wg = P.is_group ? P.w[p] : 1.0;
-                        double sg = P.is_group ? P.spec[p] : colnorm[p];
+                        double wg = P.is_group ? P.w[g] : 1.0;
+                        double sg = P.is_group ? P.spec[g] : colnorm[g];
                         th = (wg - sqrt(q)) / sg;
-                        W.thr[p] = th;
-                        if (sizeof(T) == 4) W.thrc[cur][p] = __double2float_rd(th - P.eps_test);
+                        W.thr[g] = th;
+                        thf = __double2float_rd(th - P.eps_test);
                     }
                     bool kill = false;
                     if (stat) {
                         if (P.test == 3) {
-                            double ni = colnorm[p];
-                            double dc0 = __ldcg(W.b + p) / (lam * ni);
-                            double tt = __ldcg(W.tv + p) / (ni * nstar);
+                            double ni = colnorm[g];
+                            double dc0 = __ldcg(W.b + g) / (lam * ni);
+                            double tt = __ldcg(W.tv + g) / (ni * nstar);
                             double up = dome_max(dc0, tt, psi_dome, rad0);
                             double dn = dome_max(-dc0, -tt, psi_dome, rad0);
                             kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
@@ -822,54 +844,48 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                     kept = !kill;
-                    W.keep[p] = kept;
-                    for (int i = lo_a; i < hi_a; i++) {
-                        X xv = (P.x0 && kept) ? it_from(P.x0[i], (X*)nullptr) : it_zero((X*)nullptr);
-                        W.xn[i] = xv;
-                        W.un[i] = xv;
-                        cnt += it_nz(xv);
-                    }
-                    kg += kept;
-                    ka += kept ? hi_a - lo_a : 0;
+                    if (kept && P.x0)
+                        for (int i = lo_a; i < hi_a; i++) cnt += P.x0[i] != T(0);
                 }
-                int tot;
-                int pos = block_exclusive_scan(cnt, s_tmp, &tot);
-                if (valid && cnt) {
-                    int e = a_lo + nz_base + pos;
+                int tot, totc;
+                const int pre = block_exclusive_scan(kept ? ((1 << 16) | (hi_a - lo_a)) : 0, s_tmp, &tot);
+                const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
+                if (kept) {
+                    const int ng = n_own + (pre >> 16), na = na_own + (pre & 0xffff);
+                    W.act[0][g_lo + ng] = g;
+                    if (P.is_group) W.aoff[0][g_lo + ng] = a_lo0 + na;
+                    if (f32_sphere) W.thrc[0][g_lo + ng] = thf;
+                    int e = a_lo0 + nzc + pc;
                     for (int i = lo_a; i < hi_a; i++) {
-                        const X xv = W.xn[i];
+                        const X xv = P.x0 ? it_from(P.x0[i], (X*)nullptr) : it_zero((X*)nullptr);
+                        W.xc[0][a_lo0 + na + i - lo_a] = xv;
+                        W.uc[0][a_lo0 + na + i - lo_a] = xv;
                         if (it_nz(xv)) {
+                            // u_0 = x_0: the warm start's nonzeros feed the first synthesis
                             W.nz_col[e] = i;
                             W.nz_u[e] = xv;
                             W.nz_x[e] = xv;
+                            W.nz_t[e] = f32_sphere ? __float_as_int(thf) : g;
                             e++;
                         }
                     }
                 }
-                nz_base += tot;
+                n_own += tot >> 16;
+                na_own += tot & 0xffff;
+                nzc += totc;
             }
-            int tkg, tka, dummy;
-            block_exclusive_scan(kg, s_tmp, &tkg);
-            block_exclusive_scan(ka, s_tmp, &tka);
-            (void)dummy;
             if (tid == 0) {
-                W.s_alo[b] = a_lo;
-                W.c_kg[b] = tkg;
-                W.c_ka[b] = tka;
-                W.c_nz[b] = nz_base;
-                W.c_nnzx[b] = nz_base;
+                W.c_nz[b] = nzc;
+                W.c_kg[b] = n_own;
+                W.c_ka[b] = na_own;
+                W.c_nnzx[b] = nzc;
                 Acc z0;
                 part_put(W.p_l1 + b, z0);
             }
-            if (b == G - 1 && tid == 0 && P.is_group) W.aoff[cur][nG] = K;
         }
         ok = grid_sync(bar, G, gen);
         if (!ok) return false;
 
-        int nA_g = nG, nA_a = K;  // sizes of the list `cur` refers to
-        // roles of the three iterate buffers: iC the compacted current iterate (list `cur`), iN the
-        // new values at the same positions (prox output, next momentum point), iS a spare
-        int iC = 0, iN = 2, iS = 1;
         // scalar state, meaningful in thread 0 (the values every thread needs go through s_sc)
         double &alpha = S_.alpha, &beta = S_.beta, &mu_nom = S_.mu_nom, &R2n = S_.R2n, &R2s_last = S_.R2s_last;
         double &rad = S_.rad, &lf = S_.lf, &s_unc = S_.s_unc, &sqrt_beta = S_.sqrt_beta;
@@ -889,485 +905,42 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         }
         __syncthreads();
         bool lowB = false;  // this iteration's correlation reads the low-precision copy
-        const double inv_lam = 1.0 / lam, yy_l2 = yy * inv_lam * inv_lam;
         int t = 1;
-        long long nnz_last = 0;
         for (;; t++) {
-            // ======================================== (A) scatter + synthesis
+            const bool test_now = dyn_test && t > 1;  // this (A) applies the test of iteration t-1
+            // ============== (A) test of iteration t-1 + synthesis theta_t = D ubar_{t-1} - y, D xbar_{t-1}
             {
-                // the previous test's per-CTA counts: kept groups and atoms, nonzero-list lengths
+                // every CTA's nonzero-list length, with the first kSpec entries fetched in the same trip
                 int cnz = 0;
                 if (tid < G) {
                     cnz = __ldcg(W.c_nz + tid);
-                    s_alo_s[tid] = __ldcg(W.s_alo + tid);
-                    s_kg[tid] = __ldcg(W.c_kg + tid);
-                    s_ka[tid] = __ldcg(W.c_ka + tid);
-                }
-                // directory of the per-CTA nonzero lists (exclusive prefix of their lengths)
-                int totE;
-                const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
-                if (tid < G) s_pref[tid] = exE;
-                if (tid == 0) s_pref[G] = totE;
-                if (warp == 0) {
-                    int g0 = 0, a0 = 0, gt = 0, at = 0;
-                    for (int k = lane; k < G; k += 32) {
-                        const int g = s_kg[k], a = s_ka[k];
-                        gt += g;
-                        at += a;
-                        if (k < b) { g0 += g; a0 += a; }
-                    }
-                    g0 = warp_sum(g0);
-                    a0 = warp_sum(a0);
-                    gt = warp_sum(gt);
-                    at = warp_sum(at);
-                    if (lane == 0) { s_si[1] = g0; s_si[2] = a0; s_si[10] = gt; s_si[11] = at; }
-                }
-                __syncthreads();
-                const int newA_g = s_si[10], newA_a = s_si[11];
-                if (newA_g != nA_g) {
-                    // compaction (Algorithm 3: D_t = D_{t-1} Id, Xbar_t = Id X_t): kept groups move to
-                    // their new positions; groups and atoms are counted in one packed scan
-                    int p_lo, p_hi, a_lo;
-                    cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                    const int nxt = cur ^ 1;
-                    X* const xS = xbuf(iS);
-                    X* const uS = ubuf(iS);
-                    const X* const xN = xbuf(iN);
-                    const X* const uN = ubuf(iN);
-                    int gb = s_si[1], ab = s_si[2];
-                    for (int base = p_lo; base < p_hi; base += kThreads) {
-                        const int p = base + tid;
-                        const bool valid = p < p_hi;
-                        int k = 0, lo_a = 0, sz = 0;
-                        if (valid) {
-                            k = __ldcg(W.keep + p);
-                            lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                            sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
-                        }
-                        int tot;
-                        const int pre = block_exclusive_scan(k ? ((1 << 16) | sz) : 0, s_tmp, &tot);
-                        if (k) {
-                            const int ng = gb + (pre >> 16), na = ab + (pre & 0xffff);
-                            W.act[nxt][ng] = __ldcg(W.act[cur] + p);
-                            if (P.is_group) W.aoff[nxt][ng] = na;
-                            if (f32_sphere) W.thrc[nxt][ng] = __ldcg(W.thrc[cur] + p);
-                            for (int q = 0; q < sz; q++) {
-                                xS[na + q] = ldcg_x(xN + lo_a + q);
-                                uS[na + q] = ldcg_x(uN + lo_a + q);
-                            }
-                        }
-                        gb += tot >> 16;
-                        ab += tot & 0xffff;
-                    }
-                    if (b == G - 1 && tid == 0 && P.is_group) W.aoff[nxt][gb] = ab;
-                    cur = nxt;
-                    const int tmp = iC;
-                    iC = iS;
-                    iS = tmp;
-                } else {
-                    // nothing screened: the new iterates already sit at their positions, so the
-                    // buffers swap roles instead of being copied
-                    const int tmp = iC;
-                    iC = iN;
-                    iN = tmp;
-                }
-                nA_g = newA_g;
-                nA_a = newA_a;
-
-                // synthesis over row tiles: w_u = D ubar, w_x = D xbar, from the nonzero lists of
-                // all CTAs, staged in shared memory (the correlation's buffer is free here)
-                const int E = s_pref[G];
-                if (tid == 0) cols_synth += E;
-                Acc pa_, pb_, pr_;
-                const int ntiles = (N + kRowTile - 1) / kRowTile;
-                const int cap = P.syn_cap;
-                int* const sl_col = reinterpret_cast<int*>(smem_raw);
-                X* const sl_u = reinterpret_cast<X*>(smem_raw + (size_t)cap * sizeof(int));
-                X* const sl_x = sl_u + cap;
-                const bool one = E <= cap;
-                if (one && b < ntiles) {
-                    for (int e = tid; e < E; e += kThreads) {
-                        int lo = 0, hi = G;  // largest k with s_pref[k] <= e
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (s_pref[mid] <= e) lo = mid;
-                            else hi = mid;
-                        }
-                        const int idx = s_alo_s[lo] + (e - s_pref[lo]);
-                        sl_col[e] = __ldcg(W.nz_col + idx);
-                        sl_u[e] = ldcg_x(W.nz_u + idx);
-                        sl_x[e] = ldcg_x(W.nz_x + idx);
-                    }
-                    __syncthreads();
-                }
-                for (int tile = b; tile < ntiles; tile += G) {
-                    const int r = tile * kRowTile + lane;
-                    const bool rv = r < N;
-                    const T yv = (warp == 0 && rv) ? P.y[r] : T(0);
-                    // compensated accumulation: theta = D u - y is a small difference of two
-                    // large vectors, so the sum is carried to twice the working precision
-                    typename Dot2<T>::type au, ax;
-                    for (int c0 = 0; c0 < E; c0 += cap) {
-                        const int ce = min(cap, E - c0);
-                        if (!one) {
-                            __syncthreads();
-                            for (int e = tid; e < ce; e += kThreads) {
-                                const int ee = c0 + e;
-                                int lo = 0, hi = G;
-                                while (hi - lo > 1) {
-                                    const int mid = (lo + hi) >> 1;
-                                    if (s_pref[mid] <= ee) lo = mid;
-                                    else hi = mid;
-                                }
-                                const int idx = s_alo_s[lo] + (ee - s_pref[lo]);
-                                sl_col[e] = __ldcg(W.nz_col + idx);
-                                sl_u[e] = ldcg_x(W.nz_u + idx);
-                                sl_x[e] = ldcg_x(W.nz_x + idx);
-                            }
-                            __syncthreads();
-                        }
-                        // warp w sums entries w, w + nw, w + 2 nw, ... (kSyn loads in flight a lane)
-                        for (int e0 = warp; e0 < ce; e0 += nw * kSyn) {
-                            T dv[kSyn];
+                    const int e0 = s_alo_s[tid];
 #pragma unroll
-                            for (int q = 0; q < kSyn; q++) {
-                                const int e = e0 + q * nw;
-                                dv[q] = (e < ce && rv) ? __ldg(P.D + (size_t)sl_col[e] * ld + r) : T(0);
-                            }
-#pragma unroll
-                            for (int q = 0; q < kSyn; q++) {
-                                const int e = e0 + q * nw;
-                                if (e < ce) {
-                                    syn_add(au, dv[q], sl_u[e]);
-                                    syn_add(ax, dv[q], sl_x[e]);
-                                }
-                            }
-                        }
-                    }
-                    acc_store(&s_red[0][warp][lane], au);
-                    acc_store(&s_red[1][warp][lane], ax);
-                    __syncthreads();
-                    if (warp == 0) {
-                        typename Dot2<T>::type wu, wx;
-                        for (int k = 0; k < nw; k++) {
-                            acc_merge(wu, &s_red[0][k][lane]);
-                            acc_merge(wx, &s_red[1][k][lane]);
-                        }
-                        if (rv) {
-                            const T th = (T)theta_from(wu, yv);
-                            W.theta[r] = th;
-                            pa_.add(th, yv);
-                            pb_.add(th, th);
-                            acc_resid_sq(pr_, wx, yv);
-                        }
-                    }
-                    __syncthreads();
-                }
-                if (warp == 0) {
-                    pa_ = acc_warp_reduce(pa_);
-                    pb_ = acc_warp_reduce(pb_);
-                    pr_ = acc_warp_reduce(pr_);
-                    if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
-                }
-            }
-            ok = grid_sync(bar, G, gen);
-            if (!ok) return false;
-
-            // ================================ (B) stop test, correlation + prox
-            {
-                // warps 1.. stage theta_t in shared memory (and, Lasso, the first round's columns)
-                // while warp 0 reduces the partials in a fixed order and lane 0 evaluates the gap
-                // of iteration t-1 and the stopping rule
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                const int n0 = P.is_group ? 0 : min(p_hi - p_lo, P.RA);
-                const X u_pf = tid < n0 ? ldcg_x(ubuf(iC) + p_lo + tid) : it_zero((X*)nullptr);
-                if (warp > 0) {
-                    for (int a = tid - 32; a < n0; a += kThreads - 32) cols_s[a] = __ldcg(W.act[cur] + p_lo + a);
-                    constexpr int kST = kThreads - 32, kSU = 8;
-                    for (int r0 = tid - 32; r0 < P.npad; r0 += kSU * kST) {
-                        T v[kSU];
-#pragma unroll
-                        for (int q = 0; q < kSU; q++) {
-                            const int r = r0 + q * kST;
-                            v[q] = r < N ? __ldcg(W.theta + r) : T(0);
-                        }
-#pragma unroll
-                        for (int q = 0; q < kSU; q++) {
-                            const int r = r0 + q * kST;
-                            if (r < P.npad) th_s[r] = v[q];
+                    for (int q = 0; q < kSpec; q++) {
+                        const int e = e0 + q;
+                        if (e < K) {
+                            pf4(&s_spec[tid].col[q], W.nz_col + e);
+                            pf4(&s_spec[tid].t[q], W.nz_t + e);
+                            pf8(&s_spec[tid].u[q], W.nz_u + e);
+                            pf8(&s_spec[tid].x[q], W.nz_x + e);
                         }
                     }
                 }
-                if (warp == 0) {
-                    // FISTA coefficient of this iteration, fetched ahead of the reductions
-                    const int tf_pre = t - t0;
-                    const bool tab_pre = !ista && tf_pre >= 1 && tf_pre <= P.fista_n;
-                    const double bt_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1)) : 0.0;
-                    const double lf_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1) + 1) : 0.0;
-                    // every load of the per-CTA partials is issued before any is combined
-                    X va[kMaxG / 32], vb[kMaxG / 32], vr[kMaxG / 32], vl[kMaxG / 32];
-                    int ix[kMaxG / 32];
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) {
-                        const int k = lane + 32 * q;
-                        const bool in = k < G;
-                        va[q] = in ? ldcg_x(W.p_a + k) : it_zero((X*)nullptr);
-                        vb[q] = in ? ldcg_x(W.p_b + k) : it_zero((X*)nullptr);
-                        vr[q] = in ? ldcg_x(W.p_r + k) : it_zero((X*)nullptr);
-                        vl[q] = in ? ldcg_x(W.p_l1 + k) : it_zero((X*)nullptr);
-                        ix[q] = in ? __ldcg(W.c_nnzx + k) : 0;
-                    }
-                    const double a_ = part_sum_regs<kMaxG / 32>(va);
-                    const double b_ = part_sum_regs<kMaxG / 32>(vb);
-                    const double r_ = part_sum_regs<kMaxG / 32>(vr);
-                    const double l1 = part_sum_regs<kMaxG / 32>(vl);
-                    int nx = 0;
-#pragma unroll
-                    for (int q = 0; q < kMaxG / 32; q++) nx += ix[q];
-                    nx = warp_sum(nx);
-                    if (lane == 0) {
-                        int stop = 0;
-                        if (t > 1) {
-                            // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                            primal = 0.5 * r_ + lam * l1;
-                            gap = primal - 0.5 * yy + 0.5 * lam * lam * R2n;
-                            iters = t - 1;
-                            if (low) {
-                                // the nominal gap rests on the copy's correlations: stop only on the
-                                // rigorous one (dual point scaled with the bounded max), and switch to the
-                                // FP32 master once the bulk phase reaches its tolerance or stalls
-                                const double gap_safe = primal - 0.5 * yy + 0.5 * lam * lam * R2s_last;
-                                if (gap < 0.99 * best_gap) {
-                                    best_gap = gap;
-                                    since_best = 0;
-                                } else {
-                                    since_best++;
-                                }
-                                if (!(P.tol > 0.0 && gap_safe <= P.tol * 0.5 * yy) &&
-                                    (gap <= P.lo_switch * 0.5 * yy || since_best >= 25)) {
-                                    // FP32 polish: a fresh FISTA sequence warm-started at the bulk iterate
-                                    low = 0;
-                                    t0 = t - 1;
-                                    lf = 1.0;
-                                }
-                                gap = gap_safe;
-                            }
-                            if (record && b == 0 && t - 1 <= P.hist_rows) {
-                                double* h = P.hist + (size_t)(t - 2) * 6;
-                                h[0] = (double)nA_a; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
-                            }
-                            stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
-                            // an owner shutting down (the server) may end the solve early, every 16 iterations
-                            if (P.abort_flag && (t & 15) == 0 && *P.abort_flag) stop = 1;
-                        }
-                        alpha = a_;
-                        beta = b_;
-                        // the parts of Lemma 8 that do not need max |z|, off the critical path of (C)
-                        s_unc = beta > 0.0 ? alpha * inv_lam * fast_rcp(beta) : 0.0;
-                        // an upper bound of ||theta|| is all the rounding bound of (C) needs
-                        sqrt_beta = (double)sqrtf((float)beta) * (1.0 + 1e-6);
-                        double bt = 0.0;
-                        if (!ista) {
-                            // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
-                            // read from the table (the sequence depends on t only)
-                            const int tf = t - t0;  // index in the current FISTA sequence
-                            if (tf == tf_pre && tab_pre) {
-                                bt = bt_pre;
-                                lf = lf_pre;
-                            } else if (tf <= P.fista_n) {
-                                bt = P.fista[2 * (tf - 1)];
-                                lf = P.fista[2 * (tf - 1) + 1];
-                            } else {
-                                const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
-                                bt = (lf - 1.0) / ln;
-                                lf = ln;
-                            }
-                        }
-                        s_sc[10] = bt;
-                        s_si[5] = (int)nx; s_si[6] = stop;
-                        s_si[9] = low;
-                    }
+                // the own slice's test inputs and x_{t-1} (Lasso: one group per thread), for the owner test
+                const bool opf = !P.is_group && tid < n_own;
+                if (opf) {
+                    if (f32_sphere) pf4(&s_pf_i0[tid], W.thrc[cur] + g_lo + tid);
+                    else pf4(&s_pf_i0[tid], W.act[cur] + g_lo + tid);
+                    pf8(&s_pf_x[tid], xbuf(iO) + a_lo0 + tid);
                 }
-                __syncthreads();
-                nnz_last = s_si[5];
-                lowB = s_si[9] != 0;
-                if (s_si[6]) break;
-                if (tid == 0) {
-                    cols_corr += nA_a;
-                    if (lowB) cols_lowp += nA_a;
-                }
-
-                T mloc = T(0);
-                const V* thv = reinterpret_cast<const V*>(th_s);
-                int p = p_lo;
-                while (p < p_hi) {
-                    // gather a round of whole groups, at most RA atoms
-                    int p_end = p, natoms = 0;
-                    if (!P.is_group) {
-                        p_end = min(p_hi, p + P.RA);
-                        natoms = p_end - p;
-                    } else {
-                        if (tid == 0) {
-                            while (p_end < p_hi) {
-                                const int g = __ldcg(W.act[cur] + p_end);
-                                const int sz = P.goff[g + 1] - P.goff[g];
-                                if (natoms + sz > P.RA) break;
-                                natoms += sz;
-                                p_end++;
-                            }
-                            s_si[7] = p_end;
-                            s_si[8] = natoms;
-                        }
-                        __syncthreads();
-                        p_end = s_si[7];
-                        natoms = s_si[8];
-                    }
-                    const int abase = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                    if (!P.is_group) {
-                        if (p != p_lo)  // the first round's columns were staged above
-                            for (int a = tid; a < natoms; a += kThreads) cols_s[a] = __ldcg(W.act[cur] + p + a);
-                    } else {
-                        for (int q = p + tid; q < p_end; q += kThreads) {
-                            const int g = __ldcg(W.act[cur] + q);
-                            const int off = __ldcg(W.aoff[cur] + q) - abase;
-                            for (int i = P.goff[g]; i < P.goff[g + 1]; i++) cols_s[off + i - P.goff[g]] = i;
-                        }
-                    }
-                    __syncthreads();
-                    // z = D_A^T theta: items (atom, row chunk), two per warp in flight
-                    const int nchunk = P.nchunk;
-                    const int nitems = lowB ? 0 : natoms * nchunk;
-                    if constexpr (sizeof(T) == 4) {
-                        if (lowB && P.lo_kind == 1)
-                            gemv_lowp<1, 4>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
-                                            reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
-                        else if (lowB)
-                            gemv_lowp<2, 8>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
-                                            reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
-                    }
-                    if constexpr (sizeof(T) == 4) {
-                        if (!lowB) gemv_f32<4>(P.D, ld, th_s, zpart, cols_s, natoms, nchunk, lane, warp, nw);
-                    } else {
-                        for (int j0 = warp * 2; j0 < nitems; j0 += nw * 2) {
-                            const int j1 = j0 + 1;
-                            const bool h1 = j1 < nitems;
-                            const int a0 = j0 / nchunk, c0 = j0 - a0 * nchunk;
-                            const int a1 = h1 ? j1 / nchunk : a0, c1 = h1 ? j1 - a1 * nchunk : c0;
-                            const V* col0 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a0] * ld);
-                            const V* col1 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a1] * ld);
-                            V d0[kU], d1[kU];
-#pragma unroll
-                            for (int k = 0; k < kU; k++) {
-                                const int v0 = c0 * (32 * kU) + k * 32 + lane;
-                                const int v1 = c1 * (32 * kU) + k * 32 + lane;
-                                d0[k] = v0 < ldv ? __ldg(col0 + v0) : v4zero((V*)nullptr);
-                                d1[k] = (h1 && v1 < ldv) ? __ldg(col1 + v1) : v4zero((V*)nullptr);
-                            }
-                            T s0 = T(0), s1 = T(0);
-#pragma unroll
-                            for (int k = 0; k < kU; k++) {
-                                s0 = vdot(d0[k], thv[c0 * (32 * kU) + k * 32 + lane], s0);
-                                s1 = vdot(d1[k], thv[c1 * (32 * kU) + k * 32 + lane], s1);
-                            }
-                            s0 = warp_sum(s0);
-                            s1 = warp_sum(s1);
-                            if (lane == 0) {
-                                zpart[a0 * nchunk + c0] = s0;
-                                if (h1) zpart[a1 * nchunk + c1] = s1;
-                            }
-                        }
-                    }
-                    __syncthreads();
-                    // proximal step (Table 1): x = prox_{lambda/L Omega}(u - z / L)
-                    for (int a = tid; a < natoms; a += kThreads) {
-                        T z = T(0);
-                        for (int c = 0; c < nchunk; c++) z += zpart[a * nchunk + c];
-                        if (!P.is_group) {
-                            const int ap = abase + a;
-                            const X uv = (p == p_lo && a == tid) ? u_pf : ldcg_x(ubuf(iC) + ap);
-                            xbuf(iN)[ap] = it_soft(it_grad_step(uv, z, invL), thrX);
-                            mloc = fmax(mloc, fabs(z));
-                        } else {
-                            zpart[a * nchunk] = z;
-                        }
-                    }
-                    if (P.is_group) {
-                        __syncthreads();
-                        for (int q = p + tid; q < p_end; q += kThreads) {
-                            const int g = __ldcg(W.act[cur] + q);
-                            const int off = __ldcg(W.aoff[cur] + q);
-                            const int sz = P.goff[g + 1] - P.goff[g];
-                            Acc zq, vq;
-                            for (int i = 0; i < sz; i++) {
-                                const T z = zpart[(off - abase + i) * nchunk];
-                                const X v = it_grad_step(ldcg_x(ubuf(iC) + off + i), z, invL);
-                                zq.add(z, z);
-                                acc_sq(vq, v);
-                            }
-                            const double wg = P.w[g];
-                            const double nv = sqrt(vq.value());
-                            // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
-                            const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0, (X*)nullptr);
-                            for (int i = 0; i < sz; i++) {
-                                const T z = zpart[(off - abase + i) * nchunk];
-                                xbuf(iN)[off + i] = it_scale(it_grad_step(ldcg_x(ubuf(iC) + off + i), z, invL), f);
-                            }
-                            // rounded up so that the FP32 max stays an upper bound of the FP64 value
-                            mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
-                        }
-                    }
-                    __syncthreads();
-                    p = p_end;
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-                if (lane == 0) s_dred[warp] = (double)mloc;
-                __syncthreads();
-                if (tid == 0) {
-                    T m = T(0);
-                    for (int k = 0; k < nw; k++) m = fmax(m, (T)s_dred[k]);
-                    W.p_m[b] = m;
-                }
-            }
-            ok = grid_sync(bar, G, gen);
-            if (!ok) return false;
-
-            // ===================================== (C) screening + momentum
-            {
-                // atoms are handled by warps 1.. (kCT per round); warp 0 evaluates Lemma 8
-                // while they fetch the first round's inputs (Lasso)
-                constexpr int kCT = kThreads - 32;
-                int p_lo, p_hi, a_lo;
-                cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-                int pf_gid = 0;
-                double pf_t0 = 0.0, pf_t1 = 0.0, pf_t2 = 0.0;
-                float pf_thf = 0.f;
-                X pf_x = it_zero((X*)nullptr), pf_xo = it_zero((X*)nullptr);
-                const bool pf = !P.is_group && warp > 0 && p_lo + tid - 32 < p_hi;
-                if (pf) {
-                    const int p = p_lo + tid - 32;
-                    pf_gid = __ldcg(W.act[cur] + p);
-                    pf_x = ldcg_x(xbuf(iN) + p);
-                    pf_xo = ldcg_x(xbuf(iC) + p);
-                    if (dyn_test && f32_sphere) {
-                        pf_thf = __ldcg(W.thrc[cur] + p);
-                    } else if (dyn_test && P.test == 3) {
-                        pf_t0 = colnorm[pf_gid];
-                        pf_t1 = __ldcg(W.b + pf_gid);
-                        pf_t2 = __ldcg(W.tv + pf_gid);
-                    } else if (dyn_test) {
-                        pf_t0 = __ldcg(W.thr + pf_gid);
-                    }
-                }
-                if (warp <= 1) {
-                    // warps 0 and 1 reduce the same per-CTA maxima in the same order
+                if (t > 1 && warp <= 1) {
+                    // warps 0 and 1 reduce the same per-CTA maxima of |z_{t-1}| in the same order
                     T mv[kMaxG / 32];
 #pragma unroll
-                    for (int j = 0; j < kMaxG / 32; j++) mv[j] = lane + 32 * j < G ? __ldcg(W.p_m + lane + 32 * j) : T(0);
+                    for (int jj = 0; jj < kMaxG / 32; jj++) mv[jj] = lane + 32 * jj < G ? __ldcg(W.p_m + lane + 32 * jj) : T(0);
                     T mf = T(0);
 #pragma unroll
-                    for (int j = 0; j < kMaxG / 32; j++) mf = fmax(mf, mv[j]);
+                    for (int jj = 0; jj < kMaxG / 32; jj++) mf = fmax(mf, mv[jj]);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) mf = fmax(mf, __shfl_xor_sync(0xffffffffu, mf, o));
                     const double m_nom = (double)mf;
@@ -1408,84 +981,185 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                 }
+                // directory of the per-CTA nonzero lists (exclusive prefix of their lengths)
+                int totE;
+                const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
+                if (tid < G) s_pref[tid] = exE;
+                if (tid == 0) s_pref[G] = totE;
                 __syncthreads();
-                const double radB = s_sc[8], RsB = s_sc[9];
+                pf_wait();
                 const float radF = s_radf;
-                const X btX = it_cast(s_sc[10], (X*)nullptr);
-                int nz_base = 0, kg = 0, ka = 0, nzx = 0;
+                const double radB = s_sc[8], RsB = s_sc[9];
+                // the test of iteration t-1 on one group, from its list data (FP32 threshold or group id);
+                // the owner of the group and every CTA that sums one of its atoms take the same decision
+                auto killed = [&](int td) -> bool {
+                    if (f32_sphere) return __int_as_float(td) > radF;
+                    if (P.test == 3) {
+                        // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
+                        const double ni = colnorm[td];
+                        const double dc0 = __ldcg(W.b + td) / (lam * ni);
+                        const double tt = __ldcg(W.tv + td) / (ni * nstar);
+                        const double up = dome_max(dc0, tt, psi_dome, RsB);
+                        const double dn = dome_max(-dc0, -tt, psi_dome, RsB);
+                        return (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
+                    }
+                    return __ldcg(W.thr + td) - radB > P.eps_test;
+                };
+
+                // synthesis over row tiles: w_u = D ubar, w_x = D xbar from the nonzero lists of all CTAs,
+                // staged in shared memory; atoms screened by the test of iteration t-1 contribute zero
+                const int E = totE;
+                if (tid == 0) cols_synth += E;
+                Acc pa_, pb_, pr_;
+                const int ntiles = (N + kRowTile - 1) / kRowTile;
+                const int cap = P.syn_cap;
+                int* const sl_col = reinterpret_cast<int*>(smem_raw);
+                X* const sl_u = reinterpret_cast<X*>(smem_raw + (size_t)cap * sizeof(int));
+                X* const sl_x = sl_u + cap;
+                const bool one = E <= cap;
+                if (one && b < ntiles) {
+                    if (tid < G) {
+                        const int nq = min(cnz, kSpec);
+#pragma unroll
+                        for (int q = 0; q < kSpec; q++) {
+                            if (q < nq) {
+                                const bool kq = test_now && killed(s_spec[tid].t[q]);
+                                sl_col[exE + q] = s_spec[tid].col[q];
+                                sl_u[exE + q] = kq ? it_zero((X*)nullptr) : s_spec[tid].u[q];
+                                sl_x[exE + q] = kq ? it_zero((X*)nullptr) : s_spec[tid].x[q];
+                            }
+                        }
+                    }
+                    // the entries beyond the first kSpec of a list
+                    for (int e = tid; e < E; e += kThreads) {
+                        int lo = 0, hi = G;  // largest k with s_pref[k] <= e
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (s_pref[mid] <= e) lo = mid;
+                            else hi = mid;
+                        }
+                        const int loc = e - s_pref[lo];
+                        if (loc >= kSpec) {
+                            const int idx = s_alo_s[lo] + loc;
+                            const bool kq = test_now && killed(__ldcg(W.nz_t + idx));
+                            sl_col[e] = __ldcg(W.nz_col + idx);
+                            sl_u[e] = kq ? it_zero((X*)nullptr) : ldcg_x(W.nz_u + idx);
+                            sl_x[e] = kq ? it_zero((X*)nullptr) : ldcg_x(W.nz_x + idx);
+                        }
+                    }
+                    __syncthreads();
+                }
+                for (int tile = b; tile < ntiles; tile += G) {
+                    const int r = tile * kRowTile + lane;
+                    const bool rv = r < N;
+                    const T yv = (warp == 0 && rv) ? P.y[r] : T(0);
+                    // compensated accumulation: theta = D u - y is a small difference of two
+                    // large vectors, so the sum is carried to twice the working precision
+                    typename Dot2<T>::type au, ax;
+                    for (int c0 = 0; c0 < E; c0 += cap) {
+                        const int ce = min(cap, E - c0);
+                        if (!one) {
+                            __syncthreads();
+                            for (int e = tid; e < ce; e += kThreads) {
+                                const int ee = c0 + e;
+                                int lo = 0, hi = G;
+                                while (hi - lo > 1) {
+                                    const int mid = (lo + hi) >> 1;
+                                    if (s_pref[mid] <= ee) lo = mid;
+                                    else hi = mid;
+                                }
+                                const int idx = s_alo_s[lo] + (ee - s_pref[lo]);
+                                const bool kq = test_now && killed(__ldcg(W.nz_t + idx));
+                                sl_col[e] = __ldcg(W.nz_col + idx);
+                                sl_u[e] = kq ? it_zero((X*)nullptr) : ldcg_x(W.nz_u + idx);
+                                sl_x[e] = kq ? it_zero((X*)nullptr) : ldcg_x(W.nz_x + idx);
+                            }
+                            __syncthreads();
+                        }
+                        // warp w sums entries w, w + nw, w + 2 nw, ... (kSyn loads in flight a lane)
+                        for (int e0 = warp; e0 < ce; e0 += nw * kSyn) {
+                            T dv[kSyn];
+#pragma unroll
+                            for (int q = 0; q < kSyn; q++) {
+                                const int e = e0 + q * nw;
+                                dv[q] = (e < ce && rv) ? __ldg(P.D + (size_t)sl_col[e] * ld + r) : T(0);
+                            }
+#pragma unroll
+                            for (int q = 0; q < kSyn; q++) {
+                                const int e = e0 + q * nw;
+                                if (e < ce) {
+                                    syn_add(au, dv[q], sl_u[e]);
+                                    syn_add(ax, dv[q], sl_x[e]);
+                                }
+                            }
+                        }
+                    }
+                    acc_store(&s_red[0][warp][lane], au);
+                    acc_store(&s_red[1][warp][lane], ax);
+                    __syncthreads();
+                    if (warp == 0) {
+                        typename Dot2<T>::type wu, wx;
+                        for (int k = 0; k < nw; k++) {
+                            acc_merge(wu, &s_red[0][k][lane]);
+                            acc_merge(wx, &s_red[1][k][lane]);
+                        }
+                        if (rv) {
+                            const T th = (T)theta_from(wu, yv);
+                            W.theta[r] = th;
+                            pa_.add(th, yv);
+                            pb_.add(th, th);
+                            acc_resid_sq(pr_, wx, yv);
+                        }
+                    }
+                    __syncthreads();
+                }
+
+                // owner test of iteration t-1 on the slice's live groups: keep flags, and ||x_{t-1}||_1,
+                // nonzeros and sizes of the survivors (Algorithm 3)
+                int kg = 0, ka = 0, nzx = 0;
                 Acc l1;
-                for (int base = p_lo; base < p_hi; base += kCT) {
-                    const int p = base + tid - 32;
-                    const bool valid = warp > 0 && p < p_hi;
-                    const bool use_pf = pf && base == p_lo;  // inputs fetched above
-                    int cnt = 0, lo_a = 0, sz = 0, gid = 0;
-                    X x1 = it_zero((X*)nullptr), u1 = it_zero((X*)nullptr);  // Lasso: the atom's values
-                    if (valid) {
-                        gid = use_pf ? pf_gid : __ldcg(W.act[cur] + p);
-                        lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                        sz = P.is_group ? (p + 1 < nA_g ? __ldcg(W.aoff[cur] + p + 1) : nA_a) - lo_a : 1;
-                        bool kill = false;
-                        if (dyn_test) {
-                            if (P.test == 3) {
-                                // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
-                                const double ni = use_pf ? pf_t0 : colnorm[gid];
-                                const double dc0 = (use_pf ? pf_t1 : __ldcg(W.b + gid)) / (lam * ni);
-                                const double tt = (use_pf ? pf_t2 : __ldcg(W.tv + gid)) / (ni * nstar);
-                                const double up = dome_max(dc0, tt, psi_dome, RsB);
-                                const double dn = dome_max(-dc0, -tt, psi_dome, RsB);
-                                kill = (1.0 / ni - up > P.eps_test) && (1.0 / ni - dn > P.eps_test);
-                            } else if (f32_sphere) {
-                                kill = (use_pf ? pf_thf : __ldcg(W.thrc[cur] + p)) > radF;
-                            } else {
-                                kill = (use_pf ? pf_t0 : __ldcg(W.thr + gid)) - radB > P.eps_test;
-                            }
-                        }
-                        W.keep[p] = !kill;
+                for (int base = 0; base < n_own; base += kThreads) {
+                    const int k = base + tid;
+                    if (k < n_own) {
+                        const bool first = base == 0 && opf;
+                        const int td = first ? s_pf_i0[tid]
+                                             : (f32_sphere ? __float_as_int(__ldcg(W.thrc[cur] + g_lo + k))
+                                                           : __ldcg(W.act[cur] + g_lo + k));
+                        const bool kill = test_now && killed(td);
+                        W.keep[g_lo + k] = !kill;
                         if (!kill) {
-                            Acc gq;
-                            for (int q = 0; q < sz; q++) {
-                                const X xv = use_pf ? pf_x : ldcg_x(xbuf(iN) + lo_a + q);
-                                const X xo = use_pf ? pf_xo : ldcg_x(xbuf(iC) + lo_a + q);
-                                const X uv = ista ? xv : it_momentum(xv, xo, btX);
-                                ubuf(iN)[lo_a + q] = uv;
-                                x1 = xv;
-                                u1 = uv;
-                                cnt += (it_nz(uv) || it_nz(xv));
+                            if (!P.is_group) {
+                                const X xv = first ? s_pf_x[tid] : ldcg_x(xbuf(iO) + a_lo0 + k);
+                                acc_abs(l1, xv);
                                 nzx += it_nz(xv);
-                                if (P.is_group) acc_sq(gq, xv);
-                                else acc_abs(l1, xv);
+                                ka += 1;
+                            } else {
+                                const int gid = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
+                                const int lo_a = __ldcg(W.aoff[cur] + g_lo + k);
+                                const int sz = P.goff[gid + 1] - P.goff[gid];
+                                Acc gq;
+                                for (int q = 0; q < sz; q++) {
+                                    const X xv = ldcg_x(xbuf(iO) + lo_a + q);
+                                    acc_sq(gq, xv);
+                                    nzx += it_nz(xv);
+                                }
+                                acc_add_dbl(l1, P.w[gid] * sqrt(gq.value()));
+                                ka += sz;
                             }
-                            if (P.is_group) acc_add_dbl(l1, P.w[gid] * sqrt(gq.value()));
                             kg += 1;
-                            ka += sz;
                         }
                     }
-                    int tot;
-                    const int pos = block_exclusive_scan(cnt, s_tmp, &tot);
-                    if (cnt && !P.is_group) {
-                        const int e = a_lo + nz_base + pos;
-                        W.nz_col[e] = gid;
-                        W.nz_u[e] = u1;
-                        W.nz_x[e] = x1;
-                    } else if (cnt) {
-                        int e = a_lo + nz_base + pos;
-                        for (int q = 0; q < sz; q++) {
-                            const X xv = ldcg_x(xbuf(iN) + lo_a + q);
-                            const X uv = ldcg_x(ubuf(iN) + lo_a + q);
-                            if (it_nz(uv) || it_nz(xv)) {
-                                W.nz_col[e] = P.is_group ? P.goff[gid] + q : gid;
-                                W.nz_u[e] = uv;
-                                W.nz_x[e] = xv;
-                                e++;
-                            }
-                        }
-                    }
-                    nz_base += tot;
                 }
                 // per-CTA totals: one warp-level reduction and a single block barrier
                 const int rkg = warp_sum(kg), rka = warp_sum(ka), rnx = warp_sum(nzx);
                 const Acc rl1 = acc_warp_reduce(l1);
-                if (lane == 0) { s_ired[warp] = rkg; s_tmp[warp] = rka; s_pref[warp] = rnx; acc_store(&s_red[0][warp][0], rl1); }
+                if (warp == 0) {
+                    pa_ = acc_warp_reduce(pa_);
+                    pb_ = acc_warp_reduce(pb_);
+                    pr_ = acc_warp_reduce(pr_);
+                    if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
+                }
+                if (lane == 0) { s_ired[warp] = rkg; s_tmp[warp] = rka; s_kg[warp] = rnx; acc_store(&s_red[0][warp][0], rl1); }
                 __syncthreads();
                 if (tid == 0) {
                     int tkg = 0, tka = 0, tnx = 0;
@@ -1493,15 +1167,344 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     for (int k = 0; k < nw; k++) {
                         tkg += s_ired[k];
                         tka += s_tmp[k];
-                        tnx += s_pref[k];
+                        tnx += s_kg[k];
                         acc_merge(tl1, &s_red[0][k][0]);
                     }
                     part_put(W.p_l1 + b, tl1);
-                    W.s_alo[b] = a_lo;
                     W.c_kg[b] = tkg;
                     W.c_ka[b] = tka;
-                    W.c_nz[b] = nz_base;
                     W.c_nnzx[b] = tnx;
+                }
+            }
+            ok = grid_sync(bar, G, gen);
+            if (!ok) return false;
+
+            // ======= (B) stop test, compaction of the test of t-1, correlation + prox + momentum
+            {
+                // Lasso: the first round's keep flags, columns, thresholds and iterates, fetched while
+                // warps 0 and 1 reduce the partials
+                const int n0 = P.is_group ? 0 : min(n_own, P.RA);
+                if (tid < n0) {
+                    pf4(&s_pf_i0[tid], W.keep + g_lo + tid);
+                    pf4(&s_pf_i1[tid], W.act[cur] + g_lo + tid);
+                    if (f32_sphere) pf4(&s_pf_f0[tid], W.thrc[cur] + g_lo + tid);
+                    pf8(&s_pf_u[tid], ubuf(iO) + a_lo0 + tid);
+                    pf8(&s_pf_x[tid], xbuf(iO) + a_lo0 + tid);
+                }
+                if (warp >= 2) {
+                    // stage theta_t in shared memory
+                    constexpr int kST = kThreads - 64, kSU = 8;
+                    for (int r0 = tid - 64; r0 < P.npad; r0 += kSU * kST) {
+                        T v[kSU];
+#pragma unroll
+                        for (int q = 0; q < kSU; q++) {
+                            const int r = r0 + q * kST;
+                            v[q] = r < N ? __ldcg(W.theta + r) : T(0);
+                        }
+#pragma unroll
+                        for (int q = 0; q < kSU; q++) {
+                            const int r = r0 + q * kST;
+                            if (r < P.npad) th_s[r] = v[q];
+                        }
+                    }
+                }
+                if (warp == 1) {
+                    // theta_t^T y and ||theta_t||^2: the parts of Lemma 8 that do not need max |z|
+                    X va[kMaxG / 32], vb[kMaxG / 32];
+#pragma unroll
+                    for (int q = 0; q < kMaxG / 32; q++) {
+                        const int k = lane + 32 * q;
+                        const bool in = k < G;
+                        va[q] = in ? ldcg_x(W.p_a + k) : it_zero((X*)nullptr);
+                        vb[q] = in ? ldcg_x(W.p_b + k) : it_zero((X*)nullptr);
+                    }
+                    const double a_ = part_sum_regs<kMaxG / 32>(va);
+                    const double b_ = part_sum_regs<kMaxG / 32>(vb);
+                    if (lane == 0) {
+                        alpha = a_;
+                        beta = b_;
+                        s_unc = beta > 0.0 ? alpha * inv_lam * fast_rcp(beta) : 0.0;
+                        // an upper bound of ||theta|| is all the rounding bound of the radius needs
+                        sqrt_beta = (double)sqrtf((float)beta) * (1.0 + 1e-6);
+                    }
+                }
+                if (warp == 0) {
+                    // FISTA coefficient of this iteration, fetched ahead of the reductions
+                    const int tf_pre = t - t0;
+                    const bool tab_pre = !ista && tf_pre >= 1 && tf_pre <= P.fista_n;
+                    const double bt_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1)) : 0.0;
+                    const double lf_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1) + 1) : 0.0;
+                    // every load of the per-CTA partials is issued before any is combined
+                    X vr[kMaxG / 32], vl[kMaxG / 32];
+                    int ia[kMaxG / 32], ix[kMaxG / 32];
+#pragma unroll
+                    for (int q = 0; q < kMaxG / 32; q++) {
+                        const int k = lane + 32 * q;
+                        const bool in = k < G;
+                        vr[q] = in ? ldcg_x(W.p_r + k) : it_zero((X*)nullptr);
+                        vl[q] = in ? ldcg_x(W.p_l1 + k) : it_zero((X*)nullptr);
+                        ia[q] = in ? __ldcg(W.c_ka + k) : 0;
+                        ix[q] = in ? __ldcg(W.c_nnzx + k) : 0;
+                    }
+                    const double r_ = part_sum_regs<kMaxG / 32>(vr);
+                    const double l1 = part_sum_regs<kMaxG / 32>(vl);
+                    int na = 0, nx = 0;
+#pragma unroll
+                    for (int q = 0; q < kMaxG / 32; q++) { na += ia[q]; nx += ix[q]; }
+                    na = warp_sum(na);
+                    nx = warp_sum(nx);
+                    if (lane == 0) {
+                        int stop = 0;
+                        if (t > 1) {
+                            // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
+                            primal = 0.5 * r_ + lam * l1;
+                            gap = primal - 0.5 * yy + 0.5 * lam * lam * R2n;
+                            iters = t - 1;
+                            if (low) {
+                                // the nominal gap rests on the copy's correlations: stop only on the
+                                // rigorous one (dual point scaled with the bounded max), and switch to the
+                                // FP32 master once the bulk phase reaches its tolerance or stalls
+                                const double gap_safe = primal - 0.5 * yy + 0.5 * lam * lam * R2s_last;
+                                if (gap < 0.99 * best_gap) {
+                                    best_gap = gap;
+                                    since_best = 0;
+                                } else {
+                                    since_best++;
+                                }
+                                if (!(P.tol > 0.0 && gap_safe <= P.tol * 0.5 * yy) &&
+                                    (gap <= P.lo_switch * 0.5 * yy || since_best >= 25)) {
+                                    // FP32 polish: a fresh FISTA sequence warm-started at the bulk iterate
+                                    low = 0;
+                                    t0 = t - 1;
+                                    lf = 1.0;
+                                }
+                                gap = gap_safe;
+                            }
+                            if (record && b == 0 && t - 1 <= P.hist_rows) {
+                                double* h = P.hist + (size_t)(t - 2) * 6;
+                                h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
+                            }
+                            stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                            // an owner shutting down (the server) may end the solve early, every 16 iterations
+                            if (P.abort_flag && (t & 15) == 0 && *P.abort_flag) stop = 1;
+                        }
+                        double bt = 0.0;
+                        if (!ista) {
+                            // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
+                            // read from the table (the sequence depends on t only)
+                            const int tf = t - t0;  // index in the current FISTA sequence
+                            if (tf == tf_pre && tab_pre) {
+                                bt = bt_pre;
+                                lf = lf_pre;
+                            } else if (tf <= P.fista_n) {
+                                bt = P.fista[2 * (tf - 1)];
+                                lf = P.fista[2 * (tf - 1) + 1];
+                            } else {
+                                const double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * lf * lf));
+                                bt = (lf - 1.0) / ln;
+                                lf = ln;
+                            }
+                        }
+                        s_sc[10] = bt;
+                        s_si[4] = na; s_si[5] = nx; s_si[6] = stop;
+                        s_si[9] = low;
+                    }
+                }
+                __syncthreads();
+                pf_wait();
+                lowB = s_si[9] != 0;
+                if (s_si[6]) break;
+                if (tid == 0) {
+                    cols_corr += s_si[4];
+                    if (lowB) cols_lowp += s_si[4];
+                }
+                const X btX = it_cast(s_sc[10], (X*)nullptr);
+
+                // rounds of the slice's live groups (whole groups, at most RA atoms): the survivors of
+                // the test of t-1 move to their compacted positions (list nxt, iterate buffers iO ^ 1),
+                // z = D_A^T theta_t, x_t = prox(u_{t-1} - z / L), u_t = FISTA extrapolation, nonzero list
+                const int nxt = cur ^ 1, iW = iO ^ 1;
+                X* const xW = xbuf(iW);
+                X* const uW = ubuf(iW);
+                const X* const xO = xbuf(iO);
+                const X* const uO = ubuf(iO);
+                int* const opos_s = cols_s + P.RA;
+                T mloc = T(0);
+                int kg_run = 0, ka_run = 0, nz_base = 0;
+                int k0 = 0;
+                while (k0 < n_own) {
+                    const int k = k0 + tid;  // one old live group per thread
+                    int sz = 0, gid = 0, kp = 0, lo_o = 0;
+                    float thf = 0.f;
+                    if (!P.is_group) {
+                        if (k < n_own && tid < P.RA) {
+                            sz = 1;
+                            const bool first = k0 == 0;
+                            kp = first ? s_pf_i0[tid] : __ldcg(W.keep + g_lo + k);
+                            gid = first ? s_pf_i1[tid] : __ldcg(W.act[cur] + g_lo + k);
+                            thf = f32_sphere ? (first ? s_pf_f0[tid] : __ldcg(W.thrc[cur] + g_lo + k)) : 0.f;
+                            lo_o = a_lo0 + k;
+                        }
+                    } else if (k < n_own) {
+                        kp = __ldcg(W.keep + g_lo + k);
+                        gid = __ldcg(W.act[cur] + g_lo + k);
+                        if (f32_sphere) thf = __ldcg(W.thrc[cur] + g_lo + k);
+                        lo_o = __ldcg(W.aoff[cur] + g_lo + k);
+                        sz = P.goff[gid + 1] - P.goff[gid];
+                    }
+                    int k1;
+                    if (!P.is_group) {
+                        k1 = min(n_own, k0 + P.RA);
+                    } else {
+                        // whole groups while the atoms fit in RA
+                        int tot_sz;
+                        const int ex_sz = block_exclusive_scan(sz, s_tmp, &tot_sz);
+                        const int in_round = (k < n_own && ex_sz + sz <= P.RA) ? 1 : 0;
+                        k1 = k0 + __syncthreads_count(in_round);
+                        if (k >= k1) { kp = 0; sz = 0; }
+                    }
+                    const int kept = (kp && k < k1) ? 1 : 0;
+                    int tot;
+                    const int pre = block_exclusive_scan(kept ? ((1 << 16) | sz) : 0, s_tmp, &tot);
+                    const int r_a = pre & 0xffff;  // first atom of the group within the round
+                    if (kept) {
+                        const int ng = kg_run + (pre >> 16);
+                        W.act[nxt][g_lo + ng] = gid;
+                        if (P.is_group) W.aoff[nxt][g_lo + ng] = a_lo0 + ka_run + r_a;
+                        if (f32_sphere) W.thrc[nxt][g_lo + ng] = thf;
+                        const int c0 = P.is_group ? P.goff[gid] : gid;
+                        for (int q = 0; q < sz; q++) {
+                            cols_s[r_a + q] = c0 + q;
+                            opos_s[r_a + q] = lo_o + q;
+                        }
+                    }
+                    const int natoms = tot & 0xffff;
+                    __syncthreads();
+                    // z = D_A^T theta_t: items (atom, row chunk)
+                    const int nchunk = P.nchunk;
+                    if constexpr (sizeof(T) == 4) {
+                        if (lowB && P.lo_kind == 1)
+                            gemv_lowp<1, 4>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
+                                            reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
+                        else if (lowB)
+                            gemv_lowp<2, 8>(P.Dlo, P.ld_lo, P.lo_scale, reinterpret_cast<const float*>(th_s),
+                                            reinterpret_cast<float*>(zpart), cols_s, natoms, nchunk, lane, warp, nw);
+                        else
+                            gemv_f32<4>(P.D, ld, th_s, zpart, cols_s, natoms, nchunk, lane, warp, nw);
+                    } else {
+                        const V* thv = reinterpret_cast<const V*>(th_s);
+                        const int nitems = natoms * nchunk;
+                        for (int j0 = warp * 2; j0 < nitems; j0 += nw * 2) {
+                            const int j1 = j0 + 1;
+                            const bool h1 = j1 < nitems;
+                            const int a0 = j0 / nchunk, c0 = j0 - a0 * nchunk;
+                            const int a1 = h1 ? j1 / nchunk : a0, c1 = h1 ? j1 - a1 * nchunk : c0;
+                            const V* col0 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a0] * ld);
+                            const V* col1 = reinterpret_cast<const V*>(P.D + (size_t)cols_s[a1] * ld);
+                            V d0[kU], d1[kU];
+#pragma unroll
+                            for (int q = 0; q < kU; q++) {
+                                const int v0 = c0 * (32 * kU) + q * 32 + lane;
+                                const int v1 = c1 * (32 * kU) + q * 32 + lane;
+                                d0[q] = v0 < ldv ? __ldg(col0 + v0) : v4zero((V*)nullptr);
+                                d1[q] = (h1 && v1 < ldv) ? __ldg(col1 + v1) : v4zero((V*)nullptr);
+                            }
+                            T s0 = T(0), s1 = T(0);
+#pragma unroll
+                            for (int q = 0; q < kU; q++) {
+                                s0 = vdot(d0[q], thv[c0 * (32 * kU) + q * 32 + lane], s0);
+                                s1 = vdot(d1[q], thv[c1 * (32 * kU) + q * 32 + lane], s1);
+                            }
+                            s0 = warp_sum(s0);
+                            s1 = warp_sum(s1);
+                            if (lane == 0) {
+                                zpart[a0 * nchunk + c0] = s0;
+                                if (h1) zpart[a1 * nchunk + c1] = s1;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    // proximal step (Table 1), x_t = prox_{lambda/L Omega}(u_{t-1} - z / L), and the FISTA
+                    // extrapolation u_t = x_t + bt (x_t - x_{t-1}), by the thread that owns the group
+                    int cnt = 0;
+                    if (kept) {
+                        const int an = a_lo0 + ka_run + r_a;  // new position of the group's first atom
+                        if (!P.is_group) {
+                            T z = T(0);
+                            for (int c = 0; c < nchunk; c++) z += zpart[r_a * nchunk + c];
+                            const bool first = k0 == 0;
+                            const X uo = first ? s_pf_u[tid] : ldcg_x(uO + lo_o);
+                            const X xo = first ? s_pf_x[tid] : ldcg_x(xO + lo_o);
+                            const X xv = it_soft(it_grad_step(uo, z, invL), thrX);
+                            const X uv = ista ? xv : it_momentum(xv, xo, btX);
+                            xW[an] = xv;
+                            uW[an] = uv;
+                            mloc = fmax(mloc, fabs(z));
+                            cnt = (it_nz(uv) || it_nz(xv)) ? 1 : 0;
+                        } else {
+                            Acc zq, vq;
+                            for (int q = 0; q < sz; q++) {
+                                T z = T(0);
+                                for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
+                                const X v = it_grad_step(ldcg_x(uO + lo_o + q), z, invL);
+                                zq.add(z, z);
+                                acc_sq(vq, v);
+                            }
+                            const double wg = P.w[gid];
+                            const double nv = sqrt(vq.value());
+                            // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
+                            const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0, (X*)nullptr);
+                            for (int q = 0; q < sz; q++) {
+                                T z = T(0);
+                                for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
+                                const X xv = it_scale(it_grad_step(ldcg_x(uO + lo_o + q), z, invL), f);
+                                const X uv = ista ? xv : it_momentum(xv, ldcg_x(xO + lo_o + q), btX);
+                                xW[an + q] = xv;
+                                uW[an + q] = uv;
+                                cnt += (it_nz(uv) || it_nz(xv)) ? 1 : 0;
+                            }
+                            // rounded up so that the FP32 max stays an upper bound of the FP64 value
+                            mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
+                        }
+                    }
+                    // nonzero list of (u_t, x_t), with the group's test data
+                    int totc;
+                    const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
+                    if (cnt) {
+                        const int an = a_lo0 + ka_run + r_a;
+                        const int td = f32_sphere ? __float_as_int(thf) : gid;
+                        const int c0 = P.is_group ? P.goff[gid] : gid;
+                        int e = a_lo0 + nz_base + pc;
+                        for (int q = 0; q < sz; q++) {
+                            const X xv = xW[an + q];
+                            const X uv = uW[an + q];
+                            if (it_nz(uv) || it_nz(xv)) {
+                                W.nz_col[e] = c0 + q;
+                                W.nz_u[e] = uv;
+                                W.nz_x[e] = xv;
+                                W.nz_t[e] = td;
+                                e++;
+                            }
+                        }
+                    }
+                    kg_run += tot >> 16;
+                    ka_run += natoms;
+                    nz_base += totc;
+                    k0 = k1;
+                }
+                n_own = kg_run;
+                na_own = ka_run;
+                cur = nxt;
+                iO = iW;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
+                if (lane == 0) s_dred[warp] = (double)mloc;
+                __syncthreads();
+                if (tid == 0) {
+                    T m = T(0);
+                    for (int k = 0; k < nw; k++) m = fmax(m, (T)s_dred[k]);
+                    W.p_m[b] = m;
+                    W.c_nz[b] = nz_base;
                 }
             }
             ok = grid_sync(bar, G, gen);
@@ -1509,36 +1512,32 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         }
 
         // ------------------------------------------------------------ output
-        for (int i = b * kThreads + tid; i < K; i += G * kThreads) xout[i] = T(0);
-        ok = grid_sync(bar, G, gen);
-        if (!ok) return false;
-        {
-            int p_lo, p_hi, a_lo;
-            cta_slice(P, P.is_group ? W.aoff[cur] : nullptr, nA_g, nA_a, b, G, &p_lo, &p_hi, &a_lo);
-            for (int p = p_lo + tid; p < p_hi; p += kThreads) {
-                int gid = __ldcg(W.act[cur] + p);
-                int lo_a = P.is_group ? __ldcg(W.aoff[cur] + p) : p;
-                int c0 = P.is_group ? P.goff[gid] : gid;
-                int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
-                for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(xbuf(iC) + lo_a + q));
-            }
-            if (b == 0 && tid == 0) {
-                R->iters = iters;
-                R->status = (P.tol > 0.0 && !(gap <= P.tol * 0.5 * yy)) ? kDevNotConverged : kDevOk;
-                R->n_active = nA_a;
-                R->nnz = nnz_last;
-                R->gap = gap;
-                R->primal = primal;
-                R->dual = primal - gap;
-                R->lambda = lam;
-                R->lambda_max = lstar;
-                R->cols_corr = cols_corr;
-                R->cols_synth = cols_synth;
-                R->cols_lowp = cols_lowp;
-            }
+        // x_{t-1} restricted to the survivors of the test of iteration t-1 (Algorithm 3), zero elsewhere
+        for (int i = a_lo0 + tid; i < a_hi0; i += kThreads) xout[i] = T(0);
+        __syncthreads();
+        for (int k = tid; k < n_own; k += kThreads) {
+            if (!__ldcg(W.keep + g_lo + k)) continue;
+            const int gid = __ldcg(W.act[cur] + g_lo + k);
+            const int lo_a = P.is_group ? __ldcg(W.aoff[cur] + g_lo + k) : a_lo0 + k;
+            const int c0 = P.is_group ? P.goff[gid] : gid;
+            const int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
+            for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(xbuf(iO) + lo_a + q));
         }
-        ok = grid_sync(bar, G, gen);
-        if (!ok) return false;
+        if (b == 0 && tid == 0) {
+            R->iters = iters;
+            R->status = (P.tol > 0.0 && !(gap <= P.tol * 0.5 * yy)) ? kDevNotConverged : kDevOk;
+            R->n_active = s_si[4];  // active atoms and nonzeros of the returned iterate
+            R->nnz = s_si[5];
+            R->gap = gap;
+            R->primal = primal;
+            R->dual = primal - gap;
+            R->lambda = lam;
+            R->lambda_max = lstar;
+            R->cols_corr = cols_corr;
+            R->cols_synth = cols_synth;
+            R->cols_lowp = cols_lowp;
+        }
+        __syncthreads();
     }
     return true;
 }
@@ -1562,10 +1561,10 @@ inline ds_status geometry(const DictDesc& dd, int num_sms, size_t smem_optin, Ge
     // shared memory: theta + zpart + cols, and room for n (hi/lo) in the precompute
     const size_t fixed = g->npad * sizeof(T);
     const size_t budget = smem_optin > 48 * 1024 ? smem_optin - 40 * 1024 : 48 * 1024;
-    if (fixed + 64 * (g->nchunk * sizeof(T) + 4) > budget) return DS_ERR_UNSUPPORTED;
-    g->RA = (int)std::min<size_t>(512, (budget - fixed) / (g->nchunk * sizeof(T) + 4));
+    if (fixed + 64 * (g->nchunk * sizeof(T) + 8) > budget) return DS_ERR_UNSUPPORTED;
+    g->RA = (int)std::min<size_t>(512, (budget - fixed) / (g->nchunk * sizeof(T) + 8));
     if (dd.is_group && g->RA < dd.max_gsize) return DS_ERR_UNSUPPORTED;
-    g->smem = std::max(fixed + (size_t)g->RA * (g->nchunk * sizeof(T) + 4), (size_t)g->npad * 8);
+    g->smem = std::max(fixed + (size_t)g->RA * (g->nchunk * sizeof(T) + 8), (size_t)g->npad * 8);
     if (g->smem > budget) return DS_ERR_UNSUPPORTED;
     return DS_OK;
 }
@@ -1591,13 +1590,11 @@ inline size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_la
         w->xc[k] = bp.take<X>(K);
         w->uc[k] = bp.take<X>(K);
     }
-    w->xn = bp.take<X>(K);
-    w->un = bp.take<X>(K);
     w->keep = bp.take<int>(nG);
     w->nz_col = bp.take<int>(K);
     w->nz_u = bp.take<X>(K);
     w->nz_x = bp.take<X>(K);
-    w->s_alo = bp.take<int>(G);
+    w->nz_t = bp.take<int>(K);
     w->c_kg = bp.take<int>(G);
     w->c_ka = bp.take<int>(G);
     w->c_nz = bp.take<int>(G);
