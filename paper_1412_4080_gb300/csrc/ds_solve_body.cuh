@@ -450,6 +450,7 @@ template <typename T>
 struct SolveK {
     double fmax_d, nn, nty, wstar2;
     double lam, inv_lam, yy_l2, psi, coef, delta, nstar, psi_dome, thrL, rad2_slack;
+    double hyy, hlam2, tol_abs, delta2, m2a;  // 1/2||y||^2, lambda^2/2, tol 1/2||y||^2, delta^2, -2 theta^T y / lambda
     T invL;
     typename IterT<T>::type thrX;
 };
@@ -765,6 +766,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             C_.thrX = it_cast(C_.thrL, (X*)nullptr);
             // absolute slack on the radius^2 for the FP64 rounding of its terms (all <= ||y||^2/lambda^2)
             C_.rad2_slack = 1e-14 * yy / (lm * lm);
+            C_.hyy = 0.5 * yy;
+            C_.hlam2 = 0.5 * lm * lm;
+            C_.tol_abs = P.tol * 0.5 * yy;
+            C_.delta2 = C_.delta * C_.delta;
         }
         __syncthreads();
         const double &lam = C_.lam, &psi = C_.psi, &coef = C_.coef, &delta = C_.delta, &nstar = C_.nstar;
@@ -947,7 +952,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     if (warp == 1 && lane == 0) {
                         // Lemma 8 with the nominal max |z|: the dual point of the gap (a stopping rule)
                         mu_nom = (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(fast_rcp(m_nom), s_unc) : s_unc;
-                        R2n = fmax(fma(mu_nom, fma(mu_nom, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
+                        R2n = fmax(fma(mu_nom, fma(mu_nom, beta, C_.m2a), yy_l2), 0.0);
                     }
                     if (warp == 0 && lane == 0) {
                         // Lemma 8 with a rigorous upper bound on max |z| given the FP rounding of z, for
@@ -965,12 +970,12 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             if (fabs(s_unc) > r_dn) mu_s = copysign(r_dn, s_unc);
                         }
                         // R^2 = ||y/lambda - mu theta||^2
-                        const double R2s = fmax(fma(mu_s, fma(mu_s, beta, -2.0 * alpha * inv_lam), yy_l2), 0.0);
+                        const double R2s = fmax(fma(mu_s, fma(mu_s, beta, C_.m2a), yy_l2), 0.0);
                         R2s_last = R2s;
                         if (f32_sphere) {
                             // radius of the sphere test (DST3/DGST3: sqrt(R^2 - delta^2)), rounded up to FP32
-                            const double r2 = ((P.test == 2 || P.test == 5) ? R2s - delta * delta : R2s) + rad2_slack;
-                            s_radf = __fsqrt_ru(__double2float_ru(fmax(r2, 0.0)));
+                            const double r2 = ((P.test == 2 || P.test == 5) ? R2s - C_.delta2 : R2s) + rad2_slack;
+                            s_radf = __fsqrt_ru(__double2float_ru(r2));
                         }
                         if (!f32_sphere || record) {
                             // radii rounded up a little: a larger radius only screens less
@@ -986,7 +991,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
                 if (tid < G) s_pref[tid] = exE;
                 if (tid == 0) s_pref[G] = totE;
-                __syncthreads();
+                const bool long_lists = __syncthreads_or(cnz > kSpec) != 0;
                 pf_wait();
                 const float radF = s_radf;
                 const double radB = s_sc[8], RsB = s_sc[9];
@@ -1031,7 +1036,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                     // the entries beyond the first kSpec of a list
-                    for (int e = tid; e < E; e += kThreads) {
+                    for (int e = tid; long_lists && e < E; e += kThreads) {
                         int lo = 0, hi = G;  // largest k with s_pref[k] <= e
                         while (hi - lo > 1) {
                             const int mid = (lo + hi) >> 1;
@@ -1171,6 +1176,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         acc_merge(tl1, &s_red[0][k][0]);
                     }
                     part_put(W.p_l1 + b, tl1);
+                    s_si[12] = tkg;  // kept groups of the slice: (B) skips the compaction when nothing was screened
                     W.c_kg[b] = tkg;
                     W.c_ka[b] = tka;
                     W.c_nnzx[b] = tnx;
@@ -1223,9 +1229,18 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     if (lane == 0) {
                         alpha = a_;
                         beta = b_;
-                        s_unc = beta > 0.0 ? alpha * inv_lam * fast_rcp(beta) : 0.0;
-                        // an upper bound of ||theta|| is all the rounding bound of the radius needs
-                        sqrt_beta = (double)sqrtf((float)beta) * (1.0 + 1e-6);
+                        C_.m2a = -2.0 * a_ * inv_lam;
+                        // the unclipped scaling of Lemma 8 in FP32: R^2 is stationary in mu there, and any
+                        // mu gives a valid sphere, so its rounding moves R^2 by a second-order amount only
+                        if (sizeof(T) == 8) {
+                            s_unc = b_ > 0.0 ? a_ * inv_lam * fast_rcp(b_) : 0.0;
+                            sqrt_beta = (double)sqrtf((float)b_) * (1.0 + 1e-6);
+                        } else {
+                            const float bf = (float)b_;
+                            s_unc = bf > 0.f ? (double)((float)a_ * (float)inv_lam / bf) : 0.0;
+                            // an upper bound of ||theta|| is all the rounding bound of the radius needs
+                            sqrt_beta = (double)(sqrtf(bf) * 1.000002f);
+                        }
                     }
                 }
                 if (warp == 0) {
@@ -1257,14 +1272,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         int stop = 0;
                         if (t > 1) {
                             // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                            primal = 0.5 * r_ + lam * l1;
-                            gap = primal - 0.5 * yy + 0.5 * lam * lam * R2n;
+                            primal = fma(lam, l1, 0.5 * r_);
+                            gap = fma(C_.hlam2, R2n, primal - C_.hyy);
                             iters = t - 1;
                             if (low) {
                                 // the nominal gap rests on the copy's correlations: stop only on the
                                 // rigorous one (dual point scaled with the bounded max), and switch to the
                                 // FP32 master once the bulk phase reaches its tolerance or stalls
-                                const double gap_safe = primal - 0.5 * yy + 0.5 * lam * lam * R2s_last;
+                                const double gap_safe = fma(C_.hlam2, R2s_last, primal - C_.hyy);
                                 if (gap < 0.99 * best_gap) {
                                     best_gap = gap;
                                     since_best = 0;
@@ -1284,7 +1299,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 double* h = P.hist + (size_t)(t - 2) * 6;
                                 h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
                             }
-                            stop = (P.tol > 0.0 && gap <= P.tol * 0.5 * yy) || (t - 1 >= P.max_iter);
+                            stop = (P.tol > 0.0 && gap <= C_.tol_abs) || (t - 1 >= P.max_iter);
                             // an owner shutting down (the server) may end the solve early, every 16 iterations
                             if (P.abort_flag && (t & 15) == 0 && *P.abort_flag) stop = 1;
                         }
@@ -1329,6 +1344,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 const X* const xO = xbuf(iO);
                 const X* const uO = ubuf(iO);
                 int* const opos_s = cols_s + P.RA;
+                // Lasso slice in which the last test screened nothing: positions stay, no list copy
+                const bool same = !P.is_group && s_si[12] == n_own;
                 T mloc = T(0);
                 int kg_run = 0, ka_run = 0, nz_base = 0;
                 int k0 = 0;
@@ -1364,21 +1381,32 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         if (k >= k1) { kp = 0; sz = 0; }
                     }
                     const int kept = (kp && k < k1) ? 1 : 0;
-                    int tot;
-                    const int pre = block_exclusive_scan(kept ? ((1 << 16) | sz) : 0, s_tmp, &tot);
-                    const int r_a = pre & 0xffff;  // first atom of the group within the round
-                    if (kept) {
-                        const int ng = kg_run + (pre >> 16);
-                        W.act[nxt][g_lo + ng] = gid;
-                        if (P.is_group) W.aoff[nxt][g_lo + ng] = a_lo0 + ka_run + r_a;
-                        if (f32_sphere) W.thrc[nxt][g_lo + ng] = thf;
-                        const int c0 = P.is_group ? P.goff[gid] : gid;
-                        for (int q = 0; q < sz; q++) {
-                            cols_s[r_a + q] = c0 + q;
-                            opos_s[r_a + q] = lo_o + q;
+                    int r_a, natoms, ngr;  // first atom of the group within the round; round totals
+                    if (same) {
+                        r_a = tid;
+                        natoms = ngr = k1 - k0;
+                        if (kept) {
+                            cols_s[r_a] = gid;
+                            opos_s[r_a] = lo_o;
+                        }
+                    } else {
+                        int tot;
+                        const int pre = block_exclusive_scan(kept ? ((1 << 16) | sz) : 0, s_tmp, &tot);
+                        r_a = pre & 0xffff;
+                        natoms = tot & 0xffff;
+                        ngr = tot >> 16;
+                        if (kept) {
+                            const int ng = kg_run + (pre >> 16);
+                            W.act[nxt][g_lo + ng] = gid;
+                            if (P.is_group) W.aoff[nxt][g_lo + ng] = a_lo0 + ka_run + r_a;
+                            if (f32_sphere) W.thrc[nxt][g_lo + ng] = thf;
+                            const int c0 = P.is_group ? P.goff[gid] : gid;
+                            for (int q = 0; q < sz; q++) {
+                                cols_s[r_a + q] = c0 + q;
+                                opos_s[r_a + q] = lo_o + q;
+                            }
                         }
                     }
-                    const int natoms = tot & 0xffff;
                     __syncthreads();
                     // z = D_A^T theta_t: items (atom, row chunk)
                     const int nchunk = P.nchunk;
@@ -1487,22 +1515,23 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                         }
                     }
-                    kg_run += tot >> 16;
+                    kg_run += ngr;
                     ka_run += natoms;
                     nz_base += totc;
                     k0 = k1;
                 }
                 n_own = kg_run;
                 na_own = ka_run;
-                cur = nxt;
+                if (!same) cur = nxt;
                 iO = iW;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) mloc = fmax(mloc, __shfl_xor_sync(0xffffffffu, mloc, o));
-                if (lane == 0) s_dred[warp] = (double)mloc;
+                T* const s_mw = reinterpret_cast<T*>(s_dred);  // per-warp maxima, in the type of z
+                if (lane == 0) s_mw[warp] = mloc;
                 __syncthreads();
                 if (tid == 0) {
                     T m = T(0);
-                    for (int k = 0; k < nw; k++) m = fmax(m, (T)s_dred[k]);
+                    for (int k = 0; k < nw; k++) m = fmax(m, s_mw[k]);
                     W.p_m[b] = m;
                     W.c_nz[b] = nz_base;
                 }
