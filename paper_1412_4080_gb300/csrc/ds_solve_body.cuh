@@ -42,6 +42,9 @@ struct Ws {
     int* aoff[2];
     // FP32 dictionaries, sphere tests: (threshold - eps) rounded down to FP32, in list order
     float* thrc[2];
+    // FP32 dictionaries, dynamic dome (Lemma 4), per atom and lambda: d_i^T c0, t_i = d_*^T d_i,
+    // sqrt(1 - t_i^2), 1/||d_i|| - eps rounded down
+    float4* domef;
     // iterates carry about twice the dictionary's precision: in plain FP32,
     // u - z/L would quantise z to multiples of L ulp(x), a KKT floor near 1e-6
     X* xc[2];
@@ -451,6 +454,7 @@ struct SolveK {
     double fmax_d, nn, nty, wstar2;
     double lam, inv_lam, yy_l2, psi, coef, delta, nstar, psi_dome, thrL, rad2_slack;
     double hyy, hlam2, tol_abs, delta2, m2a;  // 1/2||y||^2, lambda^2/2, tol 1/2||y||^2, delta^2, -2 theta^T y / lambda
+    float dome_f[4];  // FP32 dome test of the current iteration: R, psi, rho (rounded up), branch threshold
     T invL;
     typename IterT<T>::type thrX;
 };
@@ -794,6 +798,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         const bool sphere = P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5;
         // FP32 dictionaries run the sphere tests in FP32: thresholds rounded down, radius rounded up
         const bool f32_sphere = sizeof(T) == 4 && sphere;
+        const bool f32_dome = sizeof(T) == 4 && P.test == 3;  // (the dome is a Lasso test)
 
         // ------------------------------------------------ (C0) initial state
         // Every CTA owns the fixed slice [g_lo, g_hi) of the groups for the whole solve and keeps the
@@ -834,6 +839,13 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         th = (wg - sqrt(q)) / sg;
                         W.thr[g] = th;
                         thf = __double2float_rd(th - P.eps_test);
+                    }
+                    if (f32_dome && P.dynamic) {
+                        const double ni = colnorm[g];
+                        const double dc0 = __ldcg(W.b + g) / (lam * ni);
+                        const double tt = __ldcg(W.tv + g) / (ni * nstar);
+                        W.domef[g] = make_float4((float)dc0, (float)tt, (float)sqrt(fmax(1.0 - tt * tt, 0.0)),
+                                                 __double2float_rd(1.0 / ni - P.eps_test));
                     }
                     bool kill = false;
                     if (stat) {
@@ -977,7 +989,17 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const double r2 = ((P.test == 2 || P.test == 5) ? R2s - C_.delta2 : R2s) + rad2_slack;
                             s_radf = __fsqrt_ru(__double2float_ru(r2));
                         }
-                        if (!f32_sphere || record) {
+                        if (f32_dome) {
+                            // FP32 dome: R and rho = sqrt(R^2 - psi^2) rounded up; the second branch of the
+                            // dome maximum is taken only clear of its boundary t R = -psi
+                            const float Rf = __fsqrt_ru(__double2float_ru(R2s));
+                            const float pf = (float)psi_dome;
+                            C_.dome_f[0] = Rf;
+                            C_.dome_f[1] = pf;
+                            C_.dome_f[2] = __fsqrt_ru(__double2float_ru(fmax(R2s - psi_dome * psi_dome, 0.0)));
+                            C_.dome_f[3] = -pf + 1e-5f * (pf + Rf);
+                        }
+                        if (!(f32_sphere || f32_dome) || record) {
                             // radii rounded up a little: a larger radius only screens less
                             const double Rs = fast_sqrt(R2s) * (1.0 + 1e-13);
                             rad = (P.test == 2 || P.test == 5) ? fast_sqrt(fmax(R2s - delta * delta, 0.0)) * (1.0 + 1e-13) : Rs;
@@ -999,6 +1021,17 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 // the owner of the group and every CTA that sums one of its atoms take the same decision
                 auto killed = [&](int td) -> bool {
                     if (f32_sphere) return __int_as_float(td) > radF;
+                    if (f32_dome) {
+                        // max over the dome of +-d_i^T theta (dynamic Lemma 4) in FP32: the dome maximum is
+                        // dc0 + R for t R <= -psi, else dc0 - psi t + rho sqrt(1 - t^2) (never above dc0 + R);
+                        // the slack covers the rounding of the stored constants and of these few operations
+                        const float4 dd = __ldcg(W.domef + td);
+                        const float Rf = C_.dome_f[0], pf = C_.dome_f[1], rf = C_.dome_f[2], tb = C_.dome_f[3];
+                        const float up = dd.y * Rf > tb ? fmaf(rf, dd.z, fmaf(-pf, dd.y, dd.x)) : dd.x + Rf;
+                        const float dn = -dd.y * Rf > tb ? fmaf(rf, dd.z, fmaf(pf, dd.y, -dd.x)) : Rf - dd.x;
+                        const float sl = 1e-6f * (fabsf(dd.x) + pf * fabsf(dd.y) + rf * dd.z + Rf);
+                        return dd.w > up + sl && dd.w > dn + sl;
+                    }
                     if (P.test == 3) {
                         // Lemma 4 (dynamic dome): max over the dome of |d_i^T theta| < 1
                         const double ni = colnorm[td];
@@ -1620,6 +1653,7 @@ inline size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_la
         w->uc[k] = bp.take<X>(K);
     }
     w->keep = bp.take<int>(nG);
+    w->domef = bp.take<float4>(dd.is_group ? 0 : K);
     w->nz_col = bp.take<int>(K);
     w->nz_u = bp.take<X>(K);
     w->nz_x = bp.take<X>(K);
