@@ -454,6 +454,9 @@ struct SolveK {
     double fmax_d, nn, nty, wstar2;
     double lam, inv_lam, yy_l2, psi, coef, delta, nstar, psi_dome, thrL, rad2_slack;
     double hyy, hlam2, tol_abs, delta2, m2a;  // 1/2||y||^2, lambda^2/2, tol 1/2||y||^2, delta^2, -2 theta^T y / lambda
+    float gfm, gfm_lo;   // FP32 max |z| rounding bound per unit ||theta|| (master, low-precision copy), rounded up
+    float sqb_f, s_unc_f;  // ||theta|| (rounded up) and the unclipped Lemma 8 scaling, FP32
+    float bt_h, bt_l;      // FISTA coefficient of the iteration as a float-float pair
     float dome_f[4];  // FP32 dome test of the current iteration: R, psi, rho (rounded up), branch threshold
     T invL;
     typename IterT<T>::type thrX;
@@ -770,6 +773,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             C_.thrX = it_cast(C_.thrL, (X*)nullptr);
             // absolute slack on the radius^2 for the FP64 rounding of its terms (all <= ||y||^2/lambda^2)
             C_.rad2_slack = 1e-14 * yy / (lm * lm);
+            C_.gfm = __double2float_ru(P.gamma * fmax_d);
+            C_.gfm_lo = __double2float_ru(P.emax + P.gamma_lo * (fmax_d + P.emax));
             C_.hyy = 0.5 * yy;
             C_.hlam2 = 0.5 * lm * lm;
             C_.tol_abs = P.tol * 0.5 * yy;
@@ -971,15 +976,17 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         // the screening radius (copy: |z_i - zlo_i| <= ||d_i - dlo_i|| ||theta|| + the FP32
                         // rounding of dlo_i^T theta).  Any |mu| <= 1 / max|z| gives a feasible dual point, so
                         // the clip uses 1 / m_up rounded down.
-                        const double m_up = m_nom + (lowB ? P.emax + P.gamma_lo * (fmax_d + P.emax) : P.gamma * fmax_d) *
-                                                        sqrt_beta;
                         double mu_s = s_unc;
                         if (sizeof(T) == 8) {
+                            const double m_up = m_nom + P.gamma * fmax_d * sqrt_beta;
                             if (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) mu_s = copysign(fast_rcp(m_up), s_unc);
-                        } else if (m_up > 0.0) {
-                            const float mf_up = __double2float_ru(m_up);
-                            const double r_dn = mf_up < 3.0e38f ? (double)__frcp_rd(mf_up) : 0.0;
-                            if (fabs(s_unc) > r_dn) mu_s = copysign(r_dn, s_unc);
+                        } else {
+                            // in FP32, rounded up: m_up = m + (rounding bound per unit ||theta||) ||theta||
+                            const float m_up = __fmaf_ru(lowB ? C_.gfm_lo : C_.gfm, C_.sqb_f, (float)mf);
+                            if (m_up > 0.f) {
+                                const float r_dn = m_up < 3.0e38f ? __frcp_rd(m_up) : 0.f;
+                                if (fabsf(C_.s_unc_f) > r_dn) mu_s = (double)copysignf(r_dn, C_.s_unc_f);
+                            }
                         }
                         // R^2 = ||y/lambda - mu theta||^2
                         const double R2s = fmax(fma(mu_s, fma(mu_s, beta, C_.m2a), yy_l2), 0.0);
@@ -1270,9 +1277,12 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             sqrt_beta = (double)sqrtf((float)b_) * (1.0 + 1e-6);
                         } else {
                             const float bf = (float)b_;
-                            s_unc = bf > 0.f ? (double)((float)a_ * (float)inv_lam / bf) : 0.0;
+                            const float su = bf > 0.f ? (float)a_ * (float)inv_lam / bf : 0.f;
+                            C_.s_unc_f = su;
+                            s_unc = (double)su;
                             // an upper bound of ||theta|| is all the rounding bound of the radius needs
-                            sqrt_beta = (double)(sqrtf(bf) * 1.000002f);
+                            C_.sqb_f = __fmul_ru(__fsqrt_ru(bf), 1.000001f);
+                            sqrt_beta = (double)C_.sqb_f;
                         }
                     }
                 }
@@ -1354,6 +1364,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                         }
                         s_sc[10] = bt;
+                        if (sizeof(T) == 4) {
+                            const FF bf2 = ff_from_double(bt);
+                            C_.bt_h = bf2.h;
+                            C_.bt_l = bf2.l;
+                        }
                         s_si[4] = na; s_si[5] = nx; s_si[6] = stop;
                         s_si[9] = low;
                     }
@@ -1366,7 +1381,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     cols_corr += s_si[4];
                     if (lowB) cols_lowp += s_si[4];
                 }
-                const X btX = it_cast(s_sc[10], (X*)nullptr);
+                X btX;
+                if constexpr (sizeof(T) == 4) btX = FF{C_.bt_h, C_.bt_l};
+                else btX = s_sc[10];
 
                 // rounds of the slice's live groups (whole groups, at most RA atoms): the survivors of
                 // the test of t-1 move to their compacted positions (list nxt, iterate buffers iO ^ 1),
