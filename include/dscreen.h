@@ -285,6 +285,18 @@ ds_status ds_server_destroy(ds_server* server);
 ds_status ds_solve_lasso_noalloc(int device, void* cuda_stream, const float* D, int64_t N, int64_t K, int64_t ld,
                                  const float* y, double lambda, const ds_options* opt, float* x_out, ds_result* res);
 
+/* Self-test of the failure detection; the paper has no counterpart (its
+ * solvers run on one CPU and wait for nothing).  Every wait of the persistent
+ * kernels on other CTAs (grid barriers) gives up after a time limit (2 s),
+ * raises an error flag that the other CTAs see, and the kernel returns; the
+ * host then reports DS_ERR_TIMEOUT and the context stays usable.  This call
+ * launches a two-CTA kernel on `device` in which one CTA never arrives at the
+ * barrier, so the other's wait runs out: *status receives DS_ERR_TIMEOUT when
+ * the wait gave up as designed (DS_OK would mean it completed), *waited_ms the
+ * kernel's duration.  No fault, trap or endless loop is involved.  Errors:
+ * DS_ERR_INVALID (null pointer, no such device), DS_ERR_OOM, DS_ERR_CUDA. */
+ds_status ds_selftest_wait_timeout(int device, int* status, double* waited_ms);
+
 /* Number of CUDA kernels this context has launched so far (solves, lambda_max
  * queries and dictionary precomputes).  Errors: DS_ERR_INVALID on NULL. */
 ds_status ds_ctx_kernel_launches(const ds_ctx* ctx, int64_t* n);

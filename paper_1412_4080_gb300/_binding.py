@@ -91,6 +91,7 @@ def lib():
             L.ds_solve_path.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ds_options), vp, vp,
                                         ctypes.POINTER(ds_result)]
             L.ds_set_history.argtypes = [vp, vp, ctypes.c_int]
+            L.ds_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dp)]
             L.ds_ctx_kernel_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
             L.ds_batch_create.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp,
                                           ctypes.POINTER(vp)]
@@ -359,6 +360,16 @@ def ds_solve_lasso_noalloc(device, stream, D, y, lam, opt, x_out):
                                       ctypes.byref(opt), _ptr(x_out)[0], ctypes.byref(r))
     _check(st, "ds_solve_lasso_noalloc")
     return r.as_dict()
+
+
+def ds_selftest_wait_timeout(device: int = 0):
+    """Run the bounded-wait self-test: returns (status, waited_ms); status is DS_ERR_TIMEOUT when the
+    barrier wait that can never complete gave up as designed."""
+    st_out = ctypes.c_int(-1)
+    ms = ctypes.c_double(0.0)
+    _check(lib().ds_selftest_wait_timeout(int(device), ctypes.byref(st_out), ctypes.byref(ms)),
+           "ds_selftest_wait_timeout")
+    return st_out.value, ms.value
 
 
 def ds_set_history(ctx, hist=None):

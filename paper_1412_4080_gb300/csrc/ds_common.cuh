@@ -25,7 +25,15 @@ struct GridBarrier {
     unsigned int pad;
 };
 
-constexpr unsigned long long kSpinLimit = 1ull << 25;  // ~2 s with the backoff below
+constexpr unsigned long long kSpinLimit = 1ull << 25;  // backstop on the number of polls
+constexpr unsigned long long kWaitNs = 2000000000ull;  // a barrier wait gives up after 2 s
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p)
 {
@@ -47,8 +55,10 @@ __device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned in
 }
 
 // Returns true when every CTA arrived; false when the barrier (now or earlier)
-// failed.  `target` is the CTA's private running target (advanced by gridDim.x).
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, unsigned int& target)
+// failed or the wait exceeded limit_ns.  `target` is the CTA's private running
+// target (advanced by gridDim.x).
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks, unsigned int& target,
+                                          unsigned long long limit_ns = kWaitNs)
 {
     __shared__ int s_ok;
     if (nblocks == 1) {  // a team of one CTA: the block barrier is enough
@@ -62,9 +72,16 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned int nblocks
         // the release add orders every write of the CTA (made before the block
         // barrier above) before the arrival; no separate fence is needed
         red_release_add_u32(&bar->count, 1u);
-        unsigned long long spins = 0;
+        unsigned long long spins = 0, t0 = 0;
         while (ld_acquire_u32(&bar->count) < target) {
-            if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_volatile_u32(&bar->err))) {
+            ++spins;
+            bool give_up = spins > kSpinLimit || ((spins & 1023) == 0 && ld_volatile_u32(&bar->err));
+            if ((spins & 63) == 1) {  // the clock, every 64 polls
+                const unsigned long long now = global_ns();
+                if (spins == 1) t0 = now;
+                else if (now - t0 > limit_ns) give_up = true;
+            }
+            if (give_up) {
                 atomicExch(&bar->err, 1u);
                 ok = 0;
                 break;

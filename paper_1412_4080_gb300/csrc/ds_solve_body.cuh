@@ -407,13 +407,33 @@ __device__ __noinline__ void gemv_f32(const float* D, int ld, const float* th_s,
                 dv[q][k] = (j0 + q < nitems && v < ldv) ? __ldg(col + v) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
+        float s[IPW];
 #pragma unroll
         for (int q = 0; q < IPW; q++) {
-            float s = 0.f;
+            s[q] = 0.f;
 #pragma unroll
-            for (int k = 0; k < kU; k++) s = vdot(dv[q][k], thv[cc[q] * (32 * kU) + k * 32 + lane], s);
-            s = warp_sum(s);
-            if (lane == 0 && j0 + q < nitems) zpart[aa[q] * nchunk + cc[q]] = s;
+            for (int k = 0; k < kU; k++) s[q] = vdot(dv[q][k], thv[cc[q] * (32 * kU) + k * 32 + lane], s[q]);
+        }
+        if constexpr (IPW == 4) {
+            // the four sums in one butterfly: at offsets 16 and 8 each lane keeps the items of its half and
+            // sends the others, so lanes 8q .. 8q+7 end up with item q (the same pairs as warp_sum)
+            const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+            float k0 = h16 ? s[2] : s[0], k1 = h16 ? s[3] : s[1];
+            k0 += __shfl_xor_sync(0xffffffffu, h16 ? s[0] : s[2], 16);
+            k1 += __shfl_xor_sync(0xffffffffu, h16 ? s[1] : s[3], 16);
+            float v = h8 ? k1 : k0;
+            v += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            const int q = (h16 ? 2 : 0) + (h8 ? 1 : 0);
+            if ((lane & 7) == 0 && j0 + q < nitems) zpart[aa[q] * nchunk + cc[q]] = v;
+        } else {
+#pragma unroll
+            for (int q = 0; q < IPW; q++) {
+                const float v = warp_sum(s[q]);
+                if (lane == 0 && j0 + q < nitems) zpart[aa[q] * nchunk + cc[q]] = v;
+            }
         }
     }
 }

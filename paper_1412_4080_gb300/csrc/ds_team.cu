@@ -26,6 +26,8 @@
 
 namespace ds {
 
+constexpr unsigned long long kServerWaitNs = 120000000000ull;  // 120 s
+
 // A served request: solve parameters (with the request's own workspace, carved
 // from the server's memory pool) and device staging for y, x and the result.
 template <typename T>
@@ -117,7 +119,9 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
             }
             A.team_job[team] = j;
         }
-        if (!grid_sync(bar, A.team_size, gen)) {
+        // the team's other CTAs wait here while its leader looks for work, which may last as long as
+        // another team's solve: this wait gets a longer limit than the barriers inside a solve
+        if (!grid_sync(bar, A.team_size, gen, kServerWaitNs)) {
             if (threadIdx.x == 0) atomicExch(A.error, 1);
             return;
         }

@@ -47,3 +47,11 @@ def test_dict_create_rejects_bad_shapes_without_gpu_work():
     # null context, bad N/K/ld and bad dtype are rejected before any CUDA call
     assert L.ds_dict_create(None, D.ctypes.data, 4, 6, 4, ds.DS_FP64, None, None, 0, ds.DS_FP64,
                             ctypes.byref(h)) == ds.DS_ERR_INVALID
+
+
+def test_selftest_rejects_null_outputs_without_gpu_work():
+    L = ds.lib()
+    v = ctypes.c_double()
+    st = ctypes.c_int()
+    assert L.ds_selftest_wait_timeout(0, None, ctypes.byref(v)) == ds.DS_ERR_INVALID
+    assert L.ds_selftest_wait_timeout(0, ctypes.byref(st), None) == ds.DS_ERR_INVALID
