@@ -203,6 +203,9 @@ def main():
                     help="register the dictionary and run one 5-lambda DST3 path, then exit (profiling)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run one 64-rhs multi-RHS batch on the BF16 copy of the dictionary, then exit (profiling)")
+    ap.add_argument("--paper", action="store_true",
+                    help="the paper's screening comparison (no screening / static / dynamic, ISTA / FISTA, "
+                         "Pnoise / Gaussian) on the GPU, then exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -212,6 +215,9 @@ def main():
         return
     if args.profile_batch:
         profile_batch()
+        return
+    if args.paper:
+        paper_accounting()
         return
 
     import torch
@@ -360,6 +366,52 @@ def profile_batch():
     print(json.dumps({"solves": len(res), "converged": sum(r["status"] == 0 for r in res),
                       "iters_max": max(r["iters"] for r in res), "ms": res[0]["ms"],
                       "cols_corr": sum(r["cols_corr"] for r in res), "cols_lowp": sum(r["cols_lowp"] for r in res)}))
+
+
+PAPER_RATIOS = (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9)
+PAPER_STRATEGIES = (("none", 1), ("dst3", 0), ("safe", 1), ("dst3", 1), ("dome", 1))
+
+
+def paper_accounting():
+    """The comparison of Sec. 4.3-4.5 on the GPU: for a Pnoise and a Gaussian 2000 x 10000
+    dictionary, an observation drawn like the atoms (Sec. 4.2), ISTA and FISTA run for 200
+    iterations (the paper's cap) with no screening, static ST3 (Algorithm 1) and dynamic SAFE,
+    ST3 and Dome (Algorithm 3), at lambda / lambda_* = 0.1 ... 0.9.  Reported per run: the
+    dictionary columns read (correlations + syntheses; 2 N flops each, the paper's flops_D /
+    flops_N when divided by the unscreened count) and the kernel time against no screening."""
+    import torch
+    import gen
+    import paper_1412_4080_gb300 as ds
+    out = {"workload": "2000x10000, y drawn like the atoms (Sec. 4.2), 200 iterations, FP32", "runs": []}
+    ctx = ds.ds_create(0, torch.cuda.current_stream())
+    for kind, seed in (("pnoise", 1010), ("gaussian", 1011)):
+        g = gen.rng(seed)
+        D = gen.pnoise_dict(2000, 10000, g) if kind == "pnoise" else gen.gaussian_dict(2000, 10000, g)
+        y = gen.atom_like_y(2000, kind, g)
+        Dt = torch.from_numpy(np.ascontiguousarray(D.T.astype(np.float32))).cuda().t()
+        yt = torch.from_numpy(y.astype(np.float32)).cuda()
+        dct = ds.ds_dict_create(ctx, Dt)
+        x = torch.empty(D.shape[1], device="cuda")
+        try:
+            for alg in ("ista", "fista"):
+                for ratio in PAPER_RATIOS:
+                    base = None
+                    for test, dyn in PAPER_STRATEGIES:
+                        o = ds.ds_options_default(alg=alg, test=test, dynamic=dyn, tol_gap_rel=0.0, max_iter=200,
+                                                  lambda_rel=1)
+                        ds.ds_solve(ctx, dct, yt, ratio, o, x)  # warm the caches for the timed run
+                        r = ds.ds_solve(ctx, dct, yt, ratio, o, x)
+                        cols = r["cols_corr"] + r["cols_synth"]
+                        if base is None:
+                            base = (cols, r["ms"])
+                        out["runs"].append({"dict": kind, "alg": alg, "ratio": ratio, "test": test,
+                                            "dynamic": dyn, "iters": r["iters"], "n_active": r["n_active"],
+                                            "gap_rel": r["gap"] / (0.5 * float(y @ y)), "ms": round(r["ms"], 4),
+                                            "flops_ratio": cols / base[0], "time_ratio": r["ms"] / base[1]})
+        finally:
+            ds.ds_dict_destroy(dct)
+    ds.ds_destroy(ctx)
+    print(json.dumps(out))
 
 
 def profile_one():

@@ -89,6 +89,19 @@ def observe(D, x0, g: np.random.Generator, snr_db: float | None = 20.0, sigma: f
     return s + e * (ns / np.linalg.norm(e)) * 10.0 ** (-snr_db / 20.0)
 
 
+def atom_like_y(N: int, kind: str, g: np.random.Generator) -> np.ndarray:
+    """An observation drawn from the same distribution as the atoms (the paper's Lasso
+    experiments, Sec. 4.2): uniform on the unit sphere, or a normalised Pnoise draw."""
+    if kind == "gaussian":
+        v = g.standard_normal(N)
+    elif kind == "pnoise":
+        v = 0.1 * g.uniform(0.0, 1.0) * g.standard_normal(N)
+        v[0] += 1.0
+    else:
+        raise ValueError(kind)
+    return v / np.linalg.norm(v)
+
+
 def contiguous_groups(K: int, size: int) -> np.ndarray:
     return np.arange(0, K + 1, size, dtype=np.int64)
 

@@ -78,6 +78,9 @@ typedef struct {
     int batch_multi_rhs; /* batches: 1 (default) solves the right-hand sides of an FP32 Lasso instance
                             together, up to 64 per block, so each dictionary column read serves them all;
                             0 runs every (instance, rhs) problem on its own */
+    int warm_start;      /* ds_solve_path: 1 starts each lambda from the previous lambda's solution (a
+                            regularization path; the screening tests of each lambda stay those of its own
+                            dual problem, so they remain safe); 0 (default) starts every lambda from x0 */
 } ds_options;
 
 typedef struct {
@@ -124,7 +127,7 @@ ds_status ds_destroy(ds_ctx* ctx);
  * Groups (eq. group-lasso): group_offsets (host, n_groups + 1 entries,
  * 0 = off_0 < off_1 < ... < off_G = K) lists contiguous column ranges; weights
  * (host, n_groups entries, > 0; NULL = sqrt(group size)).  group_offsets NULL
- * = the Lasso.  Group sizes are limited to 32 columns (DS_ERR_UNSUPPORTED).
+ * = the Lasso.  Group sizes are limited to 128 columns (DS_ERR_UNSUPPORTED).
  * work_prec: dtype, or (FP32 dictionaries) DS_BF16 / DS_FP8 for the precision
  * variant: the library also keeps a BF16 copy or an FP8 e4m3 copy with one
  * scale per column (max|d_i| / 448) and the exact error norms ||d_i - copy_i||;
@@ -132,7 +135,7 @@ ds_status ds_destroy(ds_ctx* ctx);
  * with every screening radius inflated by the copy's error bound so the tests
  * stay safe, and finish with FP32 iterations on the surviving atoms.
  * Errors: DS_ERR_INVALID,
- * DS_ERR_UNSUPPORTED (N > the shared-memory limit, group > 32, work_prec),
+ * DS_ERR_UNSUPPORTED (N > the shared-memory limit, group > 128, work_prec),
  * DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
 ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64_t ld, ds_prec dtype,
                          const int64_t* group_offsets, const double* weights, int64_t n_groups,

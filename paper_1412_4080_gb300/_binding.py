@@ -39,7 +39,7 @@ class ds_options(ctypes.Structure):
     _fields_ = [("alg", ctypes.c_int), ("test", ctypes.c_int), ("dynamic", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
                 ("lambda_rel", ctypes.c_int), ("lowp_switch", ctypes.c_double),
-                ("batch_multi_rhs", ctypes.c_int)]
+                ("batch_multi_rhs", ctypes.c_int), ("warm_start", ctypes.c_int)]
 
 
 class ds_result(ctypes.Structure):

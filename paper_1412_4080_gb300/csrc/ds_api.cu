@@ -122,6 +122,7 @@ ds_status ds_options_default(ds_options* opt)
     opt->lambda_rel = 0;
     opt->lowp_switch = 0.0;
     opt->batch_multi_rhs = 1;
+    opt->warm_start = 0;
     return DS_OK;
 }
 
@@ -208,7 +209,7 @@ ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64
             if (weights && !(weights[g] > 0.0 && std::isfinite(weights[g]))) return DS_ERR_INVALID;
             max_gsize = (int)std::max<int64_t>(max_gsize, sz);
         }
-        if (max_gsize > 32) return DS_ERR_UNSUPPORTED;
+        if (max_gsize > kMaxGroup) return DS_ERR_UNSUPPORTED;
     }
     if (cudaSetDevice(ctx->device) != cudaSuccess) return DS_ERR_CUDA;
     const size_t es = elem_size(dtype);

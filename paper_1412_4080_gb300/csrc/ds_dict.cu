@@ -48,17 +48,22 @@ __global__ void colnorm_kernel(const T* __restrict__ D, int N, int K, int ld, do
 }
 
 // One CTA per group: Gram matrix (compensated dots, one warp per entry pair),
-// then thread 0 runs cyclic Jacobi on it in FP64.  The largest eigenvalue is
-// bounded above by max diagonal + Frobenius norm of the off-diagonal rest
-// (Weyl), and rounded up by a relative 1e-12.
+// then cyclic Jacobi on it in FP64, each rotation computed by thread 0 and
+// applied to the rows and columns by the whole CTA (the same arithmetic as a
+// serial sweep).  The largest eigenvalue is bounded above by max diagonal +
+// Frobenius norm of the off-diagonal rest (Weyl), and rounded up by a relative
+// 1e-12.  A (m x m, m <= kMaxGroup) lives in dynamic shared memory.
 template <typename T>
 __global__ void group_spec_kernel(const T* __restrict__ D, int N, int ld, const int* __restrict__ goff,
                                   const double* __restrict__ w, double* __restrict__ spec, double* __restrict__ fw)
 {
-    __shared__ double A[32 * 32];
+    extern __shared__ double A[];
+    __shared__ double s_cs[2];
+    __shared__ double s_part[2][32];
+    __shared__ int s_done;
     const int g = blockIdx.x;
     const int c0 = goff[g], m = goff[g + 1] - c0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int npairs = m * (m + 1) / 2;
     for (int pr = warp; pr < npairs; pr += nw) {
         int p = 0, rem = pr;
@@ -72,37 +77,61 @@ __global__ void group_spec_kernel(const T* __restrict__ D, int N, int ld, const 
         if (lane == 0) { A[p * m + q] = s; A[q * m + p] = s; }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
     double tr = 0.0;
-    for (int p = 0; p < m; p++) tr += A[p * m + p];
+    if (tid == 0)
+        for (int p = 0; p < m; p++) tr += A[p * m + p];
     for (int sweep = 0; sweep < 60; sweep++) {
         double off = 0.0, dg = 0.0;
-        for (int p = 0; p < m; p++)
-            for (int q = 0; q < m; q++) {
-                if (p != q) off += A[p * m + q] * A[p * m + q];
-                else dg += A[p * m + p] * A[p * m + p];
-            }
-        if (off <= 1e-30 * dg) break;
+        for (int e = tid; e < m * m; e += blockDim.x) {
+            const double v = A[e] * A[e];
+            if (e / m != e % m) off += v;
+            else dg += v;
+        }
+        off = warp_sum(off);
+        dg = warp_sum(dg);
+        if (lane == 0) { s_part[0][warp] = off; s_part[1][warp] = dg; }
+        __syncthreads();
+        if (tid == 0) {
+            double o = 0.0, d = 0.0;
+            for (int k = 0; k < nw; k++) { o += s_part[0][k]; d += s_part[1][k]; }
+            s_done = o <= 1e-30 * d;
+        }
+        __syncthreads();
+        if (s_done) break;
         for (int p = 0; p < m - 1; p++)
             for (int q = p + 1; q < m; q++) {
-                double apq = A[p * m + q];
-                if (apq == 0.0) continue;
-                double app = A[p * m + p], aqq = A[q * m + q];
-                double tau = (aqq - app) / (2.0 * apq);
-                double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int k = 0; k < m; k++) {
-                    double akp = A[k * m + p], akq = A[k * m + q];
-                    A[k * m + p] = c * akp - s * akq;
-                    A[k * m + q] = s * akp + c * akq;
+                if (tid == 0) {
+                    const double apq = A[p * m + q];
+                    double c = 1.0, s = 0.0;
+                    if (apq != 0.0) {
+                        const double app = A[p * m + p], aqq = A[q * m + q];
+                        const double tau = (aqq - app) / (2.0 * apq);
+                        const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                    s_cs[0] = c;
+                    s_cs[1] = s;
                 }
-                for (int k = 0; k < m; k++) {
-                    double apk = A[p * m + k], aqk = A[q * m + k];
-                    A[p * m + k] = c * apk - s * aqk;
-                    A[q * m + k] = s * apk + c * aqk;
+                __syncthreads();
+                const double c = s_cs[0], s = s_cs[1];
+                if (s != 0.0) {
+                    for (int k = tid; k < m; k += blockDim.x) {
+                        const double akp = A[k * m + p], akq = A[k * m + q];
+                        A[k * m + p] = c * akp - s * akq;
+                        A[k * m + q] = s * akp + c * akq;
+                    }
+                    __syncthreads();
+                    for (int k = tid; k < m; k += blockDim.x) {
+                        const double apk = A[p * m + k], aqk = A[q * m + k];
+                        A[p * m + k] = c * apk - s * aqk;
+                        A[q * m + k] = s * apk + c * aqk;
+                    }
                 }
+                __syncthreads();
             }
     }
+    if (tid != 0) return;
     double mx = A[0], off = 0.0;
     for (int p = 0; p < m; p++) {
         mx = fmax(mx, A[p * m + p]);
@@ -508,8 +537,15 @@ static ds_status precompute_t(ds_ctx* ctx, ds_dict* dict, const double* w_host)
     if (dict->is_group) {
         double* fw = nullptr;
         if (cudaMalloc(&fw, sizeof(double) * dict->nG) != cudaSuccess) { cudaFree(d_fmax); return DS_ERR_OOM; }
-        group_spec_kernel<T><<<dict->nG, 256, 0, s>>>(reinterpret_cast<const T*>(dict->D), N, ld, dict->goff, dict->w,
-                                                      dict->spec, fw);
+        const size_t gsm = sizeof(double) * dict->max_gsize * dict->max_gsize;
+        if (gsm > 48 * 1024 && cudaFuncSetAttribute(group_spec_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)gsm) != cudaSuccess) {
+            cudaFree(fw);
+            cudaFree(d_fmax);
+            return DS_ERR_CUDA;
+        }
+        group_spec_kernel<T><<<dict->nG, 128, gsm, s>>>(reinterpret_cast<const T*>(dict->D), N, ld, dict->goff, dict->w,
+                                                        dict->spec, fw);
         max_kernel<<<1, 1024, 0, s>>>(fw, dict->nG, d_fmax);
         cudaStreamSynchronize(s);
         cudaFree(fw);

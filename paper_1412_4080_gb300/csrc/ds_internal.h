@@ -55,6 +55,8 @@ struct ds_dict {
 
 namespace ds {
 
+constexpr int kMaxGroup = 128;  // largest group (columns) of a Group-Lasso dictionary
+
 // Per-solve result written by the solve kernel (one per lambda).
 struct DevResult {
     int iters;

@@ -82,7 +82,7 @@ struct SolveP {
     int n_lambda;
     const double* lambdas;  // device copy
     int lambda_rel;
-    int alg, test, dynamic, max_iter;
+    int alg, test, dynamic, max_iter, warm_start;
     double tol, L;
     T* x_out;
     long long ldx;
@@ -809,8 +809,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         T* xout = P.x_out + (size_t)j * P.ldx;
         DevResult* R = P.res + j;
         if (!(lam < lstar)) {
-            // x = 0 and theta = y / lambda is dual optimal (Sec. 2.2.2)
-            for (int i = b * kThreads + tid; i < K; i += G * kThreads) xout[i] = T(0);
+            // x = 0 and theta = y / lambda is dual optimal (Sec. 2.2.2); each CTA writes its own slice
+            // (a warm-started next lambda reads it back in the same CTA)
+            for (int i = a_lo0 + tid; i < a_hi0; i += kThreads) xout[i] = T(0);
             if (b == 0 && tid == 0) {
                 R->iters = 0; R->status = kDevOk; R->n_active = 0; R->nnz = 0;
                 R->gap = 0.0; R->primal = 0.5 * yy; R->dual = 0.5 * yy; R->lambda = lam; R->lambda_max = lstar;
@@ -843,6 +844,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 rad0 = (P.test == 2 || P.test == 5) ? sqrt(fmax(R2 - delta * delta, 0.0)) : sqrt(R2);
             }
             int nzc = 0;
+            // starting point: x0, or (warm-started path) the previous lambda's solution, which this CTA
+            // wrote itself (the slices are the same for every lambda)
+            const T* const x0 = (P.warm_start && j > 0) ? P.x_out + (size_t)(j - 1) * P.ldx : P.x0;
             for (int base = g_lo; base < g_hi; base += kThreads) {
                 const int g = base + tid;
                 const bool valid = g < g_hi;
@@ -886,20 +890,21 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                     kept = !kill;
-                    if (kept && P.x0)
-                        for (int i = lo_a; i < hi_a; i++) cnt += P.x0[i] != T(0);
+                    if (kept && x0)
+                        for (int i = lo_a; i < hi_a; i++) cnt += x0[i] != T(0);
                 }
                 int tot, totc;
-                const int pre = block_exclusive_scan(kept ? ((1 << 16) | (hi_a - lo_a)) : 0, s_tmp, &tot);
+                // packed scan of (groups, atoms): 512 groups of at most kMaxGroup atoms fit 20 bits
+                const int pre = block_exclusive_scan(kept ? ((1 << 20) | (hi_a - lo_a)) : 0, s_tmp, &tot);
                 const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
                 if (kept) {
-                    const int ng = n_own + (pre >> 16), na = na_own + (pre & 0xffff);
+                    const int ng = n_own + (pre >> 20), na = na_own + (pre & 0xfffff);
                     W.act[0][g_lo + ng] = g;
                     if (P.is_group) W.aoff[0][g_lo + ng] = a_lo0 + na;
                     if (f32_sphere) W.thrc[0][g_lo + ng] = thf;
                     int e = a_lo0 + nzc + pc;
                     for (int i = lo_a; i < hi_a; i++) {
-                        const X xv = P.x0 ? it_from(P.x0[i], (X*)nullptr) : it_zero((X*)nullptr);
+                        const X xv = x0 ? it_from(x0[i], (X*)nullptr) : it_zero((X*)nullptr);
                         W.xc[0][a_lo0 + na + i - lo_a] = xv;
                         W.uc[0][a_lo0 + na + i - lo_a] = xv;
                         if (it_nz(xv)) {
@@ -912,8 +917,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                 }
-                n_own += tot >> 16;
-                na_own += tot & 0xffff;
+                n_own += tot >> 20;
+                na_own += tot & 0xfffff;
                 nzc += totc;
             }
             if (tid == 0) {
@@ -1736,6 +1741,7 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.alg = opt ? opt->alg : 1;
     P.test = opt ? opt->test : 0;
     P.dynamic = opt ? opt->dynamic : 1;
+    P.warm_start = opt ? opt->warm_start : 0;
     P.max_iter = opt ? opt->max_iter : 1;
     P.tol = opt ? opt->tol_gap_rel : 0.0;
     P.L = (opt && opt->L > 0) ? opt->L : dd.L;

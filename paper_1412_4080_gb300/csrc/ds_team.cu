@@ -1069,7 +1069,7 @@ ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, 
     dmax.K = (int)max_K;
     dmax.ld = (int)max_N;
     dmax.nG = (int)max_K;
-    dmax.max_gsize = 32;
+    dmax.max_gsize = ds::kMaxGroup;
     dmax.is_group = 1;
     ds::Geometry gmax;
     if (ds::geometry<float>(dmax, S->team_size, ctx->smem_optin, &gmax) != DS_OK) return fail(DS_ERR_UNSUPPORTED);

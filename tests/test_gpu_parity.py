@@ -162,6 +162,28 @@ def test_group_lasso_fp32_parity(ctx, test, ratio):
     assert abs(r["lambda_max"] - lm) <= 1e-12 * lm
 
 
+@pytest.mark.parametrize("gsize", [50, 100])
+@pytest.mark.parametrize("test", ["gsafe", "dgst3"])
+def test_group_lasso_large_groups(ctx, test, gsize):
+    """The paper's larger groups (Sec. 4.4 sweeps 5 to 100 atoms per group): ||D_g||_2 by
+    the CTA-parallel Jacobi, and the solve, match the oracle."""
+    N, K = 500, 2000
+    D, y, _, goff, w = gen.config3(41, N=N, K=K, gsize=gsize, n_active=2)
+    D, y = _f32(D), _f32(y)
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.5 * lm
+    L = oracle.spectral_norm_sq(D, tol=1e-10, max_iter=5000) * (1 + 1e-6)
+    ref = oracle.solve(D, y, lam, goff, w, alg="fista", test=test, tol=0, max_iter=1500, L=L)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32), goff, w)
+    try:
+        x, r = _solve_gpu(ctx, dct, y, lam, torch.float32, K, test=test, tol_gap_rel=0.0, max_iter=1500, L=L)
+    finally:
+        ds.ds_dict_destroy(dct)
+    scale = np.abs(ref["x"]).max()
+    assert np.abs(x - ref["x"]).max() <= 1e-5 * scale
+    assert abs(r["lambda_max"] - lm) <= 1e-12 * lm
+
+
 def test_group_lasso_ragged_groups(ctx):
     """Groups of unequal sizes (1 to 17 atoms) and weights."""
     g = gen.rng(41)
@@ -289,3 +311,33 @@ def test_config2_full_size(ctx, ratio):
     assert _fp64_gap(D, y, x, lam) <= 2e-6 * 0.5 * yy
     c = D.T @ (y - D @ x)
     assert np.abs(c).max() <= lam * (1 + 1e-2)
+
+
+def test_warm_started_path_matches_cold_lambdas(ctx):
+    """A regularization path (descending lambda) started from each previous solution reaches
+    the same solutions as cold starts, in fewer iterations; the first lambda (>= lambda_*)
+    gives x = 0 and seeds the next one."""
+    N, K = 400, 2400
+    D, y, _ = gen.lasso_problem(N, K, seed=91, p=0.01)
+    D, y = _f32(D), _f32(y)
+    ratios = np.array([1.2, 0.8, 0.6, 0.45, 0.3, 0.2])
+    dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
+    try:
+        yt = torch.from_numpy(y).to("cuda", torch.float32)
+        res = {}
+        Xs = {}
+        for warm in (0, 1):
+            X = torch.empty((len(ratios), K), device="cuda")
+            o = ds.ds_options_default(test="dst3", tol_gap_rel=1e-7, max_iter=50000, lambda_rel=1, warm_start=warm)
+            res[warm] = ds.ds_solve_path(ctx, dct, yt, ratios, o, X)
+            Xs[warm] = X.double().cpu().numpy()
+    finally:
+        ds.ds_dict_destroy(dct)
+    yy = float(y @ y)
+    for j in range(len(ratios)):
+        for warm in (0, 1):
+            assert res[warm][j]["status"] == 0 and res[warm][j]["gap"] <= 1e-7 * 0.5 * yy
+        # both certify 1e-7: their fits differ by at most sqrt(2 gap) each
+        assert np.linalg.norm(D @ (Xs[0][j] - Xs[1][j])) <= 2 * np.sqrt(2e-7 * 0.5 * yy) * 1.01
+    assert res[1][0]["iters"] == 0 and not Xs[1][0].any()
+    assert sum(r["iters"] for r in res[1]) < sum(r["iters"] for r in res[0])

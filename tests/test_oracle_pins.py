@@ -377,6 +377,17 @@ def test_spectral_norms_match_library():
         assert np.isclose(s, np.linalg.norm(D[:, c0:c1], 2), rtol=1e-12)
 
 
+def test_group_spectral_norms_of_large_groups_match_library():
+    """Groups of 50 to 128 columns (the paper's group-size sweep goes to 100): the Jacobi
+    value is an upper bound of ||D_g||_2 and agrees with LAPACK."""
+    g = gen.rng(21)
+    D = gen.gaussian_dict(200, 300, g)
+    for c0, c1 in ((0, 50), (50, 150), (150, 278)):
+        s = oracle.group_spec_norm(D, c0, c1)
+        ref = np.linalg.norm(D[:, c0:c1], 2)
+        assert s >= ref * (1 - 1e-14) and np.isclose(s, ref, rtol=1e-10)
+
+
 @pytest.mark.parametrize("pair", [("safe", "gsafe"), ("dst3", "dgst3")])
 def test_singleton_groups_with_unequal_norms(pair):
     """The singleton-group identity also holds for atoms of unequal norms (Lemma 7's
