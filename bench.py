@@ -374,7 +374,7 @@ PAPER_STRATEGIES = (("none", 1), ("dst3", 0), ("safe", 1), ("dst3", 1), ("dome",
 
 def paper_accounting():
     """The comparison of Sec. 4.3-4.5 on the GPU: for a Pnoise and a Gaussian 2000 x 10000
-    dictionary, an observation drawn like the atoms (Sec. 4.2), ISTA and FISTA run for 200
+    dictionary, an observation drawn like the atoms (Sec. 4.2), ISTA, FISTA and Chambolle-Pock run for 200
     iterations (the paper's cap) with no screening, static ST3 (Algorithm 1) and dynamic SAFE,
     ST3 and Dome (Algorithm 3), at lambda / lambda_* = 0.1 ... 0.9.  Reported per run: the
     dictionary columns read (correlations + syntheses; 2 N flops each, the paper's flops_D /
@@ -393,7 +393,7 @@ def paper_accounting():
         dct = ds.ds_dict_create(ctx, Dt)
         x = torch.empty(D.shape[1], device="cuda")
         try:
-            for alg in ("ista", "fista"):
+            for alg in ("ista", "fista", "cp"):
                 for ratio in PAPER_RATIOS:
                     base = None
                     for test, dyn in PAPER_STRATEGIES:

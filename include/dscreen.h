@@ -50,7 +50,7 @@ typedef enum {
     DS_PENDING = 7            /* (ds_server_poll only) the request has not completed yet */
 } ds_status;
 
-typedef enum { DS_ISTA = 0, DS_FISTA = 1 } ds_alg; /* Table 1 rows */
+typedef enum { DS_ISTA = 0, DS_FISTA = 1, DS_CP = 2 } ds_alg; /* Table 1 rows (DS_CP: Chambolle-Pock) */
 
 typedef enum {
     DS_TEST_NONE = 0,
@@ -81,6 +81,12 @@ typedef struct {
     int warm_start;      /* ds_solve_path: 1 starts each lambda from the previous lambda's solution (a
                             regularization path; the screening tests of each lambda stay those of its own
                             dual problem, so they remain safe); 0 (default) starts every lambda from x0 */
+    double cp_tau;       /* DS_CP (Table 1): tau_0 and sigma_0 of the primal and dual steps (<= 0: 0.99 / sqrt(L)
+                            each, so that tau_0 sigma_0 ||D||^2 < 1); the dual iterate starts at 0 */
+    double cp_sigma;
+    double cp_gamma;     /* DS_CP: gamma >= 0 of phi_t = 1 / sqrt(1 + 2 gamma tau_{t-1}); 0 (default) keeps
+                            phi_t = 1 (the Lasso's penalty is not strongly convex: a positive gamma drives
+                            tau_t to 0) */
 } ds_options;
 
 typedef struct {

@@ -25,14 +25,15 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALGS = {"ista": 0, "fista": 1}
+ALGS = {"ista": 0, "fista": 1, "cp": 2}
 TESTS = {"none": 0, "safe": 1, "dst3": 2, "dome": 3, "gsafe": 4, "dgst3": 5}
 HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
 
 
 class _Options(ctypes.Structure):
     _fields_ = [("alg", ctypes.c_int), ("test", ctypes.c_int), ("dynamic", ctypes.c_int),
-                ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double)]
+                ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
+                ("cp_tau", ctypes.c_double), ("cp_sigma", ctypes.c_double), ("cp_gamma", ctypes.c_double)]
 
 
 class _Result(ctypes.Structure):
@@ -138,14 +139,15 @@ def dome_max(dc0, t, psi, R):
 
 
 def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynamic=True,
-          tol=1e-6, max_iter=1000, L=None, x0=None):
-    """Solve eq. (1) with Algorithm 3.  Returns a dict with x, scr_iter, hist and scalars."""
+          tol=1e-6, max_iter=1000, L=None, x0=None, cp_tau=0.0, cp_sigma=0.0, cp_gamma=0.0):
+    """Solve eq. (1) with Algorithm 3 and the ISTA, FISTA or Chambolle-Pock ("cp") update of Table 1.
+    Returns a dict with x, scr_iter, hist and scalars."""
     lib = _load()
     D, N, K, ld = _dict(D)
     y = np.ascontiguousarray(y, dtype=np.float64)
     goff, w, nG = _groups(groups, weights)
     opt = _Options(ALGS[alg], TESTS[test], 1 if dynamic else 0, int(max_iter), float(tol),
-                   float(L) if L is not None else 0.0)
+                   float(L) if L is not None else 0.0, float(cp_tau), float(cp_sigma), float(cp_gamma))
     x = np.zeros(K)
     scr = np.zeros(K, dtype=np.int32)
     hist = np.zeros((max(int(max_iter), 1), len(HIST_COLS)))

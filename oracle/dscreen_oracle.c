@@ -16,7 +16,7 @@
  *   Group-Lasso     eq. (group-lasso), Omega = sum_g w_g ||x_g||_2,
  *                   prox = group soft threshold (eq. gr_softTh)
  *   lambda_*        Sec. 2.2.2 (Lasso: ||D^T y||_inf), eq. (gstar) (groups)
- *   updates         Table 1 (ISTA and FISTA rows)
+ *   updates         Table 1 (ISTA, FISTA and Chambolle-Pock rows)
  *   general loop    Algorithm 3 (screen after each update, cumulative set)
  *   dual scaling    Lemma 8 (feasible scaled dual point closest to y/lambda)
  *   tests           Lemma 2 (SAFE), Lemma 3 (DST3), Lemma 4 (dynamic Dome),
@@ -67,6 +67,7 @@
 
 #define OR_ISTA 0
 #define OR_FISTA 1
+#define OR_CP 2 /* Chambolle-Pock (Table 1) */
 
 #define OR_TEST_NONE 0
 #define OR_TEST_SAFE 1
@@ -93,6 +94,9 @@ typedef struct {
     int max_iter;       /* iteration cap */
     double tol_gap_rel; /* stop when gap <= tol * 1/2 ||y||^2; 0 runs max_iter iterations */
     double L;           /* step constant; <= 0: power iteration on D^T D, * (1 + 1e-6) */
+    double cp_tau;      /* Chambolle-Pock tau_0 and sigma_0 (<= 0: 0.99 / sqrt(L) each, so that */
+    double cp_sigma;    /*   tau_0 sigma_0 ||D||^2 < 1) and gamma >= 0 (0: phi_t = 1 throughout) */
+    double cp_gamma;
 } or_options;
 
 typedef struct {
@@ -530,19 +534,29 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
     }
 
     double l = 1.0; /* FISTA l_0 */
+    const int cp = opt->alg == OR_CP;
+    /* Chambolle-Pock: theta_0 = 0 (dual start), tau_0, sigma_0, gamma (Table 1) */
+    double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.99 / sqrt(L);
+    double sigma = opt->cp_sigma > 0 ? opt->cp_sigma : 0.99 / sqrt(L);
+    const double gamma = opt->cp_gamma > 0 ? opt->cp_gamma : 0.0;
+    if (cp)
+        for (int64_t n = 0; n < N; n++) theta[n] = 0.0;
     int it;
     double gap = INFINITY, primal = 0.0, dual = 0.0;
     res->status = 1;
     for (it = 1; it <= opt->max_iter; it++) {
-        /* Table 1: theta_t = D_{t-1} ubar_{t-1} - y */
-        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];
+        /* Table 1: theta_t = D_{t-1} ubar_{t-1} - y (ISTA, FISTA);
+         * Chambolle-Pock: theta_t = (theta_{t-1} + sigma_{t-1} (D_{t-1} ubar_{t-1} - y)) / (1 + sigma_{t-1}) */
+        for (int64_t n = 0; n < N; n++) r[n] = -y[n];
         for (int64_t g = 0; g < G; g++) {
             if (!act[g]) continue;
             for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++)
                 if (u[i] != 0.0)
-                    for (int64_t n = 0; n < N; n++) theta[n] += D[i * ld + n] * u[i];
+                    for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * u[i];
         }
-        /* z_t = D_{t-1}^T theta_t and the proximal step x_t = prox(ubar - z/L) */
+        for (int64_t n = 0; n < N; n++) theta[n] = cp ? (theta[n] + sigma * r[n]) / (1.0 + sigma) : r[n];
+        /* z_t = D_{t-1}^T theta_t and the proximal step x_t = prox_{lambda/L}(ubar - z/L)
+         * (Chambolle-Pock: x_t = prox_{lambda tau_{t-1}}(xbar_{t-1} - tau_{t-1} z)) */
         double m = 0.0;
         for (int64_t g = 0; g < G; g++) {
             if (!act[g]) continue;
@@ -550,18 +564,25 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
             for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
                 z[i] = col_dot(D, ld, i, theta, N);
                 q += z[i] * z[i];
-                v[i] = u[i] - z[i] / L;
+                v[i] = cp ? x[i] - tau * z[i] : u[i] - z[i] / L;
             }
             double val = sqrt(q) / g_w(w, g);
             if (val > m) m = val;
-            prox_group(&c, g, v, lambda / L, xn);
+            prox_group(&c, g, v, cp ? lambda * tau : lambda / L, xn);
         }
-        /* FISTA: l_t and u_t = x_t + ((l_{t-1} - 1) / l_t)(x_t - xbar_{t-1}); ISTA: u_t = x_t */
+        /* FISTA: l_t and u_t = x_t + ((l_{t-1} - 1) / l_t)(x_t - xbar_{t-1}); ISTA: u_t = x_t;
+         * Chambolle-Pock: phi_t = 1 / sqrt(1 + 2 gamma tau_{t-1}), tau_t = phi_t tau_{t-1},
+         * sigma_t = sigma_{t-1} / phi_t, u_t = x_t + phi_t (x_t - xbar_{t-1}) */
         double beta = 0.0;
         if (opt->alg == OR_FISTA) {
             double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));
             beta = (l - 1.0) / ln;
             l = ln;
+        } else if (cp) {
+            const double phi = 1.0 / sqrt(1.0 + 2.0 * gamma * tau);
+            tau *= phi;
+            sigma /= phi;
+            beta = phi;
         }
         for (int64_t g = 0; g < G; g++) {
             if (!act[g]) continue;

@@ -40,8 +40,9 @@ ds_status ensure_io(ds_ctx* ctx, size_t bytes)
 
 bool valid_opt(const ds_options* o)
 {
-    return o && (o->alg == DS_ISTA || o->alg == DS_FISTA) && o->test >= DS_TEST_NONE && o->test <= DS_DGST3 &&
-           o->max_iter >= 1 && o->tol_gap_rel >= 0.0 && std::isfinite(o->tol_gap_rel);
+    return o && (o->alg == DS_ISTA || o->alg == DS_FISTA || o->alg == DS_CP) && o->test >= DS_TEST_NONE &&
+           o->test <= DS_DGST3 && o->max_iter >= 1 && o->tol_gap_rel >= 0.0 && std::isfinite(o->tol_gap_rel) &&
+           std::isfinite(o->cp_tau) && std::isfinite(o->cp_sigma) && o->cp_gamma >= 0.0 && std::isfinite(o->cp_gamma);
 }
 
 }  // namespace
@@ -123,6 +124,9 @@ ds_status ds_options_default(ds_options* opt)
     opt->lowp_switch = 0.0;
     opt->batch_multi_rhs = 1;
     opt->warm_start = 0;
+    opt->cp_tau = 0.0;
+    opt->cp_sigma = 0.0;
+    opt->cp_gamma = 0.0;
     return DS_OK;
 }
 

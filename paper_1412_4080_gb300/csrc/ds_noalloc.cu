@@ -78,7 +78,7 @@ extern "C" ds_status ds_solve_lasso_noalloc(int device, void* cuda_stream, const
 {
     if (!D || !y || !x_out || !opt || !res || N <= 0 || K <= 0 || ld < N) return DS_ERR_INVALID;
     if (!(lambda > 0.0) || !(opt->L > 0.0) || opt->max_iter < 1 || !(opt->tol_gap_rel >= 0.0)) return DS_ERR_INVALID;
-    if (opt->alg != DS_ISTA && opt->alg != DS_FISTA) return DS_ERR_INVALID;
+    if (opt->alg != DS_ISTA && opt->alg != DS_FISTA && opt->alg != DS_CP) return DS_ERR_INVALID;
     if (opt->test < DS_TEST_NONE || opt->test > DS_DGST3) return DS_ERR_INVALID;
     if (N > kNoAllocMaxN || K > kNoAllocMaxK) {
         fprintf(stderr, "ds_solve_lasso_noalloc: N=%lld K=%lld exceeds the fixed scratch limits N<=%lld K<=%lld\n",

@@ -83,6 +83,7 @@ struct SolveP {
     const double* lambdas;  // device copy
     int lambda_rel;
     int alg, test, dynamic, max_iter, warm_start;
+    double cp_tau0, cp_sigma0, cp_gamma;  // Chambolle-Pock (alg 2): initial steps and gamma
     double tol, L;
     T* x_out;
     long long ldx;
@@ -444,6 +445,7 @@ __device__ __noinline__ void gemv_f32(const float* D, int ld, const float* th_s,
 // memory so that it occupies no registers in the other threads.
 struct ScalarState {
     double alpha, beta, mu_nom, R2n, R2s_last, rad, lf, s_unc, sqrt_beta, gap, primal, best_gap;
+    double cp_tau, cp_sigma;  // Chambolle-Pock: tau_{t-1}, sigma_{t-1}
     long long cols_corr, cols_synth, cols_lowp;
     int iters, since_best, low, t0;  // t0: iteration at which the current FISTA sequence started
 };
@@ -479,6 +481,7 @@ struct SolveK {
     float bt_h, bt_l;      // FISTA coefficient of the iteration as a float-float pair
     float dome_f[4];  // FP32 dome test of the current iteration: R, psi, rho (rounded up), branch threshold
     T invL;
+    T cp_sig, cp_inv1ps;  // Chambolle-Pock: sigma_{t-1} and 1 / (1 + sigma_{t-1}) of the next dual update
     typename IterT<T>::type thrX;
 };
 
@@ -820,6 +823,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         }
         const bool record = (j == 0) && P.hist != nullptr;
         const bool ista = P.alg == 0;
+        const bool cp = P.alg == 2;  // Chambolle-Pock (Table 1)
         const bool dyn_test = P.dynamic && P.test != 0;
         const bool sphere = P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5;
         // FP32 dictionaries run the sphere tests in FP32: thresholds rounded down, radius rounded up
@@ -921,6 +925,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 na_own += tot & 0xfffff;
                 nzc += totc;
             }
+            if (cp)
+                for (int r = b * kRowTile + (tid / kRowTile) * G * kRowTile + tid % kRowTile; r < N;
+                     r += (kThreads / kRowTile) * G * kRowTile)
+                    W.theta[r] = T(0);
             if (tid == 0) {
                 W.c_nz[b] = nzc;
                 W.c_kg[b] = n_own;
@@ -945,6 +953,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             lf = 1.0;
             gap = best_gap = INFINITY;
             iters = since_best = t0 = 0;
+            S_.cp_tau = P.cp_tau0;
+            S_.cp_sigma = P.cp_sigma0;
+            C_.cp_sig = (T)P.cp_sigma0;
+            C_.cp_inv1ps = (T)(1.0 / (1.0 + P.cp_sigma0));
             // precision variant: bulk phase on the low-precision copy, then FP32 polish
             low = (P.lo_kind != 0 && sizeof(T) == 4) ? 1 : 0;
             cols_corr = j == 0 ? (long long)K * (need_n ? 2 : 1) : 0;
@@ -1174,7 +1186,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             acc_merge(wx, &s_red[1][k][lane]);
                         }
                         if (rv) {
-                            const T th = (T)theta_from(wu, yv);
+                            // Table 1: theta_t = D ubar_{t-1} - y; Chambolle-Pock averages it with theta_{t-1}:
+                            // theta_t = (theta_{t-1} + sigma_{t-1} (D ubar_{t-1} - y)) / (1 + sigma_{t-1})
+                            const T th = cp ? (__ldcg(W.theta + r) + C_.cp_sig * (T)theta_from(wu, yv)) * C_.cp_inv1ps
+                                            : (T)theta_from(wu, yv);
                             W.theta[r] = th;
                             pa_.add(th, yv);
                             pb_.add(th, th);
@@ -1314,7 +1329,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 if (warp == 0) {
                     // FISTA coefficient of this iteration, fetched ahead of the reductions
                     const int tf_pre = t - t0;
-                    const bool tab_pre = !ista && tf_pre >= 1 && tf_pre <= P.fista_n;
+                    const bool tab_pre = P.alg == 1 && tf_pre >= 1 && tf_pre <= P.fista_n;
                     const double bt_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1)) : 0.0;
                     const double lf_pre = tab_pre ? __ldg(P.fista + 2 * (tf_pre - 1) + 1) : 0.0;
                     // every load of the per-CTA partials is issued before any is combined
@@ -1372,7 +1387,21 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             if (P.abort_flag && (t & 15) == 0 && *P.abort_flag) stop = 1;
                         }
                         double bt = 0.0;
-                        if (!ista) {
+                        if (cp) {
+                            // Chambolle-Pock: x_t = prox_{lambda tau_{t-1}}(x_{t-1} - tau_{t-1} z), then
+                            // phi_t = 1 / sqrt(1 + 2 gamma tau_{t-1}), tau_t = phi_t tau_{t-1},
+                            // sigma_t = sigma_{t-1} / phi_t, ubar_t = x_t + phi_t (x_t - x_{t-1})
+                            const double tau = S_.cp_tau;
+                            C_.invL = (T)tau;
+                            C_.thrL = lam * tau;
+                            C_.thrX = it_cast(lam * tau, (X*)nullptr);
+                            const double phi = P.cp_gamma > 0.0 ? 1.0 / sqrt(1.0 + 2.0 * P.cp_gamma * tau) : 1.0;
+                            S_.cp_tau = phi * tau;
+                            S_.cp_sigma /= phi;
+                            C_.cp_sig = (T)S_.cp_sigma;
+                            C_.cp_inv1ps = (T)(1.0 / (1.0 + S_.cp_sigma));
+                            bt = phi;
+                        } else if (!ista) {
                             // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
                             // read from the table (the sequence depends on t only)
                             const int tf = t - t0;  // index in the current FISTA sequence
@@ -1538,7 +1567,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const bool first = k0 == 0;
                             const X uo = first ? s_pf_u[tid] : ldcg_x(uO + lo_o);
                             const X xo = first ? s_pf_x[tid] : ldcg_x(xO + lo_o);
-                            const X xv = it_soft(it_grad_step(uo, z, invL), thrX);
+                            const X xv = it_soft(it_grad_step(cp ? xo : uo, z, invL), thrX);
                             const X uv = ista ? xv : it_momentum(xv, xo, btX);
                             xW[an] = xv;
                             uW[an] = uv;
@@ -1549,7 +1578,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X v = it_grad_step(ldcg_x(uO + lo_o + q), z, invL);
+                                const X v = it_grad_step(ldcg_x((cp ? xO : uO) + lo_o + q), z, invL);
                                 zq.add(z, z);
                                 acc_sq(vq, v);
                             }
@@ -1560,7 +1589,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X xv = it_scale(it_grad_step(ldcg_x(uO + lo_o + q), z, invL), f);
+                                const X xv = it_scale(it_grad_step(ldcg_x((cp ? xO : uO) + lo_o + q), z, invL), f);
                                 const X uv = ista ? xv : it_momentum(xv, ldcg_x(xO + lo_o + q), btX);
                                 xW[an + q] = xv;
                                 uW[an + q] = uv;
@@ -1745,6 +1774,10 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.max_iter = opt ? opt->max_iter : 1;
     P.tol = opt ? opt->tol_gap_rel : 0.0;
     P.L = (opt && opt->L > 0) ? opt->L : dd.L;
+    // Chambolle-Pock steps: tau_0 sigma_0 ||D||^2 < 1 by default (0.99 / sqrt(L) each)
+    P.cp_tau0 = (opt && opt->cp_tau > 0.0) ? opt->cp_tau : 0.99 / std::sqrt(P.L);
+    P.cp_sigma0 = (opt && opt->cp_sigma > 0.0) ? opt->cp_sigma : 0.99 / std::sqrt(P.L);
+    P.cp_gamma = (opt && opt->cp_gamma > 0.0) ? opt->cp_gamma : 0.0;
     P.RA = g.RA;
     P.nchunk = g.nchunk;
     P.npad = g.npad;

@@ -265,7 +265,7 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
     std::vector<MrhsBlock> blocks;
     for (int i = 0; i < n; i++) {
         multi[i] = sizeof(T) == 4 && opt->batch_multi_rhs && !dicts[i]->is_group && opt->test <= DS_DOME &&
-                   n_rhs[i] >= 2;
+                   opt->alg != DS_CP && n_rhs[i] >= 2;
         if (!multi[i]) continue;
         // right-hand sides in order, or sorted by lambda (similar iteration counts and
         // screened sets in a block: a tighter union list and fewer idle slots)
@@ -499,7 +499,7 @@ static ds_status batch_create_cfg(ds_ctx* ctx, int n, const ds_dict* const* dict
     if (!ctx || n < 1 || !dicts || !Y || !n_rhs || !lambdas || !opt || !X_out || !out) return DS_ERR_INVALID;
     *out = nullptr;
     if (opt->max_iter < 1 || !(opt->tol_gap_rel >= 0.0) || opt->test < DS_TEST_NONE || opt->test > DS_DGST3 ||
-        (opt->alg != DS_ISTA && opt->alg != DS_FISTA) || opt->L < 0.0)
+        (opt->alg != DS_ISTA && opt->alg != DS_FISTA && opt->alg != DS_CP) || opt->L < 0.0)
         return DS_ERR_INVALID;
     const int dtype = dicts[0] ? dicts[0]->dtype : -1;
     for (int i = 0; i < n; i++) {
@@ -1147,7 +1147,7 @@ ds_status ds_server_submit(ds_server* S, const ds_dict* dict, const void* y, dou
     if (dict->dtype != DS_FP32) return DS_ERR_UNSUPPORTED;
     if (dict->N > S->max_N || dict->K > S->max_K) return DS_ERR_UNSUPPORTED;
     if (!(lambda > 0.0) || opt->max_iter < 1 || !(opt->tol_gap_rel >= 0.0) || opt->test < DS_TEST_NONE ||
-        opt->test > DS_DGST3 || (opt->alg != DS_ISTA && opt->alg != DS_FISTA) || opt->L < 0.0)
+        opt->test > DS_DGST3 || (opt->alg != DS_ISTA && opt->alg != DS_FISTA && opt->alg != DS_CP) || opt->L < 0.0)
         return DS_ERR_INVALID;
     if (dict->is_group && (opt->test == DS_SAFE || opt->test == DS_DST3 || opt->test == DS_DOME)) return DS_ERR_INVALID;
     std::lock_guard<std::mutex> lk(S->mu);

@@ -341,3 +341,66 @@ def test_warm_started_path_matches_cold_lambdas(ctx):
         assert np.linalg.norm(D @ (Xs[0][j] - Xs[1][j])) <= 2 * np.sqrt(2e-7 * 0.5 * yy) * 1.01
     assert res[1][0]["iters"] == 0 and not Xs[1][0].any()
     assert sum(r["iters"] for r in res[1]) < sum(r["iters"] for r in res[0])
+
+
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome", "none"])
+def test_chambolle_pock_matches_oracle_iterates(ctx, test):
+    """Chambolle-Pock (Table 1, gamma = 0): after a fixed number of iterations the GPU iterate
+    equals the FP64 oracle's, with screening inside every iteration (Algorithm 3)."""
+    N, K = 400, 1500
+    D, y, _ = gen.lasso_problem(N, K, seed=61, p=0.01)
+    D, y = _f32(D), _f32(y)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.5 * lm
+    L = oracle.spectral_norm_sq(D, tol=1e-10, max_iter=5000) * (1 + 1e-6)
+    tau = 0.99 / np.sqrt(L)
+    ref = oracle.solve(D, y, lam, alg="cp", test=test, tol=0, max_iter=300, L=L, cp_tau=tau, cp_sigma=tau)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32))
+    try:
+        x, r = _solve_gpu(ctx, dct, y, lam, torch.float32, K, alg="cp", test=test, tol_gap_rel=0.0, max_iter=300,
+                          L=L, cp_tau=tau, cp_sigma=tau)
+    finally:
+        ds.ds_dict_destroy(dct)
+    assert r["iters"] == 300
+    assert np.abs(x - ref["x"]).max() <= 1e-5 * np.abs(ref["x"]).max()
+    assert abs(r["gap"] - ref["gap"]) <= 1e-5 * 0.5 * float(y @ y)
+
+
+@pytest.mark.parametrize("test", ["gsafe", "dgst3"])
+def test_chambolle_pock_group_lasso_certifies_the_gap(ctx, test):
+    """Chambolle-Pock on the Group-Lasso, run to the duality gap: certified, and its objective is
+    within the tolerance of the FP64 oracle's optimum."""
+    N, K = 500, 1500
+    D, y, _, goff, w = gen.config3(62, N=N, K=K, gsize=10, n_active=4)
+    D, y = _f32(D), _f32(y)
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.4 * lm
+    ref = oracle.solve(D, y, lam, goff, w, alg="fista", test=test, tol=1e-12, max_iter=100000)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float32), goff, w)
+    try:
+        x, r = _solve_gpu(ctx, dct, y, lam, torch.float32, K, alg="cp", test=test, tol_gap_rel=1e-6, max_iter=100000)
+    finally:
+        ds.ds_dict_destroy(dct)
+    yy = float(y @ y)
+    assert r["status"] == 0 and r["gap"] <= 1e-6 * 0.5 * yy
+    xg = [x[goff[g]:goff[g + 1]] for g in range(len(w))]
+    p = 0.5 * np.sum((D @ x - y) ** 2) + lam * sum(wg * np.linalg.norm(v) for wg, v in zip(w, xg))
+    assert p - ref["primal"] <= 1.05e-6 * 0.5 * yy + 1e-9 * yy
+
+
+def test_chambolle_pock_fp64_config1(ctx):
+    """100 x 500 FP64: Chambolle-Pock with dynamic DST3 takes the oracle's iterations."""
+    D, y, _ = gen.config1(1001)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.5 * lm
+    L = oracle.spectral_norm_sq(D) * (1 + 1e-6)
+    ref = oracle.solve(D, y, lam, alg="cp", test="dst3", tol=1e-8, max_iter=100000, L=L)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D, torch.float64))
+    try:
+        x, r = _solve_gpu(ctx, dct, y, lam, torch.float64, 500, alg="cp", test="dst3", tol_gap_rel=1e-8,
+                          max_iter=100000, L=L)
+    finally:
+        ds.ds_dict_destroy(dct)
+    assert r["status"] == 0
+    assert abs(r["iters"] - ref["iters"]) <= 1
+    np.testing.assert_allclose(x, ref["x"], atol=1e-9 * np.abs(ref["x"]).max())

@@ -129,7 +129,7 @@ def test_bruteforce_and_safety_tiny(seed, test, dynamic):
     for ratio in (0.3, 0.6, 0.9):
         lam = ratio * lm
         xbf = _lasso_bruteforce(D, y, lam)
-        for alg in ("ista", "fista"):
+        for alg in ("ista", "fista", "cp"):
             r = oracle.solve(D, y, lam, alg=alg, test=test, dynamic=dynamic, tol=0, max_iter=20000)
             np.testing.assert_allclose(r["x"], xbf, atol=1e-8)
             screened = r["scr_iter"] != 0
@@ -422,3 +422,32 @@ def test_fista_rate_bound():
     ri = oracle.solve(D, y, lam, alg="ista", test="none", tol=0, max_iter=3, L=L)
     np.testing.assert_allclose(h[:2, 4], ri["hist"][:2, 4], rtol=1e-13)
     assert abs(h[2, 4] - ri["hist"][2, 4]) > 1e-10 * yy
+
+
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome"])
+def test_chambolle_pock_first_test_is_the_static_test(test):
+    """Chambolle-Pock (Table 1) starts from theta_0 = 0, so theta_1 = -sigma y / (1 + sigma) is a
+    positive multiple of -y: after the dual scaling of Lemma 8 its first dynamic test is the
+    static test of Algorithm 1, whatever sigma_0."""
+    D, y = _small_lasso(23, N=40, K=300, k=4)
+    lm, _, _ = oracle.lambda_max(D, y)
+    for ratio in (0.5, 0.8):
+        rs = oracle.solve(D, y, ratio * lm, alg="ista", test=test, dynamic=False, max_iter=1, tol=0)
+        for sig in (0.0, 0.3, 5.0):
+            rc = oracle.solve(D, y, ratio * lm, alg="cp", test=test, dynamic=True, max_iter=1, tol=0, cp_sigma=sig)
+            np.testing.assert_array_equal(rc["scr_iter"] != 0, rs["scr_iter"] != 0)
+
+
+def test_chambolle_pock_reaches_the_pinned_solution_and_gamma_stalls_it():
+    """With gamma = 0 (phi_t = 1) Chambolle-Pock converges to the minimiser pinned by the
+    KKT and brute-force tests; a positive gamma shrinks tau_t towards 0 on the Lasso (its
+    penalty is not strongly convex) and the same iteration budget no longer suffices."""
+    D, y = _small_lasso(24, N=60, K=200, k=5)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.3 * lm
+    ref = oracle.solve(D, y, lam, alg="fista", test="none", tol=1e-14, max_iter=200000)
+    r0 = oracle.solve(D, y, lam, alg="cp", test="dst3", tol=1e-12, max_iter=20000)
+    assert r0["status"] == 0
+    np.testing.assert_allclose(r0["x"], ref["x"], atol=1e-6 * np.abs(ref["x"]).max())
+    r1 = oracle.solve(D, y, lam, alg="cp", test="dst3", tol=1e-12, max_iter=20000, cp_gamma=1.0)
+    assert r1["status"] == 1
