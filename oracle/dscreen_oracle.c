@@ -23,6 +23,10 @@
  *                   Lemma 5 (GSAFE), Lemma 6 (DGST3), Lemma 7 (sphere test)
  *   static variant  Algorithm 1 / Algorithm 4 (test once at theta = -y)
  *
+ * Parity unpinned: the intermediate Chambolle-Pock iterates (the theta average and the
+ * phi, tau, sigma schedule) are pinned only through the fixed point they reach (the
+ * minimiser) and the first test (the static one); see the test suite.
+ *
  * Readings of the paper that this file takes (where the text is silent,
  * garbled or specialised):
  *  - theta follows Table 1's sign (theta = D u - y); the clip in Lemma 8
