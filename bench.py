@@ -568,7 +568,7 @@ def batched_uneven_measure(ds, ctx, dev, flush, n_inst=8, plain_per_inst=4):
                       f"{plain_per_inst} problems per instance ({cnt} solves)"}
 
 
-def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=24):
+def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=24, team_size=8):
     """Open-loop Poisson stream of mixed requests (80% Lasso / 20% Group-Lasso with
     groups of 8) on AR(1) dictionaries (rho = 0.9, unit-norm columns) of N in
     {512..2048} and K in {4096..16384}, FP32 master + FP8 e4m3 working copy with a
@@ -602,7 +602,7 @@ def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=
         Y = (S + Nz * (S.norm(dim=0) / Nz.norm(dim=0)) * 0.1).t().contiguous().cpu().numpy()
         pool.append((N, K, lasso, group, Y))
         del E, D
-    server = ds.ds_server_create(ctx, 4 << 30, 2048, 16384, 4)
+    server = ds.ds_server_create(ctx, 4 << 30, 2048, 16384, team_size)
     opts = {"lasso": ds.ds_options_default(test="dst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1),
             "group": ds.ds_options_default(test="dgst3", tol_gap_rel=TOL, max_iter=20000, lambda_rel=1)}
     # warm the server (kernel load, first launch)
@@ -662,8 +662,8 @@ def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=
             "converged": int(sum(1 for s_ in keep if s_ == 0)), "kernel_launches": st["launches"],
             "workload": "Poisson arrivals, 80% Lasso / 20% Group-Lasso (groups of 8), AR(1) rho=0.9 dictionaries "
                         "N in {512,1024,1536,2048}, K in {4096,8192,12288,16384}, lambda/lambda_max ~ U[0.1,0.9], "
-                        "FP8 e4m3 copy with per-column scale + FP32 master, gap 1e-6, FISTA + DST3/DGST3, teams of 4 "
-                        "CTAs, 4 GiB pool; plain: a sample of the same mix solved one at a time"}
+                        "FP8 e4m3 copy with per-column scale + FP32 master, gap 1e-6, FISTA + DST3/DGST3, teams of %d "
+                        "CTAs, 4 GiB pool; plain: a sample of the same mix solved one at a time" % team_size}
 
 
 def large_roofline(ds, ctx, dev, stream, peak, peak_kind):
