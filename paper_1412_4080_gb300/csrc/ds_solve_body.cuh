@@ -970,27 +970,30 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             // ============== (A) test of iteration t-1 + synthesis theta_t = D ubar_{t-1} - y, D xbar_{t-1}
             {
                 // every CTA's nonzero-list length, with the first kSpec entries fetched in the same trip
+                // (the copies are issued by warps 2.. so that warps 0 and 1 start Lemma 8 at once: slot s
+                // is issued by thread s + 64, modulo the block)
+                const int ps = (tid + kThreads - 64) % kThreads;
                 int cnz = 0;
-                if (tid < G) {
-                    cnz = __ldcg(W.c_nz + tid);
-                    const int e0 = s_alo_s[tid];
+                if (tid < G) cnz = __ldcg(W.c_nz + tid);
+                if (ps < G) {
+                    const int e0 = s_alo_s[ps];
 #pragma unroll
                     for (int q = 0; q < kSpec; q++) {
                         const int e = e0 + q;
                         if (e < K) {
-                            pf4(&s_spec[tid].col[q], W.nz_col + e);
-                            pf4(&s_spec[tid].t[q], W.nz_t + e);
-                            pf8(&s_spec[tid].u[q], W.nz_u + e);
-                            pf8(&s_spec[tid].x[q], W.nz_x + e);
+                            pf4(&s_spec[ps].col[q], W.nz_col + e);
+                            pf4(&s_spec[ps].t[q], W.nz_t + e);
+                            pf8(&s_spec[ps].u[q], W.nz_u + e);
+                            pf8(&s_spec[ps].x[q], W.nz_x + e);
                         }
                     }
                 }
-                // the own slice's test inputs and x_{t-1} (Lasso: one group per thread), for the owner test
+                // the own slice's test inputs and x_{t-1} (Lasso: one group per slot), for the owner test
                 const bool opf = !P.is_group && tid < n_own;
-                if (opf) {
-                    if (f32_sphere) pf4(&s_pf_i0[tid], W.thrc[cur] + g_lo + tid);
-                    else pf4(&s_pf_i0[tid], W.act[cur] + g_lo + tid);
-                    pf8(&s_pf_x[tid], xbuf(iO) + a_lo0 + tid);
+                if (!P.is_group && ps < n_own) {
+                    if (f32_sphere) pf4(&s_pf_i0[ps], W.thrc[cur] + g_lo + ps);
+                    else pf4(&s_pf_i0[ps], W.act[cur] + g_lo + ps);
+                    pf8(&s_pf_x[ps], xbuf(iO) + a_lo0 + ps);
                 }
                 if (t > 1 && warp <= 1) {
                     // warps 0 and 1 reduce the same per-CTA maxima of |z_{t-1}| in the same order
@@ -1057,8 +1060,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 const int exE = block_exclusive_scan(cnz, s_tmp, &totE);
                 if (tid < G) s_pref[tid] = exE;
                 if (tid == 0) s_pref[G] = totE;
+                pf_wait();  // this thread's copies have landed; the barrier below publishes them
                 const bool long_lists = __syncthreads_or(cnz > kSpec) != 0;
-                pf_wait();
                 const float radF = s_radf;
                 const double radB = s_sc[8], RsB = s_sc[9];
                 // the test of iteration t-1 on one group, from its list data (FP32 threshold or group id);
@@ -1270,12 +1273,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 // Lasso: the first round's keep flags, columns, thresholds and iterates, fetched while
                 // warps 0 and 1 reduce the partials
                 const int n0 = P.is_group ? 0 : min(n_own, P.RA);
-                if (tid < n0) {
-                    pf4(&s_pf_i0[tid], W.keep + g_lo + tid);
-                    pf4(&s_pf_i1[tid], W.act[cur] + g_lo + tid);
-                    if (f32_sphere) pf4(&s_pf_f0[tid], W.thrc[cur] + g_lo + tid);
-                    pf8(&s_pf_u[tid], ubuf(iO) + a_lo0 + tid);
-                    pf8(&s_pf_x[tid], xbuf(iO) + a_lo0 + tid);
+                {
+                    const int ps = (tid + kThreads - 64) % kThreads;  // issued by warps 2.. first
+                    if (ps < n0) {
+                        pf4(&s_pf_i0[ps], W.keep + g_lo + ps);
+                        pf4(&s_pf_i1[ps], W.act[cur] + g_lo + ps);
+                        if (f32_sphere) pf4(&s_pf_f0[ps], W.thrc[cur] + g_lo + ps);
+                        pf8(&s_pf_u[ps], ubuf(iO) + a_lo0 + ps);
+                        pf8(&s_pf_x[ps], xbuf(iO) + a_lo0 + ps);
+                    }
                 }
                 if (warp >= 2) {
                     // stage theta_t in shared memory
@@ -1427,8 +1433,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         s_si[9] = low;
                     }
                 }
+                pf_wait();  // this thread's copies have landed; the barrier below publishes them
                 __syncthreads();
-                pf_wait();
                 lowB = s_si[9] != 0;
                 if (s_si[6]) break;
                 if (tid == 0) {
