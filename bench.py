@@ -662,8 +662,8 @@ def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=
             "converged": int(sum(1 for s_ in keep if s_ == 0)), "kernel_launches": st["launches"],
             "workload": "Poisson arrivals, 80% Lasso / 20% Group-Lasso (groups of 8), AR(1) rho=0.9 dictionaries "
                         "N in {512,1024,1536,2048}, K in {4096,8192,12288,16384}, lambda/lambda_max ~ U[0.1,0.9], "
-                        "FP8 e4m3 copy with per-column scale + FP32 master, gap 1e-6, FISTA + DST3/DGST3, teams of %d "
-                        "CTAs, 4 GiB pool; plain: a sample of the same mix solved one at a time" % team_size}
+                        "FP8 e4m3 copy with per-column scale + FP32 master, gap 1e-6, FISTA + DST3/DGST3, teams of "
+                        + str(team_size) + " CTAs, 4 GiB pool; plain: a sample of the same mix solved one at a time"}
 
 
 def large_roofline(ds, ctx, dev, stream, peak, peak_kind):
