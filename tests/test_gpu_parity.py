@@ -404,3 +404,37 @@ def test_chambolle_pock_fp64_config1(ctx):
     assert r["status"] == 0
     assert abs(r["iters"] - ref["iters"]) <= 1
     np.testing.assert_allclose(x, ref["x"], atol=1e-9 * np.abs(ref["x"]).max())
+
+
+def test_bench_workload_full_size_certified_in_fp64(ctx):
+    """The benchmark's own workload at full size (2000 x 10000, seed 1002, the three tests x five
+    lambdas, in the bench's launch configuration: one path per test): every solution is
+    certified independently of the kernel's report, by an FP64 duality gap computed here from
+    the returned x with the dual point (y - D x) / lambda scaled into the feasible set."""
+    D, y, _ = gen.config2(1002)
+    D32, y32 = D.astype(np.float32), y.astype(np.float32)
+    D64, y64 = D32.astype(np.float64), y32.astype(np.float64)
+    yy = float(y64 @ y64)
+    ratios = np.array(gen.CONFIG2_RATIOS)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D64, torch.float32))
+    try:
+        yt = torch.from_numpy(y32).cuda()
+        for test in ("safe", "dst3", "dome"):
+            X = torch.empty((ratios.size, D.shape[1]), device="cuda")
+            o = ds.ds_options_default(test=test, tol_gap_rel=1e-6, max_iter=20000, lambda_rel=1)
+            res = ds.ds_solve_path(ctx, dct, yt, ratios, o, X)
+            Xh = X.double().cpu().numpy()
+            for j, r in enumerate(res):
+                assert r["status"] == 0 and r["gap"] <= 1e-6 * 0.5 * yy, (test, j, r)
+                lam = r["lambda"]
+                x = Xh[j]
+                res64 = y64 - D64 @ x
+                primal = 0.5 * res64 @ res64 + lam * np.abs(x).sum()
+                theta = res64 / lam
+                theta *= min(1.0, 1.0 / np.abs(D64.T @ theta).max())
+                dual = 0.5 * yy - 0.5 * lam * lam * np.sum((theta - y64 / lam) ** 2)
+                # the FP32 rounding of the returned x adds a little to the kernel's certified gap
+                assert primal - dual <= 1.2e-6 * 0.5 * yy, (test, j, (primal - dual) / (0.5 * yy))
+                assert abs(lam - ratios[j] * r["lambda_max"]) <= 1e-12 * lam
+    finally:
+        ds.ds_dict_destroy(dct)
