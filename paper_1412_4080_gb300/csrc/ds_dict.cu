@@ -160,6 +160,33 @@ __global__ void max_kernel(const double* __restrict__ v, int n, double* out)
 
 // ---------------------------------------------------------------- Lanczos
 
+__device__ __forceinline__ float lz_dot(float4 a, float4 b, float s)
+{
+    s = fmaf(a.x, b.x, s);
+    s = fmaf(a.y, b.y, s);
+    s = fmaf(a.z, b.z, s);
+    return fmaf(a.w, b.w, s);
+}
+__device__ __forceinline__ double lz_dot(double2 a, double2 b, double s) { return fma(a.y, b.y, fma(a.x, b.x, s)); }
+__device__ __forceinline__ float4 lz_zero(float4*) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ double2 lz_zero(double2*) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float4 vaxpy(float a, float4 d, float4 acc)
+{
+    return make_float4(fmaf(a, d.x, acc.x), fmaf(a, d.y, acc.y), fmaf(a, d.z, acc.z), fmaf(a, d.w, acc.w));
+}
+__device__ __forceinline__ double2 vaxpy(double a, double2 d, double2 acc)
+{
+    return make_double2(fma(a, d.x, acc.x), fma(a, d.y, acc.y));
+}
+__device__ __forceinline__ void vstore_parts(double* row, int v, float4 a)
+{
+    row[4 * v] = a.x; row[4 * v + 1] = a.y; row[4 * v + 2] = a.z; row[4 * v + 3] = a.w;
+}
+__device__ __forceinline__ void vstore_parts(double* row, int v, double2 a)
+{
+    row[2 * v] = a.x; row[2 * v + 1] = a.y;
+}
+
 template <typename T>
 struct LzP {
     const T* D;
@@ -169,15 +196,24 @@ struct LzP {
     double* qp;        // N, previous q_{k-1}
     double* wv;        // N, work vector
     T* p;              // K, D^T q
-    double* wpart;     // nseg x N partial products
-    double* part;      // G partials
+    double* wpart;     // G x ld partial products D p (one row per CTA)
+    double* part;      // 2 G partials (q^T w, ||w||^2)
     double* alpha;     // steps
     double* beta;      // steps
-    int nseg;
+    int nseg;          // rows of wpart (= G)
     GridBarrier* bar;
     int* err;
 };
 
+// One Lanczos step on D D^T per iteration k (three-term recurrence, FP64 vectors):
+//   (1) every CTA owns the columns [b K/G, (b+1) K/G): it computes p_i = d_i^T q_k for them
+//       (a warp per column, q staged in shared memory) and, from the same columns, its
+//       partial D p over all rows (a thread per 4-row vector, FP32 products);
+//   (2) each CTA sums the partials of its own rows in CTA order, subtracts beta_{k-1} q_{k-1},
+//       and forms its partials of q_k^T w and ||w||^2;
+//   (3) alpha_k = q_k^T w, beta_k^2 = ||w||^2 - alpha_k^2 (q_k has unit norm), and the next
+//       vector q_{k+1} = (w - alpha_k q_k) / beta_k on the CTA's rows.
+// Three grid barriers per step; every reduction has a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P)
 {
@@ -185,108 +221,77 @@ __global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P
     constexpr int EV = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* q_s = reinterpret_cast<T*>(smem_raw);
-    __shared__ double s_red[32];
+    __shared__ double s_red[2][32];
     __shared__ double s_sc[4];
-    __shared__ T s_acc[kDictThreads / 32][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kDictThreads / 32;
     const int b = blockIdx.x, G = gridDim.x;
     unsigned int gen = 0;
     const int N = P.N, K = P.K, ld = P.ld, ldv = ld / EV;
-    const int ntiles = (N + 31) / 32;
+    const int c_lo = (int)((long long)b * K / G), c_hi = (int)((long long)(b + 1) * K / G);
+    const int r_lo = (int)((long long)b * N / G), r_hi = (int)((long long)(b + 1) * N / G);
+    T* p_s = q_s + ldv * EV;  // p_i of the own columns
     for (int k = P.k0; k < P.k1; k++) {
-        // p = D^T q_k
+        // (1) p = D^T q_k on the own columns, then the partial D p over all rows
         for (int r = tid; r < ldv * EV; r += kDictThreads) q_s[r] = r < N ? (T)__ldcg(P.q + r) : T(0);
         __syncthreads();
         const V* qv = reinterpret_cast<const V*>(q_s);
-        for (int i = b * nw + warp; i < K; i += G * nw) {
+        for (int i = c_lo + warp; i < c_hi; i += nw) {
             const V* col = reinterpret_cast<const V*>(P.D + (size_t)i * ld);
             T s = T(0);
-            for (int v = lane; v < ldv; v += 32) {
-                V d = __ldg(col + v);
-                V qq = qv[v];
-                if constexpr (EV == 4) {
-                    s = fmaf(d.x, qq.x, s); s = fmaf(d.y, qq.y, s); s = fmaf(d.z, qq.z, s); s = fmaf(d.w, qq.w, s);
-                } else {
-                    s = fma(d.x, qq.x, s); s = fma(d.y, qq.y, s);
-                }
-            }
+            for (int v = lane; v < ldv; v += 32) s = lz_dot(__ldg(col + v), qv[v], s);
             s = warp_sum(s);
-            if (lane == 0) P.p[i] = s;
+            if (lane == 0) p_s[i - c_lo] = s;
+        }
+        __syncthreads();
+        for (int v = tid; v < ldv; v += kDictThreads) {
+            V acc = lz_zero((V*)nullptr);
+            int i = c_lo;
+            for (; i + 4 <= c_hi; i += 4) {
+                V d[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) d[u] = __ldg(reinterpret_cast<const V*>(P.D + (size_t)(i + u) * ld) + v);
+#pragma unroll
+                for (int u = 0; u < 4; u++) acc = vaxpy(p_s[i + u - c_lo], d[u], acc);
+            }
+            for (; i < c_hi; i++) acc = vaxpy(p_s[i - c_lo], __ldg(reinterpret_cast<const V*>(P.D + (size_t)i * ld) + v), acc);
+            vstore_parts(P.wpart + (size_t)b * ld, v, acc);
         }
         if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
-        // partial w = D p over (row tile, column segment)
-        for (int item = b; item < ntiles * P.nseg; item += G) {
-            const int tile = item % ntiles, seg = item / ntiles;
-            const int r = tile * 32 + lane;
-            const int cs = (int)((long long)seg * K / P.nseg), ce = (int)((long long)(seg + 1) * K / P.nseg);
-            T acc = T(0);
-            for (int i = cs + warp; i < ce; i += nw) {
-                T pi = __ldcg(P.p + i);
-                T d = r < N ? __ldg(P.D + (size_t)i * ld + r) : T(0);
-                acc = fma(pi, d, acc);
-            }
-            s_acc[warp][lane] = acc;
-            __syncthreads();
-            if (warp == 0 && r < N) {
-                double s = 0.0;
-                for (int k2 = 0; k2 < nw; k2++) s += (double)s_acc[k2][lane];
-                P.wpart[(size_t)seg * N + r] = s;
-            }
-            __syncthreads();
-        }
-        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
-        // w = sum of partials - beta_{k-1} q_{k-1};  alpha = q^T w
+        // (2) w = sum of the partials - beta_{k-1} q_{k-1} on the own rows; partials of q^T w and ||w||^2
         const double bprev = k > 0 ? P.beta[k - 1] : 0.0;
-        double pa = 0.0;
-        for (int r = b * kDictThreads + tid; r < N; r += G * kDictThreads) {
+        double pa = 0.0, pw = 0.0;
+        for (int r = r_lo + tid; r < r_hi; r += kDictThreads) {
             double s = 0.0;
-            for (int sg = 0; sg < P.nseg; sg++) s += __ldcg(P.wpart + (size_t)sg * N + r);
+            for (int sg = 0; sg < G; sg++) s += __ldcg(P.wpart + (size_t)sg * ld + r);
             s -= bprev * __ldcg(P.qp + r);
             P.wv[r] = s;
             pa += s * __ldcg(P.q + r);
+            pw += s * s;
         }
         pa = warp_sum(pa);
-        if (lane == 0) s_red[warp] = pa;
+        pw = warp_sum(pw);
+        if (lane == 0) { s_red[0][warp] = pa; s_red[1][warp] = pw; }
         __syncthreads();
         if (tid == 0) {
-            double t = 0.0;
-            for (int k2 = 0; k2 < nw; k2++) t += s_red[k2];
-            P.part[b] = t;
+            double ta = 0.0, tw = 0.0;
+            for (int k2 = 0; k2 < nw; k2++) { ta += s_red[0][k2]; tw += s_red[1][k2]; }
+            P.part[b] = ta;
+            P.part[G + b] = tw;
         }
         if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
+        // (3) alpha_k, beta_k and q_{k+1}
         if (warp == 0) {
-            double a = warp_sum_fixed(P.part, G, lane);
-            if (lane == 0) s_sc[0] = a;
+            const double a = warp_sum_fixed(P.part, G, lane);
+            const double ww = warp_sum_fixed(P.part + G, G, lane);
+            if (lane == 0) { s_sc[0] = a; s_sc[1] = sqrt(fmax(ww - a * a, 0.0)); }
         }
         __syncthreads();
-        const double alpha = s_sc[0];
-        double pb = 0.0;
-        for (int r = b * kDictThreads + tid; r < N; r += G * kDictThreads) {
-            double s = __ldcg(P.wv + r) - alpha * __ldcg(P.q + r);
-            P.wv[r] = s;
-            pb += s * s;
-        }
-        pb = warp_sum(pb);
-        __syncthreads();
-        if (lane == 0) s_red[warp] = pb;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int k2 = 0; k2 < nw; k2++) t += s_red[k2];
-            P.part[b] = t;
-        }
-        if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
-        if (warp == 0) {
-            double bt = sqrt(warp_sum_fixed(P.part, G, lane));
-            if (lane == 0) s_sc[1] = bt;
-        }
-        __syncthreads();
-        const double beta = s_sc[1];
+        const double alpha = s_sc[0], beta = s_sc[1];
         if (b == 0 && tid == 0) { P.alpha[k] = alpha; P.beta[k] = beta; }
-        for (int r = b * kDictThreads + tid; r < N; r += G * kDictThreads) {
-            double qk = __ldcg(P.q + r);
+        for (int r = r_lo + tid; r < r_hi; r += kDictThreads) {
+            const double qk = __ldcg(P.q + r);
             P.qp[r] = qk;
-            P.q[r] = beta > 0.0 ? __ldcg(P.wv + r) / beta : 0.0;
+            P.q[r] = beta > 0.0 ? (__ldcg(P.wv + r) - alpha * qk) / beta : 0.0;
         }
         if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
         if (!(beta > 0.0)) return;  // invariant subspace: T_k is exact
@@ -350,14 +355,13 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
 {
     const int N = (int)dict->N, K = (int)dict->K, ld = (int)dict->ld;
     const int G = ctx->num_sms;
-    const int ntiles = (N + 31) / 32;
-    const int nseg = std::max(1, std::min(64, G / std::max(1, ntiles)));
+    const int nseg = G;  // one partial of D p per CTA
     const int maxsteps = std::min(N, 320);
     // workspace
     size_t bytes = 0;
     auto sz = [&](size_t n) { bytes = align_up(bytes, 256) + n; };
-    sz(sizeof(GridBarrier)); sz(8 * N); sz(8 * N); sz(8 * N); sz(sizeof(T) * K); sz(8ull * nseg * N);
-    sz(8 * G); sz(8 * maxsteps); sz(8 * maxsteps); sz(sizeof(int));
+    sz(sizeof(GridBarrier)); sz(8 * N); sz(8 * N); sz(8 * N); sz(sizeof(T) * K); sz(8ull * nseg * ld);
+    sz(16 * G); sz(8 * maxsteps); sz(8 * maxsteps); sz(sizeof(int));
     ds_status st = ctx_reserve(ctx, bytes + 256);
     if (st != DS_OK) return st;
     char* base = reinterpret_cast<char*>(ctx->ws);
@@ -371,8 +375,8 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
     P.qp = (double*)take(8 * N);
     P.wv = (double*)take(8 * N);
     P.p = (T*)take(sizeof(T) * K);
-    P.wpart = (double*)take(8ull * nseg * N);
-    P.part = (double*)take(8 * G);
+    P.wpart = (double*)take(8ull * nseg * ld);
+    P.part = (double*)take(16 * G);
     P.alpha = (double*)take(8 * maxsteps);
     P.beta = (double*)take(8 * maxsteps);
     P.err = (int*)take(sizeof(int));
@@ -392,7 +396,7 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
     if (cudaMemcpyAsync(P.q, q0.data(), 8 * N, cudaMemcpyHostToDevice, s) != cudaSuccess) return DS_ERR_CUDA;
     if (cudaMemsetAsync(P.qp, 0, 8 * N, s) != cudaSuccess) return DS_ERR_CUDA;
     if (cudaMemsetAsync(P.err, 0, sizeof(int), s) != cudaSuccess) return DS_ERR_CUDA;
-    size_t smem = (size_t)ld * sizeof(T) + 16;
+    size_t smem = (size_t)ld * sizeof(T) + sizeof(T) * ((size_t)K / G + 2) + 16;
     if (smem > ctx->smem_optin - 16 * 1024) return DS_ERR_UNSUPPORTED;
     cudaFuncSetAttribute(lanczos_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     std::vector<double> a, bb;
