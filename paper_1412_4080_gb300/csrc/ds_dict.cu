@@ -192,9 +192,8 @@ struct LzP {
     const T* D;
     int N, K, ld;
     int k0, k1;        // steps to run
-    double* q;         // N, current Lanczos vector q_k
-    double* qp;        // N, previous q_{k-1}
-    double* wv;        // N, work vector
+    double* q;         // N, Lanczos vector q_k (q_0 on entry; each CTA rewrites its own rows)
+    double* wv;        // N, w, then the unnormalised next vector v_{k+1}
     T* p;              // K, D^T q
     double* wpart;     // G x ld partial products D p (one row per CTA)
     double* part;      // 2 G partials (q^T w, ||w||^2)
@@ -206,14 +205,14 @@ struct LzP {
 };
 
 // One Lanczos step on D D^T per iteration k (three-term recurrence, FP64 vectors):
-//   (1) every CTA owns the columns [b K/G, (b+1) K/G): it computes p_i = d_i^T q_k for them
-//       (a warp per column, q staged in shared memory) and, from the same columns, its
-//       partial D p over all rows (a thread per 4-row vector, FP32 products);
-//   (2) each CTA sums the partials of its own rows in CTA order, subtracts beta_{k-1} q_{k-1},
-//       and forms its partials of q_k^T w and ||w||^2;
-//   (3) alpha_k = q_k^T w, beta_k^2 = ||w||^2 - alpha_k^2 (q_k has unit norm), and the next
-//       vector q_{k+1} = (w - alpha_k q_k) / beta_k on the CTA's rows.
-// Three grid barriers per step; every reduction has a fixed order.
+//   (1) beta_{k-1} = ||v_k|| from the partials of the previous step, q_k = v_k / beta_{k-1}
+//       staged in shared memory; every CTA owns the columns [b K/G, (b+1) K/G): it computes
+//       p_i = d_i^T q_k for them (a warp per column) and, from the same columns, its partial
+//       D p over all rows (a thread per 4-row vector, FP32 products);
+//   (2) on its own rows: q_k stored, w = sum of the partials (CTA order) - beta_{k-1} q_{k-1},
+//       partials of alpha_k = q_k^T w;
+//   (3) v_{k+1} = w - alpha_k q_k on its own rows, partials of ||v_{k+1}||^2.
+// Three grid barriers per step; every reduction has a fixed order.  (q_0 is given in q, unit.)
 template <typename T>
 __global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P)
 {
@@ -221,7 +220,7 @@ __global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P
     constexpr int EV = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* q_s = reinterpret_cast<T*>(smem_raw);
-    __shared__ double s_red[2][32];
+    __shared__ double s_red[32];
     __shared__ double s_sc[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kDictThreads / 32;
     const int b = blockIdx.x, G = gridDim.x;
@@ -231,8 +230,18 @@ __global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P
     const int r_lo = (int)((long long)b * N / G), r_hi = (int)((long long)(b + 1) * N / G);
     T* p_s = q_s + ldv * EV;  // p_i of the own columns
     for (int k = P.k0; k < P.k1; k++) {
-        // (1) p = D^T q_k on the own columns, then the partial D p over all rows
-        for (int r = tid; r < ldv * EV; r += kDictThreads) q_s[r] = r < N ? (T)__ldcg(P.q + r) : T(0);
+        // (1) beta_{k-1}, q_k; p = D^T q_k on the own columns, then the partial D p over all rows
+        if (warp == 0) {
+            const double bt = k > 0 ? sqrt(warp_sum_fixed(P.part + G, G, lane)) : 0.0;
+            if (lane == 0) s_sc[1] = bt;
+        }
+        __syncthreads();
+        const double bprev = s_sc[1];
+        if (k > 0 && b == 0 && tid == 0) P.beta[k - 1] = bprev;
+        if (k > 0 && !(bprev > 0.0)) return;  // invariant subspace: T_{k-1} is exact (every CTA agrees)
+        const double inv_b = k > 0 ? 1.0 / bprev : 1.0;
+        const double* src = k > 0 ? P.wv : P.q;
+        for (int r = tid; r < ldv * EV; r += kDictThreads) q_s[r] = r < N ? (T)(__ldcg(src + r) * inv_b) : T(0);
         __syncthreads();
         const V* qv = reinterpret_cast<const V*>(q_s);
         for (int i = c_lo + warp; i < c_hi; i += nw) {
@@ -257,44 +266,56 @@ __global__ void __launch_bounds__(kDictThreads, 1) lanczos_kernel(const LzP<T> P
             vstore_parts(P.wpart + (size_t)b * ld, v, acc);
         }
         if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
-        // (2) w = sum of the partials - beta_{k-1} q_{k-1} on the own rows; partials of q^T w and ||w||^2
-        const double bprev = k > 0 ? P.beta[k - 1] : 0.0;
-        double pa = 0.0, pw = 0.0;
+        // (2) own rows: q_k, w = sum of the partials - beta_{k-1} q_{k-1}, partials of q_k^T w
+        double pa = 0.0;
         for (int r = r_lo + tid; r < r_hi; r += kDictThreads) {
+            const double qk = k > 0 ? __ldcg(P.wv + r) * inv_b : __ldcg(P.q + r);
+            const double qm = k > 0 ? __ldcg(P.q + r) : 0.0;  // q_{k-1}
             double s = 0.0;
             for (int sg = 0; sg < G; sg++) s += __ldcg(P.wpart + (size_t)sg * ld + r);
-            s -= bprev * __ldcg(P.qp + r);
+            s -= bprev * qm;
+            P.q[r] = qk;
             P.wv[r] = s;
-            pa += s * __ldcg(P.q + r);
-            pw += s * s;
+            pa += s * qk;
         }
         pa = warp_sum(pa);
-        pw = warp_sum(pw);
-        if (lane == 0) { s_red[0][warp] = pa; s_red[1][warp] = pw; }
+        if (lane == 0) s_red[warp] = pa;
         __syncthreads();
         if (tid == 0) {
-            double ta = 0.0, tw = 0.0;
-            for (int k2 = 0; k2 < nw; k2++) { ta += s_red[0][k2]; tw += s_red[1][k2]; }
+            double ta = 0.0;
+            for (int k2 = 0; k2 < nw; k2++) ta += s_red[k2];
             P.part[b] = ta;
-            P.part[G + b] = tw;
         }
         if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
-        // (3) alpha_k, beta_k and q_{k+1}
+        // (3) alpha_k; v_{k+1} = w - alpha_k q_k on the own rows, partials of ||v_{k+1}||^2
         if (warp == 0) {
             const double a = warp_sum_fixed(P.part, G, lane);
-            const double ww = warp_sum_fixed(P.part + G, G, lane);
-            if (lane == 0) { s_sc[0] = a; s_sc[1] = sqrt(fmax(ww - a * a, 0.0)); }
+            if (lane == 0) s_sc[0] = a;
         }
         __syncthreads();
-        const double alpha = s_sc[0], beta = s_sc[1];
-        if (b == 0 && tid == 0) { P.alpha[k] = alpha; P.beta[k] = beta; }
+        const double alpha = s_sc[0];
+        if (b == 0 && tid == 0) P.alpha[k] = alpha;
+        double pb = 0.0;
         for (int r = r_lo + tid; r < r_hi; r += kDictThreads) {
-            const double qk = __ldcg(P.q + r);
-            P.qp[r] = qk;
-            P.q[r] = beta > 0.0 ? (__ldcg(P.wv + r) - alpha * qk) / beta : 0.0;
+            const double v = __ldcg(P.wv + r) - alpha * __ldcg(P.q + r);
+            P.wv[r] = v;
+            pb += v * v;
+        }
+        pb = warp_sum(pb);
+        __syncthreads();
+        if (lane == 0) s_red[warp] = pb;
+        __syncthreads();
+        if (tid == 0) {
+            double tb = 0.0;
+            for (int k2 = 0; k2 < nw; k2++) tb += s_red[k2];
+            P.part[G + b] = tb;
         }
         if (!grid_sync(P.bar, G, gen)) { if (tid == 0) *P.err = 1; return; }
-        if (!(beta > 0.0)) return;  // invariant subspace: T_k is exact
+    }
+    // beta of the last step of this launch (the next launch recomputes it from the same partials)
+    if (b == 0 && warp == 0) {
+        const double bt = sqrt(warp_sum_fixed(P.part + G, G, lane));
+        if (lane == 0) P.beta[P.k1 - 1] = bt;
     }
 }
 
@@ -372,7 +393,6 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
     P.N = N; P.K = K; P.ld = ld;
     P.bar = (GridBarrier*)take(sizeof(GridBarrier));
     P.q = (double*)take(8 * N);
-    P.qp = (double*)take(8 * N);
     P.wv = (double*)take(8 * N);
     P.p = (T*)take(sizeof(T) * K);
     P.wpart = (double*)take(8ull * nseg * ld);
@@ -394,7 +414,6 @@ static ds_status lanczos_t(ds_ctx* ctx, ds_dict* dict)
     }
     for (int r = 0; r < N; r++) q0[r] /= sqrt(nq);
     if (cudaMemcpyAsync(P.q, q0.data(), 8 * N, cudaMemcpyHostToDevice, s) != cudaSuccess) return DS_ERR_CUDA;
-    if (cudaMemsetAsync(P.qp, 0, 8 * N, s) != cudaSuccess) return DS_ERR_CUDA;
     if (cudaMemsetAsync(P.err, 0, sizeof(int), s) != cudaSuccess) return DS_ERR_CUDA;
     size_t smem = (size_t)ld * sizeof(T) + sizeof(T) * ((size_t)K / G + 2) + 16;
     if (smem > ctx->smem_optin - 16 * 1024) return DS_ERR_UNSUPPORTED;

@@ -410,7 +410,7 @@ def test_bench_workload_full_size_certified_in_fp64(ctx):
     """The benchmark's own workload at full size (2000 x 10000, seed 1002, the three tests x five
     lambdas, in the bench's launch configuration: one path per test): every solution is
     certified independently of the kernel's report, by an FP64 duality gap computed here from
-    the returned x with the dual point (y - D x) / lambda scaled into the feasible set."""
+    the returned x with the dual point of Lemma 8 built from its residual."""
     D, y, _ = gen.config2(1002)
     D32, y32 = D.astype(np.float32), y.astype(np.float32)
     D64, y64 = D32.astype(np.float64), y32.astype(np.float64)
@@ -430,8 +430,10 @@ def test_bench_workload_full_size_certified_in_fp64(ctx):
                 x = Xh[j]
                 res64 = y64 - D64 @ x
                 primal = 0.5 * res64 @ res64 + lam * np.abs(x).sum()
-                theta = res64 / lam
-                theta *= min(1.0, 1.0 / np.abs(D64.T @ theta).max())
+                # dual point s (y - D x): the scaling closest to y / lambda within the feasible set (Lemma 8)
+                lim = 1.0 / np.abs(D64.T @ res64).max()
+                sc = float(np.clip(res64 @ y64 / (lam * (res64 @ res64)), -lim, lim))
+                theta = sc * res64
                 dual = 0.5 * yy - 0.5 * lam * lam * np.sum((theta - y64 / lam) ** 2)
                 # the FP32 rounding of the returned x adds a little to the kernel's certified gap
                 assert primal - dual <= 1.2e-6 * 0.5 * yy, (test, j, (primal - dual) / (0.5 * yy))
