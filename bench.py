@@ -189,6 +189,18 @@ def cpu_baseline(D32, y32, budget_s=30.0):
 
 # ------------------------------------------------------------------------ our arm
 
+def job_throughput(total_ms, solves_per_step, steps, world, dist=None, device="cpu"):
+    """Whole-job solves/s when each of `world` ranks ran `steps` steps of `solves_per_step`
+    independent solves on its own GPU (weak scaling, no collective on the data path): the
+    slowest rank's time, a max over ranks, sets the job's time.  Returns (value, job_ms)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return solves_per_step * steps * world / (total_ms / 1e3), total_ms
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -286,11 +298,8 @@ def main():
     launches = ds.ds_ctx_kernel_launches(ctx) - launches0
     if dist:
         dist.barrier()
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     solves_per_step = len(TESTS) * len(RATIOS)
-    value = solves_per_step * args.steps * world / (total_ms / 1e3)
+    value, total_ms = job_throughput(total_ms, solves_per_step, args.steps, world, dist, dev)
 
     # roofline of the dominant kernel (the persistent solve kernel): algorithmic bytes =
     # dictionary columns read (correlations + syntheses) x N x 4 bytes
