@@ -54,7 +54,6 @@ struct Ws {
     X* nz_u;
     X* nz_x;
     int* nz_t;  // test data of the entry's group: FP32 threshold bits (FP32 sphere tests) or group id
-    int* c_kg;
     int* c_ka;
     int* c_nz;
     int* c_nnzx;
@@ -931,7 +930,6 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     W.theta[r] = T(0);
             if (tid == 0) {
                 W.c_nz[b] = nzc;
-                W.c_kg[b] = n_own;
                 W.c_ka[b] = na_own;
                 W.c_nnzx[b] = nzc;
                 Acc z0;
@@ -1260,7 +1258,6 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     }
                     part_put(W.p_l1 + b, tl1);
                     s_si[12] = tkg;  // kept groups of the slice: (B) skips the compaction when nothing was screened
-                    W.c_kg[b] = tkg;
                     W.c_ka[b] = tka;
                     W.c_nnzx[b] = tnx;
                 }
@@ -1735,7 +1732,6 @@ inline size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_la
     w->nz_u = bp.take<X>(K);
     w->nz_x = bp.take<X>(K);
     w->nz_t = bp.take<int>(K);
-    w->c_kg = bp.take<int>(G);
     w->c_ka = bp.take<int>(G);
     w->c_nz = bp.take<int>(G);
     w->c_nnzx = bp.take<int>(G);

@@ -40,8 +40,9 @@ def _instances(seed):
     return out
 
 
+@pytest.mark.parametrize("alg", ["fista", "cp"])
 @pytest.mark.parametrize("test", ["none", "dst3"])
-def test_batch_matches_single_solves(ctx, test):
+def test_batch_matches_single_solves(ctx, test, alg):
     inst = _instances(77)
     dicts = [ds.ds_dict_create(ctx, _dev_dict(D), goff) for (D, goff, Y, lam) in inst]
     try:
@@ -50,7 +51,8 @@ def test_batch_matches_single_solves(ctx, test):
         lams = [lam.copy() for (D, goff, Y, lam) in inst]
         t_group = "dgst3" if test == "dst3" else "none"
         # one options set for all: group dictionaries read DST3 as its group form
-        opt = ds.ds_options_default(test=t_group, tol_gap_rel=0.0, max_iter=1500, lambda_rel=1)
+        # (Chambolle-Pock problems run one per team; FISTA Lasso instances as multi-RHS blocks)
+        opt = ds.ds_options_default(alg=alg, test=t_group, tol_gap_rel=0.0, max_iter=1500, lambda_rel=1)
         plan = ds.ds_batch_create(ctx, dicts, Ys, lams, opt, Xs)
         info = ds.ds_batch_info(plan)
         print("batch plan:", info)
