@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -76,7 +77,8 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the samples go to a scratch file; their summary goes into the JSON line
+        self.path = os.path.join(tempfile.gettempdir(), f"dscreen_clocks_{os.getpid()}_rank{index}.csv")
 
     def __enter__(self):
         try:
