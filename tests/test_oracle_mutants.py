@@ -1,0 +1,103 @@
+"""Planted mistakes in the FP64 oracle must each fail at least one pin.
+
+Each mutant below changes one expression of ``oracle/dscreen_oracle.c`` into a
+plausible mistake (a flipped sign, a dropped term, a wrong index or constant).
+The mutated copy is compiled into a temporary directory and the pins of
+``test_oracle_pins.py`` run against it in a child process; the mutant counts
+as caught only when a pin fails (pytest exit code 1), not when the harness
+breaks.  The unmutated source runs through the same harness as a control.
+The oracle itself is never modified.  CPU only.
+"""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dscreen_oracle.c")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# name -> (exact text in the oracle, replacement, the passage it breaks)
+MUTANTS = {
+    "dst3_centre_sign": ("cvec[n] -= psi / ns2 * sg * ds[n];", "cvec[n] += psi / ns2 * sg * ds[n];",
+                         "Lemma 3 centre"),
+    "dst3_radius_unsquared": ("R2 - c->delta * c->delta", "R2 - c->delta", "Lemma 3 radius"),
+    "dome_dropped_psi_t": ("return dc0 - psi * t + sqrt(", "return dc0 + sqrt(", "Lemma 4 maximum"),
+    "dome_branch_sign": ("if (t * R <= -psi) return dc0 + R;", "if (t * R <= psi) return dc0 + R;",
+                         "Lemma 4 case split"),
+    "dome_normal_unsigned": ("c->tdome[i] = sg * vec_dot(", "c->tdome[i] = vec_dot(", "Lemma 4 normal d_*"),
+    "safe_norm_dropped": ("(1.0 - fabs(c->dtc[g])) / c->nrm[g] - rad", "(1.0 - fabs(c->dtc[g])) - rad",
+                          "Lemma 2 for unnormalised atoms"),
+    "gsafe_weight_dropped": ("(g_w(c->w, g) - c->dtc[g]) / c->nrm[g]", "(1.0 - c->dtc[g]) / c->nrm[g]",
+                             "Lemma 5 weight"),
+    "dgst3_offset_unsquared": ("/ lam - wg * wg;", "/ lam - wg;", "Lemma 6 hyperplane offset"),
+    "dgst3_centre_sign": ("cvec[n] -= coef * nv[n] / nn;", "cvec[n] += coef * nv[n] / nn;", "Lemma 6 centre"),
+    "mu_unclipped": ("if (m > 0.0) {", "if (0) {", "Lemma 8 clip"),
+    "mu_lambda_dropped": ("vec_dot(theta, y, N) / (lambda * tt)", "vec_dot(theta, y, N) / tt",
+                          "Lemma 8 scaling"),
+    "fista_momentum": ("beta = (l - 1.0) / ln;", "beta = l / ln;", "Table 1 FISTA momentum"),
+    "momentum_direction": ("u[i] = xi + beta * (xi - x[i]);", "u[i] = xi + beta * (x[i] - xi);",
+                           "Table 1 extrapolation"),
+    "soft_threshold_half": ("double a = fabs(v[lo]) - t;", "double a = fabs(v[lo]) - 0.5 * t;",
+                            "eq. softTh"),
+    "group_threshold_weight": ("(nv - t * g_w(c->w, g)) / nv", "(nv - t) / nv", "eq. gr_softTh weight"),
+    "lambda_star_weight": ("double v = sqrt(s) / g_w(w, g);", "double v = sqrt(s);", "eq. gstar weight"),
+    "power_method_sqrt": ("double rq_new = vec_dot(u, u, N);", "double rq_new = sqrt(vec_dot(u, u, N));",
+                          "step constant ||D||^2"),
+    "jacobi_rotation_sign": ("A[k * m + p] = c * akp - s * akq;", "A[k * m + p] = c * akp + s * akq;",
+                             "||D_g||_2 for Lemmas 5-7"),
+    "dual_lambda_unsquared": ("0.5 * yy - 0.5 * lambda * lambda * R * R", "0.5 * yy - 0.5 * lambda * R * R",
+                              "dual objective of the gap"),
+    "cp_dual_unaveraged": ("(theta[n] + sigma * r[n]) / (1.0 + sigma)", "(theta[n] + sigma * r[n])",
+                           "Table 1 Chambolle-Pock dual step"),
+}
+
+_CHILD = (
+    "import sys\n"
+    "sys.path.insert(0, {root!r})\n"
+    "import oracle\n"
+    "oracle._SRC, oracle._BUILD, oracle._LIB = {src!r}, {bdir!r}, {lib!r}\n"
+    "import pytest\n"
+    "sys.exit(pytest.main([{pins!r}, '-x', '-q', '-p', 'no:cacheprovider']))\n"
+)
+
+
+def _run_pins(name, text, workdir):
+    """Compile ``text`` as the oracle and run the pins on it; returns (exit code, output tail)."""
+    bdir = os.path.join(workdir, name)
+    os.makedirs(bdir)
+    src = os.path.join(bdir, "dscreen_oracle.c")
+    lib = os.path.join(bdir, "liboracle.so")
+    with open(src, "w") as f:
+        f.write(text)
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", lib, src, "-lm"])
+    code = _CHILD.format(root=ROOT, src=src, bdir=bdir, lib=lib, pins=PINS)
+    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    return p.returncode, (p.stdout + p.stderr)[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    with open(SRC) as f:
+        base = f.read()
+    jobs = {"unmutated": base}
+    for name, (old, new, _) in MUTANTS.items():
+        assert base.count(old) == 1, f"{name}: the mutated text must occur exactly once in the oracle"
+        jobs[name] = base.replace(old, new)
+    workdir = str(tmp_path_factory.mktemp("mutants"))
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+        futs = {name: ex.submit(_run_pins, name, text, workdir) for name, text in jobs.items()}
+        return {name: f.result() for name, f in futs.items()}
+
+
+def test_unmutated_oracle_passes_the_harness(outcomes):
+    rc, tail = outcomes["unmutated"]
+    assert rc == 0, tail
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_fails_a_pin(outcomes, name):
+    rc, tail = outcomes[name]
+    assert rc == 1, f"{name} ({MUTANTS[name][2]}): pins exit code {rc}, expected a failing pin\n{tail}"

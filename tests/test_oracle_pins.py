@@ -324,6 +324,37 @@ def test_group_regions_contain_dual_optimum():
     assert np.all(np.linalg.norm(th - c) <= r["hist"][:, 3] + 1e-9)
 
 
+@pytest.mark.parametrize("test", ["gsafe", "dgst3"])
+def test_group_weights_are_a_change_of_variables(test):
+    """Eq. (1) with weights w: substituting x_g = z_g / w_g turns (D, w) into
+    (D_g / w_g, unit weights) with the same objective, so lambda_*, the static
+    screened set (Lemmas 5 and 6 through Lemma 7) and the minimiser (x = z / w)
+    must all agree between the two problems."""
+    g = gen.rng(21)
+    D = gen.gaussian_dict(50, 200, g)
+    goff = gen.contiguous_groups(200, 4)
+    G = goff.size - 1
+    w = 0.5 + 1.5 * g.random(G)
+    y = gen.observe(D, gen.group_x0(goff, 3, g), g, snr_db=20.0)
+    wcol = np.repeat(w, np.diff(goff))
+    Dz = D / wcol
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lz, _, _ = oracle.lambda_max(Dz, y, goff, np.ones(G))
+    np.testing.assert_allclose(lz, lm, rtol=1e-13)
+    partial = 0
+    for ratio in (0.6, 0.8, 0.9, 0.95):
+        lam = ratio * lm
+        rx = oracle.solve(D, y, lam, goff, w, alg="ista", test=test, dynamic=False, max_iter=1, tol=0)
+        rz = oracle.solve(Dz, y, lam, goff, np.ones(G), alg="ista", test=test, dynamic=False, max_iter=1, tol=0)
+        np.testing.assert_array_equal(rx["scr_iter"] != 0, rz["scr_iter"] != 0)
+        partial += 0 < np.count_nonzero(rx["scr_iter"]) < 200
+    assert partial >= 2
+    lam = 0.5 * lm
+    rx = oracle.solve(D, y, lam, goff, w, test=test, tol=1e-14, max_iter=100000)
+    rz = oracle.solve(Dz, y, lam, goff, np.ones(G), test=test, tol=1e-14, max_iter=100000)
+    np.testing.assert_allclose(rx["x"], rz["x"] / wcol, atol=1e-6 * np.abs(rx["x"]).max())
+
+
 # ----------------------------------------------------- Lemma 8 and Lemma 4
 
 def test_dual_scaling_is_optimal_feasible_scaling():
