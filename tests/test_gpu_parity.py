@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
 Each case runs the oracle and the GPU on the same seeded input and the same
-step constant L.  The bar (spec tolerance for FP32):
+step constant L.  The bar for FP32:
 ||x - x_oracle||_inf <= 1e-5 ||x_oracle||_inf once both have converged, and
 the GPU's own duality gap <= 1e-6 * 1/2 ||y||^2 when it stops on tolerance.
 FP64 dictionaries are held to 1e-9.  Sizes span several GEMV row chunks
