@@ -4,6 +4,7 @@ checks reject bad input before touching the GPU."""
 import ctypes
 
 import numpy as np
+import pytest
 
 import paper_1412_4080_gb300 as ds
 
@@ -55,3 +56,50 @@ def test_selftest_rejects_null_outputs_without_gpu_work():
     st = ctypes.c_int()
     assert L.ds_selftest_wait_timeout(0, None, ctypes.byref(v)) == ds.DS_ERR_INVALID
     assert L.ds_selftest_wait_timeout(0, ctypes.byref(st), None) == ds.DS_ERR_INVALID
+
+
+_DESTROY = {"ds_destroy", "ds_dict_destroy", "ds_batch_destroy", "ds_server_destroy"}
+
+
+def _zero_args(f):
+    scalars = (ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_uint64, ctypes.c_double, ctypes.c_float)
+    return [t(0) if t in scalars else None for t in f.argtypes]
+
+
+@pytest.mark.parametrize("name", [n for n in ds.declared_functions() if n != "ds_status_str"])
+def test_every_entry_point_rejects_null_handles(name):
+    """With every pointer null and every size zero, each call returns
+    DS_ERR_INVALID (destroy calls: DS_OK) before any CUDA call."""
+    f = getattr(ds.lib(), name)
+    assert f.argtypes is not None, f"{name}: the binding declares no argument types"
+    want = ds.DS_OK if name in _DESTROY else ds.DS_ERR_INVALID
+    assert f(*_zero_args(f)) == want
+
+
+def _noalloc(N=8, K=16, ld=8, lam=0.5, D_offset=0, **opt_fields):
+    """Call ds_solve_lasso_noalloc on host buffers: every case here must be
+    rejected by the argument checks, which run before the first CUDA call."""
+    D = np.zeros(ld * K + 4, dtype=np.float32)
+    y = np.zeros(N, dtype=np.float32)
+    x = np.zeros(K, dtype=np.float32)
+    o = ds.ds_options_default()
+    o.L = 1.0
+    for k, v in opt_fields.items():
+        setattr(o, k, v)
+    r = ds.ds_result()
+    return ds.lib().ds_solve_lasso_noalloc(0, None, D.ctypes.data + D_offset, N, K, ld, y.ctypes.data,
+                                           ctypes.c_double(lam), ctypes.byref(o), x.ctypes.data, ctypes.byref(r))
+
+
+@pytest.mark.parametrize("case", [
+    dict(N=0), dict(K=0), dict(ld=4), dict(lam=0.0), dict(lam=-1.0), dict(lam=float("nan")),
+    dict(L=0.0), dict(max_iter=0), dict(tol_gap_rel=-1.0), dict(tol_gap_rel=float("nan")),
+    dict(alg=7), dict(test=9), dict(ld=10, N=10), dict(D_offset=4),
+])
+def test_noalloc_rejects_bad_arguments_without_gpu_work(case):
+    assert _noalloc(**case) == ds.DS_ERR_INVALID
+
+
+def test_noalloc_reports_sizes_beyond_its_fixed_scratch():
+    assert _noalloc(N=4097, ld=4100) == ds.DS_ERR_UNSUPPORTED
+    assert _noalloc(K=16385) == ds.DS_ERR_UNSUPPORTED
