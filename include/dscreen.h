@@ -7,9 +7,10 @@
  * Problem (eq. 1):   x~ = argmin_x 1/2 ||D x - y||_2^2 + lambda * Omega(x)
  *   Lasso (eq. lasso):              Omega(x) = ||x||_1
  *   Group-Lasso (eq. group-lasso):  Omega(x) = sum_g w_g ||x_g||_2, G a partition
- * D is N x K, y has N entries.  The solver runs ISTA or FISTA (Table 1) and,
- * inside every iteration, a safe screening test (Lemmas 2-7, dual scaling by
- * Lemma 8) that removes atoms from the working dictionary (Algorithm 3).
+ * D is N x K, y has N entries.  The solver runs ISTA, FISTA or Chambolle-Pock
+ * (Table 1) and, inside every iteration, a safe screening test (Lemmas 2-7,
+ * dual scaling by Lemma 8) that removes atoms from the working dictionary
+ * (Algorithm 3).
  *
  * Conventions shared by every call:
  *  - Layout: D is column-major (atom i is the contiguous column D[:, i]),

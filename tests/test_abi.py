@@ -103,3 +103,41 @@ def test_noalloc_rejects_bad_arguments_without_gpu_work(case):
 def test_noalloc_reports_sizes_beyond_its_fixed_scratch():
     assert _noalloc(N=4097, ld=4100) == ds.DS_ERR_UNSUPPORTED
     assert _noalloc(K=16385) == ds.DS_ERR_UNSUPPORTED
+
+
+_C_USER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "dscreen.h"
+
+int main(void)
+{
+    ds_options o;
+    ds_result r;
+    if (ds_options_default(&o) != DS_OK) return 1;
+    if (o.alg != DS_FISTA || o.test != DS_DST3 || o.max_iter <= 0) return 2;
+    if (strcmp(ds_status_str(DS_ERR_TIMEOUT), "DS_ERR_TIMEOUT") != 0) return 3;
+    if (ds_solve(NULL, NULL, NULL, 1.0, &o, NULL, NULL, &r) != DS_ERR_INVALID) return 4;
+    if (ds_solve_lasso_noalloc(0, NULL, NULL, 0, 0, 0, NULL, 1.0, &o, NULL, &r) != DS_ERR_INVALID) return 5;
+    if (ds_destroy(NULL) != DS_OK) return 6;
+    puts("ok");
+    return 0;
+}
+"""
+
+
+def test_header_is_c99_and_a_c_program_links_the_library(tmp_path):
+    """The boundary is a C ABI: include/dscreen.h compiles as strict C99 and a
+    plain C program (no Python, no PyTorch) links and calls the library."""
+    import os
+    import subprocess
+
+    so = ds.build()
+    src = tmp_path / "user.c"
+    src.write_text(_C_USER)
+    exe = tmp_path / "user"
+    inc = os.path.dirname(ds.HEADER)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, str(src),
+                           so, f"-Wl,-rpath,{os.path.dirname(so)}", "-o", str(exe)])
+    p = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert p.returncode == 0 and p.stdout.strip() == "ok", (p.returncode, p.stdout, p.stderr)
