@@ -455,6 +455,115 @@ def test_fista_rate_bound():
     assert abs(h[2, 4] - ri["hist"][2, 4]) > 1e-10 * yy
 
 
+def test_fista_rate_bound_on_the_worst_case_quadratic():
+    """Beck and Teboulle's bound on Nesterov's worst-case least-squares instance,
+    where it is nearly tight: D = B/2 with B the (n+1) x n first-difference
+    matrix (D^T D = tridiag(-1, 2, -1)/4, ||D||^2 < 1 = L), y = e_1/2, and a
+    lambda small enough that x* keeps the all-positive support, so x* solves
+    D^T D x = D^T y - lambda 1 (KKT).  FISTA stays within the bound up to
+    t = n/2; ISTA, whose rate is only O(1/t), exceeds it there, so a FISTA that
+    lost its acceleration fails this pin."""
+    n = 600
+    B = np.zeros((n + 1, n))
+    B[np.arange(n), np.arange(n)] = 1.0
+    B[np.arange(1, n + 1), np.arange(n)] = -1.0
+    D = np.asfortranarray(0.5 * B)
+    y = np.zeros(n + 1)
+    y[0] = 0.5
+    lam = 1e-7
+    xs = np.linalg.solve(D.T @ D, D.T @ y - lam)
+    assert np.all(xs > 0)
+    Fs = 0.5 * np.sum((D @ xs - y) ** 2) + lam * xs.sum()
+    T = n // 2 - 1
+    t = np.arange(1, T + 1)
+    bound = 2 * 1.0 * np.sum(xs ** 2) / (t + 1) ** 2
+
+    def excess(alg):
+        h = oracle.solve(D, y, lam, alg=alg, test="none", tol=0, max_iter=T, L=1.0)["hist"]
+        F = h[:, 4] + 0.5 * (y @ y) - 0.5 * lam * lam * h[:, 2] ** 2  # primal = gap + dual
+        return (F - Fs) / bound
+
+    assert np.all(excess("fista") <= 1.0)
+    assert excess("ista").max() > 1.1
+
+
+def _region_max(D, y, lam, lstar, star_sign_col, R, dome):
+    """max_i |d_i^T theta| over {||theta - y/lambda|| <= R} (intersected with
+    {d_*^T theta <= 1} for the dome) by enumerating the region's boundary in the
+    plane of d_* and d_i: a linear function is maximised at an extreme point,
+    i.e. on the feasible arc of the circle or at an end of the chord."""
+    c0 = y / lam
+    ds = star_sign_col
+    e1 = ds / np.linalg.norm(ds)
+    ga = D.T @ e1                                    # component of d_i along e1
+    gb = np.sqrt(np.maximum(np.sum(D * D, axis=0) - ga * ga, 0.0))  # along e2(i)
+    dc = D.T @ c0
+    phi = np.linspace(0.0, 2 * np.pi, 40001)
+    a, b = R * np.cos(phi), R * np.sin(phi)
+    if dome:
+        amax = (1.0 - ds @ c0) / np.linalg.norm(ds)
+        keep = a <= amax
+        a, b = a[keep], b[keep]
+        if R * R >= amax * amax:
+            h = np.sqrt(R * R - amax * amax)
+            a = np.concatenate([a, [amax, amax]])
+            b = np.concatenate([b, [h, -h]])
+    val = dc[:, None] + ga[:, None] * a[None, :] + gb[:, None] * b[None, :]
+    return np.maximum(val.max(axis=1), (-val).max(axis=1))
+
+
+@pytest.mark.parametrize("test", ["safe", "dome"])
+def test_static_screen_equals_brute_force_region_maximum(test):
+    """Atoms of unequal norms: the static test (Sec. 2.2.2, theta = -y, so
+    mu theta = y / lambda_* and R = ||y/lambda - y/lambda_*||) screens exactly
+    the atoms whose maximum of |d_i^T theta| over the test region is below 1
+    (SAFE: the ball, Lemma 2; Dome: the ball cut by d_*^T theta <= 1, Lemma 4),
+    the maximum found by brute force; atoms within 1e-6 of 1 are not judged."""
+    g = gen.rng(41)
+    D = np.asfortranarray(gen.gaussian_dict(40, 300, g) * (0.5 + 1.5 * g.random(300)))
+    y = g.standard_normal(40)
+    lm, star, b = oracle.lambda_max(D, y)
+    ds = np.sign(b[star]) * D[:, star]
+    screened_any = 0
+    for ratio in (0.5, 0.7, 0.85, 0.95):
+        lam = ratio * lm
+        R = np.linalg.norm(y / lam - y / lm)
+        M = _region_max(D, y, lam, lm, ds, R, dome=test == "dome")
+        r = oracle.solve(D, y, lam, alg="ista", test=test, dynamic=False, max_iter=1, tol=0)
+        clear = np.abs(M - 1.0) > 1e-6
+        np.testing.assert_array_equal((r["scr_iter"] == -1)[clear], (M < 1.0)[clear])
+        screened_any += 0 < np.count_nonzero(M < 1.0) < 300
+    assert screened_any >= 2
+
+
+@pytest.mark.parametrize("alg", ["ista", "fista", "cp"])
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome", "gsafe", "dgst3"])
+def test_every_dual_point_obeys_weak_duality(alg, test):
+    """Lemma 8 makes mu_t theta_t dual feasible, so its dual value
+    1/2 ||y||^2 - lambda^2/2 R_t^2 (R_t = ||y/lambda - mu_t theta_t||) never
+    exceeds the primal optimum, at any iteration; atoms of unequal norms, group
+    weights on both sides of 1."""
+    g = gen.rng(43)
+    D = np.asfortranarray(gen.gaussian_dict(40, 160, g) * (0.5 + 1.5 * g.random(160)))
+    goff, w = None, None
+    if test in ("gsafe", "dgst3"):
+        goff = gen.contiguous_groups(160, 4)
+        w = 0.5 + 1.5 * g.random(40)
+        x0 = gen.group_x0(goff, 3, g)
+    else:
+        x0 = gen.sparse_x0(160, 5, g)
+    y = gen.observe(D, x0, g, snr_db=20.0)
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    yy = y @ y
+    for ratio in (0.3, 0.7):
+        lam = ratio * lm
+        ref = oracle.solve(D, y, lam, goff, w, alg="fista", test="none", tol=1e-14, max_iter=100000)
+        P_ub = ref["primal"]  # an upper bound of the optimum
+        h = oracle.solve(D, y, lam, goff, w, alg=alg, test=test, tol=0, max_iter=300)["hist"]
+        dual = 0.5 * yy - 0.5 * lam * lam * h[:, 2] ** 2
+        assert np.all(dual <= P_ub + 1e-13 * yy)
+
+
 @pytest.mark.parametrize("test", ["safe", "dst3", "dome"])
 def test_chambolle_pock_first_test_is_the_static_test(test):
     """Chambolle-Pock (Table 1) starts from theta_0 = 0, so theta_1 = -sigma y / (1 + sigma) is a
