@@ -64,6 +64,10 @@ MUTANTS = {
     "fista_gradient_step_from_x": ("v[i] = cp ? x[i] - tau * z[i] : u[i] - z[i] / L;",
                                    "v[i] = cp ? x[i] - tau * z[i] : x[i] - z[i] / L;", "Table 1 FISTA gradient point"),
     "fista_without_momentum": ("beta = (l - 1.0) / ln;", "beta = 0.0 * (l - 1.0) / ln;", "Table 1 FISTA momentum"),
+    "step_constant_below_norm": ("* (1.0 + 1e-6);", "* (1.0 - 1e-3);", "L >= ||D||^2 behind Table 1"),
+    "screened_atoms_rescreened": ("        if (!active_g[g]) continue;\n        int kill = 0;", "        int kill = 0;",
+                                  "Algorithm 3 screens each atom once"),
+    "warm_start_u_unset": ("{ x[i] = x0[i]; u[i] = x0[i]; }", "{ x[i] = x0[i]; }", "warm start x_0 = u_0"),
 }
 
 # Mistakes that no pin catches, each with the reason; they run as strict xfails,
@@ -77,6 +81,10 @@ KNOWN_SURVIVORS = {
                                       "still an O(1/t^2) momentum sequence within the Beck-Teboulle bound"),
     "fista_sequence_linear": ("double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));", "double ln = l + 1.0 / 3.0;",
                               "the Chambolle-Dossal sequence (t + 2) / 3, also an O(1/t^2) method"),
+    "cp_dual_start_minus_y": ("        for (int64_t n = 0; n < N; n++) theta[n] = 0.0;\n    int it;",
+                              "        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];\n    int it;",
+                              "theta_0 is not fixed by the paper: theta_0 = -y is another reading, with the same "
+                              "first test and the same fixed point"),
 }
 
 _CHILD = (

@@ -191,6 +191,30 @@ def test_gap_nonnegative_and_sets_nested(test):
     assert np.all(h[:, 4] >= -1e-12 * 0.5 * (y @ y))
     assert np.all(np.diff(h[:, 0]) <= 0)
     assert r["status"] == 0 and r["gap"] <= 1e-12 * 0.5 * (y @ y)
+    # each atom is screened once, at the first test that removes it: the atoms
+    # recorded as screened by iteration t are exactly those gone from A_t
+    s = r["scr_iter"]
+    for t in range(1, r["iters"] + 1):
+        assert np.count_nonzero((s != 0) & (s <= t)) == 300 - h[t - 1, 0]
+
+
+@pytest.mark.parametrize("alg", ["ista", "fista"])
+@pytest.mark.parametrize("test", ["none", "dst3", "dgst3"])
+def test_warm_start_at_the_minimiser_stays_there(alg, test):
+    """The minimiser is a fixed point of the proximal gradient step of Table 1
+    (ISTA; FISTA's extrapolation of two equal iterates is zero), so a solve
+    warm-started there (x_0 = u_0 = x*) has a zero gap from its first iteration."""
+    if test == "dgst3":
+        D, y, _, goff, w = gen.config3(1007, N=50, K=200, gsize=4, n_active=3)
+    else:
+        (D, y), goff, w = _small_lasso(6, N=50, K=200, k=5), None, None
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.4 * lm
+    L = oracle.spectral_norm_sq(D) * (1 + 1e-6)
+    xs = oracle.solve(D, y, lam, goff, w, test="none", tol=1e-15, max_iter=200000, L=L)["x"]
+    r = oracle.solve(D, y, lam, goff, w, alg=alg, test=test, tol=0, max_iter=3, L=L, x0=xs)
+    assert np.all(r["hist"][:, 4] <= 1e-11 * 0.5 * (y @ y))
+    np.testing.assert_allclose(r["x"], xs, atol=1e-9 * np.abs(xs).max())
 
 
 def test_scale_covariance():
@@ -403,6 +427,10 @@ def test_spectral_norms_match_library():
     D = gen.gaussian_dict(30, 90, g)
     L = oracle.spectral_norm_sq(D, tol=1e-14)
     assert np.isclose(L, np.linalg.norm(D, 2) ** 2, rtol=1e-9)
+    # the default step constant of a solve is an upper bound of ||D||_2^2
+    # (the premise of the descent lemma behind every row of Table 1)
+    r = oracle.solve(D, gen.rng(19).standard_normal(30), 0.1, test="none", max_iter=1)
+    assert np.linalg.norm(D, 2) ** 2 <= r["L"] <= np.linalg.norm(D, 2) ** 2 * (1 + 1e-5)
     for c0, c1 in ((0, 1), (0, 5), (10, 30), (40, 73)):
         s = oracle.group_spec_norm(D, c0, c1)
         assert np.isclose(s, np.linalg.norm(D[:, c0:c1], 2), rtol=1e-12)
