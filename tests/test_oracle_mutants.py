@@ -68,6 +68,9 @@ MUTANTS = {
     "screened_atoms_rescreened": ("        if (!active_g[g]) continue;\n        int kill = 0;", "        int kill = 0;",
                                   "Algorithm 3 screens each atom once"),
     "warm_start_u_unset": ("{ x[i] = x0[i]; u[i] = x0[i]; }", "{ x[i] = x0[i]; }", "warm start x_0 = u_0"),
+    "gap_at_extrapolated_point": ("            if (x[i] != 0.0)\n                for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * x[i];",
+                                  "            if (u[i] != 0.0)\n                for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * u[i];",
+                                  "the gap certifies the returned iterate"),
 }
 
 # Mistakes that no pin catches, each with the reason; they run as strict xfails,

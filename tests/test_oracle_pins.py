@@ -217,6 +217,27 @@ def test_warm_start_at_the_minimiser_stays_there(alg, test):
     np.testing.assert_allclose(r["x"], xs, atol=1e-9 * np.abs(xs).max())
 
 
+@pytest.mark.parametrize("alg", ["ista", "fista", "cp"])
+@pytest.mark.parametrize("test", ["dst3", "dgst3"])
+def test_gap_certifies_the_distance_to_the_minimiser(alg, test):
+    """For any x, P(x) - P* >= 1/2 ||D (x - x~)||^2 (the quadratic term of P is
+    exact and x~ minimises the convex rest), and the duality gap (Sec. 2.2)
+    bounds P(x_t) - P*, so 1/2 ||D (x_t - x~)||^2 <= gap_t for the iterate the
+    solver returns after t iterations."""
+    if test == "dgst3":
+        D, y, _, goff, w = gen.config3(1009, N=40, K=160, gsize=4, n_active=3)
+    else:
+        (D, y), goff, w = _small_lasso(8, N=40, K=160, k=5), None, None
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.3 * lm
+    xs = oracle.solve(D, y, lam, goff, w, test="none", tol=1e-15, max_iter=200000)["x"]
+    yy = y @ y
+    for t in (1, 2, 3, 5, 10, 30, 100):
+        r = oracle.solve(D, y, lam, goff, w, alg=alg, test=test, tol=0, max_iter=t)
+        e = D @ (r["x"] - xs)
+        assert 0.5 * (e @ e) <= r["hist"][t - 1, 4] + 1e-12 * yy
+
+
 def test_scale_covariance():
     """P(a lambda, D, a y) has solution a x(lambda, D, y)."""
     D, y = _small_lasso(6)
