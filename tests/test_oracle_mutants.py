@@ -71,6 +71,11 @@ MUTANTS = {
     "gap_at_extrapolated_point": ("            if (x[i] != 0.0)\n                for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * x[i];",
                                   "            if (u[i] != 0.0)\n                for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * u[i];",
                                   "the gap certifies the returned iterate"),
+    "history_counts_groups": ("if (act[g]) nact += (int)(g_hi(goff, g) - g_lo(goff, g));", "if (act[g]) nact += 1;",
+                              "|A_t| of the flops accounting counts atoms"),
+    "history_nonzeros_of_u": ("for (int64_t i = 0; i < K; i++) nnz += x[i] != 0.0;",
+                              "for (int64_t i = 0; i < K; i++) nnz += u[i] != 0.0;",
+                              "||x_t||_0 of the flops accounting"),
 }
 
 # Mistakes that no pin catches, each with the reason; they run as strict xfails,

@@ -238,6 +238,30 @@ def test_gap_certifies_the_distance_to_the_minimiser(alg, test):
         assert 0.5 * (e @ e) <= r["hist"][t - 1, 4] + 1e-12 * yy
 
 
+@pytest.mark.parametrize("groups", [False, True])
+def test_history_counts_atoms_and_nonzeros(groups):
+    """The per-iteration history holds the quantities of the paper's flops
+    accounting (Sec. 4.1): |A_t| counts atoms (not groups) still active after
+    the test of iteration t, i.e. K minus the atoms recorded as screened by t,
+    and ||x_t||_0 counts the nonzeros of the iterate returned after t iterations."""
+    if groups:
+        D, y, _, goff, w = gen.config3(1011, N=50, K=240, gsize=6, n_active=3)
+        test = "dgst3"
+    else:
+        (D, y), goff, w, test = _small_lasso(9, N=50, K=240, k=5), None, None, "dst3"
+    K = D.shape[1]
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.3 * lm  # small enough that atoms leave the support in the first iterations
+    r = oracle.solve(D, y, lam, goff, w, test=test, tol=1e-10, max_iter=3000)
+    h, s = r["hist"], r["scr_iter"]
+    assert r["n_active"] == K - np.count_nonzero(s) == h[r["iters"] - 1, 0]
+    assert r["nnz"] == np.count_nonzero(r["x"]) == h[r["iters"] - 1, 1]
+    for t in list(range(1, 21)) + [r["iters"]]:
+        assert h[t - 1, 0] == K - np.count_nonzero((s != 0) & (s <= t))
+        rt = oracle.solve(D, y, lam, goff, w, test=test, tol=0, max_iter=t)
+        assert h[t - 1, 1] == np.count_nonzero(rt["x"])
+
+
 def test_scale_covariance():
     """P(a lambda, D, a y) has solution a x(lambda, D, y)."""
     D, y = _small_lasso(6)
