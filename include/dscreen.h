@@ -151,7 +151,8 @@ ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64
 /* Release a dictionary (NULL is a no-op). */
 ds_status ds_dict_destroy(ds_dict* dict);
 
-/* Read back the dictionary's step constant L (>= ||D||_2^2 estimate). */
+/* Read back the dictionary's step constant L (>= ||D||_2^2 estimate).
+ * Errors: DS_ERR_INVALID (NULL dict or L). */
 ds_status ds_dict_lipschitz(const ds_dict* dict, double* L);
 
 /* lambda_* of y (Sec. 2.2.2: ||D^T y||_inf; eq. gstar: max_g ||D_g^T y|| / w_g)
@@ -174,7 +175,9 @@ ds_status ds_solve(ds_ctx* ctx, const ds_dict* dict, const void* y, double lambd
 /* Same as ds_solve for n_lambda values of lambda sharing one y (the precompute
  * of D^T y, lambda_* and the test centres runs once).  lambdas: host array
  * (absolute, or fractions of lambda_max when opt->lambda_rel).  X_out: K x
- * n_lambda, column j = solution for lambdas[j].  res: n_lambda entries. */
+ * n_lambda, column j = solution for lambdas[j].  res: n_lambda entries.
+ * Errors: those of ds_solve, and DS_ERR_INVALID for n_lambda < 1, a NULL
+ * lambdas array or a lambda that is not finite and positive. */
 ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* dict, const void* y, int n_lambda, const double* lambdas,
                         const ds_options* opt, const void* x0, void* X_out, ds_result* res);
 
@@ -198,8 +201,11 @@ ds_status ds_solve_path(ds_ctx* ctx, const ds_dict* dict, const void* y, int n_l
 typedef struct ds_batch ds_batch;
 ds_status ds_batch_create(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
                           const double* const* lambdas, const ds_options* opt, void* const* X_out, ds_batch** out);
+/* Run the batch; res as above.  Errors: DS_ERR_INVALID (NULL batch or res),
+ * DS_ERR_CUDA, DS_ERR_TIMEOUT. */
 ds_status ds_batch_run(ds_batch* batch, ds_result* res);
-/* Whether the run replays a CUDA graph, and the team layout chosen. */
+/* Whether the run replays a CUDA graph, and the team layout chosen.
+ * Errors: DS_ERR_INVALID on NULL batch. */
 ds_status ds_batch_info(const ds_batch* batch, int* uses_graph, int* teams, int* team_size);
 /* How the batch's problems run (any output pointer may be NULL):
  *   multi_rhs_blocks: blocks of up to 64 right-hand sides of one FP32 Lasso
@@ -226,9 +232,11 @@ ds_status ds_batch_layout(const ds_batch* batch, int* multi_rhs_blocks, int* mul
  * could not be built); *chosen the index of the kept schedule (0: unchanged).
  * Errors: DS_ERR_INVALID, and the errors of ds_batch_run for the plan's own run. */
 ds_status ds_batch_autotune(ds_batch* batch, int max_candidates, int* chosen, int* n_tried, float* ms_tried);
-/* The batch's current multi-RHS schedule (any output pointer may be NULL). */
+/* The batch's current multi-RHS schedule (any output pointer may be NULL).
+ * Errors: DS_ERR_INVALID on NULL batch. */
 ds_status ds_batch_schedule(const ds_batch* batch, int* tensor_bulk, int* block_rhs, int* sort_lambda,
                             double* lowp_switch);
+/* Release a batch (NULL is a no-op). */
 ds_status ds_batch_destroy(ds_batch* batch);
 /* One-shot form: create, run once, destroy. */
 ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const void* const* Y, const int* n_rhs,
@@ -252,7 +260,10 @@ ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const 
  *   ds_server_poll: DS_PENDING while the request runs; DS_OK fills res
  *     (res->ms = latency from submission to completion) and forgets the ticket.
  *   ds_server_stats: completed, in flight, waiting, kernel launches, pool bytes.
- * A server drives its own CUDA stream; calls are serialised internally. */
+ * A server drives its own CUDA stream; calls are serialised internally.
+ * Errors: DS_ERR_INVALID (null arguments, a dictionary of another context, a
+ * Lasso test on a group dictionary, an unknown ticket), DS_ERR_UNSUPPORTED (as
+ * above), DS_ERR_OOM, DS_ERR_CUDA; ds_server_destroy(NULL) is a no-op. */
 typedef struct ds_server ds_server;
 ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, int64_t max_K, int team_size,
                            ds_server** out);
@@ -272,7 +283,8 @@ ds_status ds_server_destroy(ds_server* server);
  * one fixed 3 MiB array in device memory that every GPU loading this library
  * holds until the process exits.
  *
- * Same computation as ds_solve with a Lasso dictionary (FISTA/ISTA, any test;
+ * Same computation as ds_solve with a Lasso dictionary (ISTA, FISTA or
+ * Chambolle-Pock, any test;
  * DS_GSAFE / DS_DGST3 act as singleton groups), run on `device` and ordered on
  * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
  *   D      device, FP32, column-major N x K, leading dimension ld >= N with
@@ -314,7 +326,8 @@ ds_status ds_ctx_kernel_launches(const ds_ctx* ctx, int64_t* n);
 /* Record per-iteration history of the following solves into hist (device,
  * max_rows x 6 doubles, row t-1 = iteration t: active atoms, nnz(x), R,
  * test radius, gap, mu), or stop recording (hist NULL).  Only the first
- * lambda of a path is recorded. */
+ * lambda of a path is recorded.  Errors: DS_ERR_INVALID (NULL ctx, or hist
+ * with max_rows < 1). */
 ds_status ds_set_history(ds_ctx* ctx, double* hist, int max_rows);
 
 #ifdef __cplusplus
