@@ -141,3 +141,19 @@ def test_header_is_c99_and_a_c_program_links_the_library(tmp_path):
                            so, f"-Wl,-rpath,{os.path.dirname(so)}", "-o", str(exe)])
     p = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert p.returncode == 0 and p.stdout.strip() == "ok", (p.returncode, p.stdout, p.stderr)
+
+
+def test_readme_c_example_compiles(tmp_path):
+    """The C example in README.md stays in step with the header."""
+    import os
+    import re
+    import subprocess
+
+    root = os.path.dirname(os.path.dirname(ds.HEADER))
+    with open(os.path.join(root, "README.md")) as f:
+        blocks = re.findall(r"```c\n(.*?)```", f.read(), re.S)
+    assert blocks, "README.md has no C example"
+    src = tmp_path / "readme.c"
+    src.write_text(blocks[-1])
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                           os.path.dirname(ds.HEADER), "-c", str(src), "-o", str(tmp_path / "readme.o")])
