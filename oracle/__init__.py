@@ -72,7 +72,7 @@ def _load():
         lib.or_dome_max.argtypes = [ctypes.c_double] * 4
         lib.or_dome_max.restype = ctypes.c_double
         lib.or_solve.argtypes = [dp, i64, i64, i64, dp, ctypes.c_double, i64p, dp, i64,
-                                 ctypes.POINTER(_Options), dp, dp, ctypes.POINTER(ctypes.c_int), dp,
+                                 ctypes.POINTER(_Options), dp, dp, ctypes.POINTER(ctypes.c_int), dp, dp,
                                  ctypes.POINTER(_Result)]
         lib.or_solve.restype = ctypes.c_int
         _lib = lib
@@ -141,7 +141,7 @@ def dome_max(dc0, t, psi, R):
 def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynamic=True,
           tol=1e-6, max_iter=1000, L=None, x0=None, cp_tau=0.0, cp_sigma=0.0, cp_gamma=0.0):
     """Solve eq. (1) with Algorithm 3 and the ISTA, FISTA or Chambolle-Pock ("cp") update of Table 1.
-    Returns a dict with x, scr_iter, hist and scalars."""
+    Returns a dict with x, scr_iter, hist, theta (theta_t of the last iteration) and scalars."""
     lib = _load()
     D, N, K, ld = _dict(D)
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -151,15 +151,17 @@ def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynami
     x = np.zeros(K)
     scr = np.zeros(K, dtype=np.int32)
     hist = np.zeros((max(int(max_iter), 1), len(HIST_COLS)))
+    theta = np.zeros(N)
     res = _Result()
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
     rc = lib.or_solve(_dptr(D), N, K, ld, _dptr(y), float(lam),
                       None if goff is None else goff.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                       _dptr(w), nG, ctypes.byref(opt), _dptr(x0a), _dptr(x),
-                      scr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(hist), ctypes.byref(res))
+                      scr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(hist), _dptr(theta),
+                      ctypes.byref(res))
     if rc != 0:
         raise ValueError("oracle solve rejected its input")
     it = res.iters
-    return {"x": x, "scr_iter": scr, "hist": hist[:it], "iters": it, "gap": res.gap,
+    return {"x": x, "scr_iter": scr, "hist": hist[:it], "theta": theta, "iters": it, "gap": res.gap,
             "primal": res.primal, "dual": res.dual, "lambda_max": res.lambda_max, "L": res.L,
             "n_active": res.n_active, "nnz": res.nnz, "status": res.status}

@@ -23,9 +23,11 @@
  *                   Lemma 5 (GSAFE), Lemma 6 (DGST3), Lemma 7 (sphere test)
  *   static variant  Algorithm 1 / Algorithm 4 (test once at theta = -y)
  *
- * Parity unpinned: the intermediate Chambolle-Pock iterates (the theta average and the
- * phi, tau, sigma schedule) are pinned only through the fixed point they reach (the
- * minimiser) and the first test (the static one); see the test suite.
+ * Pinned only partially: the intermediate Chambolle-Pock iterates are pinned through the
+ * fixed point they reach (the minimiser, also for tau_0 != sigma_0), the first test (the
+ * static one) and, with gamma = 0, the Fejer monotonicity of a proximal point method in
+ * the metric of the two steps; a smaller extrapolation factor, and the phi, tau, sigma
+ * schedule of gamma > 0, pass those pins (see the test suite).
  *
  * Readings of the paper that this file takes (where the text is silent,
  * garbled or specialised):
@@ -448,14 +450,16 @@ static double omega(const or_ctx* c, const double* x)
     return s;
 }
 
-/* Solve eq. (1) by Algorithm 3 with the ISTA or FISTA update of Table 1.
+/* Solve eq. (1) by Algorithm 3 with the ISTA, FISTA or Chambolle-Pock update of Table 1.
  * x_out: K coefficients.  scr_iter (nullable): per atom, the iteration at which it
  * was screened (0 = never, -1 = by the static test before the loop).
- * hist (nullable): max_iter rows of OR_NH doubles. */
+ * hist (nullable): max_iter rows of OR_NH doubles.
+ * theta_out (nullable): N doubles, theta_t of the last iteration run (Table 1's dual
+ * variable; left untouched when no iteration runs). */
 int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y, double lambda,
              const int64_t* goff, const double* w, int64_t nG,
              const or_options* opt, const double* x0,
-             double* x_out, int* scr_iter, double* hist, or_result* res)
+             double* x_out, int* scr_iter, double* hist, double* theta_out, or_result* res)
 {
     if (!D || !y || !x_out || !opt || !res || N <= 0 || K <= 0 || ld < N || !(lambda > 0)) return -1;
     if (!goff) w = NULL; /* the Lasso: singleton groups of weight 1 */
@@ -651,6 +655,8 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
     res->primal = primal;
     res->dual = dual;
     for (int64_t i = 0; i < K; i++) x_out[i] = x[i];
+    if (theta_out)
+        for (int64_t n = 0; n < N; n++) theta_out[n] = theta[n];
     if (scr_iter)
         for (int64_t g = 0; g < G; g++)
             for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) scr_iter[i] = scr[g];

@@ -76,6 +76,16 @@ MUTANTS = {
     "history_nonzeros_of_u": ("for (int64_t i = 0; i < K; i++) nnz += x[i] != 0.0;",
                               "for (int64_t i = 0; i < K; i++) nnz += u[i] != 0.0;",
                               "||x_t||_0 of the flops accounting"),
+    "cp_average_with_tau": ("(theta[n] + sigma * r[n]) / (1.0 + sigma)", "(theta[n] + sigma * r[n]) / (1.0 + tau)",
+                            "Table 1 Chambolle-Pock dual step"),
+    "cp_dual_step_tau": ("(theta[n] + sigma * r[n]) / (1.0 + sigma)", "(theta[n] + tau * r[n]) / (1.0 + sigma)",
+                         "Table 1 Chambolle-Pock dual step"),
+    "cp_primal_step_sigma": ("v[i] = cp ? x[i] - tau * z[i] : u[i] - z[i] / L;",
+                             "v[i] = cp ? x[i] - sigma * z[i] : u[i] - z[i] / L;", "Table 1 Chambolle-Pock primal step"),
+    "cp_threshold_sigma": ("cp ? lambda * tau : lambda / L", "cp ? lambda * sigma : lambda / L",
+                           "Table 1 Chambolle-Pock proximal threshold"),
+    "cp_extrapolation_dropped": ("            beta = phi;\n", "            beta = 0.0 * phi;\n",
+                                 "Table 1 Chambolle-Pock extrapolation (Arrow-Hurwicz without it)"),
 }
 
 # Mistakes that no pin catches, each with the reason; they run as strict xfails,
@@ -93,6 +103,13 @@ KNOWN_SURVIVORS = {
                               "        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];\n    int it;",
                               "theta_0 is not fixed by the paper: theta_0 = -y is another reading, with the same "
                               "first test and the same fixed point"),
+    "cp_extrapolation_halved": ("            beta = phi;\n", "            beta = 0.5 * phi;\n",
+                                "the dual objective is strongly convex, so Chambolle-Pock with a smaller "
+                                "extrapolation factor still converges to the saddle point, Fejer-monotone"),
+    "cp_default_steps_smaller": ("double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.99 / sqrt(L);",
+                                 "double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.5 / sqrt(L);",
+                                 "tau_0 and sigma_0 are not fixed by the paper: any tau_0 sigma_0 ||D||^2 < 1 is "
+                                 "another reading"),
 }
 
 _CHILD = (

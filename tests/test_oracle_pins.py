@@ -664,3 +664,45 @@ def test_chambolle_pock_reaches_the_pinned_solution_and_gamma_stalls_it():
     np.testing.assert_allclose(r0["x"], ref["x"], atol=1e-6 * np.abs(ref["x"]).max())
     r1 = oracle.solve(D, y, lam, alg="cp", test="dst3", tol=1e-12, max_iter=20000, cp_gamma=1.0)
     assert r1["status"] == 1
+    # with tau_0 != sigma_0 (tau_0 sigma_0 ||D||^2 < 1) the fixed point is still the minimiser,
+    # which fixes where each of the two steps enters the primal and the dual updates
+    Ln = np.linalg.norm(D, 2) ** 2
+    for tau, sigma in ((0.3, 3.0), (3.0, 0.3)):
+        r2 = oracle.solve(D, y, lam, alg="cp", test="dst3", tol=1e-12, max_iter=50000,
+                          cp_tau=tau / np.sqrt(Ln), cp_sigma=sigma / np.sqrt(Ln))
+        assert r2["status"] == 0
+        np.testing.assert_allclose(r2["x"], ref["x"], atol=1e-6 * np.abs(ref["x"]).max())
+
+
+@pytest.mark.parametrize("steps", [(0.35, 2.2), (2.2, 0.35), (0.99, 0.99)])
+def test_chambolle_pock_iterates_are_fejer_monotone(steps):
+    """With gamma = 0, Chambolle-Pock is a proximal point method in the metric
+    M = [[I/tau, -D^T], [-D, I/sigma]] (positive definite when tau sigma ||D||^2 < 1):
+    for z_k = (x_{t-1}, theta_t) and the saddle point z* = (x*, D x* - y) of
+    min_x max_theta theta^T D x - 1/2 ||theta||^2 - theta^T y + lambda ||x||_1,
+    every step obeys ||z_{k+1} - z*||_M^2 + ||z_{k+1} - z_k||_M^2 <= ||z_k - z*||_M^2
+    (firm nonexpansiveness of the resolvent), a property of every intermediate iterate."""
+    g = gen.rng(51)
+    D = gen.gaussian_dict(30, 90, g)
+    y = gen.observe(D, gen.sparse_x0(90, 4, g), g, sigma=0.05)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.4 * lm
+    Ln = np.linalg.norm(D, 2) ** 2
+    tau, sigma = steps[0] / np.sqrt(Ln), steps[1] / np.sqrt(Ln)
+    assert tau * sigma * Ln < 1
+    xs = oracle.solve(D, y, lam, alg="fista", test="none", tol=1e-15, max_iter=200000)["x"]
+    ts = D @ xs - y
+
+    def m2(dx, dt):
+        return dx @ dx / tau + dt @ dt / sigma - 2.0 * dt @ (D @ dx)
+
+    z = [(np.zeros(90), None)]
+    for t in range(1, 61):
+        r = oracle.solve(D, y, lam, alg="cp", test="none", tol=0, max_iter=t, cp_tau=tau, cp_sigma=sigma)
+        z[-1] = (z[-1][0], r["theta"])      # z_{t-1} = (x_{t-1}, theta_t)
+        z.append((r["x"], None))
+    z = z[:-1]
+    d0 = m2(z[0][0] - xs, z[0][1] - ts)
+    for a, b in zip(z[:-1], z[1:]):
+        lhs = m2(b[0] - xs, b[1] - ts) + m2(b[0] - a[0], b[1] - a[1])
+        assert lhs <= m2(a[0] - xs, a[1] - ts) + 1e-10 * d0
