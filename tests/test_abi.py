@@ -157,3 +157,54 @@ def test_readme_c_example_compiles(tmp_path):
     src.write_text(blocks[-1])
     subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
                            os.path.dirname(ds.HEADER), "-c", str(src), "-o", str(tmp_path / "readme.o")])
+
+
+def _c_layout(tmp_path, include, header, structs):
+    """sizeof and offsetof of every field of the given C structs, as compiled by gcc."""
+    import subprocess
+
+    lines = ["#include <stddef.h>", "#include <stdio.h>", f'#include "{header}"', "int main(void) {"]
+    for cname, fields in structs.items():
+        lines.append(f'    printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'    printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", include, str(src), "-o", str(exe), "-lm"])
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    return {k: int(v) for k, v in (line.split() for line in out if line)}
+
+
+def _check(layout, cname, cstruct, rename=None):
+    rename = rename or {}
+    assert layout[cname] == ctypes.sizeof(cstruct), cname
+    for name, _ in cstruct._fields_:
+        cfield = rename.get(name, name)
+        assert layout[f"{cname}.{cfield}"] == getattr(cstruct, name).offset, (cname, cfield)
+
+
+def test_binding_structs_match_the_c_layout(tmp_path):
+    """ds_options and ds_result of the ctypes binding have the header's layout."""
+    import os
+
+    structs = {"ds_options": [n for n, _ in ds.ds_options._fields_],
+               "ds_result": ["lambda" if n == "lambda_" else n for n, _ in ds.ds_result._fields_]}
+    lay = _c_layout(tmp_path, os.path.dirname(ds.HEADER), "dscreen.h", structs)
+    _check(lay, "ds_options", ds.ds_options)
+    _check(lay, "ds_result", ds.ds_result, {"lambda_": "lambda"})
+
+
+def test_oracle_structs_match_the_c_layout(tmp_path):
+    """The oracle's ctypes option and result structures have its C layout."""
+    import os
+
+    import oracle
+
+    src = os.path.abspath(oracle._SRC)
+    structs = {"or_options": [n for n, _ in oracle._Options._fields_],
+               "or_result": [n for n, _ in oracle._Result._fields_]}
+    lay = _c_layout(tmp_path, os.path.dirname(src), os.path.basename(src), structs)
+    _check(lay, "or_options", oracle._Options)
+    _check(lay, "or_result", oracle._Result)
