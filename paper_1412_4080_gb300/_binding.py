@@ -145,6 +145,38 @@ def _dtype_code(a):
     raise TypeError(f"dictionary dtype must be float32 or float64, got {a.dtype}")
 
 
+class _DictHandle(ctypes.c_void_p):
+    """A registered dictionary: the C handle, plus its N, K and element size for the
+    buffer checks of the calls that take it."""
+
+
+def _check_buffer(a, n, esize, name, where):
+    """A vector argument must be contiguous, hold the dictionary's element type and
+    at least n elements: the library writes and reads exactly that many through the
+    raw pointer, so a short buffer would be an out-of-bounds access."""
+    if a is None:
+        return
+    if hasattr(a, "data_ptr"):
+        count, size, contiguous = a.numel(), a.element_size(), a.is_contiguous()
+    else:
+        count, size, contiguous = a.size, a.itemsize, a.flags.c_contiguous or a.flags.f_contiguous
+    if size != esize:
+        raise TypeError(f"{where}: {name} has {size}-byte elements, the dictionary {esize}-byte ones")
+    if not contiguous:
+        raise ValueError(f"{where}: {name} must be contiguous")
+    if count < n:
+        raise ValueError(f"{where}: {name} has {count} elements, {n} needed")
+
+
+def _check_vectors(dct, where, y=None, x_out=None, x0=None, n_lambda=1):
+    N, K, esize = getattr(dct, "N", None), getattr(dct, "K", None), getattr(dct, "esize", None)
+    if N is None:
+        return
+    _check_buffer(y, N, esize, "y", where)
+    _check_buffer(x_out, K * n_lambda, esize, "x_out", where)
+    _check_buffer(x0, K, esize, "x0", where)
+
+
 def _dict_layout(D):
     N, K = D.shape
     if hasattr(D, "stride"):
@@ -193,7 +225,8 @@ def ds_dict_create(ctx, D, group_offsets=None, weights=None, work_prec=None):
     dt = _dtype_code(D)
     goff = None if group_offsets is None else np.ascontiguousarray(group_offsets, dtype=np.int64)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
-    h = ctypes.c_void_p()
+    h = _DictHandle()
+    h.N, h.K, h.esize = N, K, 4 if dt == DS_FP32 else 8
     p, _ = _ptr(D)
     st = lib().ds_dict_create(ctx, p, N, K, ld, dt, None if goff is None else goff.ctypes.data,
                               None if w is None else w.ctypes.data, 0 if goff is None else goff.size - 1,
@@ -213,12 +246,14 @@ def ds_dict_lipschitz(dct) -> float:
 
 
 def ds_lambda_max(ctx, dct, y) -> float:
+    _check_vectors(dct, "ds_lambda_max", y=y)
     v = ctypes.c_double()
     _check(lib().ds_lambda_max(ctx, dct, _ptr(y)[0], ctypes.byref(v)), "ds_lambda_max")
     return v.value
 
 
 def ds_solve(ctx, dct, y, lam, opt, x_out, x0=None):
+    _check_vectors(dct, "ds_solve", y=y, x_out=x_out, x0=x0)
     r = ds_result()
     st = lib().ds_solve(ctx, dct, _ptr(y)[0], float(lam), ctypes.byref(opt), _ptr(x0)[0], _ptr(x_out)[0],
                         ctypes.byref(r))
@@ -228,6 +263,7 @@ def ds_solve(ctx, dct, y, lam, opt, x_out, x0=None):
 
 def ds_solve_path(ctx, dct, y, lambdas, opt, X_out, x0=None):
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    _check_vectors(dct, "ds_solve_path", y=y, x_out=X_out, x0=x0, n_lambda=lam.size)
     res = (ds_result * lam.size)()
     st = lib().ds_solve_path(ctx, dct, _ptr(y)[0], int(lam.size), lam.ctypes.data, ctypes.byref(opt),
                              _ptr(x0)[0], _ptr(X_out)[0], res)

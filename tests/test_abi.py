@@ -208,3 +208,31 @@ def test_oracle_structs_match_the_c_layout(tmp_path):
     lay = _c_layout(tmp_path, os.path.dirname(src), os.path.basename(src), structs)
     _check(lay, "or_options", oracle._Options)
     _check(lay, "or_result", oracle._Result)
+
+
+def test_binding_rejects_short_or_mistyped_buffers_before_the_call():
+    """The library reads y and writes x_out through raw pointers, so the binding checks
+    their element type, contiguity and length against the registered dictionary first
+    (a short buffer would be an out-of-bounds device access)."""
+    from paper_1412_4080_gb300 import _binding as B
+
+    h = B._DictHandle()
+    h.N, h.K, h.esize = 5, 7, 4
+    o = ds.ds_options_default()
+    f32 = np.float32
+    bad = [((np.zeros(4, f32), np.zeros(7, f32)), ValueError),          # y too short
+           ((np.zeros(5, np.float64), np.zeros(7, f32)), TypeError),   # y of another type
+           ((np.zeros(5, f32), np.zeros(6, f32)), ValueError),          # x_out too short
+           ((np.zeros(5, f32), np.zeros((7, 2), f32)[:, 0]), ValueError)]  # x_out strided
+    for (y, x), exc in bad:
+        with pytest.raises(exc):
+            ds.ds_solve(None, h, y, 1.0, o, x)
+    with pytest.raises(ValueError):
+        ds.ds_solve_path(None, h, np.zeros(5, f32), [0.5, 0.3], o, np.zeros(7, f32))
+    with pytest.raises(ValueError):
+        ds.ds_solve(None, h, np.zeros(5, f32), 1.0, o, np.zeros(7, f32), x0=np.zeros(3, f32))
+    # well-formed buffers reach the library, which rejects the null context
+    with pytest.raises(ds.DscreenError):
+        ds.ds_solve(None, h, np.zeros(5, f32), 1.0, o, np.zeros(7, f32))
+    with pytest.raises(ds.DscreenError):
+        ds.ds_solve_path(None, h, np.zeros(5, f32), [0.5, 0.3], o, np.zeros((2, 7), f32))
