@@ -360,6 +360,7 @@ def ds_server_create(ctx, hbm_budget_bytes, max_N, max_K, team_size=0):
 
 def ds_server_submit(server, dct, y, lam, opt, x_out):
     """y, x_out: host float32 NumPy arrays; keep x_out alive until ds_server_poll returns a result."""
+    _check_vectors(dct, "ds_server_submit", y=y, x_out=x_out)
     t = ctypes.c_uint64()
     _check(lib().ds_server_submit(server, dct, _ptr(y)[0], float(lam), ctypes.byref(opt), _ptr(x_out)[0],
                                   ctypes.byref(t)), "ds_server_submit")
@@ -391,6 +392,10 @@ def ds_server_destroy(server):
 def ds_solve_lasso_noalloc(device, stream, D, y, lam, opt, x_out):
     """Allocation-free Lasso solve on caller-owned device buffers (opt.L > 0 required)."""
     N, K, ld = _dict_layout(D)
+    if _dtype_code(D) != DS_FP32:
+        raise TypeError("ds_solve_lasso_noalloc: D must be float32")
+    _check_buffer(y, N, 4, "y", "ds_solve_lasso_noalloc")
+    _check_buffer(x_out, K, 4, "x_out", "ds_solve_lasso_noalloc")
     r = ds_result()
     s = None if stream is None else getattr(stream, "cuda_stream", stream)
     st = lib().ds_solve_lasso_noalloc(int(device), s, _ptr(D)[0], N, K, ld, _ptr(y)[0], float(lam),

@@ -236,3 +236,24 @@ def test_binding_rejects_short_or_mistyped_buffers_before_the_call():
         ds.ds_solve(None, h, np.zeros(5, f32), 1.0, o, np.zeros(7, f32))
     with pytest.raises(ds.DscreenError):
         ds.ds_solve_path(None, h, np.zeros(5, f32), [0.5, 0.3], o, np.zeros((2, 7), f32))
+
+
+def test_server_and_allocation_free_calls_check_their_buffers():
+    from paper_1412_4080_gb300 import _binding as B
+
+    h = B._DictHandle()
+    h.N, h.K, h.esize = 5, 7, 4
+    f32 = np.float32
+    o = ds.ds_options_default(L=1.0)
+    with pytest.raises(ValueError):
+        ds.ds_server_submit(None, h, np.zeros(5, f32), 0.5, o, np.zeros(6, f32))
+    D = np.zeros((8, 16), dtype=f32, order="F")
+    with pytest.raises(TypeError):
+        ds.ds_solve_lasso_noalloc(0, None, D.astype(np.float64), np.zeros(8, f32), 0.5, o, np.zeros(16, f32))
+    with pytest.raises(ValueError):
+        ds.ds_solve_lasso_noalloc(0, None, D, np.zeros(7, f32), 0.5, o, np.zeros(16, f32))
+    with pytest.raises(ValueError):
+        ds.ds_solve_lasso_noalloc(0, None, D, np.zeros(8, f32), 0.5, o, np.zeros(15, f32))
+    # well-formed host buffers reach the library, which rejects host pointers (no GPU work)
+    with pytest.raises(ds.DscreenError):
+        ds.ds_server_submit(None, h, np.zeros(5, f32), 0.5, o, np.zeros(7, f32))
