@@ -452,7 +452,8 @@ def _rhs_block(D, R, g, lo=0.1, hi=0.9):
     S = D.astype(np.float64) @ X0
     E = g.standard_normal((N, R))
     Y = (S + E * (np.linalg.norm(S, axis=0) / np.maximum(np.linalg.norm(E, axis=0), 1e-300)) * 0.1).T
-    return Y.astype(np.float32), g.uniform(lo, hi, size=R)
+    # row r = right-hand side r, contiguous: the library reads each y as N consecutive floats
+    return np.ascontiguousarray(Y, dtype=np.float32), g.uniform(lo, hi, size=R)
 
 
 def _time_batch(ds, plan, flush, reps=2):

@@ -159,11 +159,11 @@ def _check_buffer(a, n, esize, name, where):
     if hasattr(a, "data_ptr"):
         count, size, contiguous = a.numel(), a.element_size(), a.is_contiguous()
     else:
-        count, size, contiguous = a.size, a.itemsize, a.flags.c_contiguous or a.flags.f_contiguous
+        count, size, contiguous = a.size, a.itemsize, a.flags.c_contiguous
     if size != esize:
         raise TypeError(f"{where}: {name} has {size}-byte elements, the dictionary {esize}-byte ones")
     if not contiguous:
-        raise ValueError(f"{where}: {name} must be contiguous")
+        raise ValueError(f"{where}: {name} must be contiguous (row-major)")
     if count < n:
         raise ValueError(f"{where}: {name} has {count} elements, {n} needed")
 
@@ -282,6 +282,16 @@ class _BatchArgs:
 
     def __init__(self, dicts, Ys, lambdas, Xs):
         n = len(dicts)
+        if not (len(Ys) == len(lambdas) == len(Xs) == n):
+            raise ValueError("batch: dicts, Ys, lambdas and Xs must have one entry per instance")
+        for i in range(n):
+            nrhs = int(Ys[i].shape[0]) if len(Ys[i].shape) == 2 else 1
+            d = dicts[i]
+            if getattr(d, "N", None) is not None:
+                _check_buffer(Ys[i], d.N * nrhs, d.esize, f"Ys[{i}]", "batch")
+                _check_buffer(Xs[i], d.K * nrhs, d.esize, f"Xs[{i}]", "batch")
+            if np.size(lambdas[i]) < nrhs:
+                raise ValueError(f"batch: lambdas[{i}] has {np.size(lambdas[i])} values, {nrhs} needed")
         self.n = n
         self.dicts = (ctypes.c_void_p * n)(*[d.value for d in dicts])
         self.Y = (ctypes.c_void_p * n)(*[_ptr(y)[0] for y in Ys])

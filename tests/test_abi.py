@@ -257,3 +257,24 @@ def test_server_and_allocation_free_calls_check_their_buffers():
     # well-formed host buffers reach the library, which rejects host pointers (no GPU work)
     with pytest.raises(ds.DscreenError):
         ds.ds_server_submit(None, h, np.zeros(5, f32), 0.5, o, np.zeros(7, f32))
+
+
+def test_batch_arguments_are_checked_per_instance():
+    from paper_1412_4080_gb300 import _binding as B
+
+    h = B._DictHandle()
+    h.N, h.K, h.esize = 5, 7, 4
+    f32 = np.float32
+    o = ds.ds_options_default()
+    Y = np.zeros((3, 5), f32)
+    X = np.zeros((3, 7), f32)
+    with pytest.raises(ValueError):     # right-hand sides stored column-major
+        ds.ds_solve_batch(None, [h], [np.asfortranarray(Y)[:, :]], [np.ones(3)], o, [X])
+    with pytest.raises(ValueError):     # too few solutions
+        ds.ds_solve_batch(None, [h], [Y], [np.ones(3)], o, [np.zeros((2, 7), f32)])
+    with pytest.raises(ValueError):     # too few lambdas
+        ds.ds_solve_batch(None, [h], [Y], [np.ones(2)], o, [X])
+    with pytest.raises(ValueError):     # lists of different lengths
+        ds.ds_solve_batch(None, [h, h], [Y], [np.ones(3)], o, [X])
+    with pytest.raises(ds.DscreenError):  # well-formed: the library rejects the null context
+        ds.ds_solve_batch(None, [h], [Y], [np.ones(3)], o, [X])
