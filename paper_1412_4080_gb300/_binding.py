@@ -428,4 +428,8 @@ def ds_set_history(ctx, hist=None):
     if hist is None:
         _check(lib().ds_set_history(ctx, None, 0), "ds_set_history")
     else:
+        # the library writes max_rows x 6 doubles, row t-1 = iteration t
+        if len(hist.shape) != 2 or hist.shape[1] != len(HIST_COLS):
+            raise ValueError(f"ds_set_history: hist must have shape (rows, {len(HIST_COLS)})")
+        _check_buffer(hist, hist.shape[0] * len(HIST_COLS), 8, "hist", "ds_set_history")
         _check(lib().ds_set_history(ctx, _ptr(hist)[0], int(hist.shape[0])), "ds_set_history")

@@ -278,3 +278,14 @@ def test_batch_arguments_are_checked_per_instance():
         ds.ds_solve_batch(None, [h, h], [Y], [np.ones(3)], o, [X])
     with pytest.raises(ds.DscreenError):  # well-formed: the library rejects the null context
         ds.ds_solve_batch(None, [h], [Y], [np.ones(3)], o, [X])
+
+
+def test_history_buffer_is_checked():
+    with pytest.raises(ValueError):
+        ds.ds_set_history(None, np.zeros((10, 5)))
+    with pytest.raises(TypeError):
+        ds.ds_set_history(None, np.zeros((10, 6), np.float32))
+    with pytest.raises(ValueError):
+        ds.ds_set_history(None, np.asfortranarray(np.zeros((10, 6))))
+    with pytest.raises(ds.DscreenError):  # well-formed: the library rejects the null context
+        ds.ds_set_history(None, np.zeros((10, 6)))
