@@ -225,6 +225,8 @@ def ds_dict_create(ctx, D, group_offsets=None, weights=None, work_prec=None):
     dt = _dtype_code(D)
     goff = None if group_offsets is None else np.ascontiguousarray(group_offsets, dtype=np.int64)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if w is not None and (goff is None or w.size != goff.size - 1):
+        raise ValueError("ds_dict_create: weights need group_offsets and one value per group")
     h = _DictHandle()
     h.N, h.K, h.esize = N, K, 4 if dt == DS_FP32 else 8
     p, _ = _ptr(D)

@@ -289,3 +289,14 @@ def test_history_buffer_is_checked():
         ds.ds_set_history(None, np.asfortranarray(np.zeros((10, 6))))
     with pytest.raises(ds.DscreenError):  # well-formed: the library rejects the null context
         ds.ds_set_history(None, np.zeros((10, 6)))
+
+
+def test_group_weights_are_checked_against_the_offsets():
+    D = np.zeros((4, 6), order="F")
+    goff = np.array([0, 2, 6])
+    with pytest.raises(ValueError):
+        ds.ds_dict_create(None, D, goff, np.ones(3))
+    with pytest.raises(ValueError):
+        ds.ds_dict_create(None, D, None, np.ones(2))
+    with pytest.raises(ds.DscreenError):  # well-formed: the library rejects the null context
+        ds.ds_dict_create(None, D, goff, np.ones(2))
