@@ -49,3 +49,43 @@ def test_job_throughput_single_rank_needs_no_process_group():
     import bench
     value, job_ms = bench.job_throughput(200.0, 15, 5, 1)
     assert job_ms == 200.0 and value == pytest.approx(15 * 5 / 0.2)
+
+
+def _rank_lost(rank, world, port, q):
+    import datetime
+    import time
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        os._exit(3)  # this rank dies between steps, with no collective in flight
+    import bench
+    t0 = time.time()
+    try:
+        bench.job_throughput(100.0, 15, 5, world, dist, "cpu")
+        q.put(("completed", time.time() - t0))
+    except Exception as e:  # the lost peer surfaces as an error of the collective
+        q.put((type(e).__name__, time.time() - t0))
+    q.close()
+    q.join_thread()  # the result is flushed before the hard exit
+    os._exit(0)  # skip destroy_process_group: it would wait for the dead peer
+
+
+def test_a_lost_rank_ends_the_max_over_ranks_with_an_error_gloo():
+    """Failure detection on the host: when one rank dies, the others learn it from their next
+    collective (the max over ranks of the timing), which fails within the process group's
+    timeout instead of hanging."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_lost, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+    what, waited = q.get(timeout=10)
+    print("surviving rank saw:", what, f"after {waited:.1f} s")
+    assert what != "completed" and waited < 60, (what, waited)
