@@ -553,6 +553,9 @@ static ds_status precompute_t(ds_ctx* ctx, ds_dict* dict, const double* w_host)
     cudaStream_t s = ctx->stream;
     const int N = (int)dict->N, K = (int)dict->K, ld = (int)dict->ld;
     ctx->launches += dict->is_group ? 3 : 2;  // norms, (group spectra), max
+    // the launch checks below read the thread's last error: drop a non-sticky one left by an
+    // earlier failed call (an allocation that returned DS_ERR_OOM), which is not this launch's
+    cudaGetLastError();
     colnorm_kernel<T><<<ctx->num_sms * 4, 256, 0, s>>>(reinterpret_cast<const T*>(dict->D), N, K, ld, dict->colnorm);
     if (cudaGetLastError() != cudaSuccess) return DS_ERR_CUDA;
     double* d_fmax = nullptr;

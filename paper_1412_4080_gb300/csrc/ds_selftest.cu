@@ -37,6 +37,7 @@ extern "C" ds_status ds_selftest_wait_timeout(int device, int* status, double* w
         cudaEventCreate(&e1) != cudaSuccess) {
         st = DS_ERR_CUDA;
     } else {
+        cudaGetLastError();  // the check below is about this launch, not an earlier failed call
         cudaEventRecord(e0, 0);
         selftest_wait_kernel<<<2, 32>>>(bar, dstat);
         cudaEventRecord(e1, 0);
