@@ -184,9 +184,20 @@ def cpu_baseline(D32, y32, budget_s=30.0):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    # the small FP64 case of small_fp64_latency, one solve at a time
+    import gen
+    D1, y1, _ = gen.config1(1001)
+    L1 = float(np.linalg.norm(D1, 2) ** 2) * (1 + 1e-6)
+    lm1, _, _ = oracle.lambda_max(D1, y1)
+    ms1 = []
+    for _ in range(3):
+        t1 = time.perf_counter()
+        oracle.solve(D1, y1, 0.5 * lm1, alg="ista", test="dst3", tol=1e-8, max_iter=100000, L=L1)
+        ms1.append(1e3 * (time.perf_counter() - t1))
     return {"value": n / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} oracle FISTA+DST3 solves (lambda/lambda_max = 0.9, 0.7, 0.5, 0.3, 0.1 in turn) of the "
-                      f"same problem in {dt:.1f} s, single thread"}
+                      f"same problem in {dt:.1f} s, single thread",
+            "small_fp64_latency_ms": statistics.median(ms1)}
 
 
 # ------------------------------------------------------------------------ our arm
@@ -360,10 +371,11 @@ def main():
         out["cpu_baseline"] = cpu_baseline(D32, y32)
     if world == 1 and not args.no_modes:
         # last, once every figure above is taken: a failure here is reported in its own entry
-        try:
-            out["group_lasso"] = group_measure()
-        except Exception as e:
-            out["group_lasso"] = {"error": f"{type(e).__name__}: {e}"}
+        for key, fn in (("group_lasso", group_measure), ("small_fp64_latency", config1_latency)):
+            try:
+                out[key] = fn()
+            except Exception as e:
+                out[key] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -695,6 +707,41 @@ def served_measure(ds, ctx, dev, seconds=3.0, rate=200.0, drain_s=20.0, plain_n=
 
 GROUP_RATIOS = (0.2, 0.5, 0.8)
 GROUP_TESTS = ("gsafe", "dgst3")
+
+
+def config1_latency(reps=10, warmup=3):
+    """Latency of the small FP64 case (100 x 500 Gaussian unit-norm D, 10 nonzeros, sigma 0.01,
+    seed 1001): ISTA + dynamic DST3 at lambda = 0.5 lambda_max to gap 1e-8 * 1/2 ||y||^2, one
+    ds_solve at a time, CUDA events on the library's stream (D fits in cache: no flush)."""
+    import torch
+    import gen
+    import paper_1412_4080_gb300 as ds
+    D, y, _ = gen.config1(1001)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    Dt = torch.from_numpy(np.ascontiguousarray(D.T)).to(dev).t()  # column-major (N, K), FP64
+    yt = torch.from_numpy(np.ascontiguousarray(y)).to(dev)
+    x = torch.empty(D.shape[1], dtype=torch.float64, device=dev)
+    ctx = ds.ds_create(0, stream)
+    dct = ds.ds_dict_create(ctx, Dt)
+    o = ds.ds_options_default(alg="ista", test="dst3", tol_gap_rel=1e-8, max_iter=100000, lambda_rel=1)
+    for _ in range(warmup):
+        ds.ds_solve(ctx, dct, yt, 0.5, o, x)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms, res = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        res.append(ds.ds_solve(ctx, dct, yt, 0.5, o, x))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    ds.ds_dict_destroy(dct)
+    ds.ds_destroy(ctx)
+    return {"median_ms": statistics.median(ms), "min_ms": min(ms), "iters": res[-1]["iters"],
+            "converged": all(r["status"] == 0 for r in res),
+            "workload": "100x500 FP64 Gaussian, 10 nonzeros, sigma 0.01 (seed 1001), ISTA + dynamic DST3, "
+                        "lambda = 0.5 lambda_max, gap 1e-8; one solve per call"}
 
 
 def group_measure(steps=3, warmup=3):

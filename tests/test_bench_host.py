@@ -10,3 +10,8 @@ def test_group_measurement_fails_with_an_ordinary_exception():
     process."""
     with pytest.raises(Exception):
         bench.group_measure(steps=1, warmup=0)
+
+
+def test_small_fp64_latency_fails_with_an_ordinary_exception():
+    with pytest.raises(Exception):
+        bench.config1_latency(reps=1, warmup=0)
