@@ -300,3 +300,14 @@ def test_group_weights_are_checked_against_the_offsets():
         ds.ds_dict_create(None, D, None, np.ones(2))
     with pytest.raises(ds.DscreenError):  # well-formed: the library rejects the null context
         ds.ds_dict_create(None, D, goff, np.ones(2))
+
+
+def test_oracle_compiles_without_warnings(tmp_path):
+    """The oracle's C source is warning-free under -Wall -Wextra -Wpedantic -Wshadow."""
+    import os
+    import subprocess
+
+    import oracle
+
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-Wall", "-Wextra", "-Wpedantic", "-Wshadow", "-Werror",
+                           "-fsyntax-only", os.path.abspath(oracle._SRC)])
