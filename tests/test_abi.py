@@ -311,3 +311,14 @@ def test_oracle_compiles_without_warnings(tmp_path):
 
     subprocess.check_call(["gcc", "-std=c99", "-O2", "-Wall", "-Wextra", "-Wpedantic", "-Wshadow", "-Werror",
                            "-fsyntax-only", os.path.abspath(oracle._SRC)])
+
+
+def test_header_compiles_as_cpp17(tmp_path):
+    """C++ callers include the same header (its declarations sit in extern "C")."""
+    import os
+    import subprocess
+
+    src = tmp_path / "user.cpp"
+    src.write_text('#include "dscreen.h"\nint main() { ds_options o; return ds_options_default(&o) == DS_OK ? 0 : 1; }\n')
+    subprocess.check_call(["g++", "-std=c++17", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I",
+                           os.path.dirname(ds.HEADER), "-c", str(src), "-o", str(tmp_path / "user.o")])
