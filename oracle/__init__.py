@@ -1,8 +1,9 @@
 """FP64 CPU oracle for dynamic screening (arXiv 1412.4080).
 
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
-and by the CPU-baseline leg of ``bench.py``.  The product path (the CUDA
-library under ``paper_1412_4080_gb300/`` and its binding) never imports it.
+and by ``bench.py``'s CPU-baseline leg and reference arm (``--impl reference``).
+The product path (the CUDA library under ``paper_1412_4080_gb300/`` and its
+binding) never imports it.
 
 The arithmetic lives in ``dscreen_oracle.c`` (plain C loops, double
 precision, single thread); this module compiles it with gcc on first use and

@@ -4,7 +4,8 @@
  * First-Order Algorithms for the Lasso and Group-Lasso", arXiv 1412.4080).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is compiled and called by the test
- * suite, by the smoke check and by the CPU-baseline leg of the benchmark.
+ * suite, by the smoke check, and by the benchmark's CPU-baseline leg and
+ * reference arm.
  * The product (the CUDA library and its Python binding) never links, loads
  * or calls it, and it shares no code, header, table or helper with it.
  *
