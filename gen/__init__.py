@@ -78,6 +78,19 @@ def group_x0(goff: np.ndarray, n_active: int, g: np.random.Generator) -> np.ndar
     return x
 
 
+def bernoulli_group_x0(goff: np.ndarray, p: float, g: np.random.Generator) -> np.ndarray:
+    """Each group active independently with probability p (at least one active), N(0, 1)
+    entries in the active groups (the paper's Group-Lasso data, Sec. 4.2)."""
+    nG = goff.size - 1
+    act = g.uniform(size=nG) < p
+    if not act.any():
+        act[g.integers(nG)] = True
+    x = np.zeros(int(goff[-1]))
+    for gi in np.flatnonzero(act):
+        x[goff[gi]:goff[gi + 1]] = g.standard_normal(int(goff[gi + 1] - goff[gi]))
+    return x
+
+
 def observe(D, x0, g: np.random.Generator, snr_db: float | None = 20.0, sigma: float | None = None):
     s = D @ x0
     e = g.standard_normal(D.shape[0])
@@ -154,3 +167,19 @@ def config3(seed: int = 1003, N: int = 2000, K: int = 10000, gsize: int = 10, n_
     x0 = group_x0(goff, n_active, g)
     y = observe(D, x0, g, snr_db=20.0)
     return D, y, x0, goff, w
+
+
+def paper_group_problem(gsize: int, seed: int, N: int = 2000, K: int = 10000, kind: str = "pnoise",
+                        p: float = 0.05):
+    """The paper's Group-Lasso experiment (Sec. 4.2, Sec. 4.4): a Pnoise (or Gaussian)
+    dictionary, groups of gsize atoms, each group active with probability p, N(0,1)
+    coefficients, y the l2-normalised sum of D x0 and a 20 dB Gaussian noise; weights
+    w_g = sqrt(gsize).  The paper draws random groups of equal size; the atoms are
+    i.i.d., so contiguous groups of a freshly drawn dictionary have the same law."""
+    g = rng(seed)
+    D = pnoise_dict(N, K, g) if kind == "pnoise" else gaussian_dict(N, K, g)
+    goff = contiguous_groups(K, gsize)
+    w = np.full(goff.size - 1, np.sqrt(gsize))
+    x0 = bernoulli_group_x0(goff, p, g)
+    y = observe(D, x0, g, snr_db=20.0)
+    return D, y / np.linalg.norm(y), x0, goff, w

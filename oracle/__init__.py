@@ -76,6 +76,13 @@ def _load():
                                  ctypes.POINTER(_Options), dp, dp, ctypes.POINTER(ctypes.c_int), dp, dp,
                                  ctypes.POINTER(_Result)]
         lib.or_solve.restype = ctypes.c_int
+        lib.or_solve_log.argtypes = [dp, i64, i64, i64, dp, ctypes.c_double, i64p, dp, i64,
+                                     ctypes.POINTER(_Options), dp, dp, ctypes.POINTER(ctypes.c_int), dp, dp, dp,
+                                     ctypes.c_int, ctypes.POINTER(_Result)]
+        lib.or_solve_log.restype = ctypes.c_int
+        lib.or_sequential_screen.argtypes = [dp, i64, i64, i64, dp, ctypes.c_double, i64p, dp, i64, ctypes.c_int,
+                                             dp, ctypes.POINTER(ctypes.c_int), dp, dp, dp, dp]
+        lib.or_sequential_screen.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -140,9 +147,11 @@ def dome_max(dc0, t, psi, R):
 
 
 def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynamic=True,
-          tol=1e-6, max_iter=1000, L=None, x0=None, cp_tau=0.0, cp_sigma=0.0, cp_gamma=0.0):
+          tol=1e-6, max_iter=1000, L=None, x0=None, cp_tau=0.0, cp_sigma=0.0, cp_gamma=0.0, margins=0):
     """Solve eq. (1) with Algorithm 3 and the ISTA, FISTA or Chambolle-Pock ("cp") update of Table 1.
-    Returns a dict with x, scr_iter, hist, theta (theta_t of the last iteration) and scalars."""
+    Returns a dict with x, scr_iter, hist, theta (theta_t of the last iteration) and scalars; with
+    margins=T > 0 also "margins": (min(iters, T) + 1) x G test margins, row 0 the static test, row t
+    the test of iteration t (NaN where a group was not tested)."""
     lib = _load()
     D, N, K, ld = _dict(D)
     y = np.ascontiguousarray(y, dtype=np.float64)
@@ -155,14 +164,43 @@ def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynami
     theta = np.zeros(N)
     res = _Result()
     x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
-    rc = lib.or_solve(_dptr(D), N, K, ld, _dptr(y), float(lam),
-                      None if goff is None else goff.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                      _dptr(w), nG, ctypes.byref(opt), _dptr(x0a), _dptr(x),
-                      scr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(hist), _dptr(theta),
-                      ctypes.byref(res))
+    G = K if goff is None else nG
+    rows = int(margins) + 1 if margins else 0
+    mlog = np.empty((rows, G)) if margins else None
+    rc = lib.or_solve_log(_dptr(D), N, K, ld, _dptr(y), float(lam),
+                          None if goff is None else goff.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                          _dptr(w), nG, ctypes.byref(opt), _dptr(x0a), _dptr(x),
+                          scr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(hist), _dptr(theta),
+                          _dptr(mlog), rows, ctypes.byref(res))
     if rc != 0:
         raise ValueError("oracle solve rejected its input")
     it = res.iters
-    return {"x": x, "scr_iter": scr, "hist": hist[:it], "theta": theta, "iters": it, "gap": res.gap,
-            "primal": res.primal, "dual": res.dual, "lambda_max": res.lambda_max, "L": res.L,
-            "n_active": res.n_active, "nnz": res.nnz, "status": res.status}
+    out = {"x": x, "scr_iter": scr, "hist": hist[:it], "theta": theta, "iters": it, "gap": res.gap,
+           "primal": res.primal, "dual": res.dual, "lambda_max": res.lambda_max, "L": res.L,
+           "n_active": res.n_active, "nnz": res.nnz, "status": res.status}
+    if margins:
+        out["margins"] = mlog[: min(it, rows - 1) + 1]
+    return out
+
+
+def sequential_screen(D, y, lam, theta, groups=None, weights=None, test="safe"):
+    """The safe test at lambda from the dual point theta scaled over the whole dictionary
+    (Lemma 8), e.g. theta = D x_k - y of a solution at a previous lambda_k.
+    Returns a dict: screened (K bools), margins (G), R, radius, mu."""
+    lib = _load()
+    D, N, K, ld = _dict(D)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    goff, w, nG = _groups(groups, weights)
+    G = K if goff is None else nG
+    scr = np.zeros(K, dtype=np.int32)
+    marg = np.empty(G)
+    R, rad, mu = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.or_sequential_screen(_dptr(D), N, K, ld, _dptr(y), float(lam),
+                                  None if goff is None else goff.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  _dptr(w), nG, TESTS[test], _dptr(th),
+                                  scr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _dptr(marg),
+                                  ctypes.byref(R), ctypes.byref(rad), ctypes.byref(mu))
+    if rc != 0:
+        raise ValueError("oracle sequential_screen rejected its input")
+    return {"screened": scr.astype(bool), "margins": marg, "R": R.value, "radius": rad.value, "mu": mu.value}

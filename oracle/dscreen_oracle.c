@@ -23,12 +23,12 @@
  *   tests           Lemma 2 (SAFE), Lemma 3 (DST3), Lemma 4 (dynamic Dome),
  *                   Lemma 5 (GSAFE), Lemma 6 (DGST3), Lemma 7 (sphere test)
  *   static variant  Algorithm 1 / Algorithm 4 (test once at theta = -y)
+ *   lambda paths    Sec. 5: the sequential test from a previous lambda's dual point
  *
- * Pinned only partially: the intermediate Chambolle-Pock iterates are pinned through the
- * fixed point they reach (the minimiser, also for tau_0 != sigma_0), the first test (the
- * static one) and, with gamma = 0, the Fejer monotonicity of a proximal point method in
- * the metric of the two steps; a smaller extrapolation factor, and the phi, tau, sigma
- * schedule of gamma > 0, pass those pins (see the test suite).
+ * The Table 1 recurrences (FISTA's l_t, Chambolle-Pock's steps, schedule and
+ * extrapolation) are pinned by iterates worked by hand on a 1 x 1 problem; the
+ * constants the paper leaves open (theta_0 = 0, tau_0 = sigma_0 = 0.99 / sqrt(L)) are
+ * readings, and those pins fix the oracle to them.
  *
  * Readings of the paper that this file takes (where the text is silent,
  * garbled or specialised):
@@ -376,9 +376,14 @@ static int prepare_test(or_ctx* c, const double* b)
 
 /* Apply the test with dual point theta (whose correlations with the active
  * atoms are z, m = max |z| or max ||z_g||/w_g over active groups).  Marks newly
- * screened groups in scr_group[] with iteration number it.  Returns mu. */
+ * screened groups in scr_group[] with iteration number it.  Returns mu.
+ * marg (nullable, G entries) receives each active group's test margin: the
+ * quantity the test requires to be positive (sphere tests, Lemma 7:
+ * (w_g - ||D_g^T c||) / ||D_g|| - r; Dome, Lemma 4: 1/||d_i|| minus the larger
+ * of the two dome maxima), NAN for inactive groups or without a test.  A group
+ * is screened when its margin exceeds OR_MARGIN. */
 static double screen(or_ctx* c, const double* theta, double m, const char* active_g,
-                     int* scr_group, int it, double* R_out, double* rad_out)
+                     int* scr_group, int it, double* R_out, double* rad_out, double* marg)
 {
     int64_t N = c->N, K = c->K;
     int64_t G = n_groups(c->goff, c->nG, K);
@@ -398,25 +403,28 @@ static double screen(or_ctx* c, const double* theta, double m, const char* activ
     }
     *R_out = R;
     *rad_out = rad;
+    if (marg)
+        for (int64_t g = 0; g < G; g++) marg[g] = NAN;
     if (c->test == OR_TEST_NONE) return mu;
     for (int64_t g = 0; g < G; g++) {
         if (!active_g[g]) continue;
-        int kill = 0;
+        double margin;
         if (c->test == OR_TEST_DOME) {
             /* Lemma 4 (dynamic form): max over the dome of |d_i^T theta| < 1 */
             double ni = c->nrm[g];
             double dc0 = c->b[g] / (lam * ni); /* (d_i/||d_i||)^T y / lambda */
             double up = or_dome_max(dc0, c->tdome[g], c->psi_dome, R);
             double lo = or_dome_max(-dc0, -c->tdome[g], c->psi_dome, R);
-            kill = 1.0 / ni - up > OR_MARGIN && 1.0 / ni - lo > OR_MARGIN;
+            margin = 1.0 / ni - (up > lo ? up : lo);
         } else if (c->lasso) {
             /* Lemma 2 / Lemma 3: (1 - |d_i^T c|) / ||d_i|| > r */
-            kill = (1.0 - fabs(c->dtc[g])) / c->nrm[g] - rad > OR_MARGIN;
+            margin = (1.0 - fabs(c->dtc[g])) / c->nrm[g] - rad;
         } else {
             /* Lemma 5 / Lemma 6 via Lemma 7: (w_g - ||D_g^T c||) / ||D_g|| > r */
-            kill = (g_w(c->w, g) - c->dtc[g]) / c->nrm[g] - rad > OR_MARGIN;
+            margin = (g_w(c->w, g) - c->dtc[g]) / c->nrm[g] - rad;
         }
-        if (kill) scr_group[g] = it;
+        if (marg) marg[g] = margin;
+        if (margin > OR_MARGIN) scr_group[g] = it;
     }
     return mu;
 }
@@ -456,11 +464,16 @@ static double omega(const or_ctx* c, const double* x)
  * was screened (0 = never, -1 = by the static test before the loop).
  * hist (nullable): max_iter rows of OR_NH doubles.
  * theta_out (nullable): N doubles, theta_t of the last iteration run (Table 1's dual
- * variable; left untouched when no iteration runs). */
-int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y, double lambda,
-             const int64_t* goff, const double* w, int64_t nG,
-             const or_options* opt, const double* x0,
-             double* x_out, int* scr_iter, double* hist, double* theta_out, or_result* res)
+ * variable; left untouched when no iteration runs).
+ * margin_log (nullable): margin_rows rows of G doubles (G = groups; the Lasso: K),
+ * row 0 the static test of Algorithm 1 and row t the test of iteration t (for
+ * t < margin_rows): each group's test margin (see screen()), NAN where the
+ * group was not tested. */
+int or_solve_log(const double* D, int64_t N, int64_t K, int64_t ld, const double* y, double lambda,
+                 const int64_t* goff, const double* w, int64_t nG,
+                 const or_options* opt, const double* x0,
+                 double* x_out, int* scr_iter, double* hist, double* theta_out, double* margin_log,
+                 int margin_rows, or_result* res)
 {
     if (!D || !y || !x_out || !opt || !res || N <= 0 || K <= 0 || ld < N || !(lambda > 0)) return -1;
     if (!goff) w = NULL; /* the Lasso: singleton groups of weight 1 */
@@ -486,6 +499,9 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
     for (int64_t i = 0; i < K; i++) x_out[i] = 0.0;
     if (scr_iter)
         for (int64_t i = 0; i < K; i++) scr_iter[i] = 0;
+    if (margin_rows < 1) margin_log = NULL;
+    if (margin_log)
+        for (int64_t q = 0; q < (int64_t)margin_rows * n_groups(goff, nG, K); q++) margin_log[q] = NAN;
     /* lambda >= lambda_*: x = 0, theta = y/lambda is dual optimal (Sec. 2.2.2, eq. gstar) */
     if (lambda >= c.lambda_star) {
         res->primal = 0.5 * yy;
@@ -534,7 +550,7 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
             if (val > m) m = val;
         }
         double R, rad;
-        screen(&c, theta, m, act, scr, -1, &R, &rad);
+        screen(&c, theta, m, act, scr, -1, &R, &rad, margin_log);
         for (int64_t g = 0; g < G; g++)
             if (scr[g]) {
                 act[g] = 0;
@@ -605,11 +621,12 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
         double R, rad;
         double mu;
         if (opt->dynamic && opt->test != OR_TEST_NONE) {
-            mu = screen(&c, theta, m, act, scr, it, &R, &rad);
+            mu = screen(&c, theta, m, act, scr, it, &R, &rad,
+                        margin_log && it < margin_rows ? margin_log + (size_t)it * G : NULL);
         } else {
             int save = c.test;
             c.test = OR_TEST_NONE; /* R and mu only, for the gap */
-            mu = screen(&c, theta, m, act, scr, it, &R, &rad);
+            mu = screen(&c, theta, m, act, scr, it, &R, &rad, NULL);
             c.test = save;
         }
         /* xbar_t, ubar_t: restriction to the atoms still active */
@@ -665,4 +682,75 @@ int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y,
     free(x); free(u); free(xn); free(v); free(z); free(theta); free(r); free(act); free(scr);
     free(b); free(c.dtc); free(c.nrm); free(c.tdome);
     return 0;
+}
+
+/* or_solve_log without the margin log. */
+int or_solve(const double* D, int64_t N, int64_t K, int64_t ld, const double* y, double lambda,
+             const int64_t* goff, const double* w, int64_t nG,
+             const or_options* opt, const double* x0,
+             double* x_out, int* scr_iter, double* hist, double* theta_out, or_result* res)
+{
+    return or_solve_log(D, N, K, ld, y, lambda, goff, w, nG, opt, x0, x_out, scr_iter, hist, theta_out, NULL, 0,
+                        res);
+}
+
+/* Sequential screening along a regularization path (Discussion, Sec. 5): the
+ * feasible set of the dual problem, {theta : |d_i^T theta| <= 1} (groups:
+ * ||D_g^T theta|| <= w_g), does not depend on lambda, so a dual point scaled
+ * into it from any theta -- e.g. the residual D x_k - y of the solution at a
+ * previous lambda_k -- yields, by Lemma 8 at the new lambda, a safe region for
+ * that lambda.  This applies the chosen test (Lemmas 2-7) once, with the
+ * correlations of theta with ALL atoms (the scaling must hold for the whole
+ * dictionary, not only for the atoms active at lambda_k).
+ * screened (K ints): 1 for the atoms of screened groups, else 0.
+ * margin (nullable, G doubles): each group's test margin.  *R_out, *rad_out,
+ * *mu_out (nullable): R = ||y/lambda - mu theta||, the test radius, mu.
+ * Returns 0, or -1 on bad input (or lambda >= lambda_*, where x = 0 and no
+ * test is needed). */
+int or_sequential_screen(const double* D, int64_t N, int64_t K, int64_t ld, const double* y, double lambda,
+                         const int64_t* goff, const double* w, int64_t nG, int test, const double* theta,
+                         int* screened, double* margin, double* R_out, double* rad_out, double* mu_out)
+{
+    if (!D || !y || !theta || !screened || N <= 0 || K <= 0 || ld < N || !(lambda > 0)) return -1;
+    if (!goff) w = NULL;
+    or_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.D = D; c.y = y; c.N = N; c.K = K; c.ld = ld; c.goff = goff; c.w = w; c.nG = nG;
+    c.lasso = goff == NULL;
+    c.lambda = lambda;
+    c.test = test;
+    int64_t G = n_groups(goff, nG, K);
+    double* b = (double*)malloc(sizeof(double) * K);
+    or_lambda_max(D, N, K, ld, y, goff, w, nG, &c.lambda_star, &c.star, b);
+    if (lambda >= c.lambda_star) { free(b); return -1; }
+    c.dtc = (double*)malloc(sizeof(double) * (size_t)G);
+    c.nrm = (double*)malloc(sizeof(double) * (size_t)G);
+    c.b = b;
+    c.tdome = (double*)malloc(sizeof(double) * (size_t)K);
+    char* act = (char*)malloc((size_t)G);
+    memset(act, 1, (size_t)G); /* every group is tested */
+    int* scr = (int*)calloc((size_t)G, sizeof(int));
+    int rc = prepare_test(&c, b);
+    if (rc == 0) {
+        /* m = max_g ||D_g^T theta|| / w_g over every group */
+        double m = 0.0;
+        for (int64_t g = 0; g < G; g++) {
+            double q = 0.0;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
+                double z = col_dot(D, ld, i, theta, N);
+                q += z * z;
+            }
+            double val = sqrt(q) / g_w(w, g);
+            if (val > m) m = val;
+        }
+        double R, rad;
+        double mu = screen(&c, theta, m, act, scr, 1, &R, &rad, margin);
+        for (int64_t g = 0; g < G; g++)
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) screened[i] = scr[g] != 0;
+        if (R_out) *R_out = R;
+        if (rad_out) *rad_out = rad;
+        if (mu_out) *mu_out = mu;
+    }
+    free(b); free(c.dtc); free(c.nrm); free(c.tdome); free(act); free(scr);
+    return rc;
 }

@@ -72,3 +72,16 @@ def test_named_workload_shapes():
     D, y, x0, goff, w = gen.config3(N=200, K=1000)
     assert goff.size - 1 == 100 and np.allclose(w, np.sqrt(10))
     assert sum(np.any(x0[goff[i]:goff[i + 1]] != 0) for i in range(100)) == 10
+
+
+def test_paper_group_problem_bernoulli_groups():
+    """Sec. 4.2: groups active with probability 0.05, N(0,1) coefficients in active
+    groups only, unit-norm observation, Pnoise atoms, w_g = sqrt(group size)."""
+    D, y, x0, goff, w = gen.paper_group_problem(5, seed=7, N=200, K=4000)
+    assert D.shape == (200, 4000) and np.allclose(np.linalg.norm(D, axis=0), 1.0)
+    assert abs(np.linalg.norm(y) - 1.0) < 1e-12
+    assert np.allclose(w, np.sqrt(5.0)) and goff[-1] == 4000 and np.all(np.diff(goff) == 5)
+    act = np.array([np.any(x0[goff[i]:goff[i + 1]] != 0) for i in range(goff.size - 1)])
+    assert all(np.all(x0[goff[i]:goff[i + 1]] != 0) for i in np.flatnonzero(act))
+    assert 0.03 < act.mean() < 0.07  # 800 groups, Bernoulli(0.05)
+    assert np.median(D[0]) > 0.5  # Pnoise atoms cluster around e_1 (Gaussian atoms: about 0)

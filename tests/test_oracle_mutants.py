@@ -65,7 +65,7 @@ MUTANTS = {
                                    "v[i] = cp ? x[i] - tau * z[i] : x[i] - z[i] / L;", "Table 1 FISTA gradient point"),
     "fista_without_momentum": ("beta = (l - 1.0) / ln;", "beta = 0.0 * (l - 1.0) / ln;", "Table 1 FISTA momentum"),
     "step_constant_below_norm": ("* (1.0 + 1e-6);", "* (1.0 - 1e-3);", "L >= ||D||^2 behind Table 1"),
-    "screened_atoms_rescreened": ("        if (!active_g[g]) continue;\n        int kill = 0;", "        int kill = 0;",
+    "screened_atoms_rescreened": ("        if (!active_g[g]) continue;\n        double margin;", "        double margin;",
                                   "Algorithm 3 screens each atom once"),
     "warm_start_u_unset": ("{ x[i] = x0[i]; u[i] = x0[i]; }", "{ x[i] = x0[i]; }", "warm start x_0 = u_0"),
     "gap_at_extrapolated_point": ("            if (x[i] != 0.0)\n                for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * x[i];",
@@ -86,31 +86,32 @@ MUTANTS = {
                            "Table 1 Chambolle-Pock proximal threshold"),
     "cp_extrapolation_dropped": ("            beta = phi;\n", "            beta = 0.0 * phi;\n",
                                  "Table 1 Chambolle-Pock extrapolation (Arrow-Hurwicz without it)"),
+    "cp_tau_schedule_inverted": ("tau *= phi;", "tau /= phi;", "Table 1 Chambolle-Pock step schedule (gamma > 0)"),
+    "cp_sigma_schedule_inverted": ("sigma /= phi;", "sigma *= phi;", "Table 1 Chambolle-Pock step schedule (gamma > 0)"),
+    "fista_sequence_other_constant": ("sqrt(1.0 + 4.0 * l * l)", "sqrt(1.0 + 2.0 * l * l)", "Table 1 FISTA l_t"),
+    "fista_sequence_linear": ("double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));", "double ln = l + 1.0 / 3.0;",
+                              "Table 1 FISTA l_t"),
+    "cp_dual_start_minus_y": ("        for (int64_t n = 0; n < N; n++) theta[n] = 0.0;\n    int it;",
+                              "        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];\n    int it;",
+                              "the reading theta_0 = 0 of Table 1 Chambolle-Pock"),
+    "cp_extrapolation_halved": ("            beta = phi;\n", "            beta = 0.5 * phi;\n",
+                                "Table 1 Chambolle-Pock extrapolation factor"),
+    "cp_default_steps_smaller": ("double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.99 / sqrt(L);",
+                                 "double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.5 / sqrt(L);",
+                                 "the reading tau_0 = sigma_0 = 0.99 / sqrt(L)"),
+    "margin_log_scaled_by_norm": ("if (marg) marg[g] = margin;", "if (marg) marg[g] = margin * c->nrm[g];",
+                                  "logged test margins (Lemmas 2, 4 for unnormalised atoms)"),
+    "dome_margin_smaller_maximum": ("margin = 1.0 / ni - (up > lo ? up : lo);", "margin = 1.0 / ni - (up < lo ? up : lo);",
+                                    "Lemma 4: both signs of d_i^T theta"),
+    "sequential_scaling_underestimated": ("                double z = col_dot(D, ld, i, theta, N);\n                q += z * z;",
+                                          "                double z = col_dot(D, ld, i, theta, N);\n                q += 0.25 * z * z;",
+                                          "Lemma 8 feasibility of the sequential dual point"),
+
 }
 
 # Mistakes that no pin catches, each with the reason; they run as strict xfails,
 # so a pin that starts to catch one turns its entry into a failure to update.
-KNOWN_SURVIVORS = {
-    "cp_tau_schedule_inverted": ("tau *= phi;", "tau /= phi;",
-                                 "acts only with gamma > 0 (the accelerated form for a strongly convex penalty); "
-                                 "the pins fix only that gamma = 1 stalls the Lasso"),
-    "cp_sigma_schedule_inverted": ("sigma /= phi;", "sigma *= phi;", "acts only with gamma > 0, as above"),
-    "fista_sequence_other_constant": ("sqrt(1.0 + 4.0 * l * l)", "sqrt(1.0 + 2.0 * l * l)",
-                                      "still an O(1/t^2) momentum sequence within the Beck-Teboulle bound"),
-    "fista_sequence_linear": ("double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));", "double ln = l + 1.0 / 3.0;",
-                              "the Chambolle-Dossal sequence (t + 2) / 3, also an O(1/t^2) method"),
-    "cp_dual_start_minus_y": ("        for (int64_t n = 0; n < N; n++) theta[n] = 0.0;\n    int it;",
-                              "        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];\n    int it;",
-                              "theta_0 is not fixed by the paper: theta_0 = -y is another reading, with the same "
-                              "first test and the same fixed point"),
-    "cp_extrapolation_halved": ("            beta = phi;\n", "            beta = 0.5 * phi;\n",
-                                "the dual objective is strongly convex, so Chambolle-Pock with a smaller "
-                                "extrapolation factor still converges to the saddle point, Fejer-monotone"),
-    "cp_default_steps_smaller": ("double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.99 / sqrt(L);",
-                                 "double tau = opt->cp_tau > 0 ? opt->cp_tau : 0.5 / sqrt(L);",
-                                 "tau_0 and sigma_0 are not fixed by the paper: any tau_0 sigma_0 ||D||^2 < 1 is "
-                                 "another reading"),
-}
+KNOWN_SURVIVORS = {}
 
 _CHILD = (
     "import sys\n"

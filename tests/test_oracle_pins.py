@@ -706,3 +706,196 @@ def test_chambolle_pock_iterates_are_fejer_monotone(steps):
     for a, b in zip(z[:-1], z[1:]):
         lhs = m2(b[0] - xs, b[1] - ts) + m2(b[0] - a[0], b[1] - a[1])
         assert lhs <= m2(a[0] - xs, a[1] - ts) + 1e-10 * d0
+
+
+# ------------------------------------------------- per-atom test margins
+
+def _unequal_norm_problem(seed, N=40, K=300):
+    g = gen.rng(seed)
+    D = np.asfortranarray(gen.gaussian_dict(N, K, g) * (0.5 + 1.5 * g.random(K)))
+    y = D @ gen.sparse_x0(K, 4, g) + 0.05 * g.standard_normal(N)
+    return D, y
+
+
+@pytest.mark.parametrize("test", ["safe", "dome"])
+def test_logged_margins_are_the_region_maximum(test):
+    """Dynamic tests, atoms of unequal norms: the margin logged for atom i at iteration
+    t is (1 - max |d_i^T theta| over the region of iteration t) / ||d_i|| (SAFE: the
+    ball of radius R_t about y/lambda, Lemma 2; Dome: that ball cut by
+    d_*^T theta <= 1, Lemma 4), the maximum found by brute force in the plane of d_*
+    and d_i; and an atom is screened at the first iteration whose margin is positive."""
+    D, y = _unequal_norm_problem(43)
+    K = D.shape[1]
+    lm, star, b = oracle.lambda_max(D, y)
+    ds = np.sign(b[star]) * D[:, star]
+    nrm = np.linalg.norm(D, axis=0)
+    T = 30
+    compared = screened = 0
+    for ratio in (0.5, 0.8):
+        lam = ratio * lm
+        r = oracle.solve(D, y, lam, alg="fista", test=test, tol=0, max_iter=T, margins=T)
+        M = r["margins"]
+        assert M.shape == (T + 1, K) and np.all(np.isnan(M[0]))  # no static test
+        for t in (1, 2, 5, 12, 30):
+            mx = _region_max(D, y, lam, lm, ds, r["hist"][t - 1, 2], dome=test == "dome")
+            tested = ~np.isnan(M[t])
+            np.testing.assert_allclose(M[t][tested] * nrm[tested], 1.0 - mx[tested], atol=1e-6)
+            compared += int(tested.sum())
+        s = r["scr_iter"]
+        for i in range(K):
+            pos = np.flatnonzero(~np.isnan(M[1:, i]) & (M[1:, i] > 1e-12)) + 1
+            if s[i] > 0:
+                assert pos.size == 1 and pos[0] == s[i] and np.all(np.isnan(M[s[i] + 1:, i]))
+                screened += 1
+            else:
+                assert pos.size == 0 and not np.any(np.isnan(M[1:, i]))
+    assert compared > 1000 and screened > 10
+
+
+@pytest.mark.parametrize("ratio", [0.8, 0.9])
+def test_dst3_ball_lies_between_the_dome_and_its_half_space_cut(ratio):
+    """Lemma 3 vs Lemma 4 from the same dual point: the DST3 sphere contains the dome
+    (ball cut by d_*^T theta <= 1), so every DST3 margin is at most the dome margin;
+    the dome lies in the SAFE ball, so every SAFE margin is at most the dome margin."""
+    D, y = _unequal_norm_problem(44)
+    D = gen._normalise(D)  # the dome needs unit atoms
+    lm, _, _ = oracle.lambda_max(D, y)
+    theta = D @ oracle.solve(D, y, 0.95 * lm, test="none", tol=1e-12, max_iter=50000)["x"] - y
+    m = {t: oracle.sequential_screen(D, y, ratio * lm, theta, test=t) for t in ("safe", "dst3", "dome")}
+    assert np.all(m["dst3"]["margins"] <= m["dome"]["margins"] + 1e-12)
+    assert np.all(m["safe"]["margins"] <= m["dome"]["margins"] + 1e-12)
+    assert m["dome"]["screened"].sum() >= max(m["safe"]["screened"].sum(), m["dst3"]["screened"].sum(), 1)
+
+
+# ------------------------------------- sequential screening (lambda paths)
+
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome"])
+def test_sequential_screen_is_safe_from_any_dual_point(test):
+    """Discussion (Sec. 5), regularization paths: the dual feasible set does not
+    depend on lambda, so Lemma 8's scaling of any theta over the whole dictionary
+    gives a safe region at any lambda.  Tiny problems: atoms screened from the
+    residual of the brute-force solution at the previous lambda, and from random
+    theta, are zero in the brute-force minimiser at the next lambda."""
+    screened = 0
+    for seed in (61, 62, 63):
+        g = gen.rng(seed)
+        N, K = 6, 9
+        D = gen.gaussian_dict(N, K, g)
+        y = D @ gen.sparse_x0(K, 2, g) + 0.05 * g.standard_normal(N)
+        lm, _, _ = oracle.lambda_max(D, y)
+        ratios = (0.95, 0.8, 0.6, 0.4)
+        xs = [_lasso_bruteforce(D, y, r * lm) for r in ratios]
+        for k in range(1, len(ratios)):
+            for theta in (D @ xs[k - 1] - y, g.standard_normal(N)):
+                s = oracle.sequential_screen(D, y, ratios[k] * lm, theta, test=test)
+                assert not np.any(xs[k][s["screened"]] != 0), (seed, k, test)
+                screened += int(s["screened"].sum())
+    assert screened > 5
+
+
+@pytest.mark.parametrize("test", ["safe", "dome"])
+def test_sequential_margins_are_the_region_maximum(test):
+    """The sequential test's margins equal (1 - the brute-force maximum of |d_i^T theta|
+    over its region) / ||d_i||, with R = ||y/lambda - mu theta||, where mu is no worse
+    than any feasible scaling found by a 1-D scan (Lemma 8)."""
+    D, y = _unequal_norm_problem(45)
+    if test == "dome":
+        D = gen._normalise(D)
+    lm, star, b = oracle.lambda_max(D, y)
+    ds = np.sign(b[star]) * D[:, star]
+    nrm = np.linalg.norm(D, axis=0)
+    theta = D @ oracle.solve(D, y, 0.9 * lm, test="none", tol=1e-12, max_iter=50000)["x"] - y
+    lam = 0.7 * lm
+    s = oracle.sequential_screen(D, y, lam, theta, test=test)
+    m = np.abs(D.T @ theta).max()
+    grid = np.linspace(-1 / m, 1 / m, 200001)
+    best = np.linalg.norm(grid[:, None] * theta[None, :] - y[None, :] / lam, axis=1).min()
+    assert abs(s["mu"]) * m <= 1 + 1e-12
+    assert abs(s["R"] - np.linalg.norm(s["mu"] * theta - y / lam)) <= 1e-12 * s["R"]
+    assert s["R"] <= best + 1e-12
+    mx = _region_max(D, y, lam, lm, ds, s["R"], dome=test == "dome")
+    np.testing.assert_allclose(s["margins"] * nrm, 1.0 - mx, atol=1e-6)
+    assert 0 < s["screened"].sum() < D.shape[1]
+
+
+@pytest.mark.parametrize("test", ["safe", "dst3", "dome", "gsafe", "dgst3"])
+def test_warm_started_first_test_is_the_sequential_test(test):
+    """With a warm start x_0 = u_0 = x_k (the solution at lambda_k), iteration 1's dual
+    point is theta_1 = D x_k - y and its correlations cover every atom, so the test of
+    iteration 1 at lambda_{k+1} screens exactly the atoms of the sequential test."""
+    g = gen.rng(46)
+    N, K = 50, 400
+    D = gen.gaussian_dict(N, K, g)
+    y = D @ gen.sparse_x0(K, 5, g) + 0.05 * g.standard_normal(N)
+    goff = w = None
+    if test in ("gsafe", "dgst3"):
+        goff = gen.contiguous_groups(K, 4)
+        w = np.full(goff.size - 1, 2.0)
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    xk = oracle.solve(D, y, 0.9 * lm, goff, w, test="none", tol=1e-13, max_iter=100000)["x"]
+    lam = 0.8 * lm
+    r = oracle.solve(D, y, lam, goff, w, alg="fista", test=test, tol=0, max_iter=1, x0=xk, margins=1)
+    s = oracle.sequential_screen(D, y, lam, D @ xk - y, goff, w, test=test)
+    np.testing.assert_array_equal(r["scr_iter"] == 1, s["screened"])
+    np.testing.assert_allclose(r["margins"][1], s["margins"], rtol=0, atol=1e-12)
+    assert 0 < s["screened"].sum() < K
+
+
+# ------------------------------------- Table 1 updates worked by hand (1 x 1)
+
+def _soft(v, t):
+    return np.sign(v) * max(abs(v) - t, 0.0)
+
+
+def test_fista_first_iterates_follow_the_printed_sequence():
+    """Table 1 FISTA on the 1 x 1 problem D = [d]: l_0 = 1 and
+    l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2 give l_1 = the golden ratio, l_2 and l_3
+    below; the iterates x_1 .. x_5 worked by hand from these values equal the
+    oracle's.  Another O(1/t^2) momentum sequence changes x_3 onwards."""
+    d, yv, lam, L = 1.3, 0.9, 0.05, 4.0
+    l = [1.0, (1 + np.sqrt(5.0)) / 2, 2.193527085331, 2.749791340120]
+    for t in range(1, 4):  # the printed recurrence, checked against the values above
+        assert abs(l[t] - (1 + np.sqrt(1 + 4 * l[t - 1] ** 2)) / 2) < 1e-11
+    l = [1.0]
+    for t in range(1, 6):
+        l.append((1 + np.sqrt(1 + 4 * l[-1] ** 2)) / 2)
+    x_prev, u, want = 0.0, 0.0, []
+    for t in range(1, 6):
+        x = _soft(u - d * (d * u - yv) / L, lam / L)
+        u = x + (l[t - 1] - 1) / l[t] * (x - x_prev)
+        x_prev = x
+        want.append(x)
+    D = np.array([[d]])
+    for t in range(1, 6):
+        got = oracle.solve(D, np.array([yv]), lam, alg="fista", test="none", tol=0, max_iter=t, L=L)["x"][0]
+        assert abs(got - want[t - 1]) <= 1e-14, (t, got, want[t - 1])
+
+
+@pytest.mark.parametrize("steps", [(0.3, 0.9, 0.5), (0.0, 0.0, 0.0), (0.0, 0.0, 2.0)])
+def test_chambolle_pock_first_iterates_follow_table_1(steps):
+    """Table 1 Chambolle-Pock on the 1 x 1 problem D = [d], worked by hand:
+    theta_t = (theta_{t-1} + sigma_{t-1} (d u_{t-1} - y)) / (1 + sigma_{t-1}),
+    x_t = prox_{lambda tau_{t-1}}(x_{t-1} - tau_{t-1} d theta_t),
+    phi_t = 1 / sqrt(1 + 2 gamma tau_{t-1}), tau_t = phi_t tau_{t-1},
+    sigma_t = sigma_{t-1} / phi_t, u_t = x_t + phi_t (x_t - x_{t-1}), with the readings
+    of the constants the paper leaves open: theta_0 = 0 and, when not given,
+    tau_0 = sigma_0 = 0.99 / sqrt(L)."""
+    tau0, sigma0, gamma = steps
+    d, yv, lam, L = 1.3, 0.9, 0.05, 1.69 * (1 + 1e-6)
+    tau = tau0 if tau0 > 0 else 0.99 / np.sqrt(L)
+    sigma = sigma0 if sigma0 > 0 else 0.99 / np.sqrt(L)
+    theta, x, u, want = 0.0, 0.0, 0.0, []
+    for t in range(1, 6):
+        theta = (theta + sigma * (d * u - yv)) / (1 + sigma)
+        xn = _soft(x - tau * d * theta, lam * tau)
+        phi = 1 / np.sqrt(1 + 2 * gamma * tau)
+        tau, sigma = phi * tau, sigma / phi
+        u = xn + phi * (xn - x)
+        x = xn
+        want.append((x, theta))
+    D = np.array([[d]])
+    for t in range(1, 6):
+        r = oracle.solve(D, np.array([yv]), lam, alg="cp", test="none", tol=0, max_iter=t, L=L,
+                         cp_tau=tau0, cp_sigma=sigma0, cp_gamma=gamma)
+        assert abs(r["x"][0] - want[t - 1][0]) <= 1e-14, (t, r["x"][0], want[t - 1])
+        assert abs(r["theta"][0] - want[t - 1][1]) <= 1e-14
