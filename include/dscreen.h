@@ -287,10 +287,14 @@ ds_status ds_server_destroy(ds_server* server);
  * Chambolle-Pock, any test;
  * DS_GSAFE / DS_DGST3 act as singleton groups), run on `device` and ordered on
  * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
- *   D      device, FP32, column-major N x K, leading dimension ld >= N with
- *          ld % 4 == 0 and D 16-byte aligned; rows N..ld-1, if any, must hold
- *          finite values (they are multiplied by zero).
- *   y      device, FP32, N entries.      x_out  device, FP32, K entries.
+ *   D      device memory of `device` (or managed memory), FP32, column-major
+ *          N x K, leading dimension ld with N <= ld <= N rounded up to a
+ *          multiple of 512 and ld % 4 == 0, D 16-byte aligned; rows N..ld-1, if
+ *          any, are not part of the atoms and must hold finite values (a row
+ *          slice of a taller column-major matrix qualifies).  A larger ld is
+ *          rejected with DS_ERR_UNSUPPORTED.
+ *   y      device, FP32, N entries.      x_out  device, FP32, K entries
+ *          (both on `device`, or managed).
  *   opt    host; opt->L > 0 is required (e.g. ds_dict_lipschitz of a
  *          registered copy of D, or any upper bound of ||D||_2^2).
  *   res    host.
@@ -301,9 +305,10 @@ ds_status ds_server_destroy(ds_server* server);
  * Every call shares the one scratch array per device and it keeps the last
  * call's contents; the call clears what must start at zero.  Calls whose GPU
  * work overlaps (concurrent streams, several host threads) race on the array:
- * serialise them.  Synchronous like ds_solve.  Errors: DS_ERR_INVALID (null or
- * host pointers, bad sizes or alignment, lambda <= 0, opt->L <= 0),
- * DS_ERR_UNSUPPORTED, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
+ * serialise them.  Synchronous like ds_solve.  The caller's current device is
+ * restored before the call returns.  Errors: DS_ERR_INVALID (null or host
+ * pointers, pointers to another GPU's memory, bad sizes or alignment,
+ * lambda <= 0, opt->L <= 0), DS_ERR_UNSUPPORTED, DS_ERR_CUDA, DS_ERR_TIMEOUT. */
 ds_status ds_solve_lasso_noalloc(int device, void* cuda_stream, const float* D, int64_t N, int64_t K, int64_t ld,
                                  const float* y, double lambda, const ds_options* opt, float* x_out, ds_result* res);
 
@@ -329,6 +334,17 @@ ds_status ds_ctx_kernel_launches(const ds_ctx* ctx, int64_t* n);
  * lambda of a path is recorded.  Errors: DS_ERR_INVALID (NULL ctx, or hist
  * with max_rows < 1). */
 ds_status ds_set_history(ds_ctx* ctx, double* hist, int max_rows);
+
+/* Record, for the following solves, which test iteration screened each atom
+ * (Algorithm 3's cumulative set I_t, atom by atom): scr_iter (device, capacity
+ * int32 values) receives, for each lambda j of a solve or path with
+ * (j + 1) * K <= capacity, K values at scr_iter + j * K: t >= 1 when the test
+ * of iteration t screened the atom (its group), -1 when the static test of
+ * Algorithm 1 did (dynamic = 0), 0 when the atom was never screened.  Passing
+ * NULL stops recording.  The buffer must stay valid while solves run; it is
+ * written by the solve kernels only (batches and servers do not record).
+ * Errors: DS_ERR_INVALID (NULL ctx, or scr_iter with capacity < 1). */
+ds_status ds_set_screen_log(ds_ctx* ctx, int32_t* scr_iter, int64_t capacity);
 
 #ifdef __cplusplus
 }

@@ -92,6 +92,7 @@ def lib():
             L.ds_solve_path.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ds_options), vp, vp,
                                         ctypes.POINTER(ds_result)]
             L.ds_set_history.argtypes = [vp, vp, ctypes.c_int]
+            L.ds_set_screen_log.argtypes = [vp, vp, i64]
             L.ds_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(dp)]
             L.ds_ctx_kernel_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
             L.ds_batch_create.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, ctypes.POINTER(ds_options), vp,
@@ -435,3 +436,16 @@ def ds_set_history(ctx, hist=None):
             raise ValueError(f"ds_set_history: hist must have shape (rows, {len(HIST_COLS)})")
         _check_buffer(hist, hist.shape[0] * len(HIST_COLS), 8, "hist", "ds_set_history")
         _check(lib().ds_set_history(ctx, _ptr(hist)[0], int(hist.shape[0])), "ds_set_history")
+
+
+def ds_set_screen_log(ctx, scr_iter=None):
+    """Record per-atom screening iterations of the following solves into scr_iter, an int32
+    device tensor of shape (rows, K) (row j = lambda j of a path), or stop recording (None)."""
+    if scr_iter is None:
+        _check(lib().ds_set_screen_log(ctx, None, 0), "ds_set_screen_log")
+        return
+    if str(scr_iter.dtype) not in ("torch.int32", "int32"):
+        raise TypeError("ds_set_screen_log: scr_iter must hold int32 values")
+    _check_buffer(scr_iter, 1, 4, "scr_iter", "ds_set_screen_log")
+    n = scr_iter.numel() if hasattr(scr_iter, "numel") else scr_iter.size
+    _check(lib().ds_set_screen_log(ctx, _ptr(scr_iter)[0], int(n)), "ds_set_screen_log")

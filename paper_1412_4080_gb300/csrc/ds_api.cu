@@ -194,6 +194,14 @@ ds_status ds_set_history(ds_ctx* ctx, double* hist, int max_rows)
     return DS_OK;
 }
 
+ds_status ds_set_screen_log(ds_ctx* ctx, int32_t* scr_iter, int64_t capacity)
+{
+    if (!ctx || (scr_iter && capacity < 1)) return DS_ERR_INVALID;
+    ctx->scr_log = scr_iter;
+    ctx->scr_cap = scr_iter ? capacity : 0;
+    return DS_OK;
+}
+
 ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64_t ld, ds_prec dtype,
                          const int64_t* group_offsets, const double* weights, int64_t n_groups, ds_prec work_prec,
                          ds_dict** out)

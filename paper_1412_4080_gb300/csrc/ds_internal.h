@@ -25,6 +25,8 @@ struct ds_ctx {
     size_t io_bytes;
     double* hist;
     int hist_rows;
+    int* scr_log;       // per-atom screening log of the following solves (device), scr_cap ints
+    int64_t scr_cap;
     long long launches;
     double* fista;  // device table of the FISTA sequence (coefficient, l_t), t = 1..fista_n
     int fista_n;
@@ -103,6 +105,8 @@ struct SolveEnv {
     int fista_n;
     double* hist;
     int hist_rows;
+    int* scr_log;
+    int64_t scr_cap;
 };
 
 size_t solve_ws_bytes(const DictDesc& dd, int num_sms, size_t smem_optin, int n_lambda);

@@ -21,6 +21,7 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 4096;
 constexpr int64_t kNoAllocMaxK = 16384;
 constexpr size_t kNoAllocScratchBytes = 3u << 20;  // >= the solve workspace at the limits above
+constexpr int64_t kNoAllocChunk = 512;              // rows of one FP32 correlation chunk (32 lanes x 4 x 4)
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -60,15 +61,27 @@ ds_status setup_device(int device, NoAllocDevice** out)
     return DS_OK;
 }
 
-bool on_device(const void* p)
+// A device (or managed) allocation that the kernel can read on `device`: memory of
+// another GPU would be dereferenced without peer access.
+bool on_device(const void* p, int device)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
+
+// Restores the caller's current device when the entry point returns.
+struct DeviceRestore {
+    int prev = -1;
+    ~DeviceRestore()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
 
 }  // namespace
 
@@ -87,14 +100,27 @@ extern "C" ds_status ds_solve_lasso_noalloc(int device, void* cuda_stream, const
     }
     // 16-byte vector loads: columns must start on 16-byte boundaries
     if (ld % 4 != 0 || (reinterpret_cast<uintptr_t>(D) & 15) != 0) return DS_ERR_INVALID;
+    // The kernel stages y (and d_* in the DST3/Dome precompute) in shared vectors of
+    // N rounded up to its 512-row correlation chunk, and walks each column of D up to
+    // ld: a leading dimension beyond that rounding would read past those vectors.
+    if (ld >= (int64_t(1) << 31) || ld > (N + kNoAllocChunk - 1) / kNoAllocChunk * kNoAllocChunk) {
+        fprintf(stderr, "ds_solve_lasso_noalloc: ld=%lld exceeds N=%lld rounded up to a multiple of %lld\n",
+                (long long)ld, (long long)N, (long long)kNoAllocChunk);
+        return DS_ERR_UNSUPPORTED;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
         cudaGetLastError();
         return DS_ERR_CUDA;
     }
     if (device < 0 || device >= ndev || device >= kMaxDevices) return DS_ERR_INVALID;
+    DeviceRestore restore;
+    if (cudaGetDevice(&restore.prev) != cudaSuccess) {
+        cudaGetLastError();
+        return DS_ERR_CUDA;
+    }
     if (cudaSetDevice(device) != cudaSuccess) return DS_ERR_CUDA;
-    if (!on_device(D) || !on_device(y) || !on_device(x_out)) return DS_ERR_INVALID;
+    if (!on_device(D, device) || !on_device(y, device) || !on_device(x_out, device)) return DS_ERR_INVALID;
     NoAllocDevice* dev = nullptr;
     ds_status st = setup_device(device, &dev);
     if (st != DS_OK) return st;

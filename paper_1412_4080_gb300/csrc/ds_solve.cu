@@ -97,6 +97,8 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
     P.res = res_dev;
     P.hist = env.hist;
     P.hist_rows = env.hist_rows;
+    P.scr_log = env.scr_log;
+    P.scr_rows = env.scr_log ? (int)std::min<int64_t>(env.scr_cap / std::max(dd.K, 1), 1 << 30) : 0;
     P.ws = w;
 
     cudaStream_t s = env.stream;
@@ -199,6 +201,8 @@ ds_status launch_solve(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, cons
     env.fista_n = ctx->fista_n;
     env.hist = ctx->hist;
     env.hist_rows = ctx->hist_rows;
+    env.scr_log = ctx->scr_log;
+    env.scr_cap = ctx->scr_cap;
     return launch_solve_env(env, dict_desc(dict), y_dev, x0_dev, n_lambda, lambdas_host, opt, xout_dev, ldx, res_host,
                             ms);
 }

@@ -89,6 +89,8 @@ struct SolveP {
     DevResult* res;
     double* hist;
     int hist_rows;
+    int* scr_log;  // non-null: per lambda j < scr_rows, K ints: the iteration whose test screened each atom
+    int scr_rows;
     Ws<T> ws;
     int RA, nchunk, npad;
     int syn_cap;          // nonzero-list entries the dynamic shared buffer holds (multiple of 16)
@@ -479,6 +481,7 @@ struct SolveK {
     float sqb_f, s_unc_f;  // ||theta|| (rounded up) and the unclipped Lemma 8 scaling, FP32
     float bt_h, bt_l;      // FISTA coefficient of the iteration as a float-float pair
     float dome_f[4];  // FP32 dome test of the current iteration: R, psi, rho (rounded up), branch threshold
+    int* slog;  // screening log of the current lambda (null: not recorded)
     T invL;
     T cp_sig, cp_inv1ps;  // Chambolle-Pock: sigma_{t-1} and 1 / (1 + sigma_{t-1}) of the next dual update
     typename IterT<T>::type thrX;
@@ -546,7 +549,17 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 V q = yv[v];
                 if constexpr (EV == 4) {
                     acc.add(d.x, q.x); acc.add(d.y, q.y); acc.add(d.z, q.z); acc.add(d.w, q.w);
-                    if (norms) { nrm.add(d.x, d.x); nrm.add(d.y, d.y); nrm.add(d.z, d.z); nrm.add(d.w, d.w); }
+                    if (norms) {
+                        // rows N..ld-1 of a caller's D are not part of the atom
+                        const int r0 = v * 4;
+                        if (r0 + 3 >= N) {
+                            d.x = r0 < N ? d.x : 0.f;
+                            d.y = r0 + 1 < N ? d.y : 0.f;
+                            d.z = r0 + 2 < N ? d.z : 0.f;
+                            d.w = 0.f;
+                        }
+                        nrm.add(d.x, d.x); nrm.add(d.y, d.y); nrm.add(d.z, d.z); nrm.add(d.w, d.w);
+                    }
                 } else {
                     acc.add(d.x, q.x); acc.add(d.y, q.y);
                     if (norms) { nrm.add(d.x, d.x); nrm.add(d.y, d.y); }
@@ -801,6 +814,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             C_.hlam2 = 0.5 * lm * lm;
             C_.tol_abs = P.tol * 0.5 * yy;
             C_.delta2 = C_.delta * C_.delta;
+            C_.slog = (P.scr_log && j < P.scr_rows) ? P.scr_log + (size_t)j * K : nullptr;
         }
         __syncthreads();
         const double &lam = C_.lam, &psi = C_.psi, &coef = C_.coef, &delta = C_.delta, &nstar = C_.nstar;
@@ -813,7 +827,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         if (!(lam < lstar)) {
             // x = 0 and theta = y / lambda is dual optimal (Sec. 2.2.2); each CTA writes its own slice
             // (a warm-started next lambda reads it back in the same CTA)
-            for (int i = a_lo0 + tid; i < a_hi0; i += kThreads) xout[i] = T(0);
+            for (int i = a_lo0 + tid; i < a_hi0; i += kThreads) {
+                xout[i] = T(0);
+                if (C_.slog) C_.slog[i] = 0;
+            }
             if (b == 0 && tid == 0) {
                 R->iters = 0; R->status = kDevOk; R->n_active = 0; R->nnz = 0;
                 R->gap = 0.0; R->primal = 0.5 * yy; R->dual = 0.5 * yy; R->lambda = lam; R->lambda_max = lstar;
@@ -893,6 +910,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                     kept = !kill;
+                    // screening log: -1 for the static test (Algorithm 1), 0 until screened
+                    if (C_.slog)
+                        for (int i = lo_a; i < hi_a; i++) C_.slog[i] = kill ? -1 : 0;
                     if (kept && x0)
                         for (int i = lo_a; i < hi_a; i++) cnt += x0[i] != T(0);
                 }
@@ -1213,6 +1233,12 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                                            : __ldcg(W.act[cur] + g_lo + k));
                         const bool kill = test_now && killed(td);
                         W.keep[g_lo + k] = !kill;
+                        if (kill && C_.slog) {
+                            // screening log: the test of iteration t-1 screened this group's atoms
+                            const int gs = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
+                            const int i0 = P.is_group ? P.goff[gs] : gs, i1 = P.is_group ? P.goff[gs + 1] : gs + 1;
+                            for (int i = i0; i < i1; i++) C_.slog[i] = t - 1;
+                        }
                         if (!kill) {
                             if (!P.is_group) {
                                 const X xv = first ? s_pf_x[tid] : ldcg_x(xbuf(iO) + a_lo0 + k);
@@ -1786,6 +1812,8 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.syn_cap = (int)(g.smem / (sizeof(int) + 2 * sizeof(typename IterT<T>::type))) & ~15;
     P.hist = nullptr;
     P.hist_rows = 0;
+    P.scr_log = nullptr;
+    P.scr_rows = 0;
     P.x0 = nullptr;
     P.colnorm_w = nullptr;
     P.fista = nullptr;

@@ -105,6 +105,15 @@ def test_noalloc_reports_sizes_beyond_its_fixed_scratch():
     assert _noalloc(K=16385) == ds.DS_ERR_UNSUPPORTED
 
 
+def test_noalloc_bounds_the_leading_dimension_by_the_correlation_chunk():
+    # the kernel's shared staging vectors hold N rounded up to 512 rows: a taller
+    # column stride is rejected before any CUDA call, a stride within it passes
+    # the size checks (and fails later only because these buffers are host memory)
+    assert _noalloc(N=700, ld=1028) == ds.DS_ERR_UNSUPPORTED
+    assert _noalloc(N=8, ld=516) == ds.DS_ERR_UNSUPPORTED
+    assert _noalloc(N=700, ld=1024) != ds.DS_ERR_UNSUPPORTED
+
+
 _C_USER = r"""
 #include <stdio.h>
 #include <string.h>

@@ -66,3 +66,46 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     st = ds.lib().ds_solve_lasso_noalloc(0, None, fake, 100, 20000, 100, fake, 1.0, ctypes.byref(o), fake,
                                          ctypes.byref(r))
     assert st == ds.DS_ERR_UNSUPPORTED
+
+
+def _compare_with_ds_solve(D, Dt_noalloc, y, ratio, test):
+    """ds_solve on a registered copy of D against the allocation-free call on
+    Dt_noalloc (the same atoms, possibly inside a taller column-major buffer)."""
+    K = D.shape[1]
+    ctx = ds.ds_create(0, None)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D))
+    try:
+        L = ds.ds_dict_lipschitz(dct)
+        yt = torch.from_numpy(y).to("cuda", torch.float32)
+        o = ds.ds_options_default(test=test, tol_gap_rel=1e-6, max_iter=20000, L=L, lambda_rel=1)
+        x_ref = torch.empty(K, device="cuda")
+        ref = ds.ds_solve(ctx, dct, yt, ratio, o, x_ref)
+        x_na = torch.full((K,), float("nan"), device="cuda")
+        got = ds.ds_solve_lasso_noalloc(0, None, Dt_noalloc, yt, ratio, o, x_na)
+        torch.cuda.synchronize()
+    finally:
+        ds.ds_dict_destroy(dct)
+        ds.ds_destroy(ctx)
+    a = x_ref.double().cpu().numpy()
+    b = x_na.double().cpu().numpy()
+    assert got["status"] == 0 and ref["status"] == 0
+    assert got["iters"] == ref["iters"]
+    assert np.abs(b - a).max() <= 1e-5 * np.abs(a).max()
+    assert abs(got["gap"] - ref["gap"]) <= 1e-9 * 0.5 * float(y @ y)
+
+
+def test_noalloc_at_its_documented_size_limits():
+    # N = 4096, K = 16384: the fixed scratch must hold the whole workspace on this GPU
+    D, y, _ = gen.lasso_problem(4096, 16384, seed=93, p=0.01)
+    _compare_with_ds_solve(D, _dev_dict(D), y, 0.5, "dst3")
+    assert torch.cuda.current_device() == 0
+
+
+def test_noalloc_row_slice_of_a_taller_matrix_with_nonzero_padding():
+    # D is rows 0..N-1 of an ld x K column-major buffer whose rows N..ld-1 hold
+    # nonzero finite values: they are not part of the atoms
+    N, K, ld = 700, 2000, 1024
+    D, y, _ = gen.lasso_problem(N, K, seed=94, p=0.02)
+    tall = np.ascontiguousarray(np.vstack([D, gen.rng(95).standard_normal((ld - N, K))]).T)
+    Tt = torch.from_numpy(tall).to("cuda", torch.float32).t()  # (ld, K), strides (1, ld)
+    _compare_with_ds_solve(D, Tt[:N], y, 0.7, "safe")
