@@ -26,7 +26,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALGS = {"ista": 0, "fista": 1, "cp": 2}
+ALGS = {"ista": 0, "fista": 1, "cp": 2, "sparsa": 3, "twist": 4}
 TESTS = {"none": 0, "safe": 1, "dst3": 2, "dome": 3, "gsafe": 4, "dgst3": 5}
 HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
 
@@ -34,7 +34,9 @@ HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
 class _Options(ctypes.Structure):
     _fields_ = [("alg", ctypes.c_int), ("test", ctypes.c_int), ("dynamic", ctypes.c_int),
                 ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
-                ("cp_tau", ctypes.c_double), ("cp_sigma", ctypes.c_double), ("cp_gamma", ctypes.c_double)]
+                ("cp_tau", ctypes.c_double), ("cp_sigma", ctypes.c_double), ("cp_gamma", ctypes.c_double),
+                ("step_backtracking", ctypes.c_int), ("bt_L0", ctypes.c_double), ("twist_xi1", ctypes.c_double),
+                ("gap_every", ctypes.c_int)]
 
 
 class _Result(ctypes.Structure):
@@ -147,8 +149,10 @@ def dome_max(dc0, t, psi, R):
 
 
 def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynamic=True,
-          tol=1e-6, max_iter=1000, L=None, x0=None, cp_tau=0.0, cp_sigma=0.0, cp_gamma=0.0, margins=0):
-    """Solve eq. (1) with Algorithm 3 and the ISTA, FISTA or Chambolle-Pock ("cp") update of Table 1.
+          tol=1e-6, max_iter=1000, L=None, x0=None, cp_tau=0.0, cp_sigma=0.0, cp_gamma=0.0, margins=0,
+          backtracking=False, bt_L0=0.0, twist_xi1=0.0, gap_every=1):
+    """Solve eq. (1) with Algorithm 3 and the ISTA, FISTA, Chambolle-Pock ("cp"), SpaRSA or TwIST
+    update of Table 1 (ISTA / FISTA with backtracking of L when backtracking=True).
     Returns a dict with x, scr_iter, hist, theta (theta_t of the last iteration) and scalars; with
     margins=T > 0 also "margins": (min(iters, T) + 1) x G test margins, row 0 the static test, row t
     the test of iteration t (NaN where a group was not tested)."""
@@ -157,7 +161,8 @@ def solve(D, y, lam, groups=None, weights=None, alg="fista", test="dst3", dynami
     y = np.ascontiguousarray(y, dtype=np.float64)
     goff, w, nG = _groups(groups, weights)
     opt = _Options(ALGS[alg], TESTS[test], 1 if dynamic else 0, int(max_iter), float(tol),
-                   float(L) if L is not None else 0.0, float(cp_tau), float(cp_sigma), float(cp_gamma))
+                   float(L) if L is not None else 0.0, float(cp_tau), float(cp_sigma), float(cp_gamma),
+                   1 if backtracking else 0, float(bt_L0), float(twist_xi1), int(gap_every))
     x = np.zeros(K)
     scr = np.zeros(K, dtype=np.int32)
     hist = np.zeros((max(int(max_iter), 1), len(HIST_COLS)))

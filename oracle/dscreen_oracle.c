@@ -17,7 +17,8 @@
  *   Group-Lasso     eq. (group-lasso), Omega = sum_g w_g ||x_g||_2,
  *                   prox = group soft threshold (eq. gr_softTh)
  *   lambda_*        Sec. 2.2.2 (Lasso: ||D^T y||_inf), eq. (gstar) (groups)
- *   updates         Table 1 (ISTA, FISTA and Chambolle-Pock rows)
+ *   updates         Table 1 (ISTA, FISTA, Chambolle-Pock, SpaRSA and TwIST rows;
+ *                   backtracking of L for ISTA / FISTA)
  *   general loop    Algorithm 3 (screen after each update, cumulative set)
  *   dual scaling    Lemma 8 (feasible scaled dual point closest to y/lambda)
  *   tests           Lemma 2 (SAFE), Lemma 3 (DST3), Lemma 4 (dynamic Dome),
@@ -75,6 +76,22 @@
 #define OR_ISTA 0
 #define OR_FISTA 1
 #define OR_CP 2 /* Chambolle-Pock (Table 1) */
+#define OR_SPARSA 3 /* SpaRSA (Table 1): ISTA with a Barzilai-Borwein step */
+#define OR_TWIST 4  /* TwIST (Table 1): two-step iterative shrinkage */
+
+/* Constants of the adaptive steps, which the paper leaves to the cited papers (readings):
+ * backtracking (Beck-Teboulle) multiplies L by OR_ETA until the quadratic upper model holds;
+ * SpaRSA (Wright-Nowak-Figueiredo) accepts a step when F(x_t) <= max of the last OR_SPARSA_M
+ * accepted F - OR_SPARSA_SIGMA / 2 alpha ||x_t - x_{t-1}||^2, else multiplies alpha by OR_ETA,
+ * and clips its BB step to [OR_BB_MIN, OR_BB_MAX] times L; TwIST (Bioucas-Dias-Figueiredo)
+ * replaces a step that increases F by the plain shrinkage step (its monotone variant).  After
+ * OR_RETRY_CAP rejections in one iteration the last attempt is kept. */
+#define OR_ETA 2.0
+#define OR_SPARSA_SIGMA 1e-5
+#define OR_SPARSA_M 5
+#define OR_BB_MIN 1e-10
+#define OR_BB_MAX 1e10
+#define OR_RETRY_CAP 40
 
 #define OR_TEST_NONE 0
 #define OR_TEST_SAFE 1
@@ -104,6 +121,10 @@ typedef struct {
     double cp_tau;      /* Chambolle-Pock tau_0 and sigma_0 (<= 0: 0.99 / sqrt(L) each, so that */
     double cp_sigma;    /*   tau_0 sigma_0 ||D||^2 < 1) and gamma >= 0 (0: phi_t = 1 throughout) */
     double cp_gamma;
+    int step_backtracking; /* ISTA / FISTA: 1 sets L_t by backtracking (Beck-Teboulle) from bt_L0 */
+    double bt_L0;          /* first L of the backtracking (<= 0: 1) */
+    double twist_xi1;      /* TwIST: lower eigenvalue bound xi_1 of D^T D / L (<= 0: 1e-4) */
+    int gap_every;         /* the stopping rule is evaluated every gap_every iterations (<= 1: each) */
 } or_options;
 
 typedef struct {
@@ -459,7 +480,237 @@ static double omega(const or_ctx* c, const double* x)
     return s;
 }
 
-/* Solve eq. (1) by Algorithm 3 with the ISTA, FISTA or Chambolle-Pock update of Table 1.
+/* Table 1 FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2; returns the extrapolation
+ * coefficient (l_{t-1} - 1) / l_t and advances *lp from l_{t-1} to l_t. */
+static double fista_step(double* lp)
+{
+    double l = *lp;
+    double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));
+    double beta = (l - 1.0) / ln;
+    *lp = ln;
+    return beta;
+}
+
+/* Dual objective of the gap at the dual point mu theta with R = ||y/lambda - mu theta||:
+ * Dual(v) = 1/2 ||y||^2 - lambda^2 / 2 ||v - y/lambda||^2. */
+static double dual_objective(double yy, double lambda, double R)
+{
+    return 0.5 * yy - 0.5 * lambda * lambda * R * R;
+}
+
+/* One history row (Sec. 4.1 flops accounting): atoms still active and ||x||_0, with R, the
+ * test radius, the gap and mu; also sets res->n_active and res->nnz. */
+static void record_iteration(const int64_t* goff, int64_t G, int64_t K, const char* act, const double* x,
+                             double R, double rad, double gap, double mu, double* h, or_result* res)
+{
+    int nact = 0, nnz = 0;
+    for (int64_t g = 0; g < G; g++)
+        if (act[g]) nact += (int)(g_hi(goff, g) - g_lo(goff, g));
+    for (int64_t i = 0; i < K; i++) nnz += x[i] != 0.0;
+    if (h) {
+        h[OR_H_ACTIVE] = nact;
+        h[OR_H_NNZ] = nnz;
+        h[OR_H_R] = R;
+        h[OR_H_RADIUS] = rad;
+        h[OR_H_GAP] = gap;
+        h[OR_H_MU] = mu;
+    }
+    res->n_active = nact;
+    res->nnz = nnz;
+}
+
+/* Algorithm 3 with the Table 1 rows whose step adapts from one iteration to the next:
+ *  - ISTA / FISTA with backtracking (Beck-Teboulle): L_t is the smallest OR_ETA^i L_{t-1}
+ *    for which f(xbar_t) <= f(u) + <xbar_t - u, z_t> + L_t/2 ||xbar_t - u||^2, u = ubar_{t-1}
+ *    (for the quadratic f: ||D (xbar_t - u)||^2 <= L_t ||xbar_t - u||^2);
+ *  - SpaRSA: x_t = prox_{lambda/alpha_t}(xbar_{t-1} - z_t / alpha_t), alpha_1 = L, then the
+ *    Barzilai-Borwein value ||D s||^2 / ||s||^2 of the last accepted step s, multiplied by OR_ETA
+ *    until F(xbar_t) <= max of the last OR_SPARSA_M accepted F - sigma/2 alpha_t ||s_t||^2;
+ *  - TwIST: x_t = (1 - a) x_{t-2} + (a - b) x_{t-1} + b prox_{lambda/L}(x_{t-1} - z_t / L) with
+ *    rho = (1 - sqrt(xi_1)) / (1 + sqrt(xi_1)), a = rho^2 + 1, b = 2 a / (1 + xi_1) (the bounds
+ *    xi_1 <= eig(D^T D / L) <= 1), and the plain shrinkage step prox_{lambda/L}(x_{t-1} - z_t/L)
+ *    for t = 1 and in place of any step that increases F (TwIST's monotone variant).
+ * theta_t = D u - y with u = ubar_{t-1} (ISTA, FISTA) or xbar_{t-1} (SpaRSA, TwIST).  The test
+ * of iteration t depends on theta_t only, so it is taken first and every acceptance test is
+ * evaluated at xbar_t, x_t with the atoms screened at t set to zero.  Returns the number of
+ * iterations run; *gap_out, *primal_out, *dual_out as in or_solve_log. */
+static int adaptive_loop(or_ctx* c, const or_options* opt, double L, double yy, char* act, int* scr,
+                         double* x, double* u, double* theta, double* hist, double* margin_log, int margin_rows,
+                         double* gap_out, double* primal_out, double* dual_out, or_result* res)
+{
+    const double *D = c->D, *y = c->y;
+    const int64_t N = c->N, K = c->K, ld = c->ld;
+    const int64_t* goff = c->goff;
+    const double* w = c->w;
+    const int64_t G = n_groups(goff, c->nG, K);
+    const double lambda = c->lambda;
+    const int sparsa = opt->alg == OR_SPARSA, twist = opt->alg == OR_TWIST, fista = opt->alg == OR_FISTA;
+    const int bt = !sparsa && !twist;
+    const int ge = opt->gap_every > 1 ? opt->gap_every : 1;
+    double* z = (double*)calloc(K, sizeof(double));
+    double* v = (double*)calloc(K, sizeof(double));
+    double* xn = (double*)calloc(K, sizeof(double));
+    double* xb = (double*)calloc(K, sizeof(double));
+    double* x2 = (double*)calloc(K, sizeof(double)); /* TwIST: x_{t-2} */
+    double* r = (double*)calloc(N, sizeof(double));
+    char* kill = (char*)calloc((size_t)G, 1);
+    const double xi1 = opt->twist_xi1 > 0 ? opt->twist_xi1 : 1e-4;
+    const double rho = (1.0 - sqrt(xi1)) / (1.0 + sqrt(xi1));
+    const double ta = rho * rho + 1.0, tb = 2.0 * ta / (1.0 + xi1);
+    double Lbt = opt->bt_L0 > 0 ? opt->bt_L0 : 1.0;
+    double alpha = L;
+    /* F at the starting point, the first entry of SpaRSA's history and TwIST's reference */
+    for (int64_t n = 0; n < N; n++) r[n] = -y[n];
+    for (int64_t i = 0; i < K; i++)
+        if (x[i] != 0.0)
+            for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * x[i];
+    double Fh[OR_SPARSA_M];
+    Fh[0] = 0.5 * vec_dot(r, r, N) + lambda * omega(c, x);
+    int nh = 1, hpos = 1;
+    double Fprev = Fh[0];
+    double l = 1.0; /* FISTA l_0 */
+    double gap = INFINITY, primal = 0.0, dual = 0.0;
+    int it;
+    res->status = 1;
+    for (it = 1; it <= opt->max_iter; it++) {
+        /* theta_t = D u - y */
+        for (int64_t n = 0; n < N; n++) r[n] = -y[n];
+        for (int64_t g = 0; g < G; g++) {
+            if (!act[g]) continue;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++)
+                if (u[i] != 0.0)
+                    for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * u[i];
+        }
+        for (int64_t n = 0; n < N; n++) theta[n] = r[n];
+        /* z_t = D_{t-1}^T theta_t and m (Lemma 8) */
+        double m = 0.0;
+        for (int64_t g = 0; g < G; g++) {
+            if (!act[g]) continue;
+            double q = 0.0;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
+                z[i] = col_dot(D, ld, i, theta, N);
+                q += z[i] * z[i];
+            }
+            double val = sqrt(q) / g_w(w, g);
+            if (val > m) m = val;
+        }
+        /* the test of iteration t (Algorithm 3) */
+        double R, rad, mu;
+        if (opt->dynamic && opt->test != OR_TEST_NONE) {
+            mu = screen(c, theta, m, act, scr, it, &R, &rad,
+                        margin_log && it < margin_rows ? margin_log + (size_t)it * G : NULL);
+        } else {
+            int save = c->test;
+            c->test = OR_TEST_NONE;
+            mu = screen(c, theta, m, act, scr, it, &R, &rad, NULL);
+            c->test = save;
+        }
+        for (int64_t g = 0; g < G; g++) kill[g] = act[g] && scr[g] != 0;
+        /* the step, repeated with a larger alpha (L) while its acceptance test fails */
+        double Lt = bt ? Lbt : (sparsa ? alpha : L);
+        int fallback = 0;
+        double F = 0.0, fx = 0.0, dx2 = 0.0;
+        for (int tries = 0;; tries++) {
+            for (int64_t i = 0; i < K; i++) xb[i] = 0.0;
+            for (int64_t g = 0; g < G; g++) {
+                if (!act[g]) continue;
+                for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) v[i] = (bt ? u[i] : x[i]) - z[i] / Lt;
+                prox_group(c, g, v, lambda / Lt, xn);
+                for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
+                    if (twist && it >= 2 && !fallback) xn[i] = (1.0 - ta) * x2[i] + (ta - tb) * x[i] + tb * xn[i];
+                    if (!kill[g]) xb[i] = xn[i];
+                }
+            }
+            for (int64_t n = 0; n < N; n++) r[n] = -y[n];
+            for (int64_t i = 0; i < K; i++)
+                if (xb[i] != 0.0)
+                    for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * xb[i];
+            fx = 0.5 * vec_dot(r, r, N);
+            F = fx + lambda * omega(c, xb);
+            dx2 = 0.0;
+            for (int64_t i = 0; i < K; i++) dx2 += (xb[i] - x[i]) * (xb[i] - x[i]);
+            int ok;
+            if (bt) {
+                /* the quadratic upper model of f at u: for f = 1/2 ||D x - y||^2,
+                 * f(p) = f(u) + <p - u, z> + 1/2 ||D (p - u)||^2 exactly, so the model
+                 * f(p) <= f(u) + <p - u, z> + L/2 ||p - u||^2 holds iff ||D (p - u)||^2 <= L ||p - u||^2
+                 * (this form has no cancellation near convergence) */
+                double sq = 0.0, dq = 0.0;
+                for (int64_t i = 0; i < K; i++) sq += (xb[i] - u[i]) * (xb[i] - u[i]);
+                for (int64_t n = 0; n < N; n++) {
+                    double d = 0.0;
+                    for (int64_t i = 0; i < K; i++)
+                        if (xb[i] != u[i]) d += D[i * ld + n] * (xb[i] - u[i]);
+                    dq += d * d;
+                }
+                ok = dq <= Lt * sq;
+            } else if (sparsa) {
+                double Fmax = Fh[0];
+                for (int k = 1; k < nh; k++)
+                    if (Fh[k] > Fmax) Fmax = Fh[k];
+                ok = F <= Fmax - 0.5 * OR_SPARSA_SIGMA * Lt * dx2;
+            } else {
+                ok = it == 1 || fallback || F <= Fprev;
+            }
+            if (ok || tries == OR_RETRY_CAP) break;
+            if (twist) fallback = 1;
+            else Lt *= OR_ETA;
+        }
+        /* SpaRSA: the Barzilai-Borwein value of the accepted step s = xbar_t - xbar_{t-1} */
+        if (sparsa) {
+            double ds2 = 0.0;
+            for (int64_t n = 0; n < N; n++) {
+                double d = 0.0;
+                for (int64_t i = 0; i < K; i++)
+                    if (xb[i] != x[i]) d += D[i * ld + n] * (xb[i] - x[i]);
+                ds2 += d * d;
+            }
+            alpha = Lt;
+            if (dx2 > 0.0) {
+                alpha = ds2 / dx2;
+                if (alpha < OR_BB_MIN * L) alpha = OR_BB_MIN * L;
+                if (alpha > OR_BB_MAX * L) alpha = OR_BB_MAX * L;
+            }
+        }
+        if (bt) Lbt = Lt;
+        /* FISTA: l_t and u_t = x_t + ((l_{t-1} - 1) / l_t)(x_t - xbar_{t-1}); the others: u_t = x_t */
+        const double beta = fista ? fista_step(&l) : 0.0;
+        for (int64_t g = 0; g < G; g++) {
+            if (!act[g]) continue;
+            for (int64_t i = g_lo(goff, g); i < g_hi(goff, g); i++) {
+                if (kill[g]) {
+                    x[i] = u[i] = x2[i] = 0.0;
+                } else {
+                    x2[i] = x[i];
+                    u[i] = xn[i] + beta * (xn[i] - x[i]);
+                    x[i] = xn[i];
+                }
+            }
+            if (kill[g]) act[g] = 0;
+        }
+        Fh[hpos] = F;
+        hpos = (hpos + 1) % OR_SPARSA_M;
+        if (nh < OR_SPARSA_M) nh++;
+        Fprev = F;
+        /* duality gap P(xbar_t) - Dual(mu_t theta_t) */
+        primal = F;
+        dual = dual_objective(yy, lambda, R);
+        gap = primal - dual;
+        record_iteration(goff, G, K, act, x, R, rad, gap, mu, hist ? &hist[(size_t)(it - 1) * OR_NH] : NULL, res);
+        if (opt->tol_gap_rel > 0 && it % ge == 0 && gap <= opt->tol_gap_rel * 0.5 * yy) {
+            res->status = 0;
+            break;
+        }
+    }
+    *gap_out = gap;
+    *primal_out = primal;
+    *dual_out = dual;
+    free(z); free(v); free(xn); free(xb); free(x2); free(r); free(kill);
+    return it;
+}
+
+/* Solve eq. (1) by Algorithm 3 with the ISTA, FISTA, Chambolle-Pock, SpaRSA or TwIST update
+ * of Table 1 (ISTA / FISTA optionally with backtracking; see adaptive_loop).
  * x_out: K coefficients.  scr_iter (nullable): per atom, the iteration at which it
  * was screened (0 = never, -1 = by the static test before the loop).
  * hist (nullable): max_iter rows of OR_NH doubles.
@@ -476,6 +727,7 @@ int or_solve_log(const double* D, int64_t N, int64_t K, int64_t ld, const double
                  int margin_rows, or_result* res)
 {
     if (!D || !y || !x_out || !opt || !res || N <= 0 || K <= 0 || ld < N || !(lambda > 0)) return -1;
+    if (opt->alg < OR_ISTA || opt->alg > OR_TWIST) return -1;
     if (!goff) w = NULL; /* the Lasso: singleton groups of weight 1 */
     if (goff) {
         if (nG <= 0 || goff[0] != 0 || goff[nG] != K) return -1;
@@ -558,6 +810,14 @@ int or_solve_log(const double* D, int64_t N, int64_t K, int64_t ld, const double
             }
     }
 
+    int it;
+    double gap = INFINITY, primal = 0.0, dual = 0.0;
+    if (opt->alg == OR_SPARSA || opt->alg == OR_TWIST ||
+        (opt->step_backtracking && (opt->alg == OR_ISTA || opt->alg == OR_FISTA))) {
+        it = adaptive_loop(&c, opt, L, yy, act, scr, x, u, theta, hist, margin_log, margin_rows, &gap, &primal,
+                           &dual, res);
+        goto finish;
+    }
     double l = 1.0; /* FISTA l_0 */
     const int cp = opt->alg == OR_CP;
     /* Chambolle-Pock: theta_0 = 0 (dual start), tau_0, sigma_0, gamma (Table 1) */
@@ -566,8 +826,6 @@ int or_solve_log(const double* D, int64_t N, int64_t K, int64_t ld, const double
     const double gamma = opt->cp_gamma > 0 ? opt->cp_gamma : 0.0;
     if (cp)
         for (int64_t n = 0; n < N; n++) theta[n] = 0.0;
-    int it;
-    double gap = INFINITY, primal = 0.0, dual = 0.0;
     res->status = 1;
     for (it = 1; it <= opt->max_iter; it++) {
         /* Table 1: theta_t = D_{t-1} ubar_{t-1} - y (ISTA, FISTA);
@@ -600,9 +858,7 @@ int or_solve_log(const double* D, int64_t N, int64_t K, int64_t ld, const double
          * sigma_t = sigma_{t-1} / phi_t, u_t = x_t + phi_t (x_t - xbar_{t-1}) */
         double beta = 0.0;
         if (opt->alg == OR_FISTA) {
-            double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));
-            beta = (l - 1.0) / ln;
-            l = ln;
+            beta = fista_step(&l);
         } else if (cp) {
             const double phi = 1.0 / sqrt(1.0 + 2.0 * gamma * tau);
             tau *= phi;
@@ -642,28 +898,16 @@ int or_solve_log(const double* D, int64_t N, int64_t K, int64_t ld, const double
             if (x[i] != 0.0)
                 for (int64_t n = 0; n < N; n++) r[n] += D[i * ld + n] * x[i];
         primal = 0.5 * vec_dot(r, r, N) + lambda * omega(&c, x);
-        dual = 0.5 * yy - 0.5 * lambda * lambda * R * R;
+        dual = dual_objective(yy, lambda, R);
         gap = primal - dual;
-        int nact = 0, nnz = 0;
-        for (int64_t g = 0; g < G; g++)
-            if (act[g]) nact += (int)(g_hi(goff, g) - g_lo(goff, g));
-        for (int64_t i = 0; i < K; i++) nnz += x[i] != 0.0;
-        if (hist) {
-            double* h = hist + (size_t)(it - 1) * OR_NH;
-            h[OR_H_ACTIVE] = nact;
-            h[OR_H_NNZ] = nnz;
-            h[OR_H_R] = R;
-            h[OR_H_RADIUS] = rad;
-            h[OR_H_GAP] = gap;
-            h[OR_H_MU] = mu;
-        }
-        res->n_active = nact;
-        res->nnz = nnz;
-        if (opt->tol_gap_rel > 0 && gap <= opt->tol_gap_rel * 0.5 * yy) {
+        record_iteration(goff, G, K, act, x, R, rad, gap, mu, hist ? hist + (size_t)(it - 1) * OR_NH : NULL, res);
+        if (opt->tol_gap_rel > 0 && it % (opt->gap_every > 1 ? opt->gap_every : 1) == 0 &&
+            gap <= opt->tol_gap_rel * 0.5 * yy) {
             res->status = 0;
             break;
         }
     }
+finish:
     if (it > opt->max_iter) {
         it = opt->max_iter;
         if (!(opt->tol_gap_rel > 0)) res->status = 0;

@@ -73,8 +73,8 @@ MUTANTS = {
                                   "the gap certifies the returned iterate"),
     "history_counts_groups": ("if (act[g]) nact += (int)(g_hi(goff, g) - g_lo(goff, g));", "if (act[g]) nact += 1;",
                               "|A_t| of the flops accounting counts atoms"),
-    "history_nonzeros_of_u": ("for (int64_t i = 0; i < K; i++) nnz += x[i] != 0.0;",
-                              "for (int64_t i = 0; i < K; i++) nnz += u[i] != 0.0;",
+    "history_nonzeros_of_u": ("record_iteration(goff, G, K, act, x, R, rad, gap, mu, hist ? hist +",
+                              "record_iteration(goff, G, K, act, u, R, rad, gap, mu, hist ? hist +",
                               "||x_t||_0 of the flops accounting"),
     "cp_average_with_tau": ("(theta[n] + sigma * r[n]) / (1.0 + sigma)", "(theta[n] + sigma * r[n]) / (1.0 + tau)",
                             "Table 1 Chambolle-Pock dual step"),
@@ -86,13 +86,26 @@ MUTANTS = {
                            "Table 1 Chambolle-Pock proximal threshold"),
     "cp_extrapolation_dropped": ("            beta = phi;\n", "            beta = 0.0 * phi;\n",
                                  "Table 1 Chambolle-Pock extrapolation (Arrow-Hurwicz without it)"),
+    "sparsa_bb_inverted": ("alpha = ds2 / dx2;", "alpha = dx2 / ds2;", "SpaRSA's Barzilai-Borwein step"),
+    "sparsa_first_step_unit": ("    double alpha = L;\n", "    double alpha = 1.0;\n", "SpaRSA's first step (ISTA's)"),
+    "sparsa_acceptance_loosened": ("ok = F <= Fmax - 0.5 * OR_SPARSA_SIGMA * Lt * dx2;",
+                                   "ok = F <= Fmax + 0.5 * OR_SPARSA_SIGMA * Lt * dx2 + 1e-3 * Fmax;",
+                                   "SpaRSA's nonmonotone acceptance"),
+    "twist_b_formula": ("tb = 2.0 * ta / (1.0 + xi1);", "tb = ta / (1.0 + xi1);", "TwIST's beta"),
+    "twist_monotone_reversed": ("ok = it == 1 || fallback || F <= Fprev;", "ok = it == 1 || fallback || F >= Fprev;",
+                                "TwIST's monotone safeguard"),
+    "twist_first_step_two_step": ("if (twist && it >= 2 && !fallback)", "if (twist && it >= 1 && !fallback)",
+                                  "TwIST's first (shrinkage) step"),
+    "backtracking_model_halved": ("ok = dq <= Lt * sq;", "ok = dq <= 2.0 * Lt * sq;", "Beck-Teboulle's upper model"),
+    "backtracking_no_growth": ("            else Lt *= OR_ETA;\n", "            else Lt *= 1.0;\n",
+                               "backtracking's growth of L"),
     "cp_tau_schedule_inverted": ("tau *= phi;", "tau /= phi;", "Table 1 Chambolle-Pock step schedule (gamma > 0)"),
     "cp_sigma_schedule_inverted": ("sigma /= phi;", "sigma *= phi;", "Table 1 Chambolle-Pock step schedule (gamma > 0)"),
     "fista_sequence_other_constant": ("sqrt(1.0 + 4.0 * l * l)", "sqrt(1.0 + 2.0 * l * l)", "Table 1 FISTA l_t"),
     "fista_sequence_linear": ("double ln = 0.5 * (1.0 + sqrt(1.0 + 4.0 * l * l));", "double ln = l + 1.0 / 3.0;",
                               "Table 1 FISTA l_t"),
-    "cp_dual_start_minus_y": ("        for (int64_t n = 0; n < N; n++) theta[n] = 0.0;\n    int it;",
-                              "        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];\n    int it;",
+    "cp_dual_start_minus_y": ("        for (int64_t n = 0; n < N; n++) theta[n] = 0.0;\n    res->status = 1;",
+                              "        for (int64_t n = 0; n < N; n++) theta[n] = -y[n];\n    res->status = 1;",
                               "the reading theta_0 = 0 of Table 1 Chambolle-Pock"),
     "cp_extrapolation_halved": ("            beta = phi;\n", "            beta = 0.5 * phi;\n",
                                 "Table 1 Chambolle-Pock extrapolation factor"),

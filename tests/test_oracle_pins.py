@@ -899,3 +899,159 @@ def test_chambolle_pock_first_iterates_follow_table_1(steps):
                          cp_tau=tau0, cp_sigma=sigma0, cp_gamma=gamma)
         assert abs(r["x"][0] - want[t - 1][0]) <= 1e-14, (t, r["x"][0], want[t - 1])
         assert abs(r["theta"][0] - want[t - 1][1]) <= 1e-14
+
+
+# ------------------------------- adaptive steps: backtracking, SpaRSA, TwIST
+
+ADAPTIVE = [("ista", True), ("fista", True), ("sparsa", False), ("twist", False)]
+
+
+@pytest.mark.parametrize("alg,bt", ADAPTIVE)
+@pytest.mark.parametrize("test", ["none", "safe", "dst3", "dome"])
+def test_adaptive_steps_reach_the_brute_force_minimiser(alg, bt, test):
+    """Definition 1 and Theorem 1 for the Table 1 rows whose step adapts (ISTA / FISTA with
+    backtracking, SpaRSA, TwIST): the exact minimiser, and no screened atom in its support."""
+    for seed in (71, 72):
+        g = gen.rng(seed)
+        N, K = 6, 9
+        D = gen.gaussian_dict(N, K, g)
+        y = D @ gen.sparse_x0(K, 2, g) + 0.05 * g.standard_normal(N)
+        lm, _, _ = oracle.lambda_max(D, y)
+        for ratio in (0.3, 0.7):
+            xbf = _lasso_bruteforce(D, y, ratio * lm)
+            r = oracle.solve(D, y, ratio * lm, alg=alg, backtracking=bt, test=test, tol=1e-16, max_iter=500000)
+            np.testing.assert_allclose(r["x"], xbf, atol=1e-8)
+            assert not np.any(xbf[r["scr_iter"] != 0] != 0)
+
+
+@pytest.mark.parametrize("alg,bt", ADAPTIVE)
+def test_adaptive_steps_group_lasso_kkt(alg, bt):
+    """Group-Lasso (eq. group-lasso) with DGST3: the adaptive rows reach a point satisfying
+    eq. primaldualKKT_glasso."""
+    g = gen.rng(73)
+    N, K = 40, 120
+    D = gen.gaussian_dict(N, K, g)
+    goff = gen.contiguous_groups(K, 4)
+    w = g.uniform(1.0, 2.5, size=goff.size - 1)
+    y = gen.observe(D, gen.group_x0(goff, 3, g), g)
+    lm, _, _ = oracle.lambda_max(D, y, goff, w)
+    lam = 0.4 * lm
+    r = oracle.solve(D, y, lam, goff, w, alg=alg, backtracking=bt, test="dgst3", tol=1e-14, max_iter=200000)
+    c = D.T @ (y - D @ r["x"])
+    for k in range(goff.size - 1):
+        xs, cs = r["x"][goff[k]:goff[k + 1]], c[goff[k]:goff[k + 1]]
+        if np.linalg.norm(xs) > 0:
+            np.testing.assert_allclose(cs, lam * w[k] * xs / np.linalg.norm(xs), atol=1e-6 * lam)
+        else:
+            assert np.linalg.norm(cs) <= lam * w[k] * (1 + 1e-6)
+
+
+def test_sparsa_first_iterate_is_istas_and_bb_steps_beat_ista():
+    """SpaRSA (Table 1: ISTA with the Barzilai-Borwein rule): with alpha_1 = L its first
+    iterate is ISTA's; on the ill-conditioned Pnoise dictionary of Sec. 4.2 its BB steps
+    reach the gap tolerance in far fewer iterations than ISTA; its objective obeys the
+    nonmonotone acceptance rule F(x_t) <= max of the previous 5."""
+    D, y, _ = gen.lasso_problem(200, 800, seed=74, p=0.02, kind="pnoise")
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.5 * lm
+    L = oracle.spectral_norm_sq(D) * (1 + 1e-6)
+    a = oracle.solve(D, y, lam, alg="sparsa", test="none", tol=0, max_iter=1, L=L)
+    b = oracle.solve(D, y, lam, alg="ista", test="none", tol=0, max_iter=1, L=L)
+    np.testing.assert_allclose(a["x"], b["x"], rtol=0, atol=1e-15)
+    s = oracle.solve(D, y, lam, alg="sparsa", test="dst3", tol=1e-9, max_iter=200000, L=L)
+    i = oracle.solve(D, y, lam, alg="ista", test="dst3", tol=1e-9, max_iter=200000, L=L)
+    assert s["status"] == 0 and 20 * s["iters"] < i["iters"]
+    yy = y @ y
+    h = s["hist"]
+    F = np.concatenate([[0.5 * yy], h[:, 4] + 0.5 * yy - 0.5 * lam * lam * h[:, 2] ** 2])
+    for t in range(1, F.size):
+        assert F[t] <= F[max(0, t - 5):t].max() + 1e-12 * yy
+
+
+def test_twist_is_monotone_and_fista_backtracking_obeys_its_rate():
+    """TwIST with its monotone safeguard never increases F; FISTA with backtracking (eta = 2)
+    satisfies Beck-Teboulle's bound F(x_t) - F* <= 2 eta L_f ||x_0 - x*||^2 / (t + 1)^2."""
+    D, y = _small_lasso(75, N=60, K=150, k=6)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = 0.2 * lm
+    yy = y @ y
+    ref = oracle.solve(D, y, lam, test="none", tol=1e-14, max_iter=200000)
+    Fs = 0.5 * np.sum((D @ ref["x"] - y) ** 2) + lam * np.abs(ref["x"]).sum()
+    tw = oracle.solve(D, y, lam, alg="twist", test="none", tol=0, max_iter=400)["hist"]
+    F = tw[:, 4] + 0.5 * yy - 0.5 * lam * lam * tw[:, 2] ** 2
+    assert np.all(np.diff(F) <= 1e-12 * yy) and F[-1] - Fs < 1e-6 * yy
+    bt = oracle.solve(D, y, lam, alg="fista", backtracking=True, test="none", tol=0, max_iter=400)["hist"]
+    F = bt[:, 4] + 0.5 * yy - 0.5 * lam * lam * bt[:, 2] ** 2
+    Lf = np.linalg.norm(D, 2) ** 2
+    t = np.arange(1, F.size + 1)
+    assert np.all(F - Fs <= 2 * 2.0 * Lf * np.sum(ref["x"] ** 2) / (t + 1) ** 2 + 1e-12)
+
+
+def test_adaptive_first_iterates_follow_the_cited_rules():
+    """1 x 1 problem D = [d], worked by hand from the rules the paper cites (Table 1):
+    backtracking doubles L from 1 until the quadratic model holds (for a 1 x 1 least
+    squares the model is exact, so L_1 = 2 >= d^2 = 1.69); TwIST's a = rho^2 + 1,
+    b = 2a / (1 + xi_1) with rho = (1 - sqrt(xi_1)) / (1 + sqrt(xi_1)) and its first step the
+    shrinkage step; SpaRSA's BB value on a 1 x 1 problem is d^2."""
+    d, yv, lam = 1.3, 0.9, 0.05
+    D, Y = np.array([[d]]), np.array([yv])
+    F = lambda x: 0.5 * (d * x - yv) ** 2 + lam * abs(x)
+    # FISTA with backtracking: L_1 = 2 (1 -> 2), then fixed
+    x_prev, u, l, want = 0.0, 0.0, 1.0, []
+    for t in range(1, 5):
+        xx = _soft(u - d * (d * u - yv) / 2.0, lam / 2.0)
+        ln = (1 + np.sqrt(1 + 4 * l * l)) / 2
+        u, x_prev, l = xx + (l - 1) / ln * (xx - x_prev), xx, ln
+        want.append(xx)
+    for t in range(1, 5):
+        got = oracle.solve(D, Y, lam, alg="fista", backtracking=True, test="none", tol=0, max_iter=t)["x"][0]
+        assert abs(got - want[t - 1]) <= 1e-14, (t, got, want)
+    # TwIST, xi_1 = 0.1, L = d^2 (1 + 1e-6)
+    L = d * d * (1 + 1e-6)
+    xi = 0.1
+    rho = (1 - np.sqrt(xi)) / (1 + np.sqrt(xi))
+    a, b = rho * rho + 1, 2 * (rho * rho + 1) / (1 + xi)
+    x2, x1 = 0.0, 0.0
+    want = []
+    for t in range(1, 7):
+        p = _soft(x1 - d * (d * x1 - yv) / L, lam / L)
+        xn = p if t == 1 else (1 - a) * x2 + (a - b) * x1 + b * p
+        if t > 1 and F(xn) > F(x1):
+            xn = p
+        x2, x1 = x1, xn
+        want.append(xn)
+    for t in range(1, 7):
+        got = oracle.solve(D, Y, lam, alg="twist", twist_xi1=xi, test="none", tol=0, max_iter=t, L=L)["x"][0]
+        assert abs(got - want[t - 1]) <= 1e-14, (t, got, want)
+    # SpaRSA: alpha_1 = L, then the BB value d^2 (accepted: the 1 x 1 model is exact)
+    x, want = 0.0, []
+    for t in range(1, 5):
+        al = L if t == 1 else d * d
+        x = _soft(x - d * (d * x - yv) / al, lam / al)
+        want.append(x)
+    for t in range(1, 5):
+        got = oracle.solve(D, Y, lam, alg="sparsa", test="none", tol=0, max_iter=t, L=L)["x"][0]
+        assert abs(got - want[t - 1]) <= 1e-14, (t, got, want)
+
+
+def test_gap_every_checks_the_stopping_rule_every_k_iterations():
+    D, y = _small_lasso(76)
+    lm, _, _ = oracle.lambda_max(D, y)
+    a = oracle.solve(D, y, 0.3 * lm, alg="fista", test="dst3", tol=1e-8, max_iter=100000)
+    b = oracle.solve(D, y, 0.3 * lm, alg="fista", test="dst3", tol=1e-8, max_iter=100000, gap_every=7)
+    assert b["iters"] % 7 == 0 and a["iters"] <= b["iters"] < a["iters"] + 7
+
+
+@pytest.mark.parametrize("kind,seed,ratio", [("pnoise", 76, 0.3), ("ar1", 75, 0.1), ("pnoise", 77, 0.1)])
+def test_sparsa_objective_obeys_the_nonmonotone_rule(kind, seed, ratio):
+    """SpaRSA's acceptance test (Wright-Nowak-Figueiredo): every accepted iterate satisfies
+    F(x_t) <= max of the 5 previous accepted F, over 3000 iterations on ill-conditioned
+    dictionaries (Pnoise, AR(1)) where the Barzilai-Borwein step often overshoots."""
+    D, y, _ = gen.lasso_problem(200, 800, seed=seed, p=0.02, kind=kind)
+    lm, _, _ = oracle.lambda_max(D, y)
+    lam = ratio * lm
+    yy = y @ y
+    h = oracle.solve(D, y, lam, alg="sparsa", test="none", tol=0, max_iter=3000)["hist"]
+    F = np.concatenate([[0.5 * yy], h[:, 4] + 0.5 * yy - 0.5 * lam * lam * h[:, 2] ** 2])
+    for t in range(1, F.size):
+        assert F[t] <= F[max(0, t - 5):t].max() + 1e-12 * yy, t
