@@ -51,7 +51,9 @@ typedef enum {
     DS_PENDING = 7            /* (ds_server_poll only) the request has not completed yet */
 } ds_status;
 
-typedef enum { DS_ISTA = 0, DS_FISTA = 1, DS_CP = 2 } ds_alg; /* Table 1 rows (DS_CP: Chambolle-Pock) */
+/* Table 1 rows: ISTA, FISTA, Chambolle-Pock, SpaRSA (ISTA with the Barzilai-Borwein step
+ * and its nonmonotone acceptance test) and TwIST (two-step shrinkage, monotone variant). */
+typedef enum { DS_ISTA = 0, DS_FISTA = 1, DS_CP = 2, DS_SPARSA = 3, DS_TWIST = 4 } ds_alg;
 
 typedef enum {
     DS_TEST_NONE = 0,
@@ -88,6 +90,17 @@ typedef struct {
     double cp_gamma;     /* DS_CP: gamma >= 0 of phi_t = 1 / sqrt(1 + 2 gamma tau_{t-1}); 0 (default) keeps
                             phi_t = 1 (the Lasso's penalty is not strongly convex: a positive gamma drives
                             tau_t to 0) */
+    int step_backtracking; /* DS_ISTA / DS_FISTA: 1 sets L_t by backtracking (Beck-Teboulle, the rule Table 1
+                              cites): starting from bt_L0, L is doubled until ||D (x_t - u)||^2 <= L ||x_t - u||^2
+                              (the quadratic upper model of the loss); 0 (default) keeps the fixed L */
+    double bt_L0;          /* first L of the backtracking (<= 0: 1) */
+    double twist_xi1;      /* DS_TWIST: lower bound xi_1 of the eigenvalues of D^T D / L that sets TwIST's
+                              alpha = rho^2 + 1, beta = 2 alpha / (1 + xi_1), rho = (1 - sqrt(xi_1)) /
+                              (1 + sqrt(xi_1)) (<= 0: 1e-4) */
+    int gap_every;         /* the stopping rule (duality gap) is evaluated every gap_every iterations
+                              (<= 1: every iteration) */
+    int team_size;         /* CTAs that run one solve: ds_solve / ds_solve_path (0: all SMs for large problems,
+                              fewer for small ones) and the multi-RHS blocks of batches (0: automatic) */
 } ds_options;
 
 typedef struct {
@@ -110,7 +123,8 @@ typedef struct {
 const char* ds_status_str(ds_status s);
 
 /* Fill *opt with defaults: FISTA, DST3, dynamic, max_iter 10000, tol 1e-6,
- * L from the dictionary, absolute lambda.  DS_ERR_INVALID if opt is NULL. */
+ * L from the dictionary, absolute lambda, fixed step, gap checked every
+ * iteration, automatic team size.  DS_ERR_INVALID if opt is NULL. */
 ds_status ds_options_default(ds_options* opt);
 
 /* Create a context on CUDA device `device`, ordered on `cuda_stream`
@@ -260,6 +274,8 @@ ds_status ds_solve_batch(ds_ctx* ctx, int n, const ds_dict* const* dicts, const 
  *   ds_server_poll: DS_PENDING while the request runs; DS_OK fills res
  *     (res->ms = latency from submission to completion) and forgets the ticket.
  *   ds_server_stats: completed, in flight, waiting, kernel launches, pool bytes.
+ * team_size: CTAs per team, 0 (= 4) to the number of SMs; large requests (HBM-bound) want larger
+ * teams, many small ones smaller teams.
  * A server drives its own CUDA stream; calls are serialised internally.
  * Errors: DS_ERR_INVALID (null arguments, a dictionary of another context, a
  * Lasso test on a group dictionary, an unknown ticket), DS_ERR_UNSUPPORTED (as

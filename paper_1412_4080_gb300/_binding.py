@@ -26,12 +26,12 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 (DS_OK, DS_ERR_INVALID, DS_ERR_OOM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_NOT_CONVERGED, DS_ERR_UNSUPPORTED,
  DS_PENDING) = range(8)
-DS_ISTA, DS_FISTA, DS_CP = 0, 1, 2
+DS_ISTA, DS_FISTA, DS_CP, DS_SPARSA, DS_TWIST = 0, 1, 2, 3, 4
 DS_TEST_NONE, DS_SAFE, DS_DST3, DS_DOME, DS_GSAFE, DS_DGST3 = range(6)
 DS_FP64, DS_FP32, DS_BF16, DS_FP8 = range(4)
 TESTS = {"none": DS_TEST_NONE, "safe": DS_SAFE, "dst3": DS_DST3, "dome": DS_DOME, "gsafe": DS_GSAFE,
          "dgst3": DS_DGST3}
-ALGS = {"ista": DS_ISTA, "fista": DS_FISTA, "cp": DS_CP}
+ALGS = {"ista": DS_ISTA, "fista": DS_FISTA, "cp": DS_CP, "sparsa": DS_SPARSA, "twist": DS_TWIST}
 HIST_COLS = ("active", "nnz", "R", "radius", "gap", "mu")
 
 
@@ -40,7 +40,9 @@ class ds_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("tol_gap_rel", ctypes.c_double), ("L", ctypes.c_double),
                 ("lambda_rel", ctypes.c_int), ("lowp_switch", ctypes.c_double),
                 ("batch_multi_rhs", ctypes.c_int), ("warm_start", ctypes.c_int), ("cp_tau", ctypes.c_double),
-                ("cp_sigma", ctypes.c_double), ("cp_gamma", ctypes.c_double)]
+                ("cp_sigma", ctypes.c_double), ("cp_gamma", ctypes.c_double), ("step_backtracking", ctypes.c_int),
+                ("bt_L0", ctypes.c_double), ("twist_xi1", ctypes.c_double), ("gap_every", ctypes.c_int),
+                ("team_size", ctypes.c_int)]
 
 
 class ds_result(ctypes.Structure):

@@ -40,9 +40,10 @@ ds_status ensure_io(ds_ctx* ctx, size_t bytes)
 
 bool valid_opt(const ds_options* o)
 {
-    return o && (o->alg == DS_ISTA || o->alg == DS_FISTA || o->alg == DS_CP) && o->test >= DS_TEST_NONE &&
+    return o && o->alg >= DS_ISTA && o->alg <= DS_TWIST && o->test >= DS_TEST_NONE &&
            o->test <= DS_DGST3 && o->max_iter >= 1 && o->tol_gap_rel >= 0.0 && std::isfinite(o->tol_gap_rel) &&
-           std::isfinite(o->cp_tau) && std::isfinite(o->cp_sigma) && o->cp_gamma >= 0.0 && std::isfinite(o->cp_gamma);
+           std::isfinite(o->cp_tau) && std::isfinite(o->cp_sigma) && o->cp_gamma >= 0.0 && std::isfinite(o->cp_gamma) &&
+           std::isfinite(o->bt_L0) && std::isfinite(o->twist_xi1) && o->twist_xi1 < 1.0 && o->team_size >= 0;
 }
 
 }  // namespace
@@ -127,6 +128,11 @@ ds_status ds_options_default(ds_options* opt)
     opt->cp_tau = 0.0;
     opt->cp_sigma = 0.0;
     opt->cp_gamma = 0.0;
+    opt->step_backtracking = 0;
+    opt->bt_L0 = 0.0;
+    opt->twist_xi1 = 0.0;
+    opt->gap_every = 1;
+    opt->team_size = 0;
     return DS_OK;
 }
 

@@ -139,6 +139,7 @@ struct MrhsBlock {
 struct MrhsCfg {
     int allow_tc;      // bulk phase on the tensor cores when the dictionary has a BF16 copy
     double lo_switch;  // > 0: overrides the bulk-to-FP32 switch level
+    int team_size;     // > 0: CTAs per team (else chosen from the block sizes)
 };
 struct MrhsPlan;
 ds_status mrhs_plan_create(ds_ctx* ctx, int n_blocks, const MrhsBlock* blocks, const ds_options* opt,

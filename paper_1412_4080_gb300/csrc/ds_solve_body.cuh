@@ -22,6 +22,11 @@ constexpr int kU = 4;         // 16-byte vectors per lane per GEMV item
 constexpr int kRowTile = 32;  // rows per synthesis tile
 constexpr int kSyn = 8;       // dictionary loads in flight per lane in the synthesis
 constexpr int kSpec = 2;      // entries of every nonzero list fetched with its length
+// adaptive steps (readings of the rules Table 1 cites): SpaRSA's sufficient-decrease constant (its
+// window of 5 accepted objective values is in ScalarState) and the rejections allowed per iteration,
+// after which the last attempt is kept
+constexpr double kSparsaSigma = 1e-5;
+constexpr int kRetryCap = 40;
 
 // Iterates (x, u) and per-CTA partial sums: float-float pairs for FP32
 // dictionaries, doubles for FP64 ones.
@@ -65,6 +70,16 @@ struct Ws {
     double* p_v;
     int* p_i;
     double* p_cn;
+    // adaptive steps (backtracking, SpaRSA, TwIST): a second theta buffer (the last accepted
+    // theta while a step is being tried), and per atom, at the positions of the step's iterates,
+    // the correlation z_t, the point the gradient step started from and x_{t-1}; per-CTA partials
+    // of ||xbar_t - base||^2 and ||D xbar_t - y - theta_acc||^2 = ||D (xbar_t - base)||^2
+    T* theta2;
+    T* zS;
+    X* bS;
+    X* pS;
+    X* p_sq;
+    X* p_dq;
 };
 
 template <typename T>
@@ -82,6 +97,10 @@ struct SolveP {
     const double* lambdas;  // device copy
     int lambda_rel;
     int alg, test, dynamic, max_iter, warm_start;
+    int step_mode;       // 0 fixed L (or Chambolle-Pock), 1 backtracking (ISTA/FISTA), 2 SpaRSA, 3 TwIST
+    double bt_L0;        // first L of the backtracking
+    double tw_a, tw_b;   // TwIST's alpha and beta
+    int gap_every;       // the stopping rule is evaluated every gap_every iterations
     double cp_tau0, cp_sigma0, cp_gamma;  // Chambolle-Pock (alg 2): initial steps and gamma
     double tol, L;
     T* x_out;
@@ -183,6 +202,18 @@ __device__ __forceinline__ double it_soft(double v, double thr)
 __device__ __forceinline__ FF it_momentum(FF x, FF xo, FF bt) { return ff_add(x, ff_mul(ff_sub(x, xo), bt)); }
 __device__ __forceinline__ double it_momentum(double x, double xo, double bt) { return fma(bt, x - xo, x); }
 __device__ __forceinline__ FF it_scale(FF v, FF f) { return ff_mul(v, f); }
+__device__ __forceinline__ FF it_diff(FF a, FF b) { return ff_sub(a, b); }
+// TwIST's two-step combination (1 - a) x_{t-2} + (a - b) x_{t-1} + b p
+__device__ __forceinline__ FF it_twist(FF x2, FF x1, FF p, double a, double b)
+{
+    return ff_add(ff_add(ff_mul(x2, ff_from_double(1.0 - a)), ff_mul(x1, ff_from_double(a - b))),
+                  ff_mul(p, ff_from_double(b)));
+}
+__device__ __forceinline__ double it_twist(double x2, double x1, double p, double a, double b)
+{
+    return fma(1.0 - a, x2, fma(a - b, x1, b * p));
+}
+__device__ __forceinline__ double it_diff(double a, double b) { return a - b; }
 __device__ __forceinline__ double it_scale(double v, double f) { return v * f; }
 // accumulators: |x| and x^2
 __device__ __forceinline__ void acc_abs(Dot2f& acc, FF x)
@@ -263,6 +294,20 @@ __device__ __forceinline__ void acc_resid_sq(Dot2d& acc, const Dot2d& wx, double
 {
     const double r = wx.s - y;
     acc.s = fma(r, r, acc.s);
+}
+// ((w_x - y_r) - th)^2 into an accumulator: th is the residual of the last accepted step, so the
+// difference is D (xbar - base) for the adaptive steps, formed from w_x - y in double length first
+__device__ __forceinline__ void acc_diff_sq(Dot2f& acc, const Dot2f& wx, float y, float th)
+{
+    FF t = ff_two_sum(wx.s, -y);
+    t = ff_fast_two_sum(t.h, t.l + wx.c);
+    const FF d = ff_two_sum(t.h, -th);
+    acc_sq(acc, ff_two_sum(d.h, d.l + t.l));
+}
+__device__ __forceinline__ void acc_diff_sq(Dot2d& acc, const Dot2d& wx, double y, double th)
+{
+    const double d = (wx.s - y) - th;
+    acc.s = fma(d, d, acc.s);
 }
 
 // float-float (or FP64) partial sums parked in one 8-byte shared slot
@@ -449,6 +494,15 @@ struct ScalarState {
     double cp_tau, cp_sigma;  // Chambolle-Pock: tau_{t-1}, sigma_{t-1}
     long long cols_corr, cols_synth, cols_lowp;
     int iters, since_best, low, t0;  // t0: iteration at which the current FISTA sequence started
+    // adaptive steps: the step constant being tried (backtracking L, SpaRSA alpha), the last
+    // accepted objective values (SpaRSA's nonmonotone window, TwIST's reference), the attempt's
+    // FISTA coefficient, rejections of the current step and TwIST's shrinkage-step fallback
+    double Lstep, Fprev, bt_att;
+    double Fh[5];
+    int nh, hpos, tries, fallback;
+    // Lemma 8 terms of the newest theta, committed only once its step is accepted
+    double n_alpha, n_beta, n_m2a, n_s_unc, n_sqrt_beta;
+    float n_s_unc_f, n_sqb_f;
 };
 
 // Asynchronous copies global -> shared (cp.async): prefetched values wait in shared memory, not
@@ -482,6 +536,8 @@ struct SolveK {
     float bt_h, bt_l;      // FISTA coefficient of the iteration as a float-float pair
     float dome_f[4];  // FP32 dome test of the current iteration: R, psi, rho (rounded up), branch threshold
     int* slog;  // screening log of the current lambda (null: not recorded)
+    T* thN;     // theta written by the synthesis (A) and correlated in (B)
+    T* thA;     // adaptive steps: the theta of the last accepted step
     T invL;
     T cp_sig, cp_inv1ps;  // Chambolle-Pock: sigma_{t-1} and 1 / (1 + sigma_{t-1}) of the next dual update
     typename IterT<T>::type thrX;
@@ -815,6 +871,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             C_.tol_abs = P.tol * 0.5 * yy;
             C_.delta2 = C_.delta * C_.delta;
             C_.slog = (P.scr_log && j < P.scr_rows) ? P.scr_log + (size_t)j * K : nullptr;
+            C_.thN = W.theta;
+            C_.thA = W.theta2;
         }
         __syncthreads();
         const double &lam = C_.lam, &psi = C_.psi, &coef = C_.coef, &delta = C_.delta, &nstar = C_.nstar;
@@ -839,6 +897,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         }
         const bool record = (j == 0) && P.hist != nullptr;
         const bool ista = P.alg == 0;
+        const bool fista = P.alg == 1;
         const bool cp = P.alg == 2;  // Chambolle-Pock (Table 1)
         const bool dyn_test = P.dynamic && P.test != 0;
         const bool sphere = P.test == 1 || P.test == 2 || P.test == 4 || P.test == 5;
@@ -976,7 +1035,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             C_.cp_sig = (T)P.cp_sigma0;
             C_.cp_inv1ps = (T)(1.0 / (1.0 + P.cp_sigma0));
             // precision variant: bulk phase on the low-precision copy, then FP32 polish
-            low = (P.lo_kind != 0 && sizeof(T) == 4) ? 1 : 0;
+            low = (P.lo_kind != 0 && sizeof(T) == 4 && P.step_mode == 0) ? 1 : 0;
+            S_.Lstep = P.step_mode == 1 ? P.bt_L0 : P.L;
+            S_.tries = S_.fallback = S_.nh = S_.hpos = 0;
+            S_.Fprev = INFINITY;
+            S_.bt_att = 0.0;
             cols_corr = j == 0 ? (long long)K * (need_n ? 2 : 1) : 0;
             cols_synth = cols_lowp = 0;
         }
@@ -1113,7 +1176,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 // staged in shared memory; atoms screened by the test of iteration t-1 contribute zero
                 const int E = totE;
                 if (tid == 0) cols_synth += E;
-                Acc pa_, pb_, pr_;
+                Acc pa_, pb_, pr_, pdq_;
                 const int ntiles = (N + kRowTile - 1) / kRowTile;
                 const int cap = P.syn_cap;
                 int* const sl_col = reinterpret_cast<int*>(smem_raw);
@@ -1211,7 +1274,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             // theta_t = (theta_{t-1} + sigma_{t-1} (D ubar_{t-1} - y)) / (1 + sigma_{t-1})
                             const T th = cp ? (__ldcg(W.theta + r) + C_.cp_sig * (T)theta_from(wu, yv)) * C_.cp_inv1ps
                                             : (T)theta_from(wu, yv);
-                            W.theta[r] = th;
+                            // adaptive steps: ||D (xbar_{t-1} - base)||^2 against the last accepted theta
+                            if (P.step_mode && t > 1) acc_diff_sq(pdq_, wx, yv, __ldcg(C_.thA + r));
+                            C_.thN[r] = th;
                             pa_.add(th, yv);
                             pb_.add(th, th);
                             acc_resid_sq(pr_, wx, yv);
@@ -1223,7 +1288,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 // owner test of iteration t-1 on the slice's live groups: keep flags, and ||x_{t-1}||_1,
                 // nonzeros and sizes of the survivors (Algorithm 3)
                 int kg = 0, ka = 0, nzx = 0;
-                Acc l1;
+                Acc l1, sqa;
+                const bool want_sq = P.step_mode == 1 || P.step_mode == 2;
                 for (int base = 0; base < n_own; base += kThreads) {
                     const int k = base + tid;
                     if (k < n_own) {
@@ -1238,6 +1304,20 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const int gs = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
                             const int i0 = P.is_group ? P.goff[gs] : gs, i1 = P.is_group ? P.goff[gs + 1] : gs + 1;
                             for (int i = i0; i < i1; i++) C_.slog[i] = t - 1;
+                        }
+                        if (want_sq && t > 1) {
+                            // backtracking / SpaRSA: ||xbar_{t-1} - base||^2 over the atoms of the step
+                            // (the screened ones contribute their base point: xbar is 0 there)
+                            int lo_a = a_lo0 + k, sz = 1;
+                            if (P.is_group) {
+                                const int gid = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
+                                lo_a = __ldcg(W.aoff[cur] + g_lo + k);
+                                sz = P.goff[gid + 1] - P.goff[gid];
+                            }
+                            for (int q = 0; q < sz; q++) {
+                                const X bq = ldcg_x(W.bS + lo_a + q);
+                                acc_sq(sqa, kill ? bq : it_diff(ldcg_x(xbuf(iO) + lo_a + q), bq));
+                            }
                         }
                         if (!kill) {
                             if (!P.is_group) {
@@ -1265,24 +1345,34 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 // per-CTA totals: one warp-level reduction and a single block barrier
                 const int rkg = warp_sum(kg), rka = warp_sum(ka), rnx = warp_sum(nzx);
                 const Acc rl1 = acc_warp_reduce(l1);
+                const Acc rsq = want_sq ? acc_warp_reduce(sqa) : sqa;
                 if (warp == 0) {
                     pa_ = acc_warp_reduce(pa_);
                     pb_ = acc_warp_reduce(pb_);
                     pr_ = acc_warp_reduce(pr_);
                     if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
+                    if (P.step_mode) {
+                        pdq_ = acc_warp_reduce(pdq_);
+                        if (lane == 0) part_put(W.p_dq + b, pdq_);
+                    }
                 }
-                if (lane == 0) { s_ired[warp] = rkg; s_tmp[warp] = rka; s_kg[warp] = rnx; acc_store(&s_red[0][warp][0], rl1); }
+                if (lane == 0) {
+                    s_ired[warp] = rkg; s_tmp[warp] = rka; s_kg[warp] = rnx; acc_store(&s_red[0][warp][0], rl1);
+                    if (want_sq) acc_store(&s_red[1][warp][0], rsq);
+                }
                 __syncthreads();
                 if (tid == 0) {
                     int tkg = 0, tka = 0, tnx = 0;
-                    Acc tl1;
+                    Acc tl1, tsq;
                     for (int k = 0; k < nw; k++) {
                         tkg += s_ired[k];
                         tka += s_tmp[k];
                         tnx += s_kg[k];
                         acc_merge(tl1, &s_red[0][k][0]);
+                        if (want_sq) acc_merge(tsq, &s_red[1][k][0]);
                     }
                     part_put(W.p_l1 + b, tl1);
+                    if (want_sq) part_put(W.p_sq + b, tsq);
                     s_si[12] = tkg;  // kept groups of the slice: (B) skips the compaction when nothing was screened
                     W.c_ka[b] = tka;
                     W.c_nnzx[b] = tnx;
@@ -1314,7 +1404,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 #pragma unroll
                         for (int q = 0; q < kSU; q++) {
                             const int r = r0 + q * kST;
-                            v[q] = r < N ? __ldcg(W.theta + r) : T(0);
+                            v[q] = r < N ? __ldcg(C_.thN + r) : T(0);
                         }
 #pragma unroll
                         for (int q = 0; q < kSU; q++) {
@@ -1336,22 +1426,26 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     const double a_ = part_sum_regs<kMaxG / 32>(va);
                     const double b_ = part_sum_regs<kMaxG / 32>(vb);
                     if (lane == 0) {
-                        alpha = a_;
-                        beta = b_;
-                        C_.m2a = -2.0 * a_ * inv_lam;
+                        // with an adaptive step the terms wait in S_.n_* until the step is accepted: a
+                        // rejected step is redone and the test of t-1 must keep theta_{t-1}'s terms
+                        const bool hold = P.step_mode != 0;
+                        (hold ? S_.n_alpha : alpha) = a_;
+                        (hold ? S_.n_beta : beta) = b_;
+                        (hold ? S_.n_m2a : C_.m2a) = -2.0 * a_ * inv_lam;
                         // the unclipped scaling of Lemma 8 in FP32: R^2 is stationary in mu there, and any
                         // mu gives a valid sphere, so its rounding moves R^2 by a second-order amount only
                         if (sizeof(T) == 8) {
-                            s_unc = b_ > 0.0 ? a_ * inv_lam * fast_rcp(b_) : 0.0;
-                            sqrt_beta = (double)sqrtf((float)b_) * (1.0 + 1e-6);
+                            (hold ? S_.n_s_unc : s_unc) = b_ > 0.0 ? a_ * inv_lam * fast_rcp(b_) : 0.0;
+                            (hold ? S_.n_sqrt_beta : sqrt_beta) = (double)sqrtf((float)b_) * (1.0 + 1e-6);
                         } else {
                             const float bf = (float)b_;
                             const float su = bf > 0.f ? (float)a_ * (float)inv_lam / bf : 0.f;
-                            C_.s_unc_f = su;
-                            s_unc = (double)su;
+                            (hold ? S_.n_s_unc_f : C_.s_unc_f) = su;
+                            (hold ? S_.n_s_unc : s_unc) = (double)su;
                             // an upper bound of ||theta|| is all the rounding bound of the radius needs
-                            C_.sqb_f = __fmul_ru(__fsqrt_ru(bf), 1.000001f);
-                            sqrt_beta = (double)C_.sqb_f;
+                            const float sq = __fmul_ru(__fsqrt_ru(bf), 1.000001f);
+                            (hold ? S_.n_sqb_f : C_.sqb_f) = sq;
+                            (hold ? S_.n_sqrt_beta : sqrt_beta) = (double)sq;
                         }
                     }
                 }
@@ -1375,14 +1469,73 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     }
                     const double r_ = part_sum_regs<kMaxG / 32>(vr);
                     const double l1 = part_sum_regs<kMaxG / 32>(vl);
+                    double sq_ = 0.0, dq_ = 0.0;
+                    if (P.step_mode) {
+                        // adaptive steps: ||xbar_{t-1} - base||^2 and ||D (xbar_{t-1} - base)||^2
+#pragma unroll
+                        for (int q = 0; q < kMaxG / 32; q++) {
+                            const int k = lane + 32 * q;
+                            const bool in = k < G;
+                            vr[q] = in ? ldcg_x(W.p_sq + k) : it_zero((X*)nullptr);
+                            vl[q] = in ? ldcg_x(W.p_dq + k) : it_zero((X*)nullptr);
+                        }
+                        sq_ = part_sum_regs<kMaxG / 32>(vr);
+                        dq_ = part_sum_regs<kMaxG / 32>(vl);
+                    }
                     int na = 0, nx = 0;
 #pragma unroll
                     for (int q = 0; q < kMaxG / 32; q++) { na += ia[q]; nx += ix[q]; }
                     na = warp_sum(na);
                     nx = warp_sum(nx);
                     if (lane == 0) {
-                        int stop = 0;
-                        if (t > 1) {
+                        int stop = 0, retry = 0;
+                        if (P.step_mode) {
+                            // the step that produced x_{t-1} (backtracking, SpaRSA, TwIST): its acceptance
+                            // test at xbar_{t-1}; a rejected step is redone with a larger L (alpha) or, for
+                            // TwIST, as the plain shrinkage step, before anything else of this phase
+                            const double Fcur = fma(lam, l1, 0.5 * r_);  // F(xbar_{t-1}) (t = 1: F(x_0))
+                            if (t == 1) {
+                                S_.Fh[0] = Fcur;
+                                S_.nh = 1;
+                                S_.hpos = 1;
+                                S_.Fprev = Fcur;
+                            } else {
+                                bool acc_ok;
+                                if (P.step_mode == 1) {
+                                    // Beck-Teboulle's upper model of the quadratic loss, with a slack for the
+                                    // rounding of D xbar - y and of the accepted theta
+                                    const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
+                                    acc_ok = dq_ <= S_.Lstep * sq_ + 16.0 * u * u * (beta + r_);
+                                } else if (P.step_mode == 2) {
+                                    double Fmax = S_.Fh[0];
+                                    for (int q = 1; q < S_.nh; q++) Fmax = fmax(Fmax, S_.Fh[q]);
+                                    acc_ok = Fcur <= Fmax - 0.5 * kSparsaSigma * S_.Lstep * sq_;
+                                } else {
+                                    acc_ok = S_.fallback || t == 2 || Fcur <= S_.Fprev;
+                                }
+                                if (!acc_ok && S_.tries < kRetryCap) {
+                                    retry = 1;
+                                    S_.tries++;
+                                    if (P.step_mode == 3) S_.fallback = 1;
+                                    else S_.Lstep *= 2.0;
+                                } else {
+                                    S_.tries = 0;
+                                    S_.fallback = 0;
+                                    if (P.step_mode == 2 && sq_ > 0.0)  // Barzilai-Borwein: ||D s||^2 / ||s||^2
+                                        S_.Lstep = fmin(fmax(dq_ / sq_, 1e-10 * P.L), 1e10 * P.L);
+                                    S_.Fh[S_.hpos] = Fcur;
+                                    S_.hpos = (S_.hpos + 1) % 5;
+                                    if (S_.nh < 5) S_.nh++;
+                                    S_.Fprev = Fcur;
+                                }
+                            }
+                            // the step constant of the step taken next (or redone)
+                            const double Ls = P.step_mode == 3 ? P.L : S_.Lstep;
+                            C_.invL = (T)(1.0 / Ls);
+                            C_.thrL = lam / Ls;
+                            C_.thrX = it_cast(lam / Ls, (X*)nullptr);
+                        }
+                        if (t > 1 && !retry) {
                             // P(xbar) - Dual(mu theta), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
                             primal = fma(lam, l1, 0.5 * r_);
                             gap = fma(C_.hlam2, R2n, primal - C_.hyy);
@@ -1411,12 +1564,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 double* h = P.hist + (size_t)(t - 2) * 6;
                                 h[0] = (double)na; h[1] = (double)nx; h[2] = sqrt(R2n); h[3] = rad; h[4] = gap; h[5] = mu_nom;
                             }
-                            stop = (P.tol > 0.0 && gap <= C_.tol_abs) || (t - 1 >= P.max_iter);
+                            stop = (P.tol > 0.0 && gap <= C_.tol_abs && (t - 1) % P.gap_every == 0) || (t - 1 >= P.max_iter);
                             // an owner shutting down (the server) may end the solve early, every 16 iterations
                             if (P.abort_flag && (t & 15) == 0 && *P.abort_flag) stop = 1;
                         }
                         double bt = 0.0;
-                        if (cp) {
+                        if (retry) {
+                            bt = S_.bt_att;  // the redone step keeps its FISTA coefficient
+                        } else if (cp) {
                             // Chambolle-Pock: x_t = prox_{lambda tau_{t-1}}(x_{t-1} - tau_{t-1} z), then
                             // phi_t = 1 / sqrt(1 + 2 gamma tau_{t-1}), tau_t = phi_t tau_{t-1},
                             // sigma_t = sigma_{t-1} / phi_t, ubar_t = x_t + phi_t (x_t - x_{t-1})
@@ -1430,7 +1585,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             C_.cp_sig = (T)S_.cp_sigma;
                             C_.cp_inv1ps = (T)(1.0 / (1.0 + S_.cp_sigma));
                             bt = phi;
-                        } else if (!ista) {
+                        } else if (fista) {
                             // FISTA: l_t = (1 + sqrt(1 + 4 l_{t-1}^2)) / 2, coefficient (l_{t-1} - 1) / l_t,
                             // read from the table (the sequence depends on t only)
                             const int tf = t - t0;  // index in the current FISTA sequence
@@ -1447,6 +1602,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                         }
                         s_sc[10] = bt;
+                        S_.bt_att = bt;
                         if (sizeof(T) == 4) {
                             const FF bf2 = ff_from_double(bt);
                             C_.bt_h = bf2.h;
@@ -1454,19 +1610,92 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                         s_si[4] = na; s_si[5] = nx; s_si[6] = stop;
                         s_si[9] = low;
+                        s_si[13] = retry;
                     }
                 }
                 pf_wait();  // this thread's copies have landed; the barrier below publishes them
                 __syncthreads();
                 lowB = s_si[9] != 0;
                 if (s_si[6]) break;
-                if (tid == 0) {
-                    cols_corr += s_si[4];
-                    if (lowB) cols_lowp += s_si[4];
-                }
                 X btX;
                 if constexpr (sizeof(T) == 4) btX = FF{C_.bt_h, C_.bt_l};
                 else btX = s_sc[10];
+                if (s_si[13]) {
+                    // ---- (B') the step that produced x_{t-1} failed its acceptance test: redo it from the same
+                    // base point and correlations with the new step constant (TwIST: as the plain shrinkage
+                    // step), at the same positions; atoms screened by the test of t-1 stay out of the lists
+                    X* const xR = xbuf(iO);
+                    X* const uR = ubuf(iO);
+                    int nz_base = 0;
+                    for (int base = 0; base < n_own; base += kThreads) {
+                        const int k = base + tid;
+                        int cnt = 0, gid = 0, lo_a = 0, sz = 0, td = 0;
+                        if (k < n_own && __ldcg(W.keep + g_lo + k)) {
+                            gid = __ldcg(W.act[cur] + g_lo + k);
+                            lo_a = P.is_group ? __ldcg(W.aoff[cur] + g_lo + k) : a_lo0 + k;
+                            sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
+                            td = f32_sphere ? __float_as_int(__ldcg(W.thrc[cur] + g_lo + k)) : gid;
+                            X f = it_from(T(1), (X*)nullptr);
+                            if (P.is_group) {
+                                // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
+                                Acc vq;
+                                for (int q = 0; q < sz; q++)
+                                    acc_sq(vq, it_grad_step(ldcg_x(W.bS + lo_a + q), __ldcg(W.zS + lo_a + q), invL));
+                                const double nv = sqrt(vq.value());
+                                f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * P.w[gid]) / nv) : 0.0, (X*)nullptr);
+                            }
+                            for (int q = 0; q < sz; q++) {
+                                const X v = it_grad_step(ldcg_x(W.bS + lo_a + q), __ldcg(W.zS + lo_a + q), invL);
+                                const X xv = P.is_group ? it_scale(v, f) : it_soft(v, thrX);
+                                const X pq = ldcg_x(W.pS + lo_a + q);
+                                const X uv = P.step_mode == 3 ? pq : (fista ? it_momentum(xv, pq, btX) : xv);
+                                xR[lo_a + q] = xv;
+                                uR[lo_a + q] = uv;
+                                cnt += (it_nz(xv) || (P.step_mode < 2 && it_nz(uv))) ? 1 : 0;
+                            }
+                        }
+                        int totc;
+                        const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
+                        if (cnt) {
+                            const int c0 = P.is_group ? P.goff[gid] : gid;
+                            int e = a_lo0 + nz_base + pc;
+                            for (int q = 0; q < sz; q++) {
+                                const X xv = xR[lo_a + q];
+                                const X uv = P.step_mode >= 2 ? xv : uR[lo_a + q];
+                                if (it_nz(xv) || it_nz(uv)) {
+                                    W.nz_col[e] = c0 + q;
+                                    W.nz_u[e] = uv;
+                                    W.nz_x[e] = xv;
+                                    W.nz_t[e] = td;
+                                    e++;
+                                }
+                            }
+                        }
+                        nz_base += totc;
+                    }
+                    if (tid == 0) W.c_nz[b] = nz_base;
+                    ok = grid_sync(bar, G, gen);
+                    if (!ok) return false;
+                    t--;  // the same iteration again: the test of t-1 and the synthesis of the redone step
+                    continue;
+                }
+                if (tid == 0) {
+                    cols_corr += s_si[4];
+                    if (lowB) cols_lowp += s_si[4];
+                    if (P.step_mode) {
+                        // the step was accepted: theta_t's Lemma 8 terms take effect, theta_t is the accepted theta
+                        alpha = S_.n_alpha;
+                        beta = S_.n_beta;
+                        C_.m2a = S_.n_m2a;
+                        s_unc = S_.n_s_unc;
+                        sqrt_beta = S_.n_sqrt_beta;
+                        C_.s_unc_f = S_.n_s_unc_f;
+                        C_.sqb_f = S_.n_sqb_f;
+                        T* const th = C_.thA;
+                        C_.thA = C_.thN;
+                        C_.thN = th;
+                    }
+                }
 
                 // rounds of the slice's live groups (whole groups, at most RA atoms): the survivors of
                 // the test of t-1 move to their compacted positions (list nxt, iterate buffers iO ^ 1),
@@ -1596,18 +1825,29 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const bool first = k0 == 0;
                             const X uo = first ? s_pf_u[tid] : ldcg_x(uO + lo_o);
                             const X xo = first ? s_pf_x[tid] : ldcg_x(xO + lo_o);
-                            const X xv = it_soft(it_grad_step(cp ? xo : uo, z, invL), thrX);
-                            const X uv = ista ? xv : it_momentum(xv, xo, btX);
+                            // gradient step from ubar_{t-1} (ISTA, FISTA) or x_{t-1} (CP, SpaRSA, TwIST)
+                            const X bpt = (cp || P.step_mode >= 2) ? xo : uo;
+                            X xv = it_soft(it_grad_step(bpt, z, invL), thrX);
+                            // TwIST after its first step: (1 - a) x_{t-2} + (a - b) x_{t-1} + b prox(...), with
+                            // x_{t-2} kept in the u buffer
+                            if (P.step_mode == 3 && t > 1) xv = it_twist(uo, xo, xv, P.tw_a, P.tw_b);
+                            const X uv = P.step_mode == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
                             xW[an] = xv;
                             uW[an] = uv;
+                            if (P.step_mode) {
+                                // what a redone step needs: z_t, the base point and x_{t-1}
+                                W.zS[an] = z;
+                                W.bS[an] = bpt;
+                                W.pS[an] = xo;
+                            }
                             mloc = fmax(mloc, fabs(z));
-                            cnt = (it_nz(uv) || it_nz(xv)) ? 1 : 0;
+                            cnt = (it_nz(P.step_mode >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
                         } else {
                             Acc zq, vq;
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X v = it_grad_step(ldcg_x((cp ? xO : uO) + lo_o + q), z, invL);
+                                const X v = it_grad_step(ldcg_x((cp || P.step_mode >= 2 ? xO : uO) + lo_o + q), z, invL);
                                 zq.add(z, z);
                                 acc_sq(vq, v);
                             }
@@ -1618,11 +1858,19 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X xv = it_scale(it_grad_step(ldcg_x((cp ? xO : uO) + lo_o + q), z, invL), f);
-                                const X uv = ista ? xv : it_momentum(xv, ldcg_x(xO + lo_o + q), btX);
+                                const X xo = ldcg_x(xO + lo_o + q);
+                                const X bpt = (cp || P.step_mode >= 2) ? xo : ldcg_x(uO + lo_o + q);
+                                X xv = it_scale(it_grad_step(bpt, z, invL), f);
+                                if (P.step_mode == 3 && t > 1) xv = it_twist(ldcg_x(uO + lo_o + q), xo, xv, P.tw_a, P.tw_b);
+                                const X uv = P.step_mode == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
                                 xW[an + q] = xv;
                                 uW[an + q] = uv;
-                                cnt += (it_nz(uv) || it_nz(xv)) ? 1 : 0;
+                                if (P.step_mode) {
+                                    W.zS[an + q] = z;
+                                    W.bS[an + q] = bpt;
+                                    W.pS[an + q] = xo;
+                                }
+                                cnt += (it_nz(P.step_mode >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
                             }
                             // rounded up so that the FP32 max stays an upper bound of the FP64 value
                             mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
@@ -1638,7 +1886,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         int e = a_lo0 + nz_base + pc;
                         for (int q = 0; q < sz; q++) {
                             const X xv = xW[an + q];
-                            const X uv = uW[an + q];
+                            const X uv = P.step_mode >= 2 ? xv : uW[an + q];
                             if (it_nz(uv) || it_nz(xv)) {
                                 W.nz_col[e] = c0 + q;
                                 W.nz_u[e] = uv;
@@ -1769,6 +2017,12 @@ inline size_t layout(char* base, const DictDesc& dd, const Geometry& g, int n_la
     w->p_v = bp.take<double>(G);
     w->p_i = bp.take<int>(G);
     w->p_cn = bp.take<double>(G);
+    w->theta2 = bp.take<T>(g.npad);
+    w->zS = bp.take<T>(K);
+    w->bS = bp.take<X>(K);
+    w->pS = bp.take<X>(K);
+    w->p_sq = bp.take<X>(G);
+    w->p_dq = bp.take<X>(G);
     *lam_dev = bp.take<double>(std::max(n_lambda, 1));
     *res_dev = bp.take<DevResult>(std::max(n_lambda, 1));
     *colnorm_w = dd.norms_in_kernel ? bp.take<double>(K) : nullptr;
@@ -1806,6 +2060,20 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.cp_tau0 = (opt && opt->cp_tau > 0.0) ? opt->cp_tau : 0.99 / std::sqrt(P.L);
     P.cp_sigma0 = (opt && opt->cp_sigma > 0.0) ? opt->cp_sigma : 0.99 / std::sqrt(P.L);
     P.cp_gamma = (opt && opt->cp_gamma > 0.0) ? opt->cp_gamma : 0.0;
+    P.step_mode = 0;
+    if (opt && opt->alg == DS_SPARSA) P.step_mode = 2;
+    else if (opt && opt->alg == DS_TWIST) P.step_mode = 3;
+    else if (opt && opt->step_backtracking && (opt->alg == DS_ISTA || opt->alg == DS_FISTA)) P.step_mode = 1;
+    P.bt_L0 = (opt && opt->bt_L0 > 0.0) ? opt->bt_L0 : 1.0;
+    {
+        // TwIST (Bioucas-Dias, Figueiredo): alpha = rho^2 + 1, beta = 2 alpha / (xi_1 + xi_m) with
+        // rho = (1 - sqrt(k)) / (1 + sqrt(k)), k = xi_1 / xi_m, for the eigenvalues of D^T D / L in [xi_1, 1]
+        const double xi1 = (opt && opt->twist_xi1 > 0.0) ? opt->twist_xi1 : 1e-4;
+        const double rho = (1.0 - std::sqrt(xi1)) / (1.0 + std::sqrt(xi1));
+        P.tw_a = rho * rho + 1.0;
+        P.tw_b = 2.0 * P.tw_a / (1.0 + xi1);
+    }
+    P.gap_every = (opt && opt->gap_every > 1) ? opt->gap_every : 1;
     P.RA = g.RA;
     P.nchunk = g.nchunk;
     P.npad = g.npad;

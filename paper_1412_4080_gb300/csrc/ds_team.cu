@@ -265,7 +265,7 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
     std::vector<MrhsBlock> blocks;
     for (int i = 0; i < n; i++) {
         multi[i] = sizeof(T) == 4 && opt->batch_multi_rhs && !dicts[i]->is_group && opt->test <= DS_DOME &&
-                   opt->alg != DS_CP && n_rhs[i] >= 2;
+                   (opt->alg == DS_ISTA || opt->alg == DS_FISTA) && !opt->step_backtracking && n_rhs[i] >= 2;
         if (!multi[i]) continue;
         // right-hand sides in order, or sorted by lambda (similar iteration counts and
         // screened sets in a block: a tighter union list and fewer idle slots)
@@ -316,6 +316,7 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
         MrhsCfg mc;
         mc.allow_tc = cfg.allow_tc;
         mc.lo_switch = cfg.lo_switch;
+        mc.team_size = opt->team_size;
         ms = mrhs_plan_create(ctx, (int)blocks.size(), blocks.data(), opt, mf, ctx->fista_n, mc, &B->mplan);
         if (ms != DS_OK) return ms;
     }
@@ -499,7 +500,7 @@ static ds_status batch_create_cfg(ds_ctx* ctx, int n, const ds_dict* const* dict
     if (!ctx || n < 1 || !dicts || !Y || !n_rhs || !lambdas || !opt || !X_out || !out) return DS_ERR_INVALID;
     *out = nullptr;
     if (opt->max_iter < 1 || !(opt->tol_gap_rel >= 0.0) || opt->test < DS_TEST_NONE || opt->test > DS_DGST3 ||
-        (opt->alg != DS_ISTA && opt->alg != DS_FISTA && opt->alg != DS_CP) || opt->L < 0.0)
+        opt->alg < DS_ISTA || opt->alg > DS_TWIST || opt->L < 0.0 || opt->team_size < 0)
         return DS_ERR_INVALID;
     const int dtype = dicts[0] ? dicts[0]->dtype : -1;
     for (int i = 0; i < n; i++) {
@@ -857,6 +858,8 @@ struct ds_server {
     int smem = 0;
     std::unordered_map<uint64_t, Ticket> tickets;
     std::deque<uint64_t> pending;
+    const ds_dict* last_dict = nullptr;  // dictionary of the last published request (affinity)
+    int front_bypassed = 0;              // times the oldest waiting request was passed over
     std::vector<int64_t> slot_seq;
     std::vector<uint64_t> slot_ticket;
     uint64_t next_ticket = 1;
@@ -989,17 +992,36 @@ static ds_status server_launch(ds_server* S)
     return DS_OK;
 }
 
+// Dictionary affinity: among the first kAffinityWindow waiting requests, one on the dictionary of the
+// last published request goes first, so that the requests the teams run side by side share that
+// dictionary's columns in L2; the oldest waiting request is passed over at most kMaxBypass times.
+constexpr size_t kAffinityWindow = 64;
+constexpr int kMaxBypass = 32;
+
 static ds_status server_pump(ds_server* S)
 {
     server_harvest(S);
     while (!S->pending.empty()) {
-        auto it = S->tickets.find(S->pending.front());
+        size_t pick = 0;
+        if (S->last_dict && S->front_bypassed < kMaxBypass) {
+            const size_t n = std::min(kAffinityWindow, S->pending.size());
+            for (size_t k = 0; k < n; k++) {
+                auto c = S->tickets.find(S->pending[k]);
+                if (c != S->tickets.end() && c->second.dict == S->last_dict) {
+                    pick = k;
+                    break;
+                }
+            }
+        }
+        auto it = S->tickets.find(S->pending[pick]);
         if (it == S->tickets.end()) {
-            S->pending.pop_front();
+            S->pending.erase(S->pending.begin() + pick);
             continue;
         }
         if (!server_publish(S, it->first, it->second, it->second.y.data())) break;
-        S->pending.pop_front();
+        S->last_dict = it->second.dict;
+        S->front_bypassed = pick ? S->front_bypassed + 1 : 0;
+        S->pending.erase(S->pending.begin() + pick);
     }
     // a kernel that went idle exits; relaunch it while published work is outstanding
     if (S->published > S->completed) {
@@ -1044,7 +1066,8 @@ ds_status ds_server_destroy(ds_server* S)
 ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, int64_t max_K, int team_size,
                            ds_server** out)
 {
-    if (!ctx || !out || max_N < 1 || max_K < 1 || hbm_budget_bytes < (1u << 20) || team_size < 0 || team_size > 16)
+    if (!ctx || !out || max_N < 1 || max_K < 1 || hbm_budget_bytes < (1u << 20) || team_size < 0 ||
+        team_size > std::min(ctx->num_sms, ds::kMaxG))
         return DS_ERR_INVALID;
     *out = nullptr;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return DS_ERR_CUDA;
@@ -1147,7 +1170,7 @@ ds_status ds_server_submit(ds_server* S, const ds_dict* dict, const void* y, dou
     if (dict->dtype != DS_FP32) return DS_ERR_UNSUPPORTED;
     if (dict->N > S->max_N || dict->K > S->max_K) return DS_ERR_UNSUPPORTED;
     if (!(lambda > 0.0) || opt->max_iter < 1 || !(opt->tol_gap_rel >= 0.0) || opt->test < DS_TEST_NONE ||
-        opt->test > DS_DGST3 || (opt->alg != DS_ISTA && opt->alg != DS_FISTA && opt->alg != DS_CP) || opt->L < 0.0)
+        opt->test > DS_DGST3 || opt->alg < DS_ISTA || opt->alg > DS_TWIST || opt->L < 0.0)
         return DS_ERR_INVALID;
     if (dict->is_group && (opt->test == DS_SAFE || opt->test == DS_DST3 || opt->test == DS_DOME)) return DS_ERR_INVALID;
     std::lock_guard<std::mutex> lk(S->mu);

@@ -142,14 +142,14 @@ def test_multi_rhs_degenerate_cases(ctx):
 
 
 def test_multi_rhs_one_cta_teams(ctx):
-    # more blocks than SMs: every team is one CTA and takes several blocks in turn
+    # more blocks than SMs, teams of one CTA (ds_options.team_size): each takes several blocks in turn
     g = gen.rng(304)
     insts = []
     for k in range(170):
         N = int(g.integers(40, 130))
         K = int(g.integers(100, 400))
         insts.append(_instance(1000 + k, N, K, 2))
-    opt = ds.ds_options_default(test="dst3", tol_gap_rel=0.0, max_iter=120, lambda_rel=1)
+    opt = ds.ds_options_default(test="dst3", tol_gap_rel=0.0, max_iter=120, lambda_rel=1, team_size=1)
     dicts, Ys, Xs, lams, res, layout = _run_batch(ctx, insts, opt)
     try:
         assert layout["multi_rhs_blocks"] == 170 and layout["multi_rhs_team_size"] == 1, layout
