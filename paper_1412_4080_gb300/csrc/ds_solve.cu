@@ -30,11 +30,13 @@
 
 namespace ds {
 
-template <typename T>
+// ADAPT: the kernel also runs the adaptive-step rows (backtracking, SpaRSA, TwIST); fixed-step solves
+// launch the instance without that code.
+template <typename T, bool ADAPT>
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(const SolveP<T> P)
 {
     unsigned int gen = 0;  // running barrier target, used by thread 0 only
-    if (!solve_body<T>(P, blockIdx.x, gridDim.x, P.ws.bar, gen) && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!solve_body<T, ADAPT>(P, blockIdx.x, gridDim.x, P.ws.bar, gen) && blockIdx.x == 0 && threadIdx.x == 0) {
         const int n = P.n_lambda > 0 ? P.n_lambda : 1;
         for (int j = 0; j < n; j++) P.res[j].status = kDevTimeout;
     }
@@ -121,15 +123,17 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DS_ERR_CUDA;
-    static bool attr_set[64] = {};
-    if (dev < 64 && !attr_set[dev]) {
-        if (cudaFuncSetAttribute(solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const bool adapt = P.step_mode != 0;
+    const void* kfn = adapt ? (const void*)solve_kernel<T, true> : (const void*)solve_kernel<T, false>;
+    static bool attr_set[2][64] = {};
+    if (dev < 64 && !attr_set[adapt][dev]) {
+        if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(env.smem_optin - 40 * 1024)) != cudaSuccess)
             return DS_ERR_CUDA;
-        attr_set[dev] = true;
+        attr_set[adapt][dev] = true;
     }
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, solve_kernel<T>, kThreads, g.smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, g.smem) != cudaSuccess)
         return DS_ERR_CUDA;
     if (occ < 1) return DS_ERR_UNSUPPORTED;
 
@@ -138,7 +142,7 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
         env.ctx->launches++;
         cudaEventRecord(env.ctx->ev0, s);
     }
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)solve_kernel<T>, dim3(g.G), dim3(kThreads), args, g.smem, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(g.G), dim3(kThreads), args, g.smem, s);
     if (e != cudaSuccess) {
         fprintf(stderr, "dscreen: solve launch failed: %s\n", cudaGetErrorString(e));
         return DS_ERR_CUDA;

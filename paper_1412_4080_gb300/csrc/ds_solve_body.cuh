@@ -545,10 +545,13 @@ struct SolveK {
 
 // One solve (or lambda path) by a team of G CTAs (rank b) that synchronise on
 // `bar`; `gen` is the calling thread's running barrier target.
-template <typename T>
+// ADAPT = false compiles the fixed-step rows only (ISTA, FISTA, Chambolle-Pock without backtracking):
+// the adaptive-step code below is then absent from the kernel, and so is its register pressure.
+template <typename T, bool ADAPT = true>
 __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, const int G, GridBarrier* bar,
                                            unsigned int& gen)
 {
+    const int SM = ADAPT ? P.step_mode : 0;  // adaptive step rule of this solve (0: fixed step)
     using V = typename Vec4<T>::type;
     using X = typename IterT<T>::type;
     using Acc = typename Dot2<T>::type;
@@ -1035,8 +1038,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             C_.cp_sig = (T)P.cp_sigma0;
             C_.cp_inv1ps = (T)(1.0 / (1.0 + P.cp_sigma0));
             // precision variant: bulk phase on the low-precision copy, then FP32 polish
-            low = (P.lo_kind != 0 && sizeof(T) == 4 && P.step_mode == 0) ? 1 : 0;
-            S_.Lstep = P.step_mode == 1 ? P.bt_L0 : P.L;
+            low = (P.lo_kind != 0 && sizeof(T) == 4 && SM == 0) ? 1 : 0;
+            S_.Lstep = SM == 1 ? P.bt_L0 : P.L;
             S_.tries = S_.fallback = S_.nh = S_.hpos = 0;
             S_.Fprev = INFINITY;
             S_.bt_att = 0.0;
@@ -1275,7 +1278,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const T th = cp ? (__ldcg(W.theta + r) + C_.cp_sig * (T)theta_from(wu, yv)) * C_.cp_inv1ps
                                             : (T)theta_from(wu, yv);
                             // adaptive steps: ||D (xbar_{t-1} - base)||^2 against the last accepted theta
-                            if (P.step_mode && t > 1) acc_diff_sq(pdq_, wx, yv, __ldcg(C_.thA + r));
+                            if (SM && t > 1) acc_diff_sq(pdq_, wx, yv, __ldcg(C_.thA + r));
                             C_.thN[r] = th;
                             pa_.add(th, yv);
                             pb_.add(th, th);
@@ -1289,7 +1292,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 // nonzeros and sizes of the survivors (Algorithm 3)
                 int kg = 0, ka = 0, nzx = 0;
                 Acc l1, sqa;
-                const bool want_sq = P.step_mode == 1 || P.step_mode == 2;
+                const bool want_sq = SM == 1 || SM == 2;
                 for (int base = 0; base < n_own; base += kThreads) {
                     const int k = base + tid;
                     if (k < n_own) {
@@ -1351,7 +1354,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     pb_ = acc_warp_reduce(pb_);
                     pr_ = acc_warp_reduce(pr_);
                     if (lane == 0) { part_put(W.p_a + b, pa_); part_put(W.p_b + b, pb_); part_put(W.p_r + b, pr_); }
-                    if (P.step_mode) {
+                    if (SM) {
                         pdq_ = acc_warp_reduce(pdq_);
                         if (lane == 0) part_put(W.p_dq + b, pdq_);
                     }
@@ -1428,7 +1431,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     if (lane == 0) {
                         // with an adaptive step the terms wait in S_.n_* until the step is accepted: a
                         // rejected step is redone and the test of t-1 must keep theta_{t-1}'s terms
-                        const bool hold = P.step_mode != 0;
+                        const bool hold = SM != 0;
                         (hold ? S_.n_alpha : alpha) = a_;
                         (hold ? S_.n_beta : beta) = b_;
                         (hold ? S_.n_m2a : C_.m2a) = -2.0 * a_ * inv_lam;
@@ -1470,7 +1473,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     const double r_ = part_sum_regs<kMaxG / 32>(vr);
                     const double l1 = part_sum_regs<kMaxG / 32>(vl);
                     double sq_ = 0.0, dq_ = 0.0;
-                    if (P.step_mode) {
+                    if (SM) {
                         // adaptive steps: ||xbar_{t-1} - base||^2 and ||D (xbar_{t-1} - base)||^2
 #pragma unroll
                         for (int q = 0; q < kMaxG / 32; q++) {
@@ -1489,7 +1492,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     nx = warp_sum(nx);
                     if (lane == 0) {
                         int stop = 0, retry = 0;
-                        if (P.step_mode) {
+                        if (SM) {
                             // the step that produced x_{t-1} (backtracking, SpaRSA, TwIST): its acceptance
                             // test at xbar_{t-1}; a rejected step is redone with a larger L (alpha) or, for
                             // TwIST, as the plain shrinkage step, before anything else of this phase
@@ -1501,12 +1504,12 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 S_.Fprev = Fcur;
                             } else {
                                 bool acc_ok;
-                                if (P.step_mode == 1) {
+                                if (SM == 1) {
                                     // Beck-Teboulle's upper model of the quadratic loss, with a slack for the
                                     // rounding of D xbar - y and of the accepted theta
                                     const double u = sizeof(T) == 4 ? 0x1p-24 : 0x1p-53;
                                     acc_ok = dq_ <= S_.Lstep * sq_ + 16.0 * u * u * (beta + r_);
-                                } else if (P.step_mode == 2) {
+                                } else if (SM == 2) {
                                     double Fmax = S_.Fh[0];
                                     for (int q = 1; q < S_.nh; q++) Fmax = fmax(Fmax, S_.Fh[q]);
                                     acc_ok = Fcur <= Fmax - 0.5 * kSparsaSigma * S_.Lstep * sq_;
@@ -1516,12 +1519,12 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 if (!acc_ok && S_.tries < kRetryCap) {
                                     retry = 1;
                                     S_.tries++;
-                                    if (P.step_mode == 3) S_.fallback = 1;
+                                    if (SM == 3) S_.fallback = 1;
                                     else S_.Lstep *= 2.0;
                                 } else {
                                     S_.tries = 0;
                                     S_.fallback = 0;
-                                    if (P.step_mode == 2 && sq_ > 0.0)  // Barzilai-Borwein: ||D s||^2 / ||s||^2
+                                    if (SM == 2 && sq_ > 0.0)  // Barzilai-Borwein: ||D s||^2 / ||s||^2
                                         S_.Lstep = fmin(fmax(dq_ / sq_, 1e-10 * P.L), 1e10 * P.L);
                                     S_.Fh[S_.hpos] = Fcur;
                                     S_.hpos = (S_.hpos + 1) % 5;
@@ -1530,7 +1533,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 }
                             }
                             // the step constant of the step taken next (or redone)
-                            const double Ls = P.step_mode == 3 ? P.L : S_.Lstep;
+                            const double Ls = SM == 3 ? P.L : S_.Lstep;
                             C_.invL = (T)(1.0 / Ls);
                             C_.thrL = lam / Ls;
                             C_.thrX = it_cast(lam / Ls, (X*)nullptr);
@@ -1620,7 +1623,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 X btX;
                 if constexpr (sizeof(T) == 4) btX = FF{C_.bt_h, C_.bt_l};
                 else btX = s_sc[10];
-                if (s_si[13]) {
+                if (ADAPT && s_si[13]) {
                     // ---- (B') the step that produced x_{t-1} failed its acceptance test: redo it from the same
                     // base point and correlations with the new step constant (TwIST: as the plain shrinkage
                     // step), at the same positions; atoms screened by the test of t-1 stay out of the lists
@@ -1648,10 +1651,10 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 const X v = it_grad_step(ldcg_x(W.bS + lo_a + q), __ldcg(W.zS + lo_a + q), invL);
                                 const X xv = P.is_group ? it_scale(v, f) : it_soft(v, thrX);
                                 const X pq = ldcg_x(W.pS + lo_a + q);
-                                const X uv = P.step_mode == 3 ? pq : (fista ? it_momentum(xv, pq, btX) : xv);
+                                const X uv = SM == 3 ? pq : (fista ? it_momentum(xv, pq, btX) : xv);
                                 xR[lo_a + q] = xv;
                                 uR[lo_a + q] = uv;
-                                cnt += (it_nz(xv) || (P.step_mode < 2 && it_nz(uv))) ? 1 : 0;
+                                cnt += (it_nz(xv) || (SM < 2 && it_nz(uv))) ? 1 : 0;
                             }
                         }
                         int totc;
@@ -1661,7 +1664,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             int e = a_lo0 + nz_base + pc;
                             for (int q = 0; q < sz; q++) {
                                 const X xv = xR[lo_a + q];
-                                const X uv = P.step_mode >= 2 ? xv : uR[lo_a + q];
+                                const X uv = SM >= 2 ? xv : uR[lo_a + q];
                                 if (it_nz(xv) || it_nz(uv)) {
                                     W.nz_col[e] = c0 + q;
                                     W.nz_u[e] = uv;
@@ -1682,7 +1685,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 if (tid == 0) {
                     cols_corr += s_si[4];
                     if (lowB) cols_lowp += s_si[4];
-                    if (P.step_mode) {
+                    if (SM) {
                         // the step was accepted: theta_t's Lemma 8 terms take effect, theta_t is the accepted theta
                         alpha = S_.n_alpha;
                         beta = S_.n_beta;
@@ -1826,28 +1829,28 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const X uo = first ? s_pf_u[tid] : ldcg_x(uO + lo_o);
                             const X xo = first ? s_pf_x[tid] : ldcg_x(xO + lo_o);
                             // gradient step from ubar_{t-1} (ISTA, FISTA) or x_{t-1} (CP, SpaRSA, TwIST)
-                            const X bpt = (cp || P.step_mode >= 2) ? xo : uo;
+                            const X bpt = (cp || SM >= 2) ? xo : uo;
                             X xv = it_soft(it_grad_step(bpt, z, invL), thrX);
                             // TwIST after its first step: (1 - a) x_{t-2} + (a - b) x_{t-1} + b prox(...), with
                             // x_{t-2} kept in the u buffer
-                            if (P.step_mode == 3 && t > 1) xv = it_twist(uo, xo, xv, P.tw_a, P.tw_b);
-                            const X uv = P.step_mode == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
+                            if (SM == 3 && t > 1) xv = it_twist(uo, xo, xv, P.tw_a, P.tw_b);
+                            const X uv = SM == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
                             xW[an] = xv;
                             uW[an] = uv;
-                            if (P.step_mode) {
+                            if (SM) {
                                 // what a redone step needs: z_t, the base point and x_{t-1}
                                 W.zS[an] = z;
                                 W.bS[an] = bpt;
                                 W.pS[an] = xo;
                             }
                             mloc = fmax(mloc, fabs(z));
-                            cnt = (it_nz(P.step_mode >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
+                            cnt = (it_nz(SM >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
                         } else {
                             Acc zq, vq;
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X v = it_grad_step(ldcg_x((cp || P.step_mode >= 2 ? xO : uO) + lo_o + q), z, invL);
+                                const X v = it_grad_step(ldcg_x((cp || SM >= 2 ? xO : uO) + lo_o + q), z, invL);
                                 zq.add(z, z);
                                 acc_sq(vq, v);
                             }
@@ -1859,18 +1862,18 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
                                 const X xo = ldcg_x(xO + lo_o + q);
-                                const X bpt = (cp || P.step_mode >= 2) ? xo : ldcg_x(uO + lo_o + q);
+                                const X bpt = (cp || SM >= 2) ? xo : ldcg_x(uO + lo_o + q);
                                 X xv = it_scale(it_grad_step(bpt, z, invL), f);
-                                if (P.step_mode == 3 && t > 1) xv = it_twist(ldcg_x(uO + lo_o + q), xo, xv, P.tw_a, P.tw_b);
-                                const X uv = P.step_mode == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
+                                if (SM == 3 && t > 1) xv = it_twist(ldcg_x(uO + lo_o + q), xo, xv, P.tw_a, P.tw_b);
+                                const X uv = SM == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
                                 xW[an + q] = xv;
                                 uW[an + q] = uv;
-                                if (P.step_mode) {
+                                if (SM) {
                                     W.zS[an + q] = z;
                                     W.bS[an + q] = bpt;
                                     W.pS[an + q] = xo;
                                 }
-                                cnt += (it_nz(P.step_mode >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
+                                cnt += (it_nz(SM >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
                             }
                             // rounded up so that the FP32 max stays an upper bound of the FP64 value
                             mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
@@ -1886,7 +1889,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         int e = a_lo0 + nz_base + pc;
                         for (int q = 0; q < sz; q++) {
                             const X xv = xW[an + q];
-                            const X uv = P.step_mode >= 2 ? xv : uW[an + q];
+                            const X uv = SM >= 2 ? xv : uW[an + q];
                             if (it_nz(uv) || it_nz(xv)) {
                                 W.nz_col[e] = c0 + q;
                                 W.nz_u[e] = uv;

@@ -67,7 +67,9 @@ __device__ __forceinline__ int ld_acquire_sys(const volatile int* p)
     return v;
 }
 
-template <typename T>
+// ADAPT: the solves may use the adaptive-step rows (backtracking, SpaRSA, TwIST); a batch of fixed-step
+// solves launches the instance without that code, the server (any request) the one with it.
+template <typename T, bool ADAPT = true>
 __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
 {
     __shared__ SolveP<T> sP;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
                 return;
             }
         }
-        if (!solve_body<T>(sP, rank, A.team_size, bar, gen)) {
+        if (!solve_body<T, ADAPT>(sP, rank, A.team_size, bar, gen)) {
             if (threadIdx.x == 0) atomicExch(A.error, 1);
             if (threadIdx.x == 0 && rank == 0) sP.res[0].status = kDevTimeout;
             return;
@@ -192,6 +194,12 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
     }
 }
 
+template <typename T>
+static const void* team_fn(bool adapt)
+{
+    return adapt ? (const void*)team_kernel<T, true> : (const void*)team_kernel<T, false>;
+}
+
 // ------------------------------------------------------------ team geometry
 
 // Team size: enough teams to keep every SM busy; a problem shared by fewer
@@ -209,6 +217,7 @@ static int pick_team_size(int n_jobs, int num_sms)
 struct ds_batch {
     ds_ctx* ctx;
     int dtype;
+    bool adapt = false;  // the problems use an adaptive-step row (the team kernel with that code)
     int n_jobs;
     std::vector<int> order;            // job -> position in the caller's result array
     std::vector<int> job_inst, job_rhs;
@@ -427,11 +436,13 @@ static ds_status batch_create_t(ds_ctx* ctx, int n, const ds_dict* const* dicts,
     B->args = A;
     B->grid = n_teams * team;
     B->smem = (int)gmax.smem;
-    if (cudaFuncSetAttribute(team_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    B->adapt = opt->alg == DS_SPARSA || opt->alg == DS_TWIST || opt->step_backtracking;
+    const void* kfn = team_fn<T>(B->adapt);
+    if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(ctx->smem_optin - 40 * 1024)) != cudaSuccess)
         return DS_ERR_CUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, team_kernel<T>, kThreads, B->smem) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, B->smem) != cudaSuccess || occ < 1)
         return DS_ERR_UNSUPPORTED;
     return DS_OK;
 }
@@ -453,7 +464,7 @@ static ds_status batch_enqueue_t(ds_batch* B, cudaStream_t s)
     if (cudaMemsetAsync(B->dctl, 0, B->ctl_bytes, s) != cudaSuccess) return DS_ERR_CUDA;
     if (cudaMemsetAsync(B->dres, 0, sizeof(DevResult) * B->n_jobs, s) != cudaSuccess) return DS_ERR_CUDA;
     void* args[] = {(void*)A};
-    if (cudaLaunchCooperativeKernel((const void*)team_kernel<T>, dim3(B->grid), dim3(kThreads), args, B->smem, s) !=
+    if (cudaLaunchCooperativeKernel(team_fn<T>(B->adapt), dim3(B->grid), dim3(kThreads), args, B->smem, s) !=
         cudaSuccess)
         return DS_ERR_CUDA;
     if (cudaMemcpyAsync(B->hres, B->dres, sizeof(DevResult) * B->n_jobs, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -858,8 +869,6 @@ struct ds_server {
     int smem = 0;
     std::unordered_map<uint64_t, Ticket> tickets;
     std::deque<uint64_t> pending;
-    const ds_dict* last_dict = nullptr;  // dictionary of the last published request (affinity)
-    int front_bypassed = 0;              // times the oldest waiting request was passed over
     std::vector<int64_t> slot_seq;
     std::vector<uint64_t> slot_ticket;
     uint64_t next_ticket = 1;
@@ -992,36 +1001,17 @@ static ds_status server_launch(ds_server* S)
     return DS_OK;
 }
 
-// Dictionary affinity: among the first kAffinityWindow waiting requests, one on the dictionary of the
-// last published request goes first, so that the requests the teams run side by side share that
-// dictionary's columns in L2; the oldest waiting request is passed over at most kMaxBypass times.
-constexpr size_t kAffinityWindow = 64;
-constexpr int kMaxBypass = 32;
-
 static ds_status server_pump(ds_server* S)
 {
     server_harvest(S);
     while (!S->pending.empty()) {
-        size_t pick = 0;
-        if (S->last_dict && S->front_bypassed < kMaxBypass) {
-            const size_t n = std::min(kAffinityWindow, S->pending.size());
-            for (size_t k = 0; k < n; k++) {
-                auto c = S->tickets.find(S->pending[k]);
-                if (c != S->tickets.end() && c->second.dict == S->last_dict) {
-                    pick = k;
-                    break;
-                }
-            }
-        }
-        auto it = S->tickets.find(S->pending[pick]);
+        auto it = S->tickets.find(S->pending.front());
         if (it == S->tickets.end()) {
-            S->pending.erase(S->pending.begin() + pick);
+            S->pending.pop_front();
             continue;
         }
         if (!server_publish(S, it->first, it->second, it->second.y.data())) break;
-        S->last_dict = it->second.dict;
-        S->front_bypassed = pick ? S->front_bypassed + 1 : 0;
-        S->pending.erase(S->pending.begin() + pick);
+        S->pending.pop_front();
     }
     // a kernel that went idle exits; relaunch it while published work is outstanding
     if (S->published > S->completed) {
