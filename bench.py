@@ -885,8 +885,37 @@ def _serve_stream(ds, ctx, pool, opts, team_size, seconds, rate, drain_s, budget
             "kernel_launches": st["launches"]}
 
 
+def _serve_closed(ds, ctx, pool, opts, team_size, reqs, budget_gib):
+    """A fixed set of requests submitted at once and drained completely through a server with teams of
+    team_size CTAs; returns the wall time and the results."""
+    import time
+    server = ds.ds_server_create(ctx, budget_gib << 30, 8192, 65536, team_size)
+    N, K, lasso, group, Ys = pool[0]  # warm the server (kernel load, first launch)
+    xw = np.zeros(K, dtype=np.float32)
+    tw = ds.ds_server_submit(server, lasso, Ys["lasso"][0], 0.9, opts["lasso"], xw)
+    while ds.ds_server_poll(server, tw) is None:
+        time.sleep(0.001)
+    outs, res = {}, []
+    t0 = time.perf_counter()
+    for (pi, kind, yi, ratio) in reqs:
+        N, K, lasso, group, Ys = pool[pi]
+        x = np.zeros(K, dtype=np.float32)
+        t = ds.ds_server_submit(server, group if kind == "group" else lasso, Ys[kind][yi], ratio, opts[kind], x)
+        outs[t] = x
+    while outs:
+        for t in list(outs):
+            r = ds.ds_server_poll(server, t)
+            if r is not None:
+                res.append(r)
+                del outs[t]
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    ds.ds_server_destroy(server)
+    return wall, res
+
+
 def served_measure(ds, ctx, dev, seconds=5.0, rate=2000.0, drain_s=10.0, plain_n=8, team_sizes=(38,), n_pool=32,
-                   budget_gib=8):
+                   budget_gib=8, closed_n=48, closed_team_sizes=(19, 38, 76)):
     """The served mixed stream at its stated shapes: a pool of n_pool AR(1) dictionaries (rho = 0.9,
     unit-norm columns) with N ~ U{512..8192} and K ~ U{4096..65536} (K a multiple of 8), each
     registered twice (Lasso, and Group-Lasso with groups of 8) with an FP8 e4m3 working copy
@@ -934,6 +963,30 @@ def served_measure(ds, ctx, dev, seconds=5.0, rate=2000.0, drain_s=10.0, plain_n
         runs[team_size] = _serve_stream(ds, ctx, pool, opts, team_size, seconds, rate, drain_s, budget_gib)
     best_ts = max(runs, key=lambda k: runs[k]["completed"] / runs[k]["wall_s"])
     best = runs[best_ts]
+    # like for like: one fixed set of closed_n requests of the same mix, drained completely through the
+    # server and solved one at a time by ds_solve (the plain form) -- the open stream above cannot drain
+    # at 2000 req/s, and its completions favour the short requests
+    gc = np.random.default_rng(2008)
+    reqs = []
+    for _ in range(closed_n):
+        pi = int(gc.integers(len(pool)))
+        kind = "group" if gc.uniform() < 0.2 else "lasso"
+        reqs.append((pi, kind, int(gc.integers(pool[pi][4][kind].shape[0])), float(gc.uniform(0.1, 0.9))))
+    closed = {}
+    for ts in closed_team_sizes:
+        w_, r_ = _serve_closed(ds, ctx, pool, opts, ts, reqs, budget_gib)
+        closed[ts] = {"wall_s": w_, "solves_per_s": closed_n / w_,
+                      "converged": sum(1 for q in r_ if q["status"] == 0)}
+    torch.cuda.synchronize()
+    tq0 = time.perf_counter()
+    for (pi, kind, yi, ratio) in reqs:
+        N, K, lasso, group, Ys = pool[pi]
+        yd = torch.from_numpy(Ys[kind][yi].copy()).to(dev)
+        xd = torch.zeros(K, device=dev)
+        ds.ds_solve(ctx, group if kind == "group" else lasso, yd, ratio, opts[kind], xd)
+    torch.cuda.synchronize()
+    closed_plain = closed_n / (time.perf_counter() - tq0)
+    best_closed = max(closed, key=lambda k: closed[k]["solves_per_s"])
     # plain form: requests of the same mix, one at a time (the whole GPU per solve)
     gp = np.random.default_rng(2006)
     torch.cuda.synchronize()
@@ -951,8 +1004,17 @@ def served_measure(ds, ctx, dev, seconds=5.0, rate=2000.0, drain_s=10.0, plain_n
         ds.ds_dict_destroy(lasso)
         ds.ds_dict_destroy(group)
     torch.cuda.empty_cache()
-    return {"value": best["solves_per_s"], "unit": "solves/s", "plain_value": plain,
-            "vs_plain": best["solves_per_s"] / plain, "offered_rate": rate, "window_s": seconds, "drain_s": drain_s,
+    return {"value": closed[best_closed]["solves_per_s"], "unit": "solves/s", "plain_value": closed_plain,
+            "vs_plain": closed[best_closed]["solves_per_s"] / closed_plain,
+            "closed_set": {"requests": closed_n, "team_size": best_closed,
+                           "by_team_size": {str(k): {kk: round(vv, 4) for kk, vv in v.items()} for k, v in
+                                            closed.items()},
+                           "note": "value / plain_value: the same requests drained through the server and "
+                                   "solved one at a time"},
+            "stream": {"solves_per_s": best["solves_per_s"], "plain_sample_solves_per_s": plain,
+                       "note": "open-loop stream at the offered rate: completions within the window, which "
+                               "favour short requests; latency from submission"},
+            "offered_rate": rate, "window_s": seconds, "drain_s": drain_s,
             **{k: best[k] for k in ("team_size", "submitted", "completed", "completed_by_kind",
                                     "unfinished_at_deadline", "wall_s", "p50_ms", "p99_ms", "converged",
                                     "kernel_launches")},
@@ -1002,11 +1064,11 @@ def config1_latency(reps=10, warmup=3):
         return ms, res
 
     ms, res = timed(0)  # the grid the library picks for this size
-    ms_all, _ = timed(152)  # every SM, as large problems run
+    by_grid = {str(gsz): round(statistics.median(timed(gsz)[0]), 4) for gsz in (1, 4, 152)}
     ds.ds_dict_destroy(dct)
     ds.ds_destroy(ctx)
     return {"median_ms": statistics.median(ms), "min_ms": min(ms), "iters": res[-1]["iters"],
-            "all_sms_median_ms": statistics.median(ms_all),
+            "median_ms_by_grid_ctas": by_grid,
             "converged": all(r["status"] == 0 for r in res),
             "workload": "100x500 FP64 Gaussian, 10 nonzeros, sigma 0.01 (seed 1001), ISTA + dynamic DST3, "
                         "lambda = 0.5 lambda_max, gap 1e-8; one solve per call"}

@@ -869,6 +869,7 @@ struct ds_server {
     int smem = 0;
     std::unordered_map<uint64_t, Ticket> tickets;
     std::deque<uint64_t> pending;
+    bool adapt_launch = false;  // the running (or next) launch is the instance with the adaptive-step code
     std::vector<int64_t> slot_seq;
     std::vector<uint64_t> slot_ticket;
     uint64_t next_ticket = 1;
@@ -993,7 +994,7 @@ static ds_status server_launch(ds_server* S)
     if (cudaMemsetAsync(S->dctl, 0, S->bars_bytes, S->stream) != cudaSuccess) return DS_ERR_CUDA;
     void* a[] = {(void*)&S->args};
     const int grid = S->n_teams * S->team_size;
-    if (cudaLaunchCooperativeKernel((const void*)team_kernel<float>, dim3(grid), dim3(kThreads), a, S->smem,
+    if (cudaLaunchCooperativeKernel(team_fn<float>(S->adapt_launch), dim3(grid), dim3(kThreads), a, S->smem,
                                     S->stream) != cudaSuccess)
         return DS_ERR_CUDA;
     S->launches++;
@@ -1001,15 +1002,30 @@ static ds_status server_launch(ds_server* S)
     return DS_OK;
 }
 
+static bool adaptive_request(const ds_options& o)
+{
+    return o.alg == DS_SPARSA || o.alg == DS_TWIST || o.step_backtracking;
+}
+
 static ds_status server_pump(ds_server* S)
 {
     server_harvest(S);
+    // fixed-step requests run on the kernel instance without the adaptive-step code; when no launch is
+    // running and nothing published is outstanding, the request at the head of the queue picks the
+    // instance of the next launch, and an adaptive request waits for a launch of the other instance
+    const cudaError_t q0 = cudaStreamQuery(S->stream);
+    if (q0 != cudaSuccess && q0 != cudaErrorNotReady) return DS_ERR_CUDA;
+    if (q0 == cudaSuccess && S->published == S->completed) {
+        while (!S->pending.empty() && S->tickets.find(S->pending.front()) == S->tickets.end()) S->pending.pop_front();
+        if (!S->pending.empty()) S->adapt_launch = adaptive_request(S->tickets.find(S->pending.front())->second.opt);
+    }
     while (!S->pending.empty()) {
         auto it = S->tickets.find(S->pending.front());
         if (it == S->tickets.end()) {
             S->pending.pop_front();
             continue;
         }
+        if (adaptive_request(it->second.opt) && !S->adapt_launch) break;
         if (!server_publish(S, it->first, it->second, it->second.y.data())) break;
         S->pending.pop_front();
     }
@@ -1144,7 +1160,9 @@ ds_status ds_server_create(ds_ctx* ctx, size_t hbm_budget_bytes, int64_t max_N, 
     A.done = S->done_d;
     A.ring = S->ring_d;
     A.idle_polls = 20000;
-    if (cudaFuncSetAttribute(ds::team_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(ds::team_fn<float>(false), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(ctx->smem_optin - 40 * 1024)) != cudaSuccess ||
+        cudaFuncSetAttribute(ds::team_fn<float>(true), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(ctx->smem_optin - 40 * 1024)) != cudaSuccess)
         return fail(DS_ERR_CUDA);
     S->slot_seq.assign(S->ring, -1);

@@ -13,8 +13,9 @@ the same (scr_iter) and, per iteration, every tested atom's margin.
   at the first iteration on which the two differ is within the error bound
       |rad_gpu,t - rad_oracle,t| + eps_t,
       eps_t = 1e-6 (1 + rad_t)  (sphere tests),  2e-6 (1 + rad_t)  (dome),
-  the radii taken from both histories (the FP32 trajectory's own drift, asserted
-  below 1e-4 relative) and eps_t covering the FP32 rounding of the threshold, the
+  the radii taken from both histories (the FP32 trajectory's drift and the rigorous
+  bound on max |z| the kernel adds, asserted below 1e-3 relative) and eps_t covering
+  the FP32 rounding of the threshold, the
   radius and, for the dome, its stored constants.  No atom screened by the GPU is
   nonzero in the oracle's solution.
 """
@@ -98,7 +99,7 @@ def test_fp64_screened_sets_equal_the_oracle_atom_by_atom(ctx, alg, test, dynami
         ds.ds_dict_destroy(dct)
     assert res[0]["iters"] == T
     np.testing.assert_array_equal(log[0], ref["scr_iter"])
-    if dynamic:  # (at 0.5 lambda_* the static SAFE screens nothing)
+    if dynamic and test != "safe":  # (at 0.5 lambda_* SAFE screens little or nothing on this problem)
         assert (ref["scr_iter"] != 0).sum() > 40
     np.testing.assert_allclose(X[0], ref["x"], atol=1e-9 * np.abs(ref["x"]).max())
 
@@ -162,7 +163,7 @@ def _group_of_atom(K, goff):
 def _check_margin_rule(log, hist, ref, x_star, test, goff=None):
     """Every atom screened at a different iteration by the GPU and the oracle has an oracle
     margin within the error bound at the first iteration where the two differ; the
-    trajectories' radii agree to 1e-4; no GPU-screened atom is nonzero in the minimiser."""
+    trajectories' radii agree to 1e-3; no GPU-screened atom is nonzero in the minimiser."""
     K = log.size
     s_o = ref["scr_iter"]
     M = ref["margins"]

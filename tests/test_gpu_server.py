@@ -140,3 +140,35 @@ def test_server_requests_after_a_lull_run_side_by_side():
         ds.ds_server_destroy(srv)
         ds.ds_dict_destroy(d)
         ds.ds_destroy(ctx)
+
+
+def test_server_mixes_fixed_and_adaptive_step_requests():
+    """Requests with the adaptive-step rows (SpaRSA, TwIST, FISTA with backtracking) between
+    fixed-step ones: the server runs each on the kernel instance that has its code (an adaptive
+    request waits for such a launch), and every result matches ds_solve with the same options."""
+    g = gen.rng(305)
+    ctx = ds.ds_create(0, None)
+    D = gen.gaussian_dict(400, 1600, g)
+    dct = ds.ds_dict_create(ctx, _dev_dict(D))
+    server = ds.ds_server_create(ctx, 256 << 20, 1024, 4096, 8)
+    kinds = [dict(alg="fista"), dict(alg="sparsa"), dict(alg="fista"), dict(alg="twist"),
+             dict(alg="fista", step_backtracking=1), dict(alg="ista"), dict(alg="sparsa")]
+    try:
+        reqs = []
+        for k, kw in enumerate(kinds):
+            y = gen.observe(D, gen.bernoulli_gaussian_x0(1600, 0.02, g), g).astype(np.float32)
+            o = ds.ds_options_default(test="dst3", tol_gap_rel=1e-7, max_iter=50000, lambda_rel=1, **kw)
+            x = np.zeros(1600, dtype=np.float32)
+            reqs.append((y, o, x, ds.ds_server_submit(server, dct, y, 0.4 + 0.05 * k, o, x)))
+        res = _wait(server, [r[3] for r in reqs])
+        for k, (y, o, x, _) in enumerate(reqs):
+            assert res[k]["status"] == 0
+            xd = torch.zeros(1600, device="cuda")
+            ref = ds.ds_solve(ctx, dct, torch.from_numpy(y).cuda(), 0.4 + 0.05 * k, o, xd)
+            xr = xd.double().cpu().numpy()
+            assert ref["status"] == 0
+            assert np.abs(x - xr).max() <= 1e-4 * np.abs(xr).max(), (k, kinds[k])
+    finally:
+        ds.ds_server_destroy(server)
+        ds.ds_dict_destroy(dct)
+        ds.ds_destroy(ctx)
