@@ -99,8 +99,8 @@ typedef struct {
                               (1 + sqrt(xi_1)) (<= 0: 1e-4) */
     int gap_every;         /* the stopping rule (duality gap) is evaluated every gap_every iterations
                               (<= 1: every iteration) */
-    int team_size;         /* CTAs that run one solve: ds_solve / ds_solve_path (0: all SMs for large problems,
-                              fewer for small ones) and the multi-RHS blocks of batches (0: automatic) */
+    int team_size;         /* CTAs that run one solve: ds_solve / ds_solve_path (0: one per SM) and the
+                              multi-RHS blocks of batches (0: automatic) */
 } ds_options;
 
 typedef struct {

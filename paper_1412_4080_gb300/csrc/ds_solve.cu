@@ -72,15 +72,9 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
     Geometry g;
     ds_status st = geometry<T>(dd, env.num_sms, env.smem_optin, &g);
     if (st != DS_OK) return st;
-    {
-        // grid: one CTA per SM for large problems; a small one takes fewer CTAs (about 16K FP64 or 64K FP32
-        // dictionary entries each, at least 8), so that the two grid barriers of every iteration wait for
-        // fewer arrivals; opt->team_size > 0 sets the count
-        const double per = sizeof(T) == 8 ? 16384.0 : 65536.0;
-        int want = std::max(8, (int)std::ceil((double)g.npad * (double)dd.K / per));
-        if (opt && opt->team_size > 0) want = opt->team_size;
-        g.G = std::max(1, std::min(g.G, want));
-    }
+    // grid: one CTA per SM (a small problem is not faster on fewer: its iteration is bound by serial
+    // steps and barrier waits, not by the number of arrivals); opt->team_size > 0 sets the count
+    if (opt && opt->team_size > 0) g.G = std::max(1, std::min(g.G, opt->team_size));
     Ws<T> w;
     double* lam_dev;
     DevResult* res_dev;
