@@ -40,12 +40,21 @@ WORKLOAD = ("Lasso FISTA + dynamic SAFE/DST3/Dome, FP32, D 2000x10000 Gaussian u
             "precompute + 15 solves")
 
 
+def _strip_comments(src):
+    """C++ source without its comments and blank lines (a comment edit leaves the kernel as it was)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(ln.rstrip() for ln in src.splitlines() if ln.strip())
+
+
 def solve_kernel_source_hash():
-    """sha256 (16 hex digits) of the solve kernel's sources, recorded beside each ncu capture."""
+    """sha256 (16 hex digits) of the solve kernel's sources without comments, recorded beside
+    each ncu capture."""
     import hashlib
-    src = b"".join(open(os.path.join(ROOT, "paper_1412_4080_gb300", "csrc", f), "rb").read()
-                   for f in ("ds_solve.cu", "ds_solve_body.cuh", "ds_common.cuh"))
-    return hashlib.sha256(src).hexdigest()[:16]
+    src = "".join(_strip_comments(open(os.path.join(ROOT, "paper_1412_4080_gb300", "csrc", f)).read())
+                  for f in ("ds_solve.cu", "ds_solve_body.cuh", "ds_common.cuh"))
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
 def _kernel_traffic(name="solve_kernel_config2.md", key="dram_bytes_per_launch:"):

@@ -578,11 +578,21 @@ __device__ __noinline__ void mr_synth_item(MrhsShared& S, const MrhsP& P, int r,
     const int N = P.N, K = P.K, ld = P.ld, npad = P.npad;
     int* dir = S.dir[0];
     if (warp == 0) {
-        // where each CTA's segment of the list starts (exclusive prefix of the segment lengths)
+        // where each CTA's segment of the list starts (exclusive prefix of the segment lengths);
+        // the segment lengths are loaded together first so their L2 round trips overlap
+        int cv[kMaxG / 32];
+#pragma unroll
+        for (int q = 0; q < kMaxG / 32; q++) {
+            const int bb = 32 * q + lane;
+            cv[q] = bb < G ? __ldcg(W.c_nz + bb * kMR + r) : 0;
+        }
         int run = 0;
-        for (int b0 = 0; b0 < G; b0 += 32) {
+#pragma unroll
+        for (int q = 0; q < kMaxG / 32; q++) {
+            const int b0 = 32 * q;
+            if (b0 >= G) break;
             const int bb = b0 + lane;
-            const int c = bb < G ? __ldcg(W.c_nz + bb * kMR + r) : 0;
+            const int c = cv[q];
             int x = c;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {

@@ -2,25 +2,24 @@
 // ISTA/FISTA solve (Algorithm 3 with the Table 1 updates) on one GB300.
 //
 // One CTA per SM stays resident for the whole solve.  Every iteration t is
-// three grid phases separated by bounded grid barriers:
+// two grid phases separated by bounded grid barriers:
 //
-//   (A) scatter + synthesis   compact the active set kept by the previous
-//                             test (Algorithm 3, screening of D and X) and
-//                             form theta_t = D ubar_{t-1} - y and D xbar_{t-1}
-//                             over the nonzeros only (row tiles), with FP64
-//                             partials of theta^T y, ||theta||^2 and
-//                             ||D xbar - y||^2;
-//   (B) correlation + prox    stop test on the gap of iteration t-1, then
-//                             z = D_A^T theta_t over the active atoms (the
-//                             dominant HBM stream, theta staged in shared
-//                             memory, 16-byte vector loads, warp-shuffle dots)
-//                             fused with the proximal step (soft threshold,
-//                             eq. softTh / group soft threshold, eq. gr_softTh)
-//                             and the max |z| (or max ||z_g||/w_g) partials;
-//   (C) screening + momentum  dual scaling (Lemma 8), radius of the chosen
-//                             test (Lemmas 2-7), the test itself against the
-//                             thresholds precomputed from D^T c, the FISTA
-//                             extrapolation, and per-CTA nonzero lists.
+//   (A) test + synthesis      the Lemma 8 dual scaling and the radius of the
+//                             chosen test (Lemmas 2-7) from the partials of
+//                             t-1, the test itself on each CTA's slice of the
+//                             atoms (Algorithm 3), and theta_t = D ubar_{t-1} - y
+//                             and D xbar_{t-1} over the nonzeros only (row
+//                             tiles), with the partials of theta^T y,
+//                             ||theta||^2 and ||D xbar - y||^2;
+//   (B) correlation + prox    the gap of iteration t-1 and the stopping rule
+//                             (an adaptive step's acceptance test, and its redo,
+//                             first), the compaction of the atoms the test kept,
+//                             z = D_A^T theta_t over them (the dominant stream,
+//                             theta staged in shared memory, 16-byte vector
+//                             loads, warp-shuffle dots), the proximal step (soft
+//                             threshold or group soft threshold), the FISTA
+//                             extrapolation, the max |z| (or max ||z_g|| / w_g)
+//                             partials and the per-CTA nonzero lists.
 //
 // Reductions are per-CTA partials summed in a fixed order by every CTA, so all
 // CTAs take identical decisions and the results do not depend on timing.
