@@ -30,12 +30,13 @@
 namespace ds {
 
 // ADAPT: the kernel also runs the adaptive-step rows (backtracking, SpaRSA, TwIST); fixed-step solves
-// launch the instance without that code.
-template <typename T, bool ADAPT>
+// launch the instance without that code.  GRP: the instance for Group-Lasso (1) or Lasso (0)
+// dictionaries, so that neither carries the other's code and register pressure.
+template <typename T, bool ADAPT, int GRP>
 __global__ void __launch_bounds__(kThreads, 1) solve_kernel(const SolveP<T> P)
 {
     unsigned int gen = 0;  // running barrier target, used by thread 0 only
-    if (!solve_body<T, ADAPT>(P, blockIdx.x, gridDim.x, P.ws.bar, gen) && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (!solve_body<T, ADAPT, GRP>(P, blockIdx.x, gridDim.x, P.ws.bar, gen) && blockIdx.x == 0 && threadIdx.x == 0) {
         const int n = P.n_lambda > 0 ? P.n_lambda : 1;
         for (int j = 0; j < n; j++) P.res[j].status = kDevTimeout;
     }
@@ -117,13 +118,15 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return DS_ERR_CUDA;
     const bool adapt = P.step_mode != 0;
-    const void* kfn = adapt ? (const void*)solve_kernel<T, true> : (const void*)solve_kernel<T, false>;
-    static bool attr_set[2][64] = {};
-    if (dev < 64 && !attr_set[adapt][dev]) {
+    const int grp = P.is_group ? 1 : 0;
+    const void* kfn = adapt ? (grp ? (const void*)solve_kernel<T, true, 1> : (const void*)solve_kernel<T, true, 0>)
+                            : (grp ? (const void*)solve_kernel<T, false, 1> : (const void*)solve_kernel<T, false, 0>);
+    static bool attr_set[2][2][64] = {};
+    if (dev < 64 && !attr_set[adapt][grp][dev]) {
         if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(env.smem_optin - 40 * 1024)) != cudaSuccess)
             return DS_ERR_CUDA;
-        attr_set[adapt][dev] = true;
+        attr_set[adapt][grp][dev] = true;
     }
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kfn, kThreads, g.smem) != cudaSuccess)

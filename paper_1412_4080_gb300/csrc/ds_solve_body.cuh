@@ -547,11 +547,12 @@ struct SolveK {
 // `bar`; `gen` is the calling thread's running barrier target.
 // ADAPT = false compiles the fixed-step rows only (ISTA, FISTA, Chambolle-Pock without backtracking):
 // the adaptive-step code below is then absent from the kernel, and so is its register pressure.
-template <typename T, bool ADAPT = true>
+template <typename T, bool ADAPT = true, int GRP = -1>
 __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, const int G, GridBarrier* bar,
                                            unsigned int& gen)
 {
     const int SM = ADAPT ? P.step_mode : 0;  // adaptive step rule of this solve (0: fixed step)
+    const bool is_grp = GRP < 0 ? P.is_group != 0 : GRP == 1;  // Group-Lasso (GRP: fixed at compile time)
     using V = typename Vec4<T>::type;
     using X = typename IterT<T>::type;
     using Acc = typename Dot2<T>::type;
@@ -574,7 +575,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     __shared__ ScalarState S_;
     __shared__ SolveK<T> C_;
     // per-thread prefetch slots (cp.async): two ints, a float and two iterate values
-    __shared__ int s_pf_i0[kThreads], s_pf_i1[kThreads];
+    __shared__ int s_pf_i0[kThreads], s_pf_i1[kThreads], s_pf_i2[kThreads];
     __shared__ float s_pf_f0[kThreads];
     __shared__ __align__(8) X s_pf_u[kThreads];
     __shared__ __align__(8) X s_pf_x[kThreads];
@@ -678,7 +679,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         int arg = 0x7fffffff;
         for (int g = b * kThreads + tid; g < nG; g += G * kThreads) {
             double s;
-            if (!P.is_group) {
+            if (!is_grp) {
                 s = fabs(__ldcg(W.b + g));
             } else {
                 double q = 0.0;
@@ -743,8 +744,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     if (tid == 0) { C_.nn = 0.0; C_.nty = 0.0; C_.wstar2 = 1.0; }
     if (need_n && lstar > 0.0) {
         // ---------------- n = D_{g*} D_{g*}^T y / lambda_*  (Lemma 6; Lasso: n = d_*)
-        const int c0 = P.is_group ? P.goff[star] : star;
-        const int c1 = P.is_group ? P.goff[star + 1] : star + 1;
+        const int c0 = is_grp ? P.goff[star] : star;
+        const int c1 = is_grp ? P.goff[star + 1] : star + 1;
         double nq = 0.0;
         for (int r = b * kThreads + tid; r < N; r += G * kThreads) {
             double s = 0.0;
@@ -789,7 +790,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 q += v * v;
             }
             C_.nty = q / lstar;  // n^T y = ||D_{g*}^T y||^2 / lambda_*
-            if (P.is_group) C_.wstar2 = P.w[star] * P.w[star];
+            if (is_grp) C_.wstar2 = P.w[star] * P.w[star];
         }
         // ---------------- tv = D^T n (compensated)
         for (int i = gwarp; i < K; i += total_warps) {
@@ -828,7 +829,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
     // boundaries and balanced in atoms; s_alo_s[k] = its first atom (start of its nonzero list)
     auto slice_start = [&](int k) -> int {
         if (k >= G) return nG;
-        if (!P.is_group) return (int)((long long)k * nG / G);
+        if (!is_grp) return (int)((long long)k * nG / G);
         const long long target = (long long)k * K / G;
         int lo = 0, hi = nG;  // first g with goff[g] >= target
         while (lo < hi) {
@@ -839,11 +840,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         return lo;
     };
     const int g_lo = slice_start(b), g_hi = slice_start(b + 1);
-    const int a_lo0 = P.is_group ? (g_lo < nG ? P.goff[g_lo] : K) : g_lo;
-    const int a_hi0 = P.is_group ? (g_hi < nG ? P.goff[g_hi] : K) : g_hi;
+    const int a_lo0 = is_grp ? (g_lo < nG ? P.goff[g_lo] : K) : g_lo;
+    const int a_hi0 = is_grp ? (g_hi < nG ? P.goff[g_hi] : K) : g_hi;
     for (int k = tid; k < G; k += kThreads) {
         const int gk = slice_start(k);
-        s_alo_s[k] = P.is_group ? (gk < nG ? P.goff[gk] : K) : gk;
+        s_alo_s[k] = is_grp ? (gk < nG ? P.goff[gk] : K) : gk;
     }
     __syncthreads();
 
@@ -860,7 +861,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             // DST3 / DGST3 centre c = y/lam - coef n, offset delta = ||y/lam - c|| (Lemmas 3, 6)
             C_.coef = need_n && nn > 0.0 ? (nty / lm - wstar2) / nn : 0.0;
             C_.delta = need_n && nn > 0.0 ? fabs(nty / lm - wstar2) / sqrt(nn) : 0.0;
-            C_.nstar = P.is_group ? 1.0 : colnorm[star];
+            C_.nstar = is_grp ? 1.0 : colnorm[star];
             C_.psi_dome = C_.psi / C_.nstar;
             C_.invL = (T)(1.0 / P.L);
             C_.thrL = lm / P.L;
@@ -935,8 +936,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 int kept = 0, lo_a = 0, hi_a = 0, cnt = 0;
                 float thf = 0.f;
                 if (valid) {
-                    lo_a = P.is_group ? P.goff[g] : g;
-                    hi_a = P.is_group ? P.goff[g + 1] : g + 1;
+                    lo_a = is_grp ? P.goff[g] : g;
+                    hi_a = is_grp ? P.goff[g + 1] : g + 1;
                     // threshold of the sphere tests: (w_g - ||(D^T c)_g||) / ||D_g||  (Lemma 7)
                     double th = 0.0;
                     if (sphere) {
@@ -945,8 +946,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             double dtc = __ldcg(W.b + i) / lam - ((P.test == 2 || P.test == 5) ? coef * __ldcg(W.tv + i) : 0.0);
                             q += dtc * dtc;
                         }
-                        double wg = P.is_group ? P.w[g] : 1.0;
-                        double sg = P.is_group ? P.spec[g] : colnorm[g];
+                        double wg = is_grp ? P.w[g] : 1.0;
+                        double sg = is_grp ? P.spec[g] : colnorm[g];
                         th = (wg - sqrt(q)) / sg;
                         W.thr[g] = th;
                         thf = __double2float_rd(th - P.eps_test);
@@ -985,7 +986,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 if (kept) {
                     const int ng = n_own + (pre >> 20), na = na_own + (pre & 0xfffff);
                     W.act[0][g_lo + ng] = g;
-                    if (P.is_group) W.aoff[0][g_lo + ng] = a_lo0 + na;
+                    if (is_grp) W.aoff[0][g_lo + ng] = a_lo0 + na;
                     if (f32_sphere) W.thrc[0][g_lo + ng] = thf;
                     int e = a_lo0 + nzc + pc;
                     for (int i = lo_a; i < hi_a; i++) {
@@ -1072,13 +1073,19 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                 }
-                // the own slice's test inputs and x_{t-1} (Lasso: one group per slot), for the owner test
-                const bool opf = !P.is_group && tid < n_own;
-                if (!P.is_group && ps < n_own) {
+                // the own slice's test inputs (one group per slot; Group-Lasso also the group and its first
+                // atom) and x_{t-1} (one atom per slot), for the owner test
+                const bool opf = tid < n_own;
+                if (ps < n_own) {
                     if (f32_sphere) pf4(&s_pf_i0[ps], W.thrc[cur] + g_lo + ps);
                     else pf4(&s_pf_i0[ps], W.act[cur] + g_lo + ps);
-                    pf8(&s_pf_x[ps], xbuf(iO) + a_lo0 + ps);
+                    if (is_grp) {
+                        pf4(&s_pf_i1[ps], W.act[cur] + g_lo + ps);
+                        pf4(&s_pf_i2[ps], W.aoff[cur] + g_lo + ps);
+                    }
                 }
+                const int nxs = min(na_own, kThreads);  // atoms of the slice whose x_{t-1} is staged
+                if (ps < nxs) pf8(&s_pf_x[ps], xbuf(iO) + a_lo0 + ps);
                 if (t > 1 && warp <= 1) {
                     // warps 0 and 1 reduce the same per-CTA maxima of |z_{t-1}| in the same order
                     T mv[kMaxG / 32];
@@ -1305,14 +1312,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         if (kill && C_.slog) {
                             // screening log: the test of iteration t-1 screened this group's atoms
                             const int gs = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
-                            const int i0 = P.is_group ? P.goff[gs] : gs, i1 = P.is_group ? P.goff[gs + 1] : gs + 1;
+                            const int i0 = is_grp ? P.goff[gs] : gs, i1 = is_grp ? P.goff[gs + 1] : gs + 1;
                             for (int i = i0; i < i1; i++) C_.slog[i] = t - 1;
                         }
                         if (want_sq && t > 1) {
                             // backtracking / SpaRSA: ||xbar_{t-1} - base||^2 over the atoms of the step
                             // (the screened ones contribute their base point: xbar is 0 there)
                             int lo_a = a_lo0 + k, sz = 1;
-                            if (P.is_group) {
+                            if (is_grp) {
                                 const int gid = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
                                 lo_a = __ldcg(W.aoff[cur] + g_lo + k);
                                 sz = P.goff[gid + 1] - P.goff[gid];
@@ -1323,18 +1330,19 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                         }
                         if (!kill) {
-                            if (!P.is_group) {
+                            if (!is_grp) {
                                 const X xv = first ? s_pf_x[tid] : ldcg_x(xbuf(iO) + a_lo0 + k);
                                 acc_abs(l1, xv);
                                 nzx += it_nz(xv);
                                 ka += 1;
                             } else {
-                                const int gid = f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td;
-                                const int lo_a = __ldcg(W.aoff[cur] + g_lo + k);
+                                const int gid = first ? s_pf_i1[tid] : (f32_sphere ? __ldcg(W.act[cur] + g_lo + k) : td);
+                                const int lo_a = first ? s_pf_i2[tid] : __ldcg(W.aoff[cur] + g_lo + k);
                                 const int sz = P.goff[gid + 1] - P.goff[gid];
                                 Acc gq;
                                 for (int q = 0; q < sz; q++) {
-                                    const X xv = ldcg_x(xbuf(iO) + lo_a + q);
+                                    const int j = lo_a - a_lo0 + q;  // the atom's place in the slice
+                                    const X xv = j < nxs ? s_pf_x[j] : ldcg_x(xbuf(iO) + lo_a + q);
                                     acc_sq(gq, xv);
                                     nzx += it_nz(xv);
                                 }
@@ -1388,7 +1396,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
             {
                 // Lasso: the first round's keep flags, columns, thresholds and iterates, fetched while
                 // warps 0 and 1 reduce the partials
-                const int n0 = P.is_group ? 0 : min(n_own, P.RA);
+                const int n0 = is_grp ? 0 : min(n_own, P.RA);
                 {
                     const int ps = (tid + kThreads - 64) % kThreads;  // issued by warps 2.. first
                     if (ps < n0) {
@@ -1635,11 +1643,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         int cnt = 0, gid = 0, lo_a = 0, sz = 0, td = 0;
                         if (k < n_own && __ldcg(W.keep + g_lo + k)) {
                             gid = __ldcg(W.act[cur] + g_lo + k);
-                            lo_a = P.is_group ? __ldcg(W.aoff[cur] + g_lo + k) : a_lo0 + k;
-                            sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
+                            lo_a = is_grp ? __ldcg(W.aoff[cur] + g_lo + k) : a_lo0 + k;
+                            sz = is_grp ? P.goff[gid + 1] - P.goff[gid] : 1;
                             td = f32_sphere ? __float_as_int(__ldcg(W.thrc[cur] + g_lo + k)) : gid;
                             X f = it_from(T(1), (X*)nullptr);
-                            if (P.is_group) {
+                            if (is_grp) {
                                 // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
                                 Acc vq;
                                 for (int q = 0; q < sz; q++)
@@ -1649,7 +1657,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                             for (int q = 0; q < sz; q++) {
                                 const X v = it_grad_step(ldcg_x(W.bS + lo_a + q), __ldcg(W.zS + lo_a + q), invL);
-                                const X xv = P.is_group ? it_scale(v, f) : it_soft(v, thrX);
+                                const X xv = is_grp ? it_scale(v, f) : it_soft(v, thrX);
                                 const X pq = ldcg_x(W.pS + lo_a + q);
                                 const X uv = SM == 3 ? pq : (fista ? it_momentum(xv, pq, btX) : xv);
                                 xR[lo_a + q] = xv;
@@ -1660,7 +1668,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         int totc;
                         const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
                         if (cnt) {
-                            const int c0 = P.is_group ? P.goff[gid] : gid;
+                            const int c0 = is_grp ? P.goff[gid] : gid;
                             int e = a_lo0 + nz_base + pc;
                             for (int q = 0; q < sz; q++) {
                                 const X xv = xR[lo_a + q];
@@ -1709,8 +1717,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 const X* const xO = xbuf(iO);
                 const X* const uO = ubuf(iO);
                 int* const opos_s = cols_s + P.RA;
+                // Group-Lasso: the round's old iterates u and x, staged in shared memory
+                X* const rs_u = reinterpret_cast<X*>((reinterpret_cast<uintptr_t>(opos_s + P.RA) + 7) & ~uintptr_t(7));
+                X* const rs_x = rs_u + P.RA;
                 // Lasso slice in which the last test screened nothing: positions stay, no list copy
-                const bool same = !P.is_group && s_si[12] == n_own;
+                const bool same = !is_grp && s_si[12] == n_own;
                 T mloc = T(0);
                 int kg_run = 0, ka_run = 0, nz_base = 0;
                 int k0 = 0;
@@ -1718,7 +1729,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     const int k = k0 + tid;  // one old live group per thread
                     int sz = 0, gid = 0, kp = 0, lo_o = 0;
                     float thf = 0.f;
-                    if (!P.is_group) {
+                    if (!is_grp) {
                         if (k < n_own && tid < P.RA) {
                             sz = 1;
                             const bool first = k0 == 0;
@@ -1735,7 +1746,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         sz = P.goff[gid + 1] - P.goff[gid];
                     }
                     int k1;
-                    if (!P.is_group) {
+                    if (!is_grp) {
                         k1 = min(n_own, k0 + P.RA);
                     } else {
                         // whole groups while the atoms fit in RA
@@ -1763,9 +1774,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         if (kept) {
                             const int ng = kg_run + (pre >> 16);
                             W.act[nxt][g_lo + ng] = gid;
-                            if (P.is_group) W.aoff[nxt][g_lo + ng] = a_lo0 + ka_run + r_a;
+                            if (is_grp) W.aoff[nxt][g_lo + ng] = a_lo0 + ka_run + r_a;
                             if (f32_sphere) W.thrc[nxt][g_lo + ng] = thf;
-                            const int c0 = P.is_group ? P.goff[gid] : gid;
+                            const int c0 = is_grp ? P.goff[gid] : gid;
                             for (int q = 0; q < sz; q++) {
                                 cols_s[r_a + q] = c0 + q;
                                 opos_s[r_a + q] = lo_o + q;
@@ -1773,6 +1784,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                         }
                     }
                     __syncthreads();
+                    if (is_grp) {
+                        // the round's old iterates, fetched into shared memory while the correlation runs: the
+                        // owner of a group then reads its atoms there instead of one L2 trip after another
+                        for (int r = tid; r < natoms; r += kThreads) {
+                            pf8(&rs_u[r], uO + opos_s[r]);
+                            pf8(&rs_x[r], xO + opos_s[r]);
+                        }
+                    }
                     // z = D_A^T theta_t: items (atom, row chunk)
                     const int nchunk = P.nchunk;
                     if constexpr (sizeof(T) == 4) {
@@ -1816,13 +1835,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                         }
                     }
+                    if (is_grp) pf_wait();  // this thread's staged iterates; the barrier publishes them
                     __syncthreads();
                     // proximal step (Table 1), x_t = prox_{lambda/L Omega}(u_{t-1} - z / L), and the FISTA
                     // extrapolation u_t = x_t + bt (x_t - x_{t-1}), by the thread that owns the group
                     int cnt = 0;
+                    X lx = it_zero((X*)nullptr), lu = lx;  // Lasso: x_t, u_t of the thread's atom, for the list
                     if (kept) {
                         const int an = a_lo0 + ka_run + r_a;  // new position of the group's first atom
-                        if (!P.is_group) {
+                        if (!is_grp) {
                             T z = T(0);
                             for (int c = 0; c < nchunk; c++) z += zpart[r_a * nchunk + c];
                             const bool first = k0 == 0;
@@ -1837,6 +1858,8 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             const X uv = SM == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
                             xW[an] = xv;
                             uW[an] = uv;
+                            lx = xv;
+                            lu = uv;
                             if (SM) {
                                 // what a redone step needs: z_t, the base point and x_{t-1}
                                 W.zS[an] = z;
@@ -1850,7 +1873,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X v = it_grad_step(ldcg_x((cp || SM >= 2 ? xO : uO) + lo_o + q), z, invL);
+                                const X v = it_grad_step((cp || SM >= 2) ? rs_x[r_a + q] : rs_u[r_a + q], z, invL);
                                 zq.add(z, z);
                                 acc_sq(vq, v);
                             }
@@ -1861,13 +1884,15 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             for (int q = 0; q < sz; q++) {
                                 T z = T(0);
                                 for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X xo = ldcg_x(xO + lo_o + q);
-                                const X bpt = (cp || SM >= 2) ? xo : ldcg_x(uO + lo_o + q);
+                                const X xo = rs_x[r_a + q], uo = rs_u[r_a + q];
+                                const X bpt = (cp || SM >= 2) ? xo : uo;
                                 X xv = it_scale(it_grad_step(bpt, z, invL), f);
-                                if (SM == 3 && t > 1) xv = it_twist(ldcg_x(uO + lo_o + q), xo, xv, P.tw_a, P.tw_b);
+                                if (SM == 3 && t > 1) xv = it_twist(uo, xo, xv, P.tw_a, P.tw_b);
                                 const X uv = SM == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
                                 xW[an + q] = xv;
                                 uW[an + q] = uv;
+                                rs_x[r_a + q] = xv;  // for the nonzero list below (this thread's slots)
+                                rs_u[r_a + q] = uv;
                                 if (SM) {
                                     W.zS[an + q] = z;
                                     W.bS[an + q] = bpt;
@@ -1883,13 +1908,12 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     int totc;
                     const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
                     if (cnt) {
-                        const int an = a_lo0 + ka_run + r_a;
                         const int td = f32_sphere ? __float_as_int(thf) : gid;
-                        const int c0 = P.is_group ? P.goff[gid] : gid;
+                        const int c0 = is_grp ? P.goff[gid] : gid;
                         int e = a_lo0 + nz_base + pc;
                         for (int q = 0; q < sz; q++) {
-                            const X xv = xW[an + q];
-                            const X uv = SM >= 2 ? xv : uW[an + q];
+                            const X xv = is_grp ? rs_x[r_a + q] : lx;
+                            const X uv = SM >= 2 ? xv : (is_grp ? rs_u[r_a + q] : lu);
                             if (it_nz(uv) || it_nz(xv)) {
                                 W.nz_col[e] = c0 + q;
                                 W.nz_u[e] = uv;
@@ -1931,9 +1955,9 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
         for (int k = tid; k < n_own; k += kThreads) {
             if (!__ldcg(W.keep + g_lo + k)) continue;
             const int gid = __ldcg(W.act[cur] + g_lo + k);
-            const int lo_a = P.is_group ? __ldcg(W.aoff[cur] + g_lo + k) : a_lo0 + k;
-            const int c0 = P.is_group ? P.goff[gid] : gid;
-            const int sz = P.is_group ? P.goff[gid + 1] - P.goff[gid] : 1;
+            const int lo_a = is_grp ? __ldcg(W.aoff[cur] + g_lo + k) : a_lo0 + k;
+            const int c0 = is_grp ? P.goff[gid] : gid;
+            const int sz = is_grp ? P.goff[gid + 1] - P.goff[gid] : 1;
             for (int q = 0; q < sz; q++) xout[c0 + q] = (T)it_round(ldcg_x(xbuf(iO) + lo_a + q));
         }
         if (b == 0 && tid == 0) {
@@ -1966,18 +1990,21 @@ struct Geometry {
 template <typename T>
 inline ds_status geometry(const DictDesc& dd, int num_sms, size_t smem_optin, Geometry* g)
 {
+    using X = typename IterT<T>::type;
     constexpr int EV = 16 / sizeof(T);
     const int chunk = 32 * EV * kU;
     g->nchunk = (dd.N + chunk - 1) / chunk;
     g->npad = g->nchunk * chunk;
     g->G = std::min(num_sms, kMaxG);  // one CTA per SM, within the fixed-size reductions
-    // shared memory: theta + zpart + cols, and room for n (hi/lo) in the precompute
-    const size_t fixed = g->npad * sizeof(T);
+    // shared memory: theta, then per atom of a round its z chunks, column and old position (Group-Lasso
+    // also its old iterates u and x, 8-byte aligned), and room for n (hi/lo) in the precompute
+    const size_t fixed = g->npad * sizeof(T) + 8;
+    const size_t per_atom = g->nchunk * sizeof(T) + 8 + (dd.is_group ? 2 * sizeof(X) : 0);
     const size_t budget = smem_optin > 48 * 1024 ? smem_optin - 40 * 1024 : 48 * 1024;
-    if (fixed + 64 * (g->nchunk * sizeof(T) + 8) > budget) return DS_ERR_UNSUPPORTED;
-    g->RA = (int)std::min<size_t>(512, (budget - fixed) / (g->nchunk * sizeof(T) + 8));
+    if (fixed + 64 * per_atom > budget) return DS_ERR_UNSUPPORTED;
+    g->RA = (int)std::min<size_t>(512, (budget - fixed) / per_atom);
     if (dd.is_group && g->RA < dd.max_gsize) return DS_ERR_UNSUPPORTED;
-    g->smem = std::max(fixed + (size_t)g->RA * (g->nchunk * sizeof(T) + 8), (size_t)g->npad * 8);
+    g->smem = std::max(fixed + (size_t)g->RA * per_atom, (size_t)g->npad * 8);
     if (g->smem > budget) return DS_ERR_UNSUPPORTED;
     return DS_OK;
 }

@@ -176,9 +176,14 @@ __global__ void __launch_bounds__(kThreads, 1) team_kernel(const TeamArgs<T> A)
             return;
         }
         if (A.server) {
-            // copy x and the result to the caller's host buffers, then flag completion
+            // copy x and the result to the caller's host buffers, then flag completion; every CTA wrote its
+            // own slice of x, so the team barrier comes before any CTA copies another's entries
+            if (!grid_sync(bar, A.team_size, gen)) {
+                if (threadIdx.x == 0) atomicExch(A.error, 1);
+                return;
+            }
             const T* xs = sP.x_out;
-            for (int i = rank * kThreads + threadIdx.x; i < sP.K; i += A.team_size * kThreads) host_x[i] = xs[i];
+            for (int i = rank * kThreads + threadIdx.x; i < sP.K; i += A.team_size * kThreads) host_x[i] = __ldcg(xs + i);
             __threadfence_system();
             if (!grid_sync(bar, A.team_size, gen)) {
                 if (threadIdx.x == 0) atomicExch(A.error, 1);
