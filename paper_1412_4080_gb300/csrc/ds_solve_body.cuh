@@ -159,6 +159,16 @@ template <> __device__ __forceinline__ float round_up_to<float>(double v) { retu
 template <> __device__ __forceinline__ double round_up_to<double>(double v) { return v; }
 
 // ---- iterate arithmetic (float-float for FP32 dictionaries, FP64 otherwise)
+// max over a group of ||z_g|| / w_g, rounded up so that the maximum stays an upper bound of the exact
+// value: FP32 with directed rounding (the pair summed up, 2^-20 for the error of the compensated sum);
+// FP64 as computed
+__device__ __forceinline__ float group_zmax(const Dot2f& zq, double wg)
+{
+    const float s = __fmul_ru(__fadd_ru(zq.s, zq.c), 1.000001f);
+    return __fdiv_ru(__fsqrt_ru(s), __double2float_rd(wg));
+}
+__device__ __forceinline__ double group_zmax(const Dot2d& zq, double wg) { return sqrt(zq.value()) / wg; }
+
 __device__ __forceinline__ FF ldcg_x(const FF* p)
 {
     const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
@@ -1394,17 +1404,21 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
 
             // ======= (B) stop test, compaction of the test of t-1, correlation + prox + momentum
             {
-                // Lasso: the first round's keep flags, columns, thresholds and iterates, fetched while
-                // warps 0 and 1 reduce the partials
-                const int n0 = is_grp ? 0 : min(n_own, P.RA);
+                // the first round's keep flags, groups and thresholds (Lasso: and iterates; Group-Lasso: and
+                // first atoms), fetched while warps 0 and 1 reduce the partials
+                const int n0 = min(n_own, is_grp ? kThreads : P.RA);
                 {
                     const int ps = (tid + kThreads - 64) % kThreads;  // issued by warps 2.. first
                     if (ps < n0) {
                         pf4(&s_pf_i0[ps], W.keep + g_lo + ps);
                         pf4(&s_pf_i1[ps], W.act[cur] + g_lo + ps);
                         if (f32_sphere) pf4(&s_pf_f0[ps], W.thrc[cur] + g_lo + ps);
-                        pf8(&s_pf_u[ps], ubuf(iO) + a_lo0 + ps);
-                        pf8(&s_pf_x[ps], xbuf(iO) + a_lo0 + ps);
+                        if (is_grp) {
+                            pf4(&s_pf_i2[ps], W.aoff[cur] + g_lo + ps);
+                        } else {
+                            pf8(&s_pf_u[ps], ubuf(iO) + a_lo0 + ps);
+                            pf8(&s_pf_x[ps], xbuf(iO) + a_lo0 + ps);
+                        }
                     }
                 }
                 if (warp >= 2) {
@@ -1717,7 +1731,7 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                 const X* const xO = xbuf(iO);
                 const X* const uO = ubuf(iO);
                 int* const opos_s = cols_s + P.RA;
-                // Group-Lasso: the round's old iterates u and x, staged in shared memory
+                // Group-Lasso: the round's old iterates u and x, staged in shared memory (and the steps after them)
                 X* const rs_u = reinterpret_cast<X*>((reinterpret_cast<uintptr_t>(opos_s + P.RA) + 7) & ~uintptr_t(7));
                 X* const rs_x = rs_u + P.RA;
                 // Lasso slice in which the last test screened nothing: positions stay, no list copy
@@ -1739,10 +1753,11 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             lo_o = a_lo0 + k;
                         }
                     } else if (k < n_own) {
-                        kp = __ldcg(W.keep + g_lo + k);
-                        gid = __ldcg(W.act[cur] + g_lo + k);
-                        if (f32_sphere) thf = __ldcg(W.thrc[cur] + g_lo + k);
-                        lo_o = __ldcg(W.aoff[cur] + g_lo + k);
+                        const bool first = k0 == 0;  // k < n0: prefetched
+                        kp = first ? s_pf_i0[tid] : __ldcg(W.keep + g_lo + k);
+                        gid = first ? s_pf_i1[tid] : __ldcg(W.act[cur] + g_lo + k);
+                        if (f32_sphere) thf = first ? s_pf_f0[tid] : __ldcg(W.thrc[cur] + g_lo + k);
+                        lo_o = first ? s_pf_i2[tid] : __ldcg(W.aoff[cur] + g_lo + k);
                         sz = P.goff[gid + 1] - P.goff[gid];
                     }
                     int k1;
@@ -1837,13 +1852,14 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                     }
                     if (is_grp) pf_wait();  // this thread's staged iterates; the barrier publishes them
                     __syncthreads();
-                    // proximal step (Table 1), x_t = prox_{lambda/L Omega}(u_{t-1} - z / L), and the FISTA
-                    // extrapolation u_t = x_t + bt (x_t - x_{t-1}), by the thread that owns the group
-                    int cnt = 0;
-                    X lx = it_zero((X*)nullptr), lu = lx;  // Lasso: x_t, u_t of the thread's atom, for the list
-                    if (kept) {
-                        const int an = a_lo0 + ka_run + r_a;  // new position of the group's first atom
-                        if (!is_grp) {
+                    int totc;  // entries of this round in the nonzero list of (u_t, x_t)
+                    if (!is_grp) {
+                        // proximal step (Table 1), x_t = prox_{lambda/L Omega}(u_{t-1} - z / L), and the FISTA
+                        // extrapolation u_t = x_t + bt (x_t - x_{t-1}), by the thread that owns the atom
+                        int cnt = 0;
+                        X lx = it_zero((X*)nullptr), lu = lx;  // x_t, u_t of the thread's atom, for the list
+                        if (kept) {
+                            const int an = a_lo0 + ka_run + r_a;  // new position of the atom
                             T z = T(0);
                             for (int c = 0; c < nchunk; c++) z += zpart[r_a * nchunk + c];
                             const bool first = k0 == 0;
@@ -1868,59 +1884,82 @@ __device__ __forceinline__ bool solve_body(const SolveP<T>& P, const int b, cons
                             }
                             mloc = fmax(mloc, fabs(z));
                             cnt = (it_nz(SM >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
-                        } else {
+                        }
+                        // nonzero list of (u_t, x_t), with the atom's test data
+                        const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
+                        if (cnt) {
+                            const int e = a_lo0 + nz_base + pc;
+                            W.nz_col[e] = gid;
+                            W.nz_u[e] = SM >= 2 ? lx : lu;
+                            W.nz_x[e] = lx;
+                            W.nz_t[e] = f32_sphere ? __float_as_int(thf) : gid;
+                        }
+                    } else {
+                        // Group-Lasso prox (Table 1, group soft threshold) in three steps over the round's atoms,
+                        // which sit at 0 .. natoms-1 group after group: (1) thread r: z_r and the gradient step
+                        // v_r of atom r; (2) the owner of a group: ||v_g||, the group's threshold factor and
+                        // ||z_g|| / w_g; (3) thread r: x_t, u_t and the nonzero-list entry of atom r
+                        X* const rs_f = rs_x + P.RA;  // per atom: v_r, then its group's factor
+                        const int r = tid;
+                        const bool ra_in = r < natoms;
+                        T z_r = T(0);
+                        X v_r = it_zero((X*)nullptr), xo = v_r, uo = v_r;
+                        if (ra_in) {
+                            for (int c = 0; c < nchunk; c++) z_r += zpart[r * nchunk + c];
+                            xo = rs_x[r];
+                            uo = rs_u[r];
+                            // gradient step from ubar_{t-1} (ISTA, FISTA) or x_{t-1} (CP, SpaRSA, TwIST)
+                            v_r = it_grad_step((cp || SM >= 2) ? xo : uo, z_r, invL);
+                            zpart[r * nchunk] = z_r;
+                            rs_f[r] = v_r;
+                        }
+                        __syncthreads();
+                        if (kept) {
                             Acc zq, vq;
                             for (int q = 0; q < sz; q++) {
-                                T z = T(0);
-                                for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X v = it_grad_step((cp || SM >= 2) ? rs_x[r_a + q] : rs_u[r_a + q], z, invL);
+                                const T z = zpart[(r_a + q) * nchunk];
                                 zq.add(z, z);
-                                acc_sq(vq, v);
+                                acc_sq(vq, rs_f[r_a + q]);
                             }
                             const double wg = P.w[gid];
-                            const double nv = sqrt(vq.value());
+                            const double nv = fast_sqrt(vq.value());
                             // group soft threshold: max(0, (||v_g|| - t w_g) / ||v_g||) v_g
-                            const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) / nv) : 0.0, (X*)nullptr);
+                            const X f = it_cast(nv > 0.0 ? fmax(0.0, (nv - thrL * wg) * fast_rcp(nv)) : 0.0, (X*)nullptr);
+                            const int td = f32_sphere ? __float_as_int(thf) : gid;
                             for (int q = 0; q < sz; q++) {
-                                T z = T(0);
-                                for (int c = 0; c < nchunk; c++) z += zpart[(r_a + q) * nchunk + c];
-                                const X xo = rs_x[r_a + q], uo = rs_u[r_a + q];
-                                const X bpt = (cp || SM >= 2) ? xo : uo;
-                                X xv = it_scale(it_grad_step(bpt, z, invL), f);
-                                if (SM == 3 && t > 1) xv = it_twist(uo, xo, xv, P.tw_a, P.tw_b);
-                                const X uv = SM == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
-                                xW[an + q] = xv;
-                                uW[an + q] = uv;
-                                rs_x[r_a + q] = xv;  // for the nonzero list below (this thread's slots)
-                                rs_u[r_a + q] = uv;
-                                if (SM) {
-                                    W.zS[an + q] = z;
-                                    W.bS[an + q] = bpt;
-                                    W.pS[an + q] = xo;
-                                }
-                                cnt += (it_nz(SM >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
+                                rs_f[r_a + q] = f;
+                                opos_s[r_a + q] = td;  // the group's test data, for the list (positions are read)
                             }
-                            // rounded up so that the FP32 max stays an upper bound of the FP64 value
-                            mloc = fmax(mloc, round_up_to<T>(sqrt(zq.value()) / wg));
+                            mloc = fmax(mloc, group_zmax(zq, wg));
                         }
-                    }
-                    // nonzero list of (u_t, x_t), with the group's test data
-                    int totc;
-                    const int pc = block_exclusive_scan(cnt, s_tmp, &totc);
-                    if (cnt) {
-                        const int td = f32_sphere ? __float_as_int(thf) : gid;
-                        const int c0 = is_grp ? P.goff[gid] : gid;
-                        int e = a_lo0 + nz_base + pc;
-                        for (int q = 0; q < sz; q++) {
-                            const X xv = is_grp ? rs_x[r_a + q] : lx;
-                            const X uv = SM >= 2 ? xv : (is_grp ? rs_u[r_a + q] : lu);
-                            if (it_nz(uv) || it_nz(xv)) {
-                                W.nz_col[e] = c0 + q;
-                                W.nz_u[e] = uv;
-                                W.nz_x[e] = xv;
-                                W.nz_t[e] = td;
-                                e++;
+                        __syncthreads();
+                        int nzf = 0;
+                        X xv = v_r, uv = v_r;
+                        if (ra_in) {
+                            const int an = a_lo0 + ka_run + r;  // new position of atom r
+                            xv = it_scale(v_r, rs_f[r]);
+                            // TwIST after its first step: (1 - a) x_{t-2} + (a - b) x_{t-1} + b prox(...), with
+                            // x_{t-2} kept in the u buffer
+                            if (SM == 3 && t > 1) xv = it_twist(uo, xo, xv, P.tw_a, P.tw_b);
+                            uv = SM == 3 ? xo : (ista ? xv : it_momentum(xv, xo, btX));
+                            xW[an] = xv;
+                            uW[an] = uv;
+                            if (SM) {
+                                // what a redone step needs: z_t, the base point and x_{t-1}
+                                W.zS[an] = z_r;
+                                W.bS[an] = (cp || SM >= 2) ? xo : uo;
+                                W.pS[an] = xo;
                             }
+                            nzf = (it_nz(SM >= 2 ? xv : uv) || it_nz(xv)) ? 1 : 0;
+                        }
+                        // nonzero list: one entry per nonzero atom, in atom order (the groups' order)
+                        const int pc = block_exclusive_scan(nzf, s_tmp, &totc);
+                        if (nzf) {
+                            const int e = a_lo0 + nz_base + pc;
+                            W.nz_col[e] = cols_s[r];
+                            W.nz_u[e] = SM >= 2 ? xv : uv;
+                            W.nz_x[e] = xv;
+                            W.nz_t[e] = opos_s[r];
                         }
                     }
                     kg_run += ngr;
@@ -1997,9 +2036,9 @@ inline ds_status geometry(const DictDesc& dd, int num_sms, size_t smem_optin, Ge
     g->npad = g->nchunk * chunk;
     g->G = std::min(num_sms, kMaxG);  // one CTA per SM, within the fixed-size reductions
     // shared memory: theta, then per atom of a round its z chunks, column and old position (Group-Lasso
-    // also its old iterates u and x, 8-byte aligned), and room for n (hi/lo) in the precompute
+    // also its old iterates u and x and its step v, 8-byte aligned), and room for n (hi/lo) in the precompute
     const size_t fixed = g->npad * sizeof(T) + 8;
-    const size_t per_atom = g->nchunk * sizeof(T) + 8 + (dd.is_group ? 2 * sizeof(X) : 0);
+    const size_t per_atom = g->nchunk * sizeof(T) + 8 + (dd.is_group ? 3 * sizeof(X) : 0);
     const size_t budget = smem_optin > 48 * 1024 ? smem_optin - 40 * 1024 : 48 * 1024;
     if (fixed + 64 * per_atom > budget) return DS_ERR_UNSUPPORTED;
     g->RA = (int)std::min<size_t>(512, (budget - fixed) / per_atom);
