@@ -99,8 +99,11 @@ typedef struct {
                               (1 + sqrt(xi_1)) (<= 0: 1e-4) */
     int gap_every;         /* the stopping rule (duality gap) is evaluated every gap_every iterations
                               (<= 1: every iteration) */
-    int team_size;         /* CTAs that run one solve: ds_solve / ds_solve_path (0: one per SM) and the
-                              multi-RHS blocks of batches (0: automatic) */
+    int team_size;         /* CTAs that run one solve: ds_solve / ds_solve_path (0: one per SM, except
+                              that a small FP64 Lasso problem -- N <= 256, K <= 2048, ISTA or FISTA at
+                              a fixed step, one lambda, no history -- runs on one thread-block cluster
+                              of 2 to 8 CTAs holding the dictionary in shared memory) and the multi-RHS
+                              blocks of batches (0: automatic); > 0 always runs the grid of that size */
 } ds_options;
 
 typedef struct {

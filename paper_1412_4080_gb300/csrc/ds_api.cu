@@ -270,6 +270,11 @@ ds_status ds_dict_create(ds_ctx* ctx, const void* D, int64_t N, int64_t K, int64
     }
     ds_status st = dict_precompute(ctx, d, wh.empty() ? nullptr : wh.data());
     if (st != DS_OK) return fail(st);
+    if (small_dict_eligible(dtype, d->is_group, N, K)) {
+        if (cudaMalloc(&d->Dff, sizeof(float2) * (size_t)N * K) != cudaSuccess) return fail(DS_ERR_OOM);
+        if (small_dict_split(static_cast<const double*>(d->D), ldp, (int)N, (int)K, d->Dff, s) != cudaSuccess)
+            return fail(DS_ERR_CUDA);
+    }
     if (work_prec == DS_BF16 || work_prec == DS_FP8) {
         st = dict_lowp(ctx, d, work_prec == DS_BF16 ? 1 : 2);
         if (st != DS_OK) return fail(st);
@@ -293,6 +298,7 @@ ds_status ds_dict_destroy(ds_dict* d)
     if (d->spec) cudaFree(d->spec);
     if (d->Dlo) cudaFree(d->Dlo);
     if (d->lo_scale) cudaFree(d->lo_scale);
+    if (d->Dff) cudaFree(d->Dff);
     delete d;
     return DS_OK;
 }

@@ -53,6 +53,9 @@ struct ds_dict {
     int64_t ld_lo;
     float* lo_scale;  // FP8: per-column scale (d_i ~ scale_i * q_i)
     double emax;      // max_g ||D_g - Dlo_g||_F / w_g: rounding of the copy, for the radius bound
+    // FP64 dictionaries small enough for the one-cluster solve: each entry as a float-float pair
+    // (hi, lo), K columns of N, made once here so that no solve converts on the FP64 pipe
+    float2* Dff;
 };
 
 namespace ds {
@@ -90,6 +93,7 @@ struct DictDesc {
     int ld_lo;
     const float* lo_scale;
     double emax;
+    const float2* Dff;      // FP64 dictionaries: the float-float copy (or null)
 };
 
 // Where and how a solve runs: a context (workspace reserved on demand, timing
@@ -122,6 +126,10 @@ ds_status launch_solve(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, cons
 ds_status launch_lambda_max(ds_ctx* ctx, const ds_dict* dict, const void* y_dev, double* lmax);
 ds_status dict_precompute(ds_ctx* ctx, ds_dict* dict, const double* w_host);
 ds_status dict_lowp(ds_ctx* ctx, ds_dict* dict, int kind);
+// the one-cluster solve of small FP64 Lasso problems (ds_small.cu): which dictionaries get the
+// float-float copy, and the kernel that makes it
+bool small_dict_eligible(int dtype, int is_group, long long N, long long K);
+cudaError_t small_dict_split(const double* D, long long ld, int N, int K, float2* out, cudaStream_t s);
 
 // Right-hand sides sharing a dictionary, solved together (ds_mrhs.cu): a block
 // is up to 64 problems of one FP32 Lasso instance; problem r of the block is the

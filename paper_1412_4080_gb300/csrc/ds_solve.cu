@@ -24,10 +24,15 @@
 // Reductions are per-CTA partials summed in a fixed order by every CTA, so all
 // CTAs take identical decisions and the results do not depend on timing.
 #include <cmath>
+#include <cstring>
 
 #include "ds_solve_body.cuh"
 
 namespace ds {
+
+// the one-cluster solve of small FP64 Lasso problems (ds_small.cu)
+int small_cluster_size(const SolveP<double>& P, size_t smem_optin, int* pitch);
+cudaError_t launch_small(const SolveP<double>& P, int C, int pitch, size_t smem_optin, cudaStream_t s);
 
 // ADAPT: the kernel also runs the adaptive-step rows (backtracking, SpaRSA, TwIST); fixed-step solves
 // launch the instance without that code.  GRP: the instance for Group-Lasso (1) or Lasso (0)
@@ -61,6 +66,36 @@ size_t solve_ws_bytes(const DictDesc& dd, int num_sms, size_t smem_optin, int n_
 {
     return dd.dtype == DS_FP32 ? solve_ws_bytes_t<float>(dd, num_sms, smem_optin, n_lambda)
                                : solve_ws_bytes_t<double>(dd, num_sms, smem_optin, n_lambda);
+}
+
+// Results of a launched solve: copied back on the solve's stream, then the kernel time.
+static ds_status finish_solve(const SolveEnv& env, DevResult* res_host, const DevResult* res_dev, int n_lambda,
+                              float* ms)
+{
+    cudaStream_t s = env.stream;
+    const int nr = std::max(n_lambda, 1);
+    // through the context's pinned buffer when there is one (an asynchronous copy, not a staged one)
+    DevResult* dst = res_host;
+    if (env.ctx) {
+        if (env.ctx->res_cap < (size_t)nr) {
+            if (env.ctx->h_res) cudaFreeHost(env.ctx->h_res);
+            env.ctx->h_res = nullptr;
+            env.ctx->res_cap = 0;
+            if (cudaMallocHost(&env.ctx->h_res, sizeof(DevResult) * nr) == cudaSuccess) env.ctx->res_cap = nr;
+        }
+        if (env.ctx->h_res) dst = static_cast<DevResult*>(env.ctx->h_res);
+    }
+    if (cudaMemcpyAsync(dst, res_dev, sizeof(DevResult) * nr, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return DS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DS_ERR_CUDA;
+    if (dst != res_host) std::memcpy(res_host, dst, sizeof(DevResult) * nr);
+    if (ms) {
+        *ms = 0.f;
+        if (env.ctx) cudaEventElapsedTime(ms, env.ctx->ev0, env.ctx->ev1);
+    }
+    for (int j = 0; j < std::max(n_lambda, 1); j++)
+        if (res_host[j].status == kDevTimeout) return DS_ERR_TIMEOUT;
+    return DS_OK;
 }
 
 template <typename T>
@@ -109,6 +144,26 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
     P.ws = w;
 
     cudaStream_t s = env.stream;
+    if constexpr (sizeof(T) == 8) {
+        // a small FP64 Lasso problem runs on one thread-block cluster (team_size > 0 keeps the grid); its
+        // lambda travels in the parameters, and it needs no grid barrier
+        int pitch = 0;
+        const int C = (opt && opt->team_size > 0) ? 0 : small_cluster_size(P, env.smem_optin, &pitch);
+        if (C > 0) {
+            P.lam0 = lambdas_host[0];
+            if (env.ctx) {
+                env.ctx->launches++;
+                cudaEventRecord(env.ctx->ev0, s);
+            }
+            const cudaError_t e = launch_small(P, C, pitch, env.smem_optin, s);
+            if (e != cudaSuccess) {
+                fprintf(stderr, "dscreen: small solve launch failed: %s\n", cudaGetErrorString(e));
+                return DS_ERR_CUDA;
+            }
+            if (env.ctx) cudaEventRecord(env.ctx->ev1, s);
+            return finish_solve(env, res_host, res_dev, n_lambda, ms);
+        }
+    }
     if (n_lambda > 0 &&
         cudaMemcpyAsync(lam_dev, lambdas_host, sizeof(double) * n_lambda, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return DS_ERR_CUDA;
@@ -144,18 +199,8 @@ static ds_status launch_env_t(const SolveEnv& env, const DictDesc& dd, const voi
         return DS_ERR_CUDA;
     }
     if (env.ctx) cudaEventRecord(env.ctx->ev1, s);
-    if (cudaMemcpyAsync(res_host, res_dev, sizeof(DevResult) * std::max(n_lambda, 1), cudaMemcpyDeviceToHost, s) !=
-        cudaSuccess)
-        return DS_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return DS_ERR_CUDA;
-    if (ms) {
-        *ms = 0.f;
-        if (env.ctx) cudaEventElapsedTime(ms, env.ctx->ev0, env.ctx->ev1);
-    }
-    for (int j = 0; j < std::max(n_lambda, 1); j++)
-        if (res_host[j].status == kDevTimeout) return DS_ERR_TIMEOUT;
     (void)EV;
-    return DS_OK;
+    return finish_solve(env, res_host, res_dev, n_lambda, ms);
 }
 
 ds_status launch_solve_env(const SolveEnv& env, const DictDesc& dd, const void* y_dev, const void* x0_dev, int n_lambda,
@@ -190,6 +235,7 @@ DictDesc dict_desc(const ds_dict* d)
     dd.ld_lo = (int)d->ld_lo;
     dd.lo_scale = d->lo_scale;
     dd.emax = d->emax;
+    dd.Dff = d->Dff;
     return dd;
 }
 

@@ -122,6 +122,10 @@ struct SolveP {
     int lo_kind, ld_lo;
     const float* lo_scale;
     double emax, gamma_lo, lo_switch;
+    // the one-cluster solve of small FP64 Lasso problems: the dictionary as float-float pairs (K x N)
+    // and the single lambda as given (lambda_rel applies to it)
+    const float2* Dff;
+    double lam0;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -2109,6 +2113,8 @@ inline void fill_params(SolveP<T>& P, const DictDesc& dd, const Geometry& g, con
     P.N = dd.N; P.K = dd.K; P.ld = dd.ld; P.nG = dd.nG; P.is_group = dd.is_group;
     P.goff = dd.goff; P.w = dd.w; P.spec = dd.spec; P.colnorm = dd.colnorm;
     P.fmax = dd.fmax;
+    P.Dff = sizeof(T) == 8 ? dd.Dff : nullptr;
+    P.lam0 = 0.0;
     {
         // worst-case rounding of the FP GEMV: each product goes through at most
         // kU*EV FMAs in a lane, 5 shuffle additions and nchunk chunk additions
