@@ -1044,7 +1044,8 @@ GROUP_TESTS = ("gsafe", "dgst3")
 def config1_latency(reps=10, warmup=3):
     """Latency of the small FP64 case (100 x 500 Gaussian unit-norm D, 10 nonzeros, sigma 0.01,
     seed 1001): ISTA + dynamic DST3 at lambda = 0.5 lambda_max to gap 1e-8 * 1/2 ||y||^2, one
-    ds_solve at a time, CUDA events on the library's stream (D fits in cache: no flush)."""
+    ds_solve at a time, CUDA events on the library's stream (D fits in cache: no flush).
+    team_size 0 takes the one-cluster solve (4 CTAs for this size); team_size > 0 the grid kernel."""
     import torch
     import gen
     import paper_1412_4080_gb300 as ds
@@ -1077,6 +1078,7 @@ def config1_latency(reps=10, warmup=3):
     ds.ds_dict_destroy(dct)
     ds.ds_destroy(ctx)
     return {"median_ms": statistics.median(ms), "min_ms": min(ms), "iters": res[-1]["iters"],
+            "path": "one thread-block cluster (the dictionary in shared memory as float-float pairs)",
             "median_ms_by_grid_ctas": by_grid,
             "converged": all(r["status"] == 0 for r in res),
             "workload": "100x500 FP64 Gaussian, 10 nonzeros, sigma 0.01 (seed 1001), ISTA + dynamic DST3, "
