@@ -7,18 +7,26 @@
 // C <= 8 CTAs of one cluster hold the dictionary in shared memory as
 // float-float pairs (hi + lo, about 48 significant bits; one slice of columns
 // per CTA, one atom per thread), exchange partial sums through distributed
-// shared memory and synchronise on the cluster barrier.  Iteration t:
+// shared memory and meet at one cluster barrier per iteration.  Iteration t:
 //
 //   (1) each CTA synthesises its atoms' part of D ubar_{t-1} and D xbar_{t-1}
-//       over their nonzeros, and its part of ||xbar_{t-1}||_1;  cluster barrier
-//   (2) every CTA adds the C parts in rank order: theta_t = D ubar_{t-1} - y
-//       and the residual D xbar_{t-1} - y, their sums and the duality gap of
-//       iteration t-1 (the stopping rule); each thread correlates its atom,
-//       z = d^T theta_t, and takes the proximal step and the FISTA
-//       extrapolation;                                          cluster barrier
-//   (3) every CTA takes max |z| over the cluster and rank 0's stop decision,
-//       the Lemma 8 dual scaling, the radius of the test (Lemmas 2-4), and
-//       tests its atoms (dynamic screening).
+//       over their nonzeros (the test of iteration t-1 still pending) and
+//       writes it, with its part of ||xbar_{t-1}||_1 and its max |z_{t-1}|,
+//       into its own shared memory; it arrives at the cluster barrier and,
+//       before it waits, computes the Lemma 8 terms of theta_{t-1} that do
+//       not need the cluster's max |z_{t-1}|;
+//   (2) after the barrier every CTA reads the C parts from the others' shared
+//       memory (a pull) and adds them in rank order: the cluster's max
+//       |z_{t-1}| completes the Lemma 8 dual scaling and the radius of the
+//       test of t-1 (Lemmas 2-4), while theta_t = D ubar_{t-1} - y, the
+//       residual D xbar_{t-1} - y and their sums are formed.  The test is
+//       applied to the CTA's atoms; when it may have screened a nonzero atom
+//       (the dome test: always) a second exchange takes those atoms' parts
+//       back out of theta_t;
+//   (3) the active atoms are correlated, z = d^T theta_t, with several lanes
+//       per atom when few are active, while one warp takes the duality gap of
+//       iteration t-1 and the stopping rule; then the proximal step and the
+//       FISTA extrapolation.
 //
 // Every CTA computes the scalars from the same data in the same order, and the
 // loop ends on rank 0's decision, which every CTA reads: all CTAs pass the
