@@ -326,6 +326,8 @@ def main():
                          "exit (profiling the DRAM traffic of the solve kernel)")
     ap.add_argument("--profile-batch", action="store_true",
                     help="run one 64-rhs multi-RHS batch on the BF16 copy of the dictionary, then exit (profiling)")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="run the 100x500 FP64 solve (one-cluster kernel) three times, then exit (profiling)")
     ap.add_argument("--group-only", action="store_true",
                     help="the Group-Lasso workload alone (the default run measures it last)")
     ap.add_argument("--paper", action="store_true",
@@ -343,6 +345,9 @@ def main():
         return
     if args.profile_large:
         profile_large()
+        return
+    if args.profile_small:
+        profile_small()
         return
     if args.paper:
         paper_accounting()
@@ -657,6 +662,25 @@ def profile_one():
     yy = float(y32.astype(np.float64) @ y32.astype(np.float64))
     print(json.dumps([{**{k: r[k] for k in ("iters", "status", "ms", "n_active", "nnz", "cols_corr", "cols_synth")},
                        "gap_rel": r["gap"] / (0.5 * yy)} for r in res]))
+
+
+def profile_small(reps=3):
+    """The small FP64 case (100 x 500, ISTA + DST3 at 0.5 lambda_max to gap 1e-8) solved `reps` times on
+    the one-cluster kernel; prints the iterations and times (profiling)."""
+    import torch
+    import gen
+    import paper_1412_4080_gb300 as ds
+    D, y, _ = gen.config1(1001)
+    Dt = torch.from_numpy(np.ascontiguousarray(D.T)).cuda().t()
+    yt = torch.from_numpy(np.ascontiguousarray(y)).cuda()
+    x = torch.empty(D.shape[1], dtype=torch.float64, device="cuda")
+    ctx = ds.ds_create(0, torch.cuda.current_stream())
+    dct = ds.ds_dict_create(ctx, Dt)
+    o = ds.ds_options_default(alg="ista", test="dst3", tol_gap_rel=1e-8, max_iter=100000, lambda_rel=1)
+    res = [ds.ds_solve(ctx, dct, yt, 0.5, o, x) for _ in range(reps)]
+    ds.ds_dict_destroy(dct)
+    ds.ds_destroy(ctx)
+    print(json.dumps([{k: r[k] for k in ("iters", "status", "ms", "n_active", "nnz")} for r in res]))
 
 
 def _rhs_block(D, R, g, lo=0.1, hi=0.9):
