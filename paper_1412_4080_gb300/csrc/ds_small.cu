@@ -28,6 +28,13 @@
 //       iteration t-1 and the stopping rule; then the proximal step and the
 //       FISTA extrapolation.
 //
+// When a CTA has a warp with neither atoms nor rows and the test is a sphere
+// test, (3) does not wait for the test: the other warps correlate the atoms
+// that were active before it while the spare warp runs the Lemma 8 chain,
+// the radius and the gap (FP64, one dependent operation at a time), and the
+// atoms the test then screens drop their z.  After a correction exchange the
+// correlation is redone on the corrected theta_t.
+//
 // Every CTA computes the scalars from the same data in the same order, and the
 // loop ends on rank 0's decision, which every CTA reads: all CTAs pass the
 // same barriers.  Float-float sums carry an explicit error bound into the
@@ -110,6 +117,20 @@ __device__ __forceinline__ void cluster_wait()
 {
     __syncwarp();
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Named CTA barriers for a subset of the warps (id 1 and 2; __syncthreads is id 0): `n` threads in
+// whole warps.  A warp that arrives does not wait; the barrier completes when n threads have arrived
+// or synced, and orders their shared-memory writes before the reads of the threads that synced.
+__device__ __forceinline__ void named_sync(int id, int n)
+{
+    __syncwarp();
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n)
+{
+    __syncwarp();
+    asm volatile("barrier.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 // The same dot product as a float-float pair, on four independent chains (rows r mod 4) merged exactly.
@@ -397,12 +418,19 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
     }
     // threads of the scalar chains: warps with neither atoms nor rows when there are such
     const bool spare = na_loc <= kSmThreads - 64 && N <= kSmThreads - 64;
-    const int t_rad = spare ? kSmThreads - 32 : 0, t_gap = spare ? kSmThreads - 64 : 32;
+    // (with a spare warp both chains run in it, on lanes 0 and 1, as one instruction stream)
+    const int t_rad = spare ? kSmThreads - 32 : 0, t_gap = spare ? kSmThreads - 31 : 32;
     const int aux = spare ? kSmThreads / 32 - 1 : 0;
+    // with a spare warp and a sphere test (which rarely needs a correction exchange), the other warps
+    // correlate the atoms that were active before the test of iteration t-1 while the spare warp runs
+    // the Lemma 8 chain and the duality gap; the atoms that test screens then drop their z
+    const bool ovl = spare && !(dyn && test == 3);
+    constexpr int kOvlThreads = kSmThreads - 32;  // the correlating warps of the overlapped order
     // (thr - eps)^2 rounded up to FP32, for the conservative "may screen a nonzero atom" check
     const float q2f_a = q2_a > 0.0 ? __double2float_ru(q2_a) : 0.f;
     int stop_t = 0, t_last = 1;
     double lm_beta = 0.0, lm_sunc = 0.0, lm_m2a = 0.0, lm_cup = 0.0;  // radius and gap threads
+    if (tid < kSmThreads / 32) s_wa[tid] = 0;  // the spare warp holds no atoms
     __syncthreads();
     for (int t = 1;; t++) {
         t_last = t;
@@ -499,6 +527,19 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
         }
         cluster_wait();
 
+        // the auxiliary lane's parts of ||xbar_{t-1}||_1, fetched first (merged in the gap chain) so that
+        // their loads overlap the Lemma 8 chain of the same warp
+        float l1p_s[kSmMaxC], l1p_c[kSmMaxC];
+        if (warp == aux && lane == 3) {
+#pragma unroll
+            for (int c = 0; c < kSmMaxC; c++) {
+                if (c < C) {
+                    const SmScal* q = cl.map_shared_rank(&ssc[kb], c);
+                    l1p_s[c] = q->l1s;
+                    l1p_c[c] = q->l1c;
+                }
+            }
+        }
         // ---- (2) the test of iteration t-1 (Lemma 8 with the cluster's max |z_{t-1}|, Lemmas 2-4)
         if (t > 1 && (tid == t_rad || tid == t_gap)) {
             const double beta = lm_beta, s_unc = lm_sunc, m2a = lm_m2a;
@@ -521,19 +562,18 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
                 }
             }
             const double m_nom = (double)mh + (double)ml;
+            // Lemma 8 on both threads in one instruction stream: the gap thread (lm_cup = 0) with the
+            // nominal max |z_{t-1}|, the dual point of the gap of iteration t-1; the radius thread with an
+            // upper bound on max |z| given the float-float rounding of z, for the test
+            const double m_use = m_nom + lm_cup;
+            double mu_s = s_unc;
+            if (m_use > 0.0 && fabs(s_unc) * m_use > 1.0) mu_s = copysign(rcp_lo(m_use), s_unc);
+            const double R2l = fmax(fma(mu_s, fma(mu_s, beta, m2a), yy_l2), 0.0);
             if (tid == t_gap) {
-                // Lemma 8 with the nominal max |z_{t-1}|: the dual point of the gap of iteration t-1
-                const double mu_nom =
-                    (m_nom > 0.0 && fabs(s_unc) * m_nom > 1.0) ? copysign(rcp_lo(m_nom), s_unc) : s_unc;
-                s_sc[19] = fmax(fma(mu_nom, fma(mu_nom, beta, m2a), yy_l2), 0.0);
+                s_sc[19] = R2l;
             } else {
-                // Lemma 8 with an upper bound on max |z| given the float-float rounding of z, for the test;
                 // R^2 enlarged by the bound of the errors of ||y||^2, theta^T y and ||theta||^2
-                double mu_s = s_unc;
-                const double m_up = m_nom + lm_cup;
-                if (m_up > 0.0 && fabs(s_unc) * m_up > 1.0) mu_s = copysign(rcp_lo(m_up), s_unc);
-                const double R2s = fmax(fma(mu_s, fma(mu_s, beta, m2a), yy_l2), 0.0) +
-                                   4.0 * gam * (yy_l2 + mu_s * mu_s * beta);
+                const double R2s = R2l + 4.0 * gam * (yy_l2 + mu_s * mu_s * beta);
                 // squared sphere radius (Lemma 2: R; Lemma 3: sqrt(R^2 - delta^2)), rounded up a little
                 const double rad2 = (test == 2 ? fmax(R2s - delta * delta, 0.0) : R2s) * (1.0 + 3e-13);
                 s_sc[14] = rad2;
@@ -544,18 +584,6 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
                 }
                 // a correction exchange when the test may screen a nonzero atom (the dome: always)
                 s_si[3] = dyn && (test == 3 || (double)mqc > rad2);
-            }
-        }
-        // the auxiliary lane's parts of ||xbar_{t-1}||_1, fetched now (merged after the test)
-        float l1p_s[kSmMaxC], l1p_c[kSmMaxC];
-        if (warp == aux && lane == 3) {
-#pragma unroll
-            for (int c = 0; c < kSmMaxC; c++) {
-                if (c < C) {
-                    const SmScal* q = cl.map_shared_rank(&ssc[kb], c);
-                    l1p_s[c] = q->l1s;
-                    l1p_c[c] = q->l1c;
-                }
             }
         }
         // theta_t's parts from every CTA in rank order, while the radius is computed
@@ -589,15 +617,114 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
             sm_acc(qb, th, th);   // ||theta||^2
             sm_acc(qr, rx, rx);   // ||D xbar_{t-1} - y||^2
         }
-        qa = dot2_warp_reduce(qa);
-        qb = dot2_warp_reduce(qb);
-        qr = dot2_warp_reduce(qr);
-        if (lane == 0 && warp < nwr) {
-            s_red[warp][0] = qa.s; s_red[warp][1] = qa.c;
-            s_red[warp][2] = qb.s; s_red[warp][3] = qb.c;
-            s_red[warp][4] = qr.s; s_red[warp][5] = qr.c;
+        if (!ovl || warp != aux) {  // (the spare warp of the overlapped order has no rows and is busy)
+            qa = dot2_warp_reduce(qa);
+            qb = dot2_warp_reduce(qb);
+            qr = dot2_warp_reduce(qr);
+            if (lane == 0 && warp < nwr) {
+                s_red[warp][0] = qa.s; s_red[warp][1] = qa.c;
+                s_red[warp][2] = qb.s; s_red[warp][3] = qb.c;
+                s_red[warp][4] = qr.s; s_red[warp][5] = qr.c;
+            }
         }
         if (tid == 0 && t == 1) s_si[3] = 0;
+
+        // the duality gap of iteration t-1 and the stopping rule, on the auxiliary warp: lanes 0..2 sum
+        // the three row sums over the row warps in order, lane 3 ||xbar_{t-1}||_1 from the C parts in rank
+        // order (minus the parts of a correction exchange), lane 0 then takes the gap
+        auto gap_chain = [&](bool with_corr) {
+            Dot2f acc;
+            if (lane < 3) {
+                for (int w = 0; w < nwr; w++) dot2_merge(acc, s_red[w][2 * lane], s_red[w][2 * lane + 1]);
+            } else if (lane == 3) {
+#pragma unroll
+                for (int c = 0; c < kSmMaxC; c++)
+                    if (c < C) dot2_merge(acc, l1p_s[c], l1p_c[c]);
+                if (with_corr) {
+                    float rs[kSmMaxC], rcs[kSmMaxC];
+#pragma unroll
+                    for (int c = 0; c < kSmMaxC; c++) {
+                        if (c < C) {
+                            const SmScal* r = cl.map_shared_rank(&ssc[2], c);
+                            rs[c] = -r->l1s;
+                            rcs[c] = -r->l1c;
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < kSmMaxC; c++)
+                        if (c < C) dot2_merge(acc, rs[c], rcs[c]);
+                }
+            }
+            const double sv = acc.value();
+            const double alpha = __shfl_sync(0xffffffffu, sv, 0), beta = __shfl_sync(0xffffffffu, sv, 1);
+            const double rr = __shfl_sync(0xffffffffu, sv, 2), l1v = __shfl_sync(0xffffffffu, sv, 3);
+            if (lane == 0) {
+                int stop = 0;
+                if (t > 1) {
+                    // P(xbar_{t-1}) - Dual(mu theta_{t-1}), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
+                    const double primal = fma(lam, l1v, 0.5 * rr);
+                    const double gap = fma(hlam2, s_sc[19], primal - hyy);
+                    s_out_gap = gap;
+                    s_out_primal = primal;
+                    stop = (P.tol > 0.0 && gap <= tol_abs && (t - 1) % P.gap_every == 0) || (t - 1 >= P.max_iter);
+                }
+                s_si[2] = stop;
+                s_sc[4] = alpha;  // of theta_t, for the test of iteration t
+                s_sc[5] = beta;
+            }
+        };
+        // z_t = d^T theta_t over the listed atoms s_al[0..nact), G lanes per atom; each lane sums rows
+        // q, q + G, ... on two chains and the G partial sums merge by a fixed shuffle tree
+        auto correlate = [&](int G, int nact) {
+            const int j = tid / G, q = tid - j * G;
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+            if (j < nact) {
+                const int aj = s_al[j];
+                int r = q;
+                for (; r + G < N; r += 2 * G) {
+                    sm_dot_step(s0, c0, Dh[r * pitch + aj], Dl[r * pitch + aj], s_th[r]);
+                    sm_dot_step(s1, c1, Dh[(r + G) * pitch + aj], Dl[(r + G) * pitch + aj], s_th[r + G]);
+                }
+                if (r < N) sm_dot_step(s0, c0, Dh[r * pitch + aj], Dl[r * pitch + aj], s_th[r]);
+            }
+            Dot2f acc;
+            acc.s = s0;
+            acc.c = c0;
+            dot2_merge(acc, s1, c1);
+            for (int o = 1; o < G; o <<= 1) {
+                const float os = __shfl_xor_sync(0xffffffffu, acc.s, o), oc = __shfl_xor_sync(0xffffffffu, acc.c, o);
+                dot2_merge(acc, os, oc);
+            }
+            if (q == 0 && j < nact) s_z[j] = ff_two_sum(acc.s, acc.c);
+        };
+        // this thread's atom in the list of the atoms correlated, and the warp's ballot of them
+        unsigned bact = 0;
+        int apos = 0;
+        if (ovl) {
+            if (warp != aux) {
+                named_arrive(2, kSmThreads);  // the row sums, to the auxiliary warp
+                // the atoms active before the test of iteration t-1, correlated while the auxiliary warp
+                // runs the Lemma 8 chain and the gap; those the test screens then drop their z
+                bact = __ballot_sync(0xffffffffu, active);
+                if (lane == 0) s_wa[warp] = __popc(bact);
+                named_sync(1, kOvlThreads);
+                int offa = 0, nact = 0;
+                for (int w = 0; w < kSmThreads / 32; w++) {
+                    const int cw = s_wa[w];
+                    offa += w < warp ? cw : 0;
+                    nact += cw;
+                }
+                apos = offa + __popc(bact & ((1u << lane) - 1u));
+                if (active) s_al[apos] = a;
+                int G = 1;
+                while (G < 32 && 2 * G * nact <= kOvlThreads) G *= 2;
+                named_sync(1, kOvlThreads);
+                correlate(G, nact);
+            } else {
+                named_sync(2, kSmThreads);  // the row sums of theta_t
+                gap_chain(false);
+            }
+        }
         __syncthreads();
         const int corr = s_si[3];
         // dynamic screening with theta_{t-1} (Algorithm 3): the screened atoms leave xbar and ubar
@@ -708,90 +835,28 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
             }
             __syncthreads();
         }
-        const unsigned bact = __ballot_sync(0xffffffffu, active);
-        if (lane == 0) s_wa[warp] = __popc(bact);
-        __syncthreads();
-        // ---- z_t = d^T theta_t over this CTA's active atoms, G lanes per atom (G: a power of two up to 32,
-        // as many as the atoms leave, the auxiliary warp apart); each lane sums rows q, q + G, ... on two
-        // chains and the G partial sums merge by a fixed shuffle tree
-        int offa = 0, nact = 0;
-        for (int w = 0; w < kSmThreads / 32; w++) {
-            const int cw = s_wa[w];
-            offa += w < warp ? cw : 0;
-            nact += cw;
+        if (!ovl || corr) {
+            bact = __ballot_sync(0xffffffffu, active);
+            if (lane == 0) s_wa[warp] = __popc(bact);
+            __syncthreads();
+            // ---- z_t over this CTA's active atoms, G lanes per atom (G: a power of two up to 32, as many
+            // as the atoms leave, the auxiliary warp apart), while the auxiliary warp takes the gap
+            int offa = 0, nact = 0;
+            for (int w = 0; w < kSmThreads / 32; w++) {
+                const int cw = s_wa[w];
+                offa += w < warp ? cw : 0;
+                nact += cw;
+            }
+            apos = offa + __popc(bact & ((1u << lane) - 1u));
+            if (active) s_al[apos] = a;
+            const int nlanes = aux > 0 ? kSmThreads - 32 : kSmThreads;
+            int G = 1;
+            while (G < 32 && 2 * G * nact <= nlanes) G *= 2;
+            __syncthreads();
+            if (warp == aux) gap_chain(corr != 0);
+            correlate(G, nact);
+            __syncthreads();
         }
-        const int apos = offa + __popc(bact & ((1u << lane) - 1u));
-        if (active) s_al[apos] = a;
-        const int nlanes = aux > 0 ? kSmThreads - 32 : kSmThreads;
-        int G = 1;
-        while (G < 32 && 2 * G * nact <= nlanes) G *= 2;
-        __syncthreads();
-        if (warp == aux) {  // (while the other warps correlate)
-            // lanes 0..2: the three row sums over the row warps in order; lane 3: ||xbar_{t-1}||_1 from
-            // the C parts in rank order, minus the corrections; lane 0 then: the gap of iteration t-1
-            Dot2f acc;
-            if (lane < 3) {
-                for (int w = 0; w < nwr; w++) dot2_merge(acc, s_red[w][2 * lane], s_red[w][2 * lane + 1]);
-            } else if (lane == 3) {
-#pragma unroll
-                for (int c = 0; c < kSmMaxC; c++)
-                    if (c < C) dot2_merge(acc, l1p_s[c], l1p_c[c]);
-                if (corr) {
-                    float rs[kSmMaxC], rcs[kSmMaxC];
-#pragma unroll
-                    for (int c = 0; c < kSmMaxC; c++) {
-                        if (c < C) {
-                            const SmScal* r = cl.map_shared_rank(&ssc[2], c);
-                            rs[c] = -r->l1s;
-                            rcs[c] = -r->l1c;
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < kSmMaxC; c++)
-                        if (c < C) dot2_merge(acc, rs[c], rcs[c]);
-                }
-            }
-            const double sv = acc.value();
-            const double alpha = __shfl_sync(0xffffffffu, sv, 0), beta = __shfl_sync(0xffffffffu, sv, 1);
-            const double rr = __shfl_sync(0xffffffffu, sv, 2), l1v = __shfl_sync(0xffffffffu, sv, 3);
-            if (lane == 0) {
-                int stop = 0;
-                if (t > 1) {
-                    // P(xbar_{t-1}) - Dual(mu theta_{t-1}), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                    const double primal = fma(lam, l1v, 0.5 * rr);
-                    const double gap = fma(hlam2, s_sc[19], primal - hyy);
-                    s_out_gap = gap;
-                    s_out_primal = primal;
-                    stop = (P.tol > 0.0 && gap <= tol_abs && (t - 1) % P.gap_every == 0) || (t - 1 >= P.max_iter);
-                }
-                s_si[2] = stop;
-                s_sc[4] = alpha;  // of theta_t, for the test of iteration t
-                s_sc[5] = beta;
-            }
-        }
-        {
-            const int j = tid / G, q = tid - j * G;
-            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
-            if (j < nact) {
-                const int aj = s_al[j];
-                int r = q;
-                for (; r + G < N; r += 2 * G) {
-                    sm_dot_step(s0, c0, Dh[r * pitch + aj], Dl[r * pitch + aj], s_th[r]);
-                    sm_dot_step(s1, c1, Dh[(r + G) * pitch + aj], Dl[(r + G) * pitch + aj], s_th[r + G]);
-                }
-                if (r < N) sm_dot_step(s0, c0, Dh[r * pitch + aj], Dl[r * pitch + aj], s_th[r]);
-            }
-            Dot2f acc;
-            acc.s = s0;
-            acc.c = c0;
-            dot2_merge(acc, s1, c1);
-            for (int o = 1; o < G; o <<= 1) {
-                const float os = __shfl_xor_sync(0xffffffffu, acc.s, o), oc = __shfl_xor_sync(0xffffffffu, acc.c, o);
-                dot2_merge(acc, os, oc);
-            }
-            if (q == 0 && j < nact) s_z[j] = ff_two_sum(acc.s, acc.c);
-        }
-        __syncthreads();
         // x_t = soft(ubar_{t-1} - z / L, lambda / L) and u_t (Table 1)
         FF xn = x_a, un = u_a, az = FF{0.f, 0.f};
         if (active) {
