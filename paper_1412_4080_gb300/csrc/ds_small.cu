@@ -398,6 +398,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
     FF* const pv = reinterpret_cast<FF*>(Dl + (size_t)N * pitch);
     auto slot = [&](int k) -> FF* { return pv + (size_t)k * 2 * N; };
     __shared__ SmScal ssc[3];
+    __shared__ double s_prim;  // the primal value of the gap, from warp 6 to warp 7 (overlapped order)
     __shared__ double s_lf;
     __shared__ long long s_cols_corr, s_cols_synth;
     __shared__ double s_out_gap, s_out_primal;
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
         // the auxiliary lane's parts of ||xbar_{t-1}||_1, fetched first (merged in the gap chain) so that
         // their loads overlap the Lemma 8 chain of the same warp
         float l1p_s[kSmMaxC], l1p_c[kSmMaxC];
-        if (warp == aux && lane == 3) {
+        if ((warp == aux || (ovl && warp == aux - 1)) && lane == 3) {
 #pragma unroll
             for (int c = 0; c < kSmMaxC; c++) {
                 if (c < C) {
@@ -629,10 +630,11 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
         }
         if (tid == 0 && t == 1) s_si[3] = 0;
 
-        // the duality gap of iteration t-1 and the stopping rule, on the auxiliary warp: lanes 0..2 sum
-        // the three row sums over the row warps in order, lane 3 ||xbar_{t-1}||_1 from the C parts in rank
-        // order (minus the parts of a correction exchange), lane 0 then takes the gap
-        auto gap_chain = [&](bool with_corr) {
+        // the duality gap of iteration t-1 and the stopping rule: lanes 0..2 of one warp sum the three row
+        // sums over the row warps in order, lane 3 ||xbar_{t-1}||_1 from the C parts in rank order (minus
+        // the parts of a correction exchange), lane 0 then takes the primal value; the gap needs the
+        // nominal Lemma 8 point as well (s_sc[19], from the gap thread)
+        auto primal_part = [&](bool with_corr) -> double {
             Dot2f acc;
             if (lane < 3) {
                 for (int w = 0; w < nwr; w++) dot2_merge(acc, s_red[w][2 * lane], s_red[w][2 * lane + 1]);
@@ -658,20 +660,29 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
             const double sv = acc.value();
             const double alpha = __shfl_sync(0xffffffffu, sv, 0), beta = __shfl_sync(0xffffffffu, sv, 1);
             const double rr = __shfl_sync(0xffffffffu, sv, 2), l1v = __shfl_sync(0xffffffffu, sv, 3);
+            double primal = 0.0;
             if (lane == 0) {
-                int stop = 0;
-                if (t > 1) {
-                    // P(xbar_{t-1}) - Dual(mu theta_{t-1}), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
-                    const double primal = fma(lam, l1v, 0.5 * rr);
-                    const double gap = fma(hlam2, s_sc[19], primal - hyy);
-                    s_out_gap = gap;
-                    s_out_primal = primal;
-                    stop = (P.tol > 0.0 && gap <= tol_abs && (t - 1) % P.gap_every == 0) || (t - 1 >= P.max_iter);
-                }
-                s_si[2] = stop;
+                // P(xbar_{t-1}) = lambda ||xbar_{t-1}||_1 + 1/2 ||D xbar_{t-1} - y||^2
+                primal = fma(lam, l1v, 0.5 * rr);
                 s_sc[4] = alpha;  // of theta_t, for the test of iteration t
                 s_sc[5] = beta;
             }
+            return primal;
+        };
+        auto gap_final = [&](double primal) {  // lane 0
+            int stop = 0;
+            if (t > 1) {
+                // P(xbar_{t-1}) - Dual(mu theta_{t-1}), Dual(v) = 1/2||y||^2 - lambda^2/2 ||v - y/lambda||^2
+                const double gap = fma(hlam2, s_sc[19], primal - hyy);
+                s_out_gap = gap;
+                s_out_primal = primal;
+                stop = (P.tol > 0.0 && gap <= tol_abs && (t - 1) % P.gap_every == 0) || (t - 1 >= P.max_iter);
+            }
+            s_si[2] = stop;
+        };
+        auto gap_chain = [&](bool with_corr) {
+            const double primal = primal_part(with_corr);
+            if (lane == 0) gap_final(primal);
         };
         // z_t = d^T theta_t over the listed atoms s_al[0..nact), G lanes per atom; each lane sums rows
         // q, q + G, ... on two chains and the G partial sums merge by a fixed shuffle tree
@@ -702,12 +713,12 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
         int apos = 0;
         if (ovl) {
             if (warp != aux) {
-                named_arrive(2, kSmThreads);  // the row sums, to the auxiliary warp
-                // the atoms active before the test of iteration t-1, correlated while the auxiliary warp
-                // runs the Lemma 8 chain and the gap; those the test screens then drop their z
+                // the atoms active before the test of iteration t-1, correlated by warps 0..5 while warp 7
+                // runs the Lemma 8 chain and warp 6 the primal part of the gap; those the test screens then
+                // drop their z
                 bact = __ballot_sync(0xffffffffu, active);
                 if (lane == 0) s_wa[warp] = __popc(bact);
-                named_sync(1, kOvlThreads);
+                named_sync(1, kOvlThreads);  // also publishes the row sums to warp 6
                 int offa = 0, nact = 0;
                 for (int w = 0; w < kSmThreads / 32; w++) {
                     const int cw = s_wa[w];
@@ -717,12 +728,18 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
                 apos = offa + __popc(bact & ((1u << lane) - 1u));
                 if (active) s_al[apos] = a;
                 int G = 1;
-                while (G < 32 && 2 * G * nact <= kOvlThreads) G *= 2;
+                while (G < 32 && 2 * G * nact <= kOvlThreads - 32) G *= 2;
                 named_sync(1, kOvlThreads);
-                correlate(G, nact);
+                if (warp < aux - 1) {
+                    correlate(G, nact);
+                } else {
+                    const double primal = primal_part(false);
+                    if (lane == 0) s_prim = primal;
+                    named_arrive(2, 64);  // the primal value, to warp 7
+                }
             } else {
-                named_sync(2, kSmThreads);  // the row sums of theta_t
-                gap_chain(false);
+                named_sync(2, 64);  // warp 6's primal value; s_sc[19] is this warp's own
+                if (lane == 0) gap_final(s_prim);
             }
         }
         __syncthreads();
