@@ -28,12 +28,13 @@
 //       iteration t-1 and the stopping rule; then the proximal step and the
 //       FISTA extrapolation.
 //
-// When a CTA has a warp with neither atoms nor rows and the test is a sphere
-// test, (3) does not wait for the test: the other warps correlate the atoms
-// that were active before it while the spare warp runs the Lemma 8 chain,
-// the radius and the gap (FP64, one dependent operation at a time), and the
-// atoms the test then screens drop their z.  After a correction exchange the
-// correlation is redone on the corrected theta_t.
+// When warps 6 and 7 of a CTA hold neither atoms nor rows and the test is a
+// sphere test, (3) does not wait for the test: warps 0..5 correlate the atoms
+// that were active before it while warp 7 runs the Lemma 8 chain and the
+// radius (FP64, one dependent operation at a time) and warp 6 the primal half
+// of the gap; the atoms the test then screens drop their z.  After a
+// correction exchange the correlation and the gap are redone on the corrected
+// theta_t.
 //
 // Every CTA computes the scalars from the same data in the same order, and the
 // loop ends on rank 0's decision, which every CTA reads: all CTAs pass the
@@ -422,11 +423,12 @@ __global__ void __launch_bounds__(kSmThreads, 1) small_kernel(const SolveP<doubl
     // (with a spare warp both chains run in it, on lanes 0 and 1, as one instruction stream)
     const int t_rad = spare ? kSmThreads - 32 : 0, t_gap = spare ? kSmThreads - 31 : 32;
     const int aux = spare ? kSmThreads / 32 - 1 : 0;
-    // with a spare warp and a sphere test (which rarely needs a correction exchange), the other warps
-    // correlate the atoms that were active before the test of iteration t-1 while the spare warp runs
-    // the Lemma 8 chain and the duality gap; the atoms that test screens then drop their z
+    // with the spare warps and a sphere test (which rarely needs a correction exchange), warps 0..5
+    // correlate the atoms that were active before the test of iteration t-1 while warp 7 runs the
+    // Lemma 8 chain and warp 6 the primal half of the duality gap; the atoms that test screens then
+    // drop their z
     const bool ovl = spare && !(dyn && test == 3);
-    constexpr int kOvlThreads = kSmThreads - 32;  // the correlating warps of the overlapped order
+    constexpr int kOvlThreads = kSmThreads - 32;  // warps 0..6: the list of the overlapped order
     // (thr - eps)^2 rounded up to FP32, for the conservative "may screen a nonzero atom" check
     const float q2f_a = q2_a > 0.0 ? __double2float_ru(q2_a) : 0.f;
     int stop_t = 0, t_last = 1;
